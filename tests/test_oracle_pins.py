@@ -1,0 +1,428 @@
+"""Pins of the FP64 oracle to facts fixed by the paper and by mathematics.
+
+Each test checks the oracle against something it does not compute itself:
+closed forms (Appendix A modified wavenumbers, the RK amplification
+polynomial), dense matrices assembled here entry by entry from Appendix B,
+brute-force dense solves on 8^3 grids, and the regularised-delta moment
+identities.  A dropped term, a wrong sign, a transposed axis or a wrong index
+in the oracle fails at least one of them.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ibm_oracle as O
+from paper_2406_19920_gb300 import synth
+
+
+def _grid(nx, ny, nz, Lx=2 * math.pi, Ly=2.0, Lz=2 * math.pi):
+    return (nx, ny, nz, Lx / nx, Ly / ny, Lz / nz)
+
+
+# ---------------------------------------------------------------------------
+# dense matrices written from Appendix B (independent of the oracle)
+# ---------------------------------------------------------------------------
+
+def _periodic_1d(n, h):
+    A = np.zeros((n, n))
+    for i in range(n):
+        A[i, i] = -2.0 / h ** 2
+        A[i, (i + 1) % n] += 1.0 / h ** 2
+        A[i, (i - 1) % n] += 1.0 / h ** 2
+    return A
+
+
+def _wall_1d(n, h, bc):
+    """Appendix B pencil matrix without the periodic part (kappa' = 0).
+
+    Neumann: corners A3 + A2 (A3 = -2/h^2, A2 = 1/h^2).
+    Cell Dirichlet (alpha = 2): corners A11 = A1 - A2.
+    Face Dirichlet (alpha = 1): corners A11 = A1, n-1 interior faces.
+    """
+    A2 = 1.0 / h ** 2
+    A1 = -2.0 / h ** 2
+    m = n - 1 if bc == O.FACE_DIRICHLET else n
+    A = np.zeros((m, m))
+    for i in range(m):
+        A[i, i] = A1
+        if i > 0:
+            A[i, i - 1] = A2
+        if i < m - 1:
+            A[i, i + 1] = A2
+    if bc == O.NEUMANN:
+        A[0, 0] = A[-1, -1] = A1 + A2
+    elif bc == O.CELL_DIRICHLET:
+        A[0, 0] = A[-1, -1] = A1 - A2
+    return A
+
+
+def _dense_laplacian(grid, bc):
+    """Kronecker sum for the (y, z, x) C-order unknown vector."""
+    nx, ny, nz, hx, hy, hz = grid
+    Ax, Az, Ay = _periodic_1d(nx, hx), _periodic_1d(nz, hz), _wall_1d(ny, hy, bc)
+    Iy, Iz, Ix = np.eye(Ay.shape[0]), np.eye(nz), np.eye(nx)
+    return (np.kron(np.kron(Ay, Iz), Ix) + np.kron(np.kron(Iy, Az), Ix)
+            + np.kron(np.kron(Iy, Iz), Ax))
+
+
+def _pack(f, bc):
+    return (f[1:] if bc == O.FACE_DIRICHLET else f).ravel()
+
+
+def _unpack(x, grid, bc):
+    nx, ny, nz = grid[:3]
+    if bc == O.FACE_DIRICHLET:
+        out = np.zeros((ny, nz, nx))
+        out[1:] = x.reshape(ny - 1, nz, nx)
+        return out
+    return x.reshape(ny, nz, nx)
+
+
+GRIDS_8 = [_grid(8, 8, 8), _grid(8, 8, 8, Lx=1.0, Ly=3.0, Lz=0.5), _grid(6, 8, 4, Lx=1.3, Ly=0.7, Lz=2.1)]
+
+
+# ---------------------------------------------------------------------------
+# Appendix A: modified wavenumber
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("n,h", [(8, 0.3), (32, 2 * math.pi / 32), (48, 0.01)])
+def test_modified_wavenumber_is_stencil_eigenvalue(n, h):
+    """The 3-point stencil on exp(i kappa x) returns -kappa'^2 of Appendix A."""
+    x = np.arange(n) * h
+    for m in range(n):
+        kappa = 2 * math.pi * m / (n * h)
+        f = np.exp(1j * kappa * x)
+        d2 = (np.roll(f, -1) - 2 * f + np.roll(f, 1)) / h ** 2
+        k2 = O.modified_wavenumber_sq(kappa * h, h)
+        assert np.allclose(d2, -k2 * f, rtol=0, atol=1e-9 * (4 / h ** 2))
+        # long waves: kappa'^2 -> kappa^2 at second order
+    kappa = 2 * math.pi / (n * h)
+    assert abs(O.modified_wavenumber_sq(kappa * h, h) - kappa ** 2) <= kappa ** 4 * h ** 2 / 12 * 1.01
+
+
+@pytest.mark.parametrize("bc", [O.NEUMANN, O.CELL_DIRICHLET, O.FACE_DIRICHLET])
+@pytest.mark.parametrize("n", [8, 9, 16])
+def test_wall_basis_diagonalises_appendix_b_matrix(bc, n):
+    h = 0.37
+    A = _wall_1d(n, h, bc)
+    Q, th = O.wall_basis(n, bc)
+    Qi = Q[1:] if bc == O.FACE_DIRICHLET else Q
+    assert np.allclose(Qi.T @ Qi, np.eye(Qi.shape[1]), atol=1e-13)
+    lam = O.modified_wavenumber_sq(th, h)
+    assert np.allclose(A @ Qi, -Qi * lam[None, :], atol=1e-10 / h ** 2)
+
+
+@pytest.mark.parametrize("n", [8, 9, 12])
+def test_fourier_basis_orthonormal_eigen(n):
+    h = 0.2
+    Q, th = O.fourier_basis(n)
+    assert np.allclose(Q.T @ Q, np.eye(n), atol=1e-13)
+    A = _periodic_1d(n, h)
+    assert np.allclose(A @ Q, -Q * O.modified_wavenumber_sq(th, h)[None, :], atol=1e-10 / h ** 2)
+
+
+# ---------------------------------------------------------------------------
+# Operators and solves against dense matrices (8^3 brute force)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("grid", GRIDS_8)
+@pytest.mark.parametrize("bc", [O.NEUMANN, O.CELL_DIRICHLET, O.FACE_DIRICHLET])
+def test_laplacian_matches_dense(grid, bc):
+    A = _dense_laplacian(grid, bc)
+    f = np.random.default_rng(3).standard_normal((grid[1], grid[2], grid[0]))
+    got = O.laplacian(f, grid, bc)
+    want = _unpack(A @ _pack(f, bc), grid, bc)
+    assert np.allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("grid", GRIDS_8)
+def test_poisson_matches_dense_gaussian_elimination(grid):
+    nx, ny, nz = grid[:3]
+    A = _dense_laplacian(grid, O.NEUMANN)
+    b = np.random.default_rng(4).standard_normal((ny, nz, nx))
+    # singular on constants: append the mean-zero constraint and solve the
+    # bordered system [A 1; 1^T 0] (exact for a compatible rhs)
+    N = A.shape[0]
+    B = np.zeros((N + 1, N + 1))
+    B[:N, :N] = A
+    B[:N, N] = 1.0
+    B[N, :N] = 1.0
+    rhs = np.concatenate([(b - b.mean()).ravel(), [0.0]])
+    x = np.linalg.solve(B, rhs)
+    assert abs(x[N]) < 1e-10            # compatible rhs: zero multiplier
+    phi, mean_b = O.poisson_solve(b, grid)
+    assert abs(mean_b - b.mean()) < 1e-15
+    assert O.rel_l2(phi, x[:N].reshape(ny, nz, nx)) < 1e-12
+
+
+@pytest.mark.parametrize("grid", GRIDS_8)
+@pytest.mark.parametrize("bc", [O.NEUMANN, O.CELL_DIRICHLET, O.FACE_DIRICHLET])
+@pytest.mark.parametrize("c", [1e-3, 0.25])
+def test_helmholtz_matches_dense(grid, bc, c):
+    nx, ny, nz = grid[:3]
+    A = _dense_laplacian(grid, bc)
+    r = np.random.default_rng(5).standard_normal((ny, nz, nx))
+    M = np.eye(A.shape[0]) - c * A
+    x = np.linalg.solve(M, _pack(r, bc))
+    u = O.helmholtz_solve(r, grid, c, bc)
+    assert O.rel_l2(u, _unpack(x, grid, bc)) < 1e-12
+    if bc == O.FACE_DIRICHLET:
+        assert np.all(u[0] == 0.0)
+
+
+def test_manufactured_eigenfunction_exact():
+    """Discrete eigenfunction rhs: the solve is exact to round-off."""
+    g = _grid(32, 32, 32)
+    nx, ny, nz, hx, hy, hz = g
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    mx, my, mz = 3, 5, 2
+    phi = (np.cos(math.pi * my * (j + 0.5) / ny)[:, None, None]
+           * np.sin(2 * math.pi * mz * k / nz)[None, :, None]
+           * np.cos(2 * math.pi * mx * i / nx)[None, None, :])
+    lam = (O.modified_wavenumber_sq(2 * math.pi * mx / nx, hx)
+           + O.modified_wavenumber_sq(math.pi * my / ny, hy)
+           + O.modified_wavenumber_sq(2 * math.pi * mz / nz, hz))
+    b = -lam * phi
+    got, _ = O.poisson_solve(b, g)
+    assert O.rel_l2(got, phi) < 1e-13
+    assert np.abs(O.laplacian(phi, g, O.NEUMANN) - b).max() < 1e-12 * lam
+    # Helmholtz on a cell-Dirichlet mode
+    ud = (np.sin(math.pi * 3 * (j + 0.5) / ny)[:, None, None]
+          * np.cos(2 * math.pi * 1 * k / nz)[None, :, None]
+          * np.sin(2 * math.pi * 4 * i / nx)[None, None, :])
+    lam_d = (O.modified_wavenumber_sq(2 * math.pi * 4 / nx, hx)
+             + O.modified_wavenumber_sq(math.pi * 3 / ny, hy)
+             + O.modified_wavenumber_sq(2 * math.pi * 1 / nz, hz))
+    c = 0.01
+    got = O.helmholtz_solve((1 + c * lam_d) * ud, g, c, O.CELL_DIRICHLET)
+    assert O.rel_l2(got, ud) < 1e-13
+
+
+def test_residual_and_symmetry_32():
+    g = _grid(32, 32, 32)
+    b, _ = synth.rhs_eigen_sum(32, 32, 32, workload=0)
+    phi, _ = O.poisson_solve(b, g)
+    assert O.normalised_residual(phi, b, g) <= 1e-12
+    r = np.random.default_rng(6)
+    for bc in (O.NEUMANN, O.CELL_DIRICHLET, O.FACE_DIRICHLET):
+        x, y = r.standard_normal((2, 32, 32, 32))
+        if bc == O.FACE_DIRICHLET:
+            x[0] = y[0] = 0
+        lhs = np.vdot(O.laplacian(x, g, bc), y)
+        rhs = np.vdot(x, O.laplacian(y, g, bc))
+        assert abs(lhs - rhs) <= 1e-12 * abs(lhs) + 1e-9
+
+
+def test_pin_and_mean_differ_by_constant():
+    g = _grid(16, 16, 16)
+    b = np.random.default_rng(7).standard_normal((16, 16, 16))
+    pm, _ = O.poisson_solve(b, g, "mean")
+    pp, _ = O.poisson_solve(b, g, "pin")
+    d = pp - pm
+    assert np.ptp(d) < 1e-12
+    assert abs(pp[0].mean()) < 1e-13
+    assert abs(pm.mean()) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Divergence, gradient, projection, advection
+# ---------------------------------------------------------------------------
+
+def test_div_grad_is_neumann_laplacian():
+    g = _grid(12, 10, 8, Lx=1.0, Ly=2.0, Lz=3.0)
+    phi = np.random.default_rng(8).standard_normal((10, 8, 12))
+    assert np.allclose(O.divergence(*O.gradient(phi, g), g), O.laplacian(phi, g, O.NEUMANN), atol=1e-9)
+
+
+def test_projection_makes_divergence_free():
+    g = _grid(16, 16, 16)
+    r = np.random.default_rng(9)
+    u, v, w = r.standard_normal((3, 16, 16, 16))
+    v[0] = 0
+    k = 0.37
+    d = O.divergence(u, v, w, g)
+    phi, _ = O.poisson_solve(d / k, g)
+    G = O.gradient(phi, g)
+    un, vn, wn = u - k * G[0], v - k * G[1], w - k * G[2]
+    dn = O.divergence(un, vn, wn, g)
+    assert np.abs(dn).max() <= 1e-12 * np.abs(d).max()
+    assert np.all(vn[0] == 0)
+
+
+def test_synthetic_velocity_is_discretely_divergence_free():
+    g = _grid(24, 16, 20)
+    u, v, w = synth.div_free_velocity(g, workload=1, kmax=6)
+    d = O.divergence(u, v, w, g)
+    assert np.abs(d).max() < 1e-10 * (np.abs(u).max() / g[3])
+
+
+def test_advection_conserves_momentum_and_energy():
+    """Divergence-form MAC advection: x/z momentum fluxes telescope and, for a
+    discretely divergence-free field with v = 0 on the walls, the kinetic
+    energy production sum u.N vanishes (Morinishi et al. 1998)."""
+    g = _grid(16, 12, 8, Lx=1.0, Ly=1.5, Lz=0.8)
+    u, v, w = synth.div_free_velocity(g, workload=2, kmax=5)
+    Nu, Nv, Nw = O.advection(u, v, w, g)
+    scale = np.abs(Nu).max()
+    assert abs(Nu.sum()) < 1e-11 * scale * Nu.size
+    assert abs(Nw.sum()) < 1e-11 * scale * Nw.size
+    e = np.vdot(u, Nu) + np.vdot(v[1:], Nv[1:]) + np.vdot(w, Nw)
+    assert abs(e) < 1e-11 * scale * np.abs(u).sum()
+    # a non-solenoidal field does produce energy (the test can fail)
+    r = np.random.default_rng(1)
+    a, b, c = r.standard_normal((3,) + u.shape)
+    b[0] = 0
+    Na = O.advection(a, b, c, g)
+    assert abs(np.vdot(a, Na[0]) + np.vdot(b[1:], Na[1][1:]) + np.vdot(c, Na[2])) > 1e-3
+
+
+def test_advection_of_uniform_shear_is_zero():
+    """u = U(y, z) with v = w = 0 is a steady Euler solution: N = 0."""
+    g = _grid(8, 8, 8)
+    u = np.random.default_rng(2).standard_normal((8, 8, 1)) * np.ones((8, 8, 8))
+    z = np.zeros_like(u)
+    for comp in O.advection(u, z, z, g):
+        assert np.abs(comp).max() < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# Regularised delta kernels (Eq. 2b, 2d; Roma et al. 1999, Peskin 2002)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("kernel,sum_sq,support", [(O.ROMA3, 0.5, 1.5), (O.PESKIN4, 3.0 / 8.0, 2.0)])
+def test_delta_moments(kernel, sum_sq, support):
+    r = np.random.default_rng(10).uniform(-0.5, 0.5, 2000)
+    j = np.arange(-3, 4)
+    phi = O.delta_1d(r[:, None] - j[None, :], kernel)
+    assert np.allclose(phi.sum(1), 1.0, atol=1e-14)                      # partition of unity
+    assert np.allclose(((r[:, None] - j[None, :]) * phi).sum(1), 0, atol=1e-14)   # first moment
+    assert np.allclose((phi ** 2).sum(1), sum_sq, atol=1e-14)            # sum of squares
+    assert np.all(O.delta_1d(np.array([support + 1e-9, -support - 1e-9, 3.0]), kernel) == 0)
+    assert np.all(phi >= 0)
+
+
+def _sphere(g, n, workload=0):
+    nx, ny, nz, hx, hy, hz = g
+    Lx, Ly, Lz = nx * hx, ny * hy, nz * hz
+    X, dV = synth.fibonacci_sphere(n, 0.25 * Ly / 2 * 2, (Lx / 2, Ly / 2, Lz / 2), hx)
+    return X, dV
+
+
+@pytest.mark.parametrize("kernel", [O.ROMA3, O.PESKIN4])
+def test_interp_exact_for_linear_fields(kernel):
+    g = _grid(32, 32, 32)
+    nx, ny, nz, hx, hy, hz = g
+    X, _ = _sphere(g, 300)
+    j, k, i = np.meshgrid(np.arange(ny), np.arange(nz), np.arange(nx), indexing="ij")
+    a, bx, by, bz = 0.7, 0.3, -1.1, 0.45
+    origins = {0: (0.0, 0.5, 0.5), 1: (0.5, 0.0, 0.5), 2: (0.5, 0.5, 0.0)}
+    fields = []
+    for c in range(3):
+        ox, oy, oz = origins[c]
+        fields.append(a + bx * (i + ox) * hx + by * (j + oy) * hy + bz * (k + oz) * hz)
+    fields[1][0] = 0.0
+    U = O.interp(X, *fields, g, kernel)
+    exact = a + bx * X[:, 0] + by * X[:, 1] + bz * X[:, 2]
+    for c in range(3):
+        assert np.allclose(U[:, c], exact, atol=1e-12)
+
+
+@pytest.mark.parametrize("kernel", [O.ROMA3, O.PESKIN4])
+def test_spread_conserves_force_and_moment_and_is_adjoint(kernel):
+    g = _grid(32, 32, 32)
+    nx, ny, nz, hx, hy, hz = g
+    X, dV = _sphere(g, 500)
+    F = synth.marker_forces(500, workload=0)
+    fu, fv, fw = O.spread(X, F, dV, g, kernel)
+    h3 = hx * hy * hz
+    origins = {0: (0.0, 0.5, 0.5), 1: (0.5, 0.0, 0.5), 2: (0.5, 0.5, 0.0)}
+    j, k, i = np.meshgrid(np.arange(ny), np.arange(nz), np.arange(nx), indexing="ij")
+    for c, f in enumerate((fu, fv, fw)):
+        assert abs(f.sum() * h3 - (F[:, c] * dV).sum()) < 1e-12 * np.abs(F[:, c] * dV).sum()
+        ox, oy, oz = origins[c]
+        xs = (i + ox) * hx
+        assert abs((xs * f).sum() * h3 - (X[:, 0] * F[:, c] * dV).sum()) < 1e-11
+    r = np.random.default_rng(11)
+    u, v, w = r.standard_normal((3, ny, nz, nx))
+    v[0] = 0.0
+    U = O.interp(X, u, v, w, g, kernel)
+    lhs = (dV[:, None] * U * F).sum()
+    rhs = h3 * (np.vdot(u, fu) + np.vdot(v, fv) + np.vdot(w, fw))
+    assert abs(lhs - rhs) < 1e-12 * abs(lhs) + 1e-12
+
+
+def test_interp_spread_periodic_wrap():
+    """A marker at x = 0 sees the same neighbourhood as one at x = Lx."""
+    g = _grid(16, 16, 16)
+    nx, ny, nz, hx, hy, hz = g
+    r = np.random.default_rng(12)
+    u, v, w = r.standard_normal((3, ny, nz, nx))
+    v[0] = 0
+    X1 = np.array([[0.01, 1.0, 0.02]])
+    X2 = X1 + np.array([[nx * hx, 0.0, nz * hz]])
+    assert np.allclose(O.interp(X1, u, v, w, g), O.interp(X2, u, v, w, g), atol=1e-12)
+
+
+# ---------------------------------------------------------------------------
+# RK coefficients (Rai & Moin) and one RK stage (Eq. 2a-2h)
+# ---------------------------------------------------------------------------
+
+def test_rk_coefficients_third_order_explicit_and_consistent():
+    a, b, gm, zt = map(np.array, (O.RK_ALPHA, O.RK_BETA, O.RK_GAMMA, O.RK_ZETA))
+    assert np.allclose(gm + zt, a + b)
+    assert abs((a + b).sum() - 1.0) < 1e-15
+    # explicit part on y' = lam y: stability polynomial 1 + z + z^2/2 + z^3/6
+    for z in (0.1, -0.3, 0.05 + 0.2j):
+        y, Nprev = 1.0 + 0j, 0.0
+        for n in range(3):
+            N = -z * y              # advection-like term with du/dt = -N
+            y = y + (-gm[n] * N - zt[n] * Nprev)
+            Nprev = N
+        assert abs(y - (1 + z + z ** 2 / 2 + z ** 3 / 6)) < 1e-14
+    # implicit part: second order, prod (1 + a z)/(1 - b z) = e^z + O(z^3)
+    for z in (1e-2, -2e-2):
+        R = np.prod((1 + a * z) / (1 - b * z))
+        assert abs(R - math.exp(z)) < 0.2 * abs(z) ** 3
+
+
+@pytest.mark.parametrize("stage", [1, 2, 3])
+def test_rk_stage_viscous_mode_closed_form(stage):
+    """u = sin(pi m (j+1/2)/ny) cos(2 pi q k / nz), v = w = 0, p = 0, no
+    markers: N = 0, div u = 0, so Eq. 2a-2h reduce to
+    u^n = u (1 - alpha nu dt lam) / (1 + beta nu dt lam) and phi = p^n = 0."""
+    g = _grid(16, 16, 16)
+    nx, ny, nz, hx, hy, hz = g
+    j, k = np.arange(ny), np.arange(nz)
+    m, q = 2, 3
+    u = (np.sin(math.pi * m * (j + 0.5) / ny)[:, None, None]
+         * np.cos(2 * math.pi * q * k / nz)[None, :, None]) * np.ones((1, 1, nx))
+    z = np.zeros_like(u)
+    lam = O.modified_wavenumber_sq(math.pi * m / ny, hy) + O.modified_wavenumber_sq(2 * math.pi * q / nz, hz)
+    dt, nu = 1e-2, 0.3
+    st = dict(u=u, v=z.copy(), w=z.copy(), p=z.copy(), N_prev=(z, z, z), t=0.0)
+    mk = dict(X0=np.zeros((0, 3)), dV=np.zeros(0), kind=O.MOTION_STATIC, params=())
+    new, info = O.rk_stage(st, mk, stage, dt, nu, g)
+    a, b = O.RK_ALPHA[stage - 1], O.RK_BETA[stage - 1]
+    want = u * (1 - a * nu * dt * lam) / (1 + b * nu * dt * lam)
+    assert O.rel_l2(new["u"], want) < 1e-13
+    assert np.abs(new["v"]).max() < 1e-13 and np.abs(new["w"]).max() < 1e-13
+    assert np.abs(new["p"]).max() < 1e-10
+    assert abs(new["t"] - (a + b) * dt) < 1e-16
+
+
+def test_rk_stage_projection_and_forcing_invariants():
+    g = _grid(16, 16, 16)
+    nx, ny, nz, hx, hy, hz = g
+    u, v, w = synth.div_free_velocity(g, workload=3, kmax=4)
+    z = np.zeros_like(u)
+    X0, dV = synth.fibonacci_sphere(200, 0.25, (math.pi, 1.0, math.pi), hx)
+    st = dict(u=u, v=v, w=w, p=z.copy(), N_prev=(z, z, z), t=0.0)
+    mk = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=(0.1, 0.0, 0.0))
+    new, info = O.rk_stage(st, mk, 1, 1e-3, 1e-2, g)
+    d = O.divergence(new["u"], new["v"], new["w"], g)
+    d0 = O.divergence(*info["ustar"], g)
+    assert np.abs(d).max() <= 1e-11 * max(1.0, np.abs(d0).max())
+    # Eq. 2c: F = (U^d - U^e)/dt
+    assert np.allclose(info["F"], (np.array([0.1, 0, 0])[None, :] - info["Ue"]) / 1e-3)
