@@ -1,0 +1,255 @@
+/*
+ * ibm.h -- C ABI of libibm, the GB300 (sm_103a) hot path of the immersed-
+ * boundary fractional-step solver of arXiv 2406.19920 ("A Python-based flow
+ * solver for numerical simulations using an immersed boundary method on
+ * single GPUs").
+ *
+ * Problem statement (Sec. 2.1, Eq. 2a-2h): incompressible flow on a uniform
+ * staggered (MAC) grid, periodic in x and z and bounded by no-slip walls in
+ * y, advanced by a three-stage semi-implicit RK scheme with Uhlmann's
+ * direct-forcing immersed boundary.  Each stage needs three Helmholtz solves
+ * (Eq. 2e), one Poisson solve (Eq. 2f), the interpolation / spreading pair
+ * between Eulerian grid and Lagrangian markers (Eq. 2b-2d) and a projection
+ * (Eq. 2g, 2h).  The linear systems are solved directly as in the paper's
+ * doubly periodic branch (Sec. 2.3.3, S1.1/S1.2/S2.1/S2.2): real FFT along x,
+ * complex FFT along z, one tridiagonal (Thomas) solve per Fourier pencil
+ * along y, inverse transforms.
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ * Grid: nx x ny x nz cells, spacings h = {hx, hy, hz}.  nx and nz must be
+ *   2^a 3^b with b <= 1 and 8 <= n <= 512; 8 <= ny <= 1024.
+ * Layout: every field is a dense C array [ny][nz][nx] (x fastest, then z,
+ *   then y) in DEVICE memory, of the plan's precision (float for
+ *   IBM_FP32_REFINED, double for IBM_FP64).
+ *   - cell-centred fields (p, phi, Poisson rhs) at ((i+1/2)hx,(j+1/2)hy,(k+1/2)hz)
+ *   - u on x-faces (i hx, (j+1/2)hy, (k+1/2)hz)
+ *   - w on z-faces ((i+1/2)hx, (j+1/2)hy, k hz)
+ *   - v on y-faces ((i+1/2)hx, j hy, (k+1/2)hz): plane j is face j, plane 0
+ *     is the bottom wall and the top wall face j = ny is not stored.  Both
+ *     wall faces carry v = 0: plane 0 is ignored on input and written as 0.
+ * Markers: positions X and velocities/forces are arrays [n][3] (x, y, z),
+ *   volumes dV are [n], all in device memory, plan precision.  Markers must
+ *   stay in 1.5 hy (3-point kernel) / 2 hy (4-point kernel) of the walls'
+ *   interior; support points beyond the stored planes are dropped.
+ * Ownership: all field and marker pointers belong to the caller; the plan
+ *   owns its workspace, twiddle and eigenvalue tables.
+ * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Every
+ *   call is asynchronous on it, except that when `info` is non-NULL the call
+ *   synchronises the stream before returning so that `info` is filled.
+ * Errors: every entry point returns an IBM_* code and never throws.  Bad
+ *   arguments are rejected with IBM_ERR_ARG before any launch; CUDA failures
+ *   give IBM_ERR_CUDA.  ibm_last_error() returns a thread-local message.
+ * Thread safety: a plan may be used from one host thread / stream at a time.
+ */
+#ifndef IBM_H
+#define IBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct ibm_plan_s *ibm_plan;
+typedef struct ibm_batch_s *ibm_batch;
+typedef struct ibm_server_s *ibm_server;
+
+enum {
+  IBM_OK = 0,
+  IBM_PENDING = 1,
+  IBM_ERR_ARG = -1,
+  IBM_ERR_OOM = -2,
+  IBM_ERR_CUDA = -3,
+  IBM_ERR_TIMEOUT = -4,
+  IBM_ERR_BUSY = -5,
+  IBM_ERR_UNSUPPORTED = -6,
+  IBM_ERR_CANCELLED = -7
+};
+
+/* Domain boundary conditions: periodic x and z, walls in y (the paper's
+ * doubly periodic branch, Sec. 2.3.3, with its wall axis renamed y). */
+enum { IBM_BC_PXZ_WALL_Y = 1 };
+
+/* Precision of fields and of the bulk arithmetic. */
+enum { IBM_FP64 = 0, IBM_FP32_REFINED = 1 };
+
+/* Wall rows of a Helmholtz field (Appendix B). */
+enum {
+  IBM_FIELD_CELL_NEUMANN = 0,   /* cell-centred, ghost = first value        */
+  IBM_FIELD_CELL_DIRICHLET = 1, /* cell-centred no-slip: alpha = 2, A11 = A1 - A2 */
+  IBM_FIELD_FACE_DIRICHLET = 2  /* wall-normal faces: alpha = 1, walls = 0   */
+};
+
+/* Regularised delta kernels (Sec. 2.1 cites Peskin and Roma et al.). */
+enum { IBM_DELTA_ROMA3 = 0, IBM_DELTA_PESKIN4 = 1 };
+
+/* Prescribed marker motion (L2, Sec. 2.3.2). */
+enum { IBM_MOTION_STATIC = 0, IBM_MOTION_TRANSLATE = 1, IBM_MOTION_HEAVE = 2 };
+
+typedef struct {
+  double rel_residual;  /* ||b - A x||_2 / ||b||_2 of the returned x (FP64 sums)  */
+  double removed_mean;  /* Poisson: mean(b) removed to make b compatible          */
+  double div_max;       /* substep: max |D u^n| after projection (float-float)    */
+  double div_before;    /* substep: max |D u*| before projection                  */
+  double t_ms;          /* device time of the call (events), when info is given   */
+  int refine_iters;     /* refinement steps applied                              */
+  int reserved;
+} ibm_info;
+
+/* ---------------------------------------------------------------------------
+ * Plans
+ * ------------------------------------------------------------------------- */
+
+/* Create a plan for an nx x ny x nz grid with spacings h[3] = {hx, hy, hz}.
+ * bc: IBM_BC_PXZ_WALL_Y.  precision: IBM_FP64 or IBM_FP32_REFINED.
+ * refine_iters: iterative-refinement steps on the residual for the FP32 path
+ * (0..4; ignored for FP64).  Allocates the plan's device workspace
+ * (about 4 fields) and its FP64-derived twiddle and modified-wavenumber
+ * tables (Appendix A) on the current device.  Errors: IBM_ERR_ARG for an
+ * unsupported size or spacing, IBM_ERR_OOM when the workspace does not fit. */
+int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3],
+                    int precision, int refine_iters, ibm_plan *out);
+int ibm_plan_destroy(ibm_plan plan);
+/* Select the delta kernel used by ibm_interp / ibm_spread / ibm_substep. */
+int ibm_plan_set_delta(ibm_plan plan, int kernel);
+/* Bytes of device memory the plan holds. */
+size_t ibm_plan_workspace_bytes(ibm_plan plan);
+
+/* Poisson solve, Eq. 2f (S2.1 + S2.2): L_h phi = rhs - mean(rhs) with the
+ * 7-point Laplacian, periodic x/z, homogeneous Neumann y (Appendix B,
+ * A3 + A2 corner rows), mean(phi) = 0.  rhs and phi are [ny][nz][nx]; rhs may
+ * equal phi.  The zero-wavenumber pencil is eliminated in FP64 with the
+ * paper's pin (phi_hat = 0 at the first interior point, Sec. 2.3.3), then
+ * its FP64 mean is removed. */
+int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream,
+                      ibm_info *info);
+
+/* Helmholtz solve, Eq. 2e (S1.1 + S1.2): (I - c L_h) u = rhs, c > 0, with the
+ * wall rows selected by field_bc (Appendix B).  Eq. 2e is this system with
+ * c = beta_n dt / Re.  rhs may equal u. */
+int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs,
+                        void *u, void *stream, ibm_info *info);
+
+/* Interpolation, Eq. 2b: U[m] = sum over the kernel support of u_c(x) *
+ * phi(dx/hx) phi(dy/hy) phi(dz/hz) for each component c on its own staggered
+ * sub-grid, periodic in x and z.  X, U: [n][3]; u, v, w: fields. */
+int ibm_interp(ibm_plan plan, int n, const void *X, const void *u, const void *v,
+               const void *w, void *U, void *stream);
+
+/* Spreading, Eq. 2d: f_c(x) += F_c(X) phi phi phi dV / (hx hy hz), accumulated
+ * with atomics into fu, fv, fw (not cleared first).  X, F: [n][3]; dV: [n]. */
+int ibm_spread(ibm_plan plan, int n, const void *X, const void *F, const void *dV,
+               void *fu, void *fv, void *fw, void *stream);
+
+/* State of the flow for ibm_substep (device pointers, plan precision). */
+typedef struct {
+  void *u, *v, *w, *p; /* velocity on faces and pressure, updated in place   */
+  void *Nu, *Nv, *Nw;  /* advection term of the previous stage; read for the
+                          zeta_n term and overwritten with this stage's      */
+  double t;            /* time at the start of the stage; advanced by
+                          (alpha_n + beta_n) dt                              */
+} ibm_state;
+
+/* Lagrangian markers for ibm_substep (device pointers, plan precision). */
+typedef struct {
+  int n;
+  const void *X0; /* [n][3] reference positions                          */
+  const void *dV; /* [n] volume of each marker                            */
+  void *X;        /* [n][3] out: positions at the stage time (L2)         */
+  void *Ud;       /* [n][3] out: surface velocity at the stage time (L2)  */
+  void *F;        /* [n][3] out: Lagrangian force of the stage, or NULL   */
+  int motion;     /* IBM_MOTION_*                                         */
+  double params[4]; /* TRANSLATE: (Ux,Uy,Uz); HEAVE: (amplitude, period) */
+} ibm_markers;
+
+/* One RK stage (rk_stage = 1, 2, 3) of Eq. 2a-2h with the low-storage
+ * coefficients of Rai & Moin (cited in Sec. 2.1; the paper does not print
+ * them): E1 explicit terms, L2 marker update at the stage start time, L1
+ * interpolation + force + spreading, three Helmholtz solves, divergence,
+ * Poisson solve, projection and pressure update (E3).  nu = 1/Re.
+ * Uses the plan's workspace; the plan precision sets the field type. */
+int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu,
+                ibm_markers *mk, void *stream, ibm_info *info);
+
+/* ---------------------------------------------------------------------------
+ * Batches: many independent grids solved in one CUDA-graph launch
+ * ------------------------------------------------------------------------- */
+
+/* Create a batch of `count` independent problems; dims = [count][3]
+ * (nx, ny, nz), h = [count][3].  All share precision and refine_iters. */
+int ibm_batch_create(int count, const int *dims, const double *h, int precision,
+                     int refine_iters, ibm_batch *out);
+int ibm_batch_destroy(ibm_batch batch);
+/* Poisson-solve every problem: rhs[i], phi[i] are device fields of problem
+ * i.  The whole batch is captured once into a CUDA graph per distinct
+ * pointer set and replayed as a single graph launch on `stream`. */
+int ibm_batch_poisson(ibm_batch batch, const void *const *rhs, void *const *phi,
+                      void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Serving: continuous batching of solve requests with HBM-based admission
+ * ------------------------------------------------------------------------- */
+
+enum { IBM_REQ_POISSON = 0, IBM_REQ_HELMHOLTZ = 1, IBM_REQ_SUBSTEP = 2 };
+
+typedef struct {
+  int kind;              /* IBM_REQ_*                                         */
+  int nx, ny, nz;
+  double h[3];
+  int precision;         /* IBM_FP64 / IBM_FP32_REFINED                       */
+  int refine_iters;
+  double c;              /* Helmholtz coefficient                             */
+  int field_bc;          /* Helmholtz wall rows                               */
+  const double *in;      /* HOST FP64 input: rhs [ny][nz][nx] (Poisson,
+                            Helmholtz) or u,v,w,p packed [4][ny][nz][nx]
+                            (substep)                                        */
+  double *out;           /* HOST FP64 output, same shape as `in`              */
+  int n_markers;         /* substep: markers                                  */
+  const double *X0;      /* substep: HOST [n][3]                              */
+  const double *dV;      /* substep: HOST [n]                                 */
+  int motion;
+  double params[4];
+  double dt, nu;         /* substep                                           */
+  int rk_stage;          /* substep                                           */
+} ibm_request;
+
+typedef struct {
+  int status;            /* IBM_OK, IBM_PENDING or an error code              */
+  double queue_ms;       /* submit -> admission                               */
+  double device_ms;      /* device time of the solve (events)                 */
+  double total_ms;       /* submit -> completion seen by the server           */
+  double removed_mean;
+} ibm_result;
+
+/* Create a server that admits requests while their device memory fits in
+ * hbm_budget_bytes, keeps plans resident per shape and runs admitted work
+ * on n_streams CUDA streams so that requests overlap on the device.
+ * max_queue bounds the pending queue (ibm_submit returns IBM_ERR_BUSY when
+ * full). */
+int ibm_server_create(size_t hbm_budget_bytes, int n_streams, int max_queue,
+                      ibm_server *out);
+int ibm_server_destroy(ibm_server server);
+/* Non-blocking: copies the request descriptor (not the data; `in` and `out`
+ * must stay valid until completion) and returns a ticket. */
+int ibm_submit(ibm_server server, const ibm_request *req, uint64_t *ticket);
+/* Non-blocking: IBM_PENDING while running; IBM_OK (result filled, `out`
+ * written) once done; an error code for a failed request.  A finished
+ * ticket is released by the poll that reports it. */
+int ibm_poll(ibm_server server, uint64_t ticket, ibm_result *out);
+/* Blocking variant of ibm_poll with a deadline (seconds). */
+int ibm_wait(ibm_server server, uint64_t ticket, double timeout_s, ibm_result *out);
+/* Cancel a request that has not been admitted yet. */
+int ibm_cancel(ibm_server server, uint64_t ticket);
+
+/* Thread-local description of the last error on this thread. */
+const char *ibm_last_error(void);
+/* Library version string. */
+const char *ibm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* IBM_H */

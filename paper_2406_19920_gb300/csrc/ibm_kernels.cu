@@ -1,0 +1,256 @@
+// ibm_kernels.cu -- Lagrangian operations of the immersed boundary (Sec. 2.3.2).
+//
+// Interpolation (Eq. 2b) and spreading (Eq. 2d) with a regularised delta
+// delta_h(x - X) = phi((x-X)/hx) phi((y-Y)/hy) phi((z-Z)/hz) / (hx hy hz).
+// The paper cites Peskin and Roma et al. without printing phi; ROMA3 is the
+// three-point kernel of Roma, Peskin & Berger (1999), PESKIN4 the four-point
+// kernel of Peskin (2002).  Each velocity component lives on its own
+// staggered sub-grid (origin in grid units: u (0,1/2,1/2), v (1/2,0,1/2),
+// w (1/2,1/2,0)); x and z wrap periodically; along y only stored unknowns
+// are touched (v's wall face 0 and points beyond the walls are dropped).
+//
+// One thread per (marker, component).  Grid index and offset are computed in
+// FP64 (a few operations per thread) so that the weights see the marker
+// position without the FP32 rounding of i*h; the weights and sums run in the
+// plan precision.  Spreading accumulates with global atomics as in the
+// paper's L1 kernel (Sec. 2.3.2).
+#include <cmath>
+
+#include "plan.h"
+
+namespace ibm {
+
+struct IbmGrid {
+  int nx, ny, nz;
+  double inv_h[3];
+  double vol_inv;  // 1 / (hx hy hz)
+};
+
+template <typename T> __device__ __forceinline__ T phi_roma3(T r) {
+  const T a = fabs(r);
+  if (a <= (T)0.5) return ((T)1 + sqrt((T)1 - (T)3 * a * a)) / (T)3;
+  if (a <= (T)1.5) {
+    const T t = (T)1 - a;
+    return ((T)5 - (T)3 * a - sqrt(fmax((T)0, (T)1 - (T)3 * t * t))) / (T)6;
+  }
+  return (T)0;
+}
+template <typename T> __device__ __forceinline__ T phi_peskin4(T r) {
+  const T a = fabs(r);
+  if (a <= (T)1) return ((T)3 - (T)2 * a + sqrt((T)1 + (T)4 * a - (T)4 * a * a)) / (T)8;
+  if (a <= (T)2) return ((T)5 - (T)2 * a - sqrt(fmax((T)0, (T)-7 + (T)12 * a - (T)4 * a * a))) / (T)8;
+  return (T)0;
+}
+
+template <typename T, int S> struct Support {
+  int i[S], j[S], k[S];
+  T wx[S], wy[S], wz[S];
+  bool jv[S];
+};
+
+__device__ __forceinline__ int wrap(int i, int n) {
+  i %= n;
+  return i < 0 ? i + n : i;
+}
+
+// S = 3 (ROMA3) or 4 (PESKIN4)
+template <typename T, int S>
+__device__ __forceinline__ void support(const IbmGrid &g, int comp, double X, double Y, double Z,
+                                        Support<T, S> &s) {
+  const double ox = comp == 0 ? 0.0 : 0.5;
+  const double oy = comp == 1 ? 0.0 : 0.5;
+  const double oz = comp == 2 ? 0.0 : 0.5;
+  const double sx = X * g.inv_h[0] - ox, sy = Y * g.inv_h[1] - oy, sz = Z * g.inv_h[2] - oz;
+  const double bx = (S == 3) ? floor(sx + 0.5) - 1.0 : floor(sx) - 1.0;
+  const double by = (S == 3) ? floor(sy + 0.5) - 1.0 : floor(sy) - 1.0;
+  const double bz = (S == 3) ? floor(sz + 0.5) - 1.0 : floor(sz) - 1.0;
+  const int jlo = comp == 1 ? 1 : 0;
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    const T rx = (T)(sx - (bx + q)), ry = (T)(sy - (by + q)), rz = (T)(sz - (bz + q));
+    s.wx[q] = S == 3 ? phi_roma3<T>(rx) : phi_peskin4<T>(rx);
+    s.wy[q] = S == 3 ? phi_roma3<T>(ry) : phi_peskin4<T>(ry);
+    s.wz[q] = S == 3 ? phi_roma3<T>(rz) : phi_peskin4<T>(rz);
+    s.i[q] = wrap((int)bx + q, g.nx);
+    s.k[q] = wrap((int)bz + q, g.nz);
+    s.j[q] = (int)by + q;
+    s.jv[q] = s.j[q] >= jlo && s.j[q] <= g.ny - 1;
+  }
+}
+
+// U[m][c] = sum phi phi phi f_c  (+ optional second field: u^e = u + du)
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+k_interp(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ u, const T *__restrict__ v,
+         const T *__restrict__ w, const T *__restrict__ du, const T *__restrict__ dv, const T *__restrict__ dw,
+         T *__restrict__ U, const T *__restrict__ Ud, T inv_dt, T *__restrict__ F) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int m = t / 3, c = t - 3 * m;
+  Support<T, S> s;
+  support<T, S>(g, c, (double)X[3 * m], (double)X[3 * m + 1], (double)X[3 * m + 2], s);
+  const T *f = c == 0 ? u : c == 1 ? v : w;
+  const T *df = c == 0 ? du : c == 1 ? dv : dw;
+  T acc = 0;
+#pragma unroll
+  for (int qy = 0; qy < S; ++qy) {
+    if (!s.jv[qy]) continue;
+    const size_t rowy = (size_t)s.j[qy] * g.nz;
+#pragma unroll
+    for (int qz = 0; qz < S; ++qz) {
+      const size_t row = (rowy + s.k[qz]) * g.nx;
+      const T wyz = s.wy[qy] * s.wz[qz];
+#pragma unroll
+      for (int qx = 0; qx < S; ++qx) {
+        T val = f[row + s.i[qx]];
+        if (df) val += df[row + s.i[qx]];
+        acc += wyz * s.wx[qx] * val;
+      }
+    }
+  }
+  if (U) U[t] = acc;
+  if (F) F[t] = (Ud[t] - acc) * inv_dt;  // Eq. 2c
+}
+
+// f_c += amp * phi phi phi,  amp = scale * F[m][c] * dV[m] / (hx hy hz)
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, const T *__restrict__ dV, T *fu,
+         T *fv, T *fw, T scale) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int m = t / 3, c = t - 3 * m;
+  Support<T, S> s;
+  support<T, S>(g, c, (double)X[3 * m], (double)X[3 * m + 1], (double)X[3 * m + 2], s);
+  T *f = c == 0 ? fu : c == 1 ? fv : fw;
+  const T amp = scale * F[t] * dV[m] * (T)g.vol_inv;
+#pragma unroll
+  for (int qy = 0; qy < S; ++qy) {
+    if (!s.jv[qy]) continue;
+    const size_t rowy = (size_t)s.j[qy] * g.nz;
+#pragma unroll
+    for (int qz = 0; qz < S; ++qz) {
+      const size_t row = (rowy + s.k[qz]) * g.nx;
+      const T a = amp * s.wy[qy] * s.wz[qz];
+#pragma unroll
+      for (int qx = 0; qx < S; ++qx) atomicAdd(f + row + s.i[qx], a * s.wx[qx]);
+    }
+  }
+}
+
+// L2: prescribed motion at time t (FP64 arithmetic, stored in plan precision)
+template <typename T>
+__global__ void k_motion(int n, const T *__restrict__ X0, T *__restrict__ X, T *__restrict__ Ud, int kind,
+                         double p0, double p1, double p2, double t) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= n) return;
+  double x = (double)X0[3 * m], y = (double)X0[3 * m + 1], z = (double)X0[3 * m + 2];
+  double ux = 0, uy = 0, uz = 0;
+  if (kind == IBM_MOTION_TRANSLATE) {
+    x += p0 * t; y += p1 * t; z += p2 * t;
+    ux = p0; uy = p1; uz = p2;
+  } else if (kind == IBM_MOTION_HEAVE) {
+    const double w = 2.0 * M_PI / p1;
+    y += p0 * sin(w * t);
+    uy = p0 * w * cos(w * t);
+  }
+  X[3 * m] = (T)x; X[3 * m + 1] = (T)y; X[3 * m + 2] = (T)z;
+  Ud[3 * m] = (T)ux; Ud[3 * m + 1] = (T)uy; Ud[3 * m + 2] = (T)uz;
+}
+
+static IbmGrid ibm_grid(const ibm_plan_s *p) {
+  IbmGrid g;
+  g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+  for (int d = 0; d < 3; ++d) g.inv_h[d] = 1.0 / p->h[d];
+  g.vol_inv = 1.0 / (p->h[0] * p->h[1] * p->h[2]);
+  return g;
+}
+
+template <typename T>
+cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, const T *v, const T *w,
+                          const T *du, const T *dv, const T *dw, T *U, const T *Ud, double inv_dt, T *F,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const IbmGrid g = ibm_grid(p);
+  const int blocks = ceil_div(3 * n, 256);
+  if (p->delta == IBM_DELTA_PESKIN4)
+    k_interp<T, 4><<<blocks, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
+  else
+    k_interp<T, 3><<<blocks, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, const T *dV, T *fu, T *fv, T *fw,
+                          double scale, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const IbmGrid g = ibm_grid(p);
+  const int blocks = ceil_div(3 * n, 256);
+  if (p->delta == IBM_DELTA_PESKIN4)
+    k_spread<T, 4><<<blocks, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
+  else
+    k_spread<T, 3><<<blocks, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_motion(int n, const T *X0, T *X, T *Ud, int kind, const double *params, double t,
+                          cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  k_motion<T><<<ceil_div(n, 256), 256, 0, st>>>(n, X0, X, Ud, kind, params[0], params[1], params[2], t);
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_interp<float>(const ibm_plan_s *, int, const float *, const float *, const float *,
+                                          const float *, const float *, const float *, const float *, float *,
+                                          const float *, double, float *, cudaStream_t);
+template cudaError_t launch_interp<double>(const ibm_plan_s *, int, const double *, const double *,
+                                           const double *, const double *, const double *, const double *,
+                                           const double *, double *, const double *, double, double *,
+                                           cudaStream_t);
+template cudaError_t launch_spread<float>(const ibm_plan_s *, int, const float *, const float *, const float *,
+                                          float *, float *, float *, double, cudaStream_t);
+template cudaError_t launch_spread<double>(const ibm_plan_s *, int, const double *, const double *,
+                                           const double *, double *, double *, double *, double, cudaStream_t);
+template cudaError_t launch_motion<float>(int, const float *, float *, float *, int, const double *, double,
+                                          cudaStream_t);
+template cudaError_t launch_motion<double>(int, const double *, double *, double *, int, const double *, double,
+                                           cudaStream_t);
+
+}  // namespace ibm
+
+using namespace ibm;
+
+extern "C" {
+
+int ibm_interp(ibm_plan plan, int n, const void *X, const void *u, const void *v, const void *w, void *U,
+               void *stream) {
+  if (!plan || n < 0 || (n > 0 && (!X || !u || !v || !w || !U)))
+    return set_error(IBM_ERR_ARG, "ibm_interp: bad argument");
+  if (n > (1 << 28)) return set_error(IBM_ERR_ARG, "ibm_interp: n too large");
+  cudaError_t e;
+  if (plan->precision == IBM_FP64)
+    e = launch_interp<double>(plan, n, (const double *)X, (const double *)u, (const double *)v, (const double *)w,
+                              nullptr, nullptr, nullptr, (double *)U, nullptr, 0.0, nullptr, (cudaStream_t)stream);
+  else
+    e = launch_interp<float>(plan, n, (const float *)X, (const float *)u, (const float *)v, (const float *)w,
+                             nullptr, nullptr, nullptr, (float *)U, nullptr, 0.0, nullptr, (cudaStream_t)stream);
+  return e == cudaSuccess ? IBM_OK : cuda_error(e, "ibm_interp");
+}
+
+int ibm_spread(ibm_plan plan, int n, const void *X, const void *F, const void *dV, void *fu, void *fv, void *fw,
+               void *stream) {
+  if (!plan || n < 0 || (n > 0 && (!X || !F || !dV || !fu || !fv || !fw)))
+    return set_error(IBM_ERR_ARG, "ibm_spread: bad argument");
+  if (n > (1 << 28)) return set_error(IBM_ERR_ARG, "ibm_spread: n too large");
+  cudaError_t e;
+  if (plan->precision == IBM_FP64)
+    e = launch_spread<double>(plan, n, (const double *)X, (const double *)F, (const double *)dV, (double *)fu,
+                              (double *)fv, (double *)fw, 1.0, (cudaStream_t)stream);
+  else
+    e = launch_spread<float>(plan, n, (const float *)X, (const float *)F, (const float *)dV, (float *)fu,
+                             (float *)fv, (float *)fw, 1.0, (cudaStream_t)stream);
+  return e == cudaSuccess ? IBM_OK : cuda_error(e, "ibm_spread");
+}
+
+}  // extern "C"

@@ -1,0 +1,297 @@
+// plan.cu -- plan creation, the direct solve pipeline and the exported
+// Poisson / Helmholtz entry points of libibm.
+//
+// Solve pipeline for one right-hand side (Sec. 2.3.3, doubly periodic
+// branch: S1.1 + S1.2 for Helmholtz, S2.1 + S2.2 for Poisson):
+//   1. forward real FFT along x and complex FFT along z of every y-plane;
+//   2. one tridiagonal solve along y per Fourier pencil (pencil.cu);
+//   3. inverse transforms, scaled by 1/(nx nz).
+// FP32 plans then apply `refine` steps of iterative refinement: residual
+// r = b - A x in float-float arithmetic (stencil.cu), correction solve of
+// A d = r with the same pipeline, x += d fused into the inverse transform.
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "plan.h"
+
+namespace ibm {
+
+static thread_local std::string g_last_error;
+
+int set_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+
+int cuda_error(cudaError_t e, const char *what) {
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    return set_error(IBM_ERR_OOM, "%s: %s", what, cudaGetErrorString(e));
+  }
+  return set_error(IBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+TransformGeom geom_of(const ibm_plan_s *p) {
+  TransformGeom g;
+  g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+  g.use_plane = true;
+  return g;
+}
+
+template <typename T>
+static int upload_tables(ibm_plan_s *p) {
+  const int nx = p->nx, nz = p->nz, P = p->P;
+  std::vector<cplx<T>> twx(nx), twz(nz);
+  for (int m = 0; m < nx; ++m) {
+    const double a = 2.0 * M_PI * (double)m / nx;
+    twx[m] = mk<T>((T)std::cos(a), (T)-std::sin(a));
+  }
+  for (int m = 0; m < nz; ++m) {
+    const double a = 2.0 * M_PI * (double)m / nz;
+    twz[m] = mk<T>((T)std::cos(a), (T)-std::sin(a));
+  }
+  // modified wavenumbers kappa'^2 = (2/h^2)(1 - cos(kappa h)), Appendix A
+  std::vector<T> lx(P), lz(nz);
+  for (int k = 0; k < P; ++k)
+    lx[k] = (T)(2.0 / (p->h[0] * p->h[0]) * (1.0 - std::cos(2.0 * M_PI * k / nx)));
+  for (int k = 0; k < nz; ++k)
+    lz[k] = (T)(2.0 / (p->h[2] * p->h[2]) * (1.0 - std::cos(2.0 * M_PI * k / nz)));
+  IBM_CUDA_TRY(cudaMemcpy(p->twx, twx.data(), sizeof(cplx<T>) * nx, cudaMemcpyHostToDevice));
+  IBM_CUDA_TRY(cudaMemcpy(p->twz, twz.data(), sizeof(cplx<T>) * nz, cudaMemcpyHostToDevice));
+  IBM_CUDA_TRY(cudaMemcpy(p->lamx, lx.data(), sizeof(T) * P, cudaMemcpyHostToDevice));
+  IBM_CUDA_TRY(cudaMemcpy(p->lamz, lz.data(), sizeof(T) * nz, cudaMemcpyHostToDevice));
+  return IBM_OK;
+}
+
+static void plan_free(ibm_plan_s *p) {
+  if (!p) return;
+  void *bufs[] = {p->S, p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3],
+                  p->twx, p->twz, p->lamx, p->lamz, p->dsc};
+  for (void *b : bufs)
+    if (b) cudaFree(b);
+  if (p->hsc) cudaFreeHost(p->hsc);
+  if (p->ev0) cudaEventDestroy(p->ev0);
+  if (p->ev1) cudaEventDestroy(p->ev1);
+  delete p;
+}
+
+static int dalloc(ibm_plan_s *p, void **ptr, size_t bytes) {
+  cudaError_t e = cudaMalloc(ptr, bytes);
+  if (e != cudaSuccess) {
+    *ptr = nullptr;
+    return cuda_error(e, "cudaMalloc");
+  }
+  p->bytes += bytes;
+  return IBM_OK;
+}
+
+// ---------------------------------------------------------------------------
+// solve
+// ---------------------------------------------------------------------------
+template <typename T>
+static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out, const T *addend,
+                      double *mean_out, cudaStream_t st) {
+  const TransformGeom g = geom_of(p);
+  cplx<T> *S = static_cast<cplx<T> *>(p->S);
+  const cplx<T> *twx = static_cast<const cplx<T> *>(p->twx);
+  const cplx<T> *twz = static_cast<const cplx<T> *>(p->twz);
+  IBM_CUDA_TRY(launch_forward<T>(g, in, S, twx, twz, (T)1, st));
+  IBM_CUDA_TRY(launch_pencil<T>(pp, S, static_cast<const T *>(p->lamx), static_cast<const T *>(p->lamz),
+                                mean_out, st));
+  IBM_CUDA_TRY(launch_inverse<T>(g, S, out, addend, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
+  return IBM_OK;
+}
+
+static PencilParams pencil_params(const ibm_plan_s *p, int kind, double c, int field_bc) {
+  PencilParams pp;
+  std::memset(&pp, 0, sizeof pp);
+  pp.ny = p->ny; pp.nz = p->nz; pp.P = p->P;
+  const double hy = p->h[1];
+  if (kind == 0) {
+    pp.a = 1.0 / (hy * hy);
+    pp.g_add = 0.0; pp.g_mul = 1.0;
+    pp.beta_s = pp.beta_e = 0;
+    pp.j0 = 0; pp.neg_rhs = 1; pp.zero_mode = 1;
+  } else {
+    pp.a = c / (hy * hy);
+    pp.g_add = 1.0; pp.g_mul = c;
+    const int beta = field_bc == IBM_FIELD_CELL_NEUMANN ? 0 : field_bc == IBM_FIELD_CELL_DIRICHLET ? 2 : 1;
+    pp.beta_s = pp.beta_e = beta;
+    pp.j0 = field_bc == IBM_FIELD_FACE_DIRICHLET ? 1 : 0;
+    pp.neg_rhs = 0; pp.zero_mode = 0;
+  }
+  pp.hy2 = hy * hy;
+  pp.inv_nxnz = 1.0 / ((double)p->nx * p->nz);
+  return pp;
+}
+
+static StencilCoef stencil_coef(const ibm_plan_s *p, int kind, double c, int field_bc) {
+  StencilCoef sc;
+  sc.cx = 1.0 / (p->h[0] * p->h[0]);
+  sc.cy = 1.0 / (p->h[1] * p->h[1]);
+  sc.cz = 1.0 / (p->h[2] * p->h[2]);
+  if (kind == 0) { sc.sigma = 0.0; sc.tau = 1.0; sc.bc = 0; }
+  else { sc.sigma = 1.0; sc.tau = -c; sc.bc = field_bc; }
+  return sc;
+}
+
+template <typename T>
+static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T *in, T *out, const T *addend,
+                        cudaStream_t st, ibm_info *info) {
+  const PencilParams pp = pencil_params(p, kind, c, field_bc);
+  const StencilCoef sc = stencil_coef(p, kind, c, field_bc);
+  const int iters = (p->precision == IBM_FP32_REFINED && addend == nullptr) ? p->refine : 0;
+  const bool need_b = iters > 0 || info;
+  const T *b = in;
+  if (need_b && (const void *)in == (const void *)out) {
+    IBM_CUDA_TRY(cudaMemcpyAsync(p->bsave, in, p->npts * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    b = static_cast<const T *>(p->bsave);
+  }
+  if (info) {
+    IBM_CUDA_TRY(cudaMemsetAsync(p->dsc, 0, 8 * sizeof(double), st));
+    IBM_CUDA_TRY(cudaEventRecord(p->ev0, st));
+  }
+  int rc = solve_once<T>(p, pp, b, out, addend, kind == 0 ? p->dsc : nullptr, st);
+  if (rc) return rc;
+  T *r = static_cast<T *>(p->work);
+  for (int it = 0; it < iters; ++it) {
+    IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, nullptr, st));
+    rc = solve_once<T>(p, pp, r, out, out, nullptr, st);
+    if (rc) return rc;
+  }
+  if (info) {
+    IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
+    // relative residual of the returned x (only meaningful without addend)
+    IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, p->dsc + 1, st));
+    IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IBM_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    IBM_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    const double N = (double)p->npts;
+    const double *h = p->hsc;
+    const double rr = std::max(0.0, h[1] - h[3] * h[3] / N);
+    const double bb = h[2];
+    info->rel_residual = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
+    info->removed_mean = kind == 0 ? h[0] : 0.0;
+    info->div_max = 0.0;
+    info->div_before = 0.0;
+    info->t_ms = ms;
+    info->refine_iters = iters;
+  }
+  return IBM_OK;
+}
+
+int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, void *out, const void *addend,
+               cudaStream_t st, ibm_info *info) {
+  if (p->precision == IBM_FP64)
+    return plan_solve_t<double>(p, kind, c, field_bc, static_cast<const double *>(in), static_cast<double *>(out),
+                                static_cast<const double *>(addend), st, info);
+  return plan_solve_t<float>(p, kind, c, field_bc, static_cast<const float *>(in), static_cast<float *>(out),
+                             static_cast<const float *>(addend), st, info);
+}
+
+}  // namespace ibm
+
+using namespace ibm;
+
+// ---------------------------------------------------------------------------
+// exported entry points
+// ---------------------------------------------------------------------------
+extern "C" {
+
+const char *ibm_last_error(void) { return g_last_error.c_str(); }
+const char *ibm_version(void) { return "libibm 0.1 (sm_103a)"; }
+
+int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int precision, int refine_iters,
+                    ibm_plan *out) {
+  if (!out) return set_error(IBM_ERR_ARG, "ibm_plan_create: out is NULL");
+  *out = nullptr;
+  if (bc != IBM_BC_PXZ_WALL_Y) return set_error(IBM_ERR_UNSUPPORTED, "ibm_plan_create: unsupported bc %d", bc);
+  if (!transform_size_supported(nx) || !transform_size_supported(nz))
+    return set_error(IBM_ERR_ARG, "ibm_plan_create: nx=%d nz=%d must be 2^a 3^b (b<=1) in [8,512]", nx, nz);
+  if (ny < 8 || ny > 512) return set_error(IBM_ERR_ARG, "ibm_plan_create: ny=%d outside [8,512]", ny);
+  if (!h || !(h[0] > 0) || !(h[1] > 0) || !(h[2] > 0) || !std::isfinite(h[0]) || !std::isfinite(h[1]) ||
+      !std::isfinite(h[2]))
+    return set_error(IBM_ERR_ARG, "ibm_plan_create: spacings must be finite and positive");
+  if (precision != IBM_FP64 && precision != IBM_FP32_REFINED)
+    return set_error(IBM_ERR_ARG, "ibm_plan_create: precision %d", precision);
+  if (refine_iters < 0 || refine_iters > 4)
+    return set_error(IBM_ERR_ARG, "ibm_plan_create: refine_iters %d outside [0,4]", refine_iters);
+  ibm_plan_s *p = new (std::nothrow) ibm_plan_s();
+  if (!p) return set_error(IBM_ERR_OOM, "ibm_plan_create: host allocation");
+  p->nx = nx; p->ny = ny; p->nz = nz; p->P = nx / 2 + 1;
+  p->h[0] = h[0]; p->h[1] = h[1]; p->h[2] = h[2];
+  p->precision = precision;
+  p->refine = precision == IBM_FP64 ? 0 : refine_iters;
+  p->delta = IBM_DELTA_ROMA3;
+  p->esz = precision == IBM_FP64 ? 8 : 4;
+  p->npts = (size_t)nx * ny * nz;
+  p->nspec = (size_t)ny * nz * p->P;
+  int rc = IBM_OK;
+  if ((rc = dalloc(p, &p->S, p->nspec * 2 * p->esz)) ||
+      (rc = dalloc(p, &p->work, p->npts * p->esz)) ||
+      (rc = dalloc(p, &p->bsave, p->npts * p->esz)) ||
+      (rc = dalloc(p, &p->twx, (size_t)nx * 2 * p->esz)) ||
+      (rc = dalloc(p, &p->twz, (size_t)nz * 2 * p->esz)) ||
+      (rc = dalloc(p, &p->lamx, (size_t)p->P * p->esz)) ||
+      (rc = dalloc(p, &p->lamz, (size_t)nz * p->esz)) ||
+      (rc = dalloc(p, (void **)&p->dsc, 16 * sizeof(double)))) {
+    plan_free(p);
+    return rc;
+  }
+  cudaError_t e = cudaMallocHost((void **)&p->hsc, 16 * sizeof(double));
+  if (e != cudaSuccess) { plan_free(p); return cuda_error(e, "cudaMallocHost"); }
+  if ((e = cudaEventCreate(&p->ev0)) != cudaSuccess || (e = cudaEventCreate(&p->ev1)) != cudaSuccess) {
+    plan_free(p);
+    return cuda_error(e, "cudaEventCreate");
+  }
+  rc = precision == IBM_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
+  if (rc) { plan_free(p); return rc; }
+  *out = p;
+  return IBM_OK;
+}
+
+int ibm_plan_destroy(ibm_plan plan) {
+  if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_destroy: NULL plan");
+  cudaDeviceSynchronize();
+  plan_free(plan);
+  return IBM_OK;
+}
+
+int ibm_plan_set_delta(ibm_plan plan, int kernel) {
+  if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_set_delta: NULL plan");
+  if (kernel != IBM_DELTA_ROMA3 && kernel != IBM_DELTA_PESKIN4)
+    return set_error(IBM_ERR_ARG, "ibm_plan_set_delta: kernel %d", kernel);
+  plan->delta = kernel;
+  return IBM_OK;
+}
+
+size_t ibm_plan_workspace_bytes(ibm_plan plan) { return plan ? plan->bytes : 0; }
+
+int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream, ibm_info *info) {
+  if (!plan || !rhs || !phi) return set_error(IBM_ERR_ARG, "ibm_poisson_solve: NULL argument");
+  if (!aligned_to(rhs, plan->esz) || !aligned_to(phi, plan->esz))
+    return set_error(IBM_ERR_ARG, "ibm_poisson_solve: misaligned field pointer");
+  return plan_solve(plan, 0, 0.0, 0, rhs, phi, nullptr, (cudaStream_t)stream, info);
+}
+
+int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs, void *u, void *stream,
+                        ibm_info *info) {
+  if (!plan || !rhs || !u) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: NULL argument");
+  if (!(c > 0.0) || !std::isfinite(c)) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: c must be > 0");
+  if (field_bc < IBM_FIELD_CELL_NEUMANN || field_bc > IBM_FIELD_FACE_DIRICHLET)
+    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field_bc %d", field_bc);
+  if (!aligned_to(rhs, plan->esz) || !aligned_to(u, plan->esz))
+    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: misaligned field pointer");
+  return plan_solve(plan, 1, c, field_bc, rhs, u, nullptr, (cudaStream_t)stream, info);
+}
+
+}  // extern "C"

@@ -1,0 +1,56 @@
+// plan.h -- the plan object behind ibm_plan and helpers shared by the
+// host-side translation units of libibm.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <string>
+
+#include "../../include/ibm.h"
+#include "internal.h"
+
+namespace ibm {
+
+int set_error(int code, const char *fmt, ...);
+int cuda_error(cudaError_t e, const char *what);
+
+#define IBM_CUDA_TRY(call)                                    \
+  do {                                                        \
+    cudaError_t e__ = (call);                                 \
+    if (e__ != cudaSuccess) return ::ibm::cuda_error(e__, #call); \
+  } while (0)
+
+}  // namespace ibm
+
+struct ibm_plan_s {
+  int nx, ny, nz, P;
+  double h[3];
+  int precision;     // IBM_FP64 / IBM_FP32_REFINED
+  int refine;        // refinement steps (FP32 path)
+  int delta;         // IBM_DELTA_*
+  size_t esz;        // element size: 4 or 8
+  size_t npts;       // nx * ny * nz
+  size_t nspec;      // ny * nz * P complex entries
+  void *S;           // spectrum workspace
+  void *work;        // real work field (residual / divergence)
+  void *bsave;       // copy of an in-place right-hand side
+  void *sub[4];      // substep fields (allocated on first substep)
+  void *twx, *twz;   // twiddles W_N^m (plan precision)
+  void *lamx, *lamz; // modified wavenumbers kx'^2 (P), kz'^2 (nz) (plan precision)
+  double *dsc;       // device scalars: [0] removed mean, [1..4] norms, [5..7] misc
+  double *hsc;       // pinned host mirror of dsc
+  cudaEvent_t ev0, ev1;
+  size_t bytes;      // device bytes held
+};
+
+namespace ibm {
+inline bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
+TransformGeom geom_of(const ibm_plan_s *p);
+// Solve A x = b with the plan's direct method (+ refinement for FP32).
+//   kind 0: Poisson L x = b (mean-free);  kind 1: Helmholtz (I - c L) x = b.
+// out may equal in.  addend (nullable) is added to the result: out = addend + x.
+int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, void *out, const void *addend,
+               cudaStream_t st, ibm_info *info);
+}  // namespace ibm

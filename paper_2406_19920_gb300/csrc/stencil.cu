@@ -1,0 +1,186 @@
+// stencil.cu -- 7-point residual of the Poisson / Helmholtz operators.
+//
+// r = b - (sigma x + tau L_h x), L_h the second-order central Laplacian of
+// Sec. 2.1 with periodic x, z and the ghost rule of the field's wall kind
+// along y (Appendix B).  Poisson: sigma = 0, tau = 1; Helmholtz (I - c L):
+// sigma = 1, tau = -c.  In FP32 the stencil is evaluated in float-float
+// arithmetic (exact second differences of the stored FP32 values, 1/h^2 and
+// tau carried as hi + lo pairs) and rounded once to FP32; a plain FP32
+// stencil would limit iterative refinement to ~eps32 * cond.  Optionally the
+// FP64 sums of r^2, b^2, r and b are accumulated for the relative residual.
+// An optional device scalar is subtracted from b first (the Poisson
+// right-hand side's removed mean), so the residual is that of the compatible
+// system.
+#include "internal.h"
+
+namespace ibm {
+
+enum { BC_NEUMANN = 0, BC_CELL_DIRICHLET = 1, BC_FACE_DIRICHLET = 2 };
+
+struct ffc { float hi, lo; };
+static inline ffc split_ff(double v) {
+  ffc r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
+struct ResidualArgs {
+  const double *boff;  // device scalar subtracted from b (its removed mean), or NULL
+  int nx, ny, nz, bc;
+  ffc cx, cy, cz, tau;
+  float sigma;
+  double cxd, cyd, czd, taud, sigmad;
+};
+
+// Adds the block sums of (r^2, b^2, r, b) to out[0..3] (FP64 atomics).
+__device__ __forceinline__ void block_accumulate(double r, double b, double *out) {
+  __shared__ double red[4][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  double v[4] = {r * r, b * b, r, b};
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v[q] += __shfl_xor_sync(0xffffffffu, v[q], o);
+  if (lane == 0)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) red[q][w] = v[q];
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      double t = lane < nw ? red[q][lane] : 0.0;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == 0) atomicAdd(out + q, t);
+    }
+  }
+}
+
+// one thread per point; grid covers ny * nz * nx exactly (block multiple of 32)
+__global__ void __launch_bounds__(256)
+k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float *__restrict__ r,
+               double *norms) {
+  const size_t total = (size_t)A.nx * A.ny * A.nz;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0, bb = 0.0;
+  if (idx < total) {
+    const int i = (int)(idx % A.nx);
+    const size_t t = idx / A.nx;
+    const int k = (int)(t % A.nz);
+    const int j = (int)(t / A.nz);
+    const size_t row = (size_t)A.nx;
+    const size_t pl = (size_t)A.nx * A.nz;
+    float bv = b[idx];
+    float bl = 0.0f;  // low part of b - offset
+    if (A.boff) {
+      const double off = *A.boff;
+      const float mh = (float)off;
+      const ff d = two_sum(bv, -mh);
+      bv = d.hi;
+      bl = __fadd_rn(d.lo, -(float)(off - (double)mh));
+    }
+    float res;
+    if (A.bc == BC_FACE_DIRICHLET && j == 0) {
+      res = 0.0f;
+    } else {
+      const float x0 = x[idx];
+      const float xe = x[idx - i + (i + 1 == A.nx ? 0 : i + 1)];
+      const float xw = x[idx - i + (i == 0 ? A.nx - 1 : i - 1)];
+      const size_t rowbase = idx - (size_t)k * row;
+      const float xn = x[rowbase + (size_t)(k + 1 == A.nz ? 0 : k + 1) * row];
+      const float xs = x[rowbase + (size_t)(k == 0 ? A.nz - 1 : k - 1) * row];
+      float xu, xd;  // y+1, y-1
+      if (A.bc == BC_FACE_DIRICHLET) {
+        xd = (j - 1 >= 1) ? x[idx - pl] : 0.0f;
+        xu = (j + 1 <= A.ny - 1) ? x[idx + pl] : 0.0f;
+      } else {
+        const float gsign = (A.bc == BC_NEUMANN) ? 1.0f : -1.0f;
+        xd = (j > 0) ? x[idx - pl] : gsign * x0;
+        xu = (j + 1 < A.ny) ? x[idx + pl] : gsign * x0;
+      }
+      ff L = ff_mul(ff_second_diff(xe, xw, x0), ff{A.cx.hi, A.cx.lo});
+      L = ff_add(L, ff_mul(ff_second_diff(xn, xs, x0), ff{A.cz.hi, A.cz.lo}));
+      L = ff_add(L, ff_mul(ff_second_diff(xu, xd, x0), ff{A.cy.hi, A.cy.lo}));
+      ff acc = ff_add(two_sum(bv, -A.sigma * x0), ff_from(bl));
+      acc = ff_add(acc, ff_neg(ff_mul(L, ff{A.tau.hi, A.tau.lo})));
+      res = __fadd_rn(acc.hi, acc.lo);
+    }
+    r[idx] = res;
+    rr = (double)res;
+    bb = (A.bc == BC_FACE_DIRICHLET && j == 0) ? 0.0 : (double)bv;
+  }
+  if (norms) block_accumulate(rr, bb, norms);
+}
+
+__global__ void __launch_bounds__(256)
+k_residual_f64(ResidualArgs A, const double *__restrict__ b, const double *__restrict__ x,
+               double *__restrict__ r, double *norms) {
+  const size_t total = (size_t)A.nx * A.ny * A.nz;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double rr = 0.0, bb = 0.0;
+  if (idx < total) {
+    const int i = (int)(idx % A.nx);
+    const size_t t = idx / A.nx;
+    const int k = (int)(t % A.nz);
+    const int j = (int)(t / A.nz);
+    const size_t row = (size_t)A.nx;
+    const size_t pl = (size_t)A.nx * A.nz;
+    const double bv = A.boff ? b[idx] - *A.boff : b[idx];
+    double res;
+    if (A.bc == BC_FACE_DIRICHLET && j == 0) {
+      res = 0.0;
+    } else {
+      const double x0 = x[idx];
+      const double xe = x[idx - i + (i + 1 == A.nx ? 0 : i + 1)];
+      const double xw = x[idx - i + (i == 0 ? A.nx - 1 : i - 1)];
+      const size_t rowbase = idx - (size_t)k * row;
+      const double xn = x[rowbase + (size_t)(k + 1 == A.nz ? 0 : k + 1) * row];
+      const double xs = x[rowbase + (size_t)(k == 0 ? A.nz - 1 : k - 1) * row];
+      double xu, xd;
+      if (A.bc == BC_FACE_DIRICHLET) {
+        xd = (j - 1 >= 1) ? x[idx - pl] : 0.0;
+        xu = (j + 1 <= A.ny - 1) ? x[idx + pl] : 0.0;
+      } else {
+        const double gsign = (A.bc == BC_NEUMANN) ? 1.0 : -1.0;
+        xd = (j > 0) ? x[idx - pl] : gsign * x0;
+        xu = (j + 1 < A.ny) ? x[idx + pl] : gsign * x0;
+      }
+      const double L = (xe + xw - 2.0 * x0) * A.cxd + (xn + xs - 2.0 * x0) * A.czd + (xu + xd - 2.0 * x0) * A.cyd;
+      res = bv - A.sigmad * x0 - A.taud * L;
+    }
+    r[idx] = res;
+    rr = res;
+    bb = (A.bc == BC_FACE_DIRICHLET && j == 0) ? 0.0 : bv;
+  }
+  if (norms) block_accumulate(rr, bb, norms);
+}
+
+static ResidualArgs make_args(int nx, int ny, int nz, const StencilCoef &c, const double *boff) {
+  ResidualArgs A;
+  A.boff = boff;
+  A.nx = nx; A.ny = ny; A.nz = nz; A.bc = c.bc;
+  A.cx = split_ff(c.cx); A.cy = split_ff(c.cy); A.cz = split_ff(c.cz);
+  A.tau = split_ff(c.tau);
+  A.sigma = (float)c.sigma;
+  A.cxd = c.cx; A.cyd = c.cy; A.czd = c.cz; A.taud = c.tau; A.sigmad = c.sigma;
+  return A;
+}
+
+template <>
+cudaError_t launch_residual<float>(int nx, int ny, int nz, const StencilCoef &c, const float *b, const float *x,
+                                   float *r, const double *boff, double *norms, cudaStream_t st) {
+  const size_t total = (size_t)nx * ny * nz;
+  k_residual_f32<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
+  return cudaGetLastError();
+}
+template <>
+cudaError_t launch_residual<double>(int nx, int ny, int nz, const StencilCoef &c, const double *b, const double *x,
+                                    double *r, const double *boff, double *norms, cudaStream_t st) {
+  const size_t total = (size_t)nx * ny * nz;
+  k_residual_f64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
+  return cudaGetLastError();
+}
+
+}  // namespace ibm

@@ -1,0 +1,484 @@
+// transforms.cu -- Fourier transforms along the two periodic axes (x, z).
+//
+// The paper's doubly periodic branch (Sec. 2.3.3, S1.1/S2.1) feeds the
+// pencil solver with the 2-D real FFT of the right-hand side over the
+// periodic planes and inverts it afterwards (S1.2/S2.2).  Here each y-plane
+// [nz][nx] (real) maps to a spectrum plane [nz][nx/2+1] (complex, kx
+// fastest), unnormalised forward and scaled by 1/(nx nz) on the way back.
+//
+// Real rows are transformed in pairs: rows a and b form z = a + i b, one
+// complex FFT of length nx gives Z, and A_k = (Z_k + conj Z_{N-k})/2,
+// B_k = -i (Z_k - conj Z_{N-k})/2 for k = 0..nx/2.  The inverse rebuilds
+// Z_k = A_k + i B_k from the two Hermitian half spectra.
+//
+// Two kernel families:
+//   plane kernels  one CTA per y-plane, the whole plane staged in shared
+//                  memory: x-FFT of every row pair, then z-FFT of every
+//                  column, then one coalesced store (one HBM read + one write
+//                  per direction);
+//   axis kernels   for planes larger than shared memory: x-rows and
+//                  z-columns in separate passes.
+#include "fft.cuh"
+#include "internal.h"
+
+namespace ibm {
+
+constexpr int kThreads = 256;
+
+// --------------------------------------------------------------------------
+// row-pair helpers
+// --------------------------------------------------------------------------
+
+// After fft_row on z = a + i b (row[0..N)), write the half spectra:
+// A to dstA[k*ds], B to dstB[k*ds], k = 0..N/2.  Reads everything first.
+template <typename T, int N>
+__device__ __forceinline__ void split_pair(cplx<T> *row, cplx<T> *dstA, cplx<T> *dstB, int ds, int lg,
+                                           unsigned mask) {
+  constexpr int G = FftPlan<N>::G;
+  constexpr int H = N / 2 + 1;
+  constexpr int KT = (H + G - 1) / G;
+  cplx<T> A[KT], B[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      const cplx<T> zk = row[k];
+      const cplx<T> zn = row[(N - k) % N];
+      A[t] = mk<T>((T)0.5 * (zk.x + zn.x), (T)0.5 * (zk.y - zn.y));
+      // D = zk - conj(zn); B = -i D / 2
+      B[t] = mk<T>((T)0.5 * (zk.y + zn.y), (T)-0.5 * (zk.x - zn.x));
+    }
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      dstA[k * ds] = A[t];
+      dstB[k * ds] = B[t];
+    }
+  }
+  __syncwarp(mask);
+}
+
+// Build Z_k = A_k + i B_k (k = 0..N-1, Hermitian extension) into row[0..N).
+// A at srcA[k*ss], B at srcB[k*ss]; the imaginary parts of the k = 0 and
+// k = N/2 bins are dropped as a real inverse transform does.
+template <typename T, int N>
+__device__ __forceinline__ void merge_pair(const cplx<T> *srcA, const cplx<T> *srcB, int ss, cplx<T> *row,
+                                           int lg, unsigned mask) {
+  constexpr int G = FftPlan<N>::G;
+  constexpr int H = N / 2 + 1;
+  constexpr int KT = (H + G - 1) / G;
+  cplx<T> A[KT], B[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      A[t] = srcA[k * ss];
+      B[t] = srcB[k * ss];
+      if (k == 0 || k == N / 2) { A[t].y = 0; B[t].y = 0; }
+    }
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      row[k] = mk<T>(A[t].x - B[t].y, A[t].y + B[t].x);
+      if (k > 0 && k < N / 2) row[N - k] = mk<T>(A[t].x + B[t].y, B[t].x - A[t].y);
+    }
+  }
+  __syncwarp(mask);
+}
+
+// --------------------------------------------------------------------------
+// plane kernels: one CTA per y-plane
+// --------------------------------------------------------------------------
+template <typename T, int NX, int NZ>
+__global__ void __launch_bounds__(kThreads)
+k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx_g,
+            const cplx<T> *__restrict__ twz_g, T in_scale) {
+  constexpr int P = NX / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *twz = twx + NX;
+  cplx<T> *plane = twz + NZ;  // NZ/2 pairs of (NX + 2) = NZ rows of pitch P
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x;
+  load_twiddles<T>(twx, twx_g, NX);
+  load_twiddles<T>(twz, twz_g, NZ);
+  {
+    const T *src = in + (size_t)j * NZ * NX;
+    T *pf = reinterpret_cast<T *>(plane);
+    for (int idx = tid; idx < NZ * NX; idx += kThreads) {
+      const int k = idx / NX, n = idx - k * NX;
+      pf[((k >> 1) * (NX + 2) + n) * 2 + (k & 1)] = src[idx] * in_scale;
+    }
+  }
+  __syncthreads();
+  {  // x: complex FFT of each row pair, then split into two half spectra
+    constexpr int G = FftPlan<NX>::G;
+    constexpr int NG = kThreads / G;
+    const int gid = tid / G, lg = tid % G;
+    for (int base = 0; base < NZ / 2; base += NG) {
+      const int p = base + gid;
+      const unsigned mask = __ballot_sync(0xffffffffu, p < NZ / 2);
+      if (p >= NZ / 2) continue;
+      cplx<T> *row = plane + p * (NX + 2);
+      fft_row<T, NX, false>(row, 1, twx, lg, mask);
+      split_pair<T, NX>(row, row, row + P, 1, lg, mask);
+    }
+  }
+  __syncthreads();
+  {  // z: complex FFT of each of the P columns (stride P)
+    constexpr int G = FftPlan<NZ>::G;
+    constexpr int NG = kThreads / G;
+    const int gid = tid / G, lg = tid % G;
+    for (int base = 0; base < P; base += NG) {
+      const int c = base + gid;
+      const unsigned mask = __ballot_sync(0xffffffffu, c < P);
+      if (c >= P) continue;
+      fft_row<T, NZ, false>(plane + c, P, twz, lg, mask);
+    }
+  }
+  __syncthreads();
+  cplx<T> *dst = S + (size_t)j * NZ * P;
+  for (int idx = tid; idx < NZ * P; idx += kThreads) dst[idx] = plane[idx];
+}
+
+// Inverse: spectrum plane -> real plane, out = addend + scale * result.
+template <typename T, int NX, int NZ>
+__global__ void __launch_bounds__(kThreads)
+k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx_g,
+            const cplx<T> *__restrict__ twz_g, T scale) {
+  constexpr int P = NX / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *twz = twx + NX;
+  cplx<T> *plane = twz + NZ;
+  const int j = blockIdx.x;
+  const int tid = threadIdx.x;
+  load_twiddles<T>(twx, twx_g, NX);
+  load_twiddles<T>(twz, twz_g, NZ);
+  {
+    const cplx<T> *src = S + (size_t)j * NZ * P;
+    for (int idx = tid; idx < NZ * P; idx += kThreads) plane[idx] = src[idx];
+  }
+  __syncthreads();
+  {
+    constexpr int G = FftPlan<NZ>::G;
+    constexpr int NG = kThreads / G;
+    const int gid = tid / G, lg = tid % G;
+    for (int base = 0; base < P; base += NG) {
+      const int c = base + gid;
+      const unsigned mask = __ballot_sync(0xffffffffu, c < P);
+      if (c >= P) continue;
+      fft_row<T, NZ, true>(plane + c, P, twz, lg, mask);
+    }
+  }
+  __syncthreads();
+  {
+    constexpr int G = FftPlan<NX>::G;
+    constexpr int NG = kThreads / G;
+    const int gid = tid / G, lg = tid % G;
+    T *dst = out + (size_t)j * NZ * NX;
+    const T *add = addend ? addend + (size_t)j * NZ * NX : nullptr;
+    for (int base = 0; base < NZ / 2; base += NG) {
+      const int p = base + gid;
+      const unsigned mask = __ballot_sync(0xffffffffu, p < NZ / 2);
+      if (p >= NZ / 2) continue;
+      cplx<T> *row = plane + p * (NX + 2);
+      merge_pair<T, NX>(row, row + P, 1, row, lg, mask);
+      fft_row<T, NX, true>(row, 1, twx, lg, mask);
+      T *d0 = dst + (size_t)(2 * p) * NX;
+      const T *a0 = add ? add + (size_t)(2 * p) * NX : nullptr;
+      for (int n = lg; n < NX; n += G) {
+        const cplx<T> z = row[n];
+        T v0 = z.x * scale, v1 = z.y * scale;
+        if (a0) { v0 += a0[n]; v1 += a0[NX + n]; }
+        d0[n] = v0;
+        d0[NX + n] = v1;
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------------------
+// axis kernels (planes larger than shared memory)
+// --------------------------------------------------------------------------
+
+// x forward: a CTA takes PPC row pairs of one plane.  grid (ceil(NZ/2/PPC), ny)
+template <typename T, int NX>
+__global__ void __launch_bounds__(kThreads)
+k_xfwd_rows(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx_g, int nz,
+            T in_scale) {
+  constexpr int P = NX / 2 + 1;
+  constexpr int G = FftPlan<NX>::G;
+  constexpr int PPC = kThreads / G;  // pairs per CTA
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *buf = twx + NX;  // PPC rows of NX
+  const int j = blockIdx.y;
+  const int p0 = blockIdx.x * PPC;
+  const int np = min(PPC, nz / 2 - p0);
+  const int tid = threadIdx.x;
+  load_twiddles<T>(twx, twx_g, NX);
+  {
+    const T *src = in + ((size_t)j * nz + 2 * p0) * NX;
+    T *bf = reinterpret_cast<T *>(buf);
+    for (int idx = tid; idx < np * 2 * NX; idx += kThreads) {
+      const int k = idx / NX, n = idx - k * NX;
+      bf[((k >> 1) * NX + n) * 2 + (k & 1)] = src[idx] * in_scale;
+    }
+  }
+  __syncthreads();
+  const int gid = tid / G, lg = tid % G;
+  const unsigned mask = __ballot_sync(0xffffffffu, gid < np);
+  if (gid >= np) return;
+  cplx<T> *row = buf + gid * NX;
+  fft_row<T, NX, false>(row, 1, twx, lg, mask);
+  cplx<T> *dA = S + ((size_t)j * nz + 2 * (p0 + gid)) * P;
+  split_pair<T, NX>(row, dA, dA + P, 1, lg, mask);
+}
+
+// x inverse.  out = addend + scale * result
+template <typename T, int NX>
+__global__ void __launch_bounds__(kThreads)
+k_xinv_rows(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx_g,
+            int nz, T scale) {
+  constexpr int P = NX / 2 + 1;
+  constexpr int G = FftPlan<NX>::G;
+  constexpr int PPC = kThreads / G;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *buf = twx + NX;
+  const int j = blockIdx.y;
+  const int p0 = blockIdx.x * PPC;
+  const int np = min(PPC, nz / 2 - p0);
+  const int tid = threadIdx.x;
+  load_twiddles<T>(twx, twx_g, NX);
+  __syncthreads();
+  const int gid = tid / G, lg = tid % G;
+  const unsigned mask = __ballot_sync(0xffffffffu, gid < np);
+  if (gid >= np) return;
+  const int p = p0 + gid;
+  cplx<T> *row = buf + gid * NX;
+  const cplx<T> *sA = S + ((size_t)j * nz + 2 * p) * P;
+  merge_pair<T, NX>(sA, sA + P, 1, row, lg, mask);
+  fft_row<T, NX, true>(row, 1, twx, lg, mask);
+  T *d0 = out + ((size_t)j * nz + 2 * p) * NX;
+  const T *a0 = addend ? addend + ((size_t)j * nz + 2 * p) * NX : nullptr;
+  for (int n = lg; n < NX; n += G) {
+    const cplx<T> z = row[n];
+    T v0 = z.x * scale, v1 = z.y * scale;
+    if (a0) { v0 += a0[n]; v1 += a0[NX + n]; }
+    d0[n] = v0;
+    d0[NX + n] = v1;
+  }
+}
+
+// z columns, in place: a CTA takes W consecutive kx columns of one plane.
+// grid (ceil(P / W), ny), block W * G lanes.
+template <typename T, int NZ, bool INV, int W>
+__global__ void __launch_bounds__(1024)
+k_zcols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twz_g, int P) {
+  constexpr int G = FftPlan<NZ>::G;
+  constexpr int PITCH = W + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T> *twz = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *tile = twz + NZ;  // [NZ][PITCH]
+  const int j = blockIdx.y;
+  const int c0 = blockIdx.x * W;
+  const int nc = min(W, P - c0);
+  const int tid = threadIdx.x;
+  const int nthr = W * G;
+  load_twiddles<T>(twz, twz_g, NZ);
+  cplx<T> *base = S + (size_t)j * NZ * P + c0;
+  for (int idx = tid; idx < NZ * W; idx += nthr) {
+    const int k = idx / W, c = idx - k * W;
+    if (c < nc) tile[k * PITCH + c] = base[(size_t)k * P + c];
+  }
+  __syncthreads();
+  {
+    const int gid = tid / G, lg = tid % G;
+    const unsigned mask = __ballot_sync(warp_full_mask(), gid < nc);
+    if (gid < nc) fft_row<T, NZ, INV>(tile + gid, PITCH, twz, lg, mask);
+  }
+  __syncthreads();
+  for (int idx = tid; idx < NZ * W; idx += nthr) {
+    const int k = idx / W, c = idx - k * W;
+    if (c < nc) base[(size_t)k * P + c] = tile[k * PITCH + c];
+  }
+}
+
+// --------------------------------------------------------------------------
+// dispatch
+// --------------------------------------------------------------------------
+template <typename T> size_t plane_smem_bytes(int nx, int nz) {
+  return sizeof(cplx<T>) * ((size_t)nx + nz + (size_t)nz * (nx / 2 + 1));
+}
+
+template <typename T> constexpr int zcols_width() { return sizeof(T) == 4 ? 16 : 8; }
+
+#define IBM_FOR_EACH_N(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+// plane kernels are instantiated for square-ish planes that fit in shared memory
+#define IBM_PLANE_SHAPES(X)                                                    \
+  X(8, 8) X(12, 12) X(16, 16) X(24, 24) X(32, 32) X(48, 48) X(64, 64) X(96, 96) \
+  X(128, 128) X(192, 192) X(256, 128) X(128, 256) X(64, 128) X(128, 64)
+
+template <typename T> static bool plane_supported(int nx, int nz) {
+#define X(a, b) if (nx == a && nz == b) return plane_smem_bytes<T>(nx, nz) <= kPlaneSmemLimit;
+  IBM_PLANE_SHAPES(X)
+#undef X
+  return false;
+}
+
+template <typename T, int NX, int NZ> static cudaError_t set_plane_attr() {
+  const int bytes = (int)plane_smem_bytes<T>(NX, NZ);
+  cudaError_t e = cudaFuncSetAttribute(k_plane_fwd<T, NX, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_plane_inv<T, NX, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+}
+
+template <typename T>
+cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
+                           const cplx<T> *twz, T in_scale, cudaStream_t st) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, P = nx / 2 + 1;
+  if (g.use_plane && plane_supported<T>(nx, nz)) {
+    const size_t bytes = plane_smem_bytes<T>(nx, nz);
+#define X(a, b)                                                                     \
+  if (nx == a && nz == b) {                                                         \
+    if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
+      static bool attr = false;                                                     \
+      if (!attr) { cudaError_t e = set_plane_attr<T, a, b>(); if (e) return e; attr = true; } \
+      k_plane_fwd<T, a, b><<<ny, kThreads, bytes, st>>>(in, S, twx, twz, in_scale);  \
+      return cudaGetLastError();                                                    \
+    }                                                                               \
+  }
+    IBM_PLANE_SHAPES(X)
+#undef X
+  }
+  // axis path: x rows then z columns
+  bool done = false;
+#define X(N)                                                                               \
+  if (nx == N) {                                                                           \
+    constexpr int PPC = kThreads / FftPlan<N>::G;                                          \
+    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)PPC * N);                 \
+    dim3 grid(ceil_div(nz / 2, PPC), ny);                                                  \
+    static bool attr = false;                                                              \
+    if (!attr) {                                                                           \
+      cudaError_t e = cudaFuncSetAttribute(k_xfwd_rows<T, N>,                              \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                           (int)bytes);                                    \
+      if (e) return e;                                                                     \
+      attr = true;                                                                         \
+    }                                                                                      \
+    k_xfwd_rows<T, N><<<grid, kThreads, bytes, st>>>(in, S, twx, nz, in_scale);            \
+    done = true;                                                                           \
+  }
+  IBM_FOR_EACH_N(X)
+#undef X
+  if (!done) return cudaErrorInvalidValue;
+  done = false;
+  constexpr int W = zcols_width<T>();
+#define X(N)                                                                               \
+  if (nz == N) {                                                                           \
+    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)N * (W + 1));              \
+    static bool attr = false;                                                              \
+    if (!attr) {                                                                           \
+      cudaError_t e = cudaFuncSetAttribute(k_zcols<T, N, false, W>,                        \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                           (int)bytes);                                    \
+      if (e) return e;                                                                     \
+      attr = true;                                                                         \
+    }                                                                                      \
+    dim3 grid(ceil_div(P, W), ny);                                                         \
+    k_zcols<T, N, false, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P);            \
+    done = true;                                                                           \
+  }
+  IBM_FOR_EACH_N(X)
+#undef X
+  if (!done) return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
+                           const cplx<T> *twz, T scale, cudaStream_t st) {
+  const int nx = g.nx, ny = g.ny, nz = g.nz, P = nx / 2 + 1;
+  if (g.use_plane && plane_supported<T>(nx, nz)) {
+    const size_t bytes = plane_smem_bytes<T>(nx, nz);
+#define X(a, b)                                                                     \
+  if (nx == a && nz == b) {                                                         \
+    if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
+      static bool attr = false;                                                     \
+      if (!attr) { cudaError_t e = set_plane_attr<T, a, b>(); if (e) return e; attr = true; } \
+      k_plane_inv<T, a, b><<<ny, kThreads, bytes, st>>>(S, out, addend, twx, twz, scale); \
+      return cudaGetLastError();                                                    \
+    }                                                                               \
+  }
+    IBM_PLANE_SHAPES(X)
+#undef X
+  }
+  bool done = false;
+  constexpr int W = zcols_width<T>();
+#define X(N)                                                                               \
+  if (nz == N) {                                                                           \
+    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)N * (W + 1));              \
+    static bool attr = false;                                                              \
+    if (!attr) {                                                                           \
+      cudaError_t e = cudaFuncSetAttribute(k_zcols<T, N, true, W>,                         \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                           (int)bytes);                                    \
+      if (e) return e;                                                                     \
+      attr = true;                                                                         \
+    }                                                                                      \
+    dim3 grid(ceil_div(P, W), ny);                                                         \
+    k_zcols<T, N, true, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P);             \
+    done = true;                                                                           \
+  }
+  IBM_FOR_EACH_N(X)
+#undef X
+  if (!done) return cudaErrorInvalidValue;
+  done = false;
+#define X(N)                                                                               \
+  if (nx == N) {                                                                           \
+    constexpr int PPC = kThreads / FftPlan<N>::G;                                          \
+    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)PPC * N);                 \
+    dim3 grid(ceil_div(nz / 2, PPC), ny);                                                  \
+    static bool attr = false;                                                              \
+    if (!attr) {                                                                           \
+      cudaError_t e = cudaFuncSetAttribute(k_xinv_rows<T, N>,                              \
+                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
+                                           (int)bytes);                                    \
+      if (e) return e;                                                                     \
+      attr = true;                                                                         \
+    }                                                                                      \
+    k_xinv_rows<T, N><<<grid, kThreads, bytes, st>>>(S, out, addend, twx, nz, scale);       \
+    done = true;                                                                           \
+  }
+  IBM_FOR_EACH_N(X)
+#undef X
+  if (!done) return cudaErrorInvalidValue;
+  return cudaGetLastError();
+}
+
+template cudaError_t launch_forward<float>(const TransformGeom &, const float *, float2 *, const float2 *,
+                                           const float2 *, float, cudaStream_t);
+template cudaError_t launch_forward<double>(const TransformGeom &, const double *, double2 *, const double2 *,
+                                            const double2 *, double, cudaStream_t);
+template cudaError_t launch_inverse<float>(const TransformGeom &, float2 *, float *, const float *,
+                                           const float2 *, const float2 *, float, cudaStream_t);
+template cudaError_t launch_inverse<double>(const TransformGeom &, double2 *, double *, const double *,
+                                            const double2 *, const double2 *, double, cudaStream_t);
+
+bool transform_size_supported(int n) {
+#define X(N) if (n == N) return true;
+  IBM_FOR_EACH_N(X)
+#undef X
+  return false;
+}
+
+}  // namespace ibm

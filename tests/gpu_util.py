@@ -1,0 +1,37 @@
+"""Helpers shared by the GPU tests (device transfer, tolerances)."""
+
+import math
+
+import numpy as np
+
+# Relative L2 tolerances against the FP64 oracle.
+#   FP64 path: direct method, round-off only (spec target 1e-12).
+#   FP32 path after refinement: 1e-6 (spec target); FP32 storage of the
+#   result alone contributes ~6e-8.
+TOL_FP64 = 1e-12
+TOL_FP32 = 1e-6
+# Interpolation / spreading in FP32: the weights are evaluated in FP32 from an
+# FP64 offset, each of the <= 64 products rounds once and the sums are FP32
+# (spreading adds atomics in any order).  Error bound ~ (support + log2 K)
+# eps32 relative to the sum of magnitudes; 2e-6 relative L2 covers it.
+TOL_IBM_FP32 = 2e-6
+TOL_IBM_FP64 = 1e-13
+
+
+def grid(nx, ny, nz, Lx=2 * math.pi, Ly=2.0, Lz=2 * math.pi):
+    return (nx, ny, nz, Lx / nx, Ly / ny, Lz / nz)
+
+
+def dev(a, dtype):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).to(device="cuda", dtype=dtype).contiguous()
+
+
+def host(t):
+    return t.detach().double().cpu().numpy()
+
+
+def rel_l2(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.linalg.norm((x - ref).ravel()) / max(np.linalg.norm(ref.ravel()), 1e-300))

@@ -1,0 +1,150 @@
+"""GPU parity of the Poisson and Helmholtz solves against the FP64 oracle.
+
+Every case builds a seeded synthetic right-hand side, runs the CUDA path
+through the C ABI and compares element by element with the oracle
+(relative L2).  Shapes cover the one-CTA-per-plane transform path, the
+split x/z path (planes larger than shared memory), radix-3 sizes, ragged
+pencil tiles and the smallest supported grid.
+"""
+
+import math
+
+import numpy as np
+import pytest
+
+from oracle import ibm_oracle as O
+from paper_2406_19920_gb300 import synth
+import paper_2406_19920_gb300 as ibm
+from tests.gpu_util import TOL_FP32, TOL_FP64, dev, grid, host, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SHAPES = [
+    (32, 32, 32),     # workload-0 grid, plane path
+    (8, 8, 8),        # smallest grid
+    (12, 10, 24),     # radix 3, odd ny, ragged pencil tile
+    (48, 40, 48),     # radix 3
+    (96, 33, 64),     # mixed shape, odd ny
+    (256, 12, 256),   # plane larger than shared memory (split x/z path)
+    (384, 9, 32),     # longest radix-3 row, split path
+]
+
+
+def _plan(nx, ny, nz, g, prec, refine=1):
+    return ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, refine)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+def test_poisson_fp64_matches_oracle(shape):
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    b = synth.white_noise(nx, ny, nz, workload=10, stream=0) + 0.3
+    ref, mean_b = O.poisson_solve(b, g)
+    plan = _plan(nx, ny, nz, g, ibm.IBM_FP64)
+    try:
+        rhs = dev(b, torch.float64)
+        phi = torch.empty_like(rhs)
+        info = ibm.ibm_poisson_solve(plan, rhs, phi, info=True)
+        assert rel_l2(host(phi), ref) <= TOL_FP64
+        assert abs(info["removed_mean"] - mean_b) <= 1e-12 * max(1.0, abs(mean_b))
+        assert info["rel_residual"] < 1e-12
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("refine", [1, 2])
+def test_poisson_fp32_refined_matches_oracle(shape, refine):
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    b32 = synth.white_noise(nx, ny, nz, workload=11, stream=0).astype(np.float32)
+    ref, _ = O.poisson_solve(b32.astype(np.float64), g)
+    plan = _plan(nx, ny, nz, g, ibm.IBM_FP32_REFINED, refine)
+    try:
+        rhs = dev(b32, torch.float32)
+        phi = torch.empty_like(rhs)
+        info = ibm.ibm_poisson_solve(plan, rhs, phi, info=True)
+        assert rel_l2(host(phi), ref) <= TOL_FP32
+        assert info["refine_iters"] == refine
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
+def test_poisson_workload0_eigen_rhs_both_precisions():
+    """Workload 0: 32^3, sum of 4 grid eigenfunctions + noise 1e-3."""
+    g = grid(32, 32, 32)
+    b, _ = synth.rhs_eigen_sum(32, 32, 32, workload=0)
+    for prec, dt, tol in ((ibm.IBM_FP64, torch.float64, TOL_FP64), (ibm.IBM_FP32_REFINED, torch.float32, TOL_FP32)):
+        bb = b.astype(np.float32).astype(np.float64) if dt == torch.float32 else b
+        ref, _ = O.poisson_solve(bb, g)
+        plan = _plan(32, 32, 32, g, prec)
+        try:
+            rhs = dev(bb, dt)
+            phi = torch.empty_like(rhs)
+            ibm.ibm_poisson_solve(plan, rhs, phi)
+            torch.cuda.synchronize()
+            assert rel_l2(host(phi), ref) <= tol
+        finally:
+            ibm.ibm_plan_destroy(plan)
+
+
+def test_poisson_in_place_and_128_lowpass():
+    """Workload 1 right-hand side (128^3 low-passed noise), rhs == phi."""
+    g = grid(128, 128, 128)
+    b = synth.rhs_lowpass_noise(128, 128, 128, kmax=32.0, workload=1).astype(np.float32)
+    ref, _ = O.poisson_solve(b.astype(np.float64), g)
+    plan = _plan(128, 128, 128, g, ibm.IBM_FP32_REFINED, 1)
+    try:
+        x = dev(b, torch.float32)
+        info = ibm.ibm_poisson_solve(plan, x, x, info=True)
+        err = rel_l2(host(x), ref)
+        assert err <= TOL_FP32, (err, info)
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (12, 10, 24), (256, 12, 256), (48, 17, 96)])
+@pytest.mark.parametrize("bc", [ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_CELL_DIRICHLET,
+                                ibm.IBM_FIELD_FACE_DIRICHLET])
+@pytest.mark.parametrize("c", [5e-6, 0.05])
+def test_helmholtz_matches_oracle(shape, bc, c):
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    r = synth.white_noise(nx, ny, nz, workload=12, stream=bc)
+    for prec, dt, tol in ((ibm.IBM_FP64, torch.float64, TOL_FP64), (ibm.IBM_FP32_REFINED, torch.float32, TOL_FP32)):
+        rr = r.astype(np.float32).astype(np.float64) if dt == torch.float32 else r
+        ref = O.helmholtz_solve(rr, g, c, bc)
+        plan = _plan(nx, ny, nz, g, prec, 1)
+        try:
+            rhs = dev(rr, dt)
+            u = torch.empty_like(rhs)
+            ibm.ibm_helmholtz_solve(plan, c, bc, rhs, u)
+            torch.cuda.synchronize()
+            got = host(u)
+            assert rel_l2(got, ref) <= tol, (prec, rel_l2(got, ref))
+            if bc == ibm.IBM_FIELD_FACE_DIRICHLET:
+                assert np.all(got[0] == 0.0)
+        finally:
+            ibm.ibm_plan_destroy(plan)
+
+
+def test_invalid_arguments_rejected_before_launch():
+    g = grid(32, 32, 32)
+    with pytest.raises(ibm.IbmError) as e:
+        ibm.ibm_plan_create(30, 32, 32, g[3:], ibm.IBM_FP32_REFINED, 1)
+    assert e.value.code == ibm.IBM_ERR_ARG
+    with pytest.raises(ibm.IbmError):
+        ibm.ibm_plan_create(32, 4, 32, g[3:], ibm.IBM_FP32_REFINED, 1)
+    with pytest.raises(ibm.IbmError):
+        ibm.ibm_plan_create(32, 32, 32, (1.0, -1.0, 1.0), ibm.IBM_FP64, 0)
+    plan = _plan(32, 32, 32, g, ibm.IBM_FP64)
+    try:
+        x = torch.zeros(32 * 32 * 32 + 1, dtype=torch.float64, device="cuda")
+        with pytest.raises(ibm.IbmError):
+            ibm.ibm_poisson_solve(plan, x[1:].data_ptr() + 4, x.data_ptr())
+        with pytest.raises(ibm.IbmError):
+            ibm.ibm_helmholtz_solve(plan, -1.0, 0, x, x)
+    finally:
+        ibm.ibm_plan_destroy(plan)
