@@ -1,0 +1,454 @@
+"""Benchmark: one RK stage (ibm_substep) of the immersed-boundary solver.
+
+A step is one pass of the whole hot path over one state: E1 explicit terms,
+L2 marker motion, L1 interpolation / force / spreading, three Helmholtz
+solves, divergence, the refined Poisson solve and the projection with the
+pressure update.  Workload: 128^3 grid on [0,2pi) x [0,2] x [0,2pi]
+(periodic x, z; walls in y), FP32 fields with one refinement step, a
+20,000-marker Fibonacci sphere (radius 0.25, centre (pi, 1, pi)) translating
+at 0.1 in x, a seeded discretely divergence-free velocity with energy
+spectrum ~ k^-5/3 (k <= 16).  Four independent states rotate across steps
+(4 x 56 MB > 129 MB L2) so every step reads its fields from HBM.
+
+Output: one JSON line (rank 0).  `value` is grid points advanced per second
+(all ranks), `e2e` the same through host buffers, `roofline` the dominant
+kernel's achieved HBM bandwidth from CUDA events around its launches in the
+timed region, `cpu_baseline` the FP64 CPU oracle on a bounded sample.
+`--impl reference` times that oracle alone.
+"""
+
+from __future__ import annotations
+
+import argparse
+import ctypes
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Poisson solves/s and grid-pts/s at 1 GB300 (% HBM roofline); FP32-refined vs FP64 at 1e-6; "
+          "p50/p99")
+NX = NY = NZ = 128
+N_MARKERS = 20000
+DT, NU = 1e-3, 1e-2
+N_STATES = 4
+KERNEL_SOURCES = {"forward": "transforms.cu", "inverse": "transforms.cu", "pencil": "pencil.cu",
+                  "residual": "stencil.cu", "explicit": "substep.cu", "divergence": "substep.cu",
+                  "project": "substep.cu", "interp": "ibm_kernels.cu", "spread": "ibm_kernels.cu",
+                  "motion": "ibm_kernels.cu"}
+
+
+def workload_grid():
+    from paper_2406_19920_gb300 import synth
+    return synth.grid(NX, NY, NZ)
+
+
+def make_inputs(g):
+    """Seeded host inputs (FP64) shared by the GPU arm and the CPU baseline."""
+    from paper_2406_19920_gb300 import synth
+    u, v, w = synth.div_free_velocity(g, workload=1, kmax=16.0)
+    X0, dV = synth.fibonacci_sphere(N_MARKERS, 0.25, (math.pi, 1.0, math.pi), g[3])
+    return (u, v, w), X0, dV
+
+
+# ---------------------------------------------------------------------------
+# helpers
+# ---------------------------------------------------------------------------
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def measured_peak():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def source_digest(kind):
+    p = os.path.join(ROOT, "paper_2406_19920_gb300", "csrc", KERNEL_SOURCES[kind])
+    with open(p, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def ncu_traffic(kind, workload):
+    """DRAM bytes per launch from the committed ncu summary, if the kernel
+    source is unchanged since the capture; else None."""
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            d = json.load(f)
+    except (OSError, ValueError):
+        return None
+    e = d.get(kind)
+    if not e or e.get("workload") != workload or e.get("source_sha256_16") != source_digest(kind):
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+def algorithmic_bytes(kind, launches_per_step, esz=4):
+    """Compulsory HBM bytes per launch of each kernel kind at the workload.
+
+    pts = nx ny nz real points; spec = ny nz (nx/2+1) complex entries.
+    forward: read field + write spectrum; inverse: read spectrum + write field
+    (+ read the added field for 4 of the 5 inverse launches of a stage:
+    three Helmholtz increments and the refinement update); pencil: read +
+    write spectrum; residual: read b, x, write r; explicit: read u,v,w,p,
+    N x3, write du,dv,dw, N x3; divergence: read u,v,w, write b; project: read
+    u,v,w,p,phi, write u,v,w,p.
+    """
+    pts = NX * NY * NZ
+    spec = NY * NZ * (NX // 2 + 1)
+    cs = 2 * esz
+    table = {
+        "forward": pts * esz + spec * cs,
+        "inverse": spec * cs + pts * esz + pts * esz * 4.0 / 5.0,
+        "pencil": 2 * spec * cs,
+        "residual": 3 * pts * esz,
+        "explicit": 13 * pts * esz,
+        "divergence": 4 * pts * esz,
+        "project": 9 * pts * esz,
+        "interp": N_MARKERS * 3 * (3 * esz + 27 * 2 * esz),
+        "spread": N_MARKERS * 3 * (5 * esz + 27 * esz * 2),
+        "motion": N_MARKERS * (3 + 6) * esz,
+    }
+    return table.get(kind)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_gpu(args):
+    import torch
+    import paper_2406_19920_gb300 as ibm
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    g = workload_grid()
+    (u, v, w), X0, dV = make_inputs(g)
+    f32 = torch.float32
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", f32)
+    plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
+    # N_STATES independent states; each step advances the next one
+    states, keep = [], []
+    for s in range(N_STATES):
+        fields = [dev(u), dev(v), dev(w), torch.zeros((NY, NZ, NX), dtype=f32, device="cuda")]
+        Ns = [torch.zeros((NY, NZ, NX), dtype=f32, device="cuda") for _ in range(3)]
+        st = ibm.ibm_state(*[t.data_ptr() for t in fields + Ns], 0.0)
+        states.append(st)
+        keep.append((fields, Ns))
+    X0d, dVd = dev(X0), dev(dV)
+    X = torch.empty((N_MARKERS, 3), dtype=f32, device="cuda")
+    Ud = torch.empty_like(X)
+    F = torch.empty_like(X)
+    params = (ctypes.c_double * 4)(0.1, 0.0, 0.0, 0.0)
+    mk = ibm.ibm_markers(N_MARKERS, X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
+                         ibm.IBM_MOTION_TRANSLATE, params)
+    stream = torch.cuda.current_stream()
+
+    def step(i):
+        st = states[i % N_STATES]
+        ibm.ibm_substep(plan, st, (i // N_STATES) % 3 + 1, DT, NU, mk, stream=stream)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    info = ibm.ibm_substep(plan, states[0], 1, DT, NU, mk, info=True)
+
+    def barrier():
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # ---- timed region: K steps, per-kernel events on ----
+    ibm.ibm_plan_profile(plan, True)
+    ibm.ibm_plan_profile_read(plan)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
+    barrier()
+    with ClockSampler(local) as clk:
+        ev[0].record()
+        for i in range(args.steps):
+            step(args.warmup + i)
+            ev[i + 1].record()
+        barrier()
+    prof = ibm.ibm_plan_profile_read(plan)
+    ibm.ibm_plan_profile(plan, False)
+    step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
+    total_ms = ev[0].elapsed_time(ev[-1])
+    if dist:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    pts = NX * NY * NZ
+    value = pts * args.steps * ws / (total_ms * 1e-3)
+
+    # ---- same steps without events (profiling overhead check) ----
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(args.steps):
+        step(args.warmup + args.steps + i)
+    e1.record()
+    barrier()
+    unprof_ms = e0.elapsed_time(e1)
+
+    # ---- end to end: host buffers, copies inside the timed region ----
+    host_in = [torch.from_numpy(np.ascontiguousarray(a)).to(f32).pin_memory()
+               for a in (u, v, w, np.zeros_like(u), np.zeros_like(u), np.zeros_like(u), np.zeros_like(u))]
+    host_out = [torch.empty((NY, NZ, NX), dtype=f32).pin_memory() for _ in range(4)]
+    dfields, dNs = keep[0]
+    dst_in = dfields + dNs
+    h2d = sum(t.numel() * t.element_size() for t in host_in)
+    d2h = sum(t.numel() * t.element_size() for t in host_out)
+    e2e_steps = max(3, min(args.steps, 20))
+    barrier()
+    e0.record()
+    for i in range(e2e_steps):
+        for dsrc, hsrc in zip(dst_in, host_in):
+            dsrc.copy_(hsrc, non_blocking=True)
+        states[0].t = 0.0
+        ibm.ibm_substep(plan, states[0], 1, DT, NU, mk, stream=stream)
+        for hdst, dsrc in zip(host_out, dfields):
+            hdst.copy_(dsrc, non_blocking=True)
+    e1.record()
+    barrier()
+    e2e_ms = e0.elapsed_time(e1)
+    e2e_value = pts * e2e_steps * ws / (e2e_ms * 1e-3)
+
+    # ---- standalone Poisson: FP32-refined vs FP64 at 128^3 ----
+    solves = poisson_compare(ibm, torch, g)
+
+    # ---- roofline of the dominant kernel ----
+    dom = max(prof, key=lambda k: prof[k][0])
+    dom_ms, dom_launches = prof[dom]
+    avg_ms = dom_ms / max(dom_launches, 1)
+    alg = algorithmic_bytes(dom, dom_launches / args.steps)
+    peak, peak_src = measured_peak()
+    achieved = alg / (avg_ms * 1e-3) / 1e9
+    workload_name = "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere"
+    traffic = ncu_traffic(dom, workload_name)
+    launches = sum(c for _, c in prof.values())
+
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "grid-pts/s",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": workload_name, "grid": [NX, NY, NZ], "domain": "[0,2pi)x[0,2]x[0,2pi]",
+                   "markers": N_MARKERS, "precision": "FP32 fields, FP64 zero mode, 1 float-float refinement",
+                   "l2": "4 rotating states (224 MB) > 129 MB L2", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "e2e": {"value": e2e_value, "unit": "grid-pts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": e2e_steps},
+        "gpu_launches": launches,
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms},
+        "kernels_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
+        "launches_per_step": {k: prof[k][1] / args.steps for k in prof},
+        "p50_ms": float(np.percentile(step_ms, 50)),
+        "p99_ms": float(np.percentile(step_ms, 99)),
+        "value_unprofiled": pts * args.steps * ws / (unprof_ms * 1e-3),
+        "poisson": solves,
+        "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")},
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args)
+    ibm.ibm_plan_destroy(plan)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def poisson_compare(ibm, torch, g):
+    """Standalone Poisson solves/s at 128^3: FP32 + 1 refinement vs FP64, and
+    the FP32 result's relative L2 difference from the FP64 GPU result."""
+    from paper_2406_19920_gb300 import synth
+    b = synth.rhs_lowpass_noise(NX, NY, NZ, kmax=32.0, workload=1)
+    res = {}
+    outs = {}
+    for name, prec, dt, ref in (("fp32_refined", ibm.IBM_FP32_REFINED, torch.float32, 1),
+                                ("fp64", ibm.IBM_FP64, torch.float64, 0)):
+        plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], prec, ref)
+        nb = 16  # 16 rhs + 16 solutions > L2
+        rhs = [torch.from_numpy(b).to("cuda", dt) for _ in range(nb)]
+        phi = [torch.empty_like(r) for r in rhs]
+        for i in range(3):
+            ibm.ibm_poisson_solve(plan, rhs[i], phi[i])
+        K = 40
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
+        torch.cuda.synchronize()
+        evs[0].record()
+        for i in range(K):
+            ibm.ibm_poisson_solve(plan, rhs[i % nb], phi[i % nb])
+            evs[i + 1].record()
+        torch.cuda.synchronize()
+        lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
+        ms = evs[0].elapsed_time(evs[-1]) / K
+        outs[name] = phi[0].double().cpu().numpy()
+        res[name] = {"solves_per_s": 1e3 / ms, "grid_pts_per_s": NX * NY * NZ * 1e3 / ms, "ms": ms,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "hbm_frac_method_bytes": (24 if dt == torch.float32 else 48) * NX * NY * NZ / (ms * 1e-3)
+                     / 1e9 / measured_peak()[0]}
+        ibm.ibm_plan_destroy(plan)
+        del rhs, phi
+    d = outs["fp32_refined"] - outs["fp64"]
+    res["fp32_refined_rel_l2_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(outs["fp64"]))
+    res["speedup_fp32_refined_over_fp64"] = res["fp32_refined"]["solves_per_s"] / res["fp64"]["solves_per_s"]
+    return res
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle arm
+# ---------------------------------------------------------------------------
+
+def oracle_stage_rate(n_stages):
+    """Time the FP64 oracle's RK stage on the benchmark workload."""
+    from oracle import ibm_oracle as O
+    g = workload_grid()
+    (u, v, w), X0, dV = make_inputs(g)
+    z = np.zeros_like(u)
+    st = dict(u=u, v=v, w=w, p=z.copy(), N_prev=(z, z, z), t=0.0)
+    mk = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=(0.1, 0.0, 0.0))
+    t0 = time.perf_counter()
+    for i in range(n_stages):
+        st, _ = O.rk_stage(st, mk, i % 3 + 1, DT, NU, g)
+    el = time.perf_counter() - t0
+    return NX * NY * NZ * n_stages / el, el
+
+
+def cpu_baseline(args):
+    n = 3
+    rate, el = oracle_stage_rate(n)
+    return {"value": rate, "unit": "grid-pts/s", "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d consecutive RK stages of the same 128^3 workload (FP64 numpy, dense eigen-bases, "
+                      "BLAS threads = all host cores), %.1f s" % (n, el)}
+
+
+def run_reference(args):
+    ws, rank, local = dist_env()
+    if rank != 0:
+        return
+    for _ in range(args.warmup):
+        oracle_stage_rate(1)
+    t0 = time.perf_counter()
+    stage_s = []
+    for _ in range(args.steps):
+        r, el = oracle_stage_rate(1)
+        stage_s.append(el)
+    total = time.perf_counter() - t0
+    value = NX * NY * NZ * args.steps / sum(stage_s)
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid-pts/s", "n_gpus": ws,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(stage_s) / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere", "grid": [NX, NY, NZ],
+                      "markers": N_MARKERS},
+           "cpu_baseline": {"value": value, "unit": "grid-pts/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": "one FP64 oracle RK stage of the workload per step, %.1f s total" % total},
+           "e2e": {"value": value, "unit": "grid-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -18,7 +18,7 @@
  * Conventions shared by every call
  * --------------------------------
  * Grid: nx x ny x nz cells, spacings h = {hx, hy, hz}.  nx and nz must be
- *   2^a 3^b with b <= 1 and 8 <= n <= 512; 8 <= ny <= 1024.
+ *   2^a 3^b with b <= 1 and 8 <= n <= 512; 8 <= ny <= 512.
  * Layout: every field is a dense C array [ny][nz][nx] (x fastest, then z,
  *   then y) in DEVICE memory, of the plan's precision (float for
  *   IBM_FP32_REFINED, double for IBM_FP64).
@@ -116,6 +116,29 @@ int ibm_plan_destroy(ibm_plan plan);
 int ibm_plan_set_delta(ibm_plan plan, int kernel);
 /* Bytes of device memory the plan holds. */
 size_t ibm_plan_workspace_bytes(ibm_plan plan);
+
+/* Per-kernel timing (tracing).  While enabled, every kernel the plan
+ * launches is bracketed by a pair of CUDA events on its stream; the pairs
+ * are accumulated per kernel kind (IBM_K_*).  ibm_plan_profile_read
+ * synchronises the device, writes the summed milliseconds and launch counts
+ * of the first max_kinds kinds to ms[] / launches[] (either may be NULL),
+ * clears the record and returns IBM_K_COUNT.  The paper reports per-task
+ * time shares (Sec. 4); this gives the same breakdown per kernel. */
+enum {
+  IBM_K_FORWARD = 0,   /* x/z forward transform of a right-hand side      */
+  IBM_K_PENCIL = 1,    /* tridiagonal solves along y                      */
+  IBM_K_INVERSE = 2,   /* z/x inverse transform                           */
+  IBM_K_RESIDUAL = 3,  /* refinement residual                             */
+  IBM_K_EXPLICIT = 4,  /* E1 explicit terms                               */
+  IBM_K_MOTION = 5,    /* L2 marker motion                                */
+  IBM_K_INTERP = 6,    /* L1 interpolation + force                        */
+  IBM_K_SPREAD = 7,    /* L1 spreading                                    */
+  IBM_K_DIVERGENCE = 8,/* E2 divergence                                   */
+  IBM_K_PROJECT = 9,   /* E3 projection + pressure update                 */
+  IBM_K_COUNT = 10
+};
+int ibm_plan_profile(ibm_plan plan, int enable);
+int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launches);
 
 /* Poisson solve, Eq. 2f (S2.1 + S2.2): L_h phi = rhs - mean(rhs) with the
  * 7-point Laplacian, periodic x/z, homogeneous Neumann y (Appendix B,

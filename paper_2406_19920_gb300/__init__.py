@@ -75,6 +75,8 @@ _SIG = {
     "ibm_plan_destroy": (_I, [_P]),
     "ibm_plan_set_delta": (_I, [_P, _I]),
     "ibm_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "ibm_plan_profile": (_I, [_P, _I]),
+    "ibm_plan_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ibm_poisson_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_helmholtz_solve": (_I, [_P, _D, _I, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_interp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
@@ -164,6 +166,23 @@ def ibm_plan_set_delta(plan, kernel):
 
 def ibm_plan_workspace_bytes(plan):
     return int(lib().ibm_plan_workspace_bytes(plan))
+
+
+KERNEL_KINDS = ("forward", "pencil", "inverse", "residual", "explicit", "motion", "interp", "spread",
+                "divergence", "project")
+
+
+def ibm_plan_profile(plan, enable=True):
+    return _check(lib().ibm_plan_profile(plan, 1 if enable else 0))
+
+
+def ibm_plan_profile_read(plan):
+    """{kind: (total_ms, launches)} accumulated since the last read."""
+    n = len(KERNEL_KINDS)
+    ms = (_D * n)()
+    cnt = (_I * n)()
+    _check(lib().ibm_plan_profile_read(plan, n, ms, cnt))
+    return {k: (ms[i], cnt[i]) for i, k in enumerate(KERNEL_KINDS)}
 
 
 def ibm_poisson_solve(plan, rhs, phi, stream=None, info=False):

@@ -26,6 +26,8 @@ __device__ __forceinline__ unsigned warp_full_mask() {
 }
 
 bool transform_size_supported(int n);
+// Kernels one forward (or inverse) transform launches: 1 on the plane path, 2 otherwise.
+template <typename T> int transform_launches(const TransformGeom &g);
 
 // Forward: real field [ny][nz][nx] (times in_scale) -> spectrum [ny][nz][nx/2+1].
 template <typename T>

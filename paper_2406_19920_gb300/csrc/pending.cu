@@ -3,9 +3,6 @@
 #include "plan.h"
 using namespace ibm;
 extern "C" {
-int ibm_substep(ibm_plan, ibm_state *, int, double, double, ibm_markers *, void *, ibm_info *) {
-  return set_error(IBM_ERR_UNSUPPORTED, "ibm_substep: not built");
-}
 int ibm_batch_create(int, const int *, const double *, int, int, ibm_batch *) {
   return set_error(IBM_ERR_UNSUPPORTED, "ibm_batch_create: not built");
 }

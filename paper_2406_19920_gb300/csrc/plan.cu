@@ -71,10 +71,37 @@ static int upload_tables(ibm_plan_s *p) {
   return IBM_OK;
 }
 
+ProfScope::ProfScope(ibm_plan_s *plan, int k, cudaStream_t s, int n) : p(plan), kind(k), launches(n), st(s) {
+  if (!p || !p->prof_on) return;
+  if (p->evpool.empty()) {
+    cudaEvent_t e;
+    if (cudaEventCreate(&e) != cudaSuccess) return;
+    p->evpool.push_back(e);
+  }
+  a = p->evpool.back();
+  p->evpool.pop_back();
+  cudaEventRecord(a, st);
+}
+
+ProfScope::~ProfScope() {
+  if (!a) return;
+  cudaEvent_t b;
+  if (p->evpool.empty()) {
+    if (cudaEventCreate(&b) != cudaSuccess) { p->evpool.push_back(a); return; }
+  } else {
+    b = p->evpool.back();
+    p->evpool.pop_back();
+  }
+  cudaEventRecord(b, st);
+  p->prof.push_back({kind, launches, a, b});
+}
+
 static void plan_free(ibm_plan_s *p) {
   if (!p) return;
+  for (auto &r : p->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+  for (auto e : p->evpool) cudaEventDestroy(e);
   void *bufs[] = {p->S, p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3],
-                  p->twx, p->twz, p->lamx, p->lamz, p->dsc};
+                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -103,10 +130,20 @@ static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out
   cplx<T> *S = static_cast<cplx<T> *>(p->S);
   const cplx<T> *twx = static_cast<const cplx<T> *>(p->twx);
   const cplx<T> *twz = static_cast<const cplx<T> *>(p->twz);
-  IBM_CUDA_TRY(launch_forward<T>(g, in, S, twx, twz, (T)1, st));
-  IBM_CUDA_TRY(launch_pencil<T>(pp, S, static_cast<const T *>(p->lamx), static_cast<const T *>(p->lamz),
-                                mean_out, st));
-  IBM_CUDA_TRY(launch_inverse<T>(g, S, out, addend, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
+  const int nl = transform_launches<T>(g);
+  {
+    ProfScope ps(p, IBM_K_FORWARD, st, nl);
+    IBM_CUDA_TRY(launch_forward<T>(g, in, S, twx, twz, (T)1, st));
+  }
+  {
+    ProfScope ps(p, IBM_K_PENCIL, st);
+    IBM_CUDA_TRY(launch_pencil<T>(pp, S, static_cast<const T *>(p->lamx), static_cast<const T *>(p->lamz),
+                                  mean_out, st));
+  }
+  {
+    ProfScope ps(p, IBM_K_INVERSE, st, nl);
+    IBM_CUDA_TRY(launch_inverse<T>(g, S, out, addend, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
+  }
   return IBM_OK;
 }
 
@@ -163,7 +200,11 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
   if (rc) return rc;
   T *r = static_cast<T *>(p->work);
   for (int it = 0; it < iters; ++it) {
-    IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, nullptr, st));
+    {
+      ProfScope ps(p, IBM_K_RESIDUAL, st);
+      IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, nullptr,
+                                      st));
+    }
     rc = solve_once<T>(p, pp, r, out, out, nullptr, st);
     if (rc) return rc;
   }
@@ -275,6 +316,34 @@ int ibm_plan_set_delta(ibm_plan plan, int kernel) {
 }
 
 size_t ibm_plan_workspace_bytes(ibm_plan plan) { return plan ? plan->bytes : 0; }
+
+int ibm_plan_profile(ibm_plan plan, int enable) {
+  if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_profile: NULL plan");
+  plan->prof_on = enable ? 1 : 0;
+  return IBM_OK;
+}
+
+int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launches) {
+  if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_profile_read: NULL plan");
+  IBM_CUDA_TRY(cudaDeviceSynchronize());
+  double acc[IBM_K_COUNT] = {0};
+  int cnt[IBM_K_COUNT] = {0};
+  for (auto &r : plan->prof) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < IBM_K_COUNT) {
+      acc[r.kind] += t;
+      cnt[r.kind] += r.launches;
+    }
+    plan->evpool.push_back(r.a);
+    plan->evpool.push_back(r.b);
+  }
+  plan->prof.clear();
+  for (int k = 0; k < max_kinds && k < IBM_K_COUNT; ++k) {
+    if (ms) ms[k] = acc[k];
+    if (launches) launches[k] = cnt[k];
+  }
+  return IBM_K_COUNT;
+}
 
 int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream, ibm_info *info) {
   if (!plan || !rhs || !phi) return set_error(IBM_ERR_ARG, "ibm_poisson_solve: NULL argument");

@@ -7,6 +7,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <string>
+#include <vector>
 
 #include "../../include/ibm.h"
 #include "internal.h"
@@ -36,14 +37,33 @@ struct ibm_plan_s {
   void *S;           // spectrum workspace
   void *work;        // real work field (residual / divergence)
   void *bsave;       // copy of an in-place right-hand side
-  void *sub[4];      // substep fields (allocated on first substep)
+  void *sub[4];      // substep fields du, dv, dw, phi (allocated on first substep)
+  void *mkbuf;       // marker force scratch [n][3] when the caller passes none
+  size_t mkcap;      // bytes of mkbuf
   void *twx, *twz;   // twiddles W_N^m (plan precision)
   void *lamx, *lamz; // modified wavenumbers kx'^2 (P), kz'^2 (nz) (plan precision)
   double *dsc;       // device scalars: [0] removed mean, [1..4] norms, [5..7] misc
   double *hsc;       // pinned host mirror of dsc
   cudaEvent_t ev0, ev1;
   size_t bytes;      // device bytes held
+  // per-kernel tracing (ibm_plan_profile)
+  struct ProfRec { int kind, launches; cudaEvent_t a, b; };
+  int prof_on;
+  std::vector<ProfRec> prof;
+  std::vector<cudaEvent_t> evpool;
 };
+
+namespace ibm {
+// Brackets the launches of one kernel kind with events when tracing is on.
+struct ProfScope {
+  ibm_plan_s *p;
+  int kind, launches;
+  cudaStream_t st;
+  cudaEvent_t a = nullptr;
+  ProfScope(ibm_plan_s *plan, int k, cudaStream_t s, int n = 1);
+  ~ProfScope();
+};
+}  // namespace ibm
 
 namespace ibm {
 inline bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }

@@ -1,0 +1,384 @@
+// substep.cu -- one RK stage of Eq. 2a-2h (ibm_substep).
+//
+// Order of work (the paper's flowchart for one stage, Sec. 2.3):
+//   E1  explicit terms: du = u^e - u^{n-1}
+//         = dt [(a+b) nu L u - (a+b) G p - gamma N(u) - zeta N^{n-2}]   (Eq. 2a)
+//       and N(u) stored for the next stage's zeta term;
+//   L2  marker positions / surface velocity at the stage start time;
+//   L1  U^e = interp(u^{n-1} + du) (Eq. 2b), F = (U^d - U^e)/dt (Eq. 2c),
+//       du += dt spread(F) (Eq. 2d);
+//   S1  three Helmholtz solves.  Eq. 2e, (I - c L) u* = u^e - c L u^{n-1} +
+//       dt f with c = beta dt nu, is solved in increment form
+//       (I - c L) delta = du, u* = u^{n-1} + delta (same system: subtract
+//       (I - c L) u^{n-1} from both sides); u* overwrites u;
+//   E2  b = D u* / ((a+b) dt)                                          (Eq. 2f)
+//   S2  Poisson solve L phi = b (refined on the FP32 path)
+//   E3  u^n = u* - (a+b) dt G phi, p^n = p + phi - c L phi             (Eq. 2g, 2h)
+// RK coefficients: Rai & Moin's low-storage scheme, which the paper cites
+// without printing.  Advection is the conservative MAC form div(u u) with
+// two-point averages (the paper names second-order central differences).
+#include <cmath>
+
+#include "plan.h"
+
+namespace ibm {
+
+template <typename T>
+cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, const T *v, const T *w,
+                          const T *du, const T *dv, const T *dw, T *U, const T *Ud, double inv_dt, T *F,
+                          cudaStream_t st);
+template <typename T>
+cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, const T *dV, T *fu, T *fv, T *fw,
+                          double scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_motion(int n, const T *X0, T *X, T *Ud, int kind, const double *params, double t,
+                          cudaStream_t st);
+
+static const double kAlpha[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
+static const double kBeta[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
+static const double kGamma[3] = {8.0 / 15.0, 5.0 / 12.0, 3.0 / 4.0};
+static const double kZeta[3] = {0.0, -17.0 / 60.0, -5.0 / 12.0};
+
+struct Geo {
+  int nx, ny, nz;
+  double ihx, ihy, ihz;  // 1/h
+};
+
+// field accessor with periodic x, z
+template <typename T> struct F3 {
+  const T *f;
+  int nx, nz;
+  __device__ __forceinline__ T at(int j, int k, int i) const {
+    i = i < 0 ? i + nx : (i >= nx ? i - nx : i);
+    k = k < 0 ? k + nz : (k >= nz ? k - nz : k);
+    return f[((size_t)j * nz + k) * nx + i];
+  }
+};
+
+// E1: one thread per cell index (j, k, i), all three components.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_,
+           const T *__restrict__ p_, T *Nu, T *Nv, T *Nw, T *__restrict__ du, T *__restrict__ dv,
+           T *__restrict__ dw, T c_visc, T c_pres, T gam, T zet, T dt) {
+  const size_t total = (size_t)g.nx * g.ny * g.nz;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int i = (int)(idx % g.nx);
+  const int k = (int)((idx / g.nx) % g.nz);
+  const int j = (int)(idx / ((size_t)g.nx * g.nz));
+  const int ny = g.ny;
+  const F3<T> U{u_, g.nx, g.nz}, V{v_, g.nx, g.nz}, W{w_, g.nx, g.nz}, Pp{p_, g.nx, g.nz};
+  const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
+  const T h = (T)0.5;
+  // wall-aware accessors: u, w cell-centred (no-slip ghost = -value), v faces (walls 0)
+  auto uy = [&](const F3<T> &F, int jj, int kk, int ii) -> T {
+    if (jj < 0) return -F.at(0, kk, ii);
+    if (jj >= ny) return -F.at(ny - 1, kk, ii);
+    return F.at(jj, kk, ii);
+  };
+  auto vy = [&](int jj, int kk, int ii) -> T { return (jj <= 0 || jj >= ny) ? (T)0 : V.at(jj, kk, ii); };
+
+  // ---------------- u (x-faces) ----------------
+  {
+    const T u0 = U.at(j, k, i);
+    const T lap = (U.at(j, k, i + 1) - 2 * u0 + U.at(j, k, i - 1)) * ihx * ihx +
+                  (U.at(j, k + 1, i) - 2 * u0 + U.at(j, k - 1, i)) * ihz * ihz +
+                  (uy(U, j + 1, k, i) - 2 * u0 + uy(U, j - 1, k, i)) * ihy * ihy;
+    const T uc = h * (u0 + U.at(j, k, i + 1)), ucm = h * (U.at(j, k, i - 1) + u0);
+    const T tx = (uc * uc - ucm * ucm) * ihx;
+    T fy[2];
+    for (int q = 0; q < 2; ++q) {
+      const int jj = j + q;
+      const T ve = h * (vy(jj, k, i - 1) + vy(jj, k, i));
+      const T ue = (jj <= 0 || jj >= ny) ? (T)0 : h * (U.at(jj - 1, k, i) + U.at(jj, k, i));
+      fy[q] = ve * ue;
+    }
+    T fz[2];
+    for (int q = 0; q < 2; ++q) {
+      const int kk = k + q;
+      const T we = h * (W.at(j, kk, i - 1) + W.at(j, kk, i));
+      const T ue = h * (U.at(j, kk - 1, i) + U.at(j, kk, i));
+      fz[q] = we * ue;
+    }
+    const T N = tx + (fy[1] - fy[0]) * ihy + (fz[1] - fz[0]) * ihz;
+    const T G = (Pp.at(j, k, i) - Pp.at(j, k, i - 1)) * ihx;
+    const T np = zet != (T)0 ? Nu[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
+    du[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
+    Nu[idx] = N;
+  }
+  // ---------------- w (z-faces) ----------------
+  {
+    const T w0 = W.at(j, k, i);
+    const T lap = (W.at(j, k, i + 1) - 2 * w0 + W.at(j, k, i - 1)) * ihx * ihx +
+                  (W.at(j, k + 1, i) - 2 * w0 + W.at(j, k - 1, i)) * ihz * ihz +
+                  (uy(W, j + 1, k, i) - 2 * w0 + uy(W, j - 1, k, i)) * ihy * ihy;
+    const T wc = h * (w0 + W.at(j, k + 1, i)), wcm = h * (W.at(j, k - 1, i) + w0);
+    const T tz = (wc * wc - wcm * wcm) * ihz;
+    T fx[2];
+    for (int q = 0; q < 2; ++q) {
+      const int ii = i + q;
+      const T ue = h * (U.at(j, k - 1, ii) + U.at(j, k, ii));
+      const T we = h * (W.at(j, k, ii - 1) + W.at(j, k, ii));
+      fx[q] = ue * we;
+    }
+    T fy[2];
+    for (int q = 0; q < 2; ++q) {
+      const int jj = j + q;
+      const T ve = h * (vy(jj, k - 1, i) + vy(jj, k, i));
+      const T we = (jj <= 0 || jj >= ny) ? (T)0 : h * (W.at(jj - 1, k, i) + W.at(jj, k, i));
+      fy[q] = ve * we;
+    }
+    const T N = tz + (fx[1] - fx[0]) * ihx + (fy[1] - fy[0]) * ihy;
+    const T G = (Pp.at(j, k, i) - Pp.at(j, k - 1, i)) * ihz;
+    const T np = zet != (T)0 ? Nw[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
+    dw[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
+    Nw[idx] = N;
+  }
+  // ---------------- v (y-faces, interior j = 1..ny-1) ----------------
+  if (j == 0) {
+    dv[idx] = (T)0;
+    Nv[idx] = (T)0;
+  } else {
+    const T v0 = V.at(j, k, i);
+    const T lap = (V.at(j, k, i + 1) - 2 * v0 + V.at(j, k, i - 1)) * ihx * ihx +
+                  (V.at(j, k + 1, i) - 2 * v0 + V.at(j, k - 1, i)) * ihz * ihz +
+                  (vy(j + 1, k, i) - 2 * v0 + vy(j - 1, k, i)) * ihy * ihy;
+    const T vc = h * (v0 + vy(j + 1, k, i)), vcm = h * (vy(j - 1, k, i) + v0);
+    const T ty = (vc * vc - vcm * vcm) * ihy;
+    T fx[2];
+    for (int q = 0; q < 2; ++q) {
+      const int ii = i + q;
+      const T ue = h * (U.at(j - 1, k, ii) + U.at(j, k, ii));
+      const T ve = h * (V.at(j, k, ii - 1) + V.at(j, k, ii));
+      fx[q] = ue * ve;
+    }
+    T fz[2];
+    for (int q = 0; q < 2; ++q) {
+      const int kk = k + q;
+      const T we = h * (W.at(j - 1, kk, i) + W.at(j, kk, i));
+      const T ve = h * (V.at(j, kk - 1, i) + V.at(j, kk, i));
+      fz[q] = we * ve;
+    }
+    const T N = ty + (fx[1] - fx[0]) * ihx + (fz[1] - fz[0]) * ihz;
+    const T G = (Pp.at(j, k, i) - Pp.at(j - 1, k, i)) * ihy;
+    const T np = zet != (T)0 ? Nv[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
+    dv[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
+    Nv[idx] = N;
+  }
+}
+
+__device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
+  atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
+}
+
+// |D u| at one cell: FP32 fields use float-float (exact differences), FP64 plain.
+template <typename T> struct DivCell;
+template <> struct DivCell<float> {
+  static __device__ __forceinline__ double eval(float ue, float uw, float vn, float vs, float wt, float wb,
+                                                const ff &ihx, const ff &ihy, const ff &ihz, double,
+                                                double, double) {
+    ff d = ff_mul(two_sum(ue, -uw), ihx);
+    d = ff_add(d, ff_mul(two_sum(vn, -vs), ihy));
+    d = ff_add(d, ff_mul(two_sum(wt, -wb), ihz));
+    return (double)d.hi + (double)d.lo;
+  }
+};
+template <> struct DivCell<double> {
+  static __device__ __forceinline__ double eval(double ue, double uw, double vn, double vs, double wt, double wb,
+                                                const ff &, const ff &, const ff &, double ihx, double ihy,
+                                                double ihz) {
+    return (ue - uw) * ihx + (vn - vs) * ihy + (wt - wb) * ihz;
+  }
+};
+
+// E2: b = D u / scale_den; optional max |D u| into *dmax.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_divergence(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_, T *b,
+             double inv_scale, ff ihx, ff ihy, ff ihz, double *dmax) {
+  const size_t total = (size_t)g.nx * g.ny * g.nz;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  double mx = 0.0;
+  if (idx < total) {
+    const int i = (int)(idx % g.nx);
+    const int k = (int)((idx / g.nx) % g.nz);
+    const int j = (int)(idx / ((size_t)g.nx * g.nz));
+    const F3<T> U{u_, g.nx, g.nz}, V{v_, g.nx, g.nz}, W{w_, g.nx, g.nz};
+    const T vs = j == 0 ? (T)0 : V.at(j, k, i);
+    const T vn = j + 1 >= g.ny ? (T)0 : V.at(j + 1, k, i);
+    const double d = DivCell<T>::eval(U.at(j, k, i + 1), U.at(j, k, i), vn, vs, W.at(j, k + 1, i), W.at(j, k, i),
+                                      ihx, ihy, ihz, g.ihx, g.ihy, g.ihz);
+    if (b) b[idx] = (T)(d * inv_scale);
+    mx = fabs(d);
+  }
+  if (dmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(dmax, mx);
+  }
+}
+
+// E3: u -= k G phi (in place), p += phi - c L phi (Neumann ghosts).
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_project(Geo g, T *__restrict__ u, T *__restrict__ v, T *__restrict__ w, T *__restrict__ p,
+          const T *__restrict__ phi_, T kproj, T cvisc) {
+  const size_t total = (size_t)g.nx * g.ny * g.nz;
+  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const int i = (int)(idx % g.nx);
+  const int k = (int)((idx / g.nx) % g.nz);
+  const int j = (int)(idx / ((size_t)g.nx * g.nz));
+  const F3<T> Ph{phi_, g.nx, g.nz};
+  const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
+  const T f0 = Ph.at(j, k, i);
+  const T fw = Ph.at(j, k, i - 1), fe = Ph.at(j, k, i + 1);
+  const T fs = Ph.at(j, k - 1, i), fn = Ph.at(j, k + 1, i);
+  const T fd = j > 0 ? Ph.at(j - 1, k, i) : f0;
+  const T fu = j + 1 < g.ny ? Ph.at(j + 1, k, i) : f0;
+  u[idx] -= kproj * (f0 - fw) * ihx;
+  w[idx] -= kproj * (f0 - fs) * ihz;
+  if (j > 0) v[idx] -= kproj * (f0 - fd) * ihy;
+  else v[idx] = (T)0;
+  const T lap = (fe - 2 * f0 + fw) * ihx * ihx + (fn - 2 * f0 + fs) * ihz * ihz + (fu - 2 * f0 + fd) * ihy * ihy;
+  p[idx] += f0 - cvisc * lap;
+}
+
+static ff ff_host(double v) {
+  ff r;
+  r.hi = (float)v;
+  r.lo = (float)(v - (double)r.hi);
+  return r;
+}
+
+static int ensure_substep_buffers(ibm_plan_s *p, int nmk) {
+  for (int q = 0; q < 4; ++q) {
+    if (!p->sub[q]) {
+      cudaError_t e = cudaMalloc(&p->sub[q], p->npts * p->esz);
+      if (e != cudaSuccess) { p->sub[q] = nullptr; return cuda_error(e, "substep workspace"); }
+      p->bytes += p->npts * p->esz;
+    }
+  }
+  const size_t need = (size_t)nmk * 3 * p->esz;
+  if (need > p->mkcap) {
+    if (p->mkbuf) { cudaFree(p->mkbuf); p->bytes -= p->mkcap; p->mkbuf = nullptr; p->mkcap = 0; }
+    cudaError_t e = cudaMalloc(&p->mkbuf, need);
+    if (e != cudaSuccess) { p->mkbuf = nullptr; return cuda_error(e, "marker workspace"); }
+    p->mkcap = need;
+    p->bytes += need;
+  }
+  return IBM_OK;
+}
+
+template <typename T>
+static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double nu, ibm_markers *mk,
+                     cudaStream_t st, ibm_info *info) {
+  const int n = stage - 1;
+  const double a = kAlpha[n], b = kBeta[n], gm = kGamma[n], zt = kZeta[n];
+  const double ab = a + b;
+  const double cH = b * dt * nu;  // Helmholtz coefficient of Eq. 2e
+  const int nmk = mk ? mk->n : 0;
+  int rc = ensure_substep_buffers(p, nmk);
+  if (rc) return rc;
+  Geo g{p->nx, p->ny, p->nz, 1.0 / p->h[0], 1.0 / p->h[1], 1.0 / p->h[2]};
+  T *u = (T *)s->u, *v = (T *)s->v, *w = (T *)s->w, *pr = (T *)s->p;
+  T *du = (T *)p->sub[0], *dv = (T *)p->sub[1], *dw = (T *)p->sub[2], *phi = (T *)p->sub[3];
+  T *rhs = (T *)p->bsave;
+  const unsigned blocks = (unsigned)((p->npts + 255) / 256);
+  if (info) {
+    IBM_CUDA_TRY(cudaMemsetAsync(p->dsc + 8, 0, 2 * sizeof(double), st));
+    IBM_CUDA_TRY(cudaEventRecord(p->ev0, st));
+  }
+  // E1
+  {
+    ProfScope ps(p, IBM_K_EXPLICIT, st);
+    k_explicit<T><<<blocks, 256, 0, st>>>(g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
+                                          (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt);
+    IBM_CUDA_TRY(cudaGetLastError());
+  }
+  // L2 + L1
+  if (nmk > 0) {
+    T *F = mk->F ? (T *)mk->F : (T *)p->mkbuf;
+    {
+      ProfScope ps(p, IBM_K_MOTION, st);
+      IBM_CUDA_TRY(launch_motion<T>(nmk, (const T *)mk->X0, (T *)mk->X, (T *)mk->Ud, mk->motion, mk->params, s->t,
+                                    st));
+    }
+    {
+      ProfScope ps(p, IBM_K_INTERP, st);
+      IBM_CUDA_TRY(launch_interp<T>(p, nmk, (const T *)mk->X, u, v, w, du, dv, dw, nullptr, (const T *)mk->Ud,
+                                    1.0 / dt, F, st));
+    }
+    {
+      ProfScope ps(p, IBM_K_SPREAD, st);
+      IBM_CUDA_TRY(launch_spread<T>(p, nmk, (const T *)mk->X, F, (const T *)mk->dV, du, dv, dw, dt, st));
+    }
+  }
+  // S1: Helmholtz, increment form, u* written over u
+  if ((rc = plan_solve(p, 1, cH, IBM_FIELD_CELL_DIRICHLET, du, u, u, st, nullptr))) return rc;
+  if ((rc = plan_solve(p, 1, cH, IBM_FIELD_FACE_DIRICHLET, dv, v, v, st, nullptr))) return rc;
+  if ((rc = plan_solve(p, 1, cH, IBM_FIELD_CELL_DIRICHLET, dw, w, w, st, nullptr))) return rc;
+  // E2
+  const ff fx = ff_host(g.ihx), fy = ff_host(g.ihy), fz = ff_host(g.ihz);
+  {
+    ProfScope ps(p, IBM_K_DIVERGENCE, st);
+    k_divergence<T><<<blocks, 256, 0, st>>>(g, u, v, w, rhs, 1.0 / (ab * dt), fx, fy, fz,
+                                            info ? p->dsc + 9 : nullptr);
+    IBM_CUDA_TRY(cudaGetLastError());
+  }
+  // S2
+  if ((rc = plan_solve(p, 0, 0.0, 0, rhs, phi, nullptr, st, nullptr))) return rc;
+  // E3
+  {
+    ProfScope ps(p, IBM_K_PROJECT, st);
+    k_project<T><<<blocks, 256, 0, st>>>(g, u, v, w, pr, phi, (T)(ab * dt), (T)cH);
+    IBM_CUDA_TRY(cudaGetLastError());
+  }
+  if (info) {
+    IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
+    k_divergence<T><<<blocks, 256, 0, st>>>(g, u, v, w, nullptr, 1.0, fx, fy, fz, p->dsc + 8);
+    IBM_CUDA_TRY(cudaGetLastError());
+    IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    IBM_CUDA_TRY(cudaStreamSynchronize(st));
+    float ms = 0.f;
+    IBM_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    info->rel_residual = -1.0;
+    info->removed_mean = p->hsc[0];
+    info->div_max = p->hsc[8];
+    info->div_before = p->hsc[9];
+    info->t_ms = ms;
+    info->refine_iters = p->precision == IBM_FP32_REFINED ? p->refine : 0;
+  }
+  s->t += ab * dt;
+  return IBM_OK;
+}
+
+}  // namespace ibm
+
+using namespace ibm;
+
+extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
+                           void *stream, ibm_info *info) {
+  if (!plan || !st) return set_error(IBM_ERR_ARG, "ibm_substep: NULL plan or state");
+  if (rk_stage < 1 || rk_stage > 3) return set_error(IBM_ERR_ARG, "ibm_substep: rk_stage %d", rk_stage);
+  if (!(dt > 0) || !std::isfinite(dt) || !(nu > 0) || !std::isfinite(nu))
+    return set_error(IBM_ERR_ARG, "ibm_substep: dt and nu must be finite and > 0");
+  void *fields[] = {st->u, st->v, st->w, st->p, st->Nu, st->Nv, st->Nw};
+  for (void *f : fields)
+    if (!f || !aligned_to(f, plan->esz)) return set_error(IBM_ERR_ARG, "ibm_substep: NULL or misaligned field");
+  if (mk && mk->n > 0) {
+    if (!mk->X0 || !mk->dV || !mk->X || !mk->Ud)
+      return set_error(IBM_ERR_ARG, "ibm_substep: markers need X0, dV, X and Ud");
+    if (mk->motion < IBM_MOTION_STATIC || mk->motion > IBM_MOTION_HEAVE)
+      return set_error(IBM_ERR_ARG, "ibm_substep: motion %d", mk->motion);
+    if (mk->motion == IBM_MOTION_HEAVE && !(mk->params[1] > 0))
+      return set_error(IBM_ERR_ARG, "ibm_substep: heave period must be > 0");
+    if (mk->n > (1 << 26)) return set_error(IBM_ERR_ARG, "ibm_substep: too many markers");
+  } else if (mk && mk->n < 0) {
+    return set_error(IBM_ERR_ARG, "ibm_substep: negative marker count");
+  }
+  if (plan->precision == IBM_FP64)
+    return substep_t<double>(plan, st, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
+  return substep_t<float>(plan, st, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
+}

@@ -474,6 +474,12 @@ template cudaError_t launch_inverse<float>(const TransformGeom &, float2 *, floa
 template cudaError_t launch_inverse<double>(const TransformGeom &, double2 *, double *, const double *,
                                             const double2 *, const double2 *, double, cudaStream_t);
 
+template <typename T> int transform_launches(const TransformGeom &g) {
+  return (g.use_plane && plane_supported<T>(g.nx, g.nz)) ? 1 : 2;
+}
+template int transform_launches<float>(const TransformGeom &);
+template int transform_launches<double>(const TransformGeom &);
+
 bool transform_size_supported(int n) {
 #define X(N) if (n == N) return true;
   IBM_FOR_EACH_N(X)
