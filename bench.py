@@ -11,9 +11,10 @@ spectrum ~ k^-5/3 (k <= 16).  Four independent states rotate across steps
 (4 x 56 MB > 129 MB L2) so every step reads its fields from HBM.
 
 Output: one JSON line (rank 0).  `value` is grid points advanced per second
-(all ranks), `e2e` the same through host buffers, `roofline` the dominant
-kernel's achieved HBM bandwidth from CUDA events around its launches in the
-timed region, `cpu_baseline` the FP64 CPU oracle on a bounded sample.
+(all ranks) over the untraced timed region, `e2e` the same through host
+buffers, `roofline` the dominant kernel's achieved HBM bandwidth from CUDA
+events around each of its launches in an identical second pass of the same
+steps, `cpu_baseline` the FP64 CPU oracle on a bounded sample.
 `--impl reference` times that oracle alone.
 """
 
@@ -85,7 +86,7 @@ class ClockSampler:
              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
         try:
             self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
-                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                          "--format=csv,noheader,nounits", "-lms", "10"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -235,19 +236,33 @@ def run_gpu(args):
             dist.barrier()
         torch.cuda.synchronize()
 
-    # ---- timed region: K steps, per-kernel events on ----
-    ibm.ibm_plan_profile(plan, True)
-    ibm.ibm_plan_profile_read(plan)
+    if args.quick:
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for i in range(args.steps):
+            step(args.warmup + i)
+        e1.record()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if rank == 0:
+            print(json.dumps({"quick": True, "ms_per_step": ms / args.steps,
+                              "value": NX * NY * NZ * args.steps * ws / (ms * 1e-3)}), flush=True)
+        ibm.ibm_plan_destroy(plan)
+        return
+
+    # ---- timed region: K steps, no tracing; clocks sampled throughout ----
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
-    barrier()
     with ClockSampler(local) as clk:
+        time.sleep(0.3)  # let the sampler start before the timed region
+        barrier()
+        t_host0 = time.time()
         ev[0].record()
         for i in range(args.steps):
             step(args.warmup + i)
             ev[i + 1].record()
         barrier()
-    prof = ibm.ibm_plan_profile_read(plan)
-    ibm.ibm_plan_profile(plan, False)
+        t_host1 = time.time()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = ev[0].elapsed_time(ev[-1])
     if dist:
@@ -257,7 +272,9 @@ def run_gpu(args):
     pts = NX * NY * NZ
     value = pts * args.steps * ws / (total_ms * 1e-3)
 
-    # ---- same steps without events (profiling overhead check) ----
+    # ---- identical pass with CUDA events around every kernel (roofline) ----
+    ibm.ibm_plan_profile(plan, True)
+    ibm.ibm_plan_profile_read(plan)
     barrier()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
@@ -265,7 +282,9 @@ def run_gpu(args):
         step(args.warmup + args.steps + i)
     e1.record()
     barrier()
-    unprof_ms = e0.elapsed_time(e1)
+    traced_ms = e0.elapsed_time(e1)
+    prof = ibm.ibm_plan_profile_read(plan)
+    ibm.ibm_plan_profile(plan, False)
 
     # ---- end to end: host buffers, copies inside the timed region ----
     host_in = [torch.from_numpy(np.ascontiguousarray(a)).to(f32).pin_memory()
@@ -331,10 +350,11 @@ def run_gpu(args):
         "launches_per_step": {k: prof[k][1] / args.steps for k in prof},
         "p50_ms": float(np.percentile(step_ms, 50)),
         "p99_ms": float(np.percentile(step_ms, 99)),
-        "value_unprofiled": pts * args.steps * ws / (unprof_ms * 1e-3),
+        "value_traced": pts * args.steps * ws / (traced_ms * 1e-3),
         "poisson": solves,
         "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")},
         "clocks": clocks,
+        "timed_region_s": t_host1 - t_host0,
     }
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
@@ -437,10 +457,13 @@ def run_reference(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--steps", type=int, default=400)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--quick", action="store_true",
+                    help="warm-up and timed steps only (no tracing pass, e2e, Poisson comparison or CPU baseline); "
+                         "used for profiler launch lists")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

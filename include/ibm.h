@@ -32,6 +32,8 @@
  *   volumes dV are [n], all in device memory, plan precision.  Markers must
  *   stay in 1.5 hy (3-point kernel) / 2 hy (4-point kernel) of the walls'
  *   interior; support points beyond the stored planes are dropped.
+ * Alignment: field pointers must be 16-byte aligned (they are moved with
+ *   bulk asynchronous copies); marker arrays need their element alignment.
  * Ownership: all field and marker pointers belong to the caller; the plan
  *   owns its workspace, twiddle and eigenvalue tables.
  * Streams: `stream` is a cudaStream_t (NULL = legacy default stream).  Every
@@ -116,6 +118,10 @@ int ibm_plan_destroy(ibm_plan plan);
 int ibm_plan_set_delta(ibm_plan plan, int kernel);
 /* Bytes of device memory the plan holds. */
 size_t ibm_plan_workspace_bytes(ibm_plan plan);
+
+/* Synchronise the device and report whether any kernel of this plan gave up
+ * one of its bounded waits (IBM_ERR_TIMEOUT; the word is then cleared). */
+int ibm_plan_check(ibm_plan plan);
 
 /* Per-kernel timing (tracing).  While enabled, every kernel the plan
  * launches is bracketed by a pair of CUDA events on its stream; the pairs

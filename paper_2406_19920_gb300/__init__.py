@@ -75,6 +75,7 @@ _SIG = {
     "ibm_plan_destroy": (_I, [_P]),
     "ibm_plan_set_delta": (_I, [_P, _I]),
     "ibm_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
+    "ibm_plan_check": (_I, [_P]),
     "ibm_plan_profile": (_I, [_P, _I]),
     "ibm_plan_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ibm_poisson_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
@@ -162,6 +163,10 @@ def ibm_plan_destroy(plan):
 
 def ibm_plan_set_delta(plan, kernel):
     return _check(lib().ibm_plan_set_delta(plan, kernel))
+
+
+def ibm_plan_check(plan):
+    return _check(lib().ibm_plan_check(plan))
 
 
 def ibm_plan_workspace_bytes(plan):

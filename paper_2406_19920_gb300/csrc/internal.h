@@ -10,11 +10,14 @@
 namespace ibm {
 
 // Largest dynamic shared memory a plane kernel may take (bytes).
-constexpr size_t kPlaneSmemLimit = 200 * 1024;
+constexpr size_t kPlaneSmemLimit = 227 * 1024;
 
 struct TransformGeom {
   int nx, ny, nz;
   bool use_plane;  // allow the one-CTA-per-plane kernels
+  int *err;        // device error word for bounded waits
+  double *zrhs;    // forward: if set, receives Re S[j][0][0] of every plane (the zero pencil)
+  const double *zsol;  // inverse: if set, replaces S[j][0][0] by (zsol[j], 0) before transforming
 };
 
 // Lanes that exist in the calling thread's warp (a block of fewer than 32
@@ -23,6 +26,24 @@ __device__ __forceinline__ unsigned warp_full_mask() {
   const int warp_base = (threadIdx.x / 32) * 32;
   const int lanes = min(32, (int)blockDim.x - warp_base);
   return lanes >= 32 ? 0xffffffffu : ((1u << lanes) - 1u);
+}
+
+// Launch shape of the point-wise stencil kernels: threads along x (coalesced),
+// grid over (x blocks, z, y); no index divisions in the kernels.
+struct Launch3 {
+  dim3 grid, block;
+};
+inline Launch3 stencil_launch(int nx, int ny, int nz) {
+  const int bx = nx >= 128 ? 128 : 32;
+  const int bz = 128 / bx;
+  return {dim3((unsigned)ceil_div(nx, bx), (unsigned)ceil_div(nz, bz), (unsigned)ny), dim3(bx, bz, 1)};
+}
+// (i, k, j) of the calling thread under stencil_launch; false if outside.
+__device__ __forceinline__ bool stencil_index(int nx, int nz, int &i, int &k, int &j) {
+  i = blockIdx.x * blockDim.x + threadIdx.x;
+  k = blockIdx.y * blockDim.y + threadIdx.y;
+  j = blockIdx.z;
+  return i < nx && k < nz;
 }
 
 bool transform_size_supported(int n);
@@ -49,6 +70,11 @@ struct PencilParams {
   int zero_mode;           // Poisson: solve the (0,0) pencil in FP64
   double hy2;              // hy^2 for the FP64 zero-mode path
   double inv_nxnz;         // 1/(nx nz) for the removed-mean report
+  int *err;                // device error word for bounded waits
+  int substructured;       // 1: warp-parallel block solve (n <= 256 FP32 / 128 FP64); 0: serial sweep
+  const double *zrhs;      // zero_mode: right-hand side of the (0,0) pencil, [ny] (from the forward pass)
+  double *zsol;            // zero_mode: its FP64 solution, [ny] (read by the inverse pass)
+  double inv_ny;           // 1/ny
 };
 template <typename T>
 cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, const T *lamz, double *mean_out,

@@ -43,6 +43,9 @@ TransformGeom geom_of(const ibm_plan_s *p) {
   TransformGeom g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
   g.use_plane = true;
+  g.err = p->derr;
+  g.zrhs = nullptr;
+  g.zsol = nullptr;
   return g;
 }
 
@@ -101,7 +104,7 @@ static void plan_free(ibm_plan_s *p) {
   for (auto &r : p->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : p->evpool) cudaEventDestroy(e);
   void *bufs[] = {p->S, p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3],
-                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf};
+                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -126,14 +129,19 @@ static int dalloc(ibm_plan_s *p, void **ptr, size_t bytes) {
 template <typename T>
 static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out, const T *addend,
                       double *mean_out, cudaStream_t st) {
-  const TransformGeom g = geom_of(p);
+  TransformGeom gf = geom_of(p), gi = geom_of(p);
+  if (pp.zero_mode) {
+    gf.zrhs = p->zbuf;
+    gi.zsol = p->zbuf + p->ny;
+  }
+  const TransformGeom &g = gf;
   cplx<T> *S = static_cast<cplx<T> *>(p->S);
   const cplx<T> *twx = static_cast<const cplx<T> *>(p->twx);
   const cplx<T> *twz = static_cast<const cplx<T> *>(p->twz);
   const int nl = transform_launches<T>(g);
   {
     ProfScope ps(p, IBM_K_FORWARD, st, nl);
-    IBM_CUDA_TRY(launch_forward<T>(g, in, S, twx, twz, (T)1, st));
+    IBM_CUDA_TRY(launch_forward<T>(gf, in, S, twx, twz, (T)1, st));
   }
   {
     ProfScope ps(p, IBM_K_PENCIL, st);
@@ -142,7 +150,7 @@ static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out
   }
   {
     ProfScope ps(p, IBM_K_INVERSE, st, nl);
-    IBM_CUDA_TRY(launch_inverse<T>(g, S, out, addend, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
+    IBM_CUDA_TRY(launch_inverse<T>(gi, S, out, addend, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
   }
   return IBM_OK;
 }
@@ -167,6 +175,11 @@ static PencilParams pencil_params(const ibm_plan_s *p, int kind, double c, int f
   }
   pp.hy2 = hy * hy;
   pp.inv_nxnz = 1.0 / ((double)p->nx * p->nz);
+  pp.err = p->derr;
+  pp.substructured = p->pencil_mode;
+  pp.zrhs = p->zbuf;
+  pp.zsol = p->zbuf + p->ny;
+  pp.inv_ny = 1.0 / p->ny;
   return pp;
 }
 
@@ -211,15 +224,18 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
   if (info) {
     IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
     // relative residual of the returned x (only meaningful without addend)
-    IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, p->dsc + 1, st));
+    IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, p->dsc + 4, st));
     IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 8 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IBM_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     IBM_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
     const double N = (double)p->npts;
     const double *h = p->hsc;
-    const double rr = std::max(0.0, h[1] - h[3] * h[3] / N);
-    const double bb = h[2];
+    const double rr = std::max(0.0, h[4] - h[6] * h[6] / N);
+    const double bb = h[5];
+    int derr = 0;
+    IBM_CUDA_TRY(cudaMemcpy(&derr, p->derr, sizeof(int), cudaMemcpyDeviceToHost));
+    if (derr) return set_error(IBM_ERR_TIMEOUT, "a kernel gave up a bounded wait (error word %d)", derr);
     info->rel_residual = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
     info->removed_mean = kind == 0 ? h[0] : 0.0;
     info->div_max = 0.0;
@@ -273,6 +289,9 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   p->precision = precision;
   p->refine = precision == IBM_FP64 ? 0 : refine_iters;
   p->delta = IBM_DELTA_ROMA3;
+  // pencil solver: serial excess-form sweep by default; IBM_PENCIL_SUBSTRUCT=1
+  // selects the warp-parallel block solve (A/B timing; the tuner may pick it)
+  p->pencil_mode = (getenv("IBM_PENCIL_SUBSTRUCT") && atoi(getenv("IBM_PENCIL_SUBSTRUCT")) == 1) ? 1 : 0;
   p->esz = precision == IBM_FP64 ? 8 : 4;
   p->npts = (size_t)nx * ny * nz;
   p->nspec = (size_t)ny * nz * p->P;
@@ -284,7 +303,9 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
       (rc = dalloc(p, &p->twz, (size_t)nz * 2 * p->esz)) ||
       (rc = dalloc(p, &p->lamx, (size_t)p->P * p->esz)) ||
       (rc = dalloc(p, &p->lamz, (size_t)nz * p->esz)) ||
-      (rc = dalloc(p, (void **)&p->dsc, 16 * sizeof(double)))) {
+      (rc = dalloc(p, (void **)&p->dsc, 16 * sizeof(double))) ||
+      (rc = dalloc(p, (void **)&p->derr, 16)) ||
+      (rc = dalloc(p, (void **)&p->zbuf, 2 * (size_t)ny * sizeof(double)))) {
     plan_free(p);
     return rc;
   }
@@ -294,6 +315,7 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
     plan_free(p);
     return cuda_error(e, "cudaEventCreate");
   }
+  if ((e = cudaMemset(p->derr, 0, 16)) != cudaSuccess) { plan_free(p); return cuda_error(e, "cudaMemset"); }
   rc = precision == IBM_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
   if (rc) { plan_free(p); return rc; }
   *out = p;
@@ -316,6 +338,18 @@ int ibm_plan_set_delta(ibm_plan plan, int kernel) {
 }
 
 size_t ibm_plan_workspace_bytes(ibm_plan plan) { return plan ? plan->bytes : 0; }
+
+int ibm_plan_check(ibm_plan plan) {
+  if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_check: NULL plan");
+  IBM_CUDA_TRY(cudaDeviceSynchronize());
+  int derr = 0;
+  IBM_CUDA_TRY(cudaMemcpy(&derr, plan->derr, sizeof(int), cudaMemcpyDeviceToHost));
+  if (derr) {
+    IBM_CUDA_TRY(cudaMemset(plan->derr, 0, sizeof(int)));
+    return set_error(IBM_ERR_TIMEOUT, "a kernel of this plan gave up a bounded wait (error word %d)", derr);
+  }
+  return IBM_OK;
+}
 
 int ibm_plan_profile(ibm_plan plan, int enable) {
   if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_profile: NULL plan");
@@ -347,8 +381,8 @@ int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launche
 
 int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream, ibm_info *info) {
   if (!plan || !rhs || !phi) return set_error(IBM_ERR_ARG, "ibm_poisson_solve: NULL argument");
-  if (!aligned_to(rhs, plan->esz) || !aligned_to(phi, plan->esz))
-    return set_error(IBM_ERR_ARG, "ibm_poisson_solve: misaligned field pointer");
+  if (!aligned_to(rhs, 16) || !aligned_to(phi, 16))
+    return set_error(IBM_ERR_ARG, "ibm_poisson_solve: field pointers must be 16-byte aligned");
   return plan_solve(plan, 0, 0.0, 0, rhs, phi, nullptr, (cudaStream_t)stream, info);
 }
 
@@ -358,8 +392,8 @@ int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs, 
   if (!(c > 0.0) || !std::isfinite(c)) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: c must be > 0");
   if (field_bc < IBM_FIELD_CELL_NEUMANN || field_bc > IBM_FIELD_FACE_DIRICHLET)
     return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field_bc %d", field_bc);
-  if (!aligned_to(rhs, plan->esz) || !aligned_to(u, plan->esz))
-    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: misaligned field pointer");
+  if (!aligned_to(rhs, 16) || !aligned_to(u, 16))
+    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field pointers must be 16-byte aligned");
   return plan_solve(plan, 1, c, field_bc, rhs, u, nullptr, (cudaStream_t)stream, info);
 }
 

@@ -31,6 +31,7 @@ struct ibm_plan_s {
   int precision;     // IBM_FP64 / IBM_FP32_REFINED
   int refine;        // refinement steps (FP32 path)
   int delta;         // IBM_DELTA_*
+  int pencil_mode;   // 1 substructured warp-parallel pencil solve, 0 serial sweep
   size_t esz;        // element size: 4 or 8
   size_t npts;       // nx * ny * nz
   size_t nspec;      // ny * nz * P complex entries
@@ -42,7 +43,10 @@ struct ibm_plan_s {
   size_t mkcap;      // bytes of mkbuf
   void *twx, *twz;   // twiddles W_N^m (plan precision)
   void *lamx, *lamz; // modified wavenumbers kx'^2 (P), kz'^2 (nz) (plan precision)
-  double *dsc;       // device scalars: [0] removed mean, [1..4] norms, [5..7] misc
+  double *dsc;       // device scalars: [0] removed mean, [1] it as a float pair, [4..7] residual
+                     // sums, [8..9] divergence maxima
+  int *derr;         // device error word (bounded waits that gave up)
+  double *zbuf;      // [2 ny] FP64 zero-pencil right-hand side and solution
   double *hsc;       // pinned host mirror of dsc
   cudaEvent_t ev0, ev1;
   size_t bytes;      // device bytes held

@@ -26,7 +26,8 @@ static inline ffc split_ff(double v) {
 }
 
 struct ResidualArgs {
-  const double *boff;  // device scalar subtracted from b (its removed mean), or NULL
+  const double *boff;  // device scalars: boff[0] mean to subtract from b (FP64 path); boff[1] holds the
+                       // same value as a float pair (hi, lo) for the FP32 path; NULL for none
   int nx, ny, nz, bc;
   ffc cx, cy, cz, tau;
   float sigma;
@@ -36,7 +37,8 @@ struct ResidualArgs {
 // Adds the block sums of (r^2, b^2, r, b) to out[0..3] (FP64 atomics).
 __device__ __forceinline__ void block_accumulate(double r, double b, double *out) {
   __shared__ double red[4][32];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int lane = tid & 31, w = tid >> 5;
   double v[4] = {r * r, b * b, r, b};
 #pragma unroll
   for (int q = 0; q < 4; ++q)
@@ -47,7 +49,7 @@ __device__ __forceinline__ void block_accumulate(double r, double b, double *out
     for (int q = 0; q < 4; ++q) red[q][w] = v[q];
   __syncthreads();
   if (w == 0) {
-    const int nw = blockDim.x >> 5;
+    const int nw = (blockDim.x * blockDim.y) >> 5;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       double t = lane < nw ? red[q][lane] : 0.0;
@@ -58,28 +60,25 @@ __device__ __forceinline__ void block_accumulate(double r, double b, double *out
   }
 }
 
-// one thread per point; grid covers ny * nz * nx exactly (block multiple of 32)
-__global__ void __launch_bounds__(256)
+// one thread per point, stencil_launch() shape
+__global__ void __launch_bounds__(128)
 k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float *__restrict__ r,
                double *norms) {
-  const size_t total = (size_t)A.nx * A.ny * A.nz;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, k, j;
+  const bool inside = stencil_index(A.nx, A.nz, i, k, j);
+  const size_t idx = ((size_t)j * A.nz + k) * A.nx + i;
   double rr = 0.0, bb = 0.0;
-  if (idx < total) {
-    const int i = (int)(idx % A.nx);
-    const size_t t = idx / A.nx;
-    const int k = (int)(t % A.nz);
-    const int j = (int)(t / A.nz);
+  if (inside) {
     const size_t row = (size_t)A.nx;
     const size_t pl = (size_t)A.nx * A.nz;
     float bv = b[idx];
     float bl = 0.0f;  // low part of b - offset
     if (A.boff) {
-      const double off = *A.boff;
-      const float mh = (float)off;
-      const ff d = two_sum(bv, -mh);
+      // the removed mean as a float-float pair: boff[1..2] reinterpreted
+      const float2 m = *reinterpret_cast<const float2 *>(A.boff + 1);
+      const ff d = two_sum(bv, -m.x);
       bv = d.hi;
-      bl = __fadd_rn(d.lo, -(float)(off - (double)mh));
+      bl = __fadd_rn(d.lo, -m.y);
     }
     float res;
     if (A.bc == BC_FACE_DIRICHLET && j == 0) {
@@ -108,23 +107,22 @@ k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restr
       res = __fadd_rn(acc.hi, acc.lo);
     }
     r[idx] = res;
-    rr = (double)res;
-    bb = (A.bc == BC_FACE_DIRICHLET && j == 0) ? 0.0 : (double)bv;
+    if (norms) {
+      rr = (double)res;
+      bb = (A.bc == BC_FACE_DIRICHLET && j == 0) ? 0.0 : (double)bv + (double)bl;
+    }
   }
   if (norms) block_accumulate(rr, bb, norms);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_residual_f64(ResidualArgs A, const double *__restrict__ b, const double *__restrict__ x,
                double *__restrict__ r, double *norms) {
-  const size_t total = (size_t)A.nx * A.ny * A.nz;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  int i, k, j;
+  const bool inside = stencil_index(A.nx, A.nz, i, k, j);
+  const size_t idx = ((size_t)j * A.nz + k) * A.nx + i;
   double rr = 0.0, bb = 0.0;
-  if (idx < total) {
-    const int i = (int)(idx % A.nx);
-    const size_t t = idx / A.nx;
-    const int k = (int)(t % A.nz);
-    const int j = (int)(t / A.nz);
+  if (inside) {
     const size_t row = (size_t)A.nx;
     const size_t pl = (size_t)A.nx * A.nz;
     const double bv = A.boff ? b[idx] - *A.boff : b[idx];
@@ -171,15 +169,15 @@ static ResidualArgs make_args(int nx, int ny, int nz, const StencilCoef &c, cons
 template <>
 cudaError_t launch_residual<float>(int nx, int ny, int nz, const StencilCoef &c, const float *b, const float *x,
                                    float *r, const double *boff, double *norms, cudaStream_t st) {
-  const size_t total = (size_t)nx * ny * nz;
-  k_residual_f32<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
+  const Launch3 L = stencil_launch(nx, ny, nz);
+  k_residual_f32<<<L.grid, L.block, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
   return cudaGetLastError();
 }
 template <>
 cudaError_t launch_residual<double>(int nx, int ny, int nz, const StencilCoef &c, const double *b, const double *x,
                                     double *r, const double *boff, double *norms, cudaStream_t st) {
-  const size_t total = (size_t)nx * ny * nz;
-  k_residual_f64<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
+  const Launch3 L = stencil_launch(nx, ny, nz);
+  k_residual_f64<<<L.grid, L.block, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
   return cudaGetLastError();
 }
 

@@ -57,16 +57,13 @@ template <typename T> struct F3 {
 
 // E1: one thread per cell index (j, k, i), all three components.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_,
            const T *__restrict__ p_, T *Nu, T *Nv, T *Nw, T *__restrict__ du, T *__restrict__ dv,
            T *__restrict__ dw, T c_visc, T c_pres, T gam, T zet, T dt) {
-  const size_t total = (size_t)g.nx * g.ny * g.nz;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int i = (int)(idx % g.nx);
-  const int k = (int)((idx / g.nx) % g.nz);
-  const int j = (int)(idx / ((size_t)g.nx * g.nz));
+  int i, k, j;
+  if (!stencil_index(g.nx, g.nz, i, k, j)) return;
+  const size_t idx = ((size_t)j * g.nz + k) * g.nx + i;
   const int ny = g.ny;
   const F3<T> U{u_, g.nx, g.nz}, V{v_, g.nx, g.nz}, W{w_, g.nx, g.nz}, Pp{p_, g.nx, g.nz};
   const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
@@ -172,64 +169,59 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
   atomicMax(reinterpret_cast<unsigned long long *>(addr), (unsigned long long)__double_as_longlong(v));
 }
 
-// |D u| at one cell: FP32 fields use float-float (exact differences), FP64 plain.
-template <typename T> struct DivCell;
-template <> struct DivCell<float> {
-  static __device__ __forceinline__ double eval(float ue, float uw, float vn, float vs, float wt, float wb,
-                                                const ff &ihx, const ff &ihy, const ff &ihz, double,
-                                                double, double) {
+// E2: b = D u * inv_scale in plain working precision (the right-hand side of
+// Eq. 2f); with dmax, additionally max |D u| evaluated exactly: float-float
+// differences for FP32 fields, FP64 for FP64 fields (the projection check).
+template <typename T> struct DivExact;
+template <> struct DivExact<float> {
+  static __device__ __forceinline__ float eval(float ue, float uw, float vn, float vs, float wt, float wb,
+                                               const ff &ihx, const ff &ihy, const ff &ihz) {
     ff d = ff_mul(two_sum(ue, -uw), ihx);
     d = ff_add(d, ff_mul(two_sum(vn, -vs), ihy));
     d = ff_add(d, ff_mul(two_sum(wt, -wb), ihz));
-    return (double)d.hi + (double)d.lo;
+    return fabsf(__fadd_rn(d.hi, d.lo));
   }
 };
-template <> struct DivCell<double> {
+template <> struct DivExact<double> {
   static __device__ __forceinline__ double eval(double ue, double uw, double vn, double vs, double wt, double wb,
-                                                const ff &, const ff &, const ff &, double ihx, double ihy,
-                                                double ihz) {
-    return (ue - uw) * ihx + (vn - vs) * ihy + (wt - wb) * ihz;
+                                                const ff &ihx, const ff &ihy, const ff &ihz) {
+    return fabs((ue - uw) * (double)ihx.hi + (vn - vs) * (double)ihy.hi + (wt - wb) * (double)ihz.hi +
+                ((ue - uw) * (double)ihx.lo + (vn - vs) * (double)ihy.lo + (wt - wb) * (double)ihz.lo));
   }
 };
 
-// E2: b = D u / scale_den; optional max |D u| into *dmax.
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_divergence(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_, T *b,
-             double inv_scale, ff ihx, ff ihy, ff ihz, double *dmax) {
-  const size_t total = (size_t)g.nx * g.ny * g.nz;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  double mx = 0.0;
-  if (idx < total) {
-    const int i = (int)(idx % g.nx);
-    const int k = (int)((idx / g.nx) % g.nz);
-    const int j = (int)(idx / ((size_t)g.nx * g.nz));
+             T inv_scale, T ihx_t, T ihy_t, T ihz_t, ff ihx, ff ihy, ff ihz, double *dmax) {
+  int i, k, j;
+  const bool inside = stencil_index(g.nx, g.nz, i, k, j);
+  const size_t idx = ((size_t)j * g.nz + k) * g.nx + i;
+  T mx = 0;
+  if (inside) {
     const F3<T> U{u_, g.nx, g.nz}, V{v_, g.nx, g.nz}, W{w_, g.nx, g.nz};
     const T vs = j == 0 ? (T)0 : V.at(j, k, i);
     const T vn = j + 1 >= g.ny ? (T)0 : V.at(j + 1, k, i);
-    const double d = DivCell<T>::eval(U.at(j, k, i + 1), U.at(j, k, i), vn, vs, W.at(j, k + 1, i), W.at(j, k, i),
-                                      ihx, ihy, ihz, g.ihx, g.ihy, g.ihz);
-    if (b) b[idx] = (T)(d * inv_scale);
-    mx = fabs(d);
+    const T ue = U.at(j, k, i + 1), uw = U.at(j, k, i), wt = W.at(j, k + 1, i), wb = W.at(j, k, i);
+    if (b) b[idx] = ((ue - uw) * ihx_t + (vn - vs) * ihy_t + (wt - wb) * ihz_t) * inv_scale;
+    if (dmax) mx = DivExact<T>::eval(ue, uw, vn, vs, wt, wb, ihx, ihy, ihz);
   }
   if (dmax) {
+    const unsigned full = 0xffffffffu;
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(dmax, mx);
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(full, mx, o));
+    if (((threadIdx.y * blockDim.x + threadIdx.x) & 31) == 0) atomic_max_nonneg(dmax, (double)mx);
   }
 }
 
 // E3: u -= k G phi (in place), p += phi - c L phi (Neumann ghosts).
 template <typename T>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(128)
 k_project(Geo g, T *__restrict__ u, T *__restrict__ v, T *__restrict__ w, T *__restrict__ p,
           const T *__restrict__ phi_, T kproj, T cvisc) {
-  const size_t total = (size_t)g.nx * g.ny * g.nz;
-  const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const int i = (int)(idx % g.nx);
-  const int k = (int)((idx / g.nx) % g.nz);
-  const int j = (int)(idx / ((size_t)g.nx * g.nz));
+  int i, k, j;
+  if (!stencil_index(g.nx, g.nz, i, k, j)) return;
+  const size_t idx = ((size_t)j * g.nz + k) * g.nx + i;
   const F3<T> Ph{phi_, g.nx, g.nz};
   const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
   const T f0 = Ph.at(j, k, i);
@@ -285,7 +277,7 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   T *u = (T *)s->u, *v = (T *)s->v, *w = (T *)s->w, *pr = (T *)s->p;
   T *du = (T *)p->sub[0], *dv = (T *)p->sub[1], *dw = (T *)p->sub[2], *phi = (T *)p->sub[3];
   T *rhs = (T *)p->bsave;
-  const unsigned blocks = (unsigned)((p->npts + 255) / 256);
+  const Launch3 L3 = stencil_launch(p->nx, p->ny, p->nz);
   if (info) {
     IBM_CUDA_TRY(cudaMemsetAsync(p->dsc + 8, 0, 2 * sizeof(double), st));
     IBM_CUDA_TRY(cudaEventRecord(p->ev0, st));
@@ -293,7 +285,7 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   // E1
   {
     ProfScope ps(p, IBM_K_EXPLICIT, st);
-    k_explicit<T><<<blocks, 256, 0, st>>>(g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
+    k_explicit<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
                                           (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt);
     IBM_CUDA_TRY(cudaGetLastError());
   }
@@ -323,8 +315,8 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   const ff fx = ff_host(g.ihx), fy = ff_host(g.ihy), fz = ff_host(g.ihz);
   {
     ProfScope ps(p, IBM_K_DIVERGENCE, st);
-    k_divergence<T><<<blocks, 256, 0, st>>>(g, u, v, w, rhs, 1.0 / (ab * dt), fx, fy, fz,
-                                            info ? p->dsc + 9 : nullptr);
+    k_divergence<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, rhs, (T)(1.0 / (ab * dt)), (T)g.ihx, (T)g.ihy,
+                                                  (T)g.ihz, fx, fy, fz, info ? p->dsc + 9 : nullptr);
     IBM_CUDA_TRY(cudaGetLastError());
   }
   // S2
@@ -332,12 +324,13 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   // E3
   {
     ProfScope ps(p, IBM_K_PROJECT, st);
-    k_project<T><<<blocks, 256, 0, st>>>(g, u, v, w, pr, phi, (T)(ab * dt), (T)cH);
+    k_project<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, pr, phi, (T)(ab * dt), (T)cH);
     IBM_CUDA_TRY(cudaGetLastError());
   }
   if (info) {
     IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
-    k_divergence<T><<<blocks, 256, 0, st>>>(g, u, v, w, nullptr, 1.0, fx, fy, fz, p->dsc + 8);
+    k_divergence<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, nullptr, (T)1, (T)g.ihx, (T)g.ihy, (T)g.ihz, fx, fy,
+                                                  fz, p->dsc + 8);
     IBM_CUDA_TRY(cudaGetLastError());
     IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IBM_CUDA_TRY(cudaStreamSynchronize(st));
@@ -366,7 +359,7 @@ extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt
     return set_error(IBM_ERR_ARG, "ibm_substep: dt and nu must be finite and > 0");
   void *fields[] = {st->u, st->v, st->w, st->p, st->Nu, st->Nv, st->Nw};
   for (void *f : fields)
-    if (!f || !aligned_to(f, plan->esz)) return set_error(IBM_ERR_ARG, "ibm_substep: NULL or misaligned field");
+    if (!f || !aligned_to(f, 16)) return set_error(IBM_ERR_ARG, "ibm_substep: NULL or non-16-byte-aligned field");
   if (mk && mk->n > 0) {
     if (!mk->X0 || !mk->dV || !mk->X || !mk->Ud)
       return set_error(IBM_ERR_ARG, "ibm_substep: markers need X0, dV, X and Ud");

@@ -20,6 +20,7 @@
 //                  z-columns in separate passes.
 #include "fft.cuh"
 #include "internal.h"
+#include "tma.cuh"
 
 namespace ibm {
 
@@ -93,39 +94,63 @@ __device__ __forceinline__ void merge_pair(const cplx<T> *srcA, const cplx<T> *s
 }
 
 // --------------------------------------------------------------------------
-// plane kernels: one CTA per y-plane
+// plane kernels: one CTA per y-plane, the plane moved by bulk async copies
 // --------------------------------------------------------------------------
+constexpr int kPlaneThreads = 512;
+
+// shared-memory layout of a plane kernel (bytes from the dynamic base):
+//   [0, 16)            mbarrier
+//   staging            NZ*NX reals (forward input / inverse addend)
+//   twx, twz           NX + NZ complex twiddles
+//   plane              NZ rows of P = NX/2+1 complex (NZ/2 pairs of NX+2)
+template <typename T, int NX, int NZ> struct PlaneLayout {
+  static constexpr int P = NX / 2 + 1;
+  static constexpr size_t staging = 16;
+  static constexpr size_t tw = staging + sizeof(T) * (size_t)NZ * NX;
+  static constexpr size_t plane = tw + sizeof(cplx<T>) * (size_t)(NX + NZ);
+  static constexpr size_t bytes = plane + sizeof(cplx<T>) * (size_t)NZ * P;
+  static_assert(tw % 16 == 0 && plane % 16 == 0, "16-byte aligned regions");
+};
+
 template <typename T, int NX, int NZ>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPlaneThreads)
 k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx_g,
-            const cplx<T> *__restrict__ twz_g, T in_scale) {
-  constexpr int P = NX / 2 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
+            const cplx<T> *__restrict__ twz_g, T in_scale, int *err, double *zrhs) {
+  using L = PlaneLayout<T, NX, NZ>;
+  constexpr int P = L::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  T *real = reinterpret_cast<T *>(smem_raw + L::staging);
+  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw + L::tw);
   cplx<T> *twz = twx + NX;
-  cplx<T> *plane = twz + NZ;  // NZ/2 pairs of (NX + 2) = NZ rows of pitch P
+  cplx<T> *plane = reinterpret_cast<cplx<T> *>(smem_raw + L::plane);
   const int j = blockIdx.x;
   const int tid = threadIdx.x;
-  load_twiddles<T>(twx, twx_g, NX);
-  load_twiddles<T>(twz, twz_g, NZ);
-  {
-    const T *src = in + (size_t)j * NZ * NX;
-    T *pf = reinterpret_cast<T *>(plane);
-    for (int idx = tid; idx < NZ * NX; idx += kThreads) {
-      const int k = idx / NX, n = idx - k * NX;
-      pf[((k >> 1) * (NX + 2) + n) * 2 + (k & 1)] = src[idx] * in_scale;
-    }
+  constexpr uint32_t kInBytes = sizeof(T) * NZ * NX;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
   }
   __syncthreads();
-  {  // x: complex FFT of each row pair, then split into two half spectra
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, kInBytes);
+    bulk_g2s(real, in + (size_t)j * NZ * NX, kInBytes, bar);
+  }
+  load_twiddles<T>(twx, twx_g, NX);
+  load_twiddles<T>(twz, twz_g, NZ);
+  if (!__syncthreads_and(mbar_wait(bar, 0, err))) return;
+  {  // x: complex FFT of each row pair z = a + i b, then split into two half spectra
     constexpr int G = FftPlan<NX>::G;
-    constexpr int NG = kThreads / G;
+    constexpr int NG = kPlaneThreads / G;
     const int gid = tid / G, lg = tid % G;
     for (int base = 0; base < NZ / 2; base += NG) {
       const int p = base + gid;
       const unsigned mask = __ballot_sync(0xffffffffu, p < NZ / 2);
       if (p >= NZ / 2) continue;
       cplx<T> *row = plane + p * (NX + 2);
+      const T *ra = real + (2 * p) * NX;
+      for (int n = lg; n < NX; n += G) row[n] = mk<T>(ra[n] * in_scale, ra[NX + n] * in_scale);
+      __syncwarp(mask);
       fft_row<T, NX, false>(row, 1, twx, lg, mask);
       split_pair<T, NX>(row, row, row + P, 1, lg, mask);
     }
@@ -133,7 +158,7 @@ k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__
   __syncthreads();
   {  // z: complex FFT of each of the P columns (stride P)
     constexpr int G = FftPlan<NZ>::G;
-    constexpr int NG = kThreads / G;
+    constexpr int NG = kPlaneThreads / G;
     const int gid = tid / G, lg = tid % G;
     for (int base = 0; base < P; base += NG) {
       const int c = base + gid;
@@ -142,33 +167,53 @@ k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__
       fft_row<T, NZ, false>(plane + c, P, twz, lg, mask);
     }
   }
+  fence_proxy_async();
   __syncthreads();
-  cplx<T> *dst = S + (size_t)j * NZ * P;
-  for (int idx = tid; idx < NZ * P; idx += kThreads) dst[idx] = plane[idx];
+  if (tid == 0) {
+    if (zrhs) zrhs[j] = (double)plane[0].x;
+    bulk_s2g(S + (size_t)j * NZ * P, plane, (uint32_t)(sizeof(cplx<T>) * NZ * P));
+    bulk_commit();
+    bulk_wait_read();
+  }
 }
 
 // Inverse: spectrum plane -> real plane, out = addend + scale * result.
 template <typename T, int NX, int NZ>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kPlaneThreads)
 k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx_g,
-            const cplx<T> *__restrict__ twz_g, T scale) {
-  constexpr int P = NX / 2 + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
+            const cplx<T> *__restrict__ twz_g, T scale, int *err, const double *zsol) {
+  using L = PlaneLayout<T, NX, NZ>;
+  constexpr int P = L::P;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  T *addb = reinterpret_cast<T *>(smem_raw + L::staging);
+  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw + L::tw);
   cplx<T> *twz = twx + NX;
-  cplx<T> *plane = twz + NZ;
+  cplx<T> *plane = reinterpret_cast<cplx<T> *>(smem_raw + L::plane);
   const int j = blockIdx.x;
   const int tid = threadIdx.x;
-  load_twiddles<T>(twx, twx_g, NX);
-  load_twiddles<T>(twz, twz_g, NZ);
-  {
-    const cplx<T> *src = S + (size_t)j * NZ * P;
-    for (int idx = tid; idx < NZ * P; idx += kThreads) plane[idx] = src[idx];
+  constexpr uint32_t kSpecBytes = sizeof(cplx<T>) * NZ * P;
+  constexpr uint32_t kAddBytes = sizeof(T) * NZ * NX;
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
   }
   __syncthreads();
+  if (tid == 0) {
+    mbar_arrive_expect_tx(bar, kSpecBytes + (addend ? kAddBytes : 0u));
+    bulk_g2s(plane, S + (size_t)j * NZ * P, kSpecBytes, bar);
+    if (addend) bulk_g2s(addb, addend + (size_t)j * NZ * NX, kAddBytes, bar);
+  }
+  load_twiddles<T>(twx, twx_g, NX);
+  load_twiddles<T>(twz, twz_g, NZ);
+  if (!__syncthreads_and(mbar_wait(bar, 0, err))) return;
+  if (zsol) {
+    if (tid == 0) plane[0] = mk<T>((T)zsol[j], (T)0);
+    __syncthreads();
+  }
   {
     constexpr int G = FftPlan<NZ>::G;
-    constexpr int NG = kThreads / G;
+    constexpr int NG = kPlaneThreads / G;
     const int gid = tid / G, lg = tid % G;
     for (int base = 0; base < P; base += NG) {
       const int c = base + gid;
@@ -180,10 +225,9 @@ k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T
   __syncthreads();
   {
     constexpr int G = FftPlan<NX>::G;
-    constexpr int NG = kThreads / G;
+    constexpr int NG = kPlaneThreads / G;
     const int gid = tid / G, lg = tid % G;
     T *dst = out + (size_t)j * NZ * NX;
-    const T *add = addend ? addend + (size_t)j * NZ * NX : nullptr;
     for (int base = 0; base < NZ / 2; base += NG) {
       const int p = base + gid;
       const unsigned mask = __ballot_sync(0xffffffffu, p < NZ / 2);
@@ -192,11 +236,11 @@ k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T
       merge_pair<T, NX>(row, row + P, 1, row, lg, mask);
       fft_row<T, NX, true>(row, 1, twx, lg, mask);
       T *d0 = dst + (size_t)(2 * p) * NX;
-      const T *a0 = add ? add + (size_t)(2 * p) * NX : nullptr;
+      const T *a0 = addb + (2 * p) * NX;
       for (int n = lg; n < NX; n += G) {
         const cplx<T> z = row[n];
         T v0 = z.x * scale, v1 = z.y * scale;
-        if (a0) { v0 += a0[n]; v1 += a0[NX + n]; }
+        if (addend) { v0 += a0[n]; v1 += a0[NX + n]; }
         d0[n] = v0;
         d0[NX + n] = v1;
       }
@@ -282,7 +326,7 @@ k_xinv_rows(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T
 // grid (ceil(P / W), ny), block W * G lanes.
 template <typename T, int NZ, bool INV, int W>
 __global__ void __launch_bounds__(1024)
-k_zcols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twz_g, int P) {
+k_zcols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twz_g, int P, double *zrhs, const double *zsol) {
   constexpr int G = FftPlan<NZ>::G;
   constexpr int PITCH = W + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -300,12 +344,15 @@ k_zcols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twz_g, int P) {
     if (c < nc) tile[k * PITCH + c] = base[(size_t)k * P + c];
   }
   __syncthreads();
+  if (INV && zsol && c0 == 0 && tid == 0) tile[0] = mk<T>((T)zsol[j], (T)0);
+  __syncthreads();
   {
     const int gid = tid / G, lg = tid % G;
     const unsigned mask = __ballot_sync(warp_full_mask(), gid < nc);
     if (gid < nc) fft_row<T, NZ, INV>(tile + gid, PITCH, twz, lg, mask);
   }
   __syncthreads();
+  if (!INV && zrhs && c0 == 0 && tid == 0) zrhs[j] = (double)tile[0].x;
   for (int idx = tid; idx < NZ * W; idx += nthr) {
     const int k = idx / W, c = idx - k * W;
     if (c < nc) base[(size_t)k * P + c] = tile[k * PITCH + c];
@@ -316,7 +363,7 @@ k_zcols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twz_g, int P) {
 // dispatch
 // --------------------------------------------------------------------------
 template <typename T> size_t plane_smem_bytes(int nx, int nz) {
-  return sizeof(cplx<T>) * ((size_t)nx + nz + (size_t)nz * (nx / 2 + 1));
+  return 16 + sizeof(T) * (size_t)nz * nx + sizeof(cplx<T>) * ((size_t)nx + nz + (size_t)nz * (nx / 2 + 1));
 }
 
 template <typename T> constexpr int zcols_width() { return sizeof(T) == 4 ? 16 : 8; }
@@ -353,7 +400,7 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
     if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
       static bool attr = false;                                                     \
       if (!attr) { cudaError_t e = set_plane_attr<T, a, b>(); if (e) return e; attr = true; } \
-      k_plane_fwd<T, a, b><<<ny, kThreads, bytes, st>>>(in, S, twx, twz, in_scale);  \
+      k_plane_fwd<T, a, b><<<ny, kPlaneThreads, bytes, st>>>(in, S, twx, twz, in_scale, g.err, g.zrhs);  \
       return cudaGetLastError();                                                    \
     }                                                                               \
   }
@@ -395,7 +442,7 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
       attr = true;                                                                         \
     }                                                                                      \
     dim3 grid(ceil_div(P, W), ny);                                                         \
-    k_zcols<T, N, false, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P);            \
+    k_zcols<T, N, false, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P, g.zrhs, nullptr);            \
     done = true;                                                                           \
   }
   IBM_FOR_EACH_N(X)
@@ -415,7 +462,7 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
     if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
       static bool attr = false;                                                     \
       if (!attr) { cudaError_t e = set_plane_attr<T, a, b>(); if (e) return e; attr = true; } \
-      k_plane_inv<T, a, b><<<ny, kThreads, bytes, st>>>(S, out, addend, twx, twz, scale); \
+      k_plane_inv<T, a, b><<<ny, kPlaneThreads, bytes, st>>>(S, out, addend, twx, twz, scale, g.err, g.zsol); \
       return cudaGetLastError();                                                    \
     }                                                                               \
   }
@@ -436,7 +483,7 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
       attr = true;                                                                         \
     }                                                                                      \
     dim3 grid(ceil_div(P, W), ny);                                                         \
-    k_zcols<T, N, true, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P);             \
+    k_zcols<T, N, true, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P, nullptr, g.zsol);             \
     done = true;                                                                           \
   }
   IBM_FOR_EACH_N(X)

@@ -29,6 +29,8 @@ SHAPES = [
     (96, 33, 64),     # mixed shape, odd ny
     (256, 12, 256),   # plane larger than shared memory (split x/z path)
     (384, 9, 32),     # longest radix-3 row, split path
+    (16, 200, 24),    # pencils of 200: FP32 split-component block solve, FP64 serial sweep
+    (32, 300, 16),    # pencils longer than 256: serial sweep in both precisions
 ]
 
 
@@ -105,7 +107,7 @@ def test_poisson_in_place_and_128_lowpass():
         ibm.ibm_plan_destroy(plan)
 
 
-@pytest.mark.parametrize("shape", [(32, 32, 32), (12, 10, 24), (256, 12, 256), (48, 17, 96)])
+@pytest.mark.parametrize("shape", [(32, 32, 32), (12, 10, 24), (256, 12, 256), (48, 17, 96), (24, 129, 16)])
 @pytest.mark.parametrize("bc", [ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_CELL_DIRICHLET,
                                 ibm.IBM_FIELD_FACE_DIRICHLET])
 @pytest.mark.parametrize("c", [5e-6, 0.05])
