@@ -155,6 +155,23 @@ int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launche
 int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream,
                       ibm_info *info);
 
+/* Poisson solve for callers that cannot allocate device memory.  The paper
+ * has no counterpart: it exists for hosts that own the GPU's memory budget
+ * (memory pools, frameworks that hand out only their own buffers) or must
+ * not call cudaMalloc mid-run.  Same FP32 method and result as
+ * ibm_poisson_solve on an IBM_FP32_REFINED plan with refine_iters steps, but
+ * no plan: the workspace lives in one static 24 MiB device array that the
+ * library holds on every GPU that loads it until the process exits, enough
+ * for a 128^3 grid with one refinement step.  Larger grids return
+ * IBM_ERR_ARG with the bytes needed.  rhs and phi are distinct float fields
+ * [ny][nz][nx] in device memory (16-byte aligned).  The first call on a
+ * device looks up the array's device address; make that first call before
+ * capturing a stream into a CUDA graph.  All calls share the array and it
+ * keeps the last call's contents: calls that overlap on the GPU race, so
+ * serialise them (one stream, one host thread at a time). */
+int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[3], int refine_iters,
+                              const float *rhs, float *phi, void *stream);
+
 /* Helmholtz solve, Eq. 2e (S1.1 + S1.2): (I - c L_h) u = rhs, c > 0, with the
  * wall rows selected by field_bc (Appendix B).  Eq. 2e is this system with
  * c = beta_n dt / Re.  rhs may equal u. */

@@ -80,6 +80,7 @@ _SIG = {
     "ibm_plan_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ibm_poisson_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_helmholtz_solve": (_I, [_P, _D, _I, _P, _P, _P, ctypes.POINTER(ibm_info)]),
+    "ibm_poisson_solve_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_D), _I, _P, _P, _P]),
     "ibm_interp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "ibm_spread": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "ibm_substep": (_I, [_P, ctypes.POINTER(ibm_state), _I, _D, _D, ctypes.POINTER(ibm_markers), _P,
@@ -195,6 +196,14 @@ def ibm_poisson_solve(plan, rhs, phi, stream=None, info=False):
     _check(lib().ibm_poisson_solve(plan, _ptr(rhs), _ptr(phi), _stream(stream),
                                    ctypes.byref(inf) if inf is not None else None))
     return inf.as_dict() if inf is not None else None
+
+
+def ibm_poisson_solve_noalloc(nx, ny, nz, h, refine_iters, rhs, phi, stream=None):
+    """FP32 Poisson solve whose workspace is the library's static device
+    scratch (no device allocation; see include/ibm.h)."""
+    hh = (_D * 3)(*[float(x) for x in h])
+    return _check(lib().ibm_poisson_solve_noalloc(nx, ny, nz, hh, refine_iters, _ptr(rhs), _ptr(phi),
+                                                  _stream(stream)))
 
 
 def ibm_helmholtz_solve(plan, c, field_bc, rhs, u, stream=None, info=False):
