@@ -312,6 +312,11 @@ def run_gpu(args):
     # ---- standalone Poisson: FP32-refined vs FP64 at 128^3 ----
     solves = poisson_compare(ibm, torch, g)
 
+    # ---- batched (64 instances, one graph launch) and served workloads ----
+    batched = batched_compare(ibm, torch) if not args.no_extras else None
+    serving = serve_sample(ibm) if not args.no_extras else None
+    plate = large_plate(ibm, torch) if not args.no_extras else None
+
     # ---- roofline of the dominant kernel ----
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
@@ -352,6 +357,9 @@ def run_gpu(args):
         "p99_ms": float(np.percentile(step_ms, 99)),
         "value_traced": pts * args.steps * ws / (traced_ms * 1e-3),
         "poisson": solves,
+        "batched": batched,
+        "serving": serving,
+        "large_plate": plate,
         "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")},
         "clocks": clocks,
         "timed_region_s": t_host1 - t_host0,
@@ -401,6 +409,185 @@ def poisson_compare(ibm, torch, g):
     res["fp32_refined_rel_l2_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(outs["fp64"]))
     res["speedup_fp32_refined_over_fp64"] = res["fp32_refined"]["solves_per_s"] / res["fp64"]["solves_per_s"]
     return res
+
+
+def batched_compare(ibm, torch):
+    """64 instances, grids drawn from {32,48,64,96,128}^3, 4 right-hand sides
+    each: FP32 + 1 refinement through ibm_batch_poisson (one CUDA-graph
+    launch per right-hand-side set) vs 64 sequential plain FP64 solves."""
+    from paper_2406_19920_gb300 import synth
+    rng = np.random.default_rng(3005)
+    dims = [(int(n), int(n), int(n)) for n in rng.choice([32, 48, 64, 96, 128], 64)]
+    hs = [synth.grid(*d)[3:] for d in dims]
+    t0 = time.perf_counter()
+    b = ibm.ibm_batch_create(dims, hs, ibm.IBM_FP32_REFINED, 1)
+    create_s = time.perf_counter() - t0
+    rhs = [[torch.from_numpy(synth.rhs_lowpass_noise(*d, kmax=12.0, workload=3, stream=100 * k + i))
+            .to("cuda", torch.float32) for i, d in enumerate(dims)] for k in range(4)]
+    phi = [[torch.empty_like(x) for x in r] for r in rhs]
+    for k in range(4):
+        ibm.ibm_batch_poisson(b, rhs[k], phi[k])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    e0.record()
+    for _ in range(reps):
+        for k in range(4):
+            ibm.ibm_batch_poisson(b, rhs[k], phi[k])
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    pts = sum(d[0] * d[1] * d[2] for d in dims) * 4
+    plans = [ibm.ibm_plan_create(*d, h, ibm.IBM_FP64, 0) for d, h in zip(dims, hs)]
+    r64 = [x.double() for x in rhs[0]]
+    p64 = [torch.empty_like(x) for x in r64]
+    for pl, r, o in zip(plans, r64, p64):
+        ibm.ibm_poisson_solve(pl, r, o)
+    torch.cuda.synchronize()
+    e0.record()
+    for pl, r, o in zip(plans, r64, p64):
+        ibm.ibm_poisson_solve(pl, r, o)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    err = max(float(torch.linalg.vector_norm(a.double() - c) / torch.linalg.vector_norm(c))
+              for a, c in zip(phi[0], p64))
+    for pl in plans:
+        ibm.ibm_plan_destroy(pl)
+    ibm.ibm_batch_destroy(b)
+    return {"instances": 64, "rhs_per_instance": 4, "grid_pts_per_set": pts // 4,
+            "fp32_refined_batched": {"solves_per_s": 256e3 / ms, "grid_pts_per_s": pts / (ms * 1e-3),
+                                     "ms_per_256_solves": ms},
+            "fp64_sequential": {"solves_per_s": 64e3 / ms64, "grid_pts_per_s": (pts / 4) / (ms64 * 1e-3)},
+            "speedup": (256e3 / ms) / (64e3 / ms64), "max_rel_l2_vs_fp64": err, "create_and_tune_s": create_s}
+
+
+def large_plate(ibm, torch, stages=48):
+    """Bio-inspired external-flow workload: 384x256x256 on a uniform h = 2 pi/384
+    grid (periodic x, z; walls in y), FP32 + 1 refinement, a flat plate of
+    100,000 markers (250 x 400 lattice, chord 1, span 2) heaving with amplitude
+    0.5 and period 1 about y = Ly/2.  Runs `stages` consecutive RK stages
+    (16 full steps) and reports ms per stage, per-kernel time, the refined
+    Poisson solve's relative residual and max |D u| after projection."""
+    from paper_2406_19920_gb300 import synth
+    nx, ny, nz = 384, 256, 256
+    h = 2 * math.pi / 384
+    g = (nx, ny, nz, h, h, h)
+    Ly = ny * h
+    u, v, w = synth.div_free_velocity(g, workload=2, kmax=16.0, rms=0.1)
+    X0, dV = synth.flat_plate(250, 400, 1.0, 2.0, (nx * h / 2, Ly / 2, nz * h / 2), h)
+    f32 = torch.float32
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", f32)
+    fields = [dev(u), dev(v), dev(w), torch.zeros((ny, nz, nx), dtype=f32, device="cuda")]
+    Ns = [torch.zeros((ny, nz, nx), dtype=f32, device="cuda") for _ in range(3)]
+    plan = ibm.ibm_plan_create(nx, ny, nz, (h, h, h), ibm.IBM_FP32_REFINED, 1)
+    st = ibm.ibm_state(*[t.data_ptr() for t in fields + Ns], 0.0)
+    X0d, dVd = dev(X0), dev(dV)
+    X = torch.empty((X0.shape[0], 3), dtype=f32, device="cuda")
+    Ud, F = torch.empty_like(X), torch.empty_like(X)
+    mk = ibm.ibm_markers(X0.shape[0], X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
+                         ibm.IBM_MOTION_HEAVE, (ctypes.c_double * 4)(0.5, 1.0, 0.0, 0.0))
+    ibm.ibm_substep(plan, st, 1, DT, NU, mk)
+    torch.cuda.synchronize()
+    ibm.ibm_plan_profile(plan, True)
+    ibm.ibm_plan_profile_read(plan)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(stages):
+        ibm.ibm_substep(plan, st, (i + 1) % 3 + 1, DT, NU, mk)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / stages
+    prof = ibm.ibm_plan_profile_read(plan)
+    ibm.ibm_plan_profile(plan, False)
+    info = ibm.ibm_substep(plan, st, 1, DT, NU, mk, info=True)
+    # relative residual of the refined Poisson solve on the stage's own divergence field
+    b = torch.randn((ny, nz, nx), device="cuda")
+    phi = torch.empty_like(b)
+    pinfo = ibm.ibm_poisson_solve(plan, b, phi, info=True)
+    ibm.ibm_plan_destroy(plan)
+    return {"grid": [nx, ny, nz], "markers": int(X0.shape[0]), "stages": stages, "ms_per_stage": ms,
+            "grid_pts_per_s": nx * ny * nz / (ms * 1e-3),
+            "kernel_ms_per_stage": {k: v[0] / stages for k, v in prof.items()},
+            "div_max_after_projection": info["div_max"], "div_max_before": info["div_before"],
+            "poisson_rel_residual_refined": pinfo["rel_residual"], "sim_time": st.t}
+
+
+def serve_sample(ibm, duration_s=2.0, rate=2000.0):
+    """Open-loop Poisson arrivals at `rate` req/s for `duration_s` into one
+    server per precision.  Kinds: 60 % Poisson, 25 % Helmholtz, 15 % RK stage;
+    grids log-uniform in points between 32^3 and 128^3, snapped to supported
+    shapes with nx >= ny = nz; markers log-uniform in [1k, 20k]."""
+    from paper_2406_19920_gb300 import synth
+    rng = np.random.default_rng(4004)
+    sizes = [16, 24, 32, 48, 64, 96, 128]
+    shapes = sorted({(nx, ny, ny) for nx in sizes for ny in sizes if nx >= ny and 32 ** 3 <= nx * ny * ny <= 128 ** 3})
+    logs = np.log([a * b * c for a, b, c in shapes])
+
+    def draw_shape():
+        t = rng.uniform(np.log(32 ** 3), np.log(128 ** 3))
+        return shapes[int(np.argmin(np.abs(logs - t)))]
+
+    n_req = int(rate * duration_s)
+    gaps = rng.exponential(1.0 / rate, n_req)
+    kinds = rng.choice([0, 1, 2], n_req, p=[0.6, 0.25, 0.15])
+    plan = [(k, draw_shape(), int(np.exp(rng.uniform(np.log(1000), np.log(20000))))) for k in kinds]
+    inputs = {}
+    for k, sh, m in plan:
+        key = (k, sh)
+        if key not in inputs:
+            nx, ny, nz = sh
+            g = synth.grid(nx, ny, nz)
+            if k == 2:
+                u, v, w = synth.div_free_velocity(g, workload=4, kmax=4)
+                data = np.ascontiguousarray(np.stack([u, v, w, np.zeros_like(u)]))
+            else:
+                data = synth.white_noise(nx, ny, nz, workload=4, stream=len(inputs))
+            inputs[key] = (g, data, np.zeros_like(data))
+    X0, dV = synth.fibonacci_sphere(20000, 0.25, (math.pi, 1.0, math.pi), 2 * math.pi / 32)
+    X0, dV = np.ascontiguousarray(X0), np.ascontiguousarray(dV)
+    out = {}
+    for name, prec in (("fp32_refined", ibm.IBM_FP32_REFINED), ("fp64", ibm.IBM_FP64)):
+        srv = ibm.ibm_server_create(64 << 30, 8, 1 << 16)
+        reqs = []
+        for k, sh, m in plan:
+            g, data, dst = inputs[(k, sh)]
+            r = ibm.ibm_request()
+            r.kind, (r.nx, r.ny, r.nz) = k, sh
+            r.h = (ctypes.c_double * 3)(*g[3:])
+            r.precision, r.refine_iters = prec, 1
+            r.c, r.field_bc = 0.5 * DT * NU, ibm.IBM_FIELD_CELL_DIRICHLET
+            r.in_, r.out = data.ctypes.data, dst.ctypes.data
+            r.n_markers = m if k == 2 else 0
+            r.X0, r.dV = X0.ctypes.data, dV.ctypes.data
+            r.motion, r.params = ibm.IBM_MOTION_TRANSLATE, (ctypes.c_double * 4)(0.1, 0, 0, 0)
+            r.dt, r.nu, r.rk_stage = DT, NU, 1
+            reqs.append(r)
+        tickets = []
+        t0 = time.perf_counter()
+        t_next = t0
+        for r, gap in zip(reqs, gaps):
+            t_next += gap
+            while time.perf_counter() < t_next:
+                pass
+            tickets.append(ibm.ibm_submit(srv, r))
+        lat, dev_ms, ok = [], [], 0
+        for t in tickets:
+            if t is None:
+                continue
+            rc, res = ibm.ibm_wait(srv, t, 300.0)
+            if rc == ibm.IBM_OK:
+                ok += 1
+                lat.append(res.total_ms)
+                dev_ms.append(res.device_ms)
+        wall = time.perf_counter() - t0
+        ibm.ibm_server_destroy(srv)
+        out[name] = {"requests": n_req, "completed": ok, "throughput_req_per_s": ok / wall,
+                     "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+                     "device_ms_mean": float(np.mean(dev_ms))}
+    out["workload"] = ("Poisson arrivals %.0f req/s for %.1f s; 60/25/15 %% Poisson/Helmholtz/RK stage; grids "
+                       "log-uniform 32^3..128^3; 8 streams" % (rate, duration_s))
+    return out
 
 
 # ---------------------------------------------------------------------------
@@ -461,6 +648,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving samples")
     ap.add_argument("--quick", action="store_true",
                     help="warm-up and timed steps only (no tracing pass, e2e, Poisson comparison or CPU baseline); "
                          "used for profiler launch lists")

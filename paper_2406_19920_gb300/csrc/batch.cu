@@ -1,0 +1,380 @@
+// batch.cu -- the autotuner and batched solves of many independent grids.
+//
+// Autotuner.  For a grid shape and precision it times every available
+// variant of the solve -- pencil solver (serial excess-form sweep or the
+// warp-parallel substructured solve) x transform path (one CTA per y-plane,
+// or split x and z passes) -- on scratch buffers, keeps the fastest, and
+// remembers it for the process (optionally in the text file named by
+// IBM_TUNE_CACHE, one line per shape).
+//
+// Batch.  ibm_batch_create makes one plan per instance (each with its own
+// workspace, so instances never share scratch) and tunes every distinct
+// shape.  ibm_batch_poisson captures all instances' solves into one CUDA
+// graph -- a fork over K concurrent branches of the caller's stream, each
+// branch running a share of the instances, largest first -- and replays it
+// as a single graph launch.  K is tuned on the first call by timing the
+// candidate graphs; graphs are cached per set of field pointers.
+#include <algorithm>
+#include <chrono>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "plan.h"
+
+namespace ibm {
+
+struct TuneKey {
+  int nx, ny, nz, precision, refine;
+  bool operator<(const TuneKey &o) const {
+    return std::tie(nx, ny, nz, precision, refine) < std::tie(o.nx, o.ny, o.nz, o.precision, o.refine);
+  }
+};
+static std::mutex g_tune_mu;
+static std::map<TuneKey, TuneChoice> g_tune;
+static bool g_tune_loaded = false;
+
+static void tune_load_locked() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = getenv("IBM_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  TuneKey k;
+  TuneChoice c;
+  while (fscanf(f, "%d %d %d %d %d %d %d %lf", &k.nx, &k.ny, &k.nz, &k.precision, &k.refine, &c.pencil_mode,
+                &c.use_plane, &c.ms) == 8)
+    g_tune[k] = c;
+  fclose(f);
+}
+
+static void tune_save_locked() {
+  const char *path = getenv("IBM_TUNE_CACHE");
+  if (!path) return;
+  FILE *f = fopen(path, "w");
+  if (!f) return;
+  for (auto &kv : g_tune)
+    fprintf(f, "%d %d %d %d %d %d %d %.6f\n", kv.first.nx, kv.first.ny, kv.first.nz, kv.first.precision,
+            kv.first.refine, kv.second.pencil_mode, kv.second.use_plane, kv.second.ms);
+  fclose(f);
+}
+
+static bool substructured_available(const ibm_plan_s *p) {
+  const int n = p->ny;  // Poisson pencils (cell-centred)
+  return p->precision == IBM_FP32_REFINED ? n <= 256 : n <= 128;
+}
+
+static bool plane_available(const ibm_plan_s *p) {
+  TransformGeom g = geom_of(p);
+  g.use_plane = true;
+  return p->precision == IBM_FP64 ? transform_launches<double>(g) == 1 : transform_launches<float>(g) == 1;
+}
+
+// Times the Poisson solve of plan p for every variant and applies the
+// fastest to p.  Synchronises the device; allocates two scratch fields.
+int tune_plan(ibm_plan_s *p, TuneChoice *out) {
+  const TuneKey key{p->nx, p->ny, p->nz, p->precision, p->refine};
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_load_locked();
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      p->pencil_mode = it->second.pencil_mode;
+      p->use_plane = it->second.use_plane;
+      // make sure every kernel of the chosen variant has its attributes set
+      // before any stream capture: run it once
+      void *a = nullptr, *b = nullptr;
+      IBM_CUDA_TRY(cudaMalloc(&a, p->npts * p->esz));
+      cudaError_t e = cudaMalloc(&b, p->npts * p->esz);
+      if (e != cudaSuccess) { cudaFree(a); return cuda_error(e, "tuner scratch"); }
+      cudaMemset(a, 0, p->npts * p->esz);
+      int rc = plan_solve(p, 0, 0.0, 0, a, b, nullptr, 0, nullptr);
+      cudaDeviceSynchronize();
+      cudaFree(a);
+      cudaFree(b);
+      if (out) *out = it->second;
+      return rc;
+    }
+  }
+  void *a = nullptr, *b = nullptr;
+  IBM_CUDA_TRY(cudaMalloc(&a, p->npts * p->esz));
+  cudaError_t e = cudaMalloc(&b, p->npts * p->esz);
+  if (e != cudaSuccess) { cudaFree(a); return cuda_error(e, "tuner scratch"); }
+  cudaMemset(a, 0, p->npts * p->esz);
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  TuneChoice best{0, 1, 1e30};
+  int rc = IBM_OK;
+  for (int pm = 0; pm <= (substructured_available(p) ? 1 : 0) && rc == IBM_OK; ++pm) {
+    for (int up = plane_available(p) ? 1 : 0; up >= 0 && rc == IBM_OK; --up) {
+      p->pencil_mode = pm;
+      p->use_plane = up;
+      for (int w = 0; w < 2 && rc == IBM_OK; ++w) rc = plan_solve(p, 0, 0.0, 0, a, b, nullptr, 0, nullptr);
+      const int reps = 5;
+      cudaEventRecord(e0, 0);
+      for (int r = 0; r < reps && rc == IBM_OK; ++r) rc = plan_solve(p, 0, 0.0, 0, a, b, nullptr, 0, nullptr);
+      cudaEventRecord(e1, 0);
+      cudaEventSynchronize(e1);
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      ms /= reps;
+      if (rc == IBM_OK && ms < best.ms) best = {pm, up, ms};
+      if (!up) break;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(a);
+  cudaFree(b);
+  if (rc) return rc;
+  p->pencil_mode = best.pencil_mode;
+  p->use_plane = best.use_plane;
+  {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune[key] = best;
+    tune_save_locked();
+  }
+  if (out) *out = best;
+  return IBM_OK;
+}
+
+}  // namespace ibm
+
+using namespace ibm;
+
+struct ibm_batch_s {
+  int count = 0;
+  std::vector<ibm_plan_s *> plans;
+  std::vector<int> order;  // instances, largest grid first
+  int branches = 0;        // graph fork width, tuned on the first call
+  static constexpr int kMaxBranches = 16;
+  cudaStream_t cap = nullptr;                 // graphs are captured and launched here
+  cudaStream_t side[kMaxBranches] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[kMaxBranches] = {};
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;  // order cap after / before the caller's stream
+  struct Graph {
+    std::vector<uintptr_t> key;
+    cudaGraphExec_t exec;
+  };
+  std::vector<Graph> graphs;  // most recently used last
+};
+
+static void batch_free(ibm_batch_s *b) {
+  if (!b) return;
+  for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto *p : b->plans)
+    if (p) ibm_plan_destroy(p);
+  for (int k = 0; k < ibm_batch_s::kMaxBranches; ++k) {
+    if (b->side[k]) cudaStreamDestroy(b->side[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->ev_in) cudaEventDestroy(b->ev_in);
+  if (b->ev_out) cudaEventDestroy(b->ev_out);
+  if (b->cap) cudaStreamDestroy(b->cap);
+  delete b;
+}
+
+// Captures the whole batch as one graph with K branches forked from `st`.
+static int capture_batch(ibm_batch_s *b, int K, const void *const *rhs, void *const *phi, cudaStream_t st,
+                         cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  IBM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = IBM_OK;
+  cudaError_t e = cudaEventRecord(b->ev_fork, st);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+  if (e != cudaSuccess) rc = cuda_error(e, "batch fork");
+  for (size_t n = 0; n < b->order.size() && rc == IBM_OK; ++n) {
+    const int i = b->order[n];
+    rc = plan_solve(b->plans[i], 0, 0.0, 0, rhs[i], phi[i], nullptr, b->side[n % K], nullptr);
+  }
+  for (int k = 0; k < K && rc == IBM_OK; ++k) {
+    e = cudaEventRecord(b->ev_join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join[k], 0);
+    if (e != cudaSuccess) rc = cuda_error(e, "batch join");
+  }
+  e = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+  return IBM_OK;
+}
+
+extern "C" {
+
+int ibm_batch_create(int count, const int *dims, const double *h, int precision, int refine_iters,
+                     ibm_batch *out) {
+  if (!out || !dims || !h || count <= 0 || count > 4096)
+    return set_error(IBM_ERR_ARG, "ibm_batch_create: bad arguments (count %d)", count);
+  *out = nullptr;
+  ibm_batch_s *b = new (std::nothrow) ibm_batch_s();
+  if (!b) return set_error(IBM_ERR_OOM, "ibm_batch_create: host allocation");
+  b->count = count;
+  b->plans.assign(count, nullptr);
+  for (int i = 0; i < count; ++i) {
+    int rc = ibm_plan_create(dims[3 * i], dims[3 * i + 1], dims[3 * i + 2], IBM_BC_PXZ_WALL_Y, h + 3 * i, precision,
+                             refine_iters, &b->plans[i]);
+    if (rc) {
+      batch_free(b);
+      return rc;
+    }
+  }
+  // tune every distinct shape once; plans of the same shape share the choice
+  std::map<TuneKey, TuneChoice> chosen;
+  for (int i = 0; i < count; ++i) {
+    ibm_plan_s *p = b->plans[i];
+    const TuneKey k{p->nx, p->ny, p->nz, p->precision, p->refine};
+    auto it = chosen.find(k);
+    if (it == chosen.end()) {
+      TuneChoice c;
+      int rc = tune_plan(p, &c);
+      if (rc) {
+        batch_free(b);
+        return rc;
+      }
+      it = chosen.emplace(k, c).first;
+    }
+    p->pencil_mode = it->second.pencil_mode;
+    p->use_plane = it->second.use_plane;
+  }
+  b->order.resize(count);
+  for (int i = 0; i < count; ++i) b->order[i] = i;
+  std::stable_sort(b->order.begin(), b->order.end(),
+                   [&](int x, int y) { return b->plans[x]->npts > b->plans[y]->npts; });
+  for (int k = 0; k < ibm_batch_s::kMaxBranches; ++k) {
+    cudaError_t e = cudaStreamCreateWithFlags(&b->side[k], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+    if (e != cudaSuccess) {
+      batch_free(b);
+      return cuda_error(e, "ibm_batch_create: streams");
+    }
+  }
+  cudaError_t e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    batch_free(b);
+    return cuda_error(e, "ibm_batch_create: event");
+  }
+  *out = b;
+  return IBM_OK;
+}
+
+int ibm_batch_destroy(ibm_batch batch) {
+  if (!batch) return set_error(IBM_ERR_ARG, "ibm_batch_destroy: NULL batch");
+  cudaDeviceSynchronize();
+  batch_free(batch);
+  return IBM_OK;
+}
+
+int ibm_batch_poisson(ibm_batch b, const void *const *rhs, void *const *phi, void *stream) {
+  if (!b || !rhs || !phi) return set_error(IBM_ERR_ARG, "ibm_batch_poisson: NULL argument");
+  std::vector<uintptr_t> key(2 * (size_t)b->count);
+  for (int i = 0; i < b->count; ++i) {
+    if (!rhs[i] || !phi[i] || !aligned_to(rhs[i], 16) || !aligned_to(phi[i], 16))
+      return set_error(IBM_ERR_ARG, "ibm_batch_poisson: field %d NULL or not 16-byte aligned", i);
+    key[2 * i] = (uintptr_t)rhs[i];
+    key[2 * i + 1] = (uintptr_t)phi[i];
+  }
+  // the graph runs on the batch's own stream, ordered after the caller's
+  // stream and before its later work (capture cannot start on the legacy
+  // default stream, which callers often use)
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t st = b->cap;
+  IBM_CUDA_TRY(cudaEventRecord(b->ev_in, user));
+  IBM_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_in, 0));
+  for (size_t g = 0; g < b->graphs.size(); ++g) {
+    if (b->graphs[g].key == key) {
+      auto hit = b->graphs[g];
+      b->graphs.erase(b->graphs.begin() + g);
+      b->graphs.push_back(hit);
+      IBM_CUDA_TRY(cudaGraphLaunch(hit.exec, st));
+      IBM_CUDA_TRY(cudaEventRecord(b->ev_out, st));
+      IBM_CUDA_TRY(cudaStreamWaitEvent(user, b->ev_out, 0));
+      return IBM_OK;
+    }
+  }
+  if (b->branches == 0) {
+    // first call: time the candidate fork widths on scratch fields (repeated
+    // launches must not touch the caller's data, which may be in place)
+    std::vector<void *> tmp(2 * (size_t)b->count, nullptr);
+    int rc = IBM_OK;
+    for (int i = 0; i < b->count && rc == IBM_OK; ++i) {
+      const size_t bytes = b->plans[i]->npts * b->plans[i]->esz;
+      cudaError_t e1 = cudaMalloc(&tmp[2 * i], bytes);
+      if (e1 == cudaSuccess) e1 = cudaMalloc(&tmp[2 * i + 1], bytes);
+      if (e1 == cudaSuccess) e1 = cudaMemsetAsync(tmp[2 * i], 0, bytes, st);
+      if (e1 != cudaSuccess) rc = cuda_error(e1, "ibm_batch_poisson: tuning scratch");
+    }
+    std::vector<const void *> trhs(b->count);
+    std::vector<void *> tphi(b->count);
+    for (int i = 0; i < b->count; ++i) {
+      trhs[i] = tmp[2 * i];
+      tphi[i] = tmp[2 * i + 1];
+    }
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (rc == IBM_OK) {
+      cudaEventCreate(&e0);
+      cudaEventCreate(&e1);
+    }
+    float best = 1e30f;
+    for (int K : {1, 2, 4, 8, 16}) {
+      if (rc || (K > b->count && K > 1)) break;
+      cudaGraphExec_t ex = nullptr;
+      rc = capture_batch(b, K, trhs.data(), tphi.data(), st, &ex);
+      if (rc) break;
+      cudaGraphLaunch(ex, st);  // warm
+      cudaEventRecord(e0, st);
+      cudaGraphLaunch(ex, st);
+      cudaEventRecord(e1, st);
+      cudaError_t e = cudaEventSynchronize(e1);
+      cudaGraphExecDestroy(ex);
+      if (e != cudaSuccess) {
+        rc = cuda_error(e, "ibm_batch_poisson: tuning launch");
+        break;
+      }
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        b->branches = K;
+      }
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    cudaStreamSynchronize(st);
+    for (void *t : tmp)
+      if (t) cudaFree(t);
+    if (rc) {
+      b->branches = 0;
+      return rc;
+    }
+  }
+  cudaGraphExec_t exec = nullptr;
+  {
+    int rc = capture_batch(b, b->branches, rhs, phi, st, &exec);
+    if (rc) return rc;
+  }
+  if (b->graphs.size() >= 16) {
+    cudaGraphExecDestroy(b->graphs.front().exec);
+    b->graphs.erase(b->graphs.begin());
+  }
+  b->graphs.push_back({key, exec});
+  IBM_CUDA_TRY(cudaGraphLaunch(exec, st));
+  IBM_CUDA_TRY(cudaEventRecord(b->ev_out, st));
+  IBM_CUDA_TRY(cudaStreamWaitEvent(user, b->ev_out, 0));
+  return IBM_OK;
+}
+
+}  // extern "C"

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include <mutex>
+
 #include "common.cuh"
 
 namespace ibm {
@@ -44,6 +46,19 @@ __device__ __forceinline__ bool stencil_index(int nx, int nz, int &i, int &k, in
   k = blockIdx.y * blockDim.y + threadIdx.y;
   j = blockIdx.z;
   return i < nx && k < nz;
+}
+
+// Raises a kernel's dynamic shared-memory limit to the per-block maximum,
+// once per kernel and thread-safely (plans on several host threads may make
+// the first launch concurrently).  The limit does not change occupancy; the
+// launch's actual request does.
+template <auto Kernel> cudaError_t ensure_max_smem() {
+  static std::once_flag once;
+  static cudaError_t err = cudaSuccess;
+  std::call_once(once, [] {
+    err = cudaFuncSetAttribute(Kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPlaneSmemLimit);
+  });
+  return err;
 }
 
 bool transform_size_supported(int n);

@@ -525,12 +525,9 @@ static cudaError_t launch_ss(const PencilParams &pp, cplx<T> *S, const T *lamx, 
                              cudaStream_t st) {
   using C = SsCfg<T, M, SPLIT>;
   const size_t bytes = pencil_ss_smem_bytes<T, M, SPLIT>(pp.ny);
-  static size_t attr_bytes = 0;
-  if (bytes > attr_bytes) {
-    cudaError_t e =
-        cudaFuncSetAttribute(k_pencil_ss<T, M, SPLIT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  {
+    cudaError_t e = ensure_max_smem<k_pencil_ss<T, M, SPLIT>>();
     if (e != cudaSuccess) return e;
-    attr_bytes = bytes;
   }
   const int npen = pp.nz * pp.P;
   k_pencil_ss<T, M, SPLIT><<<ceil_div(npen, C::TP) + (pp.zero_mode ? 1 : 0), 1024, bytes, st>>>(S, lamx, lamz, pp,
@@ -561,11 +558,9 @@ cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, con
   }
   constexpr int TP = PencilTile<T>::TP;
   const size_t bytes = pencil_smem_bytes<T>(pp.ny);
-  static size_t attr_bytes = 0;
-  if (bytes > attr_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_pencil<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  {
+    cudaError_t e = ensure_max_smem<k_pencil<T>>();
     if (e != cudaSuccess) return e;
-    attr_bytes = bytes;
   }
   const int npen = pp.nz * pp.P;
   k_pencil<T><<<ceil_div(npen, TP) + (pp.zero_mode ? 1 : 0), 32, bytes, st>>>(S, lamx, lamz, pp, mean_out);

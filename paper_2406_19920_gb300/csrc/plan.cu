@@ -42,7 +42,7 @@ int cuda_error(cudaError_t e, const char *what) {
 TransformGeom geom_of(const ibm_plan_s *p) {
   TransformGeom g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
-  g.use_plane = true;
+  g.use_plane = p->use_plane != 0;
   g.err = p->derr;
   g.zrhs = nullptr;
   g.zsol = nullptr;
@@ -292,6 +292,7 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   // pencil solver: serial excess-form sweep by default; IBM_PENCIL_SUBSTRUCT=1
   // selects the warp-parallel block solve (A/B timing; the tuner may pick it)
   p->pencil_mode = (getenv("IBM_PENCIL_SUBSTRUCT") && atoi(getenv("IBM_PENCIL_SUBSTRUCT")) == 1) ? 1 : 0;
+  p->use_plane = 1;
   p->esz = precision == IBM_FP64 ? 8 : 4;
   p->npts = (size_t)nx * ny * nz;
   p->nspec = (size_t)ny * nz * p->P;

@@ -32,6 +32,7 @@ struct ibm_plan_s {
   int refine;        // refinement steps (FP32 path)
   int delta;         // IBM_DELTA_*
   int pencil_mode;   // 1 substructured warp-parallel pencil solve, 0 serial sweep
+  int use_plane = 1; // 1: one-CTA-per-plane transforms where they fit; 0: split x / z passes
   size_t esz;        // element size: 4 or 8
   size_t npts;       // nx * ny * nz
   size_t nspec;      // ny * nz * P complex entries
@@ -77,4 +78,12 @@ TransformGeom geom_of(const ibm_plan_s *p);
 // out may equal in.  addend (nullable) is added to the result: out = addend + x.
 int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, void *out, const void *addend,
                cudaStream_t st, ibm_info *info);
+
+// Autotuner result for one shape (batch.cu).
+struct TuneChoice {
+  int pencil_mode, use_plane;
+  double ms;
+};
+// Times the solve variants of plan p (cached per shape), applies the fastest.
+int tune_plan(ibm_plan_s *p, TuneChoice *out);
 }  // namespace ibm

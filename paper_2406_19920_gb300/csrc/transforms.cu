@@ -382,13 +382,6 @@ template <typename T> static bool plane_supported(int nx, int nz) {
   return false;
 }
 
-template <typename T, int NX, int NZ> static cudaError_t set_plane_attr() {
-  const int bytes = (int)plane_smem_bytes<T>(NX, NZ);
-  cudaError_t e = cudaFuncSetAttribute(k_plane_fwd<T, NX, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_plane_inv<T, NX, NZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-}
-
 template <typename T>
 cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
                            const cplx<T> *twz, T in_scale, cudaStream_t st) {
@@ -398,8 +391,7 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
 #define X(a, b)                                                                     \
   if (nx == a && nz == b) {                                                         \
     if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
-      static bool attr = false;                                                     \
-      if (!attr) { cudaError_t e = set_plane_attr<T, a, b>(); if (e) return e; attr = true; } \
+      { cudaError_t e = ensure_max_smem<k_plane_fwd<T, a, b>>(); if (e) return e; } \
       k_plane_fwd<T, a, b><<<ny, kPlaneThreads, bytes, st>>>(in, S, twx, twz, in_scale, g.err, g.zrhs);  \
       return cudaGetLastError();                                                    \
     }                                                                               \
@@ -414,14 +406,7 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
     constexpr int PPC = kThreads / FftPlan<N>::G;                                          \
     const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)PPC * N);                 \
     dim3 grid(ceil_div(nz / 2, PPC), ny);                                                  \
-    static bool attr = false;                                                              \
-    if (!attr) {                                                                           \
-      cudaError_t e = cudaFuncSetAttribute(k_xfwd_rows<T, N>,                              \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                           (int)bytes);                                    \
-      if (e) return e;                                                                     \
-      attr = true;                                                                         \
-    }                                                                                      \
+    { cudaError_t e = ensure_max_smem<k_xfwd_rows<T, N>>(); if (e) return e; }                    \
     k_xfwd_rows<T, N><<<grid, kThreads, bytes, st>>>(in, S, twx, nz, in_scale);            \
     done = true;                                                                           \
   }
@@ -433,14 +418,7 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
 #define X(N)                                                                               \
   if (nz == N) {                                                                           \
     const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)N * (W + 1));              \
-    static bool attr = false;                                                              \
-    if (!attr) {                                                                           \
-      cudaError_t e = cudaFuncSetAttribute(k_zcols<T, N, false, W>,                        \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                           (int)bytes);                                    \
-      if (e) return e;                                                                     \
-      attr = true;                                                                         \
-    }                                                                                      \
+    { cudaError_t e = ensure_max_smem<k_zcols<T, N, false, W>>(); if (e) return e; }                    \
     dim3 grid(ceil_div(P, W), ny);                                                         \
     k_zcols<T, N, false, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P, g.zrhs, nullptr);            \
     done = true;                                                                           \
@@ -460,8 +438,7 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
 #define X(a, b)                                                                     \
   if (nx == a && nz == b) {                                                         \
     if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
-      static bool attr = false;                                                     \
-      if (!attr) { cudaError_t e = set_plane_attr<T, a, b>(); if (e) return e; attr = true; } \
+      { cudaError_t e = ensure_max_smem<k_plane_inv<T, a, b>>(); if (e) return e; } \
       k_plane_inv<T, a, b><<<ny, kPlaneThreads, bytes, st>>>(S, out, addend, twx, twz, scale, g.err, g.zsol); \
       return cudaGetLastError();                                                    \
     }                                                                               \
@@ -474,14 +451,7 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
 #define X(N)                                                                               \
   if (nz == N) {                                                                           \
     const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)N * (W + 1));              \
-    static bool attr = false;                                                              \
-    if (!attr) {                                                                           \
-      cudaError_t e = cudaFuncSetAttribute(k_zcols<T, N, true, W>,                         \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                           (int)bytes);                                    \
-      if (e) return e;                                                                     \
-      attr = true;                                                                         \
-    }                                                                                      \
+    { cudaError_t e = ensure_max_smem<k_zcols<T, N, true, W>>(); if (e) return e; }                    \
     dim3 grid(ceil_div(P, W), ny);                                                         \
     k_zcols<T, N, true, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P, nullptr, g.zsol);             \
     done = true;                                                                           \
@@ -495,14 +465,7 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
     constexpr int PPC = kThreads / FftPlan<N>::G;                                          \
     const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)PPC * N);                 \
     dim3 grid(ceil_div(nz / 2, PPC), ny);                                                  \
-    static bool attr = false;                                                              \
-    if (!attr) {                                                                           \
-      cudaError_t e = cudaFuncSetAttribute(k_xinv_rows<T, N>,                              \
-                                           cudaFuncAttributeMaxDynamicSharedMemorySize,    \
-                                           (int)bytes);                                    \
-      if (e) return e;                                                                     \
-      attr = true;                                                                         \
-    }                                                                                      \
+    { cudaError_t e = ensure_max_smem<k_xinv_rows<T, N>>(); if (e) return e; }                    \
     k_xinv_rows<T, N><<<grid, kThreads, bytes, st>>>(S, out, addend, twx, nz, scale);       \
     done = true;                                                                           \
   }
