@@ -68,10 +68,8 @@ static bool substructured_available(const ibm_plan_s *p) {
   return p->precision == IBM_FP32_REFINED ? n <= 256 : n <= 128;
 }
 
-static bool plane_available(const ibm_plan_s *p) {
-  TransformGeom g = geom_of(p);
-  g.use_plane = true;
-  return p->precision == IBM_FP64 ? transform_launches<double>(g) == 1 : transform_launches<float>(g) == 1;
+static int plane_candidates(const ibm_plan_s *p, int *modes) {
+  return p->precision == IBM_FP64 ? plane_modes<double>(p->nx, p->nz, modes) : plane_modes<float>(p->nx, p->nz, modes);
 }
 
 // Times the Poisson solve of plan p for every variant and applies the
@@ -108,10 +106,13 @@ int tune_plan(ibm_plan_s *p, TuneChoice *out) {
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
-  TuneChoice best{0, 1, 1e30};
+  TuneChoice best{0, p->use_plane, 1e30};
+  int modes[8];
+  const int nmodes = plane_candidates(p, modes);
   int rc = IBM_OK;
   for (int pm = 0; pm <= (substructured_available(p) ? 1 : 0) && rc == IBM_OK; ++pm) {
-    for (int up = plane_available(p) ? 1 : 0; up >= 0 && rc == IBM_OK; --up) {
+    for (int m = 0; m < nmodes && rc == IBM_OK; ++m) {
+      const int up = modes[m];
       p->pencil_mode = pm;
       p->use_plane = up;
       for (int w = 0; w < 2 && rc == IBM_OK; ++w) rc = plan_solve(p, 0, 0.0, 0, a, b, nullptr, 0, nullptr);
@@ -124,7 +125,6 @@ int tune_plan(ibm_plan_s *p, TuneChoice *out) {
       cudaEventElapsedTime(&ms, e0, e1);
       ms /= reps;
       if (rc == IBM_OK && ms < best.ms) best = {pm, up, ms};
-      if (!up) break;
     }
   }
   cudaEventDestroy(e0);

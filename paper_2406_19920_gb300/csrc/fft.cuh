@@ -158,4 +158,71 @@ __device__ __forceinline__ void load_twiddles(cplx<T> *dst, const cplx<T> *src, 
   for (int i = threadIdx.x; i < n; i += blockDim.x) dst[i] = src[i];
 }
 
+// ---------------------------------------------------------------------------
+// real row pairs: rows a, b are transformed together as z = a + i b
+// ---------------------------------------------------------------------------
+
+// After fft_row on z = a + i b (row[0..N)), write the half spectra:
+// A to dstA[k*ds], B to dstB[k*ds], k = 0..N/2.  Reads everything first.
+template <typename T, int N>
+__device__ __forceinline__ void split_pair(cplx<T> *row, cplx<T> *dstA, cplx<T> *dstB, int ds, int lg,
+                                           unsigned mask) {
+  constexpr int G = FftPlan<N>::G;
+  constexpr int H = N / 2 + 1;
+  constexpr int KT = (H + G - 1) / G;
+  cplx<T> A[KT], B[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      const cplx<T> zk = row[k];
+      const cplx<T> zn = row[(N - k) % N];
+      A[t] = mk<T>((T)0.5 * (zk.x + zn.x), (T)0.5 * (zk.y - zn.y));
+      // D = zk - conj(zn); B = -i D / 2
+      B[t] = mk<T>((T)0.5 * (zk.y + zn.y), (T)-0.5 * (zk.x - zn.x));
+    }
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      dstA[k * ds] = A[t];
+      dstB[k * ds] = B[t];
+    }
+  }
+  __syncwarp(mask);
+}
+
+// Build Z_k = A_k + i B_k (k = 0..N-1, Hermitian extension) into row[0..N).
+// A at srcA[k*ss], B at srcB[k*ss]; the imaginary parts of the k = 0 and
+// k = N/2 bins are dropped as a real inverse transform does.
+template <typename T, int N>
+__device__ __forceinline__ void merge_pair(const cplx<T> *srcA, const cplx<T> *srcB, int ss, cplx<T> *row,
+                                           int lg, unsigned mask) {
+  constexpr int G = FftPlan<N>::G;
+  constexpr int H = N / 2 + 1;
+  constexpr int KT = (H + G - 1) / G;
+  cplx<T> A[KT], B[KT];
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      A[t] = srcA[k * ss];
+      B[t] = srcB[k * ss];
+      if (k == 0 || k == N / 2) { A[t].y = 0; B[t].y = 0; }
+    }
+  }
+  __syncwarp(mask);
+#pragma unroll
+  for (int t = 0; t < KT; ++t) {
+    const int k = lg + G * t;
+    if (k < H) {
+      row[k] = mk<T>(A[t].x - B[t].y, A[t].y + B[t].x);
+      if (k > 0 && k < N / 2) row[N - k] = mk<T>(A[t].x + B[t].y, B[t].x - A[t].y);
+    }
+  }
+  __syncwarp(mask);
+}
+
 }  // namespace ibm

@@ -16,7 +16,7 @@ constexpr size_t kPlaneSmemLimit = 227 * 1024;
 
 struct TransformGeom {
   int nx, ny, nz;
-  bool use_plane;  // allow the one-CTA-per-plane kernels
+  int use_plane;   // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane
   int *err;        // device error word for bounded waits
   double *zrhs;    // forward: if set, receives Re S[j][0][0] of every plane (the zero pencil)
   const double *zsol;  // inverse: if set, replaces S[j][0][0] by (zsol[j], 0) before transforming
@@ -62,6 +62,10 @@ template <auto Kernel> cudaError_t ensure_max_smem() {
 }
 
 bool transform_size_supported(int n);
+// Plane modes (0, 1, 2, 4, 8) that can run an nx x nz plane, smallest first; returns the count.
+template <typename T> int plane_modes(int nx, int nz, int *modes);
+// Plane mode used when no tuning result is known.
+template <typename T> int default_plane_mode(int nx, int ny, int nz);
 // Kernels one forward (or inverse) transform launches: 1 on the plane path, 2 otherwise.
 template <typename T> int transform_launches(const TransformGeom &g);
 
@@ -73,6 +77,17 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
 template <typename T>
 cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
                            const cplx<T> *twz, T scale, cudaStream_t st);
+
+// Cluster plane kernels (C CTAs per y-plane, rows and columns exchanged
+// through distributed shared memory); cudaErrorNotSupported for shapes
+// without an instantiation.
+template <typename T> bool cplane_supported(int nx, int nz, int C);
+template <typename T>
+cudaError_t launch_cplane_forward(const TransformGeom &g, int C, const T *in, cplx<T> *S, const cplx<T> *twx,
+                                  const cplx<T> *twz, T in_scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_cplane_inverse(const TransformGeom &g, int C, const cplx<T> *S, T *out, const T *addend,
+                                  const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st);
 
 // Pencil solve along y (Thomas, excess form), in place on the spectrum.
 struct PencilParams {

@@ -42,7 +42,7 @@ int cuda_error(cudaError_t e, const char *what) {
 TransformGeom geom_of(const ibm_plan_s *p) {
   TransformGeom g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
-  g.use_plane = p->use_plane != 0;
+  g.use_plane = p->use_plane;
   g.err = p->derr;
   g.zrhs = nullptr;
   g.zsol = nullptr;
@@ -292,7 +292,23 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   // pencil solver: serial excess-form sweep by default; IBM_PENCIL_SUBSTRUCT=1
   // selects the warp-parallel block solve (A/B timing; the tuner may pick it)
   p->pencil_mode = (getenv("IBM_PENCIL_SUBSTRUCT") && atoi(getenv("IBM_PENCIL_SUBSTRUCT")) == 1) ? 1 : 0;
-  p->use_plane = 1;
+  // plane transforms: the default mode for the shape; IBM_PLANE_MODE=m forces
+  // mode m (0 split passes, 1 one CTA per plane, 2/4/8 cluster) and fails
+  // the plan when the shape has no such mode (A/B timing and tests)
+  p->use_plane = precision == IBM_FP64 ? default_plane_mode<double>(nx, ny, nz) : default_plane_mode<float>(nx, ny, nz);
+  if (const char *pm = getenv("IBM_PLANE_MODE")) {
+    int modes[8];
+    const int n = precision == IBM_FP64 ? plane_modes<double>(nx, nz, modes) : plane_modes<float>(nx, nz, modes);
+    const int want = atoi(pm);
+    bool found = false;
+    for (int i = 0; i < n; ++i) found |= modes[i] == want;
+    if (!found) {
+      delete p;
+      return set_error(IBM_ERR_UNSUPPORTED, "ibm_plan_create: IBM_PLANE_MODE=%d not available for %dx%d planes", want,
+                       nx, nz);
+    }
+    p->use_plane = want;
+  }
   p->esz = precision == IBM_FP64 ? 8 : 4;
   p->npts = (size_t)nx * ny * nz;
   p->nspec = (size_t)ny * nz * p->P;

@@ -27,73 +27,6 @@ namespace ibm {
 constexpr int kThreads = 256;
 
 // --------------------------------------------------------------------------
-// row-pair helpers
-// --------------------------------------------------------------------------
-
-// After fft_row on z = a + i b (row[0..N)), write the half spectra:
-// A to dstA[k*ds], B to dstB[k*ds], k = 0..N/2.  Reads everything first.
-template <typename T, int N>
-__device__ __forceinline__ void split_pair(cplx<T> *row, cplx<T> *dstA, cplx<T> *dstB, int ds, int lg,
-                                           unsigned mask) {
-  constexpr int G = FftPlan<N>::G;
-  constexpr int H = N / 2 + 1;
-  constexpr int KT = (H + G - 1) / G;
-  cplx<T> A[KT], B[KT];
-#pragma unroll
-  for (int t = 0; t < KT; ++t) {
-    const int k = lg + G * t;
-    if (k < H) {
-      const cplx<T> zk = row[k];
-      const cplx<T> zn = row[(N - k) % N];
-      A[t] = mk<T>((T)0.5 * (zk.x + zn.x), (T)0.5 * (zk.y - zn.y));
-      // D = zk - conj(zn); B = -i D / 2
-      B[t] = mk<T>((T)0.5 * (zk.y + zn.y), (T)-0.5 * (zk.x - zn.x));
-    }
-  }
-  __syncwarp(mask);
-#pragma unroll
-  for (int t = 0; t < KT; ++t) {
-    const int k = lg + G * t;
-    if (k < H) {
-      dstA[k * ds] = A[t];
-      dstB[k * ds] = B[t];
-    }
-  }
-  __syncwarp(mask);
-}
-
-// Build Z_k = A_k + i B_k (k = 0..N-1, Hermitian extension) into row[0..N).
-// A at srcA[k*ss], B at srcB[k*ss]; the imaginary parts of the k = 0 and
-// k = N/2 bins are dropped as a real inverse transform does.
-template <typename T, int N>
-__device__ __forceinline__ void merge_pair(const cplx<T> *srcA, const cplx<T> *srcB, int ss, cplx<T> *row,
-                                           int lg, unsigned mask) {
-  constexpr int G = FftPlan<N>::G;
-  constexpr int H = N / 2 + 1;
-  constexpr int KT = (H + G - 1) / G;
-  cplx<T> A[KT], B[KT];
-#pragma unroll
-  for (int t = 0; t < KT; ++t) {
-    const int k = lg + G * t;
-    if (k < H) {
-      A[t] = srcA[k * ss];
-      B[t] = srcB[k * ss];
-      if (k == 0 || k == N / 2) { A[t].y = 0; B[t].y = 0; }
-    }
-  }
-  __syncwarp(mask);
-#pragma unroll
-  for (int t = 0; t < KT; ++t) {
-    const int k = lg + G * t;
-    if (k < H) {
-      row[k] = mk<T>(A[t].x - B[t].y, A[t].y + B[t].x);
-      if (k > 0 && k < N / 2) row[N - k] = mk<T>(A[t].x + B[t].y, B[t].x - A[t].y);
-    }
-  }
-  __syncwarp(mask);
-}
-
-// --------------------------------------------------------------------------
 // plane kernels: one CTA per y-plane, the plane moved by bulk async copies
 // --------------------------------------------------------------------------
 constexpr int kPlaneThreads = 512;
@@ -386,7 +319,9 @@ template <typename T>
 cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
                            const cplx<T> *twz, T in_scale, cudaStream_t st) {
   const int nx = g.nx, ny = g.ny, nz = g.nz, P = nx / 2 + 1;
-  if (g.use_plane && plane_supported<T>(nx, nz)) {
+  if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
+    return launch_cplane_forward<T>(g, g.use_plane, in, S, twx, twz, in_scale, st);
+  if (g.use_plane == 1 && plane_supported<T>(nx, nz)) {
     const size_t bytes = plane_smem_bytes<T>(nx, nz);
 #define X(a, b)                                                                     \
   if (nx == a && nz == b) {                                                         \
@@ -433,7 +368,9 @@ template <typename T>
 cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
                            const cplx<T> *twz, T scale, cudaStream_t st) {
   const int nx = g.nx, ny = g.ny, nz = g.nz, P = nx / 2 + 1;
-  if (g.use_plane && plane_supported<T>(nx, nz)) {
+  if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
+    return launch_cplane_inverse<T>(g, g.use_plane, S, out, addend, twx, twz, scale, st);
+  if (g.use_plane == 1 && plane_supported<T>(nx, nz)) {
     const size_t bytes = plane_smem_bytes<T>(nx, nz);
 #define X(a, b)                                                                     \
   if (nx == a && nz == b) {                                                         \
@@ -485,10 +422,34 @@ template cudaError_t launch_inverse<double>(const TransformGeom &, double2 *, do
                                             const double2 *, const double2 *, double, cudaStream_t);
 
 template <typename T> int transform_launches(const TransformGeom &g) {
-  return (g.use_plane && plane_supported<T>(g.nx, g.nz)) ? 1 : 2;
+  if (g.use_plane >= 2) return cplane_supported<T>(g.nx, g.nz, g.use_plane) ? 1 : 2;
+  return (g.use_plane == 1 && plane_supported<T>(g.nx, g.nz)) ? 1 : 2;
 }
 template int transform_launches<float>(const TransformGeom &);
 template int transform_launches<double>(const TransformGeom &);
+
+template <typename T> int plane_modes(int nx, int nz, int *modes) {
+  int n = 0;
+  modes[n++] = 0;
+  if (plane_supported<T>(nx, nz)) modes[n++] = 1;
+  for (int c = 2; c <= 8; c *= 2)
+    if (cplane_supported<T>(nx, nz, c)) modes[n++] = c;
+  return n;
+}
+template int plane_modes<float>(int, int, int *);
+template int plane_modes<double>(int, int, int *);
+
+template <typename T> int default_plane_mode(int nx, int ny, int nz) {
+  // Measured on GB300 (FP32 and FP64, 128^3 to 384x256x256): the one-CTA
+  // plane kernels beat the split passes where they fit, and the cluster
+  // kernels lose to both (their row/column exchange through distributed
+  // shared memory costs more than the L2 round trip of the split passes).
+  // Clusters stay available to the tuner and to IBM_PLANE_MODE.
+  (void)ny;
+  return plane_supported<T>(nx, nz) ? 1 : 0;
+}
+template int default_plane_mode<float>(int, int, int);
+template int default_plane_mode<double>(int, int, int);
 
 bool transform_size_supported(int n) {
 #define X(N) if (n == N) return true;

@@ -8,6 +8,7 @@ pencil tiles and the smallest supported grid.
 """
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -130,6 +131,60 @@ def test_helmholtz_matches_oracle(shape, bc, c):
                 assert np.all(got[0] == 0.0)
         finally:
             ibm.ibm_plan_destroy(plan)
+
+
+# Planes with a cluster transform (C CTAs per plane exchanging rows and
+# columns through distributed shared memory), each solved in every plane
+# mode the shape has: 0 split x/z passes, 1 one CTA per plane, 2/4/8 cluster.
+PLANE_MODE_SHAPES = [
+    (64, 10, 64), (96, 9, 96), (128, 12, 128), (192, 8, 192), (256, 9, 256),
+    (384, 8, 256), (256, 8, 128), (128, 8, 256), (384, 8, 384), (512, 8, 256),
+]
+
+
+def _plan_in_mode(nx, ny, nz, g, prec, refine, mode):
+    os.environ["IBM_PLANE_MODE"] = str(mode)
+    try:
+        return ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, refine)
+    except ibm.IbmError as e:
+        assert e.code == ibm.IBM_ERR_UNSUPPORTED
+        return None
+    finally:
+        del os.environ["IBM_PLANE_MODE"]
+
+
+@pytest.mark.parametrize("shape", PLANE_MODE_SHAPES)
+def test_every_plane_mode_matches_oracle(shape):
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    b = synth.white_noise(nx, ny, nz, workload=13, stream=0) + 0.2
+    b32 = b.astype(np.float32).astype(np.float64)
+    ref64, _ = O.poisson_solve(b, g)
+    ref32, _ = O.poisson_solve(b32, g)
+    href = O.helmholtz_solve(b32, g, 0.01, ibm.IBM_FIELD_CELL_DIRICHLET)
+    ran = set()
+    for mode in (0, 1, 2, 4, 8):
+        for prec, dt, tol, bb, ref in ((ibm.IBM_FP64, torch.float64, TOL_FP64, b, ref64),
+                                       (ibm.IBM_FP32_REFINED, torch.float32, TOL_FP32, b32, ref32)):
+            plan = _plan_in_mode(nx, ny, nz, g, prec, 1, mode)
+            if plan is None:
+                continue
+            ran.add(mode)
+            try:
+                rhs = dev(bb, dt)
+                phi = torch.empty_like(rhs)
+                ibm.ibm_poisson_solve(plan, rhs, phi)
+                torch.cuda.synchronize()
+                assert rel_l2(host(phi), ref) <= tol, (mode, prec, rel_l2(host(phi), ref))
+                if prec == ibm.IBM_FP32_REFINED:
+                    u = torch.empty_like(rhs)
+                    ibm.ibm_helmholtz_solve(plan, 0.01, ibm.IBM_FIELD_CELL_DIRICHLET, rhs, u)
+                    torch.cuda.synchronize()
+                    assert rel_l2(host(u), href) <= tol, (mode, rel_l2(host(u), href))
+                ibm.ibm_plan_check(plan)
+            finally:
+                ibm.ibm_plan_destroy(plan)
+    assert 0 in ran and any(m >= 2 for m in ran), ran
 
 
 def test_invalid_arguments_rejected_before_launch():
