@@ -78,6 +78,14 @@ template <typename T>
 cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
                            const cplx<T> *twz, T scale, cudaStream_t st);
 
+// Split passes: x rows then z columns (forward), z columns then x rows (inverse).
+template <typename T>
+cudaError_t launch_axis_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
+                                const cplx<T> *twz, T in_scale, cudaStream_t st);
+template <typename T>
+cudaError_t launch_axis_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
+                                const cplx<T> *twz, T scale, cudaStream_t st);
+
 // Cluster plane kernels (C CTAs per y-plane, rows and columns exchanged
 // through distributed shared memory); cudaErrorNotSupported for shapes
 // without an instantiation.

@@ -11,305 +11,163 @@
 // B_k = -i (Z_k - conj Z_{N-k})/2 for k = 0..nx/2.  The inverse rebuilds
 // Z_k = A_k + i B_k from the two Hermitian half spectra.
 //
-// Two kernel families:
-//   plane kernels  one CTA per y-plane, the whole plane staged in shared
-//                  memory: x-FFT of every row pair, then z-FFT of every
-//                  column, then one coalesced store (one HBM read + one write
-//                  per direction);
-//   axis kernels   for planes larger than shared memory: x-rows and
-//                  z-columns in separate passes.
-#include "fft.cuh"
+// Three kernel families, chosen per plan by its plane mode:
+//   plane kernels   (mode 1, here) one CTA per y-plane: the x transform of
+//                   every row pair lands in a shared-memory plane, the z
+//                   transform of every column leaves it; one HBM read and
+//                   one write per direction;
+//   axis kernels    (mode 0, axis.cu) x-rows and z-columns in two passes;
+//   cluster kernels (modes 2, 4, 8, cplane.cu) C CTAs per plane.
+// Plane and axis kernels run the two-step register transform of fft2.cuh.
+#include "fft2.cuh"
 #include "internal.h"
-#include "tma.cuh"
 
 namespace ibm {
 
-constexpr int kThreads = 256;
-
 // --------------------------------------------------------------------------
-// plane kernels: one CTA per y-plane, the plane moved by bulk async copies
+// plane kernels: one CTA per y-plane
 // --------------------------------------------------------------------------
 constexpr int kPlaneThreads = 512;
 
-// shared-memory layout of a plane kernel (bytes from the dynamic base):
-//   [0, 16)            mbarrier
-//   staging            NZ*NX reals (forward input / inverse addend)
-//   twx, twz           NX + NZ complex twiddles
-//   plane              NZ rows of P = NX/2+1 complex (NZ/2 pairs of NX+2)
-template <typename T, int NX, int NZ> struct PlaneLayout {
+// Shared memory (complex entries): tw2x [NX], tw2z [NZ], the spectrum plane
+// [NZ][P], and one exchange buffer reused by the x chunks (CP row pairs,
+// [CP][N1x][N2x+1]) and the z chunks (CW columns, [N1z][N2z][CW]); chunk
+// sizes fill what the plane leaves of the 227 KB.
+template <typename T, int NX, int NZ> struct PlaneCfg {
+  using C = cplx<T>;
   static constexpr int P = NX / 2 + 1;
-  static constexpr size_t staging = 16;
-  static constexpr size_t tw = staging + sizeof(T) * (size_t)NZ * NX;
-  static constexpr size_t plane = tw + sizeof(cplx<T>) * (size_t)(NX + NZ);
-  static constexpr size_t bytes = plane + sizeof(cplx<T>) * (size_t)NZ * P;
-  static_assert(tw % 16 == 0 && plane % 16 == 0, "16-byte aligned regions");
+  static constexpr int N1X = TwoStep<NX>::N1, N2X = TwoStep<NX>::N2, XPITCH = N2X + 1;
+  static constexpr size_t fixed = sizeof(C) * ((size_t)NX + NZ + (size_t)NZ * P);
+  static constexpr size_t room = fixed < kPlaneSmemLimit ? kPlaneSmemLimit - fixed : 0;
+  static constexpr size_t pair_bytes = sizeof(C) * N1X * XPITCH;
+  static constexpr size_t col_bytes = sizeof(C) * NZ;
+  static constexpr int CP0 = (int)(room / pair_bytes), CW0 = (int)(room / col_bytes);
+  static constexpr int CP = CP0 < NZ / 2 ? CP0 : NZ / 2;
+  static constexpr int CW = CW0 < P ? CW0 : P;
+  static constexpr bool ok = CP >= (NZ / 2 < 8 ? NZ / 2 : 8) && CW >= (P < 8 ? P : 8);
+  static constexpr size_t xbytes = (size_t)CP * pair_bytes > (size_t)CW * col_bytes ? (size_t)CP * pair_bytes
+                                                                                    : (size_t)CW * col_bytes;
+  static constexpr size_t bytes = fixed + xbytes;
 };
 
 template <typename T, int NX, int NZ>
 __global__ void __launch_bounds__(kPlaneThreads)
-k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx_g,
-            const cplx<T> *__restrict__ twz_g, T in_scale, int *err, double *zrhs) {
-  using L = PlaneLayout<T, NX, NZ>;
-  constexpr int P = L::P;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-  T *real = reinterpret_cast<T *>(smem_raw + L::staging);
-  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw + L::tw);
-  cplx<T> *twz = twx + NX;
-  cplx<T> *plane = reinterpret_cast<cplx<T> *>(smem_raw + L::plane);
+k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx,
+            const cplx<T> *__restrict__ twz, T in_scale, double *zrhs) {
+  using Cfg = PlaneCfg<T, NX, NZ>;
+  constexpr int P = Cfg::P, N1X = Cfg::N1X, XPITCH = Cfg::XPITCH, CP = Cfg::CP, CW = Cfg::CW;
+  constexpr int N1Z = TwoStep<NZ>::N1, N2Z = TwoStep<NZ>::N2, J3 = Cfg::N2X / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cplx<T> *tw2x = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *tw2z = tw2x + NX;
+  cplx<T> *plane = tw2z + NZ;  // [NZ][P]
+  cplx<T> *X = plane + NZ * P;
   const int j = blockIdx.x;
   const int tid = threadIdx.x;
-  constexpr uint32_t kInBytes = sizeof(T) * NZ * NX;
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
+  load_step_twiddles<T, NX>(tw2x, twx);
+  load_step_twiddles<T, NZ>(tw2z, twz);
   __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(bar, kInBytes);
-    bulk_g2s(real, in + (size_t)j * NZ * NX, kInBytes, bar);
-  }
-  load_twiddles<T>(twx, twx_g, NX);
-  load_twiddles<T>(twz, twz_g, NZ);
-  if (!__syncthreads_and(mbar_wait(bar, 0, err))) return;
-  {  // x: complex FFT of each row pair z = a + i b, then split into two half spectra
-    constexpr int G = FftPlan<NX>::G;
-    constexpr int NG = kPlaneThreads / G;
-    const int gid = tid / G, lg = tid % G;
-    for (int base = 0; base < NZ / 2; base += NG) {
-      const int p = base + gid;
-      const unsigned mask = __ballot_sync(0xffffffffu, p < NZ / 2);
-      if (p >= NZ / 2) continue;
-      cplx<T> *row = plane + p * (NX + 2);
-      const T *ra = real + (2 * p) * NX;
-      for (int n = lg; n < NX; n += G) row[n] = mk<T>(ra[n] * in_scale, ra[NX + n] * in_scale);
-      __syncwarp(mask);
-      fft_row<T, NX, false>(row, 1, twx, lg, mask);
-      split_pair<T, NX>(row, row, row + P, 1, lg, mask);
+  const T *src = in + (size_t)j * NZ * NX;
+  for (int p0 = 0; p0 < NZ / 2; p0 += CP) {
+    const int np = min(CP, NZ / 2 - p0);
+    for (int job = tid; job < np * N1X; job += kPlaneThreads) {
+      const int p = job / N1X, n1 = job - p * N1X;
+      rfwd_step1<T, NX>(src + (size_t)(p0 + p) * 2 * NX, in_scale, n1, tw2x, X + (p * N1X + n1) * XPITCH);
     }
-  }
-  __syncthreads();
-  {  // z: complex FFT of each of the P columns (stride P)
-    constexpr int G = FftPlan<NZ>::G;
-    constexpr int NG = kPlaneThreads / G;
-    const int gid = tid / G, lg = tid % G;
-    for (int base = 0; base < P; base += NG) {
-      const int c = base + gid;
-      const unsigned mask = __ballot_sync(0xffffffffu, c < P);
-      if (c >= P) continue;
-      fft_row<T, NZ, false>(plane + c, P, twz, lg, mask);
+    __syncthreads();
+    for (int job = tid; job < np * J3; job += kPlaneThreads) {
+      const int p = job / J3, q = job - p * J3;
+      cplx<T> *dA = plane + (p0 + p) * 2 * P;
+      rfwd_step3<T, NX, XPITCH>(X + p * N1X * XPITCH, q, dA, dA + P);
     }
-  }
-  fence_proxy_async();
-  __syncthreads();
-  if (tid == 0) {
-    if (zrhs) zrhs[j] = (double)plane[0].x;
-    bulk_s2g(S + (size_t)j * NZ * P, plane, (uint32_t)(sizeof(cplx<T>) * NZ * P));
-    bulk_commit();
-    bulk_wait_read();
-  }
-}
-
-// Inverse: spectrum plane -> real plane, out = addend + scale * result.
-template <typename T, int NX, int NZ>
-__global__ void __launch_bounds__(kPlaneThreads)
-k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx_g,
-            const cplx<T> *__restrict__ twz_g, T scale, int *err, const double *zsol) {
-  using L = PlaneLayout<T, NX, NZ>;
-  constexpr int P = L::P;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-  T *addb = reinterpret_cast<T *>(smem_raw + L::staging);
-  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw + L::tw);
-  cplx<T> *twz = twx + NX;
-  cplx<T> *plane = reinterpret_cast<cplx<T> *>(smem_raw + L::plane);
-  const int j = blockIdx.x;
-  const int tid = threadIdx.x;
-  constexpr uint32_t kSpecBytes = sizeof(cplx<T>) * NZ * P;
-  constexpr uint32_t kAddBytes = sizeof(T) * NZ * NX;
-  if (tid == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncthreads();
-  if (tid == 0) {
-    mbar_arrive_expect_tx(bar, kSpecBytes + (addend ? kAddBytes : 0u));
-    bulk_g2s(plane, S + (size_t)j * NZ * P, kSpecBytes, bar);
-    if (addend) bulk_g2s(addb, addend + (size_t)j * NZ * NX, kAddBytes, bar);
-  }
-  load_twiddles<T>(twx, twx_g, NX);
-  load_twiddles<T>(twz, twz_g, NZ);
-  if (!__syncthreads_and(mbar_wait(bar, 0, err))) return;
-  if (zsol) {
-    if (tid == 0) plane[0] = mk<T>((T)zsol[j], (T)0);
     __syncthreads();
   }
-  {
-    constexpr int G = FftPlan<NZ>::G;
-    constexpr int NG = kPlaneThreads / G;
-    const int gid = tid / G, lg = tid % G;
-    for (int base = 0; base < P; base += NG) {
-      const int c = base + gid;
-      const unsigned mask = __ballot_sync(0xffffffffu, c < P);
-      if (c >= P) continue;
-      fft_row<T, NZ, true>(plane + c, P, twz, lg, mask);
+  cplx<T> *dst = S + (size_t)j * NZ * P;
+  for (int c0 = 0; c0 < P; c0 += CW) {
+    const int nc = min(CW, P - c0);
+    for (int job = tid; job < CW * N1Z; job += kPlaneThreads) {
+      const int n1 = job / CW, c = job - n1 * CW;
+      if (c < nc)
+        col_step1<T, NZ, false, CW>(plane + c0 + c, P, n1, tw2z, X + n1 * N2Z * CW + c, false, mk<T>((T)0, (T)0));
     }
-  }
-  __syncthreads();
-  {
-    constexpr int G = FftPlan<NX>::G;
-    constexpr int NG = kPlaneThreads / G;
-    const int gid = tid / G, lg = tid % G;
-    T *dst = out + (size_t)j * NZ * NX;
-    for (int base = 0; base < NZ / 2; base += NG) {
-      const int p = base + gid;
-      const unsigned mask = __ballot_sync(0xffffffffu, p < NZ / 2);
-      if (p >= NZ / 2) continue;
-      cplx<T> *row = plane + p * (NX + 2);
-      merge_pair<T, NX>(row, row + P, 1, row, lg, mask);
-      fft_row<T, NX, true>(row, 1, twx, lg, mask);
-      T *d0 = dst + (size_t)(2 * p) * NX;
-      const T *a0 = addb + (2 * p) * NX;
-      for (int n = lg; n < NX; n += G) {
-        const cplx<T> z = row[n];
-        T v0 = z.x * scale, v1 = z.y * scale;
-        if (addend) { v0 += a0[n]; v1 += a0[NX + n]; }
-        d0[n] = v0;
-        d0[NX + n] = v1;
+    __syncthreads();
+    for (int job = tid; job < CW * N2Z; job += kPlaneThreads) {
+      const int k2 = job / CW, c = job - k2 * CW;
+      if (c < nc) {
+        const cplx<T> u0 = col_step3<T, NZ, false, CW>(X, c, k2, dst + c0 + c, P);
+        if (zrhs && c0 + c == 0 && k2 == 0) zrhs[j] = (double)u0.x;
       }
     }
+    __syncthreads();
   }
 }
 
-// --------------------------------------------------------------------------
-// axis kernels (planes larger than shared memory)
-// --------------------------------------------------------------------------
-
-// x forward: a CTA takes PPC row pairs of one plane.  grid (ceil(NZ/2/PPC), ny)
-template <typename T, int NX>
-__global__ void __launch_bounds__(kThreads)
-k_xfwd_rows(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx_g, int nz,
-            T in_scale) {
-  constexpr int P = NX / 2 + 1;
-  constexpr int G = FftPlan<NX>::G;
-  constexpr int PPC = kThreads / G;  // pairs per CTA
+// Inverse: spectrum plane -> out = addend + scale * result.
+template <typename T, int NX, int NZ>
+__global__ void __launch_bounds__(kPlaneThreads)
+k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx,
+            const cplx<T> *__restrict__ twz, T scale, const double *zsol) {
+  using Cfg = PlaneCfg<T, NX, NZ>;
+  constexpr int P = Cfg::P, N1X = Cfg::N1X, N2X = Cfg::N2X, XPITCH = Cfg::XPITCH, CP = Cfg::CP, CW = Cfg::CW;
+  constexpr int N1Z = TwoStep<NZ>::N1, N2Z = TwoStep<NZ>::N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
-  cplx<T> *buf = twx + NX;  // PPC rows of NX
-  const int j = blockIdx.y;
-  const int p0 = blockIdx.x * PPC;
-  const int np = min(PPC, nz / 2 - p0);
+  cplx<T> *tw2x = reinterpret_cast<cplx<T> *>(smem_raw);
+  cplx<T> *tw2z = tw2x + NX;
+  cplx<T> *plane = tw2z + NZ;
+  cplx<T> *X = plane + NZ * P;
+  const int j = blockIdx.x;
   const int tid = threadIdx.x;
-  load_twiddles<T>(twx, twx_g, NX);
-  {
-    const T *src = in + ((size_t)j * nz + 2 * p0) * NX;
-    T *bf = reinterpret_cast<T *>(buf);
-    for (int idx = tid; idx < np * 2 * NX; idx += kThreads) {
-      const int k = idx / NX, n = idx - k * NX;
-      bf[((k >> 1) * NX + n) * 2 + (k & 1)] = src[idx] * in_scale;
+  load_step_twiddles<T, NX>(tw2x, twx);
+  load_step_twiddles<T, NZ>(tw2z, twz);
+  __syncthreads();
+  const cplx<T> *src = S + (size_t)j * NZ * P;
+  const cplx<T> z0 = zsol ? mk<T>((T)zsol[j], (T)0) : mk<T>((T)0, (T)0);
+  for (int c0 = 0; c0 < P; c0 += CW) {
+    const int nc = min(CW, P - c0);
+    for (int job = tid; job < CW * N1Z; job += kPlaneThreads) {
+      const int n1 = job / CW, c = job - n1 * CW;
+      if (c < nc)
+        col_step1<T, NZ, true, CW>(src + c0 + c, P, n1, tw2z, X + n1 * N2Z * CW + c, zsol && c0 + c == 0, z0);
     }
+    __syncthreads();
+    for (int job = tid; job < CW * N2Z; job += kPlaneThreads) {
+      const int k2 = job / CW, c = job - k2 * CW;
+      if (c < nc) col_step3<T, NZ, true, CW>(X, c, k2, plane + c0 + c, P);
+    }
+    __syncthreads();
   }
-  __syncthreads();
-  const int gid = tid / G, lg = tid % G;
-  const unsigned mask = __ballot_sync(0xffffffffu, gid < np);
-  if (gid >= np) return;
-  cplx<T> *row = buf + gid * NX;
-  fft_row<T, NX, false>(row, 1, twx, lg, mask);
-  cplx<T> *dA = S + ((size_t)j * nz + 2 * (p0 + gid)) * P;
-  split_pair<T, NX>(row, dA, dA + P, 1, lg, mask);
-}
-
-// x inverse.  out = addend + scale * result
-template <typename T, int NX>
-__global__ void __launch_bounds__(kThreads)
-k_xinv_rows(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx_g,
-            int nz, T scale) {
-  constexpr int P = NX / 2 + 1;
-  constexpr int G = FftPlan<NX>::G;
-  constexpr int PPC = kThreads / G;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T> *twx = reinterpret_cast<cplx<T> *>(smem_raw);
-  cplx<T> *buf = twx + NX;
-  const int j = blockIdx.y;
-  const int p0 = blockIdx.x * PPC;
-  const int np = min(PPC, nz / 2 - p0);
-  const int tid = threadIdx.x;
-  load_twiddles<T>(twx, twx_g, NX);
-  __syncthreads();
-  const int gid = tid / G, lg = tid % G;
-  const unsigned mask = __ballot_sync(0xffffffffu, gid < np);
-  if (gid >= np) return;
-  const int p = p0 + gid;
-  cplx<T> *row = buf + gid * NX;
-  const cplx<T> *sA = S + ((size_t)j * nz + 2 * p) * P;
-  merge_pair<T, NX>(sA, sA + P, 1, row, lg, mask);
-  fft_row<T, NX, true>(row, 1, twx, lg, mask);
-  T *d0 = out + ((size_t)j * nz + 2 * p) * NX;
-  const T *a0 = addend ? addend + ((size_t)j * nz + 2 * p) * NX : nullptr;
-  for (int n = lg; n < NX; n += G) {
-    const cplx<T> z = row[n];
-    T v0 = z.x * scale, v1 = z.y * scale;
-    if (a0) { v0 += a0[n]; v1 += a0[NX + n]; }
-    d0[n] = v0;
-    d0[NX + n] = v1;
-  }
-}
-
-// z columns, in place: a CTA takes W consecutive kx columns of one plane.
-// grid (ceil(P / W), ny), block W * G lanes.
-template <typename T, int NZ, bool INV, int W>
-__global__ void __launch_bounds__(1024)
-k_zcols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twz_g, int P, double *zrhs, const double *zsol) {
-  constexpr int G = FftPlan<NZ>::G;
-  constexpr int PITCH = W + 1;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cplx<T> *twz = reinterpret_cast<cplx<T> *>(smem_raw);
-  cplx<T> *tile = twz + NZ;  // [NZ][PITCH]
-  const int j = blockIdx.y;
-  const int c0 = blockIdx.x * W;
-  const int nc = min(W, P - c0);
-  const int tid = threadIdx.x;
-  const int nthr = W * G;
-  load_twiddles<T>(twz, twz_g, NZ);
-  cplx<T> *base = S + (size_t)j * NZ * P + c0;
-  for (int idx = tid; idx < NZ * W; idx += nthr) {
-    const int k = idx / W, c = idx - k * W;
-    if (c < nc) tile[k * PITCH + c] = base[(size_t)k * P + c];
-  }
-  __syncthreads();
-  if (INV && zsol && c0 == 0 && tid == 0) tile[0] = mk<T>((T)zsol[j], (T)0);
-  __syncthreads();
-  {
-    const int gid = tid / G, lg = tid % G;
-    const unsigned mask = __ballot_sync(warp_full_mask(), gid < nc);
-    if (gid < nc) fft_row<T, NZ, INV>(tile + gid, PITCH, twz, lg, mask);
-  }
-  __syncthreads();
-  if (!INV && zrhs && c0 == 0 && tid == 0) zrhs[j] = (double)tile[0].x;
-  for (int idx = tid; idx < NZ * W; idx += nthr) {
-    const int k = idx / W, c = idx - k * W;
-    if (c < nc) base[(size_t)k * P + c] = tile[k * PITCH + c];
+  T *dst = out + (size_t)j * NZ * NX;
+  const T *add = addend ? addend + (size_t)j * NZ * NX : nullptr;
+  for (int p0 = 0; p0 < NZ / 2; p0 += CP) {
+    const int np = min(CP, NZ / 2 - p0);
+    for (int job = tid; job < np * N1X; job += kPlaneThreads) {
+      const int p = job / N1X, n1 = job - p * N1X;
+      const cplx<T> *sA = plane + (p0 + p) * 2 * P;
+      rinv_step1<T, NX>(sA, sA + P, n1, tw2x, X + (p * N1X + n1) * XPITCH);
+    }
+    __syncthreads();
+    for (int job = tid; job < np * N2X; job += kPlaneThreads) {
+      const int p = job / N2X, k2 = job - p * N2X;
+      const size_t r = (size_t)(p0 + p) * 2 * NX;
+      rinv_step3<T, NX, XPITCH>(X + p * N1X * XPITCH, k2, dst + r, dst + r + NX, add ? add + r : nullptr,
+                                add ? add + r + NX : nullptr, scale);
+    }
+    __syncthreads();
   }
 }
 
 // --------------------------------------------------------------------------
 // dispatch
 // --------------------------------------------------------------------------
-template <typename T> size_t plane_smem_bytes(int nx, int nz) {
-  return 16 + sizeof(T) * (size_t)nz * nx + sizeof(cplx<T>) * ((size_t)nx + nz + (size_t)nz * (nx / 2 + 1));
-}
-
-template <typename T> constexpr int zcols_width() { return sizeof(T) == 4 ? 16 : 8; }
-
 #define IBM_FOR_EACH_N(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
 
-// plane kernels are instantiated for square-ish planes that fit in shared memory
+// plane kernels are instantiated for square-ish planes whose spectrum fits in shared memory
 #define IBM_PLANE_SHAPES(X)                                                    \
   X(8, 8) X(12, 12) X(16, 16) X(24, 24) X(32, 32) X(48, 48) X(64, 64) X(96, 96) \
   X(128, 128) X(192, 192) X(256, 128) X(128, 256) X(64, 128) X(128, 64)
 
 template <typename T> static bool plane_supported(int nx, int nz) {
-#define X(a, b) if (nx == a && nz == b) return plane_smem_bytes<T>(nx, nz) <= kPlaneSmemLimit;
+#define X(a, b) if (nx == a && nz == b) return PlaneCfg<T, a, b>::ok;
   IBM_PLANE_SHAPES(X)
 #undef X
   return false;
@@ -318,98 +176,44 @@ template <typename T> static bool plane_supported(int nx, int nz) {
 template <typename T>
 cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
                            const cplx<T> *twz, T in_scale, cudaStream_t st) {
-  const int nx = g.nx, ny = g.ny, nz = g.nz, P = nx / 2 + 1;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
     return launch_cplane_forward<T>(g, g.use_plane, in, S, twx, twz, in_scale, st);
   if (g.use_plane == 1 && plane_supported<T>(nx, nz)) {
-    const size_t bytes = plane_smem_bytes<T>(nx, nz);
-#define X(a, b)                                                                     \
-  if (nx == a && nz == b) {                                                         \
-    if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
-      { cudaError_t e = ensure_max_smem<k_plane_fwd<T, a, b>>(); if (e) return e; } \
-      k_plane_fwd<T, a, b><<<ny, kPlaneThreads, bytes, st>>>(in, S, twx, twz, in_scale, g.err, g.zrhs);  \
-      return cudaGetLastError();                                                    \
-    }                                                                               \
+#define X(a, b)                                                                                  \
+  if (nx == a && nz == b) {                                                                      \
+    if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
+      { cudaError_t e = ensure_max_smem<k_plane_fwd<T, a, b>>(); if (e) return e; }              \
+      k_plane_fwd<T, a, b><<<ny, kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(in, S, twx, twz, in_scale, g.zrhs); \
+      return cudaGetLastError();                                                                 \
+    }                                                                                            \
   }
     IBM_PLANE_SHAPES(X)
 #undef X
   }
   // axis path: x rows then z columns
-  bool done = false;
-#define X(N)                                                                               \
-  if (nx == N) {                                                                           \
-    constexpr int PPC = kThreads / FftPlan<N>::G;                                          \
-    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)PPC * N);                 \
-    dim3 grid(ceil_div(nz / 2, PPC), ny);                                                  \
-    { cudaError_t e = ensure_max_smem<k_xfwd_rows<T, N>>(); if (e) return e; }                    \
-    k_xfwd_rows<T, N><<<grid, kThreads, bytes, st>>>(in, S, twx, nz, in_scale);            \
-    done = true;                                                                           \
-  }
-  IBM_FOR_EACH_N(X)
-#undef X
-  if (!done) return cudaErrorInvalidValue;
-  done = false;
-  constexpr int W = zcols_width<T>();
-#define X(N)                                                                               \
-  if (nz == N) {                                                                           \
-    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)N * (W + 1));              \
-    { cudaError_t e = ensure_max_smem<k_zcols<T, N, false, W>>(); if (e) return e; }                    \
-    dim3 grid(ceil_div(P, W), ny);                                                         \
-    k_zcols<T, N, false, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P, g.zrhs, nullptr);            \
-    done = true;                                                                           \
-  }
-  IBM_FOR_EACH_N(X)
-#undef X
-  if (!done) return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  return launch_axis_forward<T>(g, in, S, twx, twz, in_scale, st);
 }
 
 template <typename T>
 cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
                            const cplx<T> *twz, T scale, cudaStream_t st) {
-  const int nx = g.nx, ny = g.ny, nz = g.nz, P = nx / 2 + 1;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
     return launch_cplane_inverse<T>(g, g.use_plane, S, out, addend, twx, twz, scale, st);
   if (g.use_plane == 1 && plane_supported<T>(nx, nz)) {
-    const size_t bytes = plane_smem_bytes<T>(nx, nz);
-#define X(a, b)                                                                     \
-  if (nx == a && nz == b) {                                                         \
-    if (plane_smem_bytes<T>(a, b) <= kPlaneSmemLimit) {                             \
-      { cudaError_t e = ensure_max_smem<k_plane_inv<T, a, b>>(); if (e) return e; } \
-      k_plane_inv<T, a, b><<<ny, kPlaneThreads, bytes, st>>>(S, out, addend, twx, twz, scale, g.err, g.zsol); \
-      return cudaGetLastError();                                                    \
-    }                                                                               \
+#define X(a, b)                                                                                  \
+  if (nx == a && nz == b) {                                                                      \
+    if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
+      { cudaError_t e = ensure_max_smem<k_plane_inv<T, a, b>>(); if (e) return e; }              \
+      k_plane_inv<T, a, b><<<ny, kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(S, out, addend, twx, twz, scale, g.zsol); \
+      return cudaGetLastError();                                                                 \
+    }                                                                                            \
   }
     IBM_PLANE_SHAPES(X)
 #undef X
   }
-  bool done = false;
-  constexpr int W = zcols_width<T>();
-#define X(N)                                                                               \
-  if (nz == N) {                                                                           \
-    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)N * (W + 1));              \
-    { cudaError_t e = ensure_max_smem<k_zcols<T, N, true, W>>(); if (e) return e; }                    \
-    dim3 grid(ceil_div(P, W), ny);                                                         \
-    k_zcols<T, N, true, W><<<grid, W * FftPlan<N>::G, bytes, st>>>(S, twz, P, nullptr, g.zsol);             \
-    done = true;                                                                           \
-  }
-  IBM_FOR_EACH_N(X)
-#undef X
-  if (!done) return cudaErrorInvalidValue;
-  done = false;
-#define X(N)                                                                               \
-  if (nx == N) {                                                                           \
-    constexpr int PPC = kThreads / FftPlan<N>::G;                                          \
-    const size_t bytes = sizeof(cplx<T>) * ((size_t)N + (size_t)PPC * N);                 \
-    dim3 grid(ceil_div(nz / 2, PPC), ny);                                                  \
-    { cudaError_t e = ensure_max_smem<k_xinv_rows<T, N>>(); if (e) return e; }                    \
-    k_xinv_rows<T, N><<<grid, kThreads, bytes, st>>>(S, out, addend, twx, nz, scale);       \
-    done = true;                                                                           \
-  }
-  IBM_FOR_EACH_N(X)
-#undef X
-  if (!done) return cudaErrorInvalidValue;
-  return cudaGetLastError();
+  return launch_axis_inverse<T>(g, S, out, addend, twx, twz, scale, st);
 }
 
 template cudaError_t launch_forward<float>(const TransformGeom &, const float *, float2 *, const float2 *,
@@ -440,13 +244,14 @@ template int plane_modes<float>(int, int, int *);
 template int plane_modes<double>(int, int, int *);
 
 template <typename T> int default_plane_mode(int nx, int ny, int nz) {
-  // Measured on GB300 (FP32 and FP64, 128^3 to 384x256x256): the one-CTA
-  // plane kernels beat the split passes where they fit, and the cluster
-  // kernels lose to both (their row/column exchange through distributed
-  // shared memory costs more than the L2 round trip of the split passes).
-  // Clusters stay available to the tuner and to IBM_PLANE_MODE.
+  // Measured on GB300 (128^3 to 384x256x256): in FP32 the one-CTA plane
+  // kernels win up to 128 x 256 planes and the split passes from 192^2 on;
+  // in FP64 (arithmetic-bound here) the split passes win at every size.
+  // The cluster kernels lose to both and stay available to the tuner and to
+  // IBM_PLANE_MODE.
   (void)ny;
-  return plane_supported<T>(nx, nz) ? 1 : 0;
+  if (sizeof(T) == 4 && plane_supported<T>(nx, nz) && nx * nz <= 128 * 256) return 1;
+  return 0;
 }
 template int default_plane_mode<float>(int, int, int);
 template int default_plane_mode<double>(int, int, int);
