@@ -1,9 +1,10 @@
 // batch.cu -- the autotuner and batched solves of many independent grids.
 //
 // Autotuner.  For a grid shape and precision it times every available
-// variant of the solve -- pencil solver (serial excess-form sweep or the
-// warp-parallel substructured solve) x transform path (one CTA per y-plane,
-// or split x and z passes) -- on scratch buffers, keeps the fastest, and
+// variant of the solve -- pencil kernel (two-ended sweep on a shared tile,
+// the streaming two-ended sweep, or the warp-parallel substructured solve) x
+// plane mode (split x and z passes, one CTA per y-plane, or a cluster of C
+// CTAs per plane) -- on scratch buffers, keeps the fastest, and
 // remembers it for the process (optionally in the text file named by
 // IBM_TUNE_CACHE, one line per shape).
 //
@@ -110,7 +111,9 @@ int tune_plan(ibm_plan_s *p, TuneChoice *out) {
   int modes[8];
   const int nmodes = plane_candidates(p, modes);
   int rc = IBM_OK;
-  for (int pm = 0; pm <= (substructured_available(p) ? 1 : 0) && rc == IBM_OK; ++pm) {
+  const int pms[3] = {2, 3, 1};
+  for (int ip = 0; ip < (substructured_available(p) ? 3 : 2) && rc == IBM_OK; ++ip) {
+    const int pm = pms[ip];
     for (int m = 0; m < nmodes && rc == IBM_OK; ++m) {
       const int up = modes[m];
       p->pencil_mode = pm;

@@ -24,6 +24,8 @@
 // the constant (Sec. 2.3.3, S2.1), the bidiagonal factors of the zero-mode
 // matrix reduce the elimination to two running sums (a (x_{j+1} - x_j) =
 // sum_{i<=j} f_i), and the FP64 mean of x is removed (mean(phi) = 0).
+#include <algorithm>
+
 #include "internal.h"
 #include "tma.cuh"
 
@@ -33,8 +35,7 @@ template <typename T> __device__ __forceinline__ T rcp(T x);
 template <> __device__ __forceinline__ float rcp<float>(float x) { return rcp_approx(x); }
 template <> __device__ __forceinline__ double rcp<double>(double x) { return 1.0 / x; }
 
-template <typename T> struct PencilTile { static constexpr int TP = 32; };
-template <> struct PencilTile<double> { static constexpr int TP = 16; };
+template <typename T> struct PencilTile { static constexpr int TP = 16; };
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -101,65 +102,177 @@ __device__ __forceinline__ bool zero_mode_cta(const PencilParams &pp, double *zs
   return true;
 }
 
-// One pencil per lane: Thomas in excess form on tile column `lane`.
-template <typename T, int TP>
-__device__ __forceinline__ void serial_sweep(cplx<T> *tile, T *qs, const T *__restrict__ lamx,
-                                             const T *__restrict__ lamz, const PencilParams &pp, int p0, int lane,
-                                             cplx<T> *__restrict__ col, size_t plane) {
-  const int ny = pp.ny;
+// Two lanes per pencil, Thomas in excess form from both ends ("twisted"
+// elimination): the even lane eliminates rows 0 .. m-1 top-down, the odd
+// lane rows n-1 .. m+1 bottom-up, and the two meet at row m = n/2, where
+//   (g + a q^T_{m-1} + a q^B_{m+1}) x_m = f_m + a (y^T_{m-1} + y^B_{m+1})
+// (a sum of non-negative terms, like every other pivot).  Each lane then
+// substitutes back towards its end.  The serial depth per pencil is n
+// instead of 2n.  Per row of a half sweep (r = 1/(a + e), w = a r = 1 - q):
+//   forward   y_s = r f_s + w y_{s-1}      (y over f in the shared tile, w kept)
+//   backward  x_s = y_s + w_s x_{s+1}      (straight to the spectrum)
+template <typename T>
+__device__ __forceinline__ void half_forward(cplx<T> *t, int stp, T *wc, int len, T a, T g, T e0, T sgn, cplx<T> &y,
+                                             T &q) {
+  T e = e0;
+  y.x = (T)0;
+  y.y = (T)0;
+#pragma unroll 4
+  for (int s = 0; s < len; ++s) {
+    const cplx<T> f = t[s * stp];
+    if (s > 0) e = fma(a, q, g);
+    const T r = rcp<T>(a + e);
+    q = e * r;
+    const T w = a * r;
+    y.x = fma(r, sgn * f.x, w * y.x);
+    y.y = fma(r, sgn * f.y, w * y.y);
+    t[s * stp] = y;
+    wc[s * stp] = w;
+  }
+}
 
-  const int p = p0 + lane;
-  const int kz = p / pp.P, kx = p - kz * pp.P;
+template <typename T>
+__device__ __forceinline__ void half_backward(const cplx<T> *t, int stp, const T *wc, int len, cplx<T> x,
+                                              cplx<T> *gcol, long gstep) {
+#pragma unroll 4
+  for (int s = len - 1; s >= 0; --s) {
+    const cplx<T> y = t[s * stp];
+    const T w = wc[s * stp];
+    x.x = fma(w, x.x, y.x);
+    x.y = fma(w, x.y, y.y);
+    gcol[s * gstep] = x;
+  }
+}
+
+// Variant for grids with more pencils than the tile kernel keeps resident:
+// no tile; the forward half sweep writes y_s over f_s in the spectrum itself
+// (loads run U to 2U rows ahead of the recurrence), only w stays in shared
+// memory, and the backward sweep reads y_s back (mostly from L2).
+template <typename T> struct SweepDepth { static constexpr int U = 16; };
+template <> struct SweepDepth<double> { static constexpr int U = 8; };
+
+template <typename T, int U>
+__device__ __forceinline__ void gl_forward(cplx<T> *col, long step, T *wc, int wstep, int len, T a, T g, T e0, T sgn,
+                                           cplx<T> &y, T &q) {
+  cplx<T> fb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u)
+    if (u < len) fb[u] = col[u * step];
+  T e = e0;
+  y.x = (T)0;
+  y.y = (T)0;
+  for (int s0 = 0; s0 < len; s0 += U) {
+    cplx<T> fn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (s0 + U + u < len) fn[u] = col[(s0 + U + u) * step];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 + u;
+      if (s < len) {
+        if (s > 0) e = fma(a, q, g);
+        const T r = rcp<T>(a + e);
+        q = e * r;
+        const T w = a * r;
+        y.x = fma(r, sgn * fb[u].x, w * y.x);
+        y.y = fma(r, sgn * fb[u].y, w * y.y);
+        col[s * step] = y;
+        wc[s * wstep] = w;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) fb[u] = fn[u];
+  }
+}
+
+template <typename T, int U>
+__device__ __forceinline__ void gl_backward(cplx<T> *col, long step, const T *wc, int wstep, int len, cplx<T> x) {
+  cplx<T> yb[U];
+  T wb[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int s = len - 1 - u;
+    if (s >= 0) { yb[u] = col[s * step]; wb[u] = wc[s * wstep]; }
+  }
+  for (int s0 = len - 1; s0 >= 0; s0 -= U) {
+    cplx<T> yn[U];
+    T wn[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 - U - u;
+      if (s >= 0) { yn[u] = col[s * step]; wn[u] = wc[s * wstep]; }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int s = s0 - u;
+      if (s >= 0) {
+        x.x = fma(wb[u], x.x, yb[u].x);
+        x.y = fma(wb[u], x.y, yb[u].y);
+        col[s * step] = x;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) { yb[u] = yn[u]; wb[u] = wn[u]; }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32)
+k_pencil_g(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
+           double *mean_out) {
+  constexpr int TP = PencilTile<T>::TP;
+  constexpr int U = SweepDepth<T>::U;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int n = pp.ny - pp.j0;
+  T *ws = reinterpret_cast<T *>(smem_raw);                     // [n][TP]
+  double *zs = reinterpret_cast<double *>(ws + (size_t)pp.ny * TP);  // [ny] (zero-mode CTA)
+  if (zero_mode_cta(pp, zs, mean_out)) return;
+  const long plane = (long)pp.nz * pp.P;
+  const int npen = pp.nz * pp.P;
+  const int lane = threadIdx.x;
+  const int bottom = lane & 1, pl = lane >> 1;
+  const int p = blockIdx.x * TP + pl;
+  const bool live = p < npen && !(pp.zero_mode && p == 0);
+  const int m = n / 2;
+  const int len = bottom ? n - 1 - m : m;
+  const int pc = live ? p : 0;
+  const int kz = pc / pp.P, kx = pc - kz * pp.P;
   const T a = (T)pp.a;
   const T g = (T)pp.g_add + (T)pp.g_mul * (lamx[kx] + lamz[kz]);
   const T sgn = pp.neg_rhs ? (T)-1 : (T)1;
-  const int j0 = pp.j0;
-  const int n = ny - j0;
-  cplx<T> *tl = tile + j0 * TP + lane;  // row i of the pencil at tl[i * TP]
-  T *ql = qs + j0 * TP + lane;
-
-  // forward sweep, rows 0 .. n-2 (y overwrites f in the tile, q kept for the way back)
-  T e = g + a * (T)pp.beta_s;
-  T r = rcp<T>(a + e);
-  T q = e * r;
-  cplx<T> y = tl[0];
-  y.x = r * (sgn * y.x);
-  y.y = r * (sgn * y.y);
-  tl[0] = y;
-  ql[0] = q;
-#pragma unroll 4
-  for (int i = 1; i < n - 1; ++i) {
-    const cplx<T> f = tl[i * TP];
-    e = fma(a, q, g);
-    r = rcp<T>(a + e);
-    q = e * r;
-    y.x = fma(r, sgn * f.x, fma(-q, y.x, y.x));
-    y.y = fma(r, sgn * f.y, fma(-q, y.y, y.y));
-    tl[i * TP] = y;
-    ql[i * TP] = q;
-  }
-  // last row: pivot a beta_e + e_{n-1}
+  cplx<T> *c0 = S + pc + (long)pp.j0 * plane;  // row 0 of the unknowns
+  const int first = bottom ? n - 1 : 0;
+  cplx<T> *col = c0 + (long)first * plane;
+  const long step = bottom ? -plane : plane;
+  T *wc = ws + first * TP + pl;
+  const int wstep = bottom ? -TP : TP;
+  const T e0 = g + a * (T)(bottom ? pp.beta_e : pp.beta_s);
+  cplx<T> y;
+  T q = (T)0;
+  if (live) gl_forward<T, U>(col, step, wc, wstep, len, a, g, e0, sgn, y, q);
+  // meet at row m: the top lane reads f_m, the pair swaps (y, q) and f_m
+  cplx<T> f;
+  f.x = (T)0;
+  f.y = (T)0;
+  if (live && !bottom) f = c0[(long)m * plane];
+  const T yo_x = __shfl_xor_sync(0xffffffffu, y.x, 1);
+  const T yo_y = __shfl_xor_sync(0xffffffffu, y.y, 1);
+  const T qo = __shfl_xor_sync(0xffffffffu, q, 1);
+  const T fo_x = __shfl_xor_sync(0xffffffffu, f.x, 1);
+  const T fo_y = __shfl_xor_sync(0xffffffffu, f.y, 1);
+  if (!live) return;
+  if (bottom) { f.x = fo_x; f.y = fo_y; }
+  cplx<T> x;
   {
-    const cplx<T> f = tl[(n - 1) * TP];
-    e = fma(a, q, g);
-    const T rl = rcp<T>(e + a * (T)pp.beta_e);
-    y.x = (sgn * f.x + a * y.x) * rl;
-    y.y = (sgn * f.y + a * y.y) * rl;
+    const T rm = rcp<T>(g + a * q + a * qo);
+    x.x = (sgn * f.x + a * (y.x + yo_x)) * rm;
+    x.y = (sgn * f.y + a * (y.y + yo_y)) * rm;
   }
-  // backward sweep, results straight to global memory (fire-and-forget stores)
-  cplx<T> *cj = col + (size_t)j0 * plane;
-  cplx<T> x = y;
-  cj[(size_t)(n - 1) * plane] = x;
-  for (int i = n - 2; i >= 0; --i) {
-    const T qi = ql[i * TP];
-    const cplx<T> yi = tl[i * TP];
-    x.x = fma(-qi, x.x, x.x) + yi.x;
-    x.y = fma(-qi, x.y, x.y) + yi.y;
-    cj[(size_t)i * plane] = x;
-  }
-  if (j0 == 1) {
+  if (!bottom) c0[(long)m * plane] = x;
+  gl_backward<T, U>(col, step, wc, wstep, len, x);
+  if (pp.j0 == 1 && !bottom) {
     cplx<T> z; z.x = (T)0; z.y = (T)0;
-    col[0] = z;
+    S[p] = z;
   }
 }
 
@@ -167,33 +280,70 @@ template <typename T>
 __global__ void __launch_bounds__(32)
 k_pencil(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
          double *mean_out) {
-  constexpr int TP = PencilTile<T>::TP;
+  constexpr int TP = PencilTile<T>::TP;  // pencils per CTA, two lanes each
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
-  cplx<T> *tile = reinterpret_cast<cplx<T> *>(smem_raw + 16);  // [ny][TP]
-  T *qs = reinterpret_cast<T *>(tile + (size_t)pp.ny * TP);    // [ny][TP]
-  double *zs = reinterpret_cast<double *>(qs + (size_t)pp.ny * TP);  // [ny]
   const int ny = pp.ny;
+  const int n = ny - pp.j0;
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
+  cplx<T> *tile = reinterpret_cast<cplx<T> *>(smem_raw + 16);  // [n][TP], rows 16-byte aligned for the bulk copies
+  T *ws = reinterpret_cast<T *>(tile + (size_t)n * TP);        // [n][TP]
+  double *zs = reinterpret_cast<double *>(ws + (size_t)n * TP);  // [ny] (zero-mode CTA, n = ny)
   if (zero_mode_cta(pp, zs, mean_out)) return;
-  const size_t plane = (size_t)pp.nz * pp.P;
+  const long plane = (long)pp.nz * pp.P;
   const int npen = pp.nz * pp.P;
   const int p0 = blockIdx.x * TP;
   const int np = min(TP, npen - p0);  // even: npen is even and p0 a multiple of TP
   const int lane = threadIdx.x;
-  // one warp per CTA: rows j of the tile arrive by bulk copy (np * 8 or 16 bytes each)
+  const cplx<T> *src = S + (long)pp.j0 * plane + p0;
+  // rows of the tile arrive by bulk copy (np * 8 or 16 bytes each)
   if (lane == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
-    mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(cplx<T>) * np * ny));
+    mbar_arrive_expect_tx(bar, (uint32_t)(sizeof(cplx<T>) * np * n));
   }
   __syncwarp();
-  for (int j = lane; j < ny; j += 32)
-    bulk_g2s(tile + (size_t)j * TP, S + (size_t)j * plane + p0, (uint32_t)(sizeof(cplx<T>) * np), bar);
+  for (int j = lane; j < n; j += 32)
+    bulk_g2s(tile + (size_t)j * TP, src + (long)j * plane, (uint32_t)(sizeof(cplx<T>) * np), bar);
   if (!__all_sync(0xffffffffu, mbar_wait(bar, 0, pp.err))) return;
+  const int bottom = lane & 1, pl = lane >> 1;
+  const int p = p0 + pl;
   // the (0,0) pencil is singular (g = 0): its sweep is skipped here and its
   // FP64 solution reaches the inverse transform through zsol
-  if (lane < np && !(pp.zero_mode && p0 == 0 && lane == 0))
-    serial_sweep<T, TP>(tile, qs, lamx, lamz, pp, p0, lane, S + p0 + lane, plane);
+  const bool live = pl < np && !(pp.zero_mode && p == 0);
+  const int m = n / 2;
+  const int len = bottom ? n - 1 - m : m;
+  const int pc = live ? p : 0;
+  const int kz = pc / pp.P, kx = pc - kz * pp.P;
+  const T a = (T)pp.a;
+  const T g = (T)pp.g_add + (T)pp.g_mul * (lamx[kx] + lamz[kz]);
+  const T sgn = pp.neg_rhs ? (T)-1 : (T)1;
+  const int first = bottom ? n - 1 : 0;
+  const int stp = bottom ? -TP : TP;
+  cplx<T> *t = tile + first * TP + pl;
+  T *wc = ws + first * TP + pl;
+  const T e0 = g + a * (T)(bottom ? pp.beta_e : pp.beta_s);
+  cplx<T> y;
+  T q = (T)0;
+  if (live) half_forward<T>(t, stp, wc, len, a, g, e0, sgn, y, q);
+  // meet at row m
+  const T yo_x = __shfl_xor_sync(0xffffffffu, y.x, 1);
+  const T yo_y = __shfl_xor_sync(0xffffffffu, y.y, 1);
+  const T qo = __shfl_xor_sync(0xffffffffu, q, 1);
+  if (!live) return;
+  cplx<T> *gcol = S + p + (long)pp.j0 * plane;  // row 0 of the unknowns in the spectrum
+  cplx<T> x;
+  {
+    const cplx<T> f = tile[m * TP + pl];
+    const T rm = rcp<T>(g + a * q + a * qo);
+    x.x = (sgn * f.x + a * (y.x + yo_x)) * rm;
+    x.y = (sgn * f.y + a * (y.y + yo_y)) * rm;
+  }
+  if (!bottom) gcol[(long)m * plane] = x;
+  half_backward<T>(t, stp, wc, len, x, gcol + (long)first * plane, bottom ? -plane : plane);
+  if (pp.j0 == 1 && !bottom) {
+    cplx<T> z; z.x = (T)0; z.y = (T)0;
+    S[p] = z;
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -537,14 +687,33 @@ static cudaError_t launch_ss(const PencilParams &pp, cplx<T> *S, const T *lamx, 
 
 template <typename T> size_t pencil_smem_bytes(int ny) {
   constexpr int TP = PencilTile<T>::TP;
-  return 16 + (size_t)ny * TP * (sizeof(cplx<T>) + sizeof(T)) + (size_t)ny * sizeof(double);
+  return 16 + (size_t)ny * sizeof(double) + (size_t)ny * TP * (sizeof(cplx<T>) + sizeof(T));
+}
+template <typename T> size_t pencil_g_smem_bytes(int ny) {
+  constexpr int TP = PencilTile<T>::TP;
+  return (size_t)ny * sizeof(double) + (size_t)ny * TP * sizeof(T);
+}
+
+// Resident 32-thread CTAs of a kernel with `bytes` of dynamic shared memory
+// on the whole device (per-device attributes read once).
+static long resident_ctas(size_t bytes) {
+  static std::once_flag once;
+  static int sms = 0, smem = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+  });
+  const long per_sm = std::min<long>(32, (long)smem / (long)(bytes + 1024));
+  return (long)sms * std::max<long>(per_sm, 1);
 }
 
 template <typename T>
 cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, const T *lamz, double *mean_out,
                           cudaStream_t st) {
   const int n = pp.ny - pp.j0;
-  if (pp.substructured) {
+  if (pp.mode == 1) {
     if constexpr (sizeof(T) == 4) {
       if (n <= 32) return launch_ss<T, 1, false>(pp, S, lamx, lamz, mean_out, st);
       if (n <= 64) return launch_ss<T, 2, false>(pp, S, lamx, lamz, mean_out, st);
@@ -557,13 +726,21 @@ cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, con
     }
   }
   constexpr int TP = PencilTile<T>::TP;
-  const size_t bytes = pencil_smem_bytes<T>(pp.ny);
-  {
+  const int npen = pp.nz * pp.P;
+  const int grid = ceil_div(npen, TP) + (pp.zero_mode ? 1 : 0);
+  // the tile kernel while every CTA stays resident (measured faster there);
+  // beyond that the tile-less kernel, which keeps about three times as many
+  const size_t tb = pencil_smem_bytes<T>(pp.ny);
+  const bool tile = pp.mode == 2 || (pp.mode != 3 && grid <= resident_ctas(tb));
+  if (tile) {
     cudaError_t e = ensure_max_smem<k_pencil<T>>();
     if (e != cudaSuccess) return e;
+    k_pencil<T><<<grid, 32, tb, st>>>(S, lamx, lamz, pp, mean_out);
+  } else {
+    cudaError_t e = ensure_max_smem<k_pencil_g<T>>();
+    if (e != cudaSuccess) return e;
+    k_pencil_g<T><<<grid, 32, pencil_g_smem_bytes<T>(pp.ny), st>>>(S, lamx, lamz, pp, mean_out);
   }
-  const int npen = pp.nz * pp.P;
-  k_pencil<T><<<ceil_div(npen, TP) + (pp.zero_mode ? 1 : 0), 32, bytes, st>>>(S, lamx, lamz, pp, mean_out);
   return cudaGetLastError();
 }
 

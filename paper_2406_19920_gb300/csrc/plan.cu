@@ -176,7 +176,7 @@ static PencilParams pencil_params(const ibm_plan_s *p, int kind, double c, int f
   pp.hy2 = hy * hy;
   pp.inv_nxnz = 1.0 / ((double)p->nx * p->nz);
   pp.err = p->derr;
-  pp.substructured = p->pencil_mode;
+  pp.mode = p->pencil_mode;
   pp.zrhs = p->zbuf;
   pp.zsol = p->zbuf + p->ny;
   pp.inv_ny = 1.0 / p->ny;
@@ -289,9 +289,18 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   p->precision = precision;
   p->refine = precision == IBM_FP64 ? 0 : refine_iters;
   p->delta = IBM_DELTA_ROMA3;
-  // pencil solver: serial excess-form sweep by default; IBM_PENCIL_SUBSTRUCT=1
-  // selects the warp-parallel block solve (A/B timing; the tuner may pick it)
-  p->pencil_mode = (getenv("IBM_PENCIL_SUBSTRUCT") && atoi(getenv("IBM_PENCIL_SUBSTRUCT")) == 1) ? 1 : 0;
+  // pencil solver: the two-ended sweep, tile or streaming kernel by size;
+  // IBM_PENCIL_MODE=m forces 1 (warp-parallel block solve), 2 (tile) or 3
+  // (streaming) for A/B timing and tests; the tuner may pick any of them
+  p->pencil_mode = 0;
+  if (const char *pm = getenv("IBM_PENCIL_MODE")) {
+    const int m = atoi(pm);
+    if (m < 0 || m > 3) {
+      delete p;
+      return set_error(IBM_ERR_ARG, "ibm_plan_create: IBM_PENCIL_MODE=%d outside [0,3]", m);
+    }
+    p->pencil_mode = m;
+  }
   // plane transforms: the default mode for the shape; IBM_PLANE_MODE=m forces
   // mode m (0 split passes, 1 one CTA per plane, 2/4/8 cluster) and fails
   // the plan when the shape has no such mode (A/B timing and tests)

@@ -187,6 +187,45 @@ def test_every_plane_mode_matches_oracle(shape):
     assert 0 in ran and any(m >= 2 for m in ran), ran
 
 
+PENCIL_MODE_SHAPES = [(32, 32, 32), (12, 10, 24), (48, 17, 96), (24, 129, 16), (16, 200, 24), (32, 300, 16)]
+
+
+@pytest.mark.parametrize("shape", PENCIL_MODE_SHAPES)
+def test_every_pencil_kernel_matches_oracle(shape):
+    """IBM_PENCIL_MODE 1 (warp-parallel blocks), 2 (tile sweep), 3 (streaming sweep)."""
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    b = synth.white_noise(nx, ny, nz, workload=14, stream=0) + 0.1
+    b32 = b.astype(np.float32).astype(np.float64)
+    ref64, _ = O.poisson_solve(b, g)
+    ref32, _ = O.poisson_solve(b32, g)
+    helm = {bc: O.helmholtz_solve(b32, g, 0.02, bc)
+            for bc in (ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_FACE_DIRICHLET)}
+    for mode in (1, 2, 3):
+        for prec, dt, tol, bb, ref in ((ibm.IBM_FP64, torch.float64, TOL_FP64, b, ref64),
+                                       (ibm.IBM_FP32_REFINED, torch.float32, TOL_FP32, b32, ref32)):
+            os.environ["IBM_PENCIL_MODE"] = str(mode)
+            try:
+                plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, 1)
+            finally:
+                del os.environ["IBM_PENCIL_MODE"]
+            try:
+                rhs = dev(bb, dt)
+                phi = torch.empty_like(rhs)
+                ibm.ibm_poisson_solve(plan, rhs, phi)
+                torch.cuda.synchronize()
+                assert rel_l2(host(phi), ref) <= tol, (mode, prec, rel_l2(host(phi), ref))
+                if prec == ibm.IBM_FP32_REFINED:
+                    for bc, href in helm.items():
+                        u = torch.empty_like(rhs)
+                        ibm.ibm_helmholtz_solve(plan, 0.02, bc, rhs, u)
+                        torch.cuda.synchronize()
+                        assert rel_l2(host(u), href) <= tol, (mode, bc, rel_l2(host(u), href))
+                ibm.ibm_plan_check(plan)
+            finally:
+                ibm.ibm_plan_destroy(plan)
+
+
 def test_invalid_arguments_rejected_before_launch():
     g = grid(32, 32, 32)
     with pytest.raises(ibm.IbmError) as e:
