@@ -34,8 +34,9 @@ template <typename T, int N> struct RowCfg {
 
 template <typename T, int N>
 __global__ void __launch_bounds__(kRowThreads)
-k_rows_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ tw, int npairs,
-           T in_scale) {
+k_rows_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ tw, int npairs, T in_scale) {
+  const T *__restrict__ in = in_[blockIdx.y];
+  cplx<T> *__restrict__ S = S_[blockIdx.y];
   using Cfg = RowCfg<T, N>;
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, PITCH = Cfg::PITCH, P = N / 2 + 1;
   constexpr int J3 = N2 / 2 + 1;
@@ -60,8 +61,11 @@ k_rows_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__r
 
 template <typename T, int N>
 __global__ void __launch_bounds__(kRowThreads)
-k_rows_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ tw, int npairs,
+k_rows_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<T> *__restrict__ tw, int npairs,
            T scale) {
+  const cplx<T> *__restrict__ S = S_[blockIdx.y];
+  T *out = out_[blockIdx.y];
+  const T *addend = add_[blockIdx.y];
   using Cfg = RowCfg<T, N>;
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, PITCH = Cfg::PITCH, P = N / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -99,7 +103,8 @@ template <typename T, int N> struct ColCfg {
 // plane j = col / P; element kz at S[(j NZ + kz) P + kx].
 template <typename T, int N, bool INV>
 __global__ void __launch_bounds__(ColCfg<T, N>::THREADS)
-k_cols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ tw, int P, int ncols, double *zrhs, const double *zsol) {
+k_cols(Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ tw, int P, int ncols, double *zrhs, const double *zsol) {
+  cplx<T> *__restrict__ S = S_[blockIdx.y];
   using Cfg = ColCfg<T, N>;
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, W = Cfg::W;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -134,7 +139,7 @@ k_cols(cplx<T> *__restrict__ S, const cplx<T> *__restrict__ tw, int P, int ncols
 #define IBM_AXIS_N(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
 
 template <typename T>
-cudaError_t launch_axis_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
+cudaError_t launch_axis_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx<T> *> S, const cplx<T> *twx,
                                 const cplx<T> *twz, T in_scale, cudaStream_t st) {
   const int npairs = g.ny * g.nz / 2;
   const int P = g.nx / 2 + 1;
@@ -143,7 +148,7 @@ cudaError_t launch_axis_forward(const TransformGeom &g, const T *in, cplx<T> *S,
   if (g.nx == N) {                                                                                \
     using Cfg = RowCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_rows_fwd<T, N>>(); if (e) return e; }                     \
-    k_rows_fwd<T, N><<<ceil_div(npairs, Cfg::RP), kRowThreads, Cfg::smem, st>>>(in, S, twx, npairs, in_scale); \
+    k_rows_fwd<T, N><<<dim3(ceil_div(npairs, Cfg::RP), g.nb), kRowThreads, Cfg::smem, st>>>(in, S, twx, npairs, in_scale); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -155,7 +160,7 @@ cudaError_t launch_axis_forward(const TransformGeom &g, const T *in, cplx<T> *S,
   if (g.nz == N) {                                                                                \
     using Cfg = ColCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_cols<T, N, false>>(); if (e) return e; }                  \
-    k_cols<T, N, false><<<ceil_div(ncols, Cfg::W), Cfg::THREADS, Cfg::smem, st>>>(S, twz, P, ncols, g.zrhs, nullptr); \
+    k_cols<T, N, false><<<dim3(ceil_div(ncols, Cfg::W), g.nb), Cfg::THREADS, Cfg::smem, st>>>(S, twz, P, ncols, g.zrhs, nullptr); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -165,8 +170,8 @@ cudaError_t launch_axis_forward(const TransformGeom &g, const T *in, cplx<T> *S,
 }
 
 template <typename T>
-cudaError_t launch_axis_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
-                                const cplx<T> *twz, T scale, cudaStream_t st) {
+cudaError_t launch_axis_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> out, Ptr3<const T *> addend,
+                                const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st) {
   const int npairs = g.ny * g.nz / 2;
   const int P = g.nx / 2 + 1;
   const int ncols = g.ny * P;
@@ -175,7 +180,7 @@ cudaError_t launch_axis_inverse(const TransformGeom &g, cplx<T> *S, T *out, cons
   if (g.nz == N) {                                                                                \
     using Cfg = ColCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_cols<T, N, true>>(); if (e) return e; }                   \
-    k_cols<T, N, true><<<ceil_div(ncols, Cfg::W), Cfg::THREADS, Cfg::smem, st>>>(S, twz, P, ncols, nullptr, g.zsol); \
+    k_cols<T, N, true><<<dim3(ceil_div(ncols, Cfg::W), g.nb), Cfg::THREADS, Cfg::smem, st>>>(S, twz, P, ncols, nullptr, g.zsol); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -186,7 +191,7 @@ cudaError_t launch_axis_inverse(const TransformGeom &g, cplx<T> *S, T *out, cons
   if (g.nx == N) {                                                                                \
     using Cfg = RowCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_rows_inv<T, N>>(); if (e) return e; }                     \
-    k_rows_inv<T, N><<<ceil_div(npairs, Cfg::RP), kRowThreads, Cfg::smem, st>>>(S, out, addend, twx, npairs, scale); \
+    k_rows_inv<T, N><<<dim3(ceil_div(npairs, Cfg::RP), g.nb), kRowThreads, Cfg::smem, st>>>(S, out, addend, twx, npairs, scale); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -195,13 +200,15 @@ cudaError_t launch_axis_inverse(const TransformGeom &g, cplx<T> *S, T *out, cons
   return cudaGetLastError();
 }
 
-template cudaError_t launch_axis_forward<float>(const TransformGeom &, const float *, float2 *, const float2 *,
-                                                const float2 *, float, cudaStream_t);
-template cudaError_t launch_axis_forward<double>(const TransformGeom &, const double *, double2 *, const double2 *,
-                                                 const double2 *, double, cudaStream_t);
-template cudaError_t launch_axis_inverse<float>(const TransformGeom &, float2 *, float *, const float *,
+template cudaError_t launch_axis_forward<float>(const TransformGeom &, Ptr3<const float *>, Ptr3<float2 *>,
                                                 const float2 *, const float2 *, float, cudaStream_t);
-template cudaError_t launch_axis_inverse<double>(const TransformGeom &, double2 *, double *, const double *,
+template cudaError_t launch_axis_forward<double>(const TransformGeom &, Ptr3<const double *>, Ptr3<double2 *>,
                                                  const double2 *, const double2 *, double, cudaStream_t);
+template cudaError_t launch_axis_inverse<float>(const TransformGeom &, Ptr3<float2 *>, Ptr3<float *>,
+                                                Ptr3<const float *>, const float2 *, const float2 *, float,
+                                                cudaStream_t);
+template cudaError_t launch_axis_inverse<double>(const TransformGeom &, Ptr3<double2 *>, Ptr3<double *>,
+                                                 Ptr3<const double *>, const double2 *, const double2 *, double,
+                                                 cudaStream_t);
 
 }  // namespace ibm

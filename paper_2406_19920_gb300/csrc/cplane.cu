@@ -51,8 +51,10 @@ template <typename T, int NX, int NZ, int C> struct CLayout {
 
 template <typename T, int NX, int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCThreads)
-k_cplane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx_g,
+k_cplane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ twx_g,
              const cplx<T> *__restrict__ twz_g, T in_scale, int *err, double *zrhs) {
+  const T *__restrict__ in = in_[blockIdx.y];
+  cplx<T> *__restrict__ S = S_[blockIdx.y];
   using L = CLayout<T, NX, NZ, C>;
   constexpr int P = L::P, R = L::R, PC = L::PC, PCP = L::PCP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -130,8 +132,11 @@ k_cplane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *_
 
 template <typename T, int NX, int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCThreads)
-k_cplane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx_g,
+k_cplane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<T> *__restrict__ twx_g,
              const cplx<T> *__restrict__ twz_g, T scale, int *err, const double *zsol) {
+  const cplx<T> *__restrict__ S = S_[blockIdx.y];
+  T *out = out_[blockIdx.y];
+  const T *addend = add_[blockIdx.y];
   using L = CLayout<T, NX, NZ, C>;
   constexpr int P = L::P, R = L::R, PC = L::PC, PCP = L::PCP;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -221,14 +226,14 @@ template <typename T> bool cplane_supported(int nx, int nz, int C) {
 }
 
 template <typename T>
-cudaError_t launch_cplane_forward(const TransformGeom &g, int C, const T *in, cplx<T> *S, const cplx<T> *twx,
-                                  const cplx<T> *twz, T in_scale, cudaStream_t st) {
+cudaError_t launch_cplane_forward(const TransformGeom &g, int C, Ptr3<const T *> in, Ptr3<cplx<T> *> S,
+                                  const cplx<T> *twx, const cplx<T> *twz, T in_scale, cudaStream_t st) {
 #define X(a, b, c)                                                                              \
   if (g.nx == a && g.nz == b && C == c) {                                                       \
     if constexpr (CLayout<T, a, b, c>::fwd_bytes <= kPlaneSmemLimit) {                          \
       cudaError_t e = ensure_max_smem<k_cplane_fwd<T, a, b, c>>();                              \
       if (e) return e;                                                                          \
-      k_cplane_fwd<T, a, b, c><<<g.ny * c, kCThreads, CLayout<T, a, b, c>::fwd_bytes, st>>>(    \
+      k_cplane_fwd<T, a, b, c><<<dim3(g.ny * c, g.nb), kCThreads, CLayout<T, a, b, c>::fwd_bytes, st>>>(    \
           in, S, twx, twz, in_scale, g.err, g.zrhs);                                            \
       return cudaGetLastError();                                                                \
     }                                                                                           \
@@ -239,14 +244,15 @@ cudaError_t launch_cplane_forward(const TransformGeom &g, int C, const T *in, cp
 }
 
 template <typename T>
-cudaError_t launch_cplane_inverse(const TransformGeom &g, int C, const cplx<T> *S, T *out, const T *addend,
-                                  const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st) {
+cudaError_t launch_cplane_inverse(const TransformGeom &g, int C, Ptr3<cplx<T> *> S, Ptr3<T *> out,
+                                  Ptr3<const T *> addend, const cplx<T> *twx, const cplx<T> *twz, T scale,
+                                  cudaStream_t st) {
 #define X(a, b, c)                                                                              \
   if (g.nx == a && g.nz == b && C == c) {                                                       \
     if constexpr (CLayout<T, a, b, c>::fwd_bytes <= kPlaneSmemLimit) {                          \
       cudaError_t e = ensure_max_smem<k_cplane_inv<T, a, b, c>>();                              \
       if (e) return e;                                                                          \
-      k_cplane_inv<T, a, b, c><<<g.ny * c, kCThreads, CLayout<T, a, b, c>::inv_bytes, st>>>(    \
+      k_cplane_inv<T, a, b, c><<<dim3(g.ny * c, g.nb), kCThreads, CLayout<T, a, b, c>::inv_bytes, st>>>(    \
           S, out, addend, twx, twz, scale, g.err, g.zsol);                                      \
       return cudaGetLastError();                                                                \
     }                                                                                           \
@@ -260,15 +266,16 @@ template size_t cplane_bytes<float>(int, int, int);
 template size_t cplane_bytes<double>(int, int, int);
 template bool cplane_supported<float>(int, int, int);
 template bool cplane_supported<double>(int, int, int);
-template cudaError_t launch_cplane_forward<float>(const TransformGeom &, int, const float *, float2 *,
+template cudaError_t launch_cplane_forward<float>(const TransformGeom &, int, Ptr3<const float *>, Ptr3<float2 *>,
                                                   const float2 *, const float2 *, float, cudaStream_t);
-template cudaError_t launch_cplane_forward<double>(const TransformGeom &, int, const double *, double2 *,
-                                                   const double2 *, const double2 *, double, cudaStream_t);
-template cudaError_t launch_cplane_inverse<float>(const TransformGeom &, int, const float2 *, float *,
-                                                  const float *, const float2 *, const float2 *, float,
+template cudaError_t launch_cplane_forward<double>(const TransformGeom &, int, Ptr3<const double *>,
+                                                   Ptr3<double2 *>, const double2 *, const double2 *, double,
+                                                   cudaStream_t);
+template cudaError_t launch_cplane_inverse<float>(const TransformGeom &, int, Ptr3<float2 *>, Ptr3<float *>,
+                                                  Ptr3<const float *>, const float2 *, const float2 *, float,
                                                   cudaStream_t);
-template cudaError_t launch_cplane_inverse<double>(const TransformGeom &, int, const double2 *, double *,
-                                                   const double *, const double2 *, const double2 *, double,
+template cudaError_t launch_cplane_inverse<double>(const TransformGeom &, int, Ptr3<double2 *>, Ptr3<double *>,
+                                                   Ptr3<const double *>, const double2 *, const double2 *, double,
                                                    cudaStream_t);
 
 }  // namespace ibm

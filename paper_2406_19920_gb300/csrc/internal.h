@@ -14,8 +14,19 @@ namespace ibm {
 // Largest dynamic shared memory a plane kernel may take (bytes).
 constexpr size_t kPlaneSmemLimit = 227 * 1024;
 
+// Up to three fields of one grid moved through the same launches (the
+// three velocity components of a Helmholtz stage); a kernel picks its field
+// by blockIdx.y.
+constexpr int kMaxFields = 3;
+template <typename P> struct Ptr3 {
+  P p[kMaxFields];
+  __host__ __device__ __forceinline__ P operator[](int b) const { return b == 0 ? p[0] : (b == 1 ? p[1] : p[2]); }
+};
+template <typename P> inline Ptr3<P> ptr3(P a, P b = nullptr, P c = nullptr) { return Ptr3<P>{{a, b, c}}; }
+
 struct TransformGeom {
   int nx, ny, nz;
+  int nb;          // fields in the launch (1..kMaxFields)
   int use_plane;   // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane
   int *err;        // device error word for bounded waits
   double *zrhs;    // forward: if set, receives Re S[j][0][0] of every plane (the zero pencil)
@@ -69,33 +80,35 @@ template <typename T> int default_plane_mode(int nx, int ny, int nz);
 // Kernels one forward (or inverse) transform launches: 1 on the plane path, 2 otherwise.
 template <typename T> int transform_launches(const TransformGeom &g);
 
-// Forward: real field [ny][nz][nx] (times in_scale) -> spectrum [ny][nz][nx/2+1].
+// Forward: real field [ny][nz][nx] (times in_scale) -> spectrum [ny][nz][nx/2+1],
+// for fields 0 .. g.nb-1.
 template <typename T>
-cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
+cudaError_t launch_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx<T> *> S, const cplx<T> *twx,
                            const cplx<T> *twz, T in_scale, cudaStream_t st);
 // Inverse: spectrum -> out = addend + scale * field (addend may be NULL or equal out).
 template <typename T>
-cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
-                           const cplx<T> *twz, T scale, cudaStream_t st);
+cudaError_t launch_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> out, Ptr3<const T *> addend,
+                           const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st);
 
 // Split passes: x rows then z columns (forward), z columns then x rows (inverse).
 template <typename T>
-cudaError_t launch_axis_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
+cudaError_t launch_axis_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx<T> *> S, const cplx<T> *twx,
                                 const cplx<T> *twz, T in_scale, cudaStream_t st);
 template <typename T>
-cudaError_t launch_axis_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
-                                const cplx<T> *twz, T scale, cudaStream_t st);
+cudaError_t launch_axis_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> out, Ptr3<const T *> addend,
+                                const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st);
 
 // Cluster plane kernels (C CTAs per y-plane, rows and columns exchanged
 // through distributed shared memory); cudaErrorNotSupported for shapes
 // without an instantiation.
 template <typename T> bool cplane_supported(int nx, int nz, int C);
 template <typename T>
-cudaError_t launch_cplane_forward(const TransformGeom &g, int C, const T *in, cplx<T> *S, const cplx<T> *twx,
-                                  const cplx<T> *twz, T in_scale, cudaStream_t st);
+cudaError_t launch_cplane_forward(const TransformGeom &g, int C, Ptr3<const T *> in, Ptr3<cplx<T> *> S,
+                                  const cplx<T> *twx, const cplx<T> *twz, T in_scale, cudaStream_t st);
 template <typename T>
-cudaError_t launch_cplane_inverse(const TransformGeom &g, int C, const cplx<T> *S, T *out, const T *addend,
-                                  const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st);
+cudaError_t launch_cplane_inverse(const TransformGeom &g, int C, Ptr3<cplx<T> *> S, Ptr3<T *> out,
+                                  Ptr3<const T *> addend, const cplx<T> *twx, const cplx<T> *twz, T scale,
+                                  cudaStream_t st);
 
 // Pencil solve along y (Thomas, excess form), in place on the spectrum.
 struct PencilParams {
@@ -114,9 +127,19 @@ struct PencilParams {
   const double *zrhs;      // zero_mode: right-hand side of the (0,0) pencil, [ny] (from the forward pass)
   double *zsol;            // zero_mode: its FP64 solution, [ny] (read by the inverse pass)
   double inv_ny;           // 1/ny
+  int nb;                  // fields in the launch; field b > 0 takes its wall rows from fbc[b]
+  int fbc[kMaxFields];     // beta_s | beta_e << 4 | j0 << 8 of each field
 };
+// Wall-row parameters of field b (blockIdx.y) of a pencil launch.
+__device__ __forceinline__ void pencil_field(const PencilParams &pp, int b, int &beta_s, int &beta_e, int &j0) {
+  beta_s = pp.beta_s; beta_e = pp.beta_e; j0 = pp.j0;
+  if (b > 0) {
+    const int c = b == 1 ? pp.fbc[1] : pp.fbc[2];
+    beta_s = c & 15; beta_e = (c >> 4) & 15; j0 = c >> 8;
+  }
+}
 template <typename T>
-cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, const T *lamz, double *mean_out,
+cudaError_t launch_pencil(const PencilParams &pp, Ptr3<cplx<T> *> S, const T *lamx, const T *lamz, double *mean_out,
                           cudaStream_t st);
 
 // Residual r = b - (sigma x + tau L x) with float-float arithmetic for FP32.

@@ -218,12 +218,15 @@ __device__ __forceinline__ void gl_backward(cplx<T> *col, long step, const T *wc
 
 template <typename T>
 __global__ void __launch_bounds__(32)
-k_pencil_g(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
+k_pencil_g(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
            double *mean_out) {
+  cplx<T> *__restrict__ S = S_[blockIdx.y];
+  int beta_s, beta_e, j0;
+  pencil_field(pp, blockIdx.y, beta_s, beta_e, j0);
   constexpr int TP = PencilTile<T>::TP;
   constexpr int U = SweepDepth<T>::U;
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const int n = pp.ny - pp.j0;
+  const int n = pp.ny - j0;
   T *ws = reinterpret_cast<T *>(smem_raw);                     // [n][TP]
   double *zs = reinterpret_cast<double *>(ws + (size_t)pp.ny * TP);  // [ny] (zero-mode CTA)
   if (zero_mode_cta(pp, zs, mean_out)) return;
@@ -240,13 +243,13 @@ k_pencil_g(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restr
   const T a = (T)pp.a;
   const T g = (T)pp.g_add + (T)pp.g_mul * (lamx[kx] + lamz[kz]);
   const T sgn = pp.neg_rhs ? (T)-1 : (T)1;
-  cplx<T> *c0 = S + pc + (long)pp.j0 * plane;  // row 0 of the unknowns
+  cplx<T> *c0 = S + pc + (long)j0 * plane;  // row 0 of the unknowns
   const int first = bottom ? n - 1 : 0;
   cplx<T> *col = c0 + (long)first * plane;
   const long step = bottom ? -plane : plane;
   T *wc = ws + first * TP + pl;
   const int wstep = bottom ? -TP : TP;
-  const T e0 = g + a * (T)(bottom ? pp.beta_e : pp.beta_s);
+  const T e0 = g + a * (T)(bottom ? beta_e : beta_s);
   cplx<T> y;
   T q = (T)0;
   if (live) gl_forward<T, U>(col, step, wc, wstep, len, a, g, e0, sgn, y, q);
@@ -270,7 +273,7 @@ k_pencil_g(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restr
   }
   if (!bottom) c0[(long)m * plane] = x;
   gl_backward<T, U>(col, step, wc, wstep, len, x);
-  if (pp.j0 == 1 && !bottom) {
+  if (j0 == 1 && !bottom) {
     cplx<T> z; z.x = (T)0; z.y = (T)0;
     S[p] = z;
   }
@@ -278,12 +281,15 @@ k_pencil_g(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restr
 
 template <typename T>
 __global__ void __launch_bounds__(32)
-k_pencil(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
+k_pencil(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
          double *mean_out) {
+  cplx<T> *__restrict__ S = S_[blockIdx.y];
+  int beta_s, beta_e, j0;
+  pencil_field(pp, blockIdx.y, beta_s, beta_e, j0);
   constexpr int TP = PencilTile<T>::TP;  // pencils per CTA, two lanes each
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int ny = pp.ny;
-  const int n = ny - pp.j0;
+  const int n = ny - j0;
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem_raw);
   cplx<T> *tile = reinterpret_cast<cplx<T> *>(smem_raw + 16);  // [n][TP], rows 16-byte aligned for the bulk copies
   T *ws = reinterpret_cast<T *>(tile + (size_t)n * TP);        // [n][TP]
@@ -294,7 +300,7 @@ k_pencil(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restric
   const int p0 = blockIdx.x * TP;
   const int np = min(TP, npen - p0);  // even: npen is even and p0 a multiple of TP
   const int lane = threadIdx.x;
-  const cplx<T> *src = S + (long)pp.j0 * plane + p0;
+  const cplx<T> *src = S + (long)j0 * plane + p0;
   // rows of the tile arrive by bulk copy (np * 8 or 16 bytes each)
   if (lane == 0) {
     mbar_init(bar, 1);
@@ -321,7 +327,7 @@ k_pencil(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restric
   const int stp = bottom ? -TP : TP;
   cplx<T> *t = tile + first * TP + pl;
   T *wc = ws + first * TP + pl;
-  const T e0 = g + a * (T)(bottom ? pp.beta_e : pp.beta_s);
+  const T e0 = g + a * (T)(bottom ? beta_e : beta_s);
   cplx<T> y;
   T q = (T)0;
   if (live) half_forward<T>(t, stp, wc, len, a, g, e0, sgn, y, q);
@@ -330,7 +336,7 @@ k_pencil(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restric
   const T yo_y = __shfl_xor_sync(0xffffffffu, y.y, 1);
   const T qo = __shfl_xor_sync(0xffffffffu, q, 1);
   if (!live) return;
-  cplx<T> *gcol = S + p + (long)pp.j0 * plane;  // row 0 of the unknowns in the spectrum
+  cplx<T> *gcol = S + p + (long)j0 * plane;  // row 0 of the unknowns in the spectrum
   cplx<T> x;
   {
     const cplx<T> f = tile[m * TP + pl];
@@ -340,7 +346,7 @@ k_pencil(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restric
   }
   if (!bottom) gcol[(long)m * plane] = x;
   half_backward<T>(t, stp, wc, len, x, gcol + (long)first * plane, bottom ? -plane : plane);
-  if (pp.j0 == 1 && !bottom) {
+  if (j0 == 1 && !bottom) {
     cplx<T> z; z.x = (T)0; z.y = (T)0;
     S[p] = z;
   }
@@ -710,8 +716,20 @@ static long resident_ctas(size_t bytes) {
 }
 
 template <typename T>
-cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, const T *lamz, double *mean_out,
+cudaError_t launch_pencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const T *lamx, const T *lamz, double *mean_out,
                           cudaStream_t st) {
+  if (pp.mode == 1 && pp.nb > 1) {
+    // the warp-parallel block solve takes one field per launch
+    for (int b = 0; b < pp.nb; ++b) {
+      PencilParams q = pp;
+      q.nb = 1;
+      if (b > 0) { q.beta_s = pp.fbc[b] & 15; q.beta_e = (pp.fbc[b] >> 4) & 15; q.j0 = pp.fbc[b] >> 8; }
+      cudaError_t e = launch_pencil<T>(q, ptr3<cplx<T> *>(S3[b]), lamx, lamz, mean_out, st);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  }
+  cplx<T> *S = S3[0];
   const int n = pp.ny - pp.j0;
   if (pp.mode == 1) {
     if constexpr (sizeof(T) == 4) {
@@ -728,25 +746,26 @@ cudaError_t launch_pencil(const PencilParams &pp, cplx<T> *S, const T *lamx, con
   constexpr int TP = PencilTile<T>::TP;
   const int npen = pp.nz * pp.P;
   const int grid = ceil_div(npen, TP) + (pp.zero_mode ? 1 : 0);
+  const dim3 g2(grid, pp.nb);
   // the tile kernel while every CTA stays resident (measured faster there);
   // beyond that the tile-less kernel, which keeps about three times as many
   const size_t tb = pencil_smem_bytes<T>(pp.ny);
-  const bool tile = pp.mode == 2 || (pp.mode != 3 && grid <= resident_ctas(tb));
+  const bool tile = pp.mode == 2 || (pp.mode != 3 && (long)grid * pp.nb <= resident_ctas(tb));
   if (tile) {
     cudaError_t e = ensure_max_smem<k_pencil<T>>();
     if (e != cudaSuccess) return e;
-    k_pencil<T><<<grid, 32, tb, st>>>(S, lamx, lamz, pp, mean_out);
+    k_pencil<T><<<g2, 32, tb, st>>>(S3, lamx, lamz, pp, mean_out);
   } else {
     cudaError_t e = ensure_max_smem<k_pencil_g<T>>();
     if (e != cudaSuccess) return e;
-    k_pencil_g<T><<<grid, 32, pencil_g_smem_bytes<T>(pp.ny), st>>>(S, lamx, lamz, pp, mean_out);
+    k_pencil_g<T><<<g2, 32, pencil_g_smem_bytes<T>(pp.ny), st>>>(S3, lamx, lamz, pp, mean_out);
   }
   return cudaGetLastError();
 }
 
-template cudaError_t launch_pencil<float>(const PencilParams &, float2 *, const float *, const float *, double *,
-                                          cudaStream_t);
-template cudaError_t launch_pencil<double>(const PencilParams &, double2 *, const double *, const double *,
+template cudaError_t launch_pencil<float>(const PencilParams &, Ptr3<float2 *>, const float *, const float *,
+                                          double *, cudaStream_t);
+template cudaError_t launch_pencil<double>(const PencilParams &, Ptr3<double2 *>, const double *, const double *,
                                            double *, cudaStream_t);
 
 }  // namespace ibm

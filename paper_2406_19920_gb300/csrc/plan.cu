@@ -42,6 +42,7 @@ int cuda_error(cudaError_t e, const char *what) {
 TransformGeom geom_of(const ibm_plan_s *p) {
   TransformGeom g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
+  g.nb = 1;
   g.use_plane = p->use_plane;
   g.err = p->derr;
   g.zrhs = nullptr;
@@ -103,7 +104,7 @@ static void plan_free(ibm_plan_s *p) {
   if (!p) return;
   for (auto &r : p->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : p->evpool) cudaEventDestroy(e);
-  void *bufs[] = {p->S, p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3],
+  void *bufs[] = {p->S, p->Sx[0], p->Sx[1], p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3],
                   p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -141,16 +142,17 @@ static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out
   const int nl = transform_launches<T>(g);
   {
     ProfScope ps(p, IBM_K_FORWARD, st, nl);
-    IBM_CUDA_TRY(launch_forward<T>(gf, in, S, twx, twz, (T)1, st));
+    IBM_CUDA_TRY(launch_forward<T>(gf, ptr3(in), ptr3(S), twx, twz, (T)1, st));
   }
   {
     ProfScope ps(p, IBM_K_PENCIL, st);
-    IBM_CUDA_TRY(launch_pencil<T>(pp, S, static_cast<const T *>(p->lamx), static_cast<const T *>(p->lamz),
+    IBM_CUDA_TRY(launch_pencil<T>(pp, ptr3(S), static_cast<const T *>(p->lamx), static_cast<const T *>(p->lamz),
                                   mean_out, st));
   }
   {
     ProfScope ps(p, IBM_K_INVERSE, st, nl);
-    IBM_CUDA_TRY(launch_inverse<T>(gi, S, out, addend, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
+    IBM_CUDA_TRY(launch_inverse<T>(gi, ptr3(S), ptr3(out), ptr3(addend), twx, twz,
+                                   (T)(1.0 / ((double)p->nx * p->nz)), st));
   }
   return IBM_OK;
 }
@@ -180,6 +182,7 @@ static PencilParams pencil_params(const ibm_plan_s *p, int kind, double c, int f
   pp.zrhs = p->zbuf;
   pp.zsol = p->zbuf + p->ny;
   pp.inv_ny = 1.0 / p->ny;
+  pp.nb = 1;
   return pp;
 }
 
@@ -246,6 +249,61 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
   return IBM_OK;
 }
 
+template <typename T>
+static int solve_fields_t(ibm_plan_s *p, double c, int nb, const int *field_bc, const T *const *in, T *const *out,
+                          const T *const *addend, cudaStream_t st) {
+  TransformGeom g = geom_of(p);
+  g.nb = nb;
+  g.use_plane = p->use_plane_fields;
+  PencilParams pp = pencil_params(p, 1, c, field_bc[0]);
+  pp.nb = nb;
+  for (int b = 1; b < nb; ++b) {
+    const PencilParams q = pencil_params(p, 1, c, field_bc[b]);
+    pp.fbc[b] = q.beta_s | (q.beta_e << 4) | (q.j0 << 8);
+  }
+  Ptr3<cplx<T> *> S{{static_cast<cplx<T> *>(p->S), static_cast<cplx<T> *>(p->Sx[0]),
+                     static_cast<cplx<T> *>(p->Sx[1])}};
+  Ptr3<const T *> in3{{in[0], nb > 1 ? in[1] : nullptr, nb > 2 ? in[2] : nullptr}};
+  Ptr3<T *> out3{{out[0], nb > 1 ? out[1] : nullptr, nb > 2 ? out[2] : nullptr}};
+  Ptr3<const T *> add3{{addend[0], nb > 1 ? addend[1] : nullptr, nb > 2 ? addend[2] : nullptr}};
+  const cplx<T> *twx = static_cast<const cplx<T> *>(p->twx);
+  const cplx<T> *twz = static_cast<const cplx<T> *>(p->twz);
+  const int nl = transform_launches<T>(g);
+  {
+    ProfScope ps(p, IBM_K_FORWARD, st, nl);
+    IBM_CUDA_TRY(launch_forward<T>(g, in3, S, twx, twz, (T)1, st));
+  }
+  {
+    ProfScope ps(p, IBM_K_PENCIL, st);
+    IBM_CUDA_TRY(launch_pencil<T>(pp, S, static_cast<const T *>(p->lamx), static_cast<const T *>(p->lamz), nullptr,
+                                  st));
+  }
+  {
+    ProfScope ps(p, IBM_K_INVERSE, st, nl);
+    IBM_CUDA_TRY(launch_inverse<T>(g, S, out3, add3, twx, twz, (T)(1.0 / ((double)p->nx * p->nz)), st));
+  }
+  return IBM_OK;
+}
+
+int plan_solve_fields(ibm_plan_s *p, double c, int nb, const int *field_bc, const void *const *in, void *const *out,
+                      const void *const *addend, cudaStream_t st) {
+  if (nb < 1 || nb > kMaxFields) return set_error(IBM_ERR_ARG, "plan_solve_fields: %d fields", nb);
+  for (int b = 0; b + 1 < nb; ++b) {
+    if (!p->Sx[b]) {
+      cudaError_t e = cudaMalloc(&p->Sx[b], p->nspec * 2 * p->esz);
+      if (e != cudaSuccess) { p->Sx[b] = nullptr; return cuda_error(e, "field spectrum"); }
+      p->bytes += p->nspec * 2 * p->esz;
+    }
+  }
+  if (p->precision == IBM_FP64)
+    return solve_fields_t<double>(p, c, nb, field_bc, reinterpret_cast<const double *const *>(in),
+                                  reinterpret_cast<double *const *>(out),
+                                  reinterpret_cast<const double *const *>(addend), st);
+  return solve_fields_t<float>(p, c, nb, field_bc, reinterpret_cast<const float *const *>(in),
+                               reinterpret_cast<float *const *>(out), reinterpret_cast<const float *const *>(addend),
+                               st);
+}
+
 int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, void *out, const void *addend,
                cudaStream_t st, ibm_info *info) {
   if (p->precision == IBM_FP64)
@@ -305,6 +363,22 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   // mode m (0 split passes, 1 one CTA per plane, 2/4/8 cluster) and fails
   // the plan when the shape has no such mode (A/B timing and tests)
   p->use_plane = precision == IBM_FP64 ? default_plane_mode<double>(nx, ny, nz) : default_plane_mode<float>(nx, ny, nz);
+  // three-field solves: split passes (their small CTAs share the SMs
+  // between fields); IBM_PLANE_MODE_FIELDS=m forces another mode
+  p->use_plane_fields = 0;
+  if (const char *pm = getenv("IBM_PLANE_MODE_FIELDS")) {
+    int modes[8];
+    const int n = precision == IBM_FP64 ? plane_modes<double>(nx, nz, modes) : plane_modes<float>(nx, nz, modes);
+    const int want = atoi(pm);
+    bool found = false;
+    for (int i = 0; i < n; ++i) found |= modes[i] == want;
+    if (!found) {
+      delete p;
+      return set_error(IBM_ERR_UNSUPPORTED, "ibm_plan_create: IBM_PLANE_MODE_FIELDS=%d not available for %dx%d planes",
+                       want, nx, nz);
+    }
+    p->use_plane_fields = want;
+  }
   if (const char *pm = getenv("IBM_PLANE_MODE")) {
     int modes[8];
     const int n = precision == IBM_FP64 ? plane_modes<double>(nx, nz, modes) : plane_modes<float>(nx, nz, modes);

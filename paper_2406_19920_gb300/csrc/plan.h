@@ -33,10 +33,12 @@ struct ibm_plan_s {
   int delta;         // IBM_DELTA_*
   int pencil_mode;   // 0 auto, 1 warp-parallel block solve, 2 tile sweep, 3 streaming sweep
   int use_plane = 1; // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane
+  int use_plane_fields = 0; // plane mode of three-field solves
   size_t esz;        // element size: 4 or 8
   size_t npts;       // nx * ny * nz
   size_t nspec;      // ny * nz * P complex entries
   void *S;           // spectrum workspace
+  void *Sx[2];       // spectra of fields 1 and 2 of a three-field solve (allocated on first use)
   void *work;        // real work field (residual / divergence)
   void *bsave;       // copy of an in-place right-hand side
   void *sub[4];      // substep fields du, dv, dw, phi (allocated on first substep)
@@ -78,6 +80,12 @@ TransformGeom geom_of(const ibm_plan_s *p);
 // out may equal in.  addend (nullable) is added to the result: out = addend + x.
 int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, void *out, const void *addend,
                cudaStream_t st, ibm_info *info);
+// nb <= 3 Helmholtz solves (I - c L) x_b = in_b of one grid in the same
+// launches, field b with boundary kind field_bc[b]: out_b = addend_b + x_b
+// (no refinement: the increment form keeps the FP32 error relative to the
+// addend).  Allocates the extra spectra on first use.
+int plan_solve_fields(ibm_plan_s *p, double c, int nb, const int *field_bc, const void *const *in, void *const *out,
+                      const void *const *addend, cudaStream_t st);
 
 // Autotuner result for one shape (batch.cu).
 struct TuneChoice {

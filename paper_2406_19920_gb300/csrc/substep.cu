@@ -307,10 +307,15 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
       IBM_CUDA_TRY(launch_spread<T>(p, nmk, (const T *)mk->X, F, (const T *)mk->dV, du, dv, dw, dt, st));
     }
   }
-  // S1: Helmholtz, increment form, u* written over u
-  if ((rc = plan_solve(p, 1, cH, IBM_FIELD_CELL_DIRICHLET, du, u, u, st, nullptr))) return rc;
-  if ((rc = plan_solve(p, 1, cH, IBM_FIELD_FACE_DIRICHLET, dv, v, v, st, nullptr))) return rc;
-  if ((rc = plan_solve(p, 1, cH, IBM_FIELD_CELL_DIRICHLET, dw, w, w, st, nullptr))) return rc;
+  // S1: Helmholtz, increment form, u* written over u; the three components
+  // go through the same launches
+  {
+    const int bcs[3] = {IBM_FIELD_CELL_DIRICHLET, IBM_FIELD_FACE_DIRICHLET, IBM_FIELD_CELL_DIRICHLET};
+    const void *in3[3] = {du, dv, dw};
+    void *out3[3] = {u, v, w};
+    const void *add3[3] = {u, v, w};
+    if ((rc = plan_solve_fields(p, cH, 3, bcs, in3, out3, add3, st))) return rc;
+  }
   // E2
   const ff fx = ff_host(g.ihx), fy = ff_host(g.ihy), fz = ff_host(g.ihz);
   {

@@ -52,8 +52,10 @@ template <typename T, int NX, int NZ> struct PlaneCfg {
 
 template <typename T, int NX, int NZ>
 __global__ void __launch_bounds__(kPlaneThreads)
-k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__restrict__ twx,
+k_plane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ twx,
             const cplx<T> *__restrict__ twz, T in_scale, double *zrhs) {
+  const T *__restrict__ in = in_[blockIdx.y];
+  cplx<T> *__restrict__ S = S_[blockIdx.y];
   using Cfg = PlaneCfg<T, NX, NZ>;
   constexpr int P = Cfg::P, N1X = Cfg::N1X, XPITCH = Cfg::XPITCH, CP = Cfg::CP, CW = Cfg::CW;
   constexpr int N1Z = TwoStep<NZ>::N1, N2Z = TwoStep<NZ>::N2, J3 = Cfg::N2X / 2 + 1;
@@ -105,8 +107,11 @@ k_plane_fwd(const T *__restrict__ in, cplx<T> *__restrict__ S, const cplx<T> *__
 // Inverse: spectrum plane -> out = addend + scale * result.
 template <typename T, int NX, int NZ>
 __global__ void __launch_bounds__(kPlaneThreads)
-k_plane_inv(const cplx<T> *__restrict__ S, T *out, const T *addend, const cplx<T> *__restrict__ twx,
+k_plane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<T> *__restrict__ twx,
             const cplx<T> *__restrict__ twz, T scale, const double *zsol) {
+  const cplx<T> *__restrict__ S = S_[blockIdx.y];
+  T *out = out_[blockIdx.y];
+  const T *addend = add_[blockIdx.y];
   using Cfg = PlaneCfg<T, NX, NZ>;
   constexpr int P = Cfg::P, N1X = Cfg::N1X, N2X = Cfg::N2X, XPITCH = Cfg::XPITCH, CP = Cfg::CP, CW = Cfg::CW;
   constexpr int N1Z = TwoStep<NZ>::N1, N2Z = TwoStep<NZ>::N2;
@@ -174,7 +179,7 @@ template <typename T> static bool plane_supported(int nx, int nz) {
 }
 
 template <typename T>
-cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, const cplx<T> *twx,
+cudaError_t launch_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx<T> *> S, const cplx<T> *twx,
                            const cplx<T> *twz, T in_scale, cudaStream_t st) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
@@ -184,7 +189,7 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
   if (nx == a && nz == b) {                                                                      \
     if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
       { cudaError_t e = ensure_max_smem<k_plane_fwd<T, a, b>>(); if (e) return e; }              \
-      k_plane_fwd<T, a, b><<<ny, kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(in, S, twx, twz, in_scale, g.zrhs); \
+      k_plane_fwd<T, a, b><<<dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(in, S, twx, twz, in_scale, g.zrhs); \
       return cudaGetLastError();                                                                 \
     }                                                                                            \
   }
@@ -196,8 +201,8 @@ cudaError_t launch_forward(const TransformGeom &g, const T *in, cplx<T> *S, cons
 }
 
 template <typename T>
-cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *addend, const cplx<T> *twx,
-                           const cplx<T> *twz, T scale, cudaStream_t st) {
+cudaError_t launch_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> out, Ptr3<const T *> addend,
+                           const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
     return launch_cplane_inverse<T>(g, g.use_plane, S, out, addend, twx, twz, scale, st);
@@ -206,7 +211,7 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
   if (nx == a && nz == b) {                                                                      \
     if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
       { cudaError_t e = ensure_max_smem<k_plane_inv<T, a, b>>(); if (e) return e; }              \
-      k_plane_inv<T, a, b><<<ny, kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(S, out, addend, twx, twz, scale, g.zsol); \
+      k_plane_inv<T, a, b><<<dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(S, out, addend, twx, twz, scale, g.zsol); \
       return cudaGetLastError();                                                                 \
     }                                                                                            \
   }
@@ -216,14 +221,15 @@ cudaError_t launch_inverse(const TransformGeom &g, cplx<T> *S, T *out, const T *
   return launch_axis_inverse<T>(g, S, out, addend, twx, twz, scale, st);
 }
 
-template cudaError_t launch_forward<float>(const TransformGeom &, const float *, float2 *, const float2 *,
+template cudaError_t launch_forward<float>(const TransformGeom &, Ptr3<const float *>, Ptr3<float2 *>, const float2 *,
                                            const float2 *, float, cudaStream_t);
-template cudaError_t launch_forward<double>(const TransformGeom &, const double *, double2 *, const double2 *,
-                                            const double2 *, double, cudaStream_t);
-template cudaError_t launch_inverse<float>(const TransformGeom &, float2 *, float *, const float *,
-                                           const float2 *, const float2 *, float, cudaStream_t);
-template cudaError_t launch_inverse<double>(const TransformGeom &, double2 *, double *, const double *,
+template cudaError_t launch_forward<double>(const TransformGeom &, Ptr3<const double *>, Ptr3<double2 *>,
                                             const double2 *, const double2 *, double, cudaStream_t);
+template cudaError_t launch_inverse<float>(const TransformGeom &, Ptr3<float2 *>, Ptr3<float *>, Ptr3<const float *>,
+                                           const float2 *, const float2 *, float, cudaStream_t);
+template cudaError_t launch_inverse<double>(const TransformGeom &, Ptr3<double2 *>, Ptr3<double *>,
+                                            Ptr3<const double *>, const double2 *, const double2 *, double,
+                                            cudaStream_t);
 
 template <typename T> int transform_launches(const TransformGeom &g) {
   if (g.use_plane >= 2) return cplane_supported<T>(g.nx, g.nz, g.use_plane) ? 1 : 2;

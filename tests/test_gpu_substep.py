@@ -14,6 +14,7 @@ sides see identical coordinates.
 """
 
 import math
+import os
 
 import numpy as np
 import pytest
@@ -99,6 +100,33 @@ def test_substep_matches_oracle(shape, stage, prec):
     lim = 1e-11 if prec == ibm.IBM_FP64 else 1e-5
     assert got["info"]["div_max"] <= lim * max(1.0, d0), (got["info"], d0)
     assert abs(got["info"]["div_before"] - d0) <= 1e-3 * d0
+
+
+@pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
+def test_three_field_helmholtz_every_kernel(prec):
+    """The three Helmholtz solves of a stage share launches; every plane mode
+    of those launches (split, one CTA per plane, 2-CTA cluster) and every
+    pencil kernel gives the oracle's stage."""
+    nx, ny, nz = 64, 24, 64
+    npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
+    dt_t = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+    tol = TOL_STAGE_FP64 if prec == ibm.IBM_FP64 else TOL_STAGE_FP32
+    g, (u, v, w, p), Np, X0, dV = _setup(nx, ny, nz, 300, npdt, wl=37)
+    dt, nu = 1e-3, 1e-2
+    params = (0.1, 0.0, 0.0)
+    st = dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
+    ref, _ = O.rk_stage(st, dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=params), 2, dt, nu, g)
+    for plane_mode, pencil_mode in ((0, 2), (0, 3), (1, 2), (2, 3), (0, 1)):
+        os.environ["IBM_PLANE_MODE_FIELDS"] = str(plane_mode)
+        os.environ["IBM_PENCIL_MODE"] = str(pencil_mode)
+        try:
+            got = _run_gpu(g, [u, v, w, p], Np, X0, dV, 2, dt, nu, ibm.IBM_MOTION_TRANSLATE, params, prec, dt_t, 0.0)
+        finally:
+            del os.environ["IBM_PLANE_MODE_FIELDS"]
+            del os.environ["IBM_PENCIL_MODE"]
+        errs = {k: rel_l2(got[k], ref[k]) for k in ("u", "v", "w", "p")}
+        assert max(errs.values()) <= tol, (plane_mode, pencil_mode, errs)
+        assert np.all(got["v"][0] == 0.0)
 
 
 @pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
