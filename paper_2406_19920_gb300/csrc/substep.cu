@@ -55,113 +55,161 @@ template <typename T> struct F3 {
   }
 };
 
-// E1: one thread per cell index (j, k, i), all three components.
+// E1, all three components.  A CTA owns a TX x TZ column tile and marches
+// up JC planes of y; the planes j-1, j, j+1 of u, v, w (and j of p) sit in a
+// shared-memory ring with a one-cell periodic halo in x and z, so every
+// field is read from HBM about once (plus halo and the two extra planes per
+// chunk) and every stencil point comes from shared memory.  Wall rules in
+// y: u, w cell-centred with the no-slip ghost (-value) in the Laplacian and
+// zero wall flux in the advective y-flux; v on faces, zero at the walls
+// (j = 0 stored as the wall, j = ny not stored).
+constexpr int kExTX = 32, kExTZ = 8, kExJC = 16;
+
 template <typename T>
-__global__ void __launch_bounds__(128)
+__global__ void __launch_bounds__(kExTX * kExTZ)
 k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_,
            const T *__restrict__ p_, T *Nu, T *Nv, T *Nw, T *__restrict__ du, T *__restrict__ dv,
            T *__restrict__ dw, T c_visc, T c_pres, T gam, T zet, T dt) {
-  int i, k, j;
-  if (!stencil_index(g.nx, g.nz, i, k, j)) return;
-  const size_t idx = ((size_t)j * g.nz + k) * g.nx + i;
-  const int ny = g.ny;
-  const F3<T> U{u_, g.nx, g.nz}, V{v_, g.nx, g.nz}, W{w_, g.nx, g.nz}, Pp{p_, g.nx, g.nz};
-  const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
-  const T h = (T)0.5;
-  // wall-aware accessors: u, w cell-centred (no-slip ghost = -value), v faces (walls 0)
-  auto uy = [&](const F3<T> &F, int jj, int kk, int ii) -> T {
-    if (jj < 0) return -F.at(0, kk, ii);
-    if (jj >= ny) return -F.at(ny - 1, kk, ii);
-    return F.at(jj, kk, ii);
+  constexpr int TX = kExTX, TZ = kExTZ, HX = TX + 2, HZ = TZ + 2, PL = HX * HZ, NT = TX * TZ;
+  constexpr int NL = (PL + NT - 1) / NT;  // plane elements each thread loads
+  __shared__ T su[3][PL], sv[3][PL], sw[3][PL], sp[2][PL];
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TX + tx;
+  const int i0 = blockIdx.x * TX, k0 = blockIdx.y * TZ;
+  const int jb = blockIdx.z * kExJC, je = min(ny, jb + kExJC);
+  const size_t plane = (size_t)nz * nx;
+  // halo-tile element -> offset inside a plane (periodic x, z), fixed for all planes
+  int off[NL];
+#pragma unroll
+  for (int q = 0; q < NL; ++q) {
+    const int e = tid + q * NT;
+    const int hz = e / HX, hx = e - hz * HX;
+    const int kk = ((k0 - 1 + hz) % nz + nz) % nz, ii = ((i0 - 1 + hx) % nx + nx) % nx;
+    off[q] = e < PL ? kk * nx + ii : -1;
+  }
+  // a plane's tile elements of this thread: fetched into registers one
+  // iteration ahead, stored into the ring after the iteration's compute
+  auto fetch = [&](const T *F, int jj, T (&r)[NL]) {
+    const bool ok = jj >= 0 && jj < ny;
+    const T *src = F + (size_t)(ok ? jj : 0) * plane;
+#pragma unroll
+    for (int q = 0; q < NL; ++q) r[q] = (ok && off[q] >= 0) ? src[off[q]] : (T)0;
   };
-  auto vy = [&](int jj, int kk, int ii) -> T { return (jj <= 0 || jj >= ny) ? (T)0 : V.at(jj, kk, ii); };
-
-  // ---------------- u (x-faces) ----------------
+  auto put = [&](const T (&r)[NL], T *buf) {
+#pragma unroll
+    for (int q = 0; q < NL; ++q)
+      if (off[q] >= 0) buf[tid + q * NT] = r[q];
+  };
+  auto slot = [](int jj) { return ((jj % 3) + 3) % 3; };
   {
-    const T u0 = U.at(j, k, i);
-    const T lap = (U.at(j, k, i + 1) - 2 * u0 + U.at(j, k, i - 1)) * ihx * ihx +
-                  (U.at(j, k + 1, i) - 2 * u0 + U.at(j, k - 1, i)) * ihz * ihz +
-                  (uy(U, j + 1, k, i) - 2 * u0 + uy(U, j - 1, k, i)) * ihy * ihy;
-    const T uc = h * (u0 + U.at(j, k, i + 1)), ucm = h * (U.at(j, k, i - 1) + u0);
-    const T tx = (uc * uc - ucm * ucm) * ihx;
-    T fy[2];
-    for (int q = 0; q < 2; ++q) {
-      const int jj = j + q;
-      const T ve = h * (vy(jj, k, i - 1) + vy(jj, k, i));
-      const T ue = (jj <= 0 || jj >= ny) ? (T)0 : h * (U.at(jj - 1, k, i) + U.at(jj, k, i));
-      fy[q] = ve * ue;
+    T r[NL];
+    for (int jj = jb - 1; jj <= jb + 1; ++jj) {
+      fetch(u_, jj, r); put(r, su[slot(jj)]);
+      fetch(v_, jj, r); put(r, sv[slot(jj)]);
+      fetch(w_, jj, r); put(r, sw[slot(jj)]);
     }
-    T fz[2];
-    for (int q = 0; q < 2; ++q) {
-      const int kk = k + q;
-      const T we = h * (W.at(j, kk, i - 1) + W.at(j, kk, i));
-      const T ue = h * (U.at(j, kk - 1, i) + U.at(j, kk, i));
-      fz[q] = we * ue;
-    }
-    const T N = tx + (fy[1] - fy[0]) * ihy + (fz[1] - fz[0]) * ihz;
-    const T G = (Pp.at(j, k, i) - Pp.at(j, k, i - 1)) * ihx;
-    const T np = zet != (T)0 ? Nu[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
-    du[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
-    Nu[idx] = N;
+    fetch(p_, jb, r); put(r, sp[jb & 1]);
   }
-  // ---------------- w (z-faces) ----------------
-  {
-    const T w0 = W.at(j, k, i);
-    const T lap = (W.at(j, k, i + 1) - 2 * w0 + W.at(j, k, i - 1)) * ihx * ihx +
-                  (W.at(j, k + 1, i) - 2 * w0 + W.at(j, k - 1, i)) * ihz * ihz +
-                  (uy(W, j + 1, k, i) - 2 * w0 + uy(W, j - 1, k, i)) * ihy * ihy;
-    const T wc = h * (w0 + W.at(j, k + 1, i)), wcm = h * (W.at(j, k - 1, i) + w0);
-    const T tz = (wc * wc - wcm * wcm) * ihz;
-    T fx[2];
-    for (int q = 0; q < 2; ++q) {
-      const int ii = i + q;
-      const T ue = h * (U.at(j, k - 1, ii) + U.at(j, k, ii));
-      const T we = h * (W.at(j, k, ii - 1) + W.at(j, k, ii));
-      fx[q] = ue * we;
+  __syncthreads();
+  const int i = i0 + tx, k = k0 + tz;
+  const bool inside = i < nx && k < nz;
+  const int c = (tz + 1) * HX + (tx + 1);  // this column in a halo tile
+  T p_prev = (inside && jb > 0) ? p_[(size_t)(jb - 1) * plane + (size_t)k * nx + i] : (T)0;
+  const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
+  const T ihx2 = ihx * ihx, ihy2 = ihy * ihy, ihz2 = ihz * ihz;
+  const T h = (T)0.5;
+  for (int j = jb; j < je; ++j) {
+    T ru[NL], rv[NL], rw[NL], rp[NL];
+    const bool more = j + 1 < je;
+    if (more) {
+      fetch(u_, j + 2, ru);
+      fetch(v_, j + 2, rv);
+      fetch(w_, j + 2, rw);
+      fetch(p_, j + 1, rp);
     }
-    T fy[2];
-    for (int q = 0; q < 2; ++q) {
-      const int jj = j + q;
-      const T ve = h * (vy(jj, k - 1, i) + vy(jj, k, i));
-      const T we = (jj <= 0 || jj >= ny) ? (T)0 : h * (W.at(jj - 1, k, i) + W.at(jj, k, i));
-      fy[q] = ve * we;
+    const T *sp_ = sp[j & 1];
+    if (inside) {
+      const T *Um = su[slot(j - 1)], *Uc = su[slot(j)], *Up = su[slot(j + 1)];
+      const T *Vm = sv[slot(j - 1)], *Vc = sv[slot(j)], *Vp = sv[slot(j + 1)];
+      const T *Wm = sw[slot(j - 1)], *Wc = sw[slot(j)], *Wp = sw[slot(j + 1)];
+      const bool lo = j == 0, hi = j + 1 >= ny;
+      const size_t idx = (size_t)j * plane + (size_t)k * nx + i;
+      // tile neighbours: (dk, di) relative to this column
+      auto at = [&](const T *B, int dk, int di) { return B[c + dk * HX + di]; };
+      // v on the faces of plane jj: zero at the walls jj <= 0 and jj >= ny
+      const T p0 = sp_[c];
+      // ---------------- u (x-faces) ----------------
+      {
+        const T u0 = at(Uc, 0, 0), ue = at(Uc, 0, 1), uw = at(Uc, 0, -1);
+        const T un = at(Uc, 1, 0), us = at(Uc, -1, 0);
+        const T uu = hi ? -u0 : at(Up, 0, 0), ud = lo ? -u0 : at(Um, 0, 0);
+        const T lap = (ue - 2 * u0 + uw) * ihx2 + (un - 2 * u0 + us) * ihz2 + (uu - 2 * u0 + ud) * ihy2;
+        const T uc = h * (u0 + ue), ucm = h * (uw + u0);
+        const T txx = (uc * uc - ucm * ucm) * ihx;
+        // y-flux at the faces j (q = 0) and j+1 (q = 1)
+        const T v0w = lo ? (T)0 : at(Vc, 0, -1), v0c = lo ? (T)0 : at(Vc, 0, 0);
+        const T v1w = hi ? (T)0 : at(Vp, 0, -1), v1c = hi ? (T)0 : at(Vp, 0, 0);
+        const T fy0 = lo ? (T)0 : (h * (v0w + v0c)) * (h * (at(Um, 0, 0) + u0));
+        const T fy1 = hi ? (T)0 : (h * (v1w + v1c)) * (h * (u0 + at(Up, 0, 0)));
+        const T fz0 = (h * (at(Wc, 0, -1) + at(Wc, 0, 0))) * (h * (us + u0));
+        const T fz1 = (h * (at(Wc, 1, -1) + at(Wc, 1, 0))) * (h * (u0 + un));
+        const T N = txx + (fy1 - fy0) * ihy + (fz1 - fz0) * ihz;
+        const T G = (p0 - sp_[c - 1]) * ihx;
+        const T np = zet != (T)0 ? Nu[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
+        du[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
+        Nu[idx] = N;
+      }
+      // ---------------- w (z-faces) ----------------
+      {
+        const T w0 = at(Wc, 0, 0), we = at(Wc, 0, 1), ww = at(Wc, 0, -1);
+        const T wn = at(Wc, 1, 0), ws = at(Wc, -1, 0);
+        const T wu = hi ? -w0 : at(Wp, 0, 0), wd = lo ? -w0 : at(Wm, 0, 0);
+        const T lap = (we - 2 * w0 + ww) * ihx2 + (wn - 2 * w0 + ws) * ihz2 + (wu - 2 * w0 + wd) * ihy2;
+        const T wc = h * (w0 + wn), wcm = h * (ws + w0);
+        const T tzz = (wc * wc - wcm * wcm) * ihz;
+        const T fx0 = (h * (at(Uc, -1, 0) + at(Uc, 0, 0))) * (h * (ww + w0));
+        const T fx1 = (h * (at(Uc, -1, 1) + at(Uc, 0, 1))) * (h * (w0 + we));
+        const T v0s = lo ? (T)0 : at(Vc, -1, 0), v0c = lo ? (T)0 : at(Vc, 0, 0);
+        const T v1s = hi ? (T)0 : at(Vp, -1, 0), v1c = hi ? (T)0 : at(Vp, 0, 0);
+        const T fy0 = lo ? (T)0 : (h * (v0s + v0c)) * (h * (at(Wm, 0, 0) + w0));
+        const T fy1 = hi ? (T)0 : (h * (v1s + v1c)) * (h * (w0 + at(Wp, 0, 0)));
+        const T N = tzz + (fx1 - fx0) * ihx + (fy1 - fy0) * ihy;
+        const T G = (p0 - sp_[c - HX]) * ihz;
+        const T np = zet != (T)0 ? Nw[idx] : (T)0;
+        dw[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
+        Nw[idx] = N;
+      }
+      // ---------------- v (y-faces, interior j = 1..ny-1) ----------------
+      if (lo) {
+        dv[idx] = (T)0;
+        Nv[idx] = (T)0;
+      } else {
+        const T v0 = at(Vc, 0, 0), ve = at(Vc, 0, 1), vw = at(Vc, 0, -1);
+        const T vn = at(Vc, 1, 0), vs = at(Vc, -1, 0);
+        const T vu = hi ? (T)0 : at(Vp, 0, 0), vd = j - 1 <= 0 ? (T)0 : at(Vm, 0, 0);
+        const T lap = (ve - 2 * v0 + vw) * ihx2 + (vn - 2 * v0 + vs) * ihz2 + (vu - 2 * v0 + vd) * ihy2;
+        const T vc = h * (v0 + vu), vcm = h * (vd + v0);
+        const T tyy = (vc * vc - vcm * vcm) * ihy;
+        const T fx0 = (h * (at(Um, 0, 0) + at(Uc, 0, 0))) * (h * (vw + v0));
+        const T fx1 = (h * (at(Um, 0, 1) + at(Uc, 0, 1))) * (h * (v0 + ve));
+        const T fz0 = (h * (at(Wm, 0, 0) + at(Wc, 0, 0))) * (h * (vs + v0));
+        const T fz1 = (h * (at(Wm, 1, 0) + at(Wc, 1, 0))) * (h * (v0 + vn));
+        const T N = tyy + (fx1 - fx0) * ihx + (fz1 - fz0) * ihz;
+        const T G = (p0 - p_prev) * ihy;
+        const T np = zet != (T)0 ? Nv[idx] : (T)0;
+        dv[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
+        Nv[idx] = N;
+      }
+      p_prev = p0;
     }
-    const T N = tz + (fx[1] - fx[0]) * ihx + (fy[1] - fy[0]) * ihy;
-    const T G = (Pp.at(j, k, i) - Pp.at(j, k - 1, i)) * ihz;
-    const T np = zet != (T)0 ? Nw[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
-    dw[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
-    Nw[idx] = N;
-  }
-  // ---------------- v (y-faces, interior j = 1..ny-1) ----------------
-  if (j == 0) {
-    dv[idx] = (T)0;
-    Nv[idx] = (T)0;
-  } else {
-    const T v0 = V.at(j, k, i);
-    const T lap = (V.at(j, k, i + 1) - 2 * v0 + V.at(j, k, i - 1)) * ihx * ihx +
-                  (V.at(j, k + 1, i) - 2 * v0 + V.at(j, k - 1, i)) * ihz * ihz +
-                  (vy(j + 1, k, i) - 2 * v0 + vy(j - 1, k, i)) * ihy * ihy;
-    const T vc = h * (v0 + vy(j + 1, k, i)), vcm = h * (vy(j - 1, k, i) + v0);
-    const T ty = (vc * vc - vcm * vcm) * ihy;
-    T fx[2];
-    for (int q = 0; q < 2; ++q) {
-      const int ii = i + q;
-      const T ue = h * (U.at(j - 1, k, ii) + U.at(j, k, ii));
-      const T ve = h * (V.at(j, k, ii - 1) + V.at(j, k, ii));
-      fx[q] = ue * ve;
+    __syncthreads();
+    if (more) {
+      put(ru, su[slot(j + 2)]);
+      put(rv, sv[slot(j + 2)]);
+      put(rw, sw[slot(j + 2)]);
+      put(rp, sp[(j + 1) & 1]);
+      __syncthreads();
     }
-    T fz[2];
-    for (int q = 0; q < 2; ++q) {
-      const int kk = k + q;
-      const T we = h * (W.at(j - 1, kk, i) + W.at(j, kk, i));
-      const T ve = h * (V.at(j, kk - 1, i) + V.at(j, kk, i));
-      fz[q] = we * ve;
-    }
-    const T N = ty + (fx[1] - fx[0]) * ihx + (fz[1] - fz[0]) * ihz;
-    const T G = (Pp.at(j, k, i) - Pp.at(j - 1, k, i)) * ihy;
-    const T np = zet != (T)0 ? Nv[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
-    dv[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
-    Nv[idx] = N;
   }
 }
 
@@ -285,7 +333,8 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   // E1
   {
     ProfScope ps(p, IBM_K_EXPLICIT, st);
-    k_explicit<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
+    const dim3 eg(ceil_div(p->nx, kExTX), ceil_div(p->nz, kExTZ), ceil_div(p->ny, kExJC));
+    k_explicit<T><<<eg, dim3(kExTX, kExTZ), 0, st>>>(g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
                                           (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt);
     IBM_CUDA_TRY(cudaGetLastError());
   }
