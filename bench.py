@@ -42,10 +42,18 @@ NX = NY = NZ = 128
 N_MARKERS = 20000
 DT, NU = 1e-3, 1e-2
 N_STATES = 4
-KERNEL_SOURCES = {"forward": "transforms.cu", "inverse": "transforms.cu", "pencil": "pencil.cu",
-                  "residual": "stencil.cu", "explicit": "substep.cu", "divergence": "substep.cu",
-                  "project": "substep.cu", "interp": "ibm_kernels.cu", "spread": "ibm_kernels.cu",
-                  "motion": "ibm_kernels.cu"}
+KERNEL_SOURCES = {"forward": ("transforms.cu", "axis.cu", "fft2.cuh"),
+                  "inverse": ("transforms.cu", "axis.cu", "fft2.cuh"), "pencil": ("pencil.cu",),
+                  "residual": ("stencil.cu",), "explicit": ("substep.cu",), "divergence": ("substep.cu",),
+                  "project": ("substep.cu",), "interp": ("ibm_kernels.cu",), "spread": ("ibm_kernels.cu",),
+                  "motion": ("ibm_kernels.cu",)}
+# kernel-name prefix -> kind (the names ncu prints)
+KERNEL_KIND = (("k_plane_fwd", "forward"), ("k_rows_fwd", "forward"), ("k_cplane_fwd", "forward"),
+               ("k_plane_inv", "inverse"), ("k_rows_inv", "inverse"), ("k_cplane_inv", "inverse"),
+               ("k_pencil", "pencil"), ("k_residual", "residual"), ("k_explicit", "explicit"),
+               ("k_divergence", "divergence"), ("k_project", "project"), ("k_interp", "interp"),
+               ("k_spread", "spread"), ("k_motion", "motion"))
+WORKLOAD = "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere"
 
 
 def workload_grid():
@@ -137,14 +145,16 @@ def measured_peak():
 
 
 def source_digest(kind):
-    p = os.path.join(ROOT, "paper_2406_19920_gb300", "csrc", KERNEL_SOURCES[kind])
-    with open(p, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kind]:
+        with open(os.path.join(ROOT, "paper_2406_19920_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
 
 
 def ncu_traffic(kind, workload):
-    """DRAM bytes per launch from the committed ncu summary, if the kernel
-    source is unchanged since the capture; else None."""
+    """DRAM bytes per step of a kernel kind from the committed ncu summary,
+    if its sources are unchanged since the capture; else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
@@ -154,27 +164,31 @@ def ncu_traffic(kind, workload):
     e = d.get(kind)
     if not e or e.get("workload") != workload or e.get("source_sha256_16") != source_digest(kind):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get("dram_bytes_per_step")
 
 
-def algorithmic_bytes(kind, launches_per_step, esz=4):
-    """Compulsory HBM bytes per launch of each kernel kind at the workload.
+def algorithmic_bytes(kind, esz=4):
+    """Compulsory HBM bytes per step (one RK stage) of each kernel kind.
 
-    pts = nx ny nz real points; spec = ny nz (nx/2+1) complex entries.
-    forward: read field + write spectrum; inverse: read spectrum + write field
-    (+ read the added field for 4 of the 5 inverse launches of a stage:
-    three Helmholtz increments and the refinement update); pencil: read +
-    write spectrum; residual: read b, x, write r; explicit: read u,v,w,p,
-    N x3, write du,dv,dw, N x3; divergence: read u,v,w, write b; project: read
-    u,v,w,p,phi, write u,v,w,p.
+    pts = nx ny nz real points; spec = ny nz (nx/2+1) complex entries.  A
+    stage transforms five fields each way: the three Helmholtz increments
+    (one shared launch set) and the Poisson solve plus its refinement.
+    forward: read field + write spectrum, x5; inverse: read spectrum + write
+    field, x5, plus the added field of the three Helmholtz increments and of
+    the refinement update; pencil: read + write spectrum, x5; residual: read
+    b, x, write r; explicit: read u,v,w,p, N x3, write du,dv,dw, N x3;
+    divergence: read u,v,w, write b; project: read u,v,w,p,phi, write
+    u,v,w,p; markers: positions, weights, 27-point stencils of 3 components.
+    The spectrum round trip between the split x and z passes is not counted
+    (it is not compulsory: the one-CTA plane kernels avoid it).
     """
     pts = NX * NY * NZ
     spec = NY * NZ * (NX // 2 + 1)
     cs = 2 * esz
     table = {
-        "forward": pts * esz + spec * cs,
-        "inverse": spec * cs + pts * esz + pts * esz * 4.0 / 5.0,
-        "pencil": 2 * spec * cs,
+        "forward": 5 * (pts * esz + spec * cs),
+        "inverse": 5 * (spec * cs + pts * esz) + 4 * pts * esz,
+        "pencil": 5 * 2 * spec * cs,
         "residual": 3 * pts * esz,
         "explicit": 13 * pts * esz,
         "divergence": 4 * pts * esz,
@@ -184,6 +198,64 @@ def algorithmic_bytes(kind, launches_per_step, esz=4):
         "motion": N_MARKERS * (3 + 6) * esz,
     }
     return table.get(kind)
+
+
+def kernel_kind(name):
+    name = name.replace("void ", "", 1).replace("ibm::", "")
+    if name.startswith("k_cols<"):  # k_cols<T, N, INV>
+        return "inverse" if name.split(">")[0].split(",")[-1].strip() in ("true", "1") else "forward"
+    for prefix, kind in KERNEL_KIND:
+        if name.startswith(prefix):
+            return kind
+    return None
+
+
+def ncu_summary(csv_path, steps):
+    """Per-kind launches, device time and DRAM bytes per step from an ncu
+    --csv launch list of `bench.py --quick` (profiler region = the timed
+    steps); writes profiles/dram_traffic.json and prints a markdown table."""
+    import csv
+    rows = []
+    with open(csv_path) as f:
+        lines = [ln for ln in f if ln.startswith('"')]
+    for r in csv.DictReader(lines):
+        rows.append(r)
+    agg = {}
+    for r in rows:
+        kind = kernel_kind(r["Kernel Name"])
+        if kind is None:
+            continue
+        short = r["Kernel Name"].replace("void ", "", 1).replace("ibm::", "").split("(")[0]
+        a = agg.setdefault((kind, short), {"ids": set(), "ns": 0.0, "rd": 0.0, "wr": 0.0})
+        a["ids"].add(r["ID"])
+        val = float(r["Metric Value"].replace(",", ""))
+        unit = r["Metric Unit"]
+        scale = {"ns": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6, "nsecond": 1.0,
+                 "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}.get(unit, 1.0)
+        if r["Metric Name"] == "gpu__time_duration.sum":
+            a["ns"] += val * scale
+        elif r["Metric Name"] == "dram__bytes_read.sum":
+            a["rd"] += val * scale
+        elif r["Metric Name"] == "dram__bytes_write.sum":
+            a["wr"] += val * scale
+    total_ns = sum(a["ns"] for a in agg.values())
+    print("| kernel | kind | launches/step | us/step | share | DRAM MB/step (read+write) |")
+    print("|---|---|---|---|---|---|")
+    kinds = {}
+    for (kind, name), a in sorted(agg.items(), key=lambda kv: -kv[1]["ns"]):
+        print("| %s | %s | %.1f | %.2f | %.1f%% | %.2f |" % (name, kind, len(a["ids"]) / steps, a["ns"] / 1e3 / steps,
+                                                         100 * a["ns"] / total_ns, (a["rd"] + a["wr"]) / 1e6 / steps))
+        k = kinds.setdefault(kind, {"ns": 0.0, "bytes": 0.0})
+        k["ns"] += a["ns"]
+        k["bytes"] += a["rd"] + a["wr"]
+    out = {kind: {"workload": WORKLOAD, "dram_bytes_per_step": v["bytes"] / steps,
+                  "device_us_per_step": v["ns"] / 1e3 / steps, "share": v["ns"] / total_ns,
+                  "source_sha256_16": source_digest(kind),
+                  "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the kind's launches of "
+                          "one step, each launch replayed with caches flushed"}
+           for kind, v in kinds.items()}
+    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
 
 
 # ---------------------------------------------------------------------------
@@ -239,11 +311,13 @@ def run_gpu(args):
     if args.quick:
         barrier()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.cudart().cudaProfilerStart()  # `ncu --profile-from-start off` captures these steps only
         e0.record()
         for i in range(args.steps):
             step(args.warmup + i)
         e1.record()
         barrier()
+        torch.cuda.cudart().cudaProfilerStop()
         ms = e0.elapsed_time(e1)
         if rank == 0:
             print(json.dumps({"quick": True, "ms_per_step": ms / args.steps,
@@ -317,14 +391,15 @@ def run_gpu(args):
     serving = serve_sample(ibm) if not args.no_extras else None
     plate = large_plate(ibm, torch) if not args.no_extras else None
 
-    # ---- roofline of the dominant kernel ----
+    # ---- roofline of the dominant kernel kind (all its launches of a step) ----
     dom = max(prof, key=lambda k: prof[k][0])
     dom_ms, dom_launches = prof[dom]
     avg_ms = dom_ms / max(dom_launches, 1)
-    alg = algorithmic_bytes(dom, dom_launches / args.steps)
+    dom_step_ms = dom_ms / args.steps
+    alg = algorithmic_bytes(dom)
     peak, peak_src = measured_peak()
-    achieved = alg / (avg_ms * 1e-3) / 1e9
-    workload_name = "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere"
+    achieved = alg / (dom_step_ms * 1e-3) / 1e9
+    workload_name = WORKLOAD
     traffic = ncu_traffic(dom, workload_name)
     launches = sum(c for _, c in prof.values())
 
@@ -350,7 +425,9 @@ def run_gpu(args):
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
-                     "algorithmic_bytes_per_launch": alg, "avg_launch_ms": avg_ms},
+                     "per": "step (all launches of the kind in one RK stage)",
+                     "algorithmic_bytes": alg, "ms_per_step": dom_step_ms,
+                     "launches_per_step": dom_launches / args.steps, "avg_launch_ms": avg_ms},
         "kernels_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
         "launches_per_step": {k: prof[k][1] / args.steps for k in prof},
         "p50_ms": float(np.percentile(step_ms, 50)),
@@ -651,8 +728,14 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving samples")
     ap.add_argument("--quick", action="store_true",
                     help="warm-up and timed steps only (no tracing pass, e2e, Poisson comparison or CPU baseline); "
-                         "used for profiler launch lists")
+                         "the timed steps are the profiler region, for ncu launch lists")
+    ap.add_argument("--ncu-summary", metavar="CSV",
+                    help="summarise an ncu --csv launch list of `--quick --steps K` (pass the same --steps): "
+                         "writes profiles/dram_traffic.json, prints a markdown table")
     args = ap.parse_args()
+    if args.ncu_summary:
+        ncu_summary(args.ncu_summary, args.steps)
+        return
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":

@@ -91,11 +91,15 @@ k_rows_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<
 
 template <typename T, int N> struct ColCfg {
   static constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
-  // columns per CTA: runs of >= 128 bytes per row, <= 256 threads for FP64 (register room for N2 = 32)
-  static constexpr int WMIN = sizeof(T) == 4 ? 16 : 8, WMAX = sizeof(T) == 4 ? 64 : 32;
-  static constexpr int WT = (sizeof(T) == 4 ? 256 : 128) / N2;
+  // columns per CTA: runs of >= 128 bytes per row; one thread per (column,
+  // n1) in step 1, and the same threads take the N2 step-3 DFTs of their
+  // column in turn (about 256 threads, every one busy in both steps)
+  static constexpr int WMIN = sizeof(T) == 4 ? 16 : 8, WMAX = 64;
+  static constexpr int WT0 = 256 / N1;
+  static constexpr int WS = (int)(65536 / ((size_t)N * sizeof(cplx<T>)));  // exchange tile <= 64 KB
+  static constexpr int WT = WT0 < WS ? WT0 : WS;
   static constexpr int W = WT < WMIN ? WMIN : (WT > WMAX ? WMAX : WT);
-  static constexpr int THREADS = W * N2;
+  static constexpr int THREADS = W * N1;
   static constexpr size_t smem = sizeof(cplx<T>) * ((size_t)N + (size_t)N * W);
 };
 
@@ -119,7 +123,7 @@ k_cols(Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ tw, int P, int ncols, dou
   const int j = live ? col / P : 0;
   const int kx = live ? col - j * P : 0;
   cplx<T> *base = S + (size_t)j * N * P + kx;
-  if (live && tid < W * N1) {
+  if (live) {
     const int n1 = tid / W;
     const bool sub = INV && zsol && kx == 0;
     col_step1<T, N, INV, W>(base, P, n1, tw2, X + n1 * N2 * W + c, sub,
@@ -127,9 +131,10 @@ k_cols(Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ tw, int P, int ncols, dou
   }
   __syncthreads();
   if (live) {
-    const int k2 = tid / W;
-    const cplx<T> u0 = col_step3<T, N, INV, W>(X, c, k2, base, P);
-    if (!INV && zrhs && kx == 0 && k2 == 0) zrhs[j] = (double)u0.x;
+    for (int k2 = tid / W; k2 < N2; k2 += N1) {
+      const cplx<T> u0 = col_step3<T, N, INV, W>(X, c, k2, base, P);
+      if (!INV && zrhs && kx == 0 && k2 == 0) zrhs[j] = (double)u0.x;
+    }
   }
 }
 

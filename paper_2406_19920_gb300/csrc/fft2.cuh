@@ -270,6 +270,13 @@ template <typename T, int N, int PITCH>
 __device__ __forceinline__ void rinv_step3(const cplx<T> *xp, int k2, T *da, T *db, const T *aa, const T *ab,
                                            T scale) {
   constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
+  // the addend's loads go out first and land while the DFT runs
+  T a0[N1], a1[N1];
+#pragma unroll
+  for (int k1 = 0; k1 < N1; ++k1) {
+    a0[k1] = aa ? aa[k2 + N2 * k1] : (T)0;
+    a1[k1] = aa ? ab[k2 + N2 * k1] : (T)0;
+  }
   cplx<T> u[N1];
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) u[n1] = xp[n1 * PITCH + k2];
@@ -277,10 +284,8 @@ __device__ __forceinline__ void rinv_step3(const cplx<T> *xp, int k2, T *da, T *
 #pragma unroll
   for (int k1 = 0; k1 < N1; ++k1) {
     const int k = k2 + N2 * k1;
-    T v0 = u[k1].x * scale, v1 = u[k1].y * scale;
-    if (aa) { v0 += aa[k]; v1 += ab[k]; }
-    da[k] = v0;
-    db[k] = v1;
+    da[k] = fma(u[k1].x, scale, a0[k1]);
+    db[k] = fma(u[k1].y, scale, a1[k1]);
   }
 }
 

@@ -9,11 +9,11 @@
 // w (1/2,1/2,0)); x and z wrap periodically; along y only stored unknowns
 // are touched (v's wall face 0 and points beyond the walls are dropped).
 //
-// One thread per (marker, component).  Grid index and offset are computed in
-// FP64 (a few operations per thread) so that the weights see the marker
-// position without the FP32 rounding of i*h; the weights and sums run in the
-// plan precision.  Spreading accumulates with global atomics as in the
-// paper's L1 kernel (Sec. 2.3.2).
+// One thread per (marker, component).  The stencil origin and offset are
+// computed in FP64 on the FP64 path and in float-float on the FP32 path, so
+// that the weights see the marker position without the FP32 rounding of
+// X/h; the weights and sums run in the plan precision.  Spreading
+// accumulates with global atomics as in the paper's L1 kernel (Sec. 2.3.2).
 #include <cmath>
 
 #include "plan.h"
@@ -23,7 +23,8 @@ namespace ibm {
 struct IbmGrid {
   int nx, ny, nz;
   double inv_h[3];
-  double vol_inv;  // 1 / (hx hy hz)
+  float ih_hi[3], ih_lo[3];  // 1/h as float-float for the FP32 path
+  double vol_inv;            // 1 / (hx hy hz)
 };
 
 template <typename T> __device__ __forceinline__ T phi_roma3(T r) {
@@ -42,98 +43,123 @@ template <typename T> __device__ __forceinline__ T phi_peskin4(T r) {
   return (T)0;
 }
 
-template <typename T, int S> struct Support {
-  int i[S], j[S], k[S];
-  T wx[S], wy[S], wz[S];
-  bool jv[S];
-};
-
 __device__ __forceinline__ int wrap(int i, int n) {
   i %= n;
   return i < 0 ? i + n : i;
 }
 
-// S = 3 (ROMA3) or 4 (PESKIN4)
-template <typename T, int S>
-__device__ __forceinline__ void support(const IbmGrid &g, int comp, double X, double Y, double Z,
-                                        Support<T, S> &s) {
-  const double ox = comp == 0 ? 0.0 : 0.5;
-  const double oy = comp == 1 ? 0.0 : 0.5;
-  const double oz = comp == 2 ? 0.0 : 0.5;
-  const double sx = X * g.inv_h[0] - ox, sy = Y * g.inv_h[1] - oy, sz = Z * g.inv_h[2] - oz;
-  const double bx = (S == 3) ? floor(sx + 0.5) - 1.0 : floor(sx) - 1.0;
-  const double by = (S == 3) ? floor(sy + 0.5) - 1.0 : floor(sy) - 1.0;
-  const double bz = (S == 3) ? floor(sz + 0.5) - 1.0 : floor(sz) - 1.0;
-  const int jlo = comp == 1 ? 1 : 0;
-#pragma unroll
-  for (int q = 0; q < S; ++q) {
-    const T rx = (T)(sx - (bx + q)), ry = (T)(sy - (by + q)), rz = (T)(sz - (bz + q));
-    s.wx[q] = S == 3 ? phi_roma3<T>(rx) : phi_peskin4<T>(rx);
-    s.wy[q] = S == 3 ? phi_roma3<T>(ry) : phi_peskin4<T>(ry);
-    s.wz[q] = S == 3 ? phi_roma3<T>(rz) : phi_peskin4<T>(rz);
-    s.i[q] = wrap((int)bx + q, g.nx);
-    s.k[q] = wrap((int)bz + q, g.nz);
-    s.j[q] = (int)by + q;
-    s.jv[q] = s.j[q] >= jlo && s.j[q] <= g.ny - 1;
-  }
+// Stencil origin along one axis: s = X/h - o in grid units, first index b
+// and offset f = s - b.  FP64: plain doubles.  FP32: s as a float-float (an
+// error-free product of X with 1/h split into hi + lo, and an error-free
+// sum for the half-cell shift), b from its high part, f = (hi - b) + lo;
+// f is within about 1e-7 grid units of the exact offset, and no FP64
+// instruction is issued (the FP64 pipe is narrow on this part).
+template <int S> __device__ __forceinline__ void axis_origin(double X, double ih, float, float, double o, int &b, double &f) {
+  const double sx = X * ih - o;
+  const double d = (S == 3) ? floor(sx + 0.5) - 1.0 : floor(sx) - 1.0;
+  b = (int)d;
+  f = sx - d;
+}
+template <int S> __device__ __forceinline__ void axis_origin(float X, double, float ihh, float ihl, double o, int &b, float &f) {
+  const ff p = two_prod(X, ihh);
+  const ff t = two_sum(p.hi, -(float)o);
+  const float lo = fmaf(X, ihl, p.lo) + t.lo;
+  const float hi = t.hi;
+  const float d = (S == 3) ? floorf(hi + 0.5f) - 1.0f : floorf(hi) - 1.0f;
+  b = (int)d;
+  f = (hi - d) + lo;
 }
 
-// U[m][c] = sum phi phi phi f_c  (+ optional second field: u^e = u + du)
+// Component comp's stencil origin (b*) and offsets from it (f*, grid units).
+template <typename T, int S>
+__device__ __forceinline__ void stencil_origin(const IbmGrid &g, int comp, T X, T Y, T Z, int &bx, int &by, int &bz,
+                                               T &fx, T &fy, T &fz) {
+  axis_origin<S>(X, g.inv_h[0], g.ih_hi[0], g.ih_lo[0], comp == 0 ? 0.0 : 0.5, bx, fx);
+  axis_origin<S>(Y, g.inv_h[1], g.ih_hi[1], g.ih_lo[1], comp == 1 ? 0.0 : 0.5, by, fy);
+  axis_origin<S>(Z, g.inv_h[2], g.ih_hi[2], g.ih_lo[2], comp == 2 ? 0.0 : 0.5, bz, fz);
+}
+
+// One thread per (marker, component): the whole S^3 stencil of one
+// component (its S^3 accesses independent of each other, so they overlap).
 template <typename T, int S>
 __global__ void __launch_bounds__(256)
 k_interp(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ u, const T *__restrict__ v,
-         const T *__restrict__ w, const T *__restrict__ du, const T *__restrict__ dv, const T *__restrict__ dw,
-         T *__restrict__ U, const T *__restrict__ Ud, T inv_dt, T *__restrict__ F) {
+           const T *__restrict__ w, const T *__restrict__ du, const T *__restrict__ dv, const T *__restrict__ dw,
+           T *__restrict__ U, const T *__restrict__ Ud, T inv_dt, T *__restrict__ F) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
   const int m = t / 3, c = t - 3 * m;
-  Support<T, S> s;
-  support<T, S>(g, c, (double)X[3 * m], (double)X[3 * m + 1], (double)X[3 * m + 2], s);
+  int bx, by, bz;
+  T fx, fy, fz;
+  stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], bx, by, bz, fx, fy, fz);
   const T *f = c == 0 ? u : c == 1 ? v : w;
   const T *df = c == 0 ? du : c == 1 ? dv : dw;
+  T wx[S], wz[S];
+  int ix[S], kz[S];
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    wx[q] = S == 3 ? phi_roma3<T>(fx - (T)q) : phi_peskin4<T>(fx - (T)q);
+    wz[q] = S == 3 ? phi_roma3<T>(fz - (T)q) : phi_peskin4<T>(fz - (T)q);
+    ix[q] = wrap(bx + q, g.nx);
+    kz[q] = wrap(bz + q, g.nz);
+  }
+  const int jlo = c == 1 ? 1 : 0;
   T acc = 0;
 #pragma unroll
   for (int qy = 0; qy < S; ++qy) {
-    if (!s.jv[qy]) continue;
-    const size_t rowy = (size_t)s.j[qy] * g.nz;
+    const int j = by + qy;
+    if (j < jlo || j > g.ny - 1) continue;
+    const T wy = S == 3 ? phi_roma3<T>(fy - (T)qy) : phi_peskin4<T>(fy - (T)qy);
 #pragma unroll
     for (int qz = 0; qz < S; ++qz) {
-      const size_t row = (rowy + s.k[qz]) * g.nx;
-      const T wyz = s.wy[qy] * s.wz[qz];
+      const int row = (j * g.nz + kz[qz]) * g.nx;
+      T part = 0;
 #pragma unroll
       for (int qx = 0; qx < S; ++qx) {
-        T val = f[row + s.i[qx]];
-        if (df) val += df[row + s.i[qx]];
-        acc += wyz * s.wx[qx] * val;
+        T val = f[row + ix[qx]];
+        if (df) val += df[row + ix[qx]];
+        part += wx[qx] * val;
       }
+      acc += wy * wz[qz] * part;
     }
   }
   if (U) U[t] = acc;
   if (F) F[t] = (Ud[t] - acc) * inv_dt;  // Eq. 2c
 }
 
-// f_c += amp * phi phi phi,  amp = scale * F[m][c] * dV[m] / (hx hy hz)
 template <typename T, int S>
 __global__ void __launch_bounds__(256)
 k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, const T *__restrict__ dV, T *fu,
-         T *fv, T *fw, T scale) {
+           T *fv, T *fw, T scale) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
   const int m = t / 3, c = t - 3 * m;
-  Support<T, S> s;
-  support<T, S>(g, c, (double)X[3 * m], (double)X[3 * m + 1], (double)X[3 * m + 2], s);
+  int bx, by, bz;
+  T fx, fy, fz;
+  stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], bx, by, bz, fx, fy, fz);
   T *f = c == 0 ? fu : c == 1 ? fv : fw;
   const T amp = scale * F[t] * dV[m] * (T)g.vol_inv;
+  T wx[S], wz[S];
+  int ix[S], kz[S];
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    wx[q] = S == 3 ? phi_roma3<T>(fx - (T)q) : phi_peskin4<T>(fx - (T)q);
+    wz[q] = S == 3 ? phi_roma3<T>(fz - (T)q) : phi_peskin4<T>(fz - (T)q);
+    ix[q] = wrap(bx + q, g.nx);
+    kz[q] = wrap(bz + q, g.nz);
+  }
+  const int jlo = c == 1 ? 1 : 0;
 #pragma unroll
   for (int qy = 0; qy < S; ++qy) {
-    if (!s.jv[qy]) continue;
-    const size_t rowy = (size_t)s.j[qy] * g.nz;
+    const int j = by + qy;
+    if (j < jlo || j > g.ny - 1) continue;
+    const T wy = S == 3 ? phi_roma3<T>(fy - (T)qy) : phi_peskin4<T>(fy - (T)qy);
 #pragma unroll
     for (int qz = 0; qz < S; ++qz) {
-      const size_t row = (rowy + s.k[qz]) * g.nx;
-      const T a = amp * s.wy[qy] * s.wz[qz];
+      const int row = (j * g.nz + kz[qz]) * g.nx;
+      const T a = amp * wy * wz[qz];
 #pragma unroll
-      for (int qx = 0; qx < S; ++qx) atomicAdd(f + row + s.i[qx], a * s.wx[qx]);
+      for (int qx = 0; qx < S; ++qx) atomicAdd(f + row + ix[qx], a * wx[qx]);
     }
   }
 }
@@ -161,7 +187,11 @@ __global__ void k_motion(int n, const T *__restrict__ X0, T *__restrict__ X, T *
 static IbmGrid ibm_grid(const ibm_plan_s *p) {
   IbmGrid g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
-  for (int d = 0; d < 3; ++d) g.inv_h[d] = 1.0 / p->h[d];
+  for (int d = 0; d < 3; ++d) {
+    g.inv_h[d] = 1.0 / p->h[d];
+    g.ih_hi[d] = (float)g.inv_h[d];
+    g.ih_lo[d] = (float)(g.inv_h[d] - (double)g.ih_hi[d]);
+  }
   g.vol_inv = 1.0 / (p->h[0] * p->h[1] * p->h[2]);
   return g;
 }
@@ -172,11 +202,11 @@ cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, co
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const IbmGrid g = ibm_grid(p);
-  const int blocks = ceil_div(3 * n, 256);
+  const int tb = ceil_div(3 * n, 256);
   if (p->delta == IBM_DELTA_PESKIN4)
-    k_interp<T, 4><<<blocks, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
+    k_interp<T, 4><<<tb, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
   else
-    k_interp<T, 3><<<blocks, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
+    k_interp<T, 3><<<tb, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
   return cudaGetLastError();
 }
 
@@ -185,11 +215,11 @@ cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, co
                           double scale, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const IbmGrid g = ibm_grid(p);
-  const int blocks = ceil_div(3 * n, 256);
+  const int tb = ceil_div(3 * n, 256);
   if (p->delta == IBM_DELTA_PESKIN4)
-    k_spread<T, 4><<<blocks, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
+    k_spread<T, 4><<<tb, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
   else
-    k_spread<T, 3><<<blocks, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
+    k_spread<T, 3><<<tb, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
   return cudaGetLastError();
 }
 

@@ -30,16 +30,18 @@ struct ResidualArgs {
                        // same value as a float pair (hi, lo) for the FP32 path; NULL for none
   int nx, ny, nz, bc;
   ffc cx, cy, cz, tau;
+  ffc kx, ky, kz;  // -tau c_a, split from the FP64 product
   float sigma;
   double cxd, cyd, czd, taud, sigmad;
 };
 
-// Adds the block sums of (r^2, b^2, r, b) to out[0..3] (FP64 atomics).
-__device__ __forceinline__ void block_accumulate(double r, double b, double *out) {
+// Adds the block sums of the per-thread sums (r^2, b^2, r, b) to out[0..3]
+// (FP64 atomics).
+__device__ __forceinline__ void block_accumulate(double r2, double b2, double r1, double b1, double *out) {
   __shared__ double red[4][32];
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int lane = tid & 31, w = tid >> 5;
-  double v[4] = {r * r, b * b, r, b};
+  double v[4] = {r2, b2, r1, b1};
 #pragma unroll
   for (int q = 0; q < 4; ++q)
 #pragma unroll
@@ -60,59 +62,85 @@ __device__ __forceinline__ void block_accumulate(double r, double b, double *out
   }
 }
 
-// one thread per point, stencil_launch() shape
+// FP32 residual.  The exact value
+//   r = (b - m) - sigma x0 + sum_a K_a D_a,   K_a = -tau c_a,
+// D_a = x(+1) + x(-1) - 2 x0 the second difference along axis a, is
+// evaluated as if in twice the working precision and rounded once:
+//   * D_a exactly as hi + lo (two error-free sums of FP32 values);
+//   * K_a D_a as an error-free product of the high parts plus the cross
+//     terms in FMAs (K_a is the FP64 coefficient split into hi + lo);
+//   * all high parts summed by a chain of error-free sums, all low parts and
+//     sum errors added in FP32 (cascaded summation, Ogita, Rump & Oishi
+//     2005), the two totals added last.
+// One thread per point (stencil_launch shape); periodic neighbours by
+// compare-and-select, no divisions.
+__device__ __forceinline__ void sum_into(float &S, float &E, float h) {
+  const ff t = two_sum(S, h);
+  S = t.hi;
+  E += t.lo;
+}
+
 __global__ void __launch_bounds__(128)
 k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float *__restrict__ r,
                double *norms) {
   int i, k, j;
   const bool inside = stencil_index(A.nx, A.nz, i, k, j);
-  const size_t idx = ((size_t)j * A.nz + k) * A.nx + i;
   double rr = 0.0, bb = 0.0;
   if (inside) {
-    const size_t row = (size_t)A.nx;
     const size_t pl = (size_t)A.nx * A.nz;
-    float bv = b[idx];
-    float bl = 0.0f;  // low part of b - offset
-    if (A.boff) {
-      // the removed mean as a float-float pair: boff[1..2] reinterpreted
-      const float2 m = *reinterpret_cast<const float2 *>(A.boff + 1);
-      const ff d = two_sum(bv, -m.x);
-      bv = d.hi;
-      bl = __fadd_rn(d.lo, -m.y);
-    }
-    float res;
-    if (A.bc == BC_FACE_DIRICHLET && j == 0) {
+    const size_t base = (size_t)j * pl;
+    const int c = k * A.nx + i;
+    const int oe = c - i + (i + 1 == A.nx ? 0 : i + 1), ow = c - i + (i == 0 ? A.nx - 1 : i - 1);
+    const int on = (k + 1 == A.nz ? 0 : k + 1) * A.nx + i, os = (k == 0 ? A.nz - 1 : k - 1) * A.nx + i;
+    const bool face = A.bc == BC_FACE_DIRICHLET;
+    float res, bt;
+    const float bv = b[base + c];
+    float2 m = make_float2(0.f, 0.f);
+    if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
+    if (face && j == 0) {
       res = 0.0f;
+      bt = 0.0f;
     } else {
-      const float x0 = x[idx];
-      const float xe = x[idx - i + (i + 1 == A.nx ? 0 : i + 1)];
-      const float xw = x[idx - i + (i == 0 ? A.nx - 1 : i - 1)];
-      const size_t rowbase = idx - (size_t)k * row;
-      const float xn = x[rowbase + (size_t)(k + 1 == A.nz ? 0 : k + 1) * row];
-      const float xs = x[rowbase + (size_t)(k == 0 ? A.nz - 1 : k - 1) * row];
-      float xu, xd;  // y+1, y-1
-      if (A.bc == BC_FACE_DIRICHLET) {
-        xd = (j - 1 >= 1) ? x[idx - pl] : 0.0f;
-        xu = (j + 1 <= A.ny - 1) ? x[idx + pl] : 0.0f;
+      const float x0 = x[base + c];
+      const float xe = x[base + oe], xw = x[base + ow], xn = x[base + on], xs = x[base + os];
+      float xu, xd;
+      if (face) {
+        xd = j - 1 >= 1 ? x[base - pl + c] : 0.0f;
+        xu = j + 1 <= A.ny - 1 ? x[base + pl + c] : 0.0f;
       } else {
         const float gsign = (A.bc == BC_NEUMANN) ? 1.0f : -1.0f;
-        xd = (j > 0) ? x[idx - pl] : gsign * x0;
-        xu = (j + 1 < A.ny) ? x[idx + pl] : gsign * x0;
+        xd = j > 0 ? x[base - pl + c] : gsign * x0;
+        xu = j + 1 < A.ny ? x[base + pl + c] : gsign * x0;
       }
-      ff L = ff_mul(ff_second_diff(xe, xw, x0), ff{A.cx.hi, A.cx.lo});
-      L = ff_add(L, ff_mul(ff_second_diff(xn, xs, x0), ff{A.cz.hi, A.cz.lo}));
-      L = ff_add(L, ff_mul(ff_second_diff(xu, xd, x0), ff{A.cy.hi, A.cy.lo}));
-      ff acc = ff_add(two_sum(bv, -A.sigma * x0), ff_from(bl));
-      acc = ff_add(acc, ff_neg(ff_mul(L, ff{A.tau.hi, A.tau.lo})));
-      res = __fadd_rn(acc.hi, acc.lo);
+      const float x2 = -2.0f * x0;
+      // exact second differences D = hi + lo
+      ff s = two_sum(xe, xw), t = two_sum(s.hi, x2);
+      const float Dxh = t.hi, Dxl = t.lo + s.lo;
+      s = two_sum(xn, xs); t = two_sum(s.hi, x2);
+      const float Dzh = t.hi, Dzl = t.lo + s.lo;
+      s = two_sum(xu, xd); t = two_sum(s.hi, x2);
+      const float Dyh = t.hi, Dyl = t.lo + s.lo;
+      // (b - m) - sigma x0 + sum_a K_a D_a, cascaded
+      const ff bm = two_sum(bv, -m.x);
+      float S = bm.hi, E = bm.lo - m.y;
+      bt = bm.hi + E;
+      sum_into(S, E, -A.sigma * x0);
+      ff p = two_prod(A.kx.hi, Dxh);
+      sum_into(S, E, p.hi);
+      E += fmaf(A.kx.hi, Dxl, fmaf(A.kx.lo, Dxh, p.lo));
+      p = two_prod(A.kz.hi, Dzh);
+      sum_into(S, E, p.hi);
+      E += fmaf(A.kz.hi, Dzl, fmaf(A.kz.lo, Dzh, p.lo));
+      p = two_prod(A.ky.hi, Dyh);
+      sum_into(S, E, p.hi);
+      E += fmaf(A.ky.hi, Dyl, fmaf(A.ky.lo, Dyh, p.lo));
+      res = S + E;
     }
-    r[idx] = res;
-    if (norms) {
-      rr = (double)res;
-      bb = (A.bc == BC_FACE_DIRICHLET && j == 0) ? 0.0 : (double)bv + (double)bl;
-    }
+    r[base + c] = res;
+    rr = res;
+    bb = bt;
   }
-  if (norms) block_accumulate(rr, bb, norms);
+  if (norms) block_accumulate(rr * rr, bb * bb, rr, bb, norms);
 }
 
 __global__ void __launch_bounds__(128)
@@ -152,7 +180,7 @@ k_residual_f64(ResidualArgs A, const double *__restrict__ b, const double *__res
     rr = res;
     bb = (A.bc == BC_FACE_DIRICHLET && j == 0) ? 0.0 : bv;
   }
-  if (norms) block_accumulate(rr, bb, norms);
+  if (norms) block_accumulate(rr * rr, bb * bb, rr, bb, norms);
 }
 
 static ResidualArgs make_args(int nx, int ny, int nz, const StencilCoef &c, const double *boff) {
@@ -161,6 +189,7 @@ static ResidualArgs make_args(int nx, int ny, int nz, const StencilCoef &c, cons
   A.nx = nx; A.ny = ny; A.nz = nz; A.bc = c.bc;
   A.cx = split_ff(c.cx); A.cy = split_ff(c.cy); A.cz = split_ff(c.cz);
   A.tau = split_ff(c.tau);
+  A.kx = split_ff(-c.tau * c.cx); A.ky = split_ff(-c.tau * c.cy); A.kz = split_ff(-c.tau * c.cz);
   A.sigma = (float)c.sigma;
   A.cxd = c.cx; A.cyd = c.cy; A.czd = c.cz; A.taud = c.tau; A.sigmad = c.sigma;
   return A;
