@@ -44,6 +44,7 @@ k_rows_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ 
   cplx<T> *tw2 = reinterpret_cast<cplx<T> *>(smem_raw);
   cplx<T> *X = tw2 + N;  // [RP][N1][PITCH]
   load_step_twiddles<T, N>(tw2, tw);
+  pdl_wait();  // the spectrum / fields below are the predecessor's output
   const int pair0 = blockIdx.x * RP;
   const int np = min(RP, npairs - pair0);
   __syncthreads();
@@ -72,6 +73,7 @@ k_rows_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<
   cplx<T> *tw2 = reinterpret_cast<cplx<T> *>(smem_raw);
   cplx<T> *X = tw2 + N;
   load_step_twiddles<T, N>(tw2, tw);
+  pdl_wait();  // the spectrum / fields below are the predecessor's output
   const int pair0 = blockIdx.x * RP;
   const int np = min(RP, npairs - pair0);
   __syncthreads();
@@ -115,6 +117,7 @@ k_cols(Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ tw, int P, int ncols, dou
   cplx<T> *tw2 = reinterpret_cast<cplx<T> *>(smem_raw);
   cplx<T> *X = tw2 + N;  // [N1][N2][W]
   load_step_twiddles<T, N>(tw2, tw);
+  pdl_wait();  // the spectrum / fields below are the predecessor's output
   __syncthreads();
   const int tid = threadIdx.x;
   const int c = tid % W;
@@ -153,7 +156,7 @@ cudaError_t launch_axis_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3
   if (g.nx == N) {                                                                                \
     using Cfg = RowCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_rows_fwd<T, N>>(); if (e) return e; }                     \
-    k_rows_fwd<T, N><<<dim3(ceil_div(npairs, Cfg::RP), g.nb), kRowThreads, Cfg::smem, st>>>(in, S, twx, npairs, in_scale); \
+    IBM_KTRY(launch_pdl(k_rows_fwd<T, N>, dim3(ceil_div(npairs, Cfg::RP), g.nb), kRowThreads, Cfg::smem, st, in, S, twx, npairs, in_scale)); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -165,7 +168,7 @@ cudaError_t launch_axis_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3
   if (g.nz == N) {                                                                                \
     using Cfg = ColCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_cols<T, N, false>>(); if (e) return e; }                  \
-    k_cols<T, N, false><<<dim3(ceil_div(ncols, Cfg::W), g.nb), Cfg::THREADS, Cfg::smem, st>>>(S, twz, P, ncols, g.zrhs, nullptr); \
+    IBM_KTRY(launch_pdl(k_cols<T, N, false>, dim3(ceil_div(ncols, Cfg::W), g.nb), Cfg::THREADS, Cfg::smem, st, S, twz, P, ncols, g.zrhs, nullptr)); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -185,7 +188,7 @@ cudaError_t launch_axis_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<
   if (g.nz == N) {                                                                                \
     using Cfg = ColCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_cols<T, N, true>>(); if (e) return e; }                   \
-    k_cols<T, N, true><<<dim3(ceil_div(ncols, Cfg::W), g.nb), Cfg::THREADS, Cfg::smem, st>>>(S, twz, P, ncols, nullptr, g.zsol); \
+    IBM_KTRY(launch_pdl(k_cols<T, N, true>, dim3(ceil_div(ncols, Cfg::W), g.nb), Cfg::THREADS, Cfg::smem, st, S, twz, P, ncols, nullptr, g.zsol)); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)
@@ -196,7 +199,7 @@ cudaError_t launch_axis_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<
   if (g.nx == N) {                                                                                \
     using Cfg = RowCfg<T, N>;                                                                     \
     { cudaError_t e = ensure_max_smem<k_rows_inv<T, N>>(); if (e) return e; }                     \
-    k_rows_inv<T, N><<<dim3(ceil_div(npairs, Cfg::RP), g.nb), kRowThreads, Cfg::smem, st>>>(S, out, addend, twx, npairs, scale); \
+    IBM_KTRY(launch_pdl(k_rows_inv<T, N>, dim3(ceil_div(npairs, Cfg::RP), g.nb), kRowThreads, Cfg::smem, st, S, out, addend, twx, npairs, scale)); \
     done = true;                                                                                  \
   }
   IBM_AXIS_N(X)

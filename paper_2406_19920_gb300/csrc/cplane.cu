@@ -53,6 +53,7 @@ template <typename T, int NX, int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCThreads)
 k_cplane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ twx_g,
              const cplx<T> *__restrict__ twz_g, T in_scale, int *err, double *zrhs) {
+  pdl_wait();
   const T *__restrict__ in = in_[blockIdx.y];
   cplx<T> *__restrict__ S = S_[blockIdx.y];
   using L = CLayout<T, NX, NZ, C>;
@@ -134,6 +135,7 @@ template <typename T, int NX, int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(kCThreads)
 k_cplane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<T> *__restrict__ twx_g,
              const cplx<T> *__restrict__ twz_g, T scale, int *err, const double *zsol) {
+  pdl_wait();
   const cplx<T> *__restrict__ S = S_[blockIdx.y];
   T *out = out_[blockIdx.y];
   const T *addend = add_[blockIdx.y];
@@ -233,8 +235,8 @@ cudaError_t launch_cplane_forward(const TransformGeom &g, int C, Ptr3<const T *>
     if constexpr (CLayout<T, a, b, c>::fwd_bytes <= kPlaneSmemLimit) {                          \
       cudaError_t e = ensure_max_smem<k_cplane_fwd<T, a, b, c>>();                              \
       if (e) return e;                                                                          \
-      k_cplane_fwd<T, a, b, c><<<dim3(g.ny * c, g.nb), kCThreads, CLayout<T, a, b, c>::fwd_bytes, st>>>(    \
-          in, S, twx, twz, in_scale, g.err, g.zrhs);                                            \
+      IBM_KTRY(launch_pdl(k_cplane_fwd<T, a, b, c>, dim3(g.ny * c, g.nb), kCThreads, CLayout<T, a, b, c>::fwd_bytes, st, \
+          in, S, twx, twz, in_scale, g.err, g.zrhs));                                            \
       return cudaGetLastError();                                                                \
     }                                                                                           \
   }
@@ -252,8 +254,8 @@ cudaError_t launch_cplane_inverse(const TransformGeom &g, int C, Ptr3<cplx<T> *>
     if constexpr (CLayout<T, a, b, c>::fwd_bytes <= kPlaneSmemLimit) {                          \
       cudaError_t e = ensure_max_smem<k_cplane_inv<T, a, b, c>>();                              \
       if (e) return e;                                                                          \
-      k_cplane_inv<T, a, b, c><<<dim3(g.ny * c, g.nb), kCThreads, CLayout<T, a, b, c>::inv_bytes, st>>>(    \
-          S, out, addend, twx, twz, scale, g.err, g.zsol);                                      \
+      IBM_KTRY(launch_pdl(k_cplane_inv<T, a, b, c>, dim3(g.ny * c, g.nb), kCThreads, CLayout<T, a, b, c>::inv_bytes, st, \
+          S, out, addend, twx, twz, scale, g.err, g.zsol));                                      \
       return cudaGetLastError();                                                                \
     }                                                                                           \
   }

@@ -86,6 +86,7 @@ __global__ void __launch_bounds__(256)
 k_interp(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ u, const T *__restrict__ v,
            const T *__restrict__ w, const T *__restrict__ du, const T *__restrict__ dv, const T *__restrict__ dw,
            T *__restrict__ U, const T *__restrict__ Ud, T inv_dt, T *__restrict__ F) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
   const int m = t / 3, c = t - 3 * m;
@@ -131,6 +132,7 @@ template <typename T, int S>
 __global__ void __launch_bounds__(256)
 k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, const T *__restrict__ dV, T *fu,
            T *fv, T *fw, T scale) {
+  pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
   const int m = t / 3, c = t - 3 * m;
@@ -168,6 +170,7 @@ k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, con
 template <typename T>
 __global__ void k_motion(int n, const T *__restrict__ X0, T *__restrict__ X, T *__restrict__ Ud, int kind,
                          double p0, double p1, double p2, double t) {
+  pdl_wait();
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m >= n) return;
   double x = (double)X0[3 * m], y = (double)X0[3 * m + 1], z = (double)X0[3 * m + 2];
@@ -204,9 +207,9 @@ cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, co
   const IbmGrid g = ibm_grid(p);
   const int tb = ceil_div(3 * n, 256);
   if (p->delta == IBM_DELTA_PESKIN4)
-    k_interp<T, 4><<<tb, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
+    IBM_KTRY(launch_pdl(k_interp<T, 4>, tb, 256, 0, st, g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F));
   else
-    k_interp<T, 3><<<tb, 256, 0, st>>>(g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F);
+    IBM_KTRY(launch_pdl(k_interp<T, 3>, tb, 256, 0, st, g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F));
   return cudaGetLastError();
 }
 
@@ -217,9 +220,9 @@ cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, co
   const IbmGrid g = ibm_grid(p);
   const int tb = ceil_div(3 * n, 256);
   if (p->delta == IBM_DELTA_PESKIN4)
-    k_spread<T, 4><<<tb, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
+    IBM_KTRY(launch_pdl(k_spread<T, 4>, tb, 256, 0, st, g, n, X, F, dV, fu, fv, fw, (T)scale));
   else
-    k_spread<T, 3><<<tb, 256, 0, st>>>(g, n, X, F, dV, fu, fv, fw, (T)scale);
+    IBM_KTRY(launch_pdl(k_spread<T, 3>, tb, 256, 0, st, g, n, X, F, dV, fu, fv, fw, (T)scale));
   return cudaGetLastError();
 }
 
@@ -227,7 +230,7 @@ template <typename T>
 cudaError_t launch_motion(int n, const T *X0, T *X, T *Ud, int kind, const double *params, double t,
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
-  k_motion<T><<<ceil_div(n, 256), 256, 0, st>>>(n, X0, X, Ud, kind, params[0], params[1], params[2], t);
+  IBM_KTRY(launch_pdl(k_motion<T>, ceil_div(n, 256), 256, 0, st, n, X0, X, Ud, kind, params[0], params[1], params[2], t));
   return cudaGetLastError();
 }
 

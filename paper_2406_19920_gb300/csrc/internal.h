@@ -72,6 +72,44 @@ template <auto Kernel> cudaError_t ensure_max_smem() {
   return err;
 }
 
+// Programmatic dependent launch.  Every kernel of the path is launched
+// with programmatic stream serialization: the next kernel in the stream may
+// be launched once every CTA of this one has exited (the implicit trigger),
+// which overlaps its launch and prologue with this grid's completion.
+// Before it touches memory written by its predecessor each kernel waits for
+// that grid's completion (griddepcontrol.wait, which also orders memory);
+// only plan constants (twiddle and wavenumber tables) are read before the
+// wait.  No kernel triggers early: dependents scheduled while a many-wave
+// grid still has CTAs to run would take its SM slots (measured: the E2
+// divergence at 256^3 ran at half speed).  IBM_PDL=0 turns the attribute
+// off (plain stream order; the wait is then a no-op).
+__device__ __forceinline__ void pdl_launch_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+bool pdl_enabled();
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                              Args... args) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl_enabled() ? 1 : 0;
+  cudaError_t e = cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+  return e != cudaSuccess ? e : cudaGetLastError();
+}
+
+// Returns a failed launch's error from a function returning cudaError_t.
+#define IBM_KTRY(call)                          \
+  do {                                          \
+    cudaError_t e__ = (call);                   \
+    if (e__ != cudaSuccess) return e__;         \
+  } while (0)
+
 bool transform_size_supported(int n);
 // Plane modes (0, 1, 2, 4, 8) that can run an nx x nz plane, smallest first; returns the count.
 template <typename T> int plane_modes(int nx, int nz, int *modes);

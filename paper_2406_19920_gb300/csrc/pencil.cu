@@ -220,6 +220,7 @@ template <typename T>
 __global__ void __launch_bounds__(32)
 k_pencil_g(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
            double *mean_out) {
+  pdl_wait();
   cplx<T> *__restrict__ S = S_[blockIdx.y];
   int beta_s, beta_e, j0;
   pencil_field(pp, blockIdx.y, beta_s, beta_e, j0);
@@ -283,6 +284,7 @@ template <typename T>
 __global__ void __launch_bounds__(32)
 k_pencil(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
          double *mean_out) {
+  pdl_wait();
   cplx<T> *__restrict__ S = S_[blockIdx.y];
   int beta_s, beta_e, j0;
   pencil_field(pp, blockIdx.y, beta_s, beta_e, j0);
@@ -428,6 +430,7 @@ template <typename T, int M, bool SPLIT>
 __global__ void __launch_bounds__(1024)
 k_pencil_ss(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
             double *mean_out) {
+  pdl_wait();
   using C = SsCfg<T, M, SPLIT>;
   constexpr int NW = C::NW, TP = C::TP, NC = C::NC;
   extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -686,8 +689,8 @@ static cudaError_t launch_ss(const PencilParams &pp, cplx<T> *S, const T *lamx, 
     if (e != cudaSuccess) return e;
   }
   const int npen = pp.nz * pp.P;
-  k_pencil_ss<T, M, SPLIT><<<ceil_div(npen, C::TP) + (pp.zero_mode ? 1 : 0), 1024, bytes, st>>>(S, lamx, lamz, pp,
-                                                                                             mean_out);
+  IBM_KTRY(launch_pdl(k_pencil_ss<T, M, SPLIT>, ceil_div(npen, C::TP) + (pp.zero_mode ? 1 : 0), 1024, bytes, st, S, lamx, lamz, pp,
+                                                                                             mean_out));
   return cudaGetLastError();
 }
 
@@ -754,11 +757,11 @@ cudaError_t launch_pencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const T *l
   if (tile) {
     cudaError_t e = ensure_max_smem<k_pencil<T>>();
     if (e != cudaSuccess) return e;
-    k_pencil<T><<<g2, 32, tb, st>>>(S3, lamx, lamz, pp, mean_out);
+    IBM_KTRY(launch_pdl(k_pencil<T>, g2, 32, tb, st, S3, lamx, lamz, pp, mean_out));
   } else {
     cudaError_t e = ensure_max_smem<k_pencil_g<T>>();
     if (e != cudaSuccess) return e;
-    k_pencil_g<T><<<g2, 32, pencil_g_smem_bytes<T>(pp.ny), st>>>(S3, lamx, lamz, pp, mean_out);
+    IBM_KTRY(launch_pdl(k_pencil_g<T>, g2, 32, pencil_g_smem_bytes<T>(pp.ny), st, S3, lamx, lamz, pp, mean_out));
   }
   return cudaGetLastError();
 }

@@ -39,6 +39,11 @@ int cuda_error(cudaError_t e, const char *what) {
   return set_error(IBM_ERR_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+bool pdl_enabled() {
+  static const bool on = !(getenv("IBM_PDL") && atoi(getenv("IBM_PDL")) == 0);
+  return on;
+}
+
 TransformGeom geom_of(const ibm_plan_s *p) {
   TransformGeom g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;

@@ -83,6 +83,7 @@ __device__ __forceinline__ void sum_into(float &S, float &E, float h) {
 __global__ void __launch_bounds__(128)
 k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float *__restrict__ r,
                double *norms) {
+  pdl_wait();
   int i, k, j;
   const bool inside = stencil_index(A.nx, A.nz, i, k, j);
   double rr = 0.0, bb = 0.0;
@@ -146,6 +147,7 @@ k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restr
 __global__ void __launch_bounds__(128)
 k_residual_f64(ResidualArgs A, const double *__restrict__ b, const double *__restrict__ x,
                double *__restrict__ r, double *norms) {
+  pdl_wait();
   int i, k, j;
   const bool inside = stencil_index(A.nx, A.nz, i, k, j);
   const size_t idx = ((size_t)j * A.nz + k) * A.nx + i;
@@ -199,14 +201,14 @@ template <>
 cudaError_t launch_residual<float>(int nx, int ny, int nz, const StencilCoef &c, const float *b, const float *x,
                                    float *r, const double *boff, double *norms, cudaStream_t st) {
   const Launch3 L = stencil_launch(nx, ny, nz);
-  k_residual_f32<<<L.grid, L.block, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
+  IBM_KTRY(launch_pdl(k_residual_f32, L.grid, L.block, 0, st, make_args(nx, ny, nz, c, boff), b, x, r, norms));
   return cudaGetLastError();
 }
 template <>
 cudaError_t launch_residual<double>(int nx, int ny, int nz, const StencilCoef &c, const double *b, const double *x,
                                     double *r, const double *boff, double *norms, cudaStream_t st) {
   const Launch3 L = stencil_launch(nx, ny, nz);
-  k_residual_f64<<<L.grid, L.block, 0, st>>>(make_args(nx, ny, nz, c, boff), b, x, r, norms);
+  IBM_KTRY(launch_pdl(k_residual_f64, L.grid, L.block, 0, st, make_args(nx, ny, nz, c, boff), b, x, r, norms));
   return cudaGetLastError();
 }
 

@@ -70,6 +70,7 @@ __global__ void __launch_bounds__(kExTX * kExTZ)
 k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_,
            const T *__restrict__ p_, T *Nu, T *Nv, T *Nw, T *__restrict__ du, T *__restrict__ dv,
            T *__restrict__ dw, T c_visc, T c_pres, T gam, T zet, T dt) {
+  pdl_wait();
   constexpr int TX = kExTX, TZ = kExTZ, HX = TX + 2, HZ = TZ + 2, PL = HX * HZ, NT = TX * TZ;
   constexpr int NL = (PL + NT - 1) / NT;  // plane elements each thread loads
   __shared__ T su[3][PL], sv[3][PL], sw[3][PL], sp[2][PL];
@@ -242,6 +243,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 k_divergence(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_, T *b,
              T inv_scale, T ihx_t, T ihy_t, T ihz_t, ff ihx, ff ihy, ff ihz, double *dmax) {
+  pdl_wait();
   int i, k, j;
   const bool inside = stencil_index(g.nx, g.nz, i, k, j);
   const size_t idx = ((size_t)j * g.nz + k) * g.nx + i;
@@ -267,6 +269,7 @@ template <typename T>
 __global__ void __launch_bounds__(128)
 k_project(Geo g, T *__restrict__ u, T *__restrict__ v, T *__restrict__ w, T *__restrict__ p,
           const T *__restrict__ phi_, T kproj, T cvisc) {
+  pdl_wait();
   int i, k, j;
   if (!stencil_index(g.nx, g.nz, i, k, j)) return;
   const size_t idx = ((size_t)j * g.nz + k) * g.nx + i;
@@ -334,8 +337,8 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   {
     ProfScope ps(p, IBM_K_EXPLICIT, st);
     const dim3 eg(ceil_div(p->nx, kExTX), ceil_div(p->nz, kExTZ), ceil_div(p->ny, kExJC));
-    k_explicit<T><<<eg, dim3(kExTX, kExTZ), 0, st>>>(g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
-                                          (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt);
+    IBM_CUDA_TRY(launch_pdl(k_explicit<T>, eg, dim3(kExTX, kExTZ), 0, st, g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
+                                          (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt));
     IBM_CUDA_TRY(cudaGetLastError());
   }
   // L2 + L1
@@ -369,8 +372,8 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   const ff fx = ff_host(g.ihx), fy = ff_host(g.ihy), fz = ff_host(g.ihz);
   {
     ProfScope ps(p, IBM_K_DIVERGENCE, st);
-    k_divergence<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, rhs, (T)(1.0 / (ab * dt)), (T)g.ihx, (T)g.ihy,
-                                                  (T)g.ihz, fx, fy, fz, info ? p->dsc + 9 : nullptr);
+    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, rhs, (T)(1.0 / (ab * dt)), (T)g.ihx, (T)g.ihy,
+                                                  (T)g.ihz, fx, fy, fz, info ? p->dsc + 9 : nullptr));
     IBM_CUDA_TRY(cudaGetLastError());
   }
   // S2
@@ -378,13 +381,13 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   // E3
   {
     ProfScope ps(p, IBM_K_PROJECT, st);
-    k_project<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, pr, phi, (T)(ab * dt), (T)cH);
+    IBM_CUDA_TRY(launch_pdl(k_project<T>, L3.grid, L3.block, 0, st, g, u, v, w, pr, phi, (T)(ab * dt), (T)cH));
     IBM_CUDA_TRY(cudaGetLastError());
   }
   if (info) {
     IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
-    k_divergence<T><<<L3.grid, L3.block, 0, st>>>(g, u, v, w, nullptr, (T)1, (T)g.ihx, (T)g.ihy, (T)g.ihz, fx, fy,
-                                                  fz, p->dsc + 8);
+    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, nullptr, (T)1, (T)g.ihx, (T)g.ihy, (T)g.ihz, fx, fy,
+                                                  fz, p->dsc + 8));
     IBM_CUDA_TRY(cudaGetLastError());
     IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IBM_CUDA_TRY(cudaStreamSynchronize(st));

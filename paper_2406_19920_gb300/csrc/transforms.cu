@@ -68,6 +68,7 @@ k_plane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__
   const int tid = threadIdx.x;
   load_step_twiddles<T, NX>(tw2x, twx);
   load_step_twiddles<T, NZ>(tw2z, twz);
+  pdl_wait();  // the fields below are the predecessor's output
   __syncthreads();
   const T *src = in + (size_t)j * NZ * NX;
   for (int p0 = 0; p0 < NZ / 2; p0 += CP) {
@@ -124,6 +125,7 @@ k_plane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx
   const int tid = threadIdx.x;
   load_step_twiddles<T, NX>(tw2x, twx);
   load_step_twiddles<T, NZ>(tw2z, twz);
+  pdl_wait();  // the fields below are the predecessor's output
   __syncthreads();
   const cplx<T> *src = S + (size_t)j * NZ * P;
   const cplx<T> z0 = zsol ? mk<T>((T)zsol[j], (T)0) : mk<T>((T)0, (T)0);
@@ -189,7 +191,7 @@ cudaError_t launch_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx
   if (nx == a && nz == b) {                                                                      \
     if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
       { cudaError_t e = ensure_max_smem<k_plane_fwd<T, a, b>>(); if (e) return e; }              \
-      k_plane_fwd<T, a, b><<<dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(in, S, twx, twz, in_scale, g.zrhs); \
+      IBM_KTRY(launch_pdl(k_plane_fwd<T, a, b>, dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st, in, S, twx, twz, in_scale, g.zrhs)); \
       return cudaGetLastError();                                                                 \
     }                                                                                            \
   }
@@ -211,7 +213,7 @@ cudaError_t launch_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> 
   if (nx == a && nz == b) {                                                                      \
     if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
       { cudaError_t e = ensure_max_smem<k_plane_inv<T, a, b>>(); if (e) return e; }              \
-      k_plane_inv<T, a, b><<<dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st>>>(S, out, addend, twx, twz, scale, g.zsol); \
+      IBM_KTRY(launch_pdl(k_plane_inv<T, a, b>, dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st, S, out, addend, twx, twz, scale, g.zsol)); \
       return cudaGetLastError();                                                                 \
     }                                                                                            \
   }
