@@ -136,8 +136,9 @@ enum {
   IBM_K_INVERSE = 2,   /* z/x inverse transform                           */
   IBM_K_RESIDUAL = 3,  /* refinement residual                             */
   IBM_K_EXPLICIT = 4,  /* E1 explicit terms                               */
-  IBM_K_MOTION = 5,    /* L2 marker motion                                */
-  IBM_K_INTERP = 6,    /* L1 interpolation + force                        */
+  IBM_K_MOTION = 5,    /* L2 marker motion (fused into IBM_K_INTERP: no   */
+                       /* launches of its own)                            */
+  IBM_K_INTERP = 6,    /* L2 motion + L1 interpolation + force            */
   IBM_K_SPREAD = 7,    /* L1 spreading                                    */
   IBM_K_DIVERGENCE = 8,/* E2 divergence                                   */
   IBM_K_PROJECT = 9,   /* E3 projection + pressure update                 */

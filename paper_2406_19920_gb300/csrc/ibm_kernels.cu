@@ -27,6 +27,21 @@ struct IbmGrid {
   double vol_inv;            // 1 / (hx hy hz)
 };
 
+// L2 for the rigid motions (Sec. 2.3.2 moves the markers before L1): every
+// marker is displaced by the same d(t) with velocity v(t), both evaluated on
+// the host in FP64; d also as a float-float pair for the FP32 path.
+struct RigidMotion {
+  double d[3], v[3];
+  float dh[3], dl[3];
+};
+
+// X0 + d rounded once to the working precision.
+__device__ __forceinline__ double displaced(double x0, const RigidMotion &mo, int c) { return x0 + mo.d[c]; }
+__device__ __forceinline__ float displaced(float x0, const RigidMotion &mo, int c) {
+  const ff s = two_sum(x0, mo.dh[c]);
+  return s.hi + (s.lo + mo.dl[c]);
+}
+
 template <typename T> __device__ __forceinline__ T phi_roma3(T r) {
   const T a = fabs(r);
   if (a <= (T)0.5) return ((T)1 + sqrt((T)1 - (T)3 * a * a)) / (T)3;
@@ -81,18 +96,41 @@ __device__ __forceinline__ void stencil_origin(const IbmGrid &g, int comp, T X, 
 
 // One thread per (marker, component): the whole S^3 stencil of one
 // component (its S^3 accesses independent of each other, so they overlap).
+// With X0 (the substep): the marker's position X = X0 + d and surface
+// velocity Ud = v are formed here (L2), written out, and used at once; the
+// CTA's 64 markers share their coordinates through shared memory.  Without
+// X0 (ibm_interp): X is read.
+constexpr int kMarkerThreads = 192;  // a multiple of 3 and of the warp
+
 template <typename T, int S>
-__global__ void __launch_bounds__(256)
-k_interp(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ u, const T *__restrict__ v,
-           const T *__restrict__ w, const T *__restrict__ du, const T *__restrict__ dv, const T *__restrict__ dw,
-           T *__restrict__ U, const T *__restrict__ Ud, T inv_dt, T *__restrict__ F) {
-  pdl_wait();
+__global__ void __launch_bounds__(kMarkerThreads)
+k_interp(IbmGrid g, int n, const T *X, const T *__restrict__ u, const T *__restrict__ v, const T *__restrict__ w,
+         const T *__restrict__ du, const T *__restrict__ dv, const T *__restrict__ dw, T *__restrict__ U,
+         const T *Ud, T inv_dt, T *__restrict__ F, const T *__restrict__ X0, T *Xout, T *Udout, RigidMotion mo) {
+  __shared__ T xs[kMarkerThreads];
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= 3 * n) return;
   const int m = t / 3, c = t - 3 * m;
+  T ud_c = (T)0;
+  if (X0) {
+    T xc = (T)0;
+    if (t < 3 * n) {
+      xc = (T)displaced(X0[t], mo, c);  // X0 is a caller constant: read before the wait
+      ud_c = (T)mo.v[c];
+    }
+    xs[threadIdx.x] = xc;
+    __syncthreads();
+  }
+  pdl_wait();
+  if (t >= 3 * n) return;
+  if (X0) {
+    Xout[t] = xs[threadIdx.x];
+    Udout[t] = ud_c;
+  }
+  const int ml = threadIdx.x - c;  // this marker's first thread in the CTA
+  const T mx = X0 ? xs[ml] : X[3 * m], my = X0 ? xs[ml + 1] : X[3 * m + 1], mz = X0 ? xs[ml + 2] : X[3 * m + 2];
   int bx, by, bz;
   T fx, fy, fz;
-  stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], bx, by, bz, fx, fy, fz);
+  stencil_origin<T, S>(g, c, mx, my, mz, bx, by, bz, fx, fy, fz);
   const T *f = c == 0 ? u : c == 1 ? v : w;
   const T *df = c == 0 ? du : c == 1 ? dv : dw;
   T wx[S], wz[S];
@@ -125,7 +163,7 @@ k_interp(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ u, con
     }
   }
   if (U) U[t] = acc;
-  if (F) F[t] = (Ud[t] - acc) * inv_dt;  // Eq. 2c
+  if (F) F[t] = ((X0 ? ud_c : Ud[t]) - acc) * inv_dt;  // Eq. 2c
 }
 
 template <typename T, int S>
@@ -166,27 +204,6 @@ k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, con
   }
 }
 
-// L2: prescribed motion at time t (FP64 arithmetic, stored in plan precision)
-template <typename T>
-__global__ void k_motion(int n, const T *__restrict__ X0, T *__restrict__ X, T *__restrict__ Ud, int kind,
-                         double p0, double p1, double p2, double t) {
-  pdl_wait();
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= n) return;
-  double x = (double)X0[3 * m], y = (double)X0[3 * m + 1], z = (double)X0[3 * m + 2];
-  double ux = 0, uy = 0, uz = 0;
-  if (kind == IBM_MOTION_TRANSLATE) {
-    x += p0 * t; y += p1 * t; z += p2 * t;
-    ux = p0; uy = p1; uz = p2;
-  } else if (kind == IBM_MOTION_HEAVE) {
-    const double w = 2.0 * M_PI / p1;
-    y += p0 * sin(w * t);
-    uy = p0 * w * cos(w * t);
-  }
-  X[3 * m] = (T)x; X[3 * m + 1] = (T)y; X[3 * m + 2] = (T)z;
-  Ud[3 * m] = (T)ux; Ud[3 * m + 1] = (T)uy; Ud[3 * m + 2] = (T)uz;
-}
-
 static IbmGrid ibm_grid(const ibm_plan_s *p) {
   IbmGrid g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
@@ -199,17 +216,40 @@ static IbmGrid ibm_grid(const ibm_plan_s *p) {
   return g;
 }
 
+// Rigid-motion displacement and velocity at time t (FP64, host).
+static RigidMotion rigid_motion(int kind, const double *params, double t) {
+  RigidMotion mo = {};
+  if (kind == IBM_MOTION_TRANSLATE) {
+    for (int c = 0; c < 3; ++c) { mo.d[c] = params[c] * t; mo.v[c] = params[c]; }
+  } else if (kind == IBM_MOTION_HEAVE) {
+    const double w = 2.0 * M_PI / params[1];
+    mo.d[1] = params[0] * std::sin(w * t);
+    mo.v[1] = params[0] * w * std::cos(w * t);
+  }
+  for (int c = 0; c < 3; ++c) {
+    mo.dh[c] = (float)mo.d[c];
+    mo.dl[c] = (float)(mo.d[c] - (double)mo.dh[c]);
+  }
+  return mo;
+}
+
+// Interpolation (+ force); with X0, also the L2 motion of `kind` at time t
+// (X and Ud written to Xout, Udout).
 template <typename T>
 cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, const T *v, const T *w,
                           const T *du, const T *dv, const T *dw, T *U, const T *Ud, double inv_dt, T *F,
+                          const T *X0, T *Xout, T *Udout, int kind, const double *params, double t,
                           cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
   const IbmGrid g = ibm_grid(p);
-  const int tb = ceil_div(3 * n, 256);
+  const RigidMotion mo = X0 ? rigid_motion(kind, params, t) : RigidMotion{};
+  const int tb = ceil_div(3 * n, kMarkerThreads);
   if (p->delta == IBM_DELTA_PESKIN4)
-    IBM_KTRY(launch_pdl(k_interp<T, 4>, tb, 256, 0, st, g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F));
+    IBM_KTRY(launch_pdl(k_interp<T, 4>, tb, kMarkerThreads, 0, st, g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt,
+                        F, X0, Xout, Udout, mo));
   else
-    IBM_KTRY(launch_pdl(k_interp<T, 3>, tb, 256, 0, st, g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt, F));
+    IBM_KTRY(launch_pdl(k_interp<T, 3>, tb, kMarkerThreads, 0, st, g, n, X, u, v, w, du, dv, dw, U, Ud, (T)inv_dt,
+                        F, X0, Xout, Udout, mo));
   return cudaGetLastError();
 }
 
@@ -226,29 +266,20 @@ cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, co
   return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_motion(int n, const T *X0, T *X, T *Ud, int kind, const double *params, double t,
-                          cudaStream_t st) {
-  if (n <= 0) return cudaSuccess;
-  IBM_KTRY(launch_pdl(k_motion<T>, ceil_div(n, 256), 256, 0, st, n, X0, X, Ud, kind, params[0], params[1], params[2], t));
-  return cudaGetLastError();
-}
 
 template cudaError_t launch_interp<float>(const ibm_plan_s *, int, const float *, const float *, const float *,
                                           const float *, const float *, const float *, const float *, float *,
-                                          const float *, double, float *, cudaStream_t);
+                                          const float *, double, float *, const float *, float *, float *, int,
+                                          const double *, double, cudaStream_t);
 template cudaError_t launch_interp<double>(const ibm_plan_s *, int, const double *, const double *,
                                            const double *, const double *, const double *, const double *,
                                            const double *, double *, const double *, double, double *,
+                                           const double *, double *, double *, int, const double *, double,
                                            cudaStream_t);
 template cudaError_t launch_spread<float>(const ibm_plan_s *, int, const float *, const float *, const float *,
                                           float *, float *, float *, double, cudaStream_t);
 template cudaError_t launch_spread<double>(const ibm_plan_s *, int, const double *, const double *,
                                            const double *, double *, double *, double *, double, cudaStream_t);
-template cudaError_t launch_motion<float>(int, const float *, float *, float *, int, const double *, double,
-                                          cudaStream_t);
-template cudaError_t launch_motion<double>(int, const double *, double *, double *, int, const double *, double,
-                                           cudaStream_t);
 
 }  // namespace ibm
 
@@ -264,10 +295,12 @@ int ibm_interp(ibm_plan plan, int n, const void *X, const void *u, const void *v
   cudaError_t e;
   if (plan->precision == IBM_FP64)
     e = launch_interp<double>(plan, n, (const double *)X, (const double *)u, (const double *)v, (const double *)w,
-                              nullptr, nullptr, nullptr, (double *)U, nullptr, 0.0, nullptr, (cudaStream_t)stream);
+                              nullptr, nullptr, nullptr, (double *)U, nullptr, 0.0, nullptr, nullptr, nullptr, nullptr, 0,
+                              nullptr, 0.0, (cudaStream_t)stream);
   else
     e = launch_interp<float>(plan, n, (const float *)X, (const float *)u, (const float *)v, (const float *)w,
-                             nullptr, nullptr, nullptr, (float *)U, nullptr, 0.0, nullptr, (cudaStream_t)stream);
+                             nullptr, nullptr, nullptr, (float *)U, nullptr, 0.0, nullptr, nullptr, nullptr, nullptr, 0,
+                             nullptr, 0.0, (cudaStream_t)stream);
   return e == cudaSuccess ? IBM_OK : cuda_error(e, "ibm_interp");
 }
 

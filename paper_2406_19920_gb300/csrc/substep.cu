@@ -26,13 +26,11 @@ namespace ibm {
 template <typename T>
 cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, const T *v, const T *w,
                           const T *du, const T *dv, const T *dw, T *U, const T *Ud, double inv_dt, T *F,
+                          const T *X0, T *Xout, T *Udout, int kind, const double *params, double t,
                           cudaStream_t st);
 template <typename T>
 cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, const T *dV, T *fu, T *fv, T *fw,
                           double scale, cudaStream_t st);
-template <typename T>
-cudaError_t launch_motion(int n, const T *X0, T *X, T *Ud, int kind, const double *params, double t,
-                          cudaStream_t st);
 
 static const double kAlpha[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
 static const double kBeta[3] = {4.0 / 15.0, 1.0 / 15.0, 1.0 / 6.0};
@@ -345,14 +343,12 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   if (nmk > 0) {
     T *F = mk->F ? (T *)mk->F : (T *)p->mkbuf;
     {
-      ProfScope ps(p, IBM_K_MOTION, st);
-      IBM_CUDA_TRY(launch_motion<T>(nmk, (const T *)mk->X0, (T *)mk->X, (T *)mk->Ud, mk->motion, mk->params, s->t,
-                                    st));
-    }
-    {
+      // L2 (rigid marker motion at the stage start time) fused with L1's
+      // interpolation and force
       ProfScope ps(p, IBM_K_INTERP, st);
       IBM_CUDA_TRY(launch_interp<T>(p, nmk, (const T *)mk->X, u, v, w, du, dv, dw, nullptr, (const T *)mk->Ud,
-                                    1.0 / dt, F, st));
+                                    1.0 / dt, F, (const T *)mk->X0, (T *)mk->X, (T *)mk->Ud, mk->motion, mk->params,
+                                    s->t, st));
     }
     {
       ProfScope ps(p, IBM_K_SPREAD, st);
