@@ -27,8 +27,6 @@ namespace ibm {
 // --------------------------------------------------------------------------
 // plane kernels: one CTA per y-plane
 // --------------------------------------------------------------------------
-constexpr int kPlaneThreads = 512;
-
 // Shared memory (complex entries): tw2x [NX], tw2z [NZ], the spectrum plane
 // [NZ][P], and one exchange buffer reused by the x chunks (CP row pairs,
 // [CP][N1x][N2x+1]) and the z chunks (CW columns, [N1z][N2z][CW]); chunk
@@ -48,16 +46,24 @@ template <typename T, int NX, int NZ> struct PlaneCfg {
   static constexpr size_t xbytes = (size_t)CP * pair_bytes > (size_t)CW * col_bytes ? (size_t)CP * pair_bytes
                                                                                     : (size_t)CW * col_bytes;
   static constexpr size_t bytes = fixed + xbytes;
+  // threads: enough for the largest of the x step-1, x step-3 and z step-1
+  // job counts in one round (z step 3 takes N2z / N1z rounds), <= 1024
+  static constexpr int N1Z = TwoStep<NZ>::N1;
+  static constexpr int J3 = N2X / 2 + 1;
+  static constexpr int JMAX0 = CP * N1X > CP * J3 ? CP * N1X : CP * J3;
+  static constexpr int JMAX = JMAX0 > CW * N1Z ? JMAX0 : CW * N1Z;
+  static constexpr int THREADS = JMAX >= 1024 ? 1024 : (JMAX + 31) / 32 * 32;
 };
 
 template <typename T, int NX, int NZ>
-__global__ void __launch_bounds__(kPlaneThreads)
+__global__ void __launch_bounds__(PlaneCfg<T, NX, NZ>::THREADS)
 k_plane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__ twx,
             const cplx<T> *__restrict__ twz, T in_scale, double *zrhs) {
   const T *__restrict__ in = in_[blockIdx.y];
   cplx<T> *__restrict__ S = S_[blockIdx.y];
   using Cfg = PlaneCfg<T, NX, NZ>;
   constexpr int P = Cfg::P, N1X = Cfg::N1X, XPITCH = Cfg::XPITCH, CP = Cfg::CP, CW = Cfg::CW;
+  constexpr int kPlaneThreads_ = Cfg::THREADS;
   constexpr int N1Z = TwoStep<NZ>::N1, N2Z = TwoStep<NZ>::N2, J3 = Cfg::N2X / 2 + 1;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T> *tw2x = reinterpret_cast<cplx<T> *>(smem_raw);
@@ -73,12 +79,12 @@ k_plane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__
   const T *src = in + (size_t)j * NZ * NX;
   for (int p0 = 0; p0 < NZ / 2; p0 += CP) {
     const int np = min(CP, NZ / 2 - p0);
-    for (int job = tid; job < np * N1X; job += kPlaneThreads) {
+    for (int job = tid; job < np * N1X; job += kPlaneThreads_) {
       const int p = job / N1X, n1 = job - p * N1X;
       rfwd_step1<T, NX>(src + (size_t)(p0 + p) * 2 * NX, in_scale, n1, tw2x, X + (p * N1X + n1) * XPITCH);
     }
     __syncthreads();
-    for (int job = tid; job < np * J3; job += kPlaneThreads) {
+    for (int job = tid; job < np * J3; job += kPlaneThreads_) {
       const int p = job / J3, q = job - p * J3;
       cplx<T> *dA = plane + (p0 + p) * 2 * P;
       rfwd_step3<T, NX, XPITCH>(X + p * N1X * XPITCH, q, dA, dA + P);
@@ -88,13 +94,13 @@ k_plane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__
   cplx<T> *dst = S + (size_t)j * NZ * P;
   for (int c0 = 0; c0 < P; c0 += CW) {
     const int nc = min(CW, P - c0);
-    for (int job = tid; job < CW * N1Z; job += kPlaneThreads) {
+    for (int job = tid; job < CW * N1Z; job += kPlaneThreads_) {
       const int n1 = job / CW, c = job - n1 * CW;
       if (c < nc)
         col_step1<T, NZ, false, CW>(plane + c0 + c, P, n1, tw2z, X + n1 * N2Z * CW + c, false, mk<T>((T)0, (T)0));
     }
     __syncthreads();
-    for (int job = tid; job < CW * N2Z; job += kPlaneThreads) {
+    for (int job = tid; job < CW * N2Z; job += kPlaneThreads_) {
       const int k2 = job / CW, c = job - k2 * CW;
       if (c < nc) {
         const cplx<T> u0 = col_step3<T, NZ, false, CW>(X, c, k2, dst + c0 + c, P);
@@ -107,7 +113,7 @@ k_plane_fwd(Ptr3<const T *> in_, Ptr3<cplx<T> *> S_, const cplx<T> *__restrict__
 
 // Inverse: spectrum plane -> out = addend + scale * result.
 template <typename T, int NX, int NZ>
-__global__ void __launch_bounds__(kPlaneThreads)
+__global__ void __launch_bounds__(PlaneCfg<T, NX, NZ>::THREADS)
 k_plane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx<T> *__restrict__ twx,
             const cplx<T> *__restrict__ twz, T scale, const double *zsol) {
   const cplx<T> *__restrict__ S = S_[blockIdx.y];
@@ -115,6 +121,7 @@ k_plane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx
   const T *addend = add_[blockIdx.y];
   using Cfg = PlaneCfg<T, NX, NZ>;
   constexpr int P = Cfg::P, N1X = Cfg::N1X, N2X = Cfg::N2X, XPITCH = Cfg::XPITCH, CP = Cfg::CP, CW = Cfg::CW;
+  constexpr int kPlaneThreads_ = Cfg::THREADS;
   constexpr int N1Z = TwoStep<NZ>::N1, N2Z = TwoStep<NZ>::N2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cplx<T> *tw2x = reinterpret_cast<cplx<T> *>(smem_raw);
@@ -131,13 +138,13 @@ k_plane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx
   const cplx<T> z0 = zsol ? mk<T>((T)zsol[j], (T)0) : mk<T>((T)0, (T)0);
   for (int c0 = 0; c0 < P; c0 += CW) {
     const int nc = min(CW, P - c0);
-    for (int job = tid; job < CW * N1Z; job += kPlaneThreads) {
+    for (int job = tid; job < CW * N1Z; job += kPlaneThreads_) {
       const int n1 = job / CW, c = job - n1 * CW;
       if (c < nc)
         col_step1<T, NZ, true, CW>(src + c0 + c, P, n1, tw2z, X + n1 * N2Z * CW + c, zsol && c0 + c == 0, z0);
     }
     __syncthreads();
-    for (int job = tid; job < CW * N2Z; job += kPlaneThreads) {
+    for (int job = tid; job < CW * N2Z; job += kPlaneThreads_) {
       const int k2 = job / CW, c = job - k2 * CW;
       if (c < nc) col_step3<T, NZ, true, CW>(X, c, k2, plane + c0 + c, P);
     }
@@ -147,13 +154,13 @@ k_plane_inv(Ptr3<cplx<T> *> S_, Ptr3<T *> out_, Ptr3<const T *> add_, const cplx
   const T *add = addend ? addend + (size_t)j * NZ * NX : nullptr;
   for (int p0 = 0; p0 < NZ / 2; p0 += CP) {
     const int np = min(CP, NZ / 2 - p0);
-    for (int job = tid; job < np * N1X; job += kPlaneThreads) {
+    for (int job = tid; job < np * N1X; job += kPlaneThreads_) {
       const int p = job / N1X, n1 = job - p * N1X;
       const cplx<T> *sA = plane + (p0 + p) * 2 * P;
       rinv_step1<T, NX>(sA, sA + P, n1, tw2x, X + (p * N1X + n1) * XPITCH);
     }
     __syncthreads();
-    for (int job = tid; job < np * N2X; job += kPlaneThreads) {
+    for (int job = tid; job < np * N2X; job += kPlaneThreads_) {
       const int p = job / N2X, k2 = job - p * N2X;
       const size_t r = (size_t)(p0 + p) * 2 * NX;
       rinv_step3<T, NX, XPITCH>(X + p * N1X * XPITCH, k2, dst + r, dst + r + NX, add ? add + r : nullptr,
@@ -191,7 +198,7 @@ cudaError_t launch_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx
   if (nx == a && nz == b) {                                                                      \
     if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
       { cudaError_t e = ensure_max_smem<k_plane_fwd<T, a, b>>(); if (e) return e; }              \
-      IBM_KTRY(launch_pdl(k_plane_fwd<T, a, b>, dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st, in, S, twx, twz, in_scale, g.zrhs)); \
+      IBM_KTRY(launch_pdl(k_plane_fwd<T, a, b>, dim3(ny, g.nb), PlaneCfg<T, a, b>::THREADS, PlaneCfg<T, a, b>::bytes, st, in, S, twx, twz, in_scale, g.zrhs)); \
       return cudaGetLastError();                                                                 \
     }                                                                                            \
   }
@@ -213,7 +220,7 @@ cudaError_t launch_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> 
   if (nx == a && nz == b) {                                                                      \
     if constexpr (PlaneCfg<T, a, b>::ok) {                                                       \
       { cudaError_t e = ensure_max_smem<k_plane_inv<T, a, b>>(); if (e) return e; }              \
-      IBM_KTRY(launch_pdl(k_plane_inv<T, a, b>, dim3(ny, g.nb), kPlaneThreads, PlaneCfg<T, a, b>::bytes, st, S, out, addend, twx, twz, scale, g.zsol)); \
+      IBM_KTRY(launch_pdl(k_plane_inv<T, a, b>, dim3(ny, g.nb), PlaneCfg<T, a, b>::THREADS, PlaneCfg<T, a, b>::bytes, st, S, out, addend, twx, twz, scale, g.zsol)); \
       return cudaGetLastError();                                                                 \
     }                                                                                            \
   }
