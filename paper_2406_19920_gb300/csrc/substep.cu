@@ -71,12 +71,12 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
   pdl_wait();
   constexpr int TX = kExTX, TZ = kExTZ, HX = TX + 2, HZ = TZ + 2, PL = HX * HZ, NT = TX * TZ;
   constexpr int NL = (PL + NT - 1) / NT;  // plane elements each thread loads
-  __shared__ T su[3][PL], sv[3][PL], sw[3][PL], sp[2][PL];
+  __shared__ T su[3 * PL], sv[3 * PL], sw[3 * PL], sp[2 * PL];
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int tx = threadIdx.x, tz = threadIdx.y, tid = tz * TX + tx;
   const int i0 = blockIdx.x * TX, k0 = blockIdx.y * TZ;
   const int jb = blockIdx.z * kExJC, je = min(ny, jb + kExJC);
-  const size_t plane = (size_t)nz * nx;
+  const int plane = nz * nx;  // < 2^31 for every supported grid
   // halo-tile element -> offset inside a plane (periodic x, z), fixed for all planes
   int off[NL];
 #pragma unroll
@@ -99,24 +99,32 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
     for (int q = 0; q < NL; ++q)
       if (off[q] >= 0) buf[tid + q * NT] = r[q];
   };
-  auto slot = [](int jj) { return ((jj % 3) + 3) % 3; };
+  // ring slots of the planes j-1, j, j+1 (rotated each plane, no modulo)
+  int sm = 0, s0 = PL, sp1 = 2 * PL;
   {
     T r[NL];
-    for (int jj = jb - 1; jj <= jb + 1; ++jj) {
-      fetch(u_, jj, r); put(r, su[slot(jj)]);
-      fetch(v_, jj, r); put(r, sv[slot(jj)]);
-      fetch(w_, jj, r); put(r, sw[slot(jj)]);
-    }
-    fetch(p_, jb, r); put(r, sp[jb & 1]);
+    fetch(u_, jb - 1, r); put(r, su + sm);
+    fetch(v_, jb - 1, r); put(r, sv + sm);
+    fetch(w_, jb - 1, r); put(r, sw + sm);
+    fetch(u_, jb, r); put(r, su + s0);
+    fetch(v_, jb, r); put(r, sv + s0);
+    fetch(w_, jb, r); put(r, sw + s0);
+    fetch(u_, jb + 1, r); put(r, su + sp1);
+    fetch(v_, jb + 1, r); put(r, sv + sp1);
+    fetch(w_, jb + 1, r); put(r, sw + sp1);
+    fetch(p_, jb, r); put(r, sp);
   }
   __syncthreads();
   const int i = i0 + tx, k = k0 + tz;
   const bool inside = i < nx && k < nz;
   const int c = (tz + 1) * HX + (tx + 1);  // this column in a halo tile
-  T p_prev = (inside && jb > 0) ? p_[(size_t)(jb - 1) * plane + (size_t)k * nx + i] : (T)0;
+  const int col = k * nx + i;
+  T p_prev = (inside && jb > 0) ? p_[(size_t)(jb - 1) * plane + col] : (T)0;
   const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
   const T ihx2 = ihx * ihx, ihy2 = ihy * ihy, ihz2 = ihz * ihz;
   const T h = (T)0.5;
+  const bool n_prev = zet != (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
+  int pb = 0;                       // P ring slot of plane j (0 or PL)
   for (int j = jb; j < je; ++j) {
     T ru[NL], rv[NL], rw[NL], rp[NL];
     const bool more = j + 1 < je;
@@ -126,55 +134,50 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
       fetch(w_, j + 2, rw);
       fetch(p_, j + 1, rp);
     }
-    const T *sp_ = sp[j & 1];
     if (inside) {
-      const T *Um = su[slot(j - 1)], *Uc = su[slot(j)], *Up = su[slot(j + 1)];
-      const T *Vm = sv[slot(j - 1)], *Vc = sv[slot(j)], *Vp = sv[slot(j + 1)];
-      const T *Wm = sw[slot(j - 1)], *Wc = sw[slot(j)], *Wp = sw[slot(j + 1)];
+      const T *Um = su + sm + c, *Uc = su + s0 + c, *Up = su + sp1 + c;
+      const T *Vc = sv + s0 + c, *Vm = sv + sm + c, *Vp = sv + sp1 + c;
+      const T *Wm = sw + sm + c, *Wc = sw + s0 + c, *Wp = sw + sp1 + c;
+      const T *Pc = sp + pb + c;
       const bool lo = j == 0, hi = j + 1 >= ny;
-      const size_t idx = (size_t)j * plane + (size_t)k * nx + i;
-      // tile neighbours: (dk, di) relative to this column
-      auto at = [&](const T *B, int dk, int di) { return B[c + dk * HX + di]; };
-      // v on the faces of plane jj: zero at the walls jj <= 0 and jj >= ny
-      const T p0 = sp_[c];
+      const size_t idx = (size_t)j * plane + col;
+      // tile neighbours: B[dk * HX + di] relative to this column
+      const T p0 = Pc[0];
+      const T u0 = Uc[0], v0 = Vc[0], w0 = Wc[0];
       // ---------------- u (x-faces) ----------------
       {
-        const T u0 = at(Uc, 0, 0), ue = at(Uc, 0, 1), uw = at(Uc, 0, -1);
-        const T un = at(Uc, 1, 0), us = at(Uc, -1, 0);
-        const T uu = hi ? -u0 : at(Up, 0, 0), ud = lo ? -u0 : at(Um, 0, 0);
+        const T ue = Uc[1], uw = Uc[-1], un = Uc[HX], us = Uc[-HX];
+        const T uup = Up[0], udn = Um[0];
+        const T uu = hi ? -u0 : uup, ud = lo ? -u0 : udn;
         const T lap = (ue - 2 * u0 + uw) * ihx2 + (un - 2 * u0 + us) * ihz2 + (uu - 2 * u0 + ud) * ihy2;
         const T uc = h * (u0 + ue), ucm = h * (uw + u0);
         const T txx = (uc * uc - ucm * ucm) * ihx;
-        // y-flux at the faces j (q = 0) and j+1 (q = 1)
-        const T v0w = lo ? (T)0 : at(Vc, 0, -1), v0c = lo ? (T)0 : at(Vc, 0, 0);
-        const T v1w = hi ? (T)0 : at(Vp, 0, -1), v1c = hi ? (T)0 : at(Vp, 0, 0);
-        const T fy0 = lo ? (T)0 : (h * (v0w + v0c)) * (h * (at(Um, 0, 0) + u0));
-        const T fy1 = hi ? (T)0 : (h * (v1w + v1c)) * (h * (u0 + at(Up, 0, 0)));
-        const T fz0 = (h * (at(Wc, 0, -1) + at(Wc, 0, 0))) * (h * (us + u0));
-        const T fz1 = (h * (at(Wc, 1, -1) + at(Wc, 1, 0))) * (h * (u0 + un));
+        // y-flux at the faces j (zero at the wall j = 0) and j+1 (zero at j+1 = ny)
+        const T fy0 = lo ? (T)0 : (h * (Vc[-1] + v0)) * (h * (udn + u0));
+        const T fy1 = hi ? (T)0 : (h * (Vp[-1] + Vp[0])) * (h * (u0 + uup));
+        const T fz0 = (h * (Wc[-1] + w0)) * (h * (us + u0));
+        const T fz1 = (h * (Wc[HX - 1] + Wc[HX])) * (h * (u0 + un));
         const T N = txx + (fy1 - fy0) * ihy + (fz1 - fz0) * ihz;
-        const T G = (p0 - sp_[c - 1]) * ihx;
-        const T np = zet != (T)0 ? Nu[idx] : (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
+        const T G = (p0 - Pc[-1]) * ihx;
+        const T np = n_prev ? Nu[idx] : (T)0;
         du[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
         Nu[idx] = N;
       }
       // ---------------- w (z-faces) ----------------
       {
-        const T w0 = at(Wc, 0, 0), we = at(Wc, 0, 1), ww = at(Wc, 0, -1);
-        const T wn = at(Wc, 1, 0), ws = at(Wc, -1, 0);
-        const T wu = hi ? -w0 : at(Wp, 0, 0), wd = lo ? -w0 : at(Wm, 0, 0);
+        const T we = Wc[1], ww = Wc[-1], wn = Wc[HX], ws = Wc[-HX];
+        const T wup = Wp[0], wdn = Wm[0];
+        const T wu = hi ? -w0 : wup, wd = lo ? -w0 : wdn;
         const T lap = (we - 2 * w0 + ww) * ihx2 + (wn - 2 * w0 + ws) * ihz2 + (wu - 2 * w0 + wd) * ihy2;
         const T wc = h * (w0 + wn), wcm = h * (ws + w0);
         const T tzz = (wc * wc - wcm * wcm) * ihz;
-        const T fx0 = (h * (at(Uc, -1, 0) + at(Uc, 0, 0))) * (h * (ww + w0));
-        const T fx1 = (h * (at(Uc, -1, 1) + at(Uc, 0, 1))) * (h * (w0 + we));
-        const T v0s = lo ? (T)0 : at(Vc, -1, 0), v0c = lo ? (T)0 : at(Vc, 0, 0);
-        const T v1s = hi ? (T)0 : at(Vp, -1, 0), v1c = hi ? (T)0 : at(Vp, 0, 0);
-        const T fy0 = lo ? (T)0 : (h * (v0s + v0c)) * (h * (at(Wm, 0, 0) + w0));
-        const T fy1 = hi ? (T)0 : (h * (v1s + v1c)) * (h * (w0 + at(Wp, 0, 0)));
+        const T fx0 = (h * (Uc[-HX] + u0)) * (h * (ww + w0));
+        const T fx1 = (h * (Uc[1 - HX] + Uc[1])) * (h * (w0 + we));
+        const T fy0 = lo ? (T)0 : (h * (Vc[-HX] + v0)) * (h * (wdn + w0));
+        const T fy1 = hi ? (T)0 : (h * (Vp[-HX] + Vp[0])) * (h * (w0 + wup));
         const T N = tzz + (fx1 - fx0) * ihx + (fy1 - fy0) * ihy;
-        const T G = (p0 - sp_[c - HX]) * ihz;
-        const T np = zet != (T)0 ? Nw[idx] : (T)0;
+        const T G = (p0 - Pc[-HX]) * ihz;
+        const T np = n_prev ? Nw[idx] : (T)0;
         dw[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
         Nw[idx] = N;
       }
@@ -183,19 +186,18 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
         dv[idx] = (T)0;
         Nv[idx] = (T)0;
       } else {
-        const T v0 = at(Vc, 0, 0), ve = at(Vc, 0, 1), vw = at(Vc, 0, -1);
-        const T vn = at(Vc, 1, 0), vs = at(Vc, -1, 0);
-        const T vu = hi ? (T)0 : at(Vp, 0, 0), vd = j - 1 <= 0 ? (T)0 : at(Vm, 0, 0);
+        const T ve = Vc[1], vw = Vc[-1], vn = Vc[HX], vs = Vc[-HX];
+        const T vu = hi ? (T)0 : Vp[0], vd = j - 1 <= 0 ? (T)0 : Vm[0];
         const T lap = (ve - 2 * v0 + vw) * ihx2 + (vn - 2 * v0 + vs) * ihz2 + (vu - 2 * v0 + vd) * ihy2;
         const T vc = h * (v0 + vu), vcm = h * (vd + v0);
         const T tyy = (vc * vc - vcm * vcm) * ihy;
-        const T fx0 = (h * (at(Um, 0, 0) + at(Uc, 0, 0))) * (h * (vw + v0));
-        const T fx1 = (h * (at(Um, 0, 1) + at(Uc, 0, 1))) * (h * (v0 + ve));
-        const T fz0 = (h * (at(Wm, 0, 0) + at(Wc, 0, 0))) * (h * (vs + v0));
-        const T fz1 = (h * (at(Wm, 1, 0) + at(Wc, 1, 0))) * (h * (v0 + vn));
+        const T fx0 = (h * (Um[0] + u0)) * (h * (vw + v0));
+        const T fx1 = (h * (Um[1] + Uc[1])) * (h * (v0 + ve));
+        const T fz0 = (h * (Wm[0] + w0)) * (h * (vs + v0));
+        const T fz1 = (h * (Wm[HX] + Wc[HX])) * (h * (v0 + vn));
         const T N = tyy + (fx1 - fx0) * ihx + (fz1 - fz0) * ihz;
         const T G = (p0 - p_prev) * ihy;
-        const T np = zet != (T)0 ? Nv[idx] : (T)0;
+        const T np = n_prev ? Nv[idx] : (T)0;
         dv[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
         Nv[idx] = N;
       }
@@ -203,10 +205,14 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
     }
     __syncthreads();
     if (more) {
-      put(ru, su[slot(j + 2)]);
-      put(rv, sv[slot(j + 2)]);
-      put(rw, sw[slot(j + 2)]);
-      put(rp, sp[(j + 1) & 1]);
+      // plane j+2 replaces plane j-1; the ring rotates
+      put(ru, su + sm);
+      put(rv, sv + sm);
+      put(rw, sw + sm);
+      put(rp, sp + (PL - pb));
+      const int t = sm;
+      sm = s0; s0 = sp1; sp1 = t;
+      pb = PL - pb;
       __syncthreads();
     }
   }
