@@ -289,16 +289,16 @@ __device__ __forceinline__ void rinv_step3(const cplx<T> *xp, int k2, T *da, T *
   }
 }
 
-// Columns, step 1, lane n1 of column `col` (element n at col[n * stride]);
-// x = X + n1 N2 W + c (the column's entries W apart).  With sub0, element 0
-// is replaced by v0 before transforming.
-template <typename T, int N, bool INV, int W>
-__device__ __forceinline__ void col_step1(const cplx<T> *col, size_t stride, int n1, const cplx<T> *tw2, cplx<T> *x,
-                                          bool sub0, cplx<T> v0) {
+// Columns, step 1, lane n1 of one column; at(n1, n2) points at element
+// n1 + N1 n2 of the column (so a column may be spread over several CTAs'
+// shared memory); x = X + n1 N2 W + c (the column's entries W apart).  With
+// sub0, element 0 is replaced by v0 before transforming.
+template <typename T, int N, bool INV, int W, typename At>
+__device__ __forceinline__ void col_step1_at(At at, int n1, const cplx<T> *tw2, cplx<T> *x, bool sub0, cplx<T> v0) {
   constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
   cplx<T> v[N2];
 #pragma unroll
-  for (int n2 = 0; n2 < N2; ++n2) v[n2] = col[(size_t)(n1 + N1 * n2) * stride];
+  for (int n2 = 0; n2 < N2; ++n2) v[n2] = *at(n1, n2);
   if (sub0 && n1 == 0) v[0] = v0;
   reg_dft<INV, N2>(v);
   x[0] = v[0];
@@ -309,18 +309,32 @@ __device__ __forceinline__ void col_step1(const cplx<T> *col, size_t stride, int
   }
 }
 
-// Columns, step 3, job (c, k2): writes col[(k2 + N2 k1) stride]; returns the
-// k1 = 0 output (bin k2).
-template <typename T, int N, bool INV, int W>
-__device__ __forceinline__ cplx<T> col_step3(const cplx<T> *X, int c, int k2, cplx<T> *col, size_t stride) {
+// Columns, step 3, job (c, k2): writes element k2 + N2 k1 to *at(k2, k1);
+// returns the k1 = 0 output (bin k2).
+template <typename T, int N, bool INV, int W, typename At>
+__device__ __forceinline__ cplx<T> col_step3_at(const cplx<T> *X, int c, int k2, At at) {
   constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
   cplx<T> u[N1];
 #pragma unroll
   for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[(n1 * N2 + k2) * W + c];
   reg_dft<INV, N1>(u);
 #pragma unroll
-  for (int k1 = 0; k1 < N1; ++k1) col[(size_t)(k2 + N2 * k1) * stride] = u[k1];
+  for (int k1 = 0; k1 < N1; ++k1) *at(k2, k1) = u[k1];
   return u[0];
+}
+
+// The same for a column of stride `stride` from `col`.
+template <typename T, int N, bool INV, int W>
+__device__ __forceinline__ void col_step1(const cplx<T> *col, size_t stride, int n1, const cplx<T> *tw2, cplx<T> *x,
+                                          bool sub0, cplx<T> v0) {
+  constexpr int N1 = TwoStep<N>::N1;
+  col_step1_at<T, N, INV, W>([&](int a, int b) { return col + (size_t)(a + N1 * b) * stride; }, n1, tw2, x, sub0,
+                             v0);
+}
+template <typename T, int N, bool INV, int W>
+__device__ __forceinline__ cplx<T> col_step3(const cplx<T> *X, int c, int k2, cplx<T> *col, size_t stride) {
+  constexpr int N2 = TwoStep<N>::N2;
+  return col_step3_at<T, N, INV, W>(X, c, k2, [&](int a, int b) { return col + (size_t)(a + N2 * b) * stride; });
 }
 
 }  // namespace ibm
