@@ -383,8 +383,13 @@ def run_gpu(args):
     e2e_ms = e0.elapsed_time(e1)
     e2e_value = pts * e2e_steps * ws / (e2e_ms * 1e-3)
 
-    # ---- standalone Poisson: FP32-refined vs FP64 at 128^3 ----
-    solves = poisson_compare(ibm, torch, g)
+    # ---- standalone Poisson: FP32-refined vs FP64 at 128^3, and 256^3 ----
+    solves = poisson_compare(ibm, torch, NX, (("fp32_refined", ibm.IBM_FP32_REFINED, 1), ("fp64", ibm.IBM_FP64, 0)))
+    solves_256 = None
+    if not args.no_extras:
+        solves_256 = poisson_compare(ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0),
+                                                       ("fp32_refined", ibm.IBM_FP32_REFINED, 1),
+                                                       ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20)
 
     # ---- batched (64 instances, one graph launch) and served workloads ----
     batched = batched_compare(ibm, torch) if not args.no_extras else None
@@ -434,6 +439,7 @@ def run_gpu(args):
         "p99_ms": float(np.percentile(step_ms, 99)),
         "value_traced": pts * args.steps * ws / (traced_ms * 1e-3),
         "poisson": solves,
+        "poisson_256": solves_256,
         "batched": batched,
         "serving": serving,
         "large_plate": plate,
@@ -450,22 +456,35 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
-def poisson_compare(ibm, torch, g):
-    """Standalone Poisson solves/s at 128^3: FP32 + 1 refinement vs FP64, and
-    the FP32 result's relative L2 difference from the FP64 GPU result."""
+def method_bytes(n, precision_bytes, refine):
+    """Compulsory HBM bytes of one Poisson solve on an n^3 grid: forward
+    (read field, write spectrum), pencil (read + write spectrum), inverse
+    (read spectrum, write field); a refinement step adds the residual (read
+    b and x, write r), a second solve and the read of the updated field."""
+    pts = n ** 3
+    spec = n * n * (n // 2 + 1)
+    s = precision_bytes
+    solve = pts * s + 2 * spec * s + 2 * 2 * spec * s + 2 * spec * s + pts * s
+    return solve + refine * (3 * pts * s + solve + pts * s)
+
+
+def poisson_compare(ibm, torch, n, variants, nb=16, K=40):
+    """Standalone Poisson solves on an n^3 grid ([0,2pi)x[0,2]x[0,2pi],
+    low-passed noise right-hand side): solves/s, p50/p99 latency, and the
+    achieved fraction of the measured HBM bandwidth for the solve's method
+    bytes; relative L2 of each FP32 result against the FP64 GPU result."""
     from paper_2406_19920_gb300 import synth
-    b = synth.rhs_lowpass_noise(NX, NY, NZ, kmax=32.0, workload=1)
+    g = synth.grid(n, n, n)
+    b = synth.rhs_lowpass_noise(n, n, n, kmax=min(32.0, n / 4), workload=1)
     res = {}
     outs = {}
-    for name, prec, dt, ref in (("fp32_refined", ibm.IBM_FP32_REFINED, torch.float32, 1),
-                                ("fp64", ibm.IBM_FP64, torch.float64, 0)):
-        plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], prec, ref)
-        nb = 16  # 16 rhs + 16 solutions > L2
-        rhs = [torch.from_numpy(b).to("cuda", dt) for _ in range(nb)]
+    for name, prec, ref in variants:
+        dt = torch.float32 if prec == ibm.IBM_FP32_REFINED else torch.float64
+        plan = ibm.ibm_plan_create(n, n, n, g[3:], prec, ref)
+        rhs = [torch.from_numpy(b).to("cuda", dt) for _ in range(nb)]  # nb rhs + nb solutions > L2
         phi = [torch.empty_like(r) for r in rhs]
         for i in range(3):
             ibm.ibm_poisson_solve(plan, rhs[i], phi[i])
-        K = 40
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(K + 1)]
         torch.cuda.synchronize()
         evs[0].record()
@@ -476,15 +495,20 @@ def poisson_compare(ibm, torch, g):
         lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
         ms = evs[0].elapsed_time(evs[-1]) / K
         outs[name] = phi[0].double().cpu().numpy()
-        res[name] = {"solves_per_s": 1e3 / ms, "grid_pts_per_s": NX * NY * NZ * 1e3 / ms, "ms": ms,
+        mb = method_bytes(n, 4 if dt == torch.float32 else 8, ref if dt == torch.float32 else 0)
+        res[name] = {"solves_per_s": 1e3 / ms, "grid_pts_per_s": n ** 3 * 1e3 / ms, "ms": ms,
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                     "hbm_frac_method_bytes": (24 if dt == torch.float32 else 48) * NX * NY * NZ / (ms * 1e-3)
-                     / 1e9 / measured_peak()[0]}
+                     "method_bytes": mb,
+                     "hbm_frac_method_bytes": mb / (ms * 1e-3) / 1e9 / measured_peak()[0]}
         ibm.ibm_plan_destroy(plan)
         del rhs, phi
-    d = outs["fp32_refined"] - outs["fp64"]
-    res["fp32_refined_rel_l2_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(outs["fp64"]))
-    res["speedup_fp32_refined_over_fp64"] = res["fp32_refined"]["solves_per_s"] / res["fp64"]["solves_per_s"]
+        torch.cuda.empty_cache()
+    for name in outs:
+        if name != "fp64" and "fp64" in outs:
+            d = outs[name] - outs["fp64"]
+            res[name]["rel_l2_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(outs["fp64"]))
+    if "fp32_refined" in res and "fp64" in res:
+        res["speedup_fp32_refined_over_fp64"] = res["fp32_refined"]["solves_per_s"] / res["fp64"]["solves_per_s"]
     return res
 
 
