@@ -40,6 +40,7 @@ import numpy as np
 NEUMANN = 0
 CELL_DIRICHLET = 1
 FACE_DIRICHLET = 2
+PERIODIC = 3  # the triply periodic branch (Sec. 2.3.3, S2: y periodic as well)
 
 ROMA3 = 0
 PESKIN4 = 1
@@ -99,7 +100,10 @@ def wall_basis(n, field_bc):
     Angle theta = pi m / n in every case.  Returns (Q, theta) where Q has one
     row per stored plane (n rows; for FACE_DIRICHLET row 0 is the wall face
     and is identically zero, with n-1 columns).
+    PERIODIC (no walls, the triply periodic branch): the Fourier basis.
     """
+    if field_bc == PERIODIC:
+        return fourier_basis(n)
     j = np.arange(n, dtype=np.float64)
     if field_bc == NEUMANN:
         m = np.arange(n, dtype=np.float64)
@@ -148,7 +152,7 @@ def _eigen_sum(grid, field_bc):
 # Linear solves: Eq. 2e (Helmholtz) and Eq. 2f (Poisson), Sec. 2.3.3
 # ---------------------------------------------------------------------------
 
-def poisson_solve(b, grid, nullspace="mean"):
+def poisson_solve(b, grid, nullspace="mean", ybc=NEUMANN):
     """Solve L_h phi = b - mean(b) on the staggered grid (Eq. 2f, S2 / S2.1).
 
     L_h is the 7-point Laplacian (second-order central differences, Sec. 2.1)
@@ -161,12 +165,18 @@ def poisson_solve(b, grid, nullspace="mean"):
       nullspace="pin":  the x-z mean of phi on the first interior plane is 0
                          (Sec. 2.3.3, S2.1: phi_hat(x_b + h/2, 0, 0) = 0).
     Method: exact eigen-decomposition with dense orthonormal bases.
+    ybc=PERIODIC is the triply periodic branch (Sec. 2.3.3, S2: Fourier
+    along all three axes, the divide diagonal, mean(phi) = 0).
     Returns (phi, removed_mean).
     """
     b = np.asarray(b, dtype=np.float64)
     mean_b = b.mean()
     rhs = b - mean_b
-    Q, lam = _eigen_sum(grid, NEUMANN)
+    if ybc not in (NEUMANN, PERIODIC):
+        raise ValueError("ybc must be NEUMANN or PERIODIC")
+    if ybc == PERIODIC and nullspace != "mean":
+        raise ValueError("the triply periodic branch fixes mean(phi) = 0")
+    Q, lam = _eigen_sum(grid, ybc)
     c = _to_modes(rhs, *Q)
     lam = lam.copy()
     lam[0, 0, 0] = 1.0
@@ -185,8 +195,8 @@ def helmholtz_solve(r, grid, c, field_bc):
 
     Eq. 2e reads  lap u* - (Re / (beta dt)) u* = -(Re / (beta dt)) RHS, which
     is (I - c L_h) u* = RHS with c = beta dt / Re.  field_bc selects the
-    wall rows of Appendix B.  For FACE_DIRICHLET plane 0 (the wall face) of
-    the input is ignored and of the output is 0.
+    wall rows of Appendix B (PERIODIC: no walls).  For FACE_DIRICHLET plane 0
+    (the wall face) of the input is ignored and of the output is 0.
     """
     r = np.asarray(r, dtype=np.float64)
     Q, lam = _eigen_sum(grid, field_bc)
@@ -211,6 +221,8 @@ def _ypad(f, field_bc):
         out[1] = 0.0          # stored bottom wall face
         out[0] = 0.0          # never used by interior faces
         out[-1] = 0.0         # top wall face j = ny
+    elif field_bc == PERIODIC:
+        out[0], out[-1] = f[-1], f[0]
     else:
         raise ValueError("unknown field_bc")
     return out

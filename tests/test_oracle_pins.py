@@ -61,7 +61,8 @@ def _wall_1d(n, h, bc):
 def _dense_laplacian(grid, bc):
     """Kronecker sum for the (y, z, x) C-order unknown vector."""
     nx, ny, nz, hx, hy, hz = grid
-    Ax, Az, Ay = _periodic_1d(nx, hx), _periodic_1d(nz, hz), _wall_1d(ny, hy, bc)
+    Ay = _periodic_1d(ny, hy) if bc == O.PERIODIC else _wall_1d(ny, hy, bc)
+    Ax, Az = _periodic_1d(nx, hx), _periodic_1d(nz, hz)
     Iy, Iz, Ix = np.eye(Ay.shape[0]), np.eye(nz), np.eye(nx)
     return (np.kron(np.kron(Ay, Iz), Ix) + np.kron(np.kron(Iy, Az), Ix)
             + np.kron(np.kron(Iy, Iz), Ax))
@@ -170,6 +171,68 @@ def test_helmholtz_matches_dense(grid, bc, c):
     assert O.rel_l2(u, _unpack(x, grid, bc)) < 1e-12
     if bc == O.FACE_DIRICHLET:
         assert np.all(u[0] == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# triply periodic branch (Sec. 2.3.3, S2): y periodic as well
+# ---------------------------------------------------------------------------
+
+GRIDS_3P = [_grid(8, 8, 8), _grid(6, 12, 4, Lx=1.3, Ly=0.7, Lz=2.1)]
+
+
+@pytest.mark.parametrize("grid", GRIDS_3P)
+def test_periodic_laplacian_matches_dense(grid):
+    A = _dense_laplacian(grid, O.PERIODIC)
+    f = np.random.default_rng(31).standard_normal((grid[1], grid[2], grid[0]))
+    want = (A @ f.ravel()).reshape(f.shape)
+    got = O.laplacian(f, grid, O.PERIODIC)
+    assert np.allclose(got, want, rtol=0, atol=1e-11 * np.abs(want).max())
+
+
+@pytest.mark.parametrize("grid", GRIDS_3P)
+def test_periodic_poisson_matches_dense_bordered_solve(grid):
+    nx, ny, nz = grid[:3]
+    A = _dense_laplacian(grid, O.PERIODIC)
+    b = np.random.default_rng(32).standard_normal((ny, nz, nx))
+    N = A.shape[0]
+    B = np.zeros((N + 1, N + 1))
+    B[:N, :N] = A
+    B[:N, N] = 1.0
+    B[N, :N] = 1.0
+    x = np.linalg.solve(B, np.concatenate([(b - b.mean()).ravel(), [0.0]]))
+    assert abs(x[N]) < 1e-10
+    phi, mean_b = O.poisson_solve(b, grid, ybc=O.PERIODIC)
+    assert abs(mean_b - b.mean()) < 1e-15
+    assert abs(phi.mean()) < 1e-14
+    assert O.rel_l2(phi, x[:N].reshape(ny, nz, nx)) < 1e-12
+    with pytest.raises(ValueError):
+        O.poisson_solve(b, grid, nullspace="pin", ybc=O.PERIODIC)
+
+
+@pytest.mark.parametrize("grid", GRIDS_3P)
+@pytest.mark.parametrize("c", [1e-3, 0.25])
+def test_periodic_helmholtz_matches_dense(grid, c):
+    nx, ny, nz = grid[:3]
+    A = _dense_laplacian(grid, O.PERIODIC)
+    r = np.random.default_rng(33).standard_normal((ny, nz, nx))
+    x = np.linalg.solve(np.eye(A.shape[0]) - c * A, r.ravel())
+    u = O.helmholtz_solve(r, grid, c, O.PERIODIC)
+    assert O.rel_l2(u, x.reshape(ny, nz, nx)) < 1e-12
+
+
+def test_periodic_manufactured_mode_exact():
+    """A Fourier mode in all three axes is an exact discrete eigenfunction."""
+    g = _grid(24, 16, 32, Ly=3.0)
+    nx, ny, nz, hx, hy, hz = g
+    i, j, k = np.arange(nx), np.arange(ny), np.arange(nz)
+    phi = (np.sin(2 * math.pi * 3 * j / ny)[:, None, None]
+           * np.cos(2 * math.pi * 5 * k / nz)[None, :, None]
+           * np.sin(2 * math.pi * 2 * i / nx)[None, None, :])
+    lam = (O.modified_wavenumber_sq(2 * math.pi * 2 / nx, hx) + O.modified_wavenumber_sq(2 * math.pi * 3 / ny, hy)
+           + O.modified_wavenumber_sq(2 * math.pi * 5 / nz, hz))
+    assert np.abs(O.laplacian(phi, g, O.PERIODIC) + lam * phi).max() < 1e-11 * lam
+    got, _ = O.poisson_solve(-lam * phi, g, ybc=O.PERIODIC)
+    assert O.rel_l2(got, phi) < 1e-13
 
 
 def test_manufactured_eigenfunction_exact():
