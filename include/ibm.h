@@ -70,9 +70,15 @@ enum {
   IBM_ERR_CANCELLED = -7
 };
 
-/* Domain boundary conditions: periodic x and z, walls in y (the paper's
- * doubly periodic branch, Sec. 2.3.3, with its wall axis renamed y). */
-enum { IBM_BC_PXZ_WALL_Y = 1 };
+/* Domain boundary conditions.
+ * IBM_BC_PXZ_WALL_Y: periodic x and z, walls in y (the paper's doubly
+ *   periodic branch, Sec. 2.3.3, with its wall axis renamed y): every entry
+ *   point.
+ * IBM_BC_TRIPLY_PERIODIC: periodic in all three axes (Sec. 2.3.3, S2): the
+ *   Poisson and Helmholtz solves only (ny must then be 2^a 3^b, b <= 1, in
+ *   [8, 512]); ibm_substep, ibm_interp and ibm_spread return
+ *   IBM_ERR_UNSUPPORTED for such plans. */
+enum { IBM_BC_PXZ_WALL_Y = 1, IBM_BC_TRIPLY_PERIODIC = 2 };
 
 /* Precision of fields and of the bulk arithmetic. */
 enum { IBM_FP64 = 0, IBM_FP32_REFINED = 1 };
@@ -81,7 +87,8 @@ enum { IBM_FP64 = 0, IBM_FP32_REFINED = 1 };
 enum {
   IBM_FIELD_CELL_NEUMANN = 0,   /* cell-centred, ghost = first value        */
   IBM_FIELD_CELL_DIRICHLET = 1, /* cell-centred no-slip: alpha = 2, A11 = A1 - A2 */
-  IBM_FIELD_FACE_DIRICHLET = 2  /* wall-normal faces: alpha = 1, walls = 0   */
+  IBM_FIELD_FACE_DIRICHLET = 2, /* wall-normal faces: alpha = 1, walls = 0   */
+  IBM_FIELD_PERIODIC = 3        /* no walls: the triply periodic branch's only kind */
 };
 
 /* Regularised delta kernels (Sec. 2.1 cites Peskin and Roma et al.). */
@@ -105,7 +112,8 @@ typedef struct {
  * ------------------------------------------------------------------------- */
 
 /* Create a plan for an nx x ny x nz grid with spacings h[3] = {hx, hy, hz}.
- * bc: IBM_BC_PXZ_WALL_Y.  precision: IBM_FP64 or IBM_FP32_REFINED.
+ * bc: IBM_BC_PXZ_WALL_Y or IBM_BC_TRIPLY_PERIODIC.  precision: IBM_FP64 or
+ * IBM_FP32_REFINED.
  * refine_iters: iterative-refinement steps on the residual for the FP32 path
  * (0..4; ignored for FP64).  Allocates the plan's device workspace
  * (about 4 fields) and its FP64-derived twiddle and modified-wavenumber
@@ -152,7 +160,9 @@ int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launche
  * A3 + A2 corner rows), mean(phi) = 0.  rhs and phi are [ny][nz][nx]; rhs may
  * equal phi.  The zero-wavenumber pencil is eliminated in FP64 with the
  * paper's pin (phi_hat = 0 at the first interior point, Sec. 2.3.3), then
- * its FP64 mean is removed. */
+ * its FP64 mean is removed.  On an IBM_BC_TRIPLY_PERIODIC plan y is periodic
+ * too (Sec. 2.3.3, S2): every (kx, kz) pencil is Fourier-transformed along y
+ * and divided by its eigenvalue, the (0,0,0) mode set to 0. */
 int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream,
                       ibm_info *info);
 
@@ -174,7 +184,8 @@ int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[3], int ref
                               const float *rhs, float *phi, void *stream);
 
 /* Helmholtz solve, Eq. 2e (S1.1 + S1.2): (I - c L_h) u = rhs, c > 0, with the
- * wall rows selected by field_bc (Appendix B).  Eq. 2e is this system with
+ * wall rows selected by field_bc (Appendix B; IBM_FIELD_PERIODIC, and only
+ * that, on an IBM_BC_TRIPLY_PERIODIC plan).  Eq. 2e is this system with
  * c = beta_n dt / Re.  rhs may equal u. */
 int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs,
                         void *u, void *stream, ibm_info *info);

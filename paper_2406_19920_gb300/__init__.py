@@ -18,9 +18,9 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libibm.so")
 IBM_OK, IBM_PENDING = 0, 1
 IBM_ERR_ARG, IBM_ERR_OOM, IBM_ERR_CUDA, IBM_ERR_TIMEOUT, IBM_ERR_BUSY, IBM_ERR_UNSUPPORTED, IBM_ERR_CANCELLED = \
     -1, -2, -3, -4, -5, -6, -7
-IBM_BC_PXZ_WALL_Y = 1
+IBM_BC_PXZ_WALL_Y, IBM_BC_TRIPLY_PERIODIC = 1, 2
 IBM_FP64, IBM_FP32_REFINED = 0, 1
-IBM_FIELD_CELL_NEUMANN, IBM_FIELD_CELL_DIRICHLET, IBM_FIELD_FACE_DIRICHLET = 0, 1, 2
+IBM_FIELD_CELL_NEUMANN, IBM_FIELD_CELL_DIRICHLET, IBM_FIELD_FACE_DIRICHLET, IBM_FIELD_PERIODIC = 0, 1, 2, 3
 IBM_DELTA_ROMA3, IBM_DELTA_PESKIN4 = 0, 1
 IBM_MOTION_STATIC, IBM_MOTION_TRANSLATE, IBM_MOTION_HEAVE = 0, 1, 2
 IBM_REQ_POISSON, IBM_REQ_HELMHOLTZ, IBM_REQ_SUBSTEP = 0, 1, 2

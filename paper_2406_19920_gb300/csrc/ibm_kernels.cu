@@ -291,6 +291,8 @@ int ibm_interp(ibm_plan plan, int n, const void *X, const void *u, const void *v
                void *stream) {
   if (!plan || n < 0 || (n > 0 && (!X || !u || !v || !w || !U)))
     return set_error(IBM_ERR_ARG, "ibm_interp: bad argument");
+  if (plan->bc != IBM_BC_PXZ_WALL_Y)
+    return set_error(IBM_ERR_UNSUPPORTED, "ibm_interp: the delta stencils are built for the wall-bounded branch");
   if (n > (1 << 28)) return set_error(IBM_ERR_ARG, "ibm_interp: n too large");
   cudaError_t e;
   if (plan->precision == IBM_FP64)
@@ -308,6 +310,8 @@ int ibm_spread(ibm_plan plan, int n, const void *X, const void *F, const void *d
                void *stream) {
   if (!plan || n < 0 || (n > 0 && (!X || !F || !dV || !fu || !fv || !fw)))
     return set_error(IBM_ERR_ARG, "ibm_spread: bad argument");
+  if (plan->bc != IBM_BC_PXZ_WALL_Y)
+    return set_error(IBM_ERR_UNSUPPORTED, "ibm_spread: the delta stencils are built for the wall-bounded branch");
   if (n > (1 << 28)) return set_error(IBM_ERR_ARG, "ibm_spread: n too large");
   cudaError_t e;
   if (plan->precision == IBM_FP64)

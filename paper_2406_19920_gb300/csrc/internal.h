@@ -165,6 +165,9 @@ struct PencilParams {
   const double *zrhs;      // zero_mode: right-hand side of the (0,0) pencil, [ny] (from the forward pass)
   double *zsol;            // zero_mode: its FP64 solution, [ny] (read by the inverse pass)
   double inv_ny;           // 1/ny
+  int periodic;            // triply periodic branch: y-transform + divide (twy, lamy) instead of Thomas
+  const void *twy;         // periodic: W_ny^m twiddles (plan precision)
+  const void *lamy;        // periodic: lambda_y(ky) (plan precision)
   int nb;                  // fields in the launch; field b > 0 takes its wall rows from fbc[b]
   int fbc[kMaxFields];     // beta_s | beta_e << 4 | j0 << 8 of each field
 };
@@ -179,6 +182,10 @@ __device__ __forceinline__ void pencil_field(const PencilParams &pp, int b, int 
 template <typename T>
 cudaError_t launch_pencil(const PencilParams &pp, Ptr3<cplx<T> *> S, const T *lamx, const T *lamz, double *mean_out,
                           cudaStream_t st);
+// The triply periodic branch's pencil step (periodic.cu).
+template <typename T>
+cudaError_t launch_ypencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const cplx<T> *twy, const T *lamx,
+                           const T *lamz, const T *lamy, double *mean_out, cudaStream_t st);
 
 // Residual r = b - (sigma x + tau L x) with float-float arithmetic for FP32.
 struct StencilCoef {

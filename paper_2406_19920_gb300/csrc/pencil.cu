@@ -721,6 +721,9 @@ static long resident_ctas(size_t bytes) {
 template <typename T>
 cudaError_t launch_pencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const T *lamx, const T *lamz, double *mean_out,
                           cudaStream_t st) {
+  if (pp.periodic)
+    return launch_ypencil<T>(pp, S3, static_cast<const cplx<T> *>(pp.twy), lamx, lamz,
+                             static_cast<const T *>(pp.lamy), mean_out, st);
   if (pp.mode == 1 && pp.nb > 1) {
     // the warp-parallel block solve takes one field per launch
     for (int b = 0; b < pp.nb; ++b) {

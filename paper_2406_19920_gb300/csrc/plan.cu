@@ -77,6 +77,18 @@ static int upload_tables(ibm_plan_s *p) {
   IBM_CUDA_TRY(cudaMemcpy(p->twz, twz.data(), sizeof(cplx<T>) * nz, cudaMemcpyHostToDevice));
   IBM_CUDA_TRY(cudaMemcpy(p->lamx, lx.data(), sizeof(T) * P, cudaMemcpyHostToDevice));
   IBM_CUDA_TRY(cudaMemcpy(p->lamz, lz.data(), sizeof(T) * nz, cudaMemcpyHostToDevice));
+  if (p->bc == IBM_BC_TRIPLY_PERIODIC) {
+    const int ny = p->ny;
+    std::vector<cplx<T>> twy(ny);
+    std::vector<T> ly(ny);
+    for (int m = 0; m < ny; ++m) {
+      const double a = 2.0 * M_PI * (double)m / ny;
+      twy[m] = mk<T>((T)std::cos(a), (T)-std::sin(a));
+      ly[m] = (T)(2.0 / (p->h[1] * p->h[1]) * (1.0 - std::cos(a)));
+    }
+    IBM_CUDA_TRY(cudaMemcpy(p->twy, twy.data(), sizeof(cplx<T>) * ny, cudaMemcpyHostToDevice));
+    IBM_CUDA_TRY(cudaMemcpy(p->lamy, ly.data(), sizeof(T) * ny, cudaMemcpyHostToDevice));
+  }
   return IBM_OK;
 }
 
@@ -109,7 +121,7 @@ static void plan_free(ibm_plan_s *p) {
   if (!p) return;
   for (auto &r : p->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : p->evpool) cudaEventDestroy(e);
-  void *bufs[] = {p->S, p->Sx[0], p->Sx[1], p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3],
+  void *bufs[] = {p->S, p->Sx[0], p->Sx[1], p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3], p->twy, p->lamy,
                   p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf};
   for (void *b : bufs)
     if (b) cudaFree(b);
@@ -137,8 +149,8 @@ static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out
                       double *mean_out, cudaStream_t st) {
   TransformGeom gf = geom_of(p), gi = geom_of(p);
   if (pp.zero_mode) {
-    gf.zrhs = p->zbuf;
-    gi.zsol = p->zbuf + p->ny;
+    gf.zrhs = p->zbuf;                               // plane sums of b (FP64)
+    if (!pp.periodic) gi.zsol = p->zbuf + p->ny;     // the wall branch's FP64 zero pencil
   }
   const TransformGeom &g = gf;
   cplx<T> *S = static_cast<cplx<T> *>(p->S);
@@ -188,6 +200,12 @@ static PencilParams pencil_params(const ibm_plan_s *p, int kind, double c, int f
   pp.zsol = p->zbuf + p->ny;
   pp.inv_ny = 1.0 / p->ny;
   pp.nb = 1;
+  if (p->bc == IBM_BC_TRIPLY_PERIODIC) {
+    pp.periodic = 1;
+    pp.twy = p->twy;
+    pp.lamy = p->lamy;
+    pp.beta_s = pp.beta_e = pp.j0 = 0;
+  }
   return pp;
 }
 
@@ -196,7 +214,7 @@ static StencilCoef stencil_coef(const ibm_plan_s *p, int kind, double c, int fie
   sc.cx = 1.0 / (p->h[0] * p->h[0]);
   sc.cy = 1.0 / (p->h[1] * p->h[1]);
   sc.cz = 1.0 / (p->h[2] * p->h[2]);
-  if (kind == 0) { sc.sigma = 0.0; sc.tau = 1.0; sc.bc = 0; }
+  if (kind == 0) { sc.sigma = 0.0; sc.tau = 1.0; sc.bc = p->bc == IBM_BC_TRIPLY_PERIODIC ? IBM_FIELD_PERIODIC : 0; }
   else { sc.sigma = 1.0; sc.tau = -c; sc.bc = field_bc; }
   return sc;
 }
@@ -334,7 +352,10 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
                     ibm_plan *out) {
   if (!out) return set_error(IBM_ERR_ARG, "ibm_plan_create: out is NULL");
   *out = nullptr;
-  if (bc != IBM_BC_PXZ_WALL_Y) return set_error(IBM_ERR_UNSUPPORTED, "ibm_plan_create: unsupported bc %d", bc);
+  if (bc != IBM_BC_PXZ_WALL_Y && bc != IBM_BC_TRIPLY_PERIODIC)
+    return set_error(IBM_ERR_UNSUPPORTED, "ibm_plan_create: unsupported bc %d", bc);
+  if (bc == IBM_BC_TRIPLY_PERIODIC && !transform_size_supported(ny))
+    return set_error(IBM_ERR_ARG, "ibm_plan_create: periodic ny=%d must be 2^a 3^b (b<=1) in [8,512]", ny);
   if (!transform_size_supported(nx) || !transform_size_supported(nz))
     return set_error(IBM_ERR_ARG, "ibm_plan_create: nx=%d nz=%d must be 2^a 3^b (b<=1) in [8,512]", nx, nz);
   if (ny < 8 || ny > 512) return set_error(IBM_ERR_ARG, "ibm_plan_create: ny=%d outside [8,512]", ny);
@@ -348,6 +369,7 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   ibm_plan_s *p = new (std::nothrow) ibm_plan_s();
   if (!p) return set_error(IBM_ERR_OOM, "ibm_plan_create: host allocation");
   p->nx = nx; p->ny = ny; p->nz = nz; p->P = nx / 2 + 1;
+  p->bc = bc;
   p->h[0] = h[0]; p->h[1] = h[1]; p->h[2] = h[2];
   p->precision = precision;
   p->refine = precision == IBM_FP64 ? 0 : refine_iters;
@@ -410,7 +432,9 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
       (rc = dalloc(p, &p->lamz, (size_t)nz * p->esz)) ||
       (rc = dalloc(p, (void **)&p->dsc, 16 * sizeof(double))) ||
       (rc = dalloc(p, (void **)&p->derr, 16)) ||
-      (rc = dalloc(p, (void **)&p->zbuf, 2 * (size_t)ny * sizeof(double)))) {
+      (rc = dalloc(p, (void **)&p->zbuf, 2 * (size_t)ny * sizeof(double))) ||
+      (bc == IBM_BC_TRIPLY_PERIODIC && ((rc = dalloc(p, &p->twy, (size_t)ny * 2 * p->esz)) ||
+                                        (rc = dalloc(p, &p->lamy, (size_t)ny * p->esz))))) {
     plan_free(p);
     return rc;
   }
@@ -495,8 +519,9 @@ int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs, 
                         ibm_info *info) {
   if (!plan || !rhs || !u) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: NULL argument");
   if (!(c > 0.0) || !std::isfinite(c)) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: c must be > 0");
-  if (field_bc < IBM_FIELD_CELL_NEUMANN || field_bc > IBM_FIELD_FACE_DIRICHLET)
-    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field_bc %d", field_bc);
+  if (plan->bc == IBM_BC_TRIPLY_PERIODIC ? field_bc != IBM_FIELD_PERIODIC
+                                          : (field_bc < IBM_FIELD_CELL_NEUMANN || field_bc > IBM_FIELD_FACE_DIRICHLET))
+    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field_bc %d for this plan's bc", field_bc);
   if (!aligned_to(rhs, 16) || !aligned_to(u, 16))
     return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field pointers must be 16-byte aligned");
   return plan_solve(plan, 1, c, field_bc, rhs, u, nullptr, (cudaStream_t)stream, info);

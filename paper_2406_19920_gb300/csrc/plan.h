@@ -27,6 +27,7 @@ int cuda_error(cudaError_t e, const char *what);
 
 struct ibm_plan_s {
   int nx, ny, nz, P;
+  int bc;            // IBM_BC_PXZ_WALL_Y or IBM_BC_TRIPLY_PERIODIC
   double h[3];
   int precision;     // IBM_FP64 / IBM_FP32_REFINED
   int refine;        // refinement steps (FP32 path)
@@ -45,6 +46,7 @@ struct ibm_plan_s {
   void *mkbuf;       // marker force scratch [n][3] when the caller passes none
   size_t mkcap;      // bytes of mkbuf
   void *twx, *twz;   // twiddles W_N^m (plan precision)
+  void *twy, *lamy;  // triply periodic branch: W_ny^m and lambda_y (plan precision)
   void *lamx, *lamz; // modified wavenumbers kx'^2 (P), kz'^2 (nz) (plan precision)
   double *dsc;       // device scalars: [0] removed mean, [1] it as a float pair, [4..7] residual
                      // sums, [8..9] divergence maxima

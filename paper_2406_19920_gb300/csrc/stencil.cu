@@ -2,7 +2,8 @@
 //
 // r = b - (sigma x + tau L_h x), L_h the second-order central Laplacian of
 // Sec. 2.1 with periodic x, z and the ghost rule of the field's wall kind
-// along y (Appendix B).  Poisson: sigma = 0, tau = 1; Helmholtz (I - c L):
+// along y (Appendix B; periodic for the triply periodic branch).  Poisson:
+// sigma = 0, tau = 1; Helmholtz (I - c L):
 // sigma = 1, tau = -c.  In FP32 the stencil is evaluated in float-float
 // arithmetic (exact second differences of the stored FP32 values, 1/h^2 and
 // tau carried as hi + lo pairs) and rounded once to FP32; a plain FP32
@@ -15,7 +16,7 @@
 
 namespace ibm {
 
-enum { BC_NEUMANN = 0, BC_CELL_DIRICHLET = 1, BC_FACE_DIRICHLET = 2 };
+enum { BC_NEUMANN = 0, BC_CELL_DIRICHLET = 1, BC_FACE_DIRICHLET = 2, BC_PERIODIC = 3 };
 
 struct ffc { float hi, lo; };
 static inline ffc split_ff(double v) {
@@ -108,6 +109,9 @@ k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restr
       if (face) {
         xd = j - 1 >= 1 ? x[base - pl + c] : 0.0f;
         xu = j + 1 <= A.ny - 1 ? x[base + pl + c] : 0.0f;
+      } else if (A.bc == BC_PERIODIC) {
+        xd = x[(j > 0 ? base - pl : base + (size_t)(A.ny - 1) * pl) + c];
+        xu = x[(j + 1 < A.ny ? base + pl : base - (size_t)(A.ny - 1) * pl) + c];
       } else {
         const float gsign = (A.bc == BC_NEUMANN) ? 1.0f : -1.0f;
         xd = j > 0 ? x[base - pl + c] : gsign * x0;
@@ -170,6 +174,9 @@ k_residual_f64(ResidualArgs A, const double *__restrict__ b, const double *__res
       if (A.bc == BC_FACE_DIRICHLET) {
         xd = (j - 1 >= 1) ? x[idx - pl] : 0.0;
         xu = (j + 1 <= A.ny - 1) ? x[idx + pl] : 0.0;
+      } else if (A.bc == BC_PERIODIC) {
+        xd = j > 0 ? x[idx - pl] : x[idx + (size_t)(A.ny - 1) * pl];
+        xu = j + 1 < A.ny ? x[idx + pl] : x[idx - (size_t)(A.ny - 1) * pl];
       } else {
         const double gsign = (A.bc == BC_NEUMANN) ? 1.0 : -1.0;
         xd = (j > 0) ? x[idx - pl] : gsign * x0;

@@ -413,6 +413,8 @@ using namespace ibm;
 extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
                            void *stream, ibm_info *info) {
   if (!plan || !st) return set_error(IBM_ERR_ARG, "ibm_substep: NULL plan or state");
+  if (plan->bc != IBM_BC_PXZ_WALL_Y)
+    return set_error(IBM_ERR_UNSUPPORTED, "ibm_substep: the RK stage is built for the wall-bounded branch only");
   if (rk_stage < 1 || rk_stage > 3) return set_error(IBM_ERR_ARG, "ibm_substep: rk_stage %d", rk_stage);
   if (!(dt > 0) || !std::isfinite(dt) || !(nu > 0) || !std::isfinite(nu))
     return set_error(IBM_ERR_ARG, "ibm_substep: dt and nu must be finite and > 0");
