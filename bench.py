@@ -390,6 +390,10 @@ def run_gpu(args):
         solves_256 = poisson_compare(ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0),
                                                        ("fp32_refined", ibm.IBM_FP32_REFINED, 1),
                                                        ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20)
+        # triply periodic branch (y-FFT pencil step instead of the Thomas sweep)
+        solves_256["triply_periodic"] = poisson_compare(
+            ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0), ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
+            bc=ibm.IBM_BC_TRIPLY_PERIODIC)
 
     # ---- batched (64 instances, one graph launch) and served workloads ----
     batched = batched_compare(ibm, torch) if not args.no_extras else None
@@ -468,7 +472,7 @@ def method_bytes(n, precision_bytes, refine):
     return solve + refine * (3 * pts * s + solve + pts * s)
 
 
-def poisson_compare(ibm, torch, n, variants, nb=16, K=40):
+def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None):
     """Standalone Poisson solves on an n^3 grid ([0,2pi)x[0,2]x[0,2pi],
     low-passed noise right-hand side): solves/s, p50/p99 latency, and the
     achieved fraction of the measured HBM bandwidth for the solve's method
@@ -480,7 +484,7 @@ def poisson_compare(ibm, torch, n, variants, nb=16, K=40):
     outs = {}
     for name, prec, ref in variants:
         dt = torch.float32 if prec == ibm.IBM_FP32_REFINED else torch.float64
-        plan = ibm.ibm_plan_create(n, n, n, g[3:], prec, ref)
+        plan = ibm.ibm_plan_create(n, n, n, g[3:], prec, ref, bc=bc if bc is not None else ibm.IBM_BC_PXZ_WALL_Y)
         rhs = [torch.from_numpy(b).to("cuda", dt) for _ in range(nb)]  # nb rhs + nb solutions > L2
         phi = [torch.empty_like(r) for r in rhs]
         for i in range(3):
