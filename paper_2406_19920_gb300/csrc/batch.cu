@@ -69,6 +69,10 @@ static bool substructured_available(const ibm_plan_s *p) {
   return p->precision == IBM_FP32_REFINED ? n <= 256 : n <= 128;
 }
 
+static bool segmented_available(const ibm_plan_s *p) {
+  return p->precision == IBM_FP32_REFINED ? p->ny <= 512 : p->ny <= 256;
+}
+
 static int plane_candidates(const ibm_plan_s *p, int *modes) {
   return p->precision == IBM_FP64 ? plane_modes<double>(p->nx, p->nz, modes) : plane_modes<float>(p->nx, p->nz, modes);
 }
@@ -111,8 +115,12 @@ int tune_plan(ibm_plan_s *p, TuneChoice *out) {
   int modes[8];
   const int nmodes = plane_candidates(p, modes);
   int rc = IBM_OK;
-  const int pms[3] = {2, 3, 1};
-  for (int ip = 0; ip < (substructured_available(p) ? 3 : 2) && rc == IBM_OK; ++ip) {
+  int pms[4], npm = 0;
+  if (segmented_available(p)) pms[npm++] = 4;
+  pms[npm++] = 2;
+  pms[npm++] = 3;
+  if (substructured_available(p)) pms[npm++] = 1;
+  for (int ip = 0; ip < npm && rc == IBM_OK; ++ip) {
     const int pm = pms[ip];
     for (int m = 0; m < nmodes && rc == IBM_OK; ++m) {
       const int up = modes[m];

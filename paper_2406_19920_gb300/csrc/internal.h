@@ -160,8 +160,10 @@ struct PencilParams {
   double hy2;              // hy^2 for the FP64 zero-mode path
   double inv_nxnz;         // 1/(nx nz) for the removed-mean report
   int *err;                // device error word for bounded waits
-  int mode;                // pencil kernel: 0 auto (tile or streaming by size), 1 warp-parallel block
-                           // solve (n <= 256 FP32 / 128 FP64, else auto), 2 tile, 3 streaming
+  int mode;                // pencil kernel: 0 auto (FP32: segmented where ny allows; else tile or
+                           // streaming by size), 1 warp-parallel block solve (n <= 256 FP32 / 128
+                           // FP64, else auto), 2 tile, 3 streaming, 4 segmented (ny <= 512 FP32 / 256
+                           // FP64)
   const double *zrhs;      // zero_mode: right-hand side of the (0,0) pencil, [ny] (from the forward pass)
   double *zsol;            // zero_mode: its FP64 solution, [ny] (read by the inverse pass)
   double inv_ny;           // 1/ny

@@ -355,6 +355,348 @@ k_pencil(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ l
 }
 
 // ---------------------------------------------------------------------------
+// Segmented two-ended sweep: one CTA takes 32 consecutive pencils (lane =
+// pencil, so every row access is a run of 32 complex values) and L = 2 Lh
+// warps.  The elimination order is the two-ended one of k_pencil (rows
+// 0 .. m-1 top-down, rows n-1 .. m+1 bottom-up, meeting at m = n/2); warps
+// 0 .. Lh-1 share the top half and Lh .. L-1 the bottom half, S rows each,
+// held in registers.  Along each half, with k the distance from the wall:
+//   * pivots: e_k depends on the pencil's (a, g) only.  The map
+//     e -> g + a e / (a + e) is a Moebius map with fixed points e+ > 0 and
+//     e- = -a g / e+, and z_k = (e_k - e+) / (e_k - e-) shrinks
+//     geometrically, z_k = z_0 lambda^k with lambda = (a + e-) / (a + e+) =
+//     a^2 g / (e+^2 (a + e+)), so every row's pivot follows in closed form,
+//     e_k = e+ + (e+ - e-) z_k / (1 - z_k), with no serial dependence on the
+//     rows before it (all terms are sums and products of positive numbers
+//     but z, whose absolute error only moves e_k by a few ulps of e+, far
+//     below the pivot a + e_k).  A warp whose lanes all have |z| below a
+//     sixteenth of the unit roundoff at its first row takes the converged
+//     pivot e+ for every row (constant r and w);
+//   * forward elimination y_k = r_k f_k + w_k y_{k-1} (w = a r) is a
+//     first-order linear recurrence: each warp sweeps its rows from a zero
+//     carry, keeping yhat and the product of its w, and the true values
+//     follow from the warps' (yhat_end, prod w) pairs in shared memory,
+//     y_k = yhat_k + (w_s ... w_k) y_{s-1};
+//   * every thread then forms x_m from both halves' last y and q, and back
+//     substitution x_k = y_k + w_k x_{k+1} runs the same way towards the wall.
+// One global read and one write of the spectrum; the serial depth per warp
+// is S rows of the y and x recurrences.
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(cplx<T> *dst, const cplx<T> *src) {
+  if constexpr (sizeof(T) == 4) cp_async8(dst, src);
+  else cp_async16(dst, src);
+}
+
+// Per-warp sweep variants: FULL (all S rows of the segment are unknowns, no
+// row guards) and CW (converged pivots: constant r and w).  Rows u >= len of a
+// partial segment are pass-through (r = 0, w = 1) and read as zero.
+template <typename T, int S, bool FULL, bool CW>
+__device__ __forceinline__ void seg_forward(cplx<T> (&v)[S], int len, T a, T sgn, T ep, T D, T lam, T z, T *wc,
+                                            cplx<T> &y, T &prod, T &qlast) {
+  y = mk<T>(0, 0);
+  prod = (T)1;
+  qlast = (T)0;
+  if (CW) {
+    const T r = rcp<T>(a + ep), w = a * r, rs = sgn * r;
+#pragma unroll
+    for (int u = 0; u < S; ++u) {
+      y.x = fma(w, y.x, rs * v[u].x);
+      y.y = fma(w, y.y, rs * v[u].y);
+      v[u] = y;
+      prod *= w;
+    }
+    qlast = ep * r;
+    return;
+  }
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    // e_k = e+ + (e+ - e-) z_k / (1 - z_k): no dependence on the previous
+    // row.  FP32: z_k = z_k0 exp(u log lambda) (lam holds log lambda), each
+    // to a few ulps; FP64: running product by lambda.
+    T zu;
+    if constexpr (sizeof(T) == 4) zu = z * expf((T)u * lam);
+    else { zu = z; z *= lam; }
+    const T e = fma(D * zu, rcp<T>((T)1 - zu), ep);
+    const T r = rcp<T>(a + e);
+    const bool in = FULL || u < len;
+    const T ru = in ? sgn * r : (T)0;
+    const T wu = in ? a * r : (T)1;
+    wc[32 * u] = wu;
+    y.x = fma(wu, y.x, ru * v[u].x);
+    y.y = fma(wu, y.y, ru * v[u].y);
+    v[u] = y;
+    prod *= wu;
+    if (FULL ? u == S - 1 : u == len - 1) qlast = e * r;
+  }
+}
+
+// Carry c (y before the segment) folded in, then the local back substitution
+// from a zero carry; returns xhat at the segment's first row.
+template <typename T, int S, bool FULL, bool CW>
+__device__ __forceinline__ cplx<T> seg_middle(cplx<T> (&v)[S], int len, T wconst, const T *wc, cplx<T> c) {
+  T pw = (T)1;
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    pw *= CW ? wconst : wc[32 * u];
+    const bool in = FULL || u < len;
+    v[u].x = in ? fma(pw, c.x, v[u].x) : (T)0;
+    v[u].y = in ? fma(pw, c.y, v[u].y) : (T)0;
+  }
+  cplx<T> x = mk<T>(0, 0);
+#pragma unroll
+  for (int u = S - 1; u >= 0; --u) {
+    const T wu = CW ? wconst : wc[32 * u];
+    x.x = fma(wu, x.x, v[u].x);
+    x.y = fma(wu, x.y, v[u].y);
+    v[u] = x;
+  }
+  return x;
+}
+
+// Carry c (x after the segment) folded in and the rows stored.
+template <typename T, int S, bool FULL, bool CW>
+__device__ __forceinline__ void seg_store(cplx<T> (&v)[S], int len, T wconst, const T *wc, cplx<T> c, bool live,
+                                          cplx<T> *col, long step) {
+  T pw = (T)1;
+#pragma unroll
+  for (int u = S - 1; u >= 0; --u) {
+    pw *= CW ? wconst : wc[32 * u];
+    cplx<T> o;
+    o.x = fma(pw, c.x, v[u].x);
+    o.y = fma(pw, c.y, v[u].y);
+    if (live && (FULL || u < len)) col[(long)u * step] = o;
+  }
+}
+
+template <typename T, int S, int MAXT> struct SegOcc {
+  // resident CTAs per SM the register budget is sized for (shared memory
+  // allows about as many)
+  static constexpr int value = MAXT > 256 ? 1 : (S >= 32 || sizeof(T) == 8 ? 2 : (S >= 16 ? 3 : 4));
+};
+
+// Per-lane constants of one tile (32 pencils of one field).
+template <typename T> struct SegTile {
+  cplx<T> *Sb, *c0, *col;
+  long step;
+  T g, e0;
+  int n, m, k0, len, beta_s, beta_e, j0, p;
+  bool live;
+};
+
+template <typename T, int S>
+__device__ __forceinline__ SegTile<T> seg_tile(const PencilParams &pp, Ptr3<cplx<T> *> S_, const T *lamx,
+                                               const T *lamz, int t, int nblk, int seg, int lane, int Lh) {
+  SegTile<T> ti;
+  const int field = t / nblk, blk = t - field * nblk;
+  pencil_field(pp, field, ti.beta_s, ti.beta_e, ti.j0);
+  ti.n = pp.ny - ti.j0;
+  ti.m = ti.n / 2;
+  const long plane = (long)pp.nz * pp.P;
+  const int npen = pp.nz * pp.P;
+  ti.p = blk * 32 + lane;
+  ti.live = ti.p < npen && !(pp.zero_mode && ti.p == 0);
+  const int pc = ti.p < npen ? ti.p : npen - 1;  // dead lanes compute on a valid pencil, store nothing
+  const int kz = pc / pp.P, kx = pc - kz * pp.P;
+  ti.g = (T)pp.g_add + (T)pp.g_mul * (lamx[kx] + lamz[kz]);
+  const bool top = seg < Lh;
+  ti.e0 = ti.g + (T)pp.a * (T)(top ? ti.beta_s : ti.beta_e);
+  ti.k0 = (top ? seg : seg - Lh) * S;  // distance of my first row from the wall
+  const int hl = top ? ti.m : ti.n - 1 - ti.m;
+  ti.len = max(0, min(S, hl - ti.k0));  // my rows (the same for every lane)
+  ti.step = top ? plane : -plane;
+  ti.Sb = S_[field];
+  ti.c0 = ti.Sb + (long)ti.j0 * plane + pc;  // row 0 of the unknowns
+  ti.col = ti.c0 + (long)(top ? ti.k0 : ti.n - 1 - ti.k0) * plane;
+  return ti;
+}
+
+// The tile's rows (and, for warp 0, row m) by per-thread asynchronous copies.
+template <typename T, int S>
+__device__ __forceinline__ void seg_issue(const SegTile<T> &ti, cplx<T> *tl, cplx<T> *tm, int seg, long plane) {
+#pragma unroll
+  for (int u = 0; u < S; ++u)
+    if (u < ti.len) cp_async_elem<T>(tl + 32 * u, ti.col + (long)u * ti.step);
+  if (seg == 0) cp_async_elem<T>(tm, ti.c0 + (long)ti.m * plane);
+}
+
+// Persistent: CTA b takes tiles b, b + G, ... of the (field, 32-pencil block)
+// list (G = the sweep CTAs); the copies of its next tile stream into the one
+// staging buffer while the current tile, already in registers, is solved.
+template <typename T, int S, int MAXT>
+__global__ void __launch_bounds__(MAXT, (SegOcc<T, S, MAXT>::value))
+k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ lamz, PencilParams pp,
+             double *mean_out) {
+  const int lane = threadIdx.x & 31, seg = threadIdx.x >> 5, L = blockDim.x >> 5, Lh = L >> 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  cplx<T> *tile = reinterpret_cast<cplx<T> *>(smem_raw);  // [L S + 1][32] rows by sweep slot, then row m
+  T *ws = reinterpret_cast<T *>(tile + (size_t)(L * S + 1) * 32);  // [L S][32] w of every row
+  T *cf = ws + (size_t)L * S * 32;  // [4][L][32] (yhat_end.x, .y, prod w, q of the last row)
+  T *cb = cf + 4 * L * 32;          // [2][L][32] (xhat_first.x, .y)
+  const int G = gridDim.x - (pp.zero_mode ? 1 : 0);
+  if (pp.zero_mode && blockIdx.x == G) {
+    pdl_wait();
+    zero_mode_cta(pp, reinterpret_cast<double *>(cb + 2 * L * 32), mean_out);
+    return;
+  }
+  const long plane = (long)pp.nz * pp.P;
+  const int nblk = ceil_div(pp.nz * pp.P, 32);
+  const int tiles = nblk * pp.nb;
+  const T a = (T)pp.a;
+  const T sgn = pp.neg_rhs ? (T)-1 : (T)1;
+  const bool top = seg < Lh;
+  cplx<T> *tl = tile + (size_t)seg * S * 32 + lane;
+  cplx<T> *tm = tile + (size_t)L * S * 32 + lane;
+  T *wc = ws + (size_t)seg * S * 32 + lane;  // w of my row u at wc[32 u]
+  pdl_wait();
+  int t = blockIdx.x;
+  if (t < tiles) seg_issue<T, S>(seg_tile<T, S>(pp, S_, lamx, lamz, t, nblk, seg, lane, Lh), tl, tm, seg, plane);
+  for (; t < tiles; t += G) {
+    const SegTile<T> cur = seg_tile<T, S>(pp, S_, lamx, lamz, t, nblk, seg, lane, Lh);
+    const SegTile<T> &ti = cur;
+    const T g = ti.g;
+    const int k0 = ti.k0, len = ti.len, n = ti.n, m = ti.m;
+    // pivots in closed form (fixed points e+ > 0 > e- = -a g / e+ of the
+    // Moebius map, z_k = z_0 lambda^k); the singular zero pencil (g = 0)
+    // keeps e = e0 = 0
+    T ep, D, lam, z;
+    bool cw;
+    {
+      const bool zero = g == (T)0;
+      const T gg = zero ? (T)1 : g;
+      ep = (T)0.5 * (gg + sqrt(fma(gg, gg, (T)4 * a * gg)));
+      const T emn = a * gg / ep;  // -e-
+      D = ep + emn;
+      // 1 - lambda = (a g + e+^2) / (e+ (a + e+)), free of cancellation
+      const T mu = fma(ep, ep, a * gg) / (ep * (a + ep));
+      z = (ti.e0 - ep) / (ti.e0 + emn);
+      if constexpr (sizeof(T) == 4) {
+        lam = fmaxf(log1pf(-mu), -80.0f);  // log lambda
+        z *= expf((T)k0 * lam);
+      } else {
+        lam = (T)1 - mu;
+        T lp = (T)1, base = lam;
+        for (int kk = k0; kk; kk >>= 1) {
+          if (kk & 1) lp *= base;
+          base *= base;
+        }
+        z *= lp;
+      }
+      if (zero) { ep = (T)0; D = (T)0; lam = (T)0; z = (T)0; }
+      const bool ok = fabs(z) < (sizeof(T) == 4 ? (T)0x1p-28 : (T)0x1p-56);
+      cw = __all_sync(0xffffffffu, ok) && len == S;
+    }
+    cp_async_wait_all();
+    __syncthreads();  // every copy of the tile has landed
+    cplx<T> v[S];
+#pragma unroll
+    for (int u = 0; u < S; ++u) v[u] = u < len ? tl[32 * u] : mk<T>(0, 0);
+    const cplx<T> fm = *tm;
+    __syncthreads();  // the staging buffer is free: start the next tile's copies
+    if (t + G < tiles)
+      seg_issue<T, S>(seg_tile<T, S>(pp, S_, lamx, lamz, t + G, nblk, seg, lane, Lh), tl, tm, seg, plane);
+    const bool full = len == S;
+    const T wconst = a * rcp<T>(a + ep);
+    cplx<T> y;
+    T prod, qlast;
+    if (cw) seg_forward<T, S, true, true>(v, len, a, sgn, ep, D, lam, z, wc, y, prod, qlast);
+    else if (full) seg_forward<T, S, true, false>(v, len, a, sgn, ep, D, lam, z, wc, y, prod, qlast);
+    else seg_forward<T, S, false, false>(v, len, a, sgn, ep, D, lam, z, wc, y, prod, qlast);
+    cf[(0 * L + seg) * 32 + lane] = y.x;
+    cf[(1 * L + seg) * 32 + lane] = y.y;
+    cf[(2 * L + seg) * 32 + lane] = prod;
+    cf[(3 * L + seg) * 32 + lane] = qlast;
+    __syncthreads();
+    // y at the row before mine, and the last y of both halves
+    cplx<T> c = mk<T>(0, 0);
+    cplx<T> yT = mk<T>(0, 0), yB = mk<T>(0, 0);
+    for (int s2 = 0; s2 < L; ++s2) {
+      if (s2 == seg) c = s2 < Lh ? yT : yB;
+      const T pw = cf[(2 * L + s2) * 32 + lane];
+      const T ax = cf[(0 * L + s2) * 32 + lane], ay = cf[(1 * L + s2) * 32 + lane];
+      if (s2 < Lh) {
+        yT.x = fma(pw, yT.x, ax);
+        yT.y = fma(pw, yT.y, ay);
+      } else {
+        yB.x = fma(pw, yB.x, ax);
+        yB.y = fma(pw, yB.y, ay);
+      }
+    }
+    // meeting row: (g + a q^T + a q^B) x_m = f_m + a (y^T_{m-1} + y^B_{m+1});
+    // an empty half contributes its wall term beta
+    const T qT = m > 0 ? cf[(3 * L + (m - 1) / S) * 32 + lane] : (T)cur.beta_s;
+    const T qB = n - 1 - m > 0 ? cf[(3 * L + Lh + (n - 2 - m) / S) * 32 + lane] : (T)cur.beta_e;
+    cplx<T> xm;
+    {
+      const T rm = rcp<T>(g + a * qT + a * qB);
+      xm.x = (sgn * fm.x + a * (yT.x + yB.x)) * rm;
+      xm.y = (sgn * fm.y + a * (yT.y + yB.y)) * rm;
+    }
+    cplx<T> x;
+    if (cw) x = seg_middle<T, S, true, true>(v, len, wconst, wc, c);
+    else if (full) x = seg_middle<T, S, true, false>(v, len, wconst, wc, c);
+    else x = seg_middle<T, S, false, false>(v, len, wconst, wc, c);
+    cb[(0 * L + seg) * 32 + lane] = x.x;
+    cb[(1 * L + seg) * 32 + lane] = x.y;
+    __syncthreads();
+    c = xm;  // x at the row after my last one (towards the meeting row)
+    for (int s2 = (top ? Lh : L) - 1; s2 > seg; --s2) {
+      const T pw = cf[(2 * L + s2) * 32 + lane];
+      c.x = fma(pw, c.x, cb[(0 * L + s2) * 32 + lane]);
+      c.y = fma(pw, c.y, cb[(1 * L + s2) * 32 + lane]);
+    }
+    if (cw) seg_store<T, S, true, true>(v, len, wconst, wc, c, cur.live, cur.col, cur.step);
+    else if (full) seg_store<T, S, true, false>(v, len, wconst, wc, c, cur.live, cur.col, cur.step);
+    else seg_store<T, S, false, false>(v, len, wconst, wc, c, cur.live, cur.col, cur.step);
+    if (seg == 0 && cur.live) {
+      cur.c0[(long)m * plane] = xm;
+      if (cur.j0 == 1) cur.Sb[cur.p] = mk<T>(0, 0);
+    }
+  }
+}
+
+template <typename T, int S> size_t pencil_seg_smem_bytes(int L, int ny) {
+  const size_t body = sizeof(cplx<T>) * (size_t)(L * S + 1) * 32 + sizeof(T) * ((size_t)L * S + 6 * L) * 32;
+  return ((body + 15) & ~(size_t)15) + (size_t)ny * sizeof(double);
+}
+
+template <typename T, int S, int MAXT>
+static cudaError_t launch_seg(const PencilParams &pp, Ptr3<cplx<T> *> S3, const T *lamx, const T *lamz,
+                              double *mean_out, cudaStream_t st) {
+  const int L = 2 * ceil_div(pp.ny / 2, S);  // both halves of every field (n = ny or ny - 1 rows)
+  if (32 * L > MAXT) return cudaErrorInvalidConfiguration;
+  {
+    cudaError_t e = ensure_max_smem<k_pencil_seg<T, S, MAXT>>();
+    if (e != cudaSuccess) return e;
+  }
+  const size_t bytes = pencil_seg_smem_bytes<T, S>(L, pp.ny);
+  static std::once_flag once;
+  static int sms = 0;
+  std::call_once(once, [] {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  int per_sm = 0;
+  IBM_KTRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pencil_seg<T, S, MAXT>, 32 * L, bytes));
+  const int tiles = ceil_div(pp.nz * pp.P, 32) * pp.nb;
+  const int G = std::max(1, std::min(tiles, sms * std::max(per_sm, 1)));
+  IBM_KTRY(launch_pdl(k_pencil_seg<T, S, MAXT>, G + (pp.zero_mode ? 1 : 0), 32 * L, bytes, st, S3, lamx, lamz, pp,
+                      mean_out));
+  return cudaGetLastError();
+}
+
+// Rows per warp of the segmented sweep for ny rows (0: not available; the
+// CTA has 2 ceil((ny / 2) / S) warps).
+template <typename T> static int seg_rows(int ny) {
+  if (ny < 4) return 0;
+  if (ny <= 64) return 8;
+  if (ny <= 128) return 16;
+  if (ny <= 256) return sizeof(T) == 4 ? 32 : 16;
+  return (sizeof(T) == 4 && ny <= 512) ? 32 : 0;
+}
+
+// ---------------------------------------------------------------------------
 // Substructured pencil solve: one CTA of 32 warps takes TP pencils; warp s
 // owns the block of rows [s M, (s+1) M) of every pencil, lane = pencil (or,
 // with SPLIT, lane = (pencil, real component) for 16 pencils).  Per block:
@@ -734,6 +1076,21 @@ cudaError_t launch_pencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const T *l
       if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
+  }
+  // default: the segmented sweep for FP32 (measured faster at 128^3 and
+  // 256^3); FP64 is bound by its divisions and stays on the two-ended sweep
+  if (pp.mode == 4 || (pp.mode == 0 && sizeof(T) == 4 && seg_rows<T>(pp.ny) > 0)) {
+    switch (seg_rows<T>(pp.ny)) {
+      case 8: return launch_seg<T, 8, 256>(pp, S3, lamx, lamz, mean_out, st);
+      case 16: return launch_seg<T, 16, sizeof(T) == 4 ? 256 : 512>(pp, S3, lamx, lamz, mean_out, st);
+      case 32:
+        if constexpr (sizeof(T) == 4) {
+          if (pp.ny <= 256) return launch_seg<T, 32, 256>(pp, S3, lamx, lamz, mean_out, st);
+          return launch_seg<T, 32, 512>(pp, S3, lamx, lamz, mean_out, st);
+        }
+        break;
+      default: break;
+    }
   }
   cplx<T> *S = S3[0];
   const int n = pp.ny - pp.j0;

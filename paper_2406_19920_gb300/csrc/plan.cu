@@ -374,15 +374,16 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   p->precision = precision;
   p->refine = precision == IBM_FP64 ? 0 : refine_iters;
   p->delta = IBM_DELTA_ROMA3;
-  // pencil solver: the two-ended sweep, tile or streaming kernel by size;
-  // IBM_PENCIL_MODE=m forces 1 (warp-parallel block solve), 2 (tile) or 3
-  // (streaming) for A/B timing and tests; the tuner may pick any of them
+  // pencil solver: FP32 the segmented sweep where ny allows, else the
+  // two-ended sweep (tile or streaming kernel by size); IBM_PENCIL_MODE=m forces 1
+  // (warp-parallel block solve), 2 (tile), 3 (streaming) or 4 (segmented)
+  // for A/B timing and tests; the tuner may pick any of them
   p->pencil_mode = 0;
   if (const char *pm = getenv("IBM_PENCIL_MODE")) {
     const int m = atoi(pm);
-    if (m < 0 || m > 3) {
+    if (m < 0 || m > 4) {
       delete p;
-      return set_error(IBM_ERR_ARG, "ibm_plan_create: IBM_PENCIL_MODE=%d outside [0,3]", m);
+      return set_error(IBM_ERR_ARG, "ibm_plan_create: IBM_PENCIL_MODE=%d outside [0,4]", m);
     }
     p->pencil_mode = m;
   }

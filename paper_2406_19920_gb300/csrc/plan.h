@@ -32,7 +32,7 @@ struct ibm_plan_s {
   int precision;     // IBM_FP64 / IBM_FP32_REFINED
   int refine;        // refinement steps (FP32 path)
   int delta;         // IBM_DELTA_*
-  int pencil_mode;   // 0 auto, 1 warp-parallel block solve, 2 tile sweep, 3 streaming sweep
+  int pencil_mode;   // 0 auto, 1 warp-parallel block solve, 2 tile sweep, 3 streaming sweep, 4 segmented sweep
   int use_plane = 1; // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane
   int use_plane_fields = 0; // plane mode of three-field solves
   size_t esz;        // element size: 4 or 8

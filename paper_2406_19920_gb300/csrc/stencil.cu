@@ -73,79 +73,102 @@ __device__ __forceinline__ void block_accumulate(double r2, double b2, double r1
 //   * all high parts summed by a chain of error-free sums, all low parts and
 //     sum errors added in FP32 (cascaded summation, Ogita, Rump & Oishi
 //     2005), the two totals added last.
-// One thread per point (stencil_launch shape); periodic neighbours by
-// compare-and-select, no divisions.
 __device__ __forceinline__ void sum_into(float &S, float &E, float h) {
   const ff t = two_sum(S, h);
   S = t.hi;
   E += t.lo;
 }
 
+// One point: returns r and sets bt to the compatible right-hand side b - m
+// (for the norms).  SIGMA: the Helmholtz sigma x0 term.
+template <bool SIGMA>
+__device__ __forceinline__ float residual_point(const ResidualArgs &A, float bv, float2 m, float x0, float xe, float xw,
+                                                float xn, float xs, float xu, float xd, float &bt) {
+  const float x2 = -2.0f * x0;
+  // exact second differences D = hi + lo
+  ff s = two_sum(xe, xw), t = two_sum(s.hi, x2);
+  const float Dxh = t.hi, Dxl = t.lo + s.lo;
+  s = two_sum(xn, xs); t = two_sum(s.hi, x2);
+  const float Dzh = t.hi, Dzl = t.lo + s.lo;
+  s = two_sum(xu, xd); t = two_sum(s.hi, x2);
+  const float Dyh = t.hi, Dyl = t.lo + s.lo;
+  // (b - m) - sigma x0 + sum_a K_a D_a, cascaded
+  const ff bm = two_sum(bv, -m.x);
+  float S = bm.hi, E = bm.lo - m.y;
+  bt = bm.hi + E;
+  if (SIGMA) sum_into(S, E, -A.sigma * x0);
+  ff p = two_prod(A.kx.hi, Dxh);
+  sum_into(S, E, p.hi);
+  E += fmaf(A.kx.hi, Dxl, fmaf(A.kx.lo, Dxh, p.lo));
+  p = two_prod(A.kz.hi, Dzh);
+  sum_into(S, E, p.hi);
+  E += fmaf(A.kz.hi, Dzl, fmaf(A.kz.lo, Dzh, p.lo));
+  p = two_prod(A.ky.hi, Dyh);
+  sum_into(S, E, p.hi);
+  E += fmaf(A.ky.hi, Dyl, fmaf(A.ky.lo, Dyh, p.lo));
+  return S + E;
+}
+
+// Four consecutive x points per thread (every supported nx is a multiple of
+// 4 and the ABI takes 16-byte aligned fields): every row access is a float4,
+// the x neighbours of the four come from the same float4 plus two scalars,
+// and the index arithmetic is shared.  Grid (ceil(nz nx / 4 / 128), ny), 128
+// threads.
+template <int BC, bool SIGMA>
 __global__ void __launch_bounds__(128)
-k_residual_f32(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float *__restrict__ r,
-               double *norms) {
+k_residual_f32v(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float *__restrict__ r,
+                double *norms) {
   pdl_wait();
-  int i, k, j;
-  const bool inside = stencil_index(A.nx, A.nz, i, k, j);
-  double rr = 0.0, bb = 0.0;
-  if (inside) {
+  const int q = A.nx >> 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  double r2 = 0.0, b2 = 0.0, r1 = 0.0, b1 = 0.0;
+  if (t < q * A.nz) {
+    const int k = t / q, i0 = 4 * (t - k * q);
     const size_t pl = (size_t)A.nx * A.nz;
-    const size_t base = (size_t)j * pl;
-    const int c = k * A.nx + i;
-    const int oe = c - i + (i + 1 == A.nx ? 0 : i + 1), ow = c - i + (i == 0 ? A.nx - 1 : i - 1);
-    const int on = (k + 1 == A.nz ? 0 : k + 1) * A.nx + i, os = (k == 0 ? A.nz - 1 : k - 1) * A.nx + i;
-    const bool face = A.bc == BC_FACE_DIRICHLET;
-    float res, bt;
-    const float bv = b[base + c];
-    float2 m = make_float2(0.f, 0.f);
-    if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
-    if (face && j == 0) {
-      res = 0.0f;
-      bt = 0.0f;
-    } else {
-      const float x0 = x[base + c];
-      const float xe = x[base + oe], xw = x[base + ow], xn = x[base + on], xs = x[base + os];
-      float xu, xd;
-      if (face) {
-        xd = j - 1 >= 1 ? x[base - pl + c] : 0.0f;
-        xu = j + 1 <= A.ny - 1 ? x[base + pl + c] : 0.0f;
-      } else if (A.bc == BC_PERIODIC) {
-        xd = x[(j > 0 ? base - pl : base + (size_t)(A.ny - 1) * pl) + c];
-        xu = x[(j + 1 < A.ny ? base + pl : base - (size_t)(A.ny - 1) * pl) + c];
+    const size_t at = (size_t)j * pl + (size_t)k * A.nx + i0;
+    float4 res = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (!(BC == BC_FACE_DIRICHLET && j == 0)) {
+      const size_t row = at - i0;
+      const float4 x0 = *reinterpret_cast<const float4 *>(x + at);
+      const float xW = x[row + (i0 == 0 ? A.nx - 1 : i0 - 1)];
+      const float xE = x[row + (i0 + 4 == A.nx ? 0 : i0 + 4)];
+      const long dn = (long)(k + 1 == A.nz ? -(long)(A.nz - 1) * A.nx : (long)A.nx);
+      const long ds = (long)(k == 0 ? (long)(A.nz - 1) * A.nx : -(long)A.nx);
+      const float4 xn = *reinterpret_cast<const float4 *>(x + at + dn);
+      const float4 xs = *reinterpret_cast<const float4 *>(x + at + ds);
+      float4 xd, xu;
+      if (BC == BC_FACE_DIRICHLET) {
+        xd = j - 1 >= 1 ? *reinterpret_cast<const float4 *>(x + at - pl) : make_float4(0.f, 0.f, 0.f, 0.f);
+        xu = j + 1 <= A.ny - 1 ? *reinterpret_cast<const float4 *>(x + at + pl) : make_float4(0.f, 0.f, 0.f, 0.f);
+      } else if (BC == BC_PERIODIC) {
+        xd = *reinterpret_cast<const float4 *>(x + (j > 0 ? at - pl : at + (size_t)(A.ny - 1) * pl));
+        xu = *reinterpret_cast<const float4 *>(x + (j + 1 < A.ny ? at + pl : at - (size_t)(A.ny - 1) * pl));
       } else {
-        const float gsign = (A.bc == BC_NEUMANN) ? 1.0f : -1.0f;
-        xd = j > 0 ? x[base - pl + c] : gsign * x0;
-        xu = j + 1 < A.ny ? x[base + pl + c] : gsign * x0;
+        const float gs = BC == BC_NEUMANN ? 1.0f : -1.0f;
+        xd = j > 0 ? *reinterpret_cast<const float4 *>(x + at - pl)
+                   : make_float4(gs * x0.x, gs * x0.y, gs * x0.z, gs * x0.w);
+        xu = j + 1 < A.ny ? *reinterpret_cast<const float4 *>(x + at + pl)
+                          : make_float4(gs * x0.x, gs * x0.y, gs * x0.z, gs * x0.w);
       }
-      const float x2 = -2.0f * x0;
-      // exact second differences D = hi + lo
-      ff s = two_sum(xe, xw), t = two_sum(s.hi, x2);
-      const float Dxh = t.hi, Dxl = t.lo + s.lo;
-      s = two_sum(xn, xs); t = two_sum(s.hi, x2);
-      const float Dzh = t.hi, Dzl = t.lo + s.lo;
-      s = two_sum(xu, xd); t = two_sum(s.hi, x2);
-      const float Dyh = t.hi, Dyl = t.lo + s.lo;
-      // (b - m) - sigma x0 + sum_a K_a D_a, cascaded
-      const ff bm = two_sum(bv, -m.x);
-      float S = bm.hi, E = bm.lo - m.y;
-      bt = bm.hi + E;
-      sum_into(S, E, -A.sigma * x0);
-      ff p = two_prod(A.kx.hi, Dxh);
-      sum_into(S, E, p.hi);
-      E += fmaf(A.kx.hi, Dxl, fmaf(A.kx.lo, Dxh, p.lo));
-      p = two_prod(A.kz.hi, Dzh);
-      sum_into(S, E, p.hi);
-      E += fmaf(A.kz.hi, Dzl, fmaf(A.kz.lo, Dzh, p.lo));
-      p = two_prod(A.ky.hi, Dyh);
-      sum_into(S, E, p.hi);
-      E += fmaf(A.ky.hi, Dyl, fmaf(A.ky.lo, Dyh, p.lo));
-      res = S + E;
+      const float4 bv = *reinterpret_cast<const float4 *>(b + at);
+      float2 m = make_float2(0.f, 0.f);
+      if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
+      float bt0, bt1, bt2, bt3;
+      res.x = residual_point<SIGMA>(A, bv.x, m, x0.x, x0.y, xW, xn.x, xs.x, xu.x, xd.x, bt0);
+      res.y = residual_point<SIGMA>(A, bv.y, m, x0.y, x0.z, x0.x, xn.y, xs.y, xu.y, xd.y, bt1);
+      res.z = residual_point<SIGMA>(A, bv.z, m, x0.z, x0.w, x0.y, xn.z, xs.z, xu.z, xd.z, bt2);
+      res.w = residual_point<SIGMA>(A, bv.w, m, x0.w, xE, x0.z, xn.w, xs.w, xu.w, xd.w, bt3);
+      if (norms) {
+        r2 = (double)res.x * res.x + (double)res.y * res.y + (double)res.z * res.z + (double)res.w * res.w;
+        b2 = (double)bt0 * bt0 + (double)bt1 * bt1 + (double)bt2 * bt2 + (double)bt3 * bt3;
+        r1 = (double)res.x + res.y + res.z + res.w;
+        b1 = (double)bt0 + bt1 + bt2 + bt3;
+      }
     }
-    r[base + c] = res;
-    rr = res;
-    bb = bt;
+    *reinterpret_cast<float4 *>(r + at) = res;
   }
-  if (norms) block_accumulate(rr * rr, bb * bb, rr, bb, norms);
+  if (norms) block_accumulate(r2, b2, r1, b1, norms);
 }
 
 __global__ void __launch_bounds__(128)
@@ -204,13 +227,34 @@ static ResidualArgs make_args(int nx, int ny, int nz, const StencilCoef &c, cons
   return A;
 }
 
+template <int BC, bool SIGMA>
+static cudaError_t launch_residual_f32(const ResidualArgs &A, const float *b, const float *x, float *r, double *norms,
+                                       cudaStream_t st) {
+  const int units = A.nz * (A.nx / 4);
+  IBM_KTRY(launch_pdl(k_residual_f32v<BC, SIGMA>, dim3((unsigned)ceil_div(units, 128), (unsigned)A.ny), 128, 0, st, A,
+                      b, x, r, norms));
+  return cudaGetLastError();
+}
+
 template <>
 cudaError_t launch_residual<float>(int nx, int ny, int nz, const StencilCoef &c, const float *b, const float *x,
                                    float *r, const double *boff, double *norms, cudaStream_t st) {
-  const Launch3 L = stencil_launch(nx, ny, nz);
-  IBM_KTRY(launch_pdl(k_residual_f32, L.grid, L.block, 0, st, make_args(nx, ny, nz, c, boff), b, x, r, norms));
-  return cudaGetLastError();
+  if (nx % 4 != 0 || ((uintptr_t)b | (uintptr_t)x | (uintptr_t)r) & 15u) return cudaErrorInvalidValue;
+  const ResidualArgs A = make_args(nx, ny, nz, c, boff);
+  const bool sg = c.sigma != 0.0;
+#define IBM_RES_BC(B)                                                                             \
+  case B:                                                                                         \
+    return sg ? launch_residual_f32<B, true>(A, b, x, r, norms, st) : launch_residual_f32<B, false>(A, b, x, r, norms, st);
+  switch (c.bc) {
+    IBM_RES_BC(BC_NEUMANN)
+    IBM_RES_BC(BC_CELL_DIRICHLET)
+    IBM_RES_BC(BC_FACE_DIRICHLET)
+    IBM_RES_BC(BC_PERIODIC)
+    default: return cudaErrorInvalidValue;
+  }
+#undef IBM_RES_BC
 }
+
 template <>
 cudaError_t launch_residual<double>(int nx, int ny, int nz, const StencilCoef &c, const double *b, const double *x,
                                     double *r, const double *boff, double *norms, cudaStream_t st) {

@@ -192,7 +192,7 @@ PENCIL_MODE_SHAPES = [(32, 32, 32), (12, 10, 24), (48, 17, 96), (24, 129, 16), (
 
 @pytest.mark.parametrize("shape", PENCIL_MODE_SHAPES)
 def test_every_pencil_kernel_matches_oracle(shape):
-    """IBM_PENCIL_MODE 1 (warp-parallel blocks), 2 (tile sweep), 3 (streaming sweep)."""
+    """IBM_PENCIL_MODE 1 (warp-parallel blocks), 2 (tile sweep), 3 (streaming sweep), 4 (segmented sweep)."""
     nx, ny, nz = shape
     g = grid(nx, ny, nz)
     b = synth.white_noise(nx, ny, nz, workload=14, stream=0) + 0.1
@@ -201,7 +201,7 @@ def test_every_pencil_kernel_matches_oracle(shape):
     ref32, _ = O.poisson_solve(b32, g)
     helm = {bc: O.helmholtz_solve(b32, g, 0.02, bc)
             for bc in (ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_FACE_DIRICHLET)}
-    for mode in (1, 2, 3):
+    for mode in (1, 2, 3, 4):
         for prec, dt, tol, bb, ref in ((ibm.IBM_FP64, torch.float64, TOL_FP64, b, ref64),
                                        (ibm.IBM_FP32_REFINED, torch.float32, TOL_FP32, b32, ref32)):
             os.environ["IBM_PENCIL_MODE"] = str(mode)
@@ -224,6 +224,61 @@ def test_every_pencil_kernel_matches_oracle(shape):
                 ibm.ibm_plan_check(plan)
             finally:
                 ibm.ibm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("shape", [(32, 256, 32), (16, 500, 16), (24, 129, 16)])
+def test_segmented_sweep_unrefined_fp32_accuracy(shape):
+    """Without refinement the FP32 error is the sweep's own: the segmented
+    sweep (pivot prefix, carries combined across warps) stays within a small
+    factor of the single two-ended sweep on long, near-singular pencils."""
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    b32 = synth.white_noise(nx, ny, nz, workload=15, stream=0).astype(np.float32)
+    ref, _ = O.poisson_solve(b32.astype(np.float64), g)
+    errs = {}
+    for mode in (3, 4):
+        os.environ["IBM_PENCIL_MODE"] = str(mode)
+        try:
+            plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], ibm.IBM_FP32_REFINED, 0)
+        finally:
+            del os.environ["IBM_PENCIL_MODE"]
+        try:
+            rhs = dev(b32, torch.float32)
+            phi = torch.empty_like(rhs)
+            ibm.ibm_poisson_solve(plan, rhs, phi)
+            torch.cuda.synchronize()
+            errs[mode] = rel_l2(host(phi), ref)
+        finally:
+            ibm.ibm_plan_destroy(plan)
+    assert errs[4] <= 1e-5, errs
+    assert errs[4] <= 2.0 * errs[3] + 1e-7, errs
+
+
+def test_fp32_fields_must_be_16_byte_aligned():
+    """The four-point residual and the vector loads need 16-byte aligned
+    fields: an element-aligned view at an odd offset is refused before any
+    launch, the aligned view of the same buffer solves."""
+    nx, ny, nz = 32, 24, 16
+    g = grid(nx, ny, nz)
+    n = nx * ny * nz
+    b32 = synth.white_noise(nx, ny, nz, workload=16, stream=0).astype(np.float32)
+    ref, _ = O.poisson_solve(b32.astype(np.float64), g)
+    plan = _plan(nx, ny, nz, g, ibm.IBM_FP32_REFINED, 2)
+    try:
+        buf = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        out = torch.zeros(n + 4, dtype=torch.float32, device="cuda")
+        for off in (1, 3):
+            with pytest.raises(ibm.IbmError) as e:
+                ibm.ibm_poisson_solve(plan, buf[off:off + n].view(ny, nz, nx), out[off:off + n].view(ny, nz, nx))
+            assert e.value.code == ibm.IBM_ERR_ARG
+        rhs = buf[4:4 + n].view(ny, nz, nx)
+        rhs.copy_(dev(b32, torch.float32))
+        phi = out[4:4 + n].view(ny, nz, nx)
+        ibm.ibm_poisson_solve(plan, rhs, phi)
+        torch.cuda.synchronize()
+        assert rel_l2(host(phi), ref) <= TOL_FP32
+    finally:
+        ibm.ibm_plan_destroy(plan)
 
 
 def test_invalid_arguments_rejected_before_launch():

@@ -116,7 +116,7 @@ def test_three_field_helmholtz_every_kernel(prec):
     params = (0.1, 0.0, 0.0)
     st = dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
     ref, _ = O.rk_stage(st, dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=params), 2, dt, nu, g)
-    for plane_mode, pencil_mode in ((0, 2), (0, 3), (1, 2), (2, 3), (0, 1)):
+    for plane_mode, pencil_mode in ((0, 2), (0, 3), (1, 2), (2, 3), (0, 1), (1, 4)):
         os.environ["IBM_PLANE_MODE_FIELDS"] = str(plane_mode)
         os.environ["IBM_PENCIL_MODE"] = str(pencil_mode)
         try:
