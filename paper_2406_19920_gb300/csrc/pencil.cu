@@ -364,14 +364,14 @@ k_pencil(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ l
 //   * pivots: e_k depends on the pencil's (a, g) only.  The map
 //     e -> g + a e / (a + e) is a Moebius map with fixed points e+ > 0 and
 //     e- = -a g / e+, and z_k = (e_k - e+) / (e_k - e-) shrinks
-//     geometrically, z_k = z_0 lambda^k with lambda = (a + e-) / (a + e+) =
-//     a^2 g / (e+^2 (a + e+)), so every row's pivot follows in closed form,
-//     e_k = e+ + (e+ - e-) z_k / (1 - z_k), with no serial dependence on the
-//     rows before it (all terms are sums and products of positive numbers
-//     but z, whose absolute error only moves e_k by a few ulps of e+, far
-//     below the pivot a + e_k).  A warp whose lanes all have |z| below a
-//     sixteenth of the unit roundoff at its first row takes the converged
-//     pivot e+ for every row (constant r and w);
+//     geometrically, z_k = z_0 lambda^k with 1 - lambda =
+//     (a g + e+^2) / (e+ (a + e+)), so the pivot at any row follows in closed
+//     form, e_k = e+ + (e+ - e-) z_k / (1 - z_k) (all terms sums and
+//     products of positive numbers but z, whose absolute error only moves
+//     e_k by a few ulps of e+, far below the pivot a + e_k).  A warp takes
+//     its first row's pivot from it and runs the recurrence through its own
+//     rows, or, when all its lanes have |z| below a sixteenth of the unit
+//     roundoff there, the converged pivot e+ for every row (constant r, w);
 //   * forward elimination y_k = r_k f_k + w_k y_{k-1} (w = a r) is a
 //     first-order linear recurrence: each warp sweeps its rows from a zero
 //     carry, keeping yhat and the product of its w, and the true values
@@ -392,8 +392,8 @@ __device__ __forceinline__ void cp_async_elem(cplx<T> *dst, const cplx<T> *src) 
 // row guards) and CW (converged pivots: constant r and w).  Rows u >= len of a
 // partial segment are pass-through (r = 0, w = 1) and read as zero.
 template <typename T, int S, bool FULL, bool CW>
-__device__ __forceinline__ void seg_forward(cplx<T> (&v)[S], int len, T a, T sgn, T ep, T D, T lam, T z, T *wc,
-                                            cplx<T> &y, T &prod, T &qlast) {
+__device__ __forceinline__ void seg_forward(cplx<T> (&v)[S], int len, int k0, T a, T g, T e0, T sgn, T ep, T D, T z,
+                                            T *wc, cplx<T> &y, T &prod, T &qlast) {
   y = mk<T>(0, 0);
   prod = (T)1;
   qlast = (T)0;
@@ -409,16 +409,17 @@ __device__ __forceinline__ void seg_forward(cplx<T> (&v)[S], int len, T a, T sgn
     qlast = ep * r;
     return;
   }
+  // from the closed-form pivot at the segment's first row, the recurrence
+  // e_{k+1} = g + a q_k (the same operations as a single sweep)
+  T e = k0 == 0 ? e0 : fma(D * z, rcp<T>((T)1 - z), ep);
+  T r = rcp<T>(a + e), q = e * r;
 #pragma unroll
   for (int u = 0; u < S; ++u) {
-    // e_k = e+ + (e+ - e-) z_k / (1 - z_k): no dependence on the previous
-    // row.  FP32: z_k = z_k0 exp(u log lambda) (lam holds log lambda), each
-    // to a few ulps; FP64: running product by lambda.
-    T zu;
-    if constexpr (sizeof(T) == 4) zu = z * expf((T)u * lam);
-    else { zu = z; z *= lam; }
-    const T e = fma(D * zu, rcp<T>((T)1 - zu), ep);
-    const T r = rcp<T>(a + e);
+    if (u > 0) {
+      e = fma(a, q, g);
+      r = rcp<T>(a + e);
+      q = e * r;
+    }
     const bool in = FULL || u < len;
     const T ru = in ? sgn * r : (T)0;
     const T wu = in ? a * r : (T)1;
@@ -427,7 +428,7 @@ __device__ __forceinline__ void seg_forward(cplx<T> (&v)[S], int len, T a, T sgn
     y.y = fma(wu, y.y, ru * v[u].y);
     v[u] = y;
     prod *= wu;
-    if (FULL ? u == S - 1 : u == len - 1) qlast = e * r;
+    if (FULL ? u == S - 1 : u == len - 1) qlast = q;
   }
 }
 
@@ -559,9 +560,10 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
     // pivots in closed form (fixed points e+ > 0 > e- = -a g / e+ of the
     // Moebius map, z_k = z_0 lambda^k); the singular zero pencil (g = 0)
     // keeps e = e0 = 0
-    T ep, D, lam, z;
+    T ep, D, z;
     bool cw;
     {
+      T lam;
       const bool zero = g == (T)0;
       const T gg = zero ? (T)1 : g;
       ep = (T)0.5 * (gg + sqrt(fma(gg, gg, (T)4 * a * gg)));
@@ -582,7 +584,7 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
         }
         z *= lp;
       }
-      if (zero) { ep = (T)0; D = (T)0; lam = (T)0; z = (T)0; }
+      if (zero) { ep = (T)0; D = (T)0; z = (T)0; }
       const bool ok = fabs(z) < (sizeof(T) == 4 ? (T)0x1p-28 : (T)0x1p-56);
       cw = __all_sync(0xffffffffu, ok) && len == S;
     }
@@ -599,9 +601,9 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
     const T wconst = a * rcp<T>(a + ep);
     cplx<T> y;
     T prod, qlast;
-    if (cw) seg_forward<T, S, true, true>(v, len, a, sgn, ep, D, lam, z, wc, y, prod, qlast);
-    else if (full) seg_forward<T, S, true, false>(v, len, a, sgn, ep, D, lam, z, wc, y, prod, qlast);
-    else seg_forward<T, S, false, false>(v, len, a, sgn, ep, D, lam, z, wc, y, prod, qlast);
+    if (cw) seg_forward<T, S, true, true>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
+    else if (full) seg_forward<T, S, true, false>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
+    else seg_forward<T, S, false, false>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
     cf[(0 * L + seg) * 32 + lane] = y.x;
     cf[(1 * L + seg) * 32 + lane] = y.y;
     cf[(2 * L + seg) * 32 + lane] = prod;
