@@ -124,6 +124,23 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3],
 int ibm_plan_destroy(ibm_plan plan);
 /* Select the delta kernel used by ibm_interp / ibm_spread / ibm_substep. */
 int ibm_plan_set_delta(ibm_plan plan, int kernel);
+/* Spreading (Eq. 2d) used by ibm_spread / ibm_substep.
+ *   IBM_SPREAD_ATOMIC  (default) the paper's L1 kernel (Sec. 2.3.2): one
+ *                      thread per (marker, component) adds its S^3 shares
+ *                      with global atomics; the order of the additions, and so
+ *                      the last bits of f, vary from run to run.
+ *   IBM_SPREAD_GATHER  the alternative Sec. 2.3.2 describes and sets aside:
+ *                      one thread per Eulerian point gathers the shares of the
+ *                      markers whose stencils cover it.  Markers are binned by
+ *                      stencil origin into 4^3 bricks per component (counting
+ *                      sort, each brick's entries ordered by marker index), so
+ *                      every point sums its shares in a fixed order: f is
+ *                      bitwise the same on every run.  Needs plan workspace of
+ *                      about 12 bytes per brick and 40 bytes per marker
+ *                      component (allocated on first use; IBM_ERR_OOM if it
+ *                      cannot be). */
+enum { IBM_SPREAD_ATOMIC = 0, IBM_SPREAD_GATHER = 1 };
+int ibm_plan_set_spread(ibm_plan plan, int mode);
 /* Bytes of device memory the plan holds. */
 size_t ibm_plan_workspace_bytes(ibm_plan plan);
 

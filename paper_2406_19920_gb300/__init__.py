@@ -22,6 +22,7 @@ IBM_BC_PXZ_WALL_Y, IBM_BC_TRIPLY_PERIODIC = 1, 2
 IBM_FP64, IBM_FP32_REFINED = 0, 1
 IBM_FIELD_CELL_NEUMANN, IBM_FIELD_CELL_DIRICHLET, IBM_FIELD_FACE_DIRICHLET, IBM_FIELD_PERIODIC = 0, 1, 2, 3
 IBM_DELTA_ROMA3, IBM_DELTA_PESKIN4 = 0, 1
+IBM_SPREAD_ATOMIC, IBM_SPREAD_GATHER = 0, 1
 IBM_MOTION_STATIC, IBM_MOTION_TRANSLATE, IBM_MOTION_HEAVE = 0, 1, 2
 IBM_REQ_POISSON, IBM_REQ_HELMHOLTZ, IBM_REQ_SUBSTEP = 0, 1, 2
 
@@ -74,6 +75,7 @@ _SIG = {
     "ibm_plan_create": (_I, [_I, _I, _I, _I, ctypes.POINTER(_D), _I, _I, ctypes.POINTER(_P)]),
     "ibm_plan_destroy": (_I, [_P]),
     "ibm_plan_set_delta": (_I, [_P, _I]),
+    "ibm_plan_set_spread": (_I, [_P, _I]),
     "ibm_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
     "ibm_plan_check": (_I, [_P]),
     "ibm_plan_profile": (_I, [_P, _I]),
@@ -164,6 +166,10 @@ def ibm_plan_destroy(plan):
 
 def ibm_plan_set_delta(plan, kernel):
     return _check(lib().ibm_plan_set_delta(plan, kernel))
+
+
+def ibm_plan_set_spread(plan, mode):
+    return _check(lib().ibm_plan_set_spread(plan, mode))
 
 
 def ibm_plan_check(plan):

@@ -14,6 +14,7 @@
 // that the weights see the marker position without the FP32 rounding of
 // X/h; the weights and sums run in the plan precision.  Spreading
 // accumulates with global atomics as in the paper's L1 kernel (Sec. 2.3.2).
+#include <algorithm>
 #include <cmath>
 
 #include "plan.h"
@@ -204,6 +205,277 @@ k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, con
   }
 }
 
+// ---------------------------------------------------------------------------
+// Deterministic spreading by Eulerian gather (IBM_SPREAD_GATHER).
+//
+// Every (marker, component) entry t = 3 m + c gets a stencil record (origin
+// b, offsets f, amplitude F dV / (hx hy hz)).  Entries are grouped by the
+// cell of their origin in component c's grid (y shifted by 2 so that origins
+// below the first row have a cell too): a counting sort into 4^3 bricks,
+// then, per non-empty brick, a counting sort into its 64 cells, and each
+// cell's entries ordered by t.  A grid point is covered exactly by the
+// entries whose origin lies in one of the S^3 cells at most S - 1 below it
+// along each axis; it visits those cells in a fixed order and their entries
+// in t order, so its sum has the same order on every run.  Only target
+// bricks (those some stencil touches) are visited.
+// ---------------------------------------------------------------------------
+constexpr int kBrick = 4;
+constexpr int kCells = kBrick * kBrick * kBrick;
+
+template <typename T> struct StencilRec {
+  int bx, by, bz;  // origin (bx, bz wrapped into the periodic range)
+  T fx, fy, fz, amp;
+};
+
+struct BrickGeom {
+  int nbx, nby, nbz, nb;  // bricks per axis and per component (nb = nbx nby nbz)
+};
+
+__device__ __forceinline__ int brick_of(const BrickGeom &bg, int c, int xb, int yb, int zb) {
+  return ((c * bg.nbz + zb) * bg.nby + yb) * bg.nbx + xb;
+}
+
+// Cell (wrapped x, z; y + 2 clamped, so that any origin, even one of a marker
+// outside the walls, has one) of a stencil origin: its brick and its index
+// in the brick.
+__device__ __forceinline__ void origin_cell(const IbmGrid &g, const BrickGeom &bg, int c, int bx, int by, int bz,
+                                            int &brick, int &cell) {
+  const int x = wrap(bx, g.nx), z = wrap(bz, g.nz), y = min(max(by + 2, 0), bg.nby * kBrick - 1);
+  brick = brick_of(bg, c, x / kBrick, y / kBrick, z / kBrick);
+  cell = ((z % kBrick) * kBrick + y % kBrick) * kBrick + x % kBrick;
+}
+
+// Block-wide exclusive scan of one int per thread.
+__device__ __forceinline__ int block_excl_scan(int v, int *warp_sums) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int incl = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += u;
+  }
+  if (lane == 31) warp_sums[w] = incl;
+  __syncthreads();
+  if (w == 0) {
+    const int nw = blockDim.x >> 5;
+    const int x = lane < nw ? warp_sums[lane] : 0;
+    int xi = x;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += u;
+    }
+    if (lane < nw) warp_sums[lane] = xi - x;
+  }
+  __syncthreads();
+  const int r = warp_sums[w] + incl - v;
+  __syncthreads();
+  return r;
+}
+
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+k_gather_prep(IbmGrid g, BrickGeom bg, int n, const T *__restrict__ X, const T *__restrict__ F,
+              const T *__restrict__ dV, T scale, StencilRec<T> *__restrict__ rec, int *__restrict__ count,
+              int *__restrict__ target, int *__restrict__ tlist, int *__restrict__ blist, int *__restrict__ cnt) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const int m = t / 3, c = t - 3 * m;
+  StencilRec<T> r;
+  stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], r.bx, r.by, r.bz, r.fx, r.fy, r.fz);
+  r.amp = scale * F[t] * dV[m] * (T)g.vol_inv;
+  const int bx_raw = r.bx, bz_raw = r.bz;
+  r.bx = wrap(r.bx, g.nx);  // records keep the periodic origins wrapped
+  r.bz = wrap(r.bz, g.nz);
+  rec[t] = r;
+  int brick, cell;
+  origin_cell(g, bg, c, r.bx, r.by, r.bz, brick, cell);
+  // the first entry of a brick lists it (list order is immaterial: every
+  // brick's range and every point's sum are formed in a fixed order later)
+  if (atomicAdd(count + brick, 1) == 0) blist[atomicAdd(cnt + 1, 1)] = brick;
+  // bricks the stencil touches (points b .. b + S - 1 per axis)
+  const int xa = r.bx / kBrick, xe = wrap(bx_raw + S - 1, g.nx) / kBrick;
+  const int za = r.bz / kBrick, ze = wrap(bz_raw + S - 1, g.nz) / kBrick;
+  const int ya = min(max(r.by + 2, 0), bg.nby * kBrick - 1) / kBrick;
+  const int ye = min(max(r.by + 2 + S - 1, 0), bg.nby * kBrick - 1) / kBrick;
+  const int xs[2] = {xa, xe}, ys[2] = {ya, ye}, zs[2] = {za, ze};
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int d = 0; d < 2; ++d) {
+        const int tb = brick_of(bg, c, xs[d], ys[b], zs[a]);
+        if (target[tb] == 0 && atomicExch(target + tb, 1) == 0) tlist[atomicAdd(cnt, 1)] = tb;
+      }
+}
+
+// One CTA of 1024 threads: the entry ranges of the listed non-empty bricks
+// (offq[q] .. offq[q + 1] for brick blist[q]; rank[blist[q]] = q).
+__global__ void __launch_bounds__(1024)
+k_gather_ranges(const int *__restrict__ count, const int *__restrict__ blist, const int *__restrict__ cnt,
+                int *__restrict__ offq, int *__restrict__ rank) {
+  __shared__ int ws[32];
+  __shared__ int tot;
+  const int nb = cnt[1];
+  int carry = 0;
+  for (int base = 0; base < nb; base += blockDim.x) {
+    const int q = base + threadIdx.x;
+    const int v = q < nb ? count[blist[q]] : 0;
+    const int e = block_excl_scan(v, ws) + carry;
+    if (q < nb) { offq[q] = e; rank[blist[q]] = q; }
+    if (threadIdx.x == blockDim.x - 1) tot = e + v;
+    __syncthreads();
+    carry = tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) offq[nb] = carry;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gather_scatter(IbmGrid g, BrickGeom bg, int n, const StencilRec<T> *__restrict__ rec, const int *__restrict__ offq,
+                 const int *__restrict__ rank, int *__restrict__ fill, int *__restrict__ entry) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= 3 * n) return;
+  const StencilRec<T> r = rec[t];
+  int brick, cell;
+  origin_cell(g, bg, t % 3, r.bx, r.by, r.bz, brick, cell);
+  entry[offq[rank[brick]] + atomicAdd(fill + brick, 1)] = t;
+}
+
+// Per listed brick (one CTA each, grid-stride): its entries by cell (cell
+// offsets, relative to the brick's range, in coff[q * 65 ..]) and, within a
+// cell, in ascending t, as their records in srec.  A brick's entries are
+// grouped in shared memory up to kSortCap of them, in global memory
+// (sorted[]) beyond.
+constexpr int kSortCap = 6144;
+
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_gather_cells(IbmGrid g, BrickGeom bg, const StencilRec<T> *__restrict__ rec, const int *__restrict__ offq,
+               const int *__restrict__ blist, const int *__restrict__ cnt, const int *__restrict__ entry,
+               int *__restrict__ sorted, int *__restrict__ coff, StencilRec<T> *__restrict__ srec) {
+  __shared__ int hist[kCells], start[kCells + 1], fillc[kCells];
+  __shared__ int buf[kSortCap];
+  const int nb = cnt[1];
+  for (int q = blockIdx.x; q < nb; q += gridDim.x) {
+    const int b = blist[q];
+    const int lo = offq[q], hi = offq[q + 1];
+    const int c = b / bg.nb;
+    int *dst = hi - lo <= kSortCap ? buf : sorted + lo;
+    if (threadIdx.x < kCells) { hist[threadIdx.x] = 0; fillc[threadIdx.x] = 0; }
+    __syncthreads();
+    for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+      const StencilRec<T> r = rec[entry[e]];
+      int brick, cell;
+      origin_cell(g, bg, c, r.bx, r.by, r.bz, brick, cell);
+      atomicAdd(hist + cell, 1);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      int acc = 0;
+      for (int k = 0; k < kCells; ++k) { start[k] = acc; acc += hist[k]; }
+      start[kCells] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x <= kCells) coff[(size_t)q * (kCells + 1) + threadIdx.x] = start[threadIdx.x];
+    for (int e = lo + threadIdx.x; e < hi; e += blockDim.x) {
+      const int t = entry[e];
+      const StencilRec<T> r = rec[t];
+      int brick, cell;
+      origin_cell(g, bg, c, r.bx, r.by, r.bz, brick, cell);
+      dst[start[cell] + atomicAdd(fillc + cell, 1)] = t;
+    }
+    __syncthreads();
+    // t order within each cell: an entry's place is the number of entries of
+    // its cell with a smaller t (t values are distinct)
+    for (int e = threadIdx.x; e < hi - lo; e += blockDim.x) {
+      const int t = dst[e];
+      int cell = 0;
+      while (start[cell + 1] <= e) ++cell;
+      int rk = 0;
+      for (int i = start[cell]; i < start[cell + 1]; ++i) rk += dst[i] < t ? 1 : 0;
+      srec[lo + start[cell] + rk] = rec[t];
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA of 8 warps per target brick (grid-stride over the target list).
+// The entry ranges of the (4 + S - 1)^3 origin cells its points can need are
+// looked up once into shared memory; then a warp takes the brick's points in
+// turn, and for each of a point's S^3 origin cells (fixed order) lane l takes
+// the cell's entries l, l + 32, ...; the lanes' sums are added by a fixed
+// butterfly: the same order on every run.
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+k_gather(IbmGrid g, BrickGeom bg, const int *__restrict__ tlist, const int *__restrict__ cnt,
+         const int *__restrict__ count, const int *__restrict__ offq, const int *__restrict__ rank,
+         const int *__restrict__ coff, const StencilRec<T> *__restrict__ srec, T *fu, T *fv, T *fw) {
+  constexpr int E = kBrick + S - 1;  // origin cells per axis
+  __shared__ int rlo[E * E * E], rhi[E * E * E];
+  const int nt = cnt[0];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  for (int q = blockIdx.x; q < nt; q += gridDim.x) {
+    const int bid = tlist[q];
+    const int c = bid / bg.nb;
+    int rem = bid - c * bg.nb;
+    const int zb = rem / (bg.nby * bg.nbx);
+    rem -= zb * bg.nby * bg.nbx;
+    const int yb = rem / bg.nbx, xb = rem - yb * bg.nbx;
+    const int i0 = xb * kBrick - (S - 1), k0 = zb * kBrick - (S - 1), j0 = yb * kBrick - 2 - (S - 1);
+    for (int u = threadIdx.x; u < E * E * E; u += blockDim.x) {
+      const int ox = u % E, oy = (u / E) % E, oz = u / (E * E);
+      int brick, cell;
+      origin_cell(g, bg, c, i0 + ox, j0 + oy, k0 + oz, brick, cell);
+      int a = 0, z = 0;
+      if (count[brick] != 0) {
+        const int qq = rank[brick];
+        const int base = offq[qq];
+        const int *co = coff + (size_t)qq * (kCells + 1);
+        a = base + co[cell];
+        z = base + co[cell + 1];
+      }
+      rlo[u] = a;
+      rhi[u] = z;
+    }
+    __syncthreads();
+    const int jlo = c == 1 ? 1 : 0;
+    T *f = c == 0 ? fu : c == 1 ? fv : fw;
+    for (int pt = w; pt < kCells; pt += 8) {
+      const int px = pt % kBrick, py = (pt / kBrick) % kBrick, pz = pt / (kBrick * kBrick);
+      const int i = xb * kBrick + px, k = zb * kBrick + pz, j = yb * kBrick + py - 2;
+      if (j < jlo || j > g.ny - 1) continue;  // warp-uniform
+      T acc = (T)0;
+      bool any = false;
+      for (int qz = 0; qz < S; ++qz) {
+        for (int qy = 0; qy < S; ++qy) {
+          for (int qx = 0; qx < S; ++qx) {
+            const int u = ((pz + S - 1 - qz) * E + (py + S - 1 - qy)) * E + (px + S - 1 - qx);
+            const int bx = i - qx < 0 ? i - qx + g.nx : i - qx, by = j - qy;
+            const int bz = k - qz < 0 ? k - qz + g.nz : k - qz;
+            for (int e = rlo[u] + lane; e < rhi[u]; e += 32) {
+              const StencilRec<T> r = srec[e];
+              // the cell holds every origin that maps to it; keep the exact one
+              if (r.bx != bx || r.by != by || r.bz != bz) continue;
+              const T wx = S == 3 ? phi_roma3<T>(r.fx - (T)qx) : phi_peskin4<T>(r.fx - (T)qx);
+              const T wy = S == 3 ? phi_roma3<T>(r.fy - (T)qy) : phi_peskin4<T>(r.fy - (T)qy);
+              const T wz = S == 3 ? phi_roma3<T>(r.fz - (T)qz) : phi_peskin4<T>(r.fz - (T)qz);
+              acc += r.amp * (wy * wz) * wx;
+              any = true;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (__any_sync(0xffffffffu, any) && lane == 0) f[((size_t)j * g.nz + k) * g.nx + i] += acc;
+    }
+    __syncthreads();  // the range tables are reused by the next brick
+  }
+}
+
 static IbmGrid ibm_grid(const ibm_plan_s *p) {
   IbmGrid g;
   g.nx = p->nx; g.ny = p->ny; g.nz = p->nz;
@@ -253,10 +525,67 @@ cudaError_t launch_interp(const ibm_plan_s *p, int n, const T *X, const T *u, co
   return cudaGetLastError();
 }
 
+// Workspace of the gather: ints count, fill, target, rank (len each), tlist,
+// blist, offq (len + 1 each), cnt (2), entry, sorted (3 n each), coff
+// (min(3 n, len) x 65); then the stencil records and the same in cell order
+// (3 n each).
+template <typename T>
+static int spread_gather(ibm_plan_s *p, int n, const T *X, const T *F, const T *dV, T *fu, T *fv, T *fw,
+                         double scale, cudaStream_t st) {
+  const IbmGrid g = ibm_grid(p);
+  BrickGeom bg;
+  bg.nbx = ceil_div(p->nx, kBrick);
+  bg.nby = ceil_div(p->ny + 4, kBrick);
+  bg.nbz = ceil_div(p->nz, kBrick);
+  bg.nb = bg.nbx * bg.nby * bg.nbz;
+  const int len = 3 * bg.nb;
+  const size_t ne = 3 * (size_t)n;
+  const size_t nbrk = std::min(ne, (size_t)len);
+  const size_t ints = 4 * (size_t)len + 3 * ((size_t)len + 1) + 2 + 2 * ne + nbrk * (kCells + 1);
+  const size_t rec_off = (ints * sizeof(int) + 15) & ~(size_t)15;
+  const size_t need = rec_off + 2 * ne * sizeof(StencilRec<T>);
+  if (need > p->gcap) {
+    if (p->gbuf) { cudaFree(p->gbuf); p->bytes -= p->gcap; p->gbuf = nullptr; p->gcap = 0; }
+    cudaError_t e = cudaMalloc(&p->gbuf, need);
+    if (e != cudaSuccess) { p->gbuf = nullptr; return set_error(IBM_ERR_OOM, "gather-spreading workspace"); }
+    p->gcap = need;
+    p->bytes += need;
+  }
+  int *count = static_cast<int *>(p->gbuf);
+  int *fill = count + len, *target = fill + len, *rank = target + len;
+  int *tlist = rank + len, *blist = tlist + len + 1, *offq = blist + len + 1, *cnt = offq + len + 1;
+  int *entry = cnt + 2, *sorted = entry + ne, *coff = sorted + ne;
+  StencilRec<T> *rec = reinterpret_cast<StencilRec<T> *>(static_cast<char *>(p->gbuf) + rec_off);
+  StencilRec<T> *srec = rec + ne;
+  IBM_CUDA_TRY(cudaMemsetAsync(count, 0, 3 * (size_t)len * sizeof(int), st));  // count, fill, target
+  IBM_CUDA_TRY(cudaMemsetAsync(cnt, 0, 2 * sizeof(int), st));
+  const int tb = ceil_div((int)ne, 256);
+  if (p->delta == IBM_DELTA_PESKIN4)
+    k_gather_prep<T, 4><<<tb, 256, 0, st>>>(g, bg, n, X, F, dV, (T)scale, rec, count, target, tlist, blist, cnt);
+  else
+    k_gather_prep<T, 3><<<tb, 256, 0, st>>>(g, bg, n, X, F, dV, (T)scale, rec, count, target, tlist, blist, cnt);
+  k_gather_ranges<<<1, 1024, 0, st>>>(count, blist, cnt, offq, rank);
+  k_gather_scatter<T><<<tb, 256, 0, st>>>(g, bg, n, rec, offq, rank, fill, entry);
+  const int cgrid = (int)std::min(nbrk, (size_t)152 * 8);
+  k_gather_cells<T><<<cgrid, 256, 0, st>>>(g, bg, rec, offq, blist, cnt, entry, sorted, coff, srec);
+  const int grid = std::min(len, 152 * 8);
+  if (p->delta == IBM_DELTA_PESKIN4)
+    k_gather<T, 4><<<grid, 256, 0, st>>>(g, bg, tlist, cnt, count, offq, rank, coff, srec, fu, fv, fw);
+  else
+    k_gather<T, 3><<<grid, 256, 0, st>>>(g, bg, tlist, cnt, count, offq, rank, coff, srec, fu, fv, fw);
+  IBM_CUDA_TRY(cudaGetLastError());
+  return IBM_OK;
+}
+
 template <typename T>
 cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, const T *dV, T *fu, T *fv, T *fw,
                           double scale, cudaStream_t st) {
   if (n <= 0) return cudaSuccess;
+  if (p->spread == IBM_SPREAD_GATHER) {
+    // the workspace may grow: the plan is single-stream, so it is not in use
+    const int rc = spread_gather<T>(const_cast<ibm_plan_s *>(p), n, X, F, dV, fu, fv, fw, scale, st);
+    return rc == IBM_OK ? cudaSuccess : cudaErrorMemoryAllocation;
+  }
   const IbmGrid g = ibm_grid(p);
   const int tb = ceil_div(3 * n, 256);
   if (p->delta == IBM_DELTA_PESKIN4)

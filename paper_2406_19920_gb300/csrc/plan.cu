@@ -122,7 +122,7 @@ static void plan_free(ibm_plan_s *p) {
   for (auto &r : p->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : p->evpool) cudaEventDestroy(e);
   void *bufs[] = {p->S, p->Sx[0], p->Sx[1], p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3], p->twy, p->lamy,
-                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf};
+                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf, p->gbuf};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -464,6 +464,14 @@ int ibm_plan_set_delta(ibm_plan plan, int kernel) {
   if (kernel != IBM_DELTA_ROMA3 && kernel != IBM_DELTA_PESKIN4)
     return set_error(IBM_ERR_ARG, "ibm_plan_set_delta: kernel %d", kernel);
   plan->delta = kernel;
+  return IBM_OK;
+}
+
+int ibm_plan_set_spread(ibm_plan plan, int mode) {
+  if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_set_spread: NULL plan");
+  if (mode != IBM_SPREAD_ATOMIC && mode != IBM_SPREAD_GATHER)
+    return set_error(IBM_ERR_ARG, "ibm_plan_set_spread: mode %d", mode);
+  plan->spread = mode;
   return IBM_OK;
 }
 

@@ -45,6 +45,9 @@ struct ibm_plan_s {
   void *sub[4];      // substep fields du, dv, dw, phi (allocated on first substep)
   void *mkbuf;       // marker force scratch [n][3] when the caller passes none
   size_t mkcap;      // bytes of mkbuf
+  int spread = 0;    // IBM_SPREAD_ATOMIC / IBM_SPREAD_GATHER
+  void *gbuf = nullptr;  // gather-spreading workspace (bins, sorted entries, stencil records)
+  size_t gcap = 0;       // bytes of gbuf
   void *twx, *twz;   // twiddles W_N^m (plan precision)
   void *twy, *lamy;  // triply periodic branch: W_ny^m and lambda_y (plan precision)
   void *lamx, *lamz; // modified wavenumbers kx'^2 (P), kz'^2 (nz) (plan precision)

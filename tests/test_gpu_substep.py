@@ -44,11 +44,13 @@ def _setup(nx, ny, nz, nmk, npdt, wl):
     return g, [cast(a) for a in (u, v, w, p)], [cast(a) for a in Np], cast(X0), cast(dV)
 
 
-def _run_gpu(g, fields, Np, X0, dV, stage, dt, nu, motion, params, prec, dt_t, t0):
+def _run_gpu(g, fields, Np, X0, dV, stage, dt, nu, motion, params, prec, dt_t, t0, spread=None):
     nx, ny, nz = g[:3]
     n = len(X0)
     plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, 1)
     try:
+        if spread is not None:
+            ibm.ibm_plan_set_spread(plan, spread)
         d = [dev(a, dt_t) for a in fields]
         dN = [dev(a, dt_t) for a in Np]
         st = ibm.ibm_state(d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(),
@@ -147,3 +149,24 @@ def test_marker_motion_heave(prec):
     tol = 1e-14 if prec == ibm.IBM_FP64 else 1e-7
     assert rel_l2(got["X"], Xr) <= tol
     assert rel_l2(got["Ud"], Udr) <= tol
+
+
+@pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
+def test_substep_with_gather_spreading(prec):
+    """The RK stage with the deterministic Eulerian-gather spreading gives the
+    oracle's stage, and the same bytes on a second run."""
+    nx, ny, nz = 32, 32, 32
+    npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
+    dt_t = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+    tol = TOL_STAGE_FP64 if prec == ibm.IBM_FP64 else TOL_STAGE_FP32
+    g, (u, v, w, p), Np, X0, dV = _setup(nx, ny, nz, 800, npdt, wl=41)
+    dt, nu = 1e-3, 1e-2
+    params = (0.1, 0.0, 0.0)
+    st = dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
+    ref, _ = O.rk_stage(st, dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=params), 2, dt, nu, g)
+    runs = [_run_gpu(g, [u, v, w, p], Np, X0, dV, 2, dt, nu, ibm.IBM_MOTION_TRANSLATE, params, prec, dt_t, 0.0,
+                     spread=ibm.IBM_SPREAD_GATHER) for _ in range(2)]
+    errs = {k: rel_l2(runs[0][k], ref[k]) for k in ("u", "v", "w", "p")}
+    assert max(errs.values()) <= tol, errs
+    for k in ("u", "v", "w", "p"):
+        assert np.array_equal(runs[0][k], runs[1][k]), k
