@@ -395,6 +395,9 @@ def run_gpu(args):
             ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0), ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
             bc=ibm.IBM_BC_TRIPLY_PERIODIC)
 
+    # ---- spreading: atomic L1 kernel vs deterministic Eulerian gather ----
+    spreading = spread_compare(ibm, torch) if not args.no_extras else None
+
     # ---- batched (64 instances, one graph launch) and served workloads ----
     batched = batched_compare(ibm, torch) if not args.no_extras else None
     serving = serve_sample(ibm) if not args.no_extras else None
@@ -444,6 +447,7 @@ def run_gpu(args):
         "value_traced": pts * args.steps * ws / (traced_ms * 1e-3),
         "poisson": solves,
         "poisson_256": solves_256,
+        "spreading": spreading,
         "batched": batched,
         "serving": serving,
         "large_plate": plate,
@@ -514,6 +518,61 @@ def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None):
     if "fp32_refined" in res and "fp64" in res:
         res["speedup_fp32_refined_over_fp64"] = res["fp32_refined"]["solves_per_s"] / res["fp64"]["solves_per_s"]
     return res
+
+
+def spread_compare(ibm, torch):
+    """Spreading (Eq. 2d) of a Fibonacci sphere at 128^3, FP32: the atomic L1
+    kernel against the deterministic Eulerian gather, us per call and markers
+    per second, and whether four repeated calls give the same bytes."""
+    from paper_2406_19920_gb300 import synth
+    res = {}
+    g = workload_grid()
+    for n in (N_MARKERS, 100000):
+        X, dV = synth.fibonacci_sphere(n, 0.25, (math.pi, 1.0, math.pi), g[3])
+        F = synth.marker_forces(n, workload=3)
+        plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
+        Xd, Fd, dVd = (torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float32) for a in (X, F, dV))
+        row = {}
+        for name, mode in (("atomic", ibm.IBM_SPREAD_ATOMIC), ("gather", ibm.IBM_SPREAD_GATHER)):
+            ibm.ibm_plan_set_spread(plan, mode)
+            outs = []
+            for _ in range(4):
+                f = [torch.zeros((NY, NZ, NX), dtype=torch.float32, device="cuda") for _ in range(3)]
+                ibm.ibm_spread(plan, n, Xd, Fd, dVd, *f)
+                outs.append(f)
+            torch.cuda.synchronize()
+            same = all(torch.equal(a, b) for o in outs[1:] for a, b in zip(outs[0], o))
+            f = outs[0]
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            K = 20
+            e0.record()
+            for _ in range(K):
+                ibm.ibm_spread(plan, n, Xd, Fd, dVd, *f)
+            e1.record()
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) / K * 1e3
+            row[name] = {"us": us, "markers_per_s": n / (us * 1e-6), "bitwise_repeatable": bool(same)}
+        res["sphere_%dk" % (n // 1000)] = row
+        ibm.ibm_plan_destroy(plan)
+    return res
+
+
+def solve_twice(n):
+    """Two refined FP32 Poisson solves on an n^3 grid of the workload domain
+    (N(0,1) right-hand side): the launch sequence the profiles of the 256^3
+    solve are taken from."""
+    import torch
+    import paper_2406_19920_gb300 as ibm
+    from paper_2406_19920_gb300 import synth
+    g = synth.grid(n, n, n)
+    plan = ibm.ibm_plan_create(n, n, n, g[3:], ibm.IBM_FP32_REFINED, 1)
+    b = torch.randn((n, n, n), device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(1))
+    x = torch.empty_like(b)
+    for _ in range(2):
+        ibm.ibm_poisson_solve(plan, b, x)
+    torch.cuda.synchronize()
+    ibm.ibm_plan_check(plan)
+    ibm.ibm_plan_destroy(plan)
 
 
 def batched_compare(ibm, torch):
@@ -760,9 +819,15 @@ def main():
     ap.add_argument("--ncu-summary", metavar="CSV",
                     help="summarise an ncu --csv launch list of `--quick --steps K` (pass the same --steps): "
                          "writes profiles/dram_traffic.json, prints a markdown table")
+    ap.add_argument("--solve", type=int, metavar="N",
+                    help="profiling aid: two refined FP32 Poisson solves on an N^3 grid (the first one warms up), "
+                         "then exit; `ncu -s <launches of one solve>` captures the second")
     args = ap.parse_args()
     if args.ncu_summary:
         ncu_summary(args.ncu_summary, args.steps)
+        return
+    if args.solve:
+        solve_twice(args.solve)
         return
     if args.warmup < 3:
         args.warmup = 3
