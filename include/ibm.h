@@ -207,6 +207,29 @@ int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[3], int ref
 int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs,
                         void *u, void *stream, ibm_info *info);
 
+/* The same solves with non-homogeneous wall data (Appendix B: the first and
+ * last rows of each pencil carry the boundary values on their right-hand
+ * sides; the paper's BC2.2 forms those terms from the 2D FFT of the ghost
+ * planes, here they are added to a copy of rhs before the forward transform,
+ * which is the same by linearity).  g_lo / g_hi are [nz][nx] planes in the
+ * plan precision (device, 16-byte aligned) at the wall y = 0 / y = Ly; NULL
+ * means 0 on that wall.
+ *   ibm_poisson_solve_bc    q = dphi/dy at the walls (inhomogeneous
+ *                           Neumann; the mean of the resulting right-hand
+ *                           side is removed and reported as for
+ *                           ibm_poisson_solve).
+ *   ibm_helmholtz_solve_bc  g is the wall value of u for the Dirichlet kinds
+ *                           (cell-centred: ghost = 2 g - u_0; wall faces: the
+ *                           face value, written to plane 0 of u) and du/dy
+ *                           at the wall for IBM_FIELD_CELL_NEUMANN.
+ * rhs is not modified (the plan's scratch field holds the copy); rhs may
+ * equal the output.  IBM_ERR_UNSUPPORTED on a triply periodic plan. */
+int ibm_poisson_solve_bc(ibm_plan plan, const void *rhs, void *phi, const void *q_lo,
+                         const void *q_hi, void *stream, ibm_info *info);
+int ibm_helmholtz_solve_bc(ibm_plan plan, double c, int field_bc, const void *rhs,
+                           void *u, const void *g_lo, const void *g_hi, void *stream,
+                           ibm_info *info);
+
 /* Interpolation, Eq. 2b: U[m] = sum over the kernel support of u_c(x) *
  * phi(dx/hx) phi(dy/hy) phi(dz/hz) for each component c on its own staggered
  * sub-grid, periodic in x and z.  X, U: [n][3]; u, v, w: fields. */

@@ -152,7 +152,7 @@ def _eigen_sum(grid, field_bc):
 # Linear solves: Eq. 2e (Helmholtz) and Eq. 2f (Poisson), Sec. 2.3.3
 # ---------------------------------------------------------------------------
 
-def poisson_solve(b, grid, nullspace="mean", ybc=NEUMANN):
+def poisson_solve(b, grid, nullspace="mean", ybc=NEUMANN, q_lo=None, q_hi=None):
     """Solve L_h phi = b - mean(b) on the staggered grid (Eq. 2f, S2 / S2.1).
 
     L_h is the 7-point Laplacian (second-order central differences, Sec. 2.1)
@@ -167,9 +167,17 @@ def poisson_solve(b, grid, nullspace="mean", ybc=NEUMANN):
     Method: exact eigen-decomposition with dense orthonormal bases.
     ybc=PERIODIC is the triply periodic branch (Sec. 2.3.3, S2: Fourier
     along all three axes, the divide diagonal, mean(phi) = 0).
+    q_lo, q_hi ([nz][nx] or None): inhomogeneous Neumann data dphi/dy at the
+    walls (Appendix B, the right-hand sides of the first and last pencil
+    rows): L_h phi with those ghosts equals b, i.e. the homogeneous system
+    with b minus the data's share of the operator.
     Returns (phi, removed_mean).
     """
     b = np.asarray(b, dtype=np.float64)
+    if q_lo is not None or q_hi is not None:
+        if ybc != NEUMANN:
+            raise ValueError("wall data needs the wall-bounded branch")
+        b = b - laplacian(np.zeros_like(b), grid, NEUMANN, q_lo, q_hi)
     mean_b = b.mean()
     rhs = b - mean_b
     if ybc not in (NEUMANN, PERIODIC):
@@ -190,37 +198,58 @@ def poisson_solve(b, grid, nullspace="mean", ybc=NEUMANN):
     return phi, mean_b
 
 
-def helmholtz_solve(r, grid, c, field_bc):
+def helmholtz_solve(r, grid, c, field_bc, g_lo=None, g_hi=None):
     """Solve (I - c L_h) u = r (Eq. 2e, S1 / S1.1).
 
     Eq. 2e reads  lap u* - (Re / (beta dt)) u* = -(Re / (beta dt)) RHS, which
     is (I - c L_h) u* = RHS with c = beta dt / Re.  field_bc selects the
     wall rows of Appendix B (PERIODIC: no walls).  For FACE_DIRICHLET plane 0
-    (the wall face) of the input is ignored and of the output is 0.
+    (the wall face) of the input is ignored and of the output is 0, or g_lo.
+    g_lo, g_hi ([nz][nx] or None): inhomogeneous wall data (the wall value
+    for the Dirichlet kinds, du/dy at the wall for NEUMANN); L_h then uses
+    the ghosts of laplacian(..., g_lo, g_hi), which is the homogeneous system
+    with r plus c times the data's share of the operator.
     """
     r = np.asarray(r, dtype=np.float64)
+    wall = g_lo is not None or g_hi is not None
+    if wall:
+        if field_bc == PERIODIC:
+            raise ValueError("wall data needs the wall-bounded branch")
+        r = r + c * laplacian(np.zeros_like(r), grid, field_bc, g_lo, g_hi)
     Q, lam = _eigen_sum(grid, field_bc)
     coeff = _to_modes(r, *Q) / (1.0 + c * lam)
-    return _from_modes(coeff, *Q)
+    u = _from_modes(coeff, *Q)
+    if wall and field_bc == FACE_DIRICHLET and g_lo is not None:
+        u[0] = g_lo
+    return u
 
 
 # ---------------------------------------------------------------------------
 # Finite-difference operators (Sec. 2.1: second-order central, ghost points)
 # ---------------------------------------------------------------------------
 
-def _ypad(f, field_bc):
-    """f with one ghost plane below and above along y."""
+def _ypad(f, field_bc, hy=1.0, g_lo=None, g_hi=None):
+    """f with one ghost plane below and above along y.
+
+    Wall data (Appendix B; 0 where None): NEUMANN g = df/dy at the wall,
+    ghost f_{-1} = f_0 - hy g_lo, f_ny = f_{ny-1} + hy g_hi;
+    CELL_DIRICHLET g = the wall value, ghost 2 g - f (the wall halfway);
+    FACE_DIRICHLET g = the wall-face values (face 0 is the stored plane 0,
+    face ny the ghost above)."""
     ny = f.shape[0]
+    zero = np.zeros(f.shape[1:])
+    gl = zero if g_lo is None else np.asarray(g_lo, dtype=np.float64)
+    gh = zero if g_hi is None else np.asarray(g_hi, dtype=np.float64)
     out = np.empty((ny + 2,) + f.shape[1:])
     out[1:-1] = f
     if field_bc == NEUMANN:
-        out[0], out[-1] = f[0], f[-1]
+        out[0], out[-1] = f[0] - hy * gl, f[-1] + hy * gh
     elif field_bc == CELL_DIRICHLET:
-        out[0], out[-1] = -f[0], -f[-1]
+        out[0], out[-1] = 2.0 * gl - f[0], 2.0 * gh - f[-1]
     elif field_bc == FACE_DIRICHLET:
-        out[1] = 0.0          # stored bottom wall face
+        out[1] = gl           # stored bottom wall face
         out[0] = 0.0          # never used by interior faces
-        out[-1] = 0.0         # top wall face j = ny
+        out[-1] = gh          # top wall face j = ny
     elif field_bc == PERIODIC:
         out[0], out[-1] = f[-1], f[0]
     else:
@@ -228,18 +257,19 @@ def _ypad(f, field_bc):
     return out
 
 
-def laplacian(f, grid, field_bc):
+def laplacian(f, grid, field_bc, g_lo=None, g_hi=None):
     """7-point L_h f: sum over axes of (f_{+1} - 2 f + f_{-1}) / h^2.
 
-    Periodic in x and z; y uses the ghost rule of field_bc.  For
-    FACE_DIRICHLET the wall plane of the result is 0.
+    Periodic in x and z; y uses the ghost rule of field_bc with the wall
+    data g_lo, g_hi (see _ypad; None is 0).  For FACE_DIRICHLET the wall
+    plane of f is the face value g_lo and that of the result is 0.
     """
     nx, ny, nz, hx, hy, hz = grid
     f = np.asarray(f, dtype=np.float64)
     if field_bc == FACE_DIRICHLET:
         f = f.copy()
-        f[0] = 0.0
-    g = _ypad(f, field_bc)
+        f[0] = 0.0 if g_lo is None else g_lo
+    g = _ypad(f, field_bc, hy, g_lo, g_hi)
     out = (np.roll(f, -1, 2) - 2.0 * f + np.roll(f, 1, 2)) / (hx * hx)
     out += (np.roll(f, -1, 1) - 2.0 * f + np.roll(f, 1, 1)) / (hz * hz)
     out += (g[2:] - 2.0 * f + g[:-2]) / (hy * hy)

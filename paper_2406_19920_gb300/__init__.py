@@ -82,6 +82,8 @@ _SIG = {
     "ibm_plan_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ibm_poisson_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_helmholtz_solve": (_I, [_P, _D, _I, _P, _P, _P, ctypes.POINTER(ibm_info)]),
+    "ibm_poisson_solve_bc": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
+    "ibm_helmholtz_solve_bc": (_I, [_P, _D, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_poisson_solve_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_D), _I, _P, _P, _P]),
     "ibm_interp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "ibm_spread": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
@@ -216,6 +218,22 @@ def ibm_helmholtz_solve(plan, c, field_bc, rhs, u, stream=None, info=False):
     inf = ibm_info() if info else None
     _check(lib().ibm_helmholtz_solve(plan, float(c), field_bc, _ptr(rhs), _ptr(u), _stream(stream),
                                      ctypes.byref(inf) if inf is not None else None))
+    return inf.as_dict() if inf is not None else None
+
+
+def ibm_poisson_solve_bc(plan, rhs, phi, q_lo=None, q_hi=None, stream=None, info=False):
+    """Poisson solve with dphi/dy = q_lo, q_hi ([nz][nx] planes or None) at the walls."""
+    inf = ibm_info() if info else None
+    _check(lib().ibm_poisson_solve_bc(plan, _ptr(rhs), _ptr(phi), _ptr(q_lo), _ptr(q_hi), _stream(stream),
+                                      ctypes.byref(inf) if inf is not None else None))
+    return inf.as_dict() if inf is not None else None
+
+
+def ibm_helmholtz_solve_bc(plan, c, field_bc, rhs, u, g_lo=None, g_hi=None, stream=None, info=False):
+    """Helmholtz solve with wall data g_lo, g_hi ([nz][nx] planes or None)."""
+    inf = ibm_info() if info else None
+    _check(lib().ibm_helmholtz_solve_bc(plan, float(c), field_bc, _ptr(rhs), _ptr(u), _ptr(g_lo), _ptr(g_hi),
+                                        _stream(stream), ctypes.byref(inf) if inf is not None else None))
     return inf.as_dict() if inf is not None else None
 
 

@@ -198,5 +198,9 @@ struct StencilCoef {
 template <typename T>
 cudaError_t launch_residual(int nx, int ny, int nz, const StencilCoef &c, const T *b, const T *x, T *r,
                             const double *boff, double *norms, cudaStream_t st);
+// dst plane jlo += clo g_lo, plane jhi += chi g_hi ([nz][nx] planes; NULL skips a side).
+template <typename T>
+cudaError_t launch_wall_rhs(int nx, int nz, T *dst, int jlo, int jhi, const T *glo, const T *ghi, double clo,
+                            double chi, cudaStream_t st);
 
 }  // namespace ibm

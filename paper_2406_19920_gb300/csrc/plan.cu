@@ -336,6 +336,41 @@ int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, 
                              static_cast<const float *>(addend), st, info);
 }
 
+// A solve with non-homogeneous wall data: the data's share of the operator
+// moves to the right-hand side (a copy in bsave), the homogeneous solve runs
+// on it, and a face field's wall plane gets its value.  Operator
+// A x = sigma x + tau L x (Poisson: L; Helmholtz: I - c L); the ghost rules
+// with wall data g (Appendix B) add B(g) to L x on the rows next to a wall:
+//   cell Neumann (g = dx/dy at the wall)      row 0: -g_lo / hy,    row ny-1: +g_hi / hy
+//   cell Dirichlet (g = the wall value)       row 0: +2 g_lo / hy^2, row ny-1: +2 g_hi / hy^2
+//   face Dirichlet (g = the wall face value)  row 1: +g_lo / hy^2,   row ny-1: +g_hi / hy^2
+// so the right-hand side becomes b - tau B(g).
+static int solve_bc(ibm_plan_s *p, int kind, double c, int field_bc, const void *rhs, void *out, const void *glo,
+                    const void *ghi, cudaStream_t st, ibm_info *info) {
+  const double hy = p->h[1];
+  const double tau = kind == 0 ? 1.0 : -c;
+  const int fb = kind == 0 ? IBM_FIELD_CELL_NEUMANN : field_bc;
+  double blo, bhi;
+  int jlo = 0, jhi = p->ny - 1;
+  if (fb == IBM_FIELD_CELL_NEUMANN) { blo = -1.0 / hy; bhi = 1.0 / hy; }
+  else if (fb == IBM_FIELD_CELL_DIRICHLET) { blo = bhi = 2.0 / (hy * hy); }
+  else { blo = bhi = 1.0 / (hy * hy); jlo = 1; }
+  IBM_CUDA_TRY(cudaMemcpyAsync(p->bsave, rhs, p->npts * p->esz, cudaMemcpyDeviceToDevice, st));
+  if (p->precision == IBM_FP64)
+    IBM_CUDA_TRY(launch_wall_rhs<double>(p->nx, p->nz, static_cast<double *>(p->bsave), jlo, jhi,
+                                         static_cast<const double *>(glo), static_cast<const double *>(ghi),
+                                         -tau * blo, -tau * bhi, st));
+  else
+    IBM_CUDA_TRY(launch_wall_rhs<float>(p->nx, p->nz, static_cast<float *>(p->bsave), jlo, jhi,
+                                        static_cast<const float *>(glo), static_cast<const float *>(ghi),
+                                        -tau * blo, -tau * bhi, st));
+  const int rc = plan_solve(p, kind, c, field_bc, p->bsave, out, nullptr, st, info);
+  if (rc) return rc;
+  if (fb == IBM_FIELD_FACE_DIRICHLET && glo)
+    IBM_CUDA_TRY(cudaMemcpyAsync(out, glo, (size_t)p->nx * p->nz * p->esz, cudaMemcpyDeviceToDevice, st));
+  return IBM_OK;
+}
+
 }  // namespace ibm
 
 using namespace ibm;
@@ -534,6 +569,29 @@ int ibm_helmholtz_solve(ibm_plan plan, double c, int field_bc, const void *rhs, 
   if (!aligned_to(rhs, 16) || !aligned_to(u, 16))
     return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve: field pointers must be 16-byte aligned");
   return plan_solve(plan, 1, c, field_bc, rhs, u, nullptr, (cudaStream_t)stream, info);
+}
+
+int ibm_poisson_solve_bc(ibm_plan plan, const void *rhs, void *phi, const void *q_lo, const void *q_hi, void *stream,
+                         ibm_info *info) {
+  if (!plan || !rhs || !phi) return set_error(IBM_ERR_ARG, "ibm_poisson_solve_bc: NULL argument");
+  if (plan->bc == IBM_BC_TRIPLY_PERIODIC)
+    return set_error(IBM_ERR_UNSUPPORTED, "ibm_poisson_solve_bc: the triply periodic branch has no walls");
+  if (!aligned_to(rhs, 16) || !aligned_to(phi, 16) || !aligned_to(q_lo, 16) || !aligned_to(q_hi, 16))
+    return set_error(IBM_ERR_ARG, "ibm_poisson_solve_bc: field pointers must be 16-byte aligned");
+  return solve_bc(plan, 0, 0.0, 0, rhs, phi, q_lo, q_hi, (cudaStream_t)stream, info);
+}
+
+int ibm_helmholtz_solve_bc(ibm_plan plan, double c, int field_bc, const void *rhs, void *u, const void *g_lo,
+                           const void *g_hi, void *stream, ibm_info *info) {
+  if (!plan || !rhs || !u) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve_bc: NULL argument");
+  if (!(c > 0.0) || !std::isfinite(c)) return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve_bc: c must be > 0");
+  if (plan->bc == IBM_BC_TRIPLY_PERIODIC)
+    return set_error(IBM_ERR_UNSUPPORTED, "ibm_helmholtz_solve_bc: the triply periodic branch has no walls");
+  if (field_bc < IBM_FIELD_CELL_NEUMANN || field_bc > IBM_FIELD_FACE_DIRICHLET)
+    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve_bc: field_bc %d", field_bc);
+  if (!aligned_to(rhs, 16) || !aligned_to(u, 16) || !aligned_to(g_lo, 16) || !aligned_to(g_hi, 16))
+    return set_error(IBM_ERR_ARG, "ibm_helmholtz_solve_bc: field pointers must be 16-byte aligned");
+  return solve_bc(plan, 1, c, field_bc, rhs, u, g_lo, g_hi, (cudaStream_t)stream, info);
 }
 
 }  // extern "C"

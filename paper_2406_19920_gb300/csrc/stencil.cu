@@ -255,6 +255,34 @@ cudaError_t launch_residual<float>(int nx, int ny, int nz, const StencilCoef &c,
 #undef IBM_RES_BC
 }
 
+// Wall data's share of the 7-point operator, moved to the right-hand side
+// (Appendix B: the first and last rows of each pencil carry the boundary
+// values; BC2.2 forms the same terms from the FFT of the ghost planes).
+// dst[jlo] += clo g_lo, dst[jhi] += chi g_hi over one x-z plane each (either
+// g may be NULL).  One thread per plane point.
+template <typename T>
+__global__ void __launch_bounds__(256)
+k_wall_rhs(int npl, T *dst, size_t plane, int jlo, int jhi, const T *glo, const T *ghi, T clo, T chi) {
+  pdl_wait();
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= npl) return;
+  if (glo) dst[(size_t)jlo * plane + i] += clo * glo[i];
+  if (ghi) dst[(size_t)jhi * plane + i] += chi * ghi[i];
+}
+
+template <typename T>
+cudaError_t launch_wall_rhs(int nx, int nz, T *dst, int jlo, int jhi, const T *glo, const T *ghi, double clo,
+                            double chi, cudaStream_t st) {
+  const int npl = nx * nz;
+  IBM_KTRY(launch_pdl(k_wall_rhs<T>, ceil_div(npl, 256), 256, 0, st, npl, dst, (size_t)npl, jlo, jhi, glo, ghi,
+                      (T)clo, (T)chi));
+  return cudaGetLastError();
+}
+template cudaError_t launch_wall_rhs<float>(int, int, float *, int, int, const float *, const float *, double, double,
+                                            cudaStream_t);
+template cudaError_t launch_wall_rhs<double>(int, int, double *, int, int, const double *, const double *, double,
+                                             double, cudaStream_t);
+
 template <>
 cudaError_t launch_residual<double>(int nx, int ny, int nz, const StencilCoef &c, const double *b, const double *x,
                                     double *r, const double *boff, double *norms, cudaStream_t st) {

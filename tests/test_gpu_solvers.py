@@ -281,6 +281,64 @@ def test_fp32_fields_must_be_16_byte_aligned():
         ibm.ibm_plan_destroy(plan)
 
 
+@pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
+@pytest.mark.parametrize("shape", [(32, 24, 16), (48, 17, 96)])
+def test_solves_with_wall_data_match_oracle(prec, shape):
+    """Inhomogeneous wall data (Appendix B's boundary right-hand sides, BC2.2):
+    Poisson with dphi/dy on both walls and Helmholtz with wall values / wall
+    slopes for every field kind, against the oracle; rhs left untouched."""
+    nx, ny, nz = shape
+    g = grid(nx, ny, nz)
+    dt = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+    npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
+    tol = TOL_FP64 if prec == ibm.IBM_FP64 else TOL_FP32
+    rng = np.random.default_rng(nx + ny)
+    b = synth.white_noise(nx, ny, nz, workload=17, stream=0).astype(npdt).astype(np.float64)
+    lo, hi = (rng.standard_normal((nz, nx)).astype(npdt).astype(np.float64) for _ in range(2))
+    plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, 1)
+    try:
+        rhs, glo, ghi = dev(b, dt), dev(lo, dt), dev(hi, dt)
+        keep = rhs.clone()
+        phi = torch.empty_like(rhs)
+        info = ibm.ibm_poisson_solve_bc(plan, rhs, phi, glo, ghi, info=True)
+        ref, removed = O.poisson_solve(b, g, q_lo=lo, q_hi=hi)
+        assert rel_l2(host(phi), ref) <= tol
+        assert abs(info["removed_mean"] - removed) <= 1e-5 * max(1.0, abs(removed))
+        for bc in (ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_CELL_DIRICHLET, ibm.IBM_FIELD_FACE_DIRICHLET):
+            u = torch.empty_like(rhs)
+            ibm.ibm_helmholtz_solve_bc(plan, 0.02, bc, rhs, u, glo, ghi)
+            torch.cuda.synchronize()
+            href = O.helmholtz_solve(b, g, 0.02, bc, lo, hi)
+            assert rel_l2(host(u), href) <= tol, bc
+            # one wall only
+            ibm.ibm_helmholtz_solve_bc(plan, 0.02, bc, rhs, u, None, ghi)
+            torch.cuda.synchronize()
+            assert rel_l2(host(u), O.helmholtz_solve(b, g, 0.02, bc, None, hi)) <= tol, bc
+        assert torch.equal(rhs, keep)
+        # in place
+        ibm.ibm_helmholtz_solve_bc(plan, 0.02, ibm.IBM_FIELD_CELL_DIRICHLET, rhs, rhs, glo, ghi)
+        torch.cuda.synchronize()
+        assert rel_l2(host(rhs), O.helmholtz_solve(b, g, 0.02, ibm.IBM_FIELD_CELL_DIRICHLET, lo, hi)) <= tol
+        ibm.ibm_plan_check(plan)
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
+def test_wall_data_rejected_without_walls():
+    g = grid(16, 16, 16)
+    plan = ibm.ibm_plan_create(16, 16, 16, g[3:], ibm.IBM_FP64, 0, bc=ibm.IBM_BC_TRIPLY_PERIODIC)
+    try:
+        x = torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda")
+        with pytest.raises(ibm.IbmError) as e:
+            ibm.ibm_poisson_solve_bc(plan, x, x, x[0], x[0])
+        assert e.value.code == ibm.IBM_ERR_UNSUPPORTED
+        with pytest.raises(ibm.IbmError) as e:
+            ibm.ibm_helmholtz_solve_bc(plan, 0.1, ibm.IBM_FIELD_CELL_NEUMANN, x, x, x[0], x[0])
+        assert e.value.code == ibm.IBM_ERR_UNSUPPORTED
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
 def test_invalid_arguments_rejected_before_launch():
     g = grid(32, 32, 32)
     with pytest.raises(ibm.IbmError) as e:

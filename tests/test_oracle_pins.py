@@ -489,3 +489,68 @@ def test_rk_stage_projection_and_forcing_invariants():
     assert np.abs(d).max() <= 1e-11 * max(1.0, np.abs(d0).max())
     # Eq. 2c: F = (U^d - U^e)/dt
     assert np.allclose(info["F"], (np.array([0.1, 0, 0])[None, :] - info["Ue"]) / 1e-3)
+
+
+# ---------------------------------------------------------------------------
+# Inhomogeneous wall data (Appendix B: boundary values on the first and last
+# pencil rows' right-hand sides)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("bc", [O.NEUMANN, O.CELL_DIRICHLET, O.FACE_DIRICHLET])
+def test_wall_data_ghosts_exact_on_linear_fields(bc):
+    """The ghost rules with wall data reproduce a field linear in y exactly:
+    a Neumann ghost from the slope, a cell-Dirichlet ghost by reflection
+    through the wall value, a face-Dirichlet wall face at its value.  The
+    7-point Laplacian of such a field vanishes on every row, wall rows
+    included."""
+    grid = _grid(8, 10, 6, Ly=1.7)
+    nx, ny, nz, hx, hy, hz = grid
+    a, bslope = 0.7, -2.3
+    ones = np.ones((nz, nx))
+    if bc == O.FACE_DIRICHLET:
+        y = np.arange(ny) * hy                 # faces j = 0 .. ny-1
+        g_lo, g_hi = a * ones, (a + bslope * ny * hy) * ones
+    else:
+        y = (np.arange(ny) + 0.5) * hy         # cell centres
+        if bc == O.NEUMANN:
+            g_lo = g_hi = bslope * ones
+        else:
+            g_lo, g_hi = a * ones, (a + bslope * ny * hy) * ones
+    f = (a + bslope * y)[:, None, None] * np.ones((ny, nz, nx))
+    L = O.laplacian(f, grid, bc, g_lo, g_hi)
+    assert np.max(np.abs(L)) <= 1e-9 / hy ** 2
+    # and the homogeneous rule does not (the data matter)
+    assert np.max(np.abs(O.laplacian(f, grid, bc))) > 1e-3
+
+
+@pytest.mark.parametrize("bc", [O.NEUMANN, O.CELL_DIRICHLET, O.FACE_DIRICHLET])
+def test_helmholtz_with_wall_data_manufactured(bc):
+    """(I - c L_h) u = r with the ghosts of the wall data: the solve with that
+    data returns u (face fields: plane 0 is the wall value)."""
+    grid = _grid(8, 12, 6, Ly=1.3)
+    nx, ny, nz = grid[:3]
+    rng = np.random.default_rng(61 + bc)
+    u = rng.standard_normal((ny, nz, nx))
+    g_lo, g_hi = rng.standard_normal((2, nz, nx))
+    if bc == O.FACE_DIRICHLET:
+        u[0] = g_lo
+    c = 0.03
+    r = u - c * O.laplacian(u, grid, bc, g_lo, g_hi)
+    got = O.helmholtz_solve(r, grid, c, bc, g_lo, g_hi)
+    assert np.max(np.abs(got - u)) <= 1e-11 * np.max(np.abs(u))
+
+
+def test_poisson_with_flux_manufactured():
+    """L_h phi = b with the Neumann ghosts of dphi/dy = q at the walls: the
+    solve returns phi up to its mean, and the data-corrected right-hand side
+    is compatible (discrete divergence theorem: nothing to remove)."""
+    grid = _grid(8, 10, 6, Ly=1.1)
+    nx, ny, nz = grid[:3]
+    rng = np.random.default_rng(7)
+    phi = rng.standard_normal((ny, nz, nx))
+    phi -= phi.mean()
+    q_lo, q_hi = rng.standard_normal((2, nz, nx))
+    b = O.laplacian(phi, grid, O.NEUMANN, q_lo, q_hi)
+    got, removed = O.poisson_solve(b, grid, q_lo=q_lo, q_hi=q_hi)
+    assert abs(removed) <= 1e-12 * np.max(np.abs(b))
+    assert np.max(np.abs(got - phi)) <= 1e-11 * np.max(np.abs(phi))
