@@ -262,6 +262,23 @@ def ncu_summary(csv_path, steps):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def job_ms(ms, dist=None, device="cpu"):
+    """The job's time: the maximum of the ranks' times (every rank runs the
+    same steps between the same barriers)."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([float(ms)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world_size, ms):
+    """Whole-job rate: the units all ranks processed over the job's time
+    (weak scaling: each rank advances its own replica)."""
+    return units_per_rank * world_size / (ms * 1e-3)
+
+
 def run_gpu(args):
     import torch
     import paper_2406_19920_gb300 as ibm
@@ -338,13 +355,9 @@ def run_gpu(args):
         barrier()
         t_host1 = time.time()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
-    total_ms = ev[0].elapsed_time(ev[-1])
-    if dist:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = job_ms(ev[0].elapsed_time(ev[-1]), dist, "cuda")
     pts = NX * NY * NZ
-    value = pts * args.steps * ws / (total_ms * 1e-3)
+    value = job_throughput(pts * args.steps, ws, total_ms)
 
     # ---- identical pass with CUDA events around every kernel (roofline) ----
     ibm.ibm_plan_profile(plan, True)
