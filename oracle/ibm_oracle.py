@@ -278,10 +278,13 @@ def laplacian(f, grid, field_bc, g_lo=None, g_hi=None):
     return out
 
 
-def divergence(u, v, w, grid):
-    """Cell-centred D(u, v, w) (E2, Sec. 2.3.1); v = 0 on both wall faces."""
+def divergence(u, v, w, grid, v_lo=0.0, v_hi=None):
+    """Cell-centred D(u, v, w) (E2, Sec. 2.3.1).  The wall faces carry v_lo
+    (bottom, a scalar) and v_hi (top, a [nz][nx] plane or None for 0):
+    0 on both for no-slip walls."""
     nx, ny, nz, hx, hy, hz = grid
-    vv = np.concatenate([np.zeros((1, nz, nx)), v[1:], np.zeros((1, nz, nx))])
+    top = np.zeros((1, nz, nx)) if v_hi is None else np.asarray(v_hi, dtype=np.float64)[None]
+    vv = np.concatenate([np.full((1, nz, nx), float(v_lo)), v[1:], top])
     return ((np.roll(u, -1, 2) - u) / hx
             + (vv[1:] - vv[:-1]) / hy
             + (np.roll(w, -1, 1) - w) / hz)
@@ -297,17 +300,23 @@ def gradient(phi, grid):
     return gu, gv, gw
 
 
-def advection(u, v, w, grid):
+def advection(u, v, w, grid, wall=None):
     """Divergence-form MAC advection N = div(u u) on the staggered grid.
 
     The paper discretises (u . grad) u with second-order central differences
     (Sec. 2.1) without printing the staggered formula; this is the standard
     conservative form with two-point averages, which equals the advective
     form to O(h^2) for a discretely divergence-free field and conserves
-    momentum and kinetic energy.  Walls carry v = 0, so fluxes through them
-    vanish.  Returns (Nu, Nv, Nw) on the u, v, w positions.
+    momentum and kinetic energy.  No-slip walls carry v = 0, so fluxes
+    through them vanish.  wall = (v_lo, u_hi, v_hi, w_hi) gives an inflow
+    face (v = v_lo, u = w = 0) at y = 0 and outlet values at y = Ly (u, w at
+    the wall, v on the face): the wall values of u and w enter the y-fluxes
+    through their ghosts 2 g - u.  Returns (Nu, Nv, Nw) on the u, v, w
+    positions.
     """
     nx, ny, nz, hx, hy, hz = grid
+    if wall is not None:
+        return _advection_wall(u, v, w, grid, wall)
     xm = lambda f: np.roll(f, 1, 2)     # f[..., i-1]
     xp = lambda f: np.roll(f, -1, 2)    # f[..., i+1]
     zm = lambda f: np.roll(f, 1, 1)
@@ -364,6 +373,61 @@ def advection(u, v, w, grid):
     fy_w = v_ez2 * w_ey2
     ty_w = (fy_w[1:] - fy_w[:-1]) / hy
     Nw = tx_w + ty_w + tz_w
+    return Nu, Nv, Nw
+
+
+def _advection_wall(u, v, w, grid, wall):
+    """advection() with the inflow / outlet wall data (see there)."""
+    nx, ny, nz, hx, hy, hz = grid
+    v_lo, u_hi, v_hi, w_hi = wall
+    xm = lambda f: np.roll(f, 1, 2)
+    xp = lambda f: np.roll(f, -1, 2)
+    zm = lambda f: np.roll(f, 1, 1)
+    zp = lambda f: np.roll(f, -1, 1)
+    vf = np.concatenate([np.full((1, nz, nx), float(v_lo)), v[1:], np.asarray(v_hi, dtype=np.float64)[None]])
+    # u, w with their ghost planes (wall values 0 at the inlet, u_hi / w_hi at the outlet)
+    u_pad = np.concatenate([-u[:1], u, 2.0 * np.asarray(u_hi)[None] - u[-1:]])
+    w_pad = np.concatenate([-w[:1], w, 2.0 * np.asarray(w_hi)[None] - w[-1:]])
+
+    uc = 0.5 * (u + xp(u))
+    tx = (uc * uc - xm(uc) * xm(uc)) / hx
+    v_e = 0.5 * (vf + xm(vf))
+    u_e = 0.5 * (u_pad[:-1] + u_pad[1:])             # u at the y-faces 0 .. ny (walls: the wall value)
+    fy = v_e * u_e
+    ty = (fy[1:] - fy[:-1]) / hy
+    w_e = 0.5 * (w + xm(w))
+    u_ez = 0.5 * (u + zm(u))
+    fz = w_e * u_ez
+    tz = (zp(fz) - fz) / hz
+    Nu = tx + ty + tz
+
+    vc = 0.5 * (vf[:-1] + vf[1:])
+    ty_v = np.zeros((ny, nz, nx))
+    ty_v[1:] = (vc[1:] * vc[1:] - vc[:-1] * vc[:-1]) / hy
+    u_ey = np.zeros((ny, nz, nx))
+    u_ey[1:] = 0.5 * (u[1:] + u[:-1])
+    v_ex = 0.5 * (vf[:-1] + xm(vf[:-1]))
+    fx = u_ey * v_ex
+    tx_v = (xp(fx) - fx) / hx
+    w_ey = np.zeros((ny, nz, nx))
+    w_ey[1:] = 0.5 * (w[1:] + w[:-1])
+    v_ez = 0.5 * (vf[:-1] + zm(vf[:-1]))
+    fz_v = w_ey * v_ez
+    tz_v = (zp(fz_v) - fz_v) / hz
+    Nv = tx_v + ty_v + tz_v
+    Nv[0] = 0.0
+
+    wc = 0.5 * (w + zp(w))
+    tz_w = (wc * wc - zm(wc) * zm(wc)) / hz
+    u_ez2 = 0.5 * (u + zm(u))
+    w_ex = 0.5 * (w + xm(w))
+    fx_w = u_ez2 * w_ex
+    tx_w = (xp(fx_w) - fx_w) / hx
+    v_ez2 = 0.5 * (vf + zm(vf))
+    w_e2 = 0.5 * (w_pad[:-1] + w_pad[1:])
+    fy_w = v_ez2 * w_e2
+    ty_w = (fy_w[1:] - fy_w[:-1]) / hy
+    Nw = tz_w + tx_w + ty_w
     return Nu, Nv, Nw
 
 
@@ -506,7 +570,26 @@ def marker_motion(X0, t, kind, params):
     return X, Ud
 
 
-def rk_stage(state, markers, stage, dt, nu, grid, kernel=ROMA3):
+def outflow_update(inout, u, v, w, grid, step):
+    """The outlet condition d phi/dt + C d phi/dy = 0 (Sec. 3, inflow-outflow
+    configuration) advanced over one stage step (alpha + beta) dt by
+    first-order upwinding from the last interior value (the distance to it
+    is hy/2 for u, w at the wall, hy for v's outlet face).  The paper leaves
+    the discretisation to a reference; this is the reading used here.  The
+    outlet v is then shifted by a constant so that the outflow through the
+    top face equals the inflow through the bottom one (global mass balance,
+    which keeps the Poisson right-hand side compatible).  Returns new
+    (u_out, v_out, w_out)."""
+    nx, ny, nz, hx, hy, hz = grid
+    C = inout["c_out"]
+    uo = inout["u_out"] - step * C * (inout["u_out"] - u[-1]) / (0.5 * hy)
+    wo = inout["w_out"] - step * C * (inout["w_out"] - w[-1]) / (0.5 * hy)
+    vo = inout["v_out"] - step * C * (inout["v_out"] - v[-1]) / hy
+    vo = vo + (inout["v_in"] - vo.mean())
+    return uo, vo, wo
+
+
+def rk_stage(state, markers, stage, dt, nu, grid, kernel=ROMA3, inout=None):
     """One stage n = stage (1, 2, 3) of the RK system, Eq. 2a-2h.
 
     state: dict with u, v, w, p (ny, nz, nx) and N_prev = (Nu, Nv, Nw), the
@@ -514,6 +597,15 @@ def rk_stage(state, markers, stage, dt, nu, grid, kernel=ROMA3):
            the time at the start of this stage.
     markers: dict with X0 (N,3), dV (N,), motion kind and params; the stage
            forces with X, U^d evaluated at the stage start time.
+    inout: None for no-slip walls; else the inflow-outflow configuration
+           (Sec. 3): dict with v_in (the wall-normal inflow through y = 0,
+           where u = w = 0), c_out (outlet advection speed) and the outlet
+           values u_out, v_out, w_out ([nz][nx]; u, w at the wall y = Ly, v
+           on its face).  The outlet values are advanced first
+           (outflow_update) and, with the inflow, are the wall data of the
+           whole stage: the explicit terms, the Helmholtz solves (Appendix B
+           boundary rows), the divergence and the projection all see them.
+           The new values are returned in new_state["inout"].
     Re^{-1} = nu.  Returns (new_state, info) where info holds U^e, F, phi.
     """
     n = stage - 1
@@ -521,17 +613,28 @@ def rk_stage(state, markers, stage, dt, nu, grid, kernel=ROMA3):
     ab = a + b
     u, v, w, p = state["u"], state["v"], state["w"], state["p"]
     bcs = (CELL_DIRICHLET, FACE_DIRICHLET, CELL_DIRICHLET)
+    if inout is None:
+        glo, ghi, v_lo, v_hi, wall = (None,) * 3, (None,) * 3, 0.0, None, None
+    else:
+        nxg, nyg, nzg = grid[:3]
+        uo, vo, wo = outflow_update(inout, u, v, w, grid, ab * dt)
+        zero = np.zeros((nzg, nxg))
+        glo = (zero, np.full((nzg, nxg), float(inout["v_in"])), zero)
+        ghi = (uo, vo, wo)
+        v_lo, v_hi, wall = inout["v_in"], vo, (inout["v_in"], uo, vo, wo)
+        v = v.copy()
+        v[0] = inout["v_in"]
     vel = (u, v, w)
-    N = advection(u, v, w, grid)
+    N = advection(u, v, w, grid, wall)
     Np = state["N_prev"]
     G = gradient(p, grid)
     # Eq. 2a: explicit estimate
     ue = []
     for c in range(3):
-        e = vel[c] + dt * (ab * nu * laplacian(vel[c], grid, bcs[c])
+        e = vel[c] + dt * (ab * nu * laplacian(vel[c], grid, bcs[c], glo[c], ghi[c])
                            - ab * G[c] - g * N[c] - z * Np[c])
         if c == 1:
-            e[0] = 0.0
+            e[0] = v_lo
         ue.append(e)
     # Eq. 2b-2d: interpolation, Lagrangian force, spreading
     X, Ud = marker_motion(markers["X0"], state["t"], markers["kind"], markers["params"])
@@ -542,18 +645,23 @@ def rk_stage(state, markers, stage, dt, nu, grid, kernel=ROMA3):
     cH = b * dt * nu
     us = []
     for c in range(3):
-        rhs = ue[c] - cH * laplacian(vel[c], grid, bcs[c]) + dt * f[c]
-        us.append(helmholtz_solve(rhs, grid, cH, bcs[c]))
+        rhs = ue[c] - cH * laplacian(vel[c], grid, bcs[c], glo[c], ghi[c]) + dt * f[c]
+        if inout is None:
+            us.append(helmholtz_solve(rhs, grid, cH, bcs[c]))
+        else:
+            us.append(helmholtz_solve(rhs, grid, cH, bcs[c], glo[c], ghi[c]))
     # Eq. 2f: Poisson for the pseudo-pressure
-    rhs_phi = divergence(*us, grid) / (ab * dt)
+    rhs_phi = divergence(*us, grid, v_lo, v_hi) / (ab * dt)
     phi, _ = poisson_solve(rhs_phi, grid)
     # Eq. 2g: projection
     Gphi = gradient(phi, grid)
     un = [us[c] - ab * dt * Gphi[c] for c in range(3)]
-    un[1][0] = 0.0
+    un[1][0] = v_lo
     # Eq. 2h: pressure update
     pn = p + phi - cH * laplacian(phi, grid, NEUMANN)
     new = dict(u=un[0], v=un[1], w=un[2], p=pn, N_prev=N, t=state["t"] + ab * dt)
+    if inout is not None:
+        new["inout"] = dict(inout, u_out=uo, v_out=vo, w_out=wo)
     return new, dict(Ue=Ue, F=F, phi=phi, rhs_phi=rhs_phi, ustar=us)
 
 

@@ -554,3 +554,83 @@ def test_poisson_with_flux_manufactured():
     got, removed = O.poisson_solve(b, grid, q_lo=q_lo, q_hi=q_hi)
     assert abs(removed) <= 1e-12 * np.max(np.abs(b))
     assert np.max(np.abs(got - phi)) <= 1e-11 * np.max(np.abs(phi))
+
+
+# ---------------------------------------------------------------------------
+# Inflow-outflow RK stage (Sec. 3's inflow-outflow configuration)
+# ---------------------------------------------------------------------------
+
+def _io_state(g, wl):
+    nx, ny, nz = g[:3]
+    u, v, w = synth.div_free_velocity(g, workload=wl, kmax=4)
+    r = np.random.default_rng(wl)
+    p = 0.1 * r.standard_normal((ny, nz, nx))
+    Np = [0.5 * r.standard_normal((ny, nz, nx)) for _ in range(3)]
+    Np[1][0] = 0.0
+    return dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
+
+
+_NO_MARKERS = dict(X0=np.zeros((0, 3)), dV=np.zeros(0), kind=O.MOTION_STATIC, params=(0, 0, 0))
+
+
+def test_advection_with_zero_wall_data_is_the_no_slip_form():
+    g = _grid(16, 12, 8, Lx=1.0, Ly=1.5, Lz=0.8)
+    nx, ny, nz = g[:3]
+    u, v, w = synth.div_free_velocity(g, workload=5, kmax=5)
+    z = np.zeros((nz, nx))
+    ref = O.advection(u, v, w, g)
+    got = O.advection(u, v, w, g, (0.0, z, z, z))
+    for a, b in zip(got, ref):
+        assert np.max(np.abs(a - b)) <= 1e-13 * np.max(np.abs(b))
+
+
+def test_inout_stage_with_zero_data_is_the_no_slip_stage():
+    """No inflow, a resting outlet (C = 0, zero outlet values): the
+    inflow-outflow stage is the no-slip stage."""
+    g = _grid(16, 12, 8, Lx=2 * math.pi, Ly=2.0, Lz=2 * math.pi)
+    nx, ny, nz = g[:3]
+    st = _io_state(g, 3)
+    z = np.zeros((nz, nx))
+    io = dict(v_in=0.0, c_out=0.0, u_out=z, v_out=z, w_out=z)
+    ref, _ = O.rk_stage(st, _NO_MARKERS, 2, 1e-3, 1e-2, g)
+    got, _ = O.rk_stage(st, _NO_MARKERS, 2, 1e-3, 1e-2, g, inout=io)
+    for k in ("u", "v", "w", "p"):
+        assert np.max(np.abs(got[k] - ref[k])) <= 1e-12 * np.max(np.abs(ref[k])), k
+
+
+def test_inout_stage_keeps_uniform_through_flow():
+    """v = U everywhere (inlet, interior faces and outlet), u = w = 0, uniform
+    pressure, C = U: a steady state of the stage, kept to rounding."""
+    g = _grid(12, 10, 8, Lx=1.3, Ly=1.7, Lz=0.9)
+    nx, ny, nz = g[:3]
+    U = 0.8
+    zf = np.zeros((ny, nz, nx))
+    st = dict(u=zf.copy(), v=np.full((ny, nz, nx), U), w=zf.copy(), p=np.full((ny, nz, nx), 0.3),
+              N_prev=(zf, zf, zf), t=0.0)
+    z = np.zeros((nz, nx))
+    io = dict(v_in=U, c_out=U, u_out=z, v_out=np.full((nz, nx), U), w_out=z)
+    for stage in (1, 2, 3):
+        new, info = O.rk_stage(st, _NO_MARKERS, stage, 2e-3, 1e-2, g, inout=io)
+        assert np.max(np.abs(new["u"])) <= 1e-12 and np.max(np.abs(new["w"])) <= 1e-12
+        assert np.max(np.abs(new["v"] - U)) <= 1e-12
+        assert np.max(np.abs(new["p"] - 0.3)) <= 1e-12
+        assert np.max(np.abs(new["inout"]["v_out"] - U)) <= 1e-12
+        st, io = new, new["inout"]
+
+
+def test_inout_stage_projects_onto_the_through_flow():
+    """With inflow and an advected outlet the projected field is discretely
+    divergence-free with the stage's wall faces, and the outlet carries out
+    what the inlet brings in."""
+    g = _grid(16, 12, 8, Lx=2 * math.pi, Ly=2.0, Lz=2 * math.pi)
+    nx, ny, nz = g[:3]
+    st = _io_state(g, 4)
+    r = np.random.default_rng(4)
+    io = dict(v_in=0.5, c_out=0.5, u_out=0.1 * r.standard_normal((nz, nx)),
+              v_out=0.5 + 0.1 * r.standard_normal((nz, nx)), w_out=0.1 * r.standard_normal((nz, nx)))
+    new, _ = O.rk_stage(st, _NO_MARKERS, 1, 1e-3, 1e-2, g, inout=io)
+    vo = new["inout"]["v_out"]
+    assert abs(vo.mean() - 0.5) <= 1e-14
+    d = O.divergence(new["u"], new["v"], new["w"], g, 0.5, vo)
+    assert np.max(np.abs(d)) <= 1e-10 * np.max(np.abs(new["v"])) / g[4]
+    assert np.all(new["v"][0] == 0.5)
