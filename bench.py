@@ -415,6 +415,7 @@ def run_gpu(args):
     batched = batched_compare(ibm, torch) if not args.no_extras else None
     serving = serve_sample(ibm) if not args.no_extras else None
     plate = large_plate(ibm, torch) if not args.no_extras else None
+    plate_inflow = large_plate(ibm, torch, v_in=1.0) if not args.no_extras else None
 
     # ---- roofline of the dominant kernel kind (all its launches of a step) ----
     dom = max(prof, key=lambda k: prof[k][0])
@@ -464,6 +465,7 @@ def run_gpu(args):
         "batched": batched,
         "serving": serving,
         "large_plate": plate,
+        "large_plate_inflow": plate_inflow,
         "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")},
         "clocks": clocks,
         "timed_region_s": t_host1 - t_host0,
@@ -639,13 +641,16 @@ def batched_compare(ibm, torch):
             "speedup": (256e3 / ms) / (64e3 / ms64), "max_rel_l2_vs_fp64": err, "create_and_tune_s": create_s}
 
 
-def large_plate(ibm, torch, stages=48):
+def large_plate(ibm, torch, stages=48, v_in=None):
     """Bio-inspired external-flow workload: 384x256x256 on a uniform h = 2 pi/384
     grid (periodic x, z; walls in y), FP32 + 1 refinement, a flat plate of
     100,000 markers (250 x 400 lattice, chord 1, span 2) heaving with amplitude
     0.5 and period 1 about y = Ly/2.  Runs `stages` consecutive RK stages
     (16 full steps) and reports ms per stage, per-kernel time, the refined
-    Poisson solve's relative residual and max |D u| after projection."""
+    Poisson solve's relative residual and max |D u| after projection.
+    v_in: no-slip walls if None; else the inflow-outflow walls (inflow v_in
+    through y = 0, an outlet advected at speed v_in) with the uniform
+    through-flow v_in added to the initial field."""
     from paper_2406_19920_gb300 import synth
     nx, ny, nz = 384, 256, 256
     h = 2 * math.pi / 384
@@ -655,8 +660,18 @@ def large_plate(ibm, torch, stages=48):
     X0, dV = synth.flat_plate(250, 400, 1.0, 2.0, (nx * h / 2, Ly / 2, nz * h / 2), h)
     f32 = torch.float32
     dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", f32)
+    if v_in is not None:
+        v = v + v_in
     fields = [dev(u), dev(v), dev(w), torch.zeros((ny, nz, nx), dtype=f32, device="cuda")]
     Ns = [torch.zeros((ny, nz, nx), dtype=f32, device="cuda") for _ in range(3)]
+    outlet = [torch.zeros((nz, nx), dtype=f32, device="cuda") for _ in range(3)]
+    outlet[1] += 0.0 if v_in is None else v_in
+    io = ibm.ibm_inout(0.0 if v_in is None else v_in, 0.0 if v_in is None else v_in,
+                       *[t.data_ptr() for t in outlet])
+    if v_in is None:
+        substep = lambda s, info=False: ibm.ibm_substep(plan, st, s, DT, NU, mk, info=info)
+    else:
+        substep = lambda s, info=False: ibm.ibm_substep_inout(plan, st, io, s, DT, NU, mk, info=info)
     plan = ibm.ibm_plan_create(nx, ny, nz, (h, h, h), ibm.IBM_FP32_REFINED, 1)
     st = ibm.ibm_state(*[t.data_ptr() for t in fields + Ns], 0.0)
     X0d, dVd = dev(X0), dev(dV)
@@ -664,26 +679,27 @@ def large_plate(ibm, torch, stages=48):
     Ud, F = torch.empty_like(X), torch.empty_like(X)
     mk = ibm.ibm_markers(X0.shape[0], X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
                          ibm.IBM_MOTION_HEAVE, (ctypes.c_double * 4)(0.5, 1.0, 0.0, 0.0))
-    ibm.ibm_substep(plan, st, 1, DT, NU, mk)
+    substep(1)
     torch.cuda.synchronize()
     ibm.ibm_plan_profile(plan, True)
     ibm.ibm_plan_profile_read(plan)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record()
     for i in range(stages):
-        ibm.ibm_substep(plan, st, (i + 1) % 3 + 1, DT, NU, mk)
+        substep((i + 1) % 3 + 1)
     e1.record()
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1) / stages
     prof = ibm.ibm_plan_profile_read(plan)
     ibm.ibm_plan_profile(plan, False)
-    info = ibm.ibm_substep(plan, st, 1, DT, NU, mk, info=True)
+    info = substep(1, info=True)
     # relative residual of the refined Poisson solve on the stage's own divergence field
     b = torch.randn((ny, nz, nx), device="cuda")
     phi = torch.empty_like(b)
     pinfo = ibm.ibm_poisson_solve(plan, b, phi, info=True)
     ibm.ibm_plan_destroy(plan)
-    return {"grid": [nx, ny, nz], "markers": int(X0.shape[0]), "stages": stages, "ms_per_stage": ms,
+    walls = "no-slip" if v_in is None else "inflow v_in = %g, advected outlet" % v_in
+    return {"grid": [nx, ny, nz], "walls": walls, "markers": int(X0.shape[0]), "stages": stages, "ms_per_stage": ms,
             "grid_pts_per_s": nx * ny * nz / (ms * 1e-3),
             "kernel_ms_per_stage": {k: v[0] / stages for k, v in prof.items()},
             "div_max_after_projection": info["div_max"], "div_max_before": info["div_before"],

@@ -167,7 +167,8 @@ enum {
   IBM_K_SPREAD = 7,    /* L1 spreading                                    */
   IBM_K_DIVERGENCE = 8,/* E2 divergence                                   */
   IBM_K_PROJECT = 9,   /* E3 projection + pressure update                 */
-  IBM_K_COUNT = 10
+  IBM_K_OUTFLOW = 10,  /* outlet update + mass balance (inflow-outflow)   */
+  IBM_K_COUNT = 11
 };
 int ibm_plan_profile(ibm_plan plan, int enable);
 int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launches);
@@ -270,6 +271,34 @@ typedef struct {
  * Uses the plan's workspace; the plan precision sets the field type. */
 int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu,
                 ibm_markers *mk, void *stream, ibm_info *info);
+
+/* Wall data of the inflow-outflow configuration (Sec. 3): a uniform inflow
+ * v = v_in through the y = 0 face (u = w = 0 on that wall) and an outlet at
+ * y = Ly advected with d phi/dt + c_out d phi/dy = 0.  u_out, w_out hold u
+ * and w on the outlet wall, v_out the wall-normal velocity on the outlet
+ * face: device planes [nz][nx] of the plan precision, owned by the caller,
+ * updated in place every stage. */
+typedef struct {
+  double v_in;   /* inflow speed (finite)                                   */
+  double c_out;  /* outlet advection speed (finite, >= 0)                   */
+  void *u_out, *v_out, *w_out;
+} ibm_inout;
+
+/* One RK stage as ibm_substep, with the inflow-outflow walls of ibm_inout
+ * in place of the no-slip walls.  The stage first advances the outlet
+ * values over its step (alpha_n + beta_n) dt by first-order upwinding from
+ * the last interior plane and shifts v_out by a constant so that its mean
+ * equals v_in (outflow = inflow; the Poisson right-hand side keeps zero
+ * mean), and stores v = v_in on plane 0 of v.  Those values are the wall
+ * data of the whole stage: the explicit terms (Laplacian ghosts 2 g - u,
+ * advective fluxes through the walls), the divergence and the projection
+ * see them; the Helmholtz increment solves need none (the data are the
+ * same at both ends of the increment).  The paper gives the outlet's
+ * discretisation only by reference; the upwind form is the reading used
+ * here.  Returns IBM_ERR_ARG for NULL io or planes, a non-finite v_in or a
+ * negative or non-finite c_out; otherwise as ibm_substep. */
+int ibm_substep_inout(ibm_plan plan, ibm_state *st, const ibm_inout *io, int rk_stage, double dt,
+                      double nu, ibm_markers *mk, void *stream, ibm_info *info);
 
 /* ---------------------------------------------------------------------------
  * Batches: many independent grids solved in one CUDA-graph launch

@@ -53,6 +53,11 @@ class ibm_markers(ctypes.Structure):
                 ("params", ctypes.c_double * 4)]
 
 
+class ibm_inout(ctypes.Structure):
+    _fields_ = [("v_in", ctypes.c_double), ("c_out", ctypes.c_double), ("u_out", ctypes.c_void_p),
+                ("v_out", ctypes.c_void_p), ("w_out", ctypes.c_void_p)]
+
+
 class ibm_request(ctypes.Structure):
     _fields_ = [("kind", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
                 ("h", ctypes.c_double * 3), ("precision", ctypes.c_int), ("refine_iters", ctypes.c_int),
@@ -89,6 +94,8 @@ _SIG = {
     "ibm_spread": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "ibm_substep": (_I, [_P, ctypes.POINTER(ibm_state), _I, _D, _D, ctypes.POINTER(ibm_markers), _P,
                          ctypes.POINTER(ibm_info)]),
+    "ibm_substep_inout": (_I, [_P, ctypes.POINTER(ibm_state), ctypes.POINTER(ibm_inout), _I, _D, _D,
+                               ctypes.POINTER(ibm_markers), _P, ctypes.POINTER(ibm_info)]),
     "ibm_batch_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I, _I, ctypes.POINTER(_P)]),
     "ibm_batch_destroy": (_I, [_P]),
     "ibm_batch_poisson": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
@@ -183,7 +190,7 @@ def ibm_plan_workspace_bytes(plan):
 
 
 KERNEL_KINDS = ("forward", "pencil", "inverse", "residual", "explicit", "motion", "interp", "spread",
-                "divergence", "project")
+                "divergence", "project", "outflow")
 
 
 def ibm_plan_profile(plan, enable=True):
@@ -251,6 +258,16 @@ def ibm_substep(plan, state, rk_stage, dt, nu, markers, stream=None, info=False)
     inf = ibm_info() if info else None
     _check(lib().ibm_substep(plan, ctypes.byref(state), rk_stage, float(dt), float(nu), ctypes.byref(markers),
                              _stream(stream), ctypes.byref(inf) if inf is not None else None))
+    return inf.as_dict() if inf is not None else None
+
+
+def ibm_substep_inout(plan, state, inout, rk_stage, dt, nu, markers, stream=None, info=False):
+    """As ibm_substep with inflow-outflow walls; inout: ibm_inout (outlet
+    planes as device pointers, updated in place)."""
+    inf = ibm_info() if info else None
+    _check(lib().ibm_substep_inout(plan, ctypes.byref(state), ctypes.byref(inout), rk_stage, float(dt), float(nu),
+                                   ctypes.byref(markers), _stream(stream),
+                                   ctypes.byref(inf) if inf is not None else None))
     return inf.as_dict() if inf is not None else None
 
 

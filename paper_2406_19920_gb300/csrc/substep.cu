@@ -61,13 +61,20 @@ template <typename T> struct F3 {
 // y: u, w cell-centred with the no-slip ghost (-value) in the Laplacian and
 // zero wall flux in the advective y-flux; v on faces, zero at the walls
 // (j = 0 stored as the wall, j = ny not stored).
+//
+// IO: the inflow-outflow walls of Sec. 3 instead.  The y = 0 face carries
+// v = v_lo with u = w = 0 there (the ghost -value and the zero y-flux of
+// u, w are unchanged; v's lower neighbour at j = 1 is v_lo); the y = Ly
+// wall carries the outlet planes uo, wo (u, w at the wall: ghost 2 g - u in
+// the Laplacian, flux v_face * g) and vo (v on the outlet face), [nz][nx].
 constexpr int kExTX = 32, kExTZ = 8, kExJC = 16;
 
-template <typename T>
+template <typename T, bool IO>
 __global__ void __launch_bounds__(kExTX * kExTZ)
 k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_,
            const T *__restrict__ p_, T *Nu, T *Nv, T *Nw, T *__restrict__ du, T *__restrict__ dv,
-           T *__restrict__ dw, T c_visc, T c_pres, T gam, T zet, T dt) {
+           T *__restrict__ dw, T c_visc, T c_pres, T gam, T zet, T dt, T v_lo, const T *__restrict__ uo,
+           const T *__restrict__ vo, const T *__restrict__ wo) {
   pdl_wait();
   constexpr int TX = kExTX, TZ = kExTZ, HX = TX + 2, HZ = TZ + 2, PL = HX * HZ, NT = TX * TZ;
   constexpr int NL = (PL + NT - 1) / NT;  // plane elements each thread loads
@@ -144,17 +151,24 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
       // tile neighbours: B[dk * HX + di] relative to this column
       const T p0 = Pc[0];
       const T u0 = Uc[0], v0 = Vc[0], w0 = Wc[0];
+      // outlet wall values at this column (IO, top row only)
+      T ug = 0, wg = 0, vgo = 0, vgw = 0, vgs = 0;
+      if (IO && hi) {
+        const int iw = i == 0 ? nx - 1 : i - 1, ks = k == 0 ? nz - 1 : k - 1;
+        ug = uo[col]; wg = wo[col]; vgo = vo[col];
+        vgw = vo[k * nx + iw]; vgs = vo[ks * nx + i];
+      }
       // ---------------- u (x-faces) ----------------
       {
         const T ue = Uc[1], uw = Uc[-1], un = Uc[HX], us = Uc[-HX];
         const T uup = Up[0], udn = Um[0];
-        const T uu = hi ? -u0 : uup, ud = lo ? -u0 : udn;
+        const T uu = hi ? (IO ? 2 * ug - u0 : -u0) : uup, ud = lo ? -u0 : udn;
         const T lap = (ue - 2 * u0 + uw) * ihx2 + (un - 2 * u0 + us) * ihz2 + (uu - 2 * u0 + ud) * ihy2;
         const T uc = h * (u0 + ue), ucm = h * (uw + u0);
         const T txx = (uc * uc - ucm * ucm) * ihx;
         // y-flux at the faces j (zero at the wall j = 0) and j+1 (zero at j+1 = ny)
         const T fy0 = lo ? (T)0 : (h * (Vc[-1] + v0)) * (h * (udn + u0));
-        const T fy1 = hi ? (T)0 : (h * (Vp[-1] + Vp[0])) * (h * (u0 + uup));
+        const T fy1 = hi ? (IO ? (h * (vgw + vgo)) * ug : (T)0) : (h * (Vp[-1] + Vp[0])) * (h * (u0 + uup));
         const T fz0 = (h * (Wc[-1] + w0)) * (h * (us + u0));
         const T fz1 = (h * (Wc[HX - 1] + Wc[HX])) * (h * (u0 + un));
         const T N = txx + (fy1 - fy0) * ihy + (fz1 - fz0) * ihz;
@@ -167,14 +181,14 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
       {
         const T we = Wc[1], ww = Wc[-1], wn = Wc[HX], ws = Wc[-HX];
         const T wup = Wp[0], wdn = Wm[0];
-        const T wu = hi ? -w0 : wup, wd = lo ? -w0 : wdn;
+        const T wu = hi ? (IO ? 2 * wg - w0 : -w0) : wup, wd = lo ? -w0 : wdn;
         const T lap = (we - 2 * w0 + ww) * ihx2 + (wn - 2 * w0 + ws) * ihz2 + (wu - 2 * w0 + wd) * ihy2;
         const T wc = h * (w0 + wn), wcm = h * (ws + w0);
         const T tzz = (wc * wc - wcm * wcm) * ihz;
         const T fx0 = (h * (Uc[-HX] + u0)) * (h * (ww + w0));
         const T fx1 = (h * (Uc[1 - HX] + Uc[1])) * (h * (w0 + we));
         const T fy0 = lo ? (T)0 : (h * (Vc[-HX] + v0)) * (h * (wdn + w0));
-        const T fy1 = hi ? (T)0 : (h * (Vp[-HX] + Vp[0])) * (h * (w0 + wup));
+        const T fy1 = hi ? (IO ? (h * (vgs + vgo)) * wg : (T)0) : (h * (Vp[-HX] + Vp[0])) * (h * (w0 + wup));
         const T N = tzz + (fx1 - fx0) * ihx + (fy1 - fy0) * ihy;
         const T G = (p0 - Pc[-HX]) * ihz;
         const T np = n_prev ? Nw[idx] : (T)0;
@@ -187,7 +201,7 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
         Nv[idx] = (T)0;
       } else {
         const T ve = Vc[1], vw = Vc[-1], vn = Vc[HX], vs = Vc[-HX];
-        const T vu = hi ? (T)0 : Vp[0], vd = j - 1 <= 0 ? (T)0 : Vm[0];
+        const T vu = hi ? (IO ? vgo : (T)0) : Vp[0], vd = j - 1 <= 0 ? (IO ? v_lo : (T)0) : Vm[0];
         const T lap = (ve - 2 * v0 + vw) * ihx2 + (vn - 2 * v0 + vs) * ihz2 + (vu - 2 * v0 + vd) * ihy2;
         const T vc = h * (v0 + vu), vcm = h * (vd + v0);
         const T tyy = (vc * vc - vcm * vcm) * ihy;
@@ -225,6 +239,8 @@ __device__ __forceinline__ void atomic_max_nonneg(double *addr, double v) {
 // E2: b = D u * inv_scale in plain working precision (the right-hand side of
 // Eq. 2f); with dmax, additionally max |D u| evaluated exactly: float-float
 // differences for FP32 fields, FP64 for FP64 fields (the projection check).
+// The wall faces carry v_lo (y = 0) and v_hi ([nz][nx] at y = Ly, NULL for
+// 0).
 template <typename T> struct DivExact;
 template <> struct DivExact<float> {
   static __device__ __forceinline__ float eval(float ue, float uw, float vn, float vs, float wt, float wb,
@@ -246,7 +262,8 @@ template <> struct DivExact<double> {
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_divergence(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *__restrict__ w_, T *b,
-             T inv_scale, T ihx_t, T ihy_t, T ihz_t, ff ihx, ff ihy, ff ihz, double *dmax) {
+             T inv_scale, T ihx_t, T ihy_t, T ihz_t, ff ihx, ff ihy, ff ihz, double *dmax, T v_lo,
+             const T *__restrict__ v_hi) {
   pdl_wait();
   int i, k, j;
   const bool inside = stencil_index(g.nx, g.nz, i, k, j);
@@ -254,8 +271,8 @@ k_divergence(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T 
   T mx = 0;
   if (inside) {
     const F3<T> U{u_, g.nx, g.nz}, V{v_, g.nx, g.nz}, W{w_, g.nx, g.nz};
-    const T vs = j == 0 ? (T)0 : V.at(j, k, i);
-    const T vn = j + 1 >= g.ny ? (T)0 : V.at(j + 1, k, i);
+    const T vs = j == 0 ? v_lo : V.at(j, k, i);
+    const T vn = j + 1 >= g.ny ? (v_hi ? v_hi[k * g.nx + i] : (T)0) : V.at(j + 1, k, i);
     const T ue = U.at(j, k, i + 1), uw = U.at(j, k, i), wt = W.at(j, k + 1, i), wb = W.at(j, k, i);
     if (b) b[idx] = ((ue - uw) * ihx_t + (vn - vs) * ihy_t + (wt - wb) * ihz_t) * inv_scale;
     if (dmax) mx = DivExact<T>::eval(ue, uw, vn, vs, wt, wb, ihx, ihy, ihz);
@@ -268,11 +285,12 @@ k_divergence(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T 
   }
 }
 
-// E3: u -= k G phi (in place), p += phi - c L phi (Neumann ghosts).
+// E3: u -= k G phi (in place), p += phi - c L phi (Neumann ghosts); the
+// y = 0 face of v is set to v_lo.
 template <typename T>
 __global__ void __launch_bounds__(128)
 k_project(Geo g, T *__restrict__ u, T *__restrict__ v, T *__restrict__ w, T *__restrict__ p,
-          const T *__restrict__ phi_, T kproj, T cvisc) {
+          const T *__restrict__ phi_, T kproj, T cvisc, T v_lo) {
   pdl_wait();
   int i, k, j;
   if (!stencil_index(g.nx, g.nz, i, k, j)) return;
@@ -287,9 +305,71 @@ k_project(Geo g, T *__restrict__ u, T *__restrict__ v, T *__restrict__ w, T *__r
   u[idx] -= kproj * (f0 - fw) * ihx;
   w[idx] -= kproj * (f0 - fs) * ihz;
   if (j > 0) v[idx] -= kproj * (f0 - fd) * ihy;
-  else v[idx] = (T)0;
+  else v[idx] = v_lo;
   const T lap = (fe - 2 * f0 + fw) * ihx * ihx + (fn - 2 * f0 + fs) * ihz * ihz + (fu - 2 * f0 + fd) * ihy * ihy;
   p[idx] += f0 - cvisc * lap;
+}
+
+// Outlet condition of the inflow-outflow configuration (Sec. 3):
+// d phi/dt + C d phi/dy = 0 at y = Ly, advanced over the stage step
+// (alpha + beta) dt by first-order upwinding from the last interior value
+// (cu = step C / (hy/2) for u, w at the wall, cv = step C / hy for v's outlet
+// face).  Also stores v = v_in on the inflow face (plane 0 of v) and writes
+// each CTA's FP64 sum of the new outlet v to part[blockIdx.x] (fixed-order
+// tree, so the total is reproducible).
+constexpr int kOutT = 256;
+template <typename T>
+__global__ void __launch_bounds__(kOutT)
+k_outflow_update(int ncol, const T *__restrict__ ul, const T *__restrict__ vl, const T *__restrict__ wl, T *uo,
+                 T *vo, T *wo, T *v0, T cu, T cv, T v_in, double *part) {
+  pdl_wait();
+  __shared__ double ws[kOutT / 32];
+  const int col = blockIdx.x * kOutT + threadIdx.x;
+  double s = 0.0;
+  if (col < ncol) {
+    uo[col] -= cu * (uo[col] - ul[col]);
+    wo[col] -= cu * (wo[col] - wl[col]);
+    const T vn = vo[col] - cv * (vo[col] - vl[col]);
+    vo[col] = vn;
+    v0[col] = v_in;
+    s = (double)vn;
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kOutT / 32; ++q) t += ws[q];
+    part[blockIdx.x] = t;
+  }
+}
+
+// Global mass balance: the outlet v is shifted by a constant so that its
+// mean equals v_in (outflow = inflow; the Poisson right-hand side then has
+// zero mean).  Every CTA sums the nparts partial sums in the same order.
+template <typename T>
+__global__ void __launch_bounds__(kOutT)
+k_outflow_shift(int ncol, T *vo, double v_in, const double *__restrict__ part, int nparts, double inv_ncol) {
+  pdl_wait();
+  __shared__ double ws[kOutT / 32];
+  __shared__ double shift;
+  double s = 0.0;
+  for (int q = threadIdx.x; q < nparts; q += kOutT) s += part[q];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < kOutT / 32; ++q) t += ws[q];
+    shift = v_in - t * inv_ncol;
+  }
+  __syncthreads();
+  const int col = blockIdx.x * kOutT + threadIdx.x;
+  if (col < ncol) vo[col] = (T)((double)vo[col] + shift);
 }
 
 static ff ff_host(double v) {
@@ -319,8 +399,8 @@ static int ensure_substep_buffers(ibm_plan_s *p, int nmk) {
 }
 
 template <typename T>
-static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double nu, ibm_markers *mk,
-                     cudaStream_t st, ibm_info *info) {
+static int substep_t(ibm_plan_s *p, ibm_state *s, const ibm_inout *io, int stage, double dt, double nu,
+                     ibm_markers *mk, cudaStream_t st, ibm_info *info) {
   const int n = stage - 1;
   const double a = kAlpha[n], b = kBeta[n], gm = kGamma[n], zt = kZeta[n];
   const double ab = a + b;
@@ -337,13 +417,34 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
     IBM_CUDA_TRY(cudaMemsetAsync(p->dsc + 8, 0, 2 * sizeof(double), st));
     IBM_CUDA_TRY(cudaEventRecord(p->ev0, st));
   }
+  // inflow-outflow walls: outlet values advanced to the end of the stage
+  // and made mass-conserving; they are the wall data of the whole stage
+  const T v_lo = io ? (T)io->v_in : (T)0;
+  T *uo = io ? (T *)io->u_out : nullptr, *vo = io ? (T *)io->v_out : nullptr, *wo = io ? (T *)io->w_out : nullptr;
+  if (io) {
+    ProfScope ps(p, IBM_K_OUTFLOW, st, 2);
+    const int ncol = p->nx * p->nz, nparts = ceil_div(ncol, kOutT);
+    const size_t last = (size_t)(p->ny - 1) * ncol;
+    const double step = ab * dt;
+    double *part = (double *)p->work;
+    IBM_CUDA_TRY(launch_pdl(k_outflow_update<T>, dim3(nparts), dim3(kOutT), 0, st, ncol, (const T *)(u + last),
+                            (const T *)(v + last), (const T *)(w + last), uo, vo, wo, v,
+                            (T)(step * io->c_out * 2.0 * g.ihy), (T)(step * io->c_out * g.ihy), v_lo, part));
+    IBM_CUDA_TRY(launch_pdl(k_outflow_shift<T>, dim3(nparts), dim3(kOutT), 0, st, ncol, vo, io->v_in,
+                            (const double *)part, nparts, 1.0 / ncol));
+  }
   // E1
   {
     ProfScope ps(p, IBM_K_EXPLICIT, st);
     const dim3 eg(ceil_div(p->nx, kExTX), ceil_div(p->nz, kExTZ), ceil_div(p->ny, kExJC));
-    IBM_CUDA_TRY(launch_pdl(k_explicit<T>, eg, dim3(kExTX, kExTZ), 0, st, g, u, v, w, pr, (T *)s->Nu, (T *)s->Nv, (T *)s->Nw, du, dv, dw,
-                                          (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt));
-    IBM_CUDA_TRY(cudaGetLastError());
+    if (io)
+      IBM_CUDA_TRY(launch_pdl(k_explicit<T, true>, eg, dim3(kExTX, kExTZ), 0, st, g, u, v, w, pr, (T *)s->Nu,
+                              (T *)s->Nv, (T *)s->Nw, du, dv, dw, (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt, v_lo,
+                              (const T *)uo, (const T *)vo, (const T *)wo));
+    else
+      IBM_CUDA_TRY(launch_pdl(k_explicit<T, false>, eg, dim3(kExTX, kExTZ), 0, st, g, u, v, w, pr, (T *)s->Nu,
+                              (T *)s->Nv, (T *)s->Nw, du, dv, dw, (T)(ab * nu), (T)ab, (T)gm, (T)zt, (T)dt, (T)0,
+                              (const T *)nullptr, (const T *)nullptr, (const T *)nullptr));
   }
   // L2 + L1
   if (nmk > 0) {
@@ -374,23 +475,21 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
   const ff fx = ff_host(g.ihx), fy = ff_host(g.ihy), fz = ff_host(g.ihz);
   {
     ProfScope ps(p, IBM_K_DIVERGENCE, st);
-    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, rhs, (T)(1.0 / (ab * dt)), (T)g.ihx, (T)g.ihy,
-                                                  (T)g.ihz, fx, fy, fz, info ? p->dsc + 9 : nullptr));
-    IBM_CUDA_TRY(cudaGetLastError());
+    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, rhs, (T)(1.0 / (ab * dt)),
+                            (T)g.ihx, (T)g.ihy, (T)g.ihz, fx, fy, fz, info ? p->dsc + 9 : nullptr, v_lo,
+                            (const T *)vo));
   }
   // S2
   if ((rc = plan_solve(p, 0, 0.0, 0, rhs, phi, nullptr, st, nullptr))) return rc;
   // E3
   {
     ProfScope ps(p, IBM_K_PROJECT, st);
-    IBM_CUDA_TRY(launch_pdl(k_project<T>, L3.grid, L3.block, 0, st, g, u, v, w, pr, phi, (T)(ab * dt), (T)cH));
-    IBM_CUDA_TRY(cudaGetLastError());
+    IBM_CUDA_TRY(launch_pdl(k_project<T>, L3.grid, L3.block, 0, st, g, u, v, w, pr, phi, (T)(ab * dt), (T)cH, v_lo));
   }
   if (info) {
     IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
-    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, nullptr, (T)1, (T)g.ihx, (T)g.ihy, (T)g.ihz, fx, fy,
-                                                  fz, p->dsc + 8));
-    IBM_CUDA_TRY(cudaGetLastError());
+    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, nullptr, (T)1, (T)g.ihx,
+                            (T)g.ihy, (T)g.ihz, fx, fy, fz, p->dsc + 8, v_lo, (const T *)vo));
     IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IBM_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -410,8 +509,8 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, int stage, double dt, double n
 
 using namespace ibm;
 
-extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
-                           void *stream, ibm_info *info) {
+static int substep_entry(ibm_plan plan, ibm_state *st, const ibm_inout *io, int rk_stage, double dt, double nu,
+                         ibm_markers *mk, void *stream, ibm_info *info) {
   if (!plan || !st) return set_error(IBM_ERR_ARG, "ibm_substep: NULL plan or state");
   if (plan->bc != IBM_BC_PXZ_WALL_Y)
     return set_error(IBM_ERR_UNSUPPORTED, "ibm_substep: the RK stage is built for the wall-bounded branch only");
@@ -432,7 +531,25 @@ extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt
   } else if (mk && mk->n < 0) {
     return set_error(IBM_ERR_ARG, "ibm_substep: negative marker count");
   }
+  if (io) {
+    if (!std::isfinite(io->v_in) || !std::isfinite(io->c_out) || io->c_out < 0)
+      return set_error(IBM_ERR_ARG, "ibm_substep_inout: v_in must be finite and c_out finite and >= 0");
+    const void *planes[] = {io->u_out, io->v_out, io->w_out};
+    for (const void *f : planes)
+      if (!f) return set_error(IBM_ERR_ARG, "ibm_substep_inout: NULL outlet plane");
+  }
   if (plan->precision == IBM_FP64)
-    return substep_t<double>(plan, st, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
-  return substep_t<float>(plan, st, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
+    return substep_t<double>(plan, st, io, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
+  return substep_t<float>(plan, st, io, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
+}
+
+extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
+                           void *stream, ibm_info *info) {
+  return substep_entry(plan, st, nullptr, rk_stage, dt, nu, mk, stream, info);
+}
+
+extern "C" int ibm_substep_inout(ibm_plan plan, ibm_state *st, const ibm_inout *io, int rk_stage, double dt,
+                                 double nu, ibm_markers *mk, void *stream, ibm_info *info) {
+  if (!io) return set_error(IBM_ERR_ARG, "ibm_substep_inout: NULL inflow-outflow data");
+  return substep_entry(plan, st, io, rk_stage, dt, nu, mk, stream, info);
 }

@@ -69,6 +69,118 @@ def _run_gpu(g, fields, Np, X0, dV, stage, dt, nu, motion, params, prec, dt_t, t
         ibm.ibm_plan_destroy(plan)
 
 
+def _run_gpu_inout(g, fields, Np, X0, dV, io, stages, dt, nu, params, prec, dt_t):
+    """Stages `stages` (a sequence of 1..3) of ibm_substep_inout in a row;
+    the outlet planes carry over from stage to stage on the device."""
+    nx, ny, nz = g[:3]
+    n = len(X0)
+    plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, 1)
+    try:
+        d = [dev(a, dt_t) for a in fields]
+        dN = [dev(a, dt_t) for a in Np]
+        st = ibm.ibm_state(d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), d[3].data_ptr(),
+                           dN[0].data_ptr(), dN[1].data_ptr(), dN[2].data_ptr(), 0.0)
+        planes = [dev(io[k], dt_t) for k in ("u_out", "v_out", "w_out")]
+        dio = ibm.ibm_inout(io["v_in"], io["c_out"], *[t.data_ptr() for t in planes])
+        X0d, dVd = dev(X0, dt_t), dev(dV, dt_t)
+        X = torch.empty((n, 3), dtype=dt_t, device="cuda")
+        Ud = torch.empty_like(X)
+        F = torch.empty_like(X)
+        mk = ibm.ibm_markers(n, X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
+                             ibm.IBM_MOTION_TRANSLATE, ctypes_d4(params))
+        info = None
+        for s in stages:
+            info = ibm.ibm_substep_inout(plan, st, dio, s, dt, nu, mk, info=True)
+        return dict(u=host(d[0]), v=host(d[1]), w=host(d[2]), p=host(d[3]), N=[host(a) for a in dN],
+                    F=host(F), u_out=host(planes[0]), v_out=host(planes[1]), w_out=host(planes[2]), t=st.t,
+                    info=info)
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
+def _inout_data(nx, nz, npdt, seed):
+    r = np.random.default_rng(seed)
+    cast = lambda a: np.asarray(a).astype(npdt).astype(np.float64)
+    return dict(v_in=0.5, c_out=0.6, u_out=cast(0.1 * r.standard_normal((nz, nx))),
+                v_out=cast(0.5 + 0.1 * r.standard_normal((nz, nx))), w_out=cast(0.1 * r.standard_normal((nz, nx))))
+
+
+@pytest.mark.parametrize("shape", [(32, 32, 32), (48, 24, 24)])
+@pytest.mark.parametrize("stage", [1, 2, 3])
+@pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
+def test_inout_substep_matches_oracle(shape, stage, prec):
+    """Inflow-outflow walls (Sec. 3): one stage, every field and the
+    advanced outlet planes against the oracle."""
+    nx, ny, nz = shape
+    npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
+    dt_t = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+    tol = TOL_STAGE_FP64 if prec == ibm.IBM_FP64 else TOL_STAGE_FP32
+    g, (u, v, w, p), Np, X0, dV = _setup(nx, ny, nz, 800, npdt, wl=50 + stage)
+    io = _inout_data(nx, nz, npdt, 60 + stage)
+    dt, nu = 1e-3, 1e-2
+    params = (0.1, 0.0, 0.0)
+    st = dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
+    mk = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=params)
+    ref, rinfo = O.rk_stage(st, mk, stage, dt, nu, g, inout=io)
+    got = _run_gpu_inout(g, [u, v, w, p], Np, X0, dV, io, [stage], dt, nu, params, prec, dt_t)
+    errs = {k: rel_l2(got[k], ref[k]) for k in ("u", "v", "w", "p")}
+    errs.update({"N%d" % c: rel_l2(got["N"][c], ref["N_prev"][c]) for c in range(3)})
+    errs.update({k: rel_l2(got[k], ref["inout"][k]) for k in ("u_out", "v_out", "w_out")})
+    errs["F"] = rel_l2(got["F"], rinfo["F"])
+    assert max(errs.values()) <= tol, errs
+    assert np.all(got["v"][0] == npdt(io["v_in"]))
+    # outflow = inflow to rounding of the stored outlet plane
+    assert abs(got["v_out"].mean() - io["v_in"]) <= (1e-14 if prec == ibm.IBM_FP64 else 1e-6)
+    vo = ref["inout"]["v_out"]
+    d0 = np.abs(O.divergence(*rinfo["ustar"], g, io["v_in"], vo)).max()
+    lim = 1e-11 if prec == ibm.IBM_FP64 else 1e-5
+    assert got["info"]["div_max"] <= lim * max(1.0, d0), (got["info"], d0)
+    assert abs(got["info"]["div_before"] - d0) <= 1e-3 * d0
+
+
+@pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
+def test_inout_full_rk_step_matches_oracle(prec):
+    """Three stages in a row (one time step): the outlet planes and N^{n-2}
+    carry over on the device exactly as in the oracle."""
+    nx, ny, nz = 48, 24, 32
+    npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
+    dt_t = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+    g, (u, v, w, p), Np, X0, dV = _setup(nx, ny, nz, 500, npdt, wl=71)
+    io = _inout_data(nx, nz, npdt, 72)
+    dt, nu = 2e-3, 1e-2
+    params = (0.1, 0.0, 0.0)
+    st = dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
+    mk = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=params)
+    ref_io = io
+    for s in (1, 2, 3):
+        st, _ = O.rk_stage(st, mk, s, dt, nu, g, inout=ref_io)
+        ref_io = st["inout"]
+    got = _run_gpu_inout(g, [u, v, w, p], Np, X0, dV, io, (1, 2, 3), dt, nu, params, prec, dt_t)
+    tol = 3 * (TOL_STAGE_FP64 if prec == ibm.IBM_FP64 else TOL_STAGE_FP32)
+    errs = {k: rel_l2(got[k], st[k]) for k in ("u", "v", "w", "p")}
+    errs.update({k: rel_l2(got[k], ref_io[k]) for k in ("u_out", "v_out", "w_out")})
+    assert max(errs.values()) <= tol, errs
+    assert abs(got["t"] - dt) < 1e-15
+
+
+def test_inout_arguments_rejected():
+    g = grid(16, 16, 16)
+    plan = ibm.ibm_plan_create(16, 16, 16, g[3:], ibm.IBM_FP64, 1)
+    try:
+        f = [torch.zeros((16, 16, 16), dtype=torch.float64, device="cuda") for _ in range(7)]
+        st = ibm.ibm_state(*[t.data_ptr() for t in f], 0.0)
+        pl = [torch.zeros((16, 16), dtype=torch.float64, device="cuda") for _ in range(3)]
+        mk = ibm.ibm_markers(0, None, None, None, None, None, ibm.IBM_MOTION_STATIC, ctypes_d4(()))
+        bad = [ibm.ibm_inout(0.5, -1.0, *[t.data_ptr() for t in pl]),
+               ibm.ibm_inout(float("nan"), 0.5, *[t.data_ptr() for t in pl]),
+               ibm.ibm_inout(0.5, 0.5, pl[0].data_ptr(), None, pl[2].data_ptr())]
+        for io in bad:
+            with pytest.raises(ibm.IbmError):
+                ibm.ibm_substep_inout(plan, st, io, 1, 1e-3, 1e-2, mk)
+    finally:
+        ibm.ibm_plan_destroy(plan)
+
+
 def ctypes_d4(params):
     import ctypes
     vals = list(params) + [0.0] * (4 - len(params))
