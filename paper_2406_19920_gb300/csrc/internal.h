@@ -27,11 +27,16 @@ template <typename P> inline Ptr3<P> ptr3(P a, P b = nullptr, P c = nullptr) { r
 struct TransformGeom {
   int nx, ny, nz;
   int nb;          // fields in the launch (1..kMaxFields)
-  int use_plane;   // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane
+  int use_plane;   // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane;
+                   // kPlaneDft tensor-core DFT products
   int *err;        // device error word for bounded waits
   double *zrhs;    // forward: if set, receives Re S[j][0][0] of every plane (the zero pencil)
   const double *zsol;  // inverse: if set, replaces S[j][0][0] by (zsol[j], 0) before transforming
+  const void *dft_fwd, *dft_inv;  // plane mode kPlaneDft: the DFT matrix tables (FP32 plans)
 };
+
+// Plane mode of the tensor-core DFT transforms (dft_tc.cu).
+constexpr int kPlaneDft = -1;
 
 // Lanes that exist in the calling thread's warp (a block of fewer than 32
 // threads has a partial last warp).
@@ -111,7 +116,7 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
   } while (0)
 
 bool transform_size_supported(int n);
-// Plane modes (0, 1, 2, 4, 8) that can run an nx x nz plane, smallest first; returns the count.
+// Plane modes (kPlaneDft, 0, 1, 2, 4, 8) that can run an nx x nz plane; returns the count.
 template <typename T> int plane_modes(int nx, int nz, int *modes);
 // Plane mode used when no tuning result is known.
 template <typename T> int default_plane_mode(int nx, int ny, int nz);
@@ -127,6 +132,15 @@ cudaError_t launch_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx
 template <typename T>
 cudaError_t launch_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> out, Ptr3<const T *> addend,
                            const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st);
+
+// Tensor-core DFT plane transforms (FP32; nx, nz in {8, 16, 24, 32, 48, 64}):
+// the same contracts as launch_forward / launch_inverse.
+bool dft_tc_supported(int nx, int nz);
+cudaError_t dft_tc_upload(int nx, int nz, void **fwd, void **inv, size_t *bytes);
+cudaError_t launch_dft_forward(const TransformGeom &g, Ptr3<const float *> in, Ptr3<float2 *> S, float in_scale,
+                               cudaStream_t st);
+cudaError_t launch_dft_inverse(const TransformGeom &g, Ptr3<float2 *> S, Ptr3<float *> out,
+                               Ptr3<const float *> addend, float scale, cudaStream_t st);
 
 // Split passes: x rows then z columns (forward), z columns then x rows (inverse).
 template <typename T>

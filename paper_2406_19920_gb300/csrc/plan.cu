@@ -52,6 +52,8 @@ TransformGeom geom_of(const ibm_plan_s *p) {
   g.err = p->derr;
   g.zrhs = nullptr;
   g.zsol = nullptr;
+  g.dft_fwd = p->dftf;
+  g.dft_inv = p->dfti;
   return g;
 }
 
@@ -122,7 +124,7 @@ static void plan_free(ibm_plan_s *p) {
   for (auto &r : p->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
   for (auto e : p->evpool) cudaEventDestroy(e);
   void *bufs[] = {p->S, p->Sx[0], p->Sx[1], p->work, p->bsave, p->sub[0], p->sub[1], p->sub[2], p->sub[3], p->twy, p->lamy,
-                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf, p->gbuf};
+                  p->twx, p->twz, p->lamx, p->lamz, p->dsc, p->mkbuf, p->derr, p->zbuf, p->gbuf, p->dftf, p->dfti};
   for (void *b : bufs)
     if (b) cudaFree(b);
   if (p->hsc) cudaFreeHost(p->hsc);
@@ -423,8 +425,9 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
     p->pencil_mode = m;
   }
   // plane transforms: the default mode for the shape; IBM_PLANE_MODE=m forces
-  // mode m (0 split passes, 1 one CTA per plane, 2/4/8 cluster) and fails
-  // the plan when the shape has no such mode (A/B timing and tests)
+  // mode m (0 split passes, 1 one CTA per plane, 2/4/8 cluster, -1 tensor-core
+  // DFT products) and fails the plan when the shape has no such mode (A/B
+  // timing and tests)
   p->use_plane = precision == IBM_FP64 ? default_plane_mode<double>(nx, ny, nz) : default_plane_mode<float>(nx, ny, nz);
   // three-field solves: split passes (their small CTAs share the SMs
   // between fields); IBM_PLANE_MODE_FIELDS=m forces another mode
@@ -483,6 +486,14 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   if ((e = cudaMemset(p->derr, 0, 16)) != cudaSuccess) { plan_free(p); return cuda_error(e, "cudaMemset"); }
   rc = precision == IBM_FP64 ? upload_tables<double>(p) : upload_tables<float>(p);
   if (rc) { plan_free(p); return rc; }
+  if (precision == IBM_FP32_REFINED && dft_tc_supported(nx, nz)) {
+    size_t tb = 0;
+    if ((e = dft_tc_upload(nx, nz, &p->dftf, &p->dfti, &tb)) != cudaSuccess) {
+      plan_free(p);
+      return cuda_error(e, "DFT tables");
+    }
+    p->bytes += tb;
+  }
   *out = p;
   return IBM_OK;
 }

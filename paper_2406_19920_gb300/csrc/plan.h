@@ -33,7 +33,8 @@ struct ibm_plan_s {
   int refine;        // refinement steps (FP32 path)
   int delta;         // IBM_DELTA_*
   int pencil_mode;   // 0 auto, 1 warp-parallel block solve, 2 tile sweep, 3 streaming sweep, 4 segmented sweep
-  int use_plane = 1; // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane
+  int use_plane = 1; // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane;
+                     // -1 (kPlaneDft) tensor-core DFT products (FP32, short planes)
   int use_plane_fields = 0; // plane mode of three-field solves
   size_t esz;        // element size: 4 or 8
   size_t npts;       // nx * ny * nz
@@ -49,6 +50,7 @@ struct ibm_plan_s {
   void *gbuf = nullptr;  // gather-spreading workspace (bins, sorted entries, stencil records)
   size_t gcap = 0;       // bytes of gbuf
   void *twx, *twz;   // twiddles W_N^m (plan precision)
+  void *dftf = nullptr, *dfti = nullptr;  // tensor-core DFT matrix tables (FP32 plans with short planes)
   void *twy, *lamy;  // triply periodic branch: W_ny^m and lambda_y (plan precision)
   void *lamx, *lamz; // modified wavenumbers kx'^2 (P), kz'^2 (nz) (plan precision)
   double *dsc;       // device scalars: [0] removed mean, [1] it as a float pair, [4..7] residual

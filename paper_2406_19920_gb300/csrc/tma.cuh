@@ -58,6 +58,24 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *e
   return false;
 }
 
+// As mbar_wait, bounded by wall time (the %globaltimer nanosecond clock)
+// instead of a poll count: for waits on tensor-core work, whose polls may
+// each suspend the thread for a hardware-chosen time.
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, int *err, uint64_t limit_ns) {
+  const uint64_t t0 = global_ns();
+  while (!mbar_try_wait(bar, parity))
+    if (global_ns() - t0 > limit_ns) {
+      if (err) atomicOr(err, kErrTimeout);
+      return false;
+    }
+  return true;
+}
+
 // global -> shared, completion counted on `bar` (bytes % 16 == 0, aligned).
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
   asm volatile(

@@ -191,6 +191,9 @@ template <typename T>
 cudaError_t launch_forward(const TransformGeom &g, Ptr3<const T *> in, Ptr3<cplx<T> *> S, const cplx<T> *twx,
                            const cplx<T> *twz, T in_scale, cudaStream_t st) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if constexpr (sizeof(T) == 4) {
+    if (g.use_plane == kPlaneDft && g.dft_fwd) return launch_dft_forward(g, in, S, in_scale, st);
+  }
   if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
     return launch_cplane_forward<T>(g, g.use_plane, in, S, twx, twz, in_scale, st);
   if (g.use_plane == 1 && plane_supported<T>(nx, nz)) {
@@ -213,6 +216,9 @@ template <typename T>
 cudaError_t launch_inverse(const TransformGeom &g, Ptr3<cplx<T> *> S, Ptr3<T *> out, Ptr3<const T *> addend,
                            const cplx<T> *twx, const cplx<T> *twz, T scale, cudaStream_t st) {
   const int nx = g.nx, ny = g.ny, nz = g.nz;
+  if constexpr (sizeof(T) == 4) {
+    if (g.use_plane == kPlaneDft && g.dft_inv) return launch_dft_inverse(g, S, out, addend, scale, st);
+  }
   if (g.use_plane >= 2 && cplane_supported<T>(nx, nz, g.use_plane))
     return launch_cplane_inverse<T>(g, g.use_plane, S, out, addend, twx, twz, scale, st);
   if (g.use_plane == 1 && plane_supported<T>(nx, nz)) {
@@ -241,6 +247,7 @@ template cudaError_t launch_inverse<double>(const TransformGeom &, Ptr3<double2 
                                             cudaStream_t);
 
 template <typename T> int transform_launches(const TransformGeom &g) {
+  if (g.use_plane == kPlaneDft) return (sizeof(T) == 4 && g.dft_fwd) ? 1 : 2;
   if (g.use_plane >= 2) return cplane_supported<T>(g.nx, g.nz, g.use_plane) ? 1 : 2;
   return (g.use_plane == 1 && plane_supported<T>(g.nx, g.nz)) ? 1 : 2;
 }
@@ -249,6 +256,7 @@ template int transform_launches<double>(const TransformGeom &);
 
 template <typename T> int plane_modes(int nx, int nz, int *modes) {
   int n = 0;
+  if (sizeof(T) == 4 && dft_tc_supported(nx, nz)) modes[n++] = kPlaneDft;
   modes[n++] = 0;
   if (plane_supported<T>(nx, nz)) modes[n++] = 1;
   for (int c = 2; c <= 8; c *= 2)

@@ -219,7 +219,8 @@ def test_substep_matches_oracle(shape, stage, prec):
 @pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
 def test_three_field_helmholtz_every_kernel(prec):
     """The three Helmholtz solves of a stage share launches; every plane mode
-    of those launches (split, one CTA per plane, 2-CTA cluster) and every
+    of those launches (split, one CTA per plane, 2-CTA cluster, tensor-core
+    DFT products) and every
     pencil kernel gives the oracle's stage."""
     nx, ny, nz = 64, 24, 64
     npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
@@ -230,7 +231,9 @@ def test_three_field_helmholtz_every_kernel(prec):
     params = (0.1, 0.0, 0.0)
     st = dict(u=u, v=v, w=w, p=p, N_prev=tuple(Np), t=0.0)
     ref, _ = O.rk_stage(st, dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=params), 2, dt, nu, g)
-    for plane_mode, pencil_mode in ((0, 2), (0, 3), (1, 2), (2, 3), (0, 1), (1, 4)):
+    for plane_mode, pencil_mode in ((0, 2), (0, 3), (1, 2), (2, 3), (0, 1), (1, 4), (-1, 4)):
+        if plane_mode == -1 and prec == ibm.IBM_FP64:
+            continue  # the tensor-core DFT mode (-1) exists for FP32 plans only
         os.environ["IBM_PLANE_MODE_FIELDS"] = str(plane_mode)
         os.environ["IBM_PENCIL_MODE"] = str(pencil_mode)
         try:
