@@ -413,6 +413,7 @@ def run_gpu(args):
 
     # ---- batched (64 instances, one graph launch) and served workloads ----
     batched = batched_compare(ibm, torch) if not args.no_extras else None
+    dft = dft_compare(ibm, torch) if not args.no_extras else None
     serving = serve_sample(ibm) if not args.no_extras else None
     plate = large_plate(ibm, torch) if not args.no_extras else None
     plate_inflow = large_plate(ibm, torch, v_in=1.0) if not args.no_extras else None
@@ -463,6 +464,7 @@ def run_gpu(args):
         "poisson_256": solves_256,
         "spreading": spreading,
         "batched": batched,
+        "dft_tensor_core": dft,
         "serving": serving,
         "large_plate": plate,
         "large_plate_inflow": plate_inflow,
@@ -572,15 +574,21 @@ def spread_compare(ibm, torch):
     return res
 
 
-def solve_twice(n):
+def solve_twice(n, plane_mode=None):
     """Two refined FP32 Poisson solves on an n^3 grid of the workload domain
     (N(0,1) right-hand side): the launch sequence the profiles of the 256^3
-    solve are taken from."""
+    solve are taken from.  plane_mode: forces that plane mode of the
+    transforms (-1 the tensor-core DFT products)."""
     import torch
     import paper_2406_19920_gb300 as ibm
     from paper_2406_19920_gb300 import synth
     g = synth.grid(n, n, n)
-    plan = ibm.ibm_plan_create(n, n, n, g[3:], ibm.IBM_FP32_REFINED, 1)
+    if plane_mode is not None:
+        os.environ["IBM_PLANE_MODE"] = str(plane_mode)
+    try:
+        plan = ibm.ibm_plan_create(n, n, n, g[3:], ibm.IBM_FP32_REFINED, 1)
+    finally:
+        os.environ.pop("IBM_PLANE_MODE", None)
     b = torch.randn((n, n, n), device="cuda", dtype=torch.float32, generator=torch.Generator("cuda").manual_seed(1))
     x = torch.empty_like(b)
     for _ in range(2):
@@ -590,32 +598,47 @@ def solve_twice(n):
     ibm.ibm_plan_destroy(plan)
 
 
-def batched_compare(ibm, torch):
-    """64 instances, grids drawn from {32,48,64,96,128}^3, 4 right-hand sides
-    each: FP32 + 1 refinement through ibm_batch_poisson (one CUDA-graph
-    launch per right-hand-side set) vs 64 sequential plain FP64 solves."""
-    from paper_2406_19920_gb300 import synth
-    rng = np.random.default_rng(3005)
-    dims = [(int(n), int(n), int(n)) for n in rng.choice([32, 48, 64, 96, 128], 64)]
-    hs = [synth.grid(*d)[3:] for d in dims]
+def _batch_ms(ibm, torch, dims, hs, rhs, phi, reps=5):
+    """Creates (and tunes) a batch, runs the four right-hand-side sets once,
+    then times `reps` rounds of them; returns (batch, ms per round, create s)."""
     t0 = time.perf_counter()
     b = ibm.ibm_batch_create(dims, hs, ibm.IBM_FP32_REFINED, 1)
     create_s = time.perf_counter() - t0
-    rhs = [[torch.from_numpy(synth.rhs_lowpass_noise(*d, kmax=12.0, workload=3, stream=100 * k + i))
-            .to("cuda", torch.float32) for i, d in enumerate(dims)] for k in range(4)]
-    phi = [[torch.empty_like(x) for x in r] for r in rhs]
     for k in range(4):
         ibm.ibm_batch_poisson(b, rhs[k], phi[k])
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    reps = 5
     e0.record()
     for _ in range(reps):
         for k in range(4):
             ibm.ibm_batch_poisson(b, rhs[k], phi[k])
     e1.record()
     torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
+    return b, e0.elapsed_time(e1) / reps, create_s
+
+
+def batched_compare(ibm, torch):
+    """64 instances, grids drawn from {32,48,64,96,128}^3, 4 right-hand sides
+    each: FP32 + 1 refinement through ibm_batch_poisson (one CUDA-graph
+    launch per right-hand-side set) vs 64 sequential plain FP64 solves.  The
+    batch is tuned twice: with every plane mode (the tensor-core DFT mode
+    included for the short planes) and with CUDA-core FFTs only
+    (IBM_TUNE_DFT=0)."""
+    from paper_2406_19920_gb300 import synth
+    rng = np.random.default_rng(3005)
+    dims = [(int(n), int(n), int(n)) for n in rng.choice([32, 48, 64, 96, 128], 64)]
+    hs = [synth.grid(*d)[3:] for d in dims]
+    rhs = [[torch.from_numpy(synth.rhs_lowpass_noise(*d, kmax=12.0, workload=3, stream=100 * k + i))
+            .to("cuda", torch.float32) for i, d in enumerate(dims)] for k in range(4)]
+    phi = [[torch.empty_like(x) for x in r] for r in rhs]
+    os.environ["IBM_TUNE_DFT"] = "0"
+    try:
+        b_fft, ms_fft, _ = _batch_ms(ibm, torch, dims, hs, rhs, phi)
+    finally:
+        del os.environ["IBM_TUNE_DFT"]
+    ibm.ibm_batch_destroy(b_fft)
+    b, ms, create_s = _batch_ms(ibm, torch, dims, hs, rhs, phi)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     pts = sum(d[0] * d[1] * d[2] for d in dims) * 4
     plans = [ibm.ibm_plan_create(*d, h, ibm.IBM_FP64, 0) for d, h in zip(dims, hs)]
     r64 = [x.double() for x in rhs[0]]
@@ -637,8 +660,57 @@ def batched_compare(ibm, torch):
     return {"instances": 64, "rhs_per_instance": 4, "grid_pts_per_set": pts // 4,
             "fp32_refined_batched": {"solves_per_s": 256e3 / ms, "grid_pts_per_s": pts / (ms * 1e-3),
                                      "ms_per_256_solves": ms},
+            "fp32_refined_batched_fft_only": {"solves_per_s": 256e3 / ms_fft, "ms_per_256_solves": ms_fft},
             "fp64_sequential": {"solves_per_s": 64e3 / ms64, "grid_pts_per_s": (pts / 4) / (ms64 * 1e-3)},
             "speedup": (256e3 / ms) / (64e3 / ms64), "max_rel_l2_vs_fp64": err, "create_and_tune_s": create_s}
+
+
+def dft_compare(ibm, torch, sizes=(32, 48, 64), reps=50):
+    """Tensor-core DFT plane transforms against the CUDA-core FFT kernels on
+    the short planes of the batched workload: an n^3 FP32 Poisson solve with
+    one refinement step (two forward and two inverse transforms) in each
+    plane mode.  Reports the solve time and the forward / inverse transform
+    time per solve (event trace of the plan), and the relative L2 distance
+    of the DFT-mode solution from the FFT-mode one."""
+    from paper_2406_19920_gb300 import synth
+    out = {}
+    for n in sizes:
+        g = synth.grid(n, n, n)
+        b = torch.from_numpy(synth.rhs_lowpass_noise(n, n, n, kmax=12.0, workload=3, stream=7)).to("cuda",
+                                                                                                   torch.float32)
+        row, sols = {}, {}
+        for name, mode in (("dft_tc", -1), ("fft_plane", 1), ("fft_split", 0)):
+            os.environ["IBM_PLANE_MODE"] = str(mode)
+            try:
+                plan = ibm.ibm_plan_create(n, n, n, g[3:], ibm.IBM_FP32_REFINED, 1)
+            finally:
+                del os.environ["IBM_PLANE_MODE"]
+            phi = torch.empty_like(b)
+            for _ in range(5):
+                ibm.ibm_poisson_solve(plan, b, phi)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(reps):
+                ibm.ibm_poisson_solve(plan, b, phi)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / reps
+            ibm.ibm_plan_profile(plan, True)
+            ibm.ibm_plan_profile_read(plan)
+            for _ in range(reps):
+                ibm.ibm_poisson_solve(plan, b, phi)
+            torch.cuda.synchronize()
+            prof = ibm.ibm_plan_profile_read(plan)
+            ibm.ibm_plan_profile(plan, False)
+            ibm.ibm_plan_destroy(plan)
+            sols[name] = phi.double()
+            row[name] = {"solve_us": ms * 1e3, "forward_us_per_solve": prof["forward"][0] / reps * 1e3,
+                         "inverse_us_per_solve": prof["inverse"][0] / reps * 1e3}
+        row["dft_vs_fft_rel_l2"] = float(torch.linalg.vector_norm(sols["dft_tc"] - sols["fft_plane"])
+                                         / torch.linalg.vector_norm(sols["fft_plane"]))
+        out["%d^3" % n] = row
+    return out
 
 
 def large_plate(ibm, torch, stages=48, v_in=None):
@@ -851,12 +923,15 @@ def main():
     ap.add_argument("--solve", type=int, metavar="N",
                     help="profiling aid: two refined FP32 Poisson solves on an N^3 grid (the first one warms up), "
                          "then exit; `ncu -s <launches of one solve>` captures the second")
+    ap.add_argument("--plane-mode", type=int, default=None, metavar="M",
+                    help="with --solve: force plane mode M of the transforms (0 split, 1 one CTA per plane, "
+                         "2/4/8 cluster, -1 tensor-core DFT products)")
     args = ap.parse_args()
     if args.ncu_summary:
         ncu_summary(args.ncu_summary, args.steps)
         return
     if args.solve:
-        solve_twice(args.solve)
+        solve_twice(args.solve, args.plane_mode)
         return
     if args.warmup < 3:
         args.warmup = 3

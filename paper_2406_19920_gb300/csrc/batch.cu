@@ -3,10 +3,11 @@
 // Autotuner.  For a grid shape and precision it times every available
 // variant of the solve -- pencil kernel (two-ended sweep on a shared tile,
 // the streaming two-ended sweep, or the warp-parallel substructured solve) x
-// plane mode (split x and z passes, one CTA per y-plane, or a cluster of C
-// CTAs per plane) -- on scratch buffers, keeps the fastest, and
-// remembers it for the process (optionally in the text file named by
-// IBM_TUNE_CACHE, one line per shape).
+// plane mode (split x and z passes, one CTA per y-plane, a cluster of C
+// CTAs per plane, or tensor-core DFT products) -- on scratch buffers, keeps
+// the fastest, and remembers it for the process (optionally in the text
+// file named by IBM_TUNE_CACHE, one line per shape).  IBM_TUNE_DFT=0 leaves
+// the tensor-core DFT mode out of the candidates (CUDA-core FFTs only).
 //
 // Batch.  ibm_batch_create makes one plan per instance (each with its own
 // workspace, so instances never share scratch) and tunes every distinct
@@ -29,11 +30,16 @@
 namespace ibm {
 
 struct TuneKey {
-  int nx, ny, nz, precision, refine;
+  int nx, ny, nz, precision, refine, dft;  // dft: the tensor-core DFT mode was a candidate
   bool operator<(const TuneKey &o) const {
-    return std::tie(nx, ny, nz, precision, refine) < std::tie(o.nx, o.ny, o.nz, o.precision, o.refine);
+    return std::tie(nx, ny, nz, precision, refine, dft) < std::tie(o.nx, o.ny, o.nz, o.precision, o.refine, o.dft);
   }
 };
+
+static bool tune_dft_allowed() {
+  const char *e = getenv("IBM_TUNE_DFT");
+  return !(e && atoi(e) == 0);
+}
 static std::mutex g_tune_mu;
 static std::map<TuneKey, TuneChoice> g_tune;
 static bool g_tune_loaded = false;
@@ -47,8 +53,8 @@ static void tune_load_locked() {
   if (!f) return;
   TuneKey k;
   TuneChoice c;
-  while (fscanf(f, "%d %d %d %d %d %d %d %lf", &k.nx, &k.ny, &k.nz, &k.precision, &k.refine, &c.pencil_mode,
-                &c.use_plane, &c.ms) == 8)
+  while (fscanf(f, "%d %d %d %d %d %d %d %d %lf", &k.nx, &k.ny, &k.nz, &k.precision, &k.refine, &k.dft,
+                &c.pencil_mode, &c.use_plane, &c.ms) == 9)
     g_tune[k] = c;
   fclose(f);
 }
@@ -59,8 +65,8 @@ static void tune_save_locked() {
   FILE *f = fopen(path, "w");
   if (!f) return;
   for (auto &kv : g_tune)
-    fprintf(f, "%d %d %d %d %d %d %d %.6f\n", kv.first.nx, kv.first.ny, kv.first.nz, kv.first.precision,
-            kv.first.refine, kv.second.pencil_mode, kv.second.use_plane, kv.second.ms);
+    fprintf(f, "%d %d %d %d %d %d %d %d %.6f\n", kv.first.nx, kv.first.ny, kv.first.nz, kv.first.precision,
+            kv.first.refine, kv.first.dft, kv.second.pencil_mode, kv.second.use_plane, kv.second.ms);
   fclose(f);
 }
 
@@ -74,13 +80,15 @@ static bool segmented_available(const ibm_plan_s *p) {
 }
 
 static int plane_candidates(const ibm_plan_s *p, int *modes) {
-  return p->precision == IBM_FP64 ? plane_modes<double>(p->nx, p->nz, modes) : plane_modes<float>(p->nx, p->nz, modes);
+  int n = p->precision == IBM_FP64 ? plane_modes<double>(p->nx, p->nz, modes) : plane_modes<float>(p->nx, p->nz, modes);
+  if (!tune_dft_allowed()) n = (int)(std::remove(modes, modes + n, kPlaneDft) - modes);
+  return n;
 }
 
 // Times the Poisson solve of plan p for every variant and applies the
 // fastest to p.  Synchronises the device; allocates two scratch fields.
 int tune_plan(ibm_plan_s *p, TuneChoice *out) {
-  const TuneKey key{p->nx, p->ny, p->nz, p->precision, p->refine};
+  const TuneKey key{p->nx, p->ny, p->nz, p->precision, p->refine, tune_dft_allowed() ? 1 : 0};
   {
     std::lock_guard<std::mutex> lock(g_tune_mu);
     tune_load_locked();
@@ -244,7 +252,7 @@ int ibm_batch_create(int count, const int *dims, const double *h, int precision,
   std::map<TuneKey, TuneChoice> chosen;
   for (int i = 0; i < count; ++i) {
     ibm_plan_s *p = b->plans[i];
-    const TuneKey k{p->nx, p->ny, p->nz, p->precision, p->refine};
+    const TuneKey k{p->nx, p->ny, p->nz, p->precision, p->refine, tune_dft_allowed() ? 1 : 0};
     auto it = chosen.find(k);
     if (it == chosen.end()) {
       TuneChoice c;

@@ -18,8 +18,8 @@
 // in registers (mma3, acc_ld); the unrefined error then stays within a few
 // times the FFT path's.
 //
-// One CTA owns a group of G = min(128/nz, 128/P) consecutive y-planes, so
-// both MMAs of a direction have M = 128 rows:
+// One CTA owns a group of G <= min(128/nz, 128/P) consecutive y-planes
+// (dft_shape), so both MMAs of a direction fit M = 128 rows:
 //   forward  stage 1: rows (g, k) of the planes' x rows (G nz <= 128),
 //                     N = 2 P8 columns (c, m): Y_c[g][k][m]
 //            stage 2: rows (g, m) (G P <= 128), N = 2 nz columns (c', kz),
@@ -87,10 +87,17 @@ struct DftShape {
   uint32_t r1i, r2i, r3i;  // inverse
 };
 
+static int dft_grid_cap();
+
+// Planes per CTA: one while that gives at most two CTAs per SM (the chain
+// of copies, MMAs and tensor-memory reads of a group is latency-bound, so
+// more CTAs beat fuller MMAs), else the fewest that keep to that bound, at
+// most min(128/nz, 128/P) (both MMAs of a direction within M = 128 rows).
 static DftShape dft_shape(int nx, int ny, int nz) {
   DftShape d;
   d.nx = nx; d.nz = nz; d.P = nx / 2 + 1;
-  d.G = std::min(128 / nz, 128 / d.P);
+  const int gmax = std::min(128 / nz, 128 / d.P);
+  d.G = std::max(1, std::min(gmax, (ny + dft_grid_cap() - 1) / dft_grid_cap()));
   d.ngroups = (ny + d.G - 1) / d.G;
   d.P8 = rup(d.P, 8); d.N1 = 2 * d.P8;
   d.P4 = rup(d.P, 4); d.Kf = 2 * d.P4; d.Nf = rup(nx, 16);
