@@ -148,6 +148,16 @@ size_t ibm_plan_workspace_bytes(ibm_plan plan);
  * one of its bounded waits (IBM_ERR_TIMEOUT; the word is then cleared). */
 int ibm_plan_check(ibm_plan plan);
 
+/* Diagnostic of the bounded waits (no fault is involved): launches one CTA
+ * that allocates tensor memory, waits on an mbarrier that nothing completes,
+ * gives up after limit_ms milliseconds (0 < limit_ms <= 5000), records the
+ * timeout in the plan's error word, frees the tensor memory and returns.
+ * The next ibm_plan_check (after the stream has drained) returns
+ * IBM_ERR_TIMEOUT; the plan and the context stay usable.  This is the path
+ * every kernel that waits on bulk copies or tensor-core work takes when a
+ * wait runs out. */
+int ibm_selftest_timeout(ibm_plan plan, double limit_ms, void *stream);
+
 /* Per-kernel timing (tracing).  While enabled, every kernel the plan
  * launches is bracketed by a pair of CUDA events on its stream; the pairs
  * are accumulated per kernel kind (IBM_K_*).  ibm_plan_profile_read

@@ -83,6 +83,7 @@ _SIG = {
     "ibm_plan_set_spread": (_I, [_P, _I]),
     "ibm_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
     "ibm_plan_check": (_I, [_P]),
+    "ibm_selftest_timeout": (_I, [_P, _D, _P]),
     "ibm_plan_profile": (_I, [_P, _I]),
     "ibm_plan_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ibm_poisson_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
@@ -269,6 +270,10 @@ def ibm_substep_inout(plan, state, inout, rk_stage, dt, nu, markers, stream=None
                                    ctypes.byref(markers), _stream(stream),
                                    ctypes.byref(inf) if inf is not None else None))
     return inf.as_dict() if inf is not None else None
+
+
+def ibm_selftest_timeout(plan, limit_ms, stream=None):
+    return _check(lib().ibm_selftest_timeout(plan, float(limit_ms), _stream(stream)))
 
 
 def ibm_batch_create(dims, hs, precision=IBM_FP32_REFINED, refine_iters=1):

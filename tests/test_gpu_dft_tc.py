@@ -139,3 +139,34 @@ def test_dft_mode_in_place_and_repeated():
         assert all(torch.equal(outs[0], o) for o in outs[1:])
     finally:
         ibm.ibm_plan_destroy(plan)
+
+
+def test_bounded_wait_runs_out_and_plan_stays_usable():
+    """A wait on an mbarrier that nothing completes (the bounded-wait path of
+    the tensor-core and bulk-copy kernels) gives up after its limit,
+    reports IBM_ERR_TIMEOUT through the plan's error word and frees its
+    tensor memory; the same plan then solves (in the tensor-core DFT mode)
+    to the oracle."""
+    import time
+    nx, ny, nz = 32, 16, 32
+    g = grid(nx, ny, nz)
+    plan = _plan(nx, ny, nz, g, 1, DFT)
+    try:
+        t0 = time.perf_counter()
+        ibm.ibm_selftest_timeout(plan, 50.0)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        assert 0.04 <= dt < 5.0, dt
+        with pytest.raises(ibm.IbmError) as e:
+            ibm.ibm_plan_check(plan)
+        assert e.value.code == ibm.IBM_ERR_TIMEOUT
+        ibm.ibm_plan_check(plan)  # the word was cleared
+        b32 = (synth.white_noise(nx, ny, nz, workload=94, stream=0) + 0.2).astype(np.float32).astype(np.float64)
+        ref, _ = O.poisson_solve(b32, g)
+        assert rel_l2(_poisson(plan, b32), ref) <= TOL_FP32
+        ibm.ibm_plan_check(plan)
+        with pytest.raises(ibm.IbmError) as e:
+            ibm.ibm_selftest_timeout(plan, 0.0)
+        assert e.value.code == ibm.IBM_ERR_ARG
+    finally:
+        ibm.ibm_plan_destroy(plan)
