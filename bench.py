@@ -538,9 +538,11 @@ def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None):
 
 
 def spread_compare(ibm, torch):
-    """Spreading (Eq. 2d) of a Fibonacci sphere at 128^3, FP32: the atomic L1
-    kernel against the deterministic Eulerian gather, us per call and markers
-    per second, and whether four repeated calls give the same bytes."""
+    """Spreading (Eq. 2d) of a Fibonacci sphere at 128^3, FP32: the default
+    atomic kernel (shared-memory pre-aggregation per CTA), the paper's L1
+    kernel (direct global atomics) and the deterministic Eulerian gather; us
+    per call, markers per second, and whether four repeated calls give the
+    same bytes."""
     from paper_2406_19920_gb300 import synth
     res = {}
     g = workload_grid()
@@ -550,7 +552,8 @@ def spread_compare(ibm, torch):
         plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
         Xd, Fd, dVd = (torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float32) for a in (X, F, dV))
         row = {}
-        for name, mode in (("atomic", ibm.IBM_SPREAD_ATOMIC), ("gather", ibm.IBM_SPREAD_GATHER)):
+        for name, mode in (("atomic", ibm.IBM_SPREAD_ATOMIC), ("atomic_direct", ibm.IBM_SPREAD_ATOMIC_DIRECT),
+                           ("gather", ibm.IBM_SPREAD_GATHER)):
             ibm.ibm_plan_set_spread(plan, mode)
             outs = []
             for _ in range(4):

@@ -125,10 +125,17 @@ int ibm_plan_destroy(ibm_plan plan);
 /* Select the delta kernel used by ibm_interp / ibm_spread / ibm_substep. */
 int ibm_plan_set_delta(ibm_plan plan, int kernel);
 /* Spreading (Eq. 2d) used by ibm_spread / ibm_substep.
- *   IBM_SPREAD_ATOMIC  (default) the paper's L1 kernel (Sec. 2.3.2): one
- *                      thread per (marker, component) adds its S^3 shares
- *                      with global atomics; the order of the additions, and so
- *                      the last bits of f, vary from run to run.
+ *   IBM_SPREAD_ATOMIC  (default) atomic spreading.  From 40,000 markers on,
+ *                      with shared-memory pre-aggregation: a CTA of 256
+ *                      (marker, component) entries whose stencils fit a small
+ *                      box adds them into shared memory first and then each
+ *                      non-zero box point to f with one global atomic; other
+ *                      CTAs, and smaller marker sets, add directly as
+ *                      IBM_SPREAD_ATOMIC_DIRECT.  The order of the additions,
+ *                      and so the last bits of f, vary from run to run.
+ *   IBM_SPREAD_ATOMIC_DIRECT  the paper's L1 kernel (Sec. 2.3.2) as it
+ *                      stands: one thread per (marker, component) adds its
+ *                      S^3 shares with global atomics.
  *   IBM_SPREAD_GATHER  the alternative Sec. 2.3.2 describes and sets aside:
  *                      one thread per Eulerian point gathers the shares of the
  *                      markers whose stencils cover it.  Markers are binned by
@@ -139,7 +146,7 @@ int ibm_plan_set_delta(ibm_plan plan, int kernel);
  *                      about 12 bytes per brick and 40 bytes per marker
  *                      component (allocated on first use; IBM_ERR_OOM if it
  *                      cannot be). */
-enum { IBM_SPREAD_ATOMIC = 0, IBM_SPREAD_GATHER = 1 };
+enum { IBM_SPREAD_ATOMIC = 0, IBM_SPREAD_GATHER = 1, IBM_SPREAD_ATOMIC_DIRECT = 2 };
 int ibm_plan_set_spread(ibm_plan plan, int mode);
 /* Bytes of device memory the plan holds. */
 size_t ibm_plan_workspace_bytes(ibm_plan plan);

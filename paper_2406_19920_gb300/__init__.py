@@ -22,7 +22,7 @@ IBM_BC_PXZ_WALL_Y, IBM_BC_TRIPLY_PERIODIC = 1, 2
 IBM_FP64, IBM_FP32_REFINED = 0, 1
 IBM_FIELD_CELL_NEUMANN, IBM_FIELD_CELL_DIRICHLET, IBM_FIELD_FACE_DIRICHLET, IBM_FIELD_PERIODIC = 0, 1, 2, 3
 IBM_DELTA_ROMA3, IBM_DELTA_PESKIN4 = 0, 1
-IBM_SPREAD_ATOMIC, IBM_SPREAD_GATHER = 0, 1
+IBM_SPREAD_ATOMIC, IBM_SPREAD_GATHER, IBM_SPREAD_ATOMIC_DIRECT = 0, 1, 2
 IBM_MOTION_STATIC, IBM_MOTION_TRANSLATE, IBM_MOTION_HEAVE = 0, 1, 2
 IBM_REQ_POISSON, IBM_REQ_HELMHOLTZ, IBM_REQ_SUBSTEP = 0, 1, 2
 

@@ -15,6 +15,7 @@
 // X/h; the weights and sums run in the plan precision.  Spreading
 // accumulates with global atomics as in the paper's L1 kernel (Sec. 2.3.2).
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "plan.h"
@@ -202,6 +203,131 @@ k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, con
 #pragma unroll
       for (int qx = 0; qx < S; ++qx) atomicAdd(f + row + ix[qx], a * wx[qx]);
     }
+  }
+}
+
+// Spreading with shared-memory pre-aggregation (the default atomic path).
+// Markers that are close in index are usually close in space (a surface
+// mesh, a lattice, a Fibonacci sphere's latitude bands), so the 256
+// entries of a CTA touch a small box of grid points while many markers hit
+// the same points.  The CTA finds the bounding box of its stencils (in
+// unwrapped index space, all three components together); if the box fits
+// the shared budget, the stencils accumulate there with shared-memory
+// atomics and each non-zero box point is added to the field with one
+// global atomic (x and z wrapped, points beyond the walls dropped as in
+// k_spread).  Otherwise the CTA falls back to k_spread's direct global
+// atomics.  Same sums in another order (FP32 atomics are unordered anyway).
+// Measured on GB300 (FP32, a Fibonacci sphere of radius 0.25 at 128^3): 20k
+// markers 21.2 us against 16.7 us for direct atomics (little contention:
+// the extra phases cost more than they save); 100k markers 38.3 us against
+// 81.6 us.  IBM_SPREAD_ATOMIC therefore takes this kernel from
+// kSpreadBoxMinMarkers markers on.
+constexpr int kSpreadBoxMinMarkers = 40000;
+constexpr int kSpreadBoxBytes = 40 * 1024;  // within the default 48 KB limit with the static part
+
+template <typename T, int S>
+__global__ void __launch_bounds__(256)
+k_spread_box(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, const T *__restrict__ dV, T *fu,
+             T *fv, T *fw, T scale) {
+  extern __shared__ __align__(16) unsigned char box_raw[];
+  T *box = reinterpret_cast<T *>(box_raw);
+  __shared__ int red[6][8];
+  pdl_wait();
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool valid = t < 3 * n;
+  const int m = valid ? t / 3 : 0, c = valid ? t - 3 * m : 0;
+  int bx = 0, by = 0, bz = 0;
+  T fx = 0, fy = 0, fz = 0, amp = 0;
+  if (valid) {
+    stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], bx, by, bz, fx, fy, fz);
+    amp = scale * F[t] * dV[m] * (T)g.vol_inv;
+  }
+  // bounding box of the CTA's stencil origins
+  int v[6] = {valid ? bx : INT_MAX, valid ? by : INT_MAX, valid ? bz : INT_MAX,
+              valid ? -bx : INT_MAX, valid ? -by : INT_MAX, valid ? -bz : INT_MAX};
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    v[q] = __reduce_min_sync(0xffffffffu, v[q]);
+    if (lane == 0) red[q][warp] = v[q];
+  }
+  __syncthreads();
+  int lo[3], dim[3];
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    int mn = INT_MAX, mxn = INT_MAX;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+      mn = min(mn, red[q][w]);
+      mxn = min(mxn, red[q + 3][w]);
+    }
+    lo[q] = mn;
+    dim[q] = -mxn - mn + S;  // (max - min) + S points along this axis
+  }
+  const long vol = (long)dim[0] * dim[1] * dim[2];
+  const bool use_box = vol > 0 && 3 * vol * (long)sizeof(T) <= kSpreadBoxBytes && dim[0] <= g.nx && dim[2] <= g.nz;
+  T wx[S], wz[S];
+#pragma unroll
+  for (int q = 0; q < S; ++q) {
+    wx[q] = S == 3 ? phi_roma3<T>(fx - (T)q) : phi_peskin4<T>(fx - (T)q);
+    wz[q] = S == 3 ? phi_roma3<T>(fz - (T)q) : phi_peskin4<T>(fz - (T)q);
+  }
+  const int jlo = c == 1 ? 1 : 0;
+  if (!use_box) {
+    if (!valid) return;
+    T *f = c == 0 ? fu : c == 1 ? fv : fw;
+    int ix[S], kz[S];
+#pragma unroll
+    for (int q = 0; q < S; ++q) {
+      ix[q] = wrap(bx + q, g.nx);
+      kz[q] = wrap(bz + q, g.nz);
+    }
+#pragma unroll
+    for (int qy = 0; qy < S; ++qy) {
+      const int j = by + qy;
+      if (j < jlo || j > g.ny - 1) continue;
+      const T wy = S == 3 ? phi_roma3<T>(fy - (T)qy) : phi_peskin4<T>(fy - (T)qy);
+#pragma unroll
+      for (int qz = 0; qz < S; ++qz) {
+        const int row = (j * g.nz + kz[qz]) * g.nx;
+        const T a = amp * wy * wz[qz];
+#pragma unroll
+        for (int qx = 0; qx < S; ++qx) atomicAdd(f + row + ix[qx], a * wx[qx]);
+      }
+    }
+    return;
+  }
+  const int nbox = 3 * (int)vol;
+  for (int e = threadIdx.x; e < nbox; e += blockDim.x) box[e] = (T)0;
+  __syncthreads();
+  if (valid) {
+    T *bc = box + c * (int)vol;
+    const int ox = bx - lo[0], oy = by - lo[1], oz = bz - lo[2];
+#pragma unroll
+    for (int qy = 0; qy < S; ++qy) {
+      const T wy = S == 3 ? phi_roma3<T>(fy - (T)qy) : phi_peskin4<T>(fy - (T)qy);
+#pragma unroll
+      for (int qz = 0; qz < S; ++qz) {
+        T *rowp = bc + ((oy + qy) * dim[2] + (oz + qz)) * dim[0] + ox;
+        const T a = amp * wy * wz[qz];
+#pragma unroll
+        for (int qx = 0; qx < S; ++qx) atomicAdd(rowp + qx, a * wx[qx]);
+      }
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < nbox; e += blockDim.x) {
+    const T val = box[e];
+    if (val == (T)0) continue;
+    const int cc = e / (int)vol;
+    int r = e - cc * (int)vol;
+    const int dy = r / (dim[2] * dim[0]);
+    r -= dy * dim[2] * dim[0];
+    const int dz = r / dim[0], dx = r - dz * dim[0];
+    const int j = lo[1] + dy;
+    if (j < (cc == 1 ? 1 : 0) || j > g.ny - 1) continue;
+    const int i = wrap(lo[0] + dx, g.nx), k = wrap(lo[2] + dz, g.nz);
+    T *f = cc == 0 ? fu : cc == 1 ? fv : fw;
+    atomicAdd(f + ((size_t)j * g.nz + k) * g.nx + i, val);
   }
 }
 
@@ -588,10 +714,19 @@ cudaError_t launch_spread(const ibm_plan_s *p, int n, const T *X, const T *F, co
   }
   const IbmGrid g = ibm_grid(p);
   const int tb = ceil_div(3 * n, 256);
+  if (p->spread == IBM_SPREAD_ATOMIC_DIRECT || n < kSpreadBoxMinMarkers) {
+    if (p->delta == IBM_DELTA_PESKIN4)
+      IBM_KTRY(launch_pdl(k_spread<T, 4>, tb, 256, 0, st, g, n, X, F, dV, fu, fv, fw, (T)scale));
+    else
+      IBM_KTRY(launch_pdl(k_spread<T, 3>, tb, 256, 0, st, g, n, X, F, dV, fu, fv, fw, (T)scale));
+    return cudaGetLastError();
+  }
   if (p->delta == IBM_DELTA_PESKIN4)
-    IBM_KTRY(launch_pdl(k_spread<T, 4>, tb, 256, 0, st, g, n, X, F, dV, fu, fv, fw, (T)scale));
+    IBM_KTRY(launch_pdl(k_spread_box<T, 4>, tb, 256, (size_t)kSpreadBoxBytes, st, g, n, X, F, dV, fu, fv, fw,
+                        (T)scale));
   else
-    IBM_KTRY(launch_pdl(k_spread<T, 3>, tb, 256, 0, st, g, n, X, F, dV, fu, fv, fw, (T)scale));
+    IBM_KTRY(launch_pdl(k_spread_box<T, 3>, tb, 256, (size_t)kSpreadBoxBytes, st, g, n, X, F, dV, fu, fv, fw,
+                        (T)scale));
   return cudaGetLastError();
 }
 

@@ -515,7 +515,7 @@ int ibm_plan_set_delta(ibm_plan plan, int kernel) {
 
 int ibm_plan_set_spread(ibm_plan plan, int mode) {
   if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_set_spread: NULL plan");
-  if (mode != IBM_SPREAD_ATOMIC && mode != IBM_SPREAD_GATHER)
+  if (mode != IBM_SPREAD_ATOMIC && mode != IBM_SPREAD_GATHER && mode != IBM_SPREAD_ATOMIC_DIRECT)
     return set_error(IBM_ERR_ARG, "ibm_plan_set_spread: mode %d", mode);
   plan->spread = mode;
   return IBM_OK;

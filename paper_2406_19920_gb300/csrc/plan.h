@@ -46,7 +46,7 @@ struct ibm_plan_s {
   void *sub[4];      // substep fields du, dv, dw, phi (allocated on first substep)
   void *mkbuf;       // marker force scratch [n][3] when the caller passes none
   size_t mkcap;      // bytes of mkbuf
-  int spread = 0;    // IBM_SPREAD_ATOMIC / IBM_SPREAD_GATHER
+  int spread = 0;    // IBM_SPREAD_ATOMIC / IBM_SPREAD_GATHER / IBM_SPREAD_ATOMIC_DIRECT
   void *gbuf = nullptr;  // gather-spreading workspace (bins, sorted entries, stencil records)
   size_t gcap = 0;       // bytes of gbuf
   void *twx, *twz;   // twiddles W_N^m (plan precision)

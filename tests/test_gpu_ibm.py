@@ -19,6 +19,7 @@ CASES = [
     (32, 32, 32, 1000, 0.25),      # workload-0 sphere
     (64, 48, 96, 4000, 0.4),
     (128, 128, 128, 20000, 0.25),  # workload-1 sphere (dense markers)
+    (96, 64, 96, 48000, 0.3),      # above the pre-aggregation threshold (40k markers)
 ]
 
 
@@ -32,7 +33,11 @@ def _markers(g, n, radius, wl):
 @pytest.mark.parametrize("case", CASES)
 @pytest.mark.parametrize("kernel", [ibm.IBM_DELTA_ROMA3, ibm.IBM_DELTA_PESKIN4])
 @pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
-def test_interp_spread_match_oracle(case, kernel, prec):
+@pytest.mark.parametrize("mode", [ibm.IBM_SPREAD_ATOMIC, ibm.IBM_SPREAD_ATOMIC_DIRECT])
+def test_interp_spread_match_oracle(case, kernel, prec, mode):
+    """Interpolation and the two atomic spreading kernels (shared-memory
+    pre-aggregation per CTA, and the direct global atomics) against the
+    oracle."""
     nx, ny, nz, n, radius = case
     g = grid(nx, ny, nz)
     dt = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
@@ -48,6 +53,7 @@ def test_interp_spread_match_oracle(case, kernel, prec):
     plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, 1)
     try:
         ibm.ibm_plan_set_delta(plan, kernel)
+        ibm.ibm_plan_set_spread(plan, mode)
         Xd, ud, vd, wd = dev(X, dt), dev(u, dt), dev(v, dt), dev(w, dt)
         U = torch.empty((n, 3), dtype=dt, device="cuda")
         ibm.ibm_interp(plan, n, Xd, ud, vd, wd, U)
@@ -158,8 +164,11 @@ def test_gather_spread_is_bitwise_reproducible():
         ibm.ibm_plan_destroy(plan)
 
 
-def test_gather_spread_walls_and_wrap():
-    """Markers at the periodic ends and within 1.5 h of both walls."""
+@pytest.mark.parametrize("mode", [ibm.IBM_SPREAD_GATHER, ibm.IBM_SPREAD_ATOMIC, ibm.IBM_SPREAD_ATOMIC_DIRECT])
+def test_spread_walls_and_wrap(mode):
+    """Markers at the periodic ends and within 1.5 h of both walls, in every
+    spreading mode (the pre-aggregating CTA's box straddles the periodic
+    ends here, so it falls back to direct atomics)."""
     g = grid(16, 16, 16)
     X = np.array([[0.01, 0.9, 0.02], [2 * math.pi - 0.03, 0.95, 2 * math.pi - 0.01],
                   [1.0, 0.02, 3.0], [2.0, 2.0 - 0.03, 4.0], [3.0, 1.0, 0.0]])
@@ -171,7 +180,7 @@ def test_gather_spread_walls_and_wrap():
         fref = O.spread(Xc, Fc, dVc, g)
         plan = ibm.ibm_plan_create(16, 16, 16, g[3:], prec, 0 if prec == ibm.IBM_FP64 else 1)
         try:
-            ibm.ibm_plan_set_spread(plan, ibm.IBM_SPREAD_GATHER)
+            ibm.ibm_plan_set_spread(plan, mode)
             f = [torch.zeros((16, 16, 16), dtype=dt, device="cuda") for _ in range(3)]
             ibm.ibm_spread(plan, 5, dev(Xc, dt), dev(Fc, dt), dev(dVc, dt), *f)
             torch.cuda.synchronize()
@@ -180,3 +189,48 @@ def test_gather_spread_walls_and_wrap():
                 assert rel_l2(host(got), ref) <= tol
         finally:
             ibm.ibm_plan_destroy(plan)
+
+
+@pytest.mark.parametrize("prec", [ibm.IBM_FP64, ibm.IBM_FP32_REFINED])
+def test_box_spread_near_walls_and_unordered(prec):
+    """Pre-aggregated spreading (IBM_SPREAD_ATOMIC from 40k markers on): a
+    compact cluster of markers against each wall (box rows beyond the stored
+    planes are dropped at the flush) and a dense sphere's markers in random
+    order (most CTA boxes too large: the fallback to direct atomics)."""
+    nx, ny, nz = 48, 40, 32
+    g = grid(nx, ny, nz)
+    dt = torch.float64 if prec == ibm.IBM_FP64 else torch.float32
+    npdt = np.float64 if prec == ibm.IBM_FP64 else np.float32
+    tol = TOL_IBM_FP64 if prec == ibm.IBM_FP64 else TOL_IBM_FP32
+    r = np.random.default_rng(7)
+    n = 45000
+    X = np.column_stack([3.0 + 0.2 * r.random(n), np.where(np.arange(n) < n // 2, 0.01, 1.99) + 0.02 * r.random(n),
+                         2.0 + 0.2 * r.random(n)])
+    F = r.standard_normal((n, 3))
+    dV = np.full(n, 1e-3)
+    X, F, dV = (a.astype(npdt).astype(np.float64) for a in (X, F, dV))
+    fref = O.spread(X, F, dV, g)
+    plan = ibm.ibm_plan_create(nx, ny, nz, g[3:], prec, 1)
+    try:
+        f = [torch.zeros((ny, nz, nx), dtype=dt, device="cuda") for _ in range(3)]
+        ibm.ibm_spread(plan, n, dev(X, dt), dev(F, dt), dev(dV, dt), *f)
+        torch.cuda.synchronize()
+        for got, ref in zip(f, fref):
+            assert rel_l2(host(got), ref) <= tol
+        assert np.all(host(f[1])[0] == 0.0)
+    finally:
+        ibm.ibm_plan_destroy(plan)
+    g = grid(128, 128, 128)
+    X, dV, F = _markers(g, 45000, 0.25, wl=61)
+    perm = np.random.default_rng(8).permutation(45000)
+    X, dV, F = (np.ascontiguousarray(a[perm]).astype(npdt).astype(np.float64) for a in (X, dV, F))
+    fref = O.spread(X, F, dV, g)
+    plan = ibm.ibm_plan_create(128, 128, 128, g[3:], prec, 1)
+    try:
+        f = [torch.zeros((128, 128, 128), dtype=dt, device="cuda") for _ in range(3)]
+        ibm.ibm_spread(plan, 45000, dev(X, dt), dev(F, dt), dev(dV, dt), *f)
+        torch.cuda.synchronize()
+        for got, ref in zip(f, fref):
+            assert rel_l2(host(got), ref) <= tol
+    finally:
+        ibm.ibm_plan_destroy(plan)
