@@ -293,8 +293,8 @@ int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu
  * v = v_in through the y = 0 face (u = w = 0 on that wall) and an outlet at
  * y = Ly advected with d phi/dt + c_out d phi/dy = 0.  u_out, w_out hold u
  * and w on the outlet wall, v_out the wall-normal velocity on the outlet
- * face: device planes [nz][nx] of the plan precision, owned by the caller,
- * updated in place every stage. */
+ * face: device planes [nz][nx] of the plan precision, 16-byte aligned,
+ * owned by the caller, updated in place every stage. */
 typedef struct {
   double v_in;   /* inflow speed (finite)                                   */
   double c_out;  /* outlet advection speed (finite, >= 0)                   */
@@ -312,8 +312,9 @@ typedef struct {
  * see them; the Helmholtz increment solves need none (the data are the
  * same at both ends of the increment).  The paper gives the outlet's
  * discretisation only by reference; the upwind form is the reading used
- * here.  Returns IBM_ERR_ARG for NULL io or planes, a non-finite v_in or a
- * negative or non-finite c_out; otherwise as ibm_substep. */
+ * here.  Returns IBM_ERR_ARG for NULL io, NULL or misaligned planes, a
+ * non-finite v_in or a negative or non-finite c_out; otherwise as
+ * ibm_substep. */
 int ibm_substep_inout(ibm_plan plan, ibm_state *st, const ibm_inout *io, int rk_stage, double dt,
                       double nu, ibm_markers *mk, void *stream, ibm_info *info);
 

@@ -310,6 +310,117 @@ k_project(Geo g, T *__restrict__ u, T *__restrict__ v, T *__restrict__ w, T *__r
   p[idx] += f0 - cvisc * lap;
 }
 
+// FP32 versions of E2 and E3 with four consecutive x points per thread:
+// float4 rows, the x neighbours from the same float4 plus one or two
+// scalars, shared index arithmetic (the one-point kernels are load-latency
+// bound).  Each point's arithmetic is the one-point kernel's, in the same
+// order.  Grid (ceil(nz nx / 4 / 128), ny), 128 threads; nx % 4 == 0 and
+// 16-byte aligned fields.
+__device__ __forceinline__ float4 ld4(const float *p) { return *reinterpret_cast<const float4 *>(p); }
+__device__ __forceinline__ float comp4(const float4 &a, int q) { return q == 0 ? a.x : q == 1 ? a.y : q == 2 ? a.z : a.w; }
+__device__ __forceinline__ void set4(float4 &a, int q, float v) {
+  if (q == 0) a.x = v; else if (q == 1) a.y = v; else if (q == 2) a.z = v; else a.w = v;
+}
+
+__global__ void __launch_bounds__(128)
+k_divergence_f32v(Geo g, const float *__restrict__ u_, const float *__restrict__ v_, const float *__restrict__ w_,
+                  float *b, float inv_scale, float ihx_t, float ihy_t, float ihz_t, ff ihx, ff ihy, ff ihz,
+                  double *dmax, float v_lo, const float *__restrict__ v_hi) {
+  pdl_wait();
+  const int q4 = g.nx >> 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  float mx = 0.f;
+  if (t < q4 * g.nz) {
+    const int k = t / q4, i0 = 4 * (t - k * q4);
+    const size_t pl = (size_t)g.nx * g.nz;
+    const size_t at = (size_t)j * pl + (size_t)k * g.nx + i0;
+    const float4 uc = ld4(u_ + at);
+    const float uE = u_[at - i0 + (i0 + 4 == g.nx ? 0 : i0 + 4)];
+    const float4 vs = j == 0 ? make_float4(v_lo, v_lo, v_lo, v_lo) : ld4(v_ + at);
+    const float4 vn = j + 1 >= g.ny ? (v_hi ? ld4(v_hi + (size_t)k * g.nx + i0) : make_float4(0.f, 0.f, 0.f, 0.f))
+                                    : ld4(v_ + at + pl);
+    const float4 wb = ld4(w_ + at);
+    const float4 wt = ld4(w_ + at + (k + 1 == g.nz ? -(long)(g.nz - 1) * g.nx : (long)g.nx));
+    float4 out;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const float ue = q < 3 ? comp4(uc, q + 1) : uE, uw = comp4(uc, q);
+      const float vnq = comp4(vn, q), vsq = comp4(vs, q), wtq = comp4(wt, q), wbq = comp4(wb, q);
+      set4(out, q, ((ue - uw) * ihx_t + (vnq - vsq) * ihy_t + (wtq - wbq) * ihz_t) * inv_scale);
+      if (dmax) mx = fmaxf(mx, DivExact<float>::eval(ue, uw, vnq, vsq, wtq, wbq, ihx, ihy, ihz));
+    }
+    if (b) *reinterpret_cast<float4 *>(b + at) = out;
+  }
+  if (dmax) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) atomic_max_nonneg(dmax, (double)mx);
+  }
+}
+
+__global__ void __launch_bounds__(128)
+k_project_f32v(Geo g, float *__restrict__ u, float *__restrict__ v, float *__restrict__ w, float *__restrict__ p,
+               const float *__restrict__ phi, float kproj, float cvisc, float v_lo) {
+  pdl_wait();
+  const int q4 = g.nx >> 2;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y;
+  if (t >= q4 * g.nz) return;
+  const int k = t / q4, i0 = 4 * (t - k * q4);
+  const size_t pl = (size_t)g.nx * g.nz;
+  const size_t at = (size_t)j * pl + (size_t)k * g.nx + i0;
+  const float ihx = (float)g.ihx, ihy = (float)g.ihy, ihz = (float)g.ihz;
+  const float4 f0 = ld4(phi + at);
+  const float fW = phi[at - i0 + (i0 == 0 ? g.nx - 1 : i0 - 1)];
+  const float fE = phi[at - i0 + (i0 + 4 == g.nx ? 0 : i0 + 4)];
+  const float4 fs = ld4(phi + at + (k == 0 ? (long)(g.nz - 1) * g.nx : -(long)g.nx));
+  const float4 fn = ld4(phi + at + (k + 1 == g.nz ? -(long)(g.nz - 1) * g.nx : (long)g.nx));
+  const float4 fd = j > 0 ? ld4(phi + at - pl) : f0;
+  const float4 fu = j + 1 < g.ny ? ld4(phi + at + pl) : f0;
+  float4 uu = ld4(u + at), vv = ld4(v + at), ww = ld4(w + at), pp = ld4(p + at);
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const float c0 = comp4(f0, q);
+    const float fw = q == 0 ? fW : comp4(f0, q - 1), fe = q < 3 ? comp4(f0, q + 1) : fE;
+    const float fsq = comp4(fs, q), fnq = comp4(fn, q), fdq = comp4(fd, q), fuq = comp4(fu, q);
+    set4(uu, q, comp4(uu, q) - kproj * (c0 - fw) * ihx);
+    set4(ww, q, comp4(ww, q) - kproj * (c0 - fsq) * ihz);
+    set4(vv, q, j > 0 ? comp4(vv, q) - kproj * (c0 - fdq) * ihy : v_lo);
+    const float lap = (fe - 2 * c0 + fw) * ihx * ihx + (fnq - 2 * c0 + fsq) * ihz * ihz + (fuq - 2 * c0 + fdq) * ihy * ihy;
+    set4(pp, q, comp4(pp, q) + (c0 - cvisc * lap));
+  }
+  *reinterpret_cast<float4 *>(u + at) = uu;
+  *reinterpret_cast<float4 *>(v + at) = vv;
+  *reinterpret_cast<float4 *>(w + at) = ww;
+  *reinterpret_cast<float4 *>(p + at) = pp;
+}
+
+// E2 / E3 launches: the four-point FP32 kernels, the one-point kernels for FP64.
+template <typename T>
+static cudaError_t launch_divergence(const Geo &g, const Launch3 &L3, const T *u, const T *v, const T *w, T *b,
+                                     double inv_scale, const ff &fx, const ff &fy, const ff &fz, double *dmax, T v_lo,
+                                     const T *v_hi, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    const dim3 grid((unsigned)ceil_div(g.nz * (g.nx / 4), 128), (unsigned)g.ny);
+    return launch_pdl(k_divergence_f32v, grid, dim3(128), 0, st, g, u, v, w, b, (float)inv_scale, (float)g.ihx,
+                      (float)g.ihy, (float)g.ihz, fx, fy, fz, dmax, v_lo, v_hi);
+  } else {
+    return launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, b, (T)inv_scale, (T)g.ihx, (T)g.ihy,
+                      (T)g.ihz, fx, fy, fz, dmax, v_lo, v_hi);
+  }
+}
+template <typename T>
+static cudaError_t launch_project(const Geo &g, const Launch3 &L3, T *u, T *v, T *w, T *p, const T *phi, double kproj,
+                                  double cvisc, T v_lo, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    const dim3 grid((unsigned)ceil_div(g.nz * (g.nx / 4), 128), (unsigned)g.ny);
+    return launch_pdl(k_project_f32v, grid, dim3(128), 0, st, g, u, v, w, p, phi, (float)kproj, (float)cvisc, v_lo);
+  } else {
+    return launch_pdl(k_project<T>, L3.grid, L3.block, 0, st, g, u, v, w, p, phi, (T)kproj, (T)cvisc, v_lo);
+  }
+}
+
 // Outlet condition of the inflow-outflow configuration (Sec. 3):
 // d phi/dt + C d phi/dy = 0 at y = Ly, advanced over the stage step
 // (alpha + beta) dt by first-order upwinding from the last interior value
@@ -475,21 +586,20 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, const ibm_inout *io, int stage
   const ff fx = ff_host(g.ihx), fy = ff_host(g.ihy), fz = ff_host(g.ihz);
   {
     ProfScope ps(p, IBM_K_DIVERGENCE, st);
-    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, rhs, (T)(1.0 / (ab * dt)),
-                            (T)g.ihx, (T)g.ihy, (T)g.ihz, fx, fy, fz, info ? p->dsc + 9 : nullptr, v_lo,
-                            (const T *)vo));
+    IBM_CUDA_TRY(launch_divergence<T>(g, L3, u, v, w, rhs, 1.0 / (ab * dt), fx, fy, fz, info ? p->dsc + 9 : nullptr,
+                                      v_lo, (const T *)vo, st));
   }
   // S2
   if ((rc = plan_solve(p, 0, 0.0, 0, rhs, phi, nullptr, st, nullptr))) return rc;
   // E3
   {
     ProfScope ps(p, IBM_K_PROJECT, st);
-    IBM_CUDA_TRY(launch_pdl(k_project<T>, L3.grid, L3.block, 0, st, g, u, v, w, pr, phi, (T)(ab * dt), (T)cH, v_lo));
+    IBM_CUDA_TRY(launch_project<T>(g, L3, u, v, w, pr, phi, ab * dt, cH, v_lo, st));
   }
   if (info) {
     IBM_CUDA_TRY(cudaEventRecord(p->ev1, st));
-    IBM_CUDA_TRY(launch_pdl(k_divergence<T>, L3.grid, L3.block, 0, st, g, u, v, w, nullptr, (T)1, (T)g.ihx,
-                            (T)g.ihy, (T)g.ihz, fx, fy, fz, p->dsc + 8, v_lo, (const T *)vo));
+    IBM_CUDA_TRY(launch_divergence<T>(g, L3, u, v, w, (T *)nullptr, 1.0, fx, fy, fz, p->dsc + 8, v_lo,
+                                      (const T *)vo, st));
     IBM_CUDA_TRY(cudaMemcpyAsync(p->hsc, p->dsc, 16 * sizeof(double), cudaMemcpyDeviceToHost, st));
     IBM_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
@@ -536,7 +646,8 @@ static int substep_entry(ibm_plan plan, ibm_state *st, const ibm_inout *io, int 
       return set_error(IBM_ERR_ARG, "ibm_substep_inout: v_in must be finite and c_out finite and >= 0");
     const void *planes[] = {io->u_out, io->v_out, io->w_out};
     for (const void *f : planes)
-      if (!f) return set_error(IBM_ERR_ARG, "ibm_substep_inout: NULL outlet plane");
+      if (!f || !aligned_to(f, 16))
+        return set_error(IBM_ERR_ARG, "ibm_substep_inout: NULL or non-16-byte-aligned outlet plane");
   }
   if (plan->precision == IBM_FP64)
     return substep_t<double>(plan, st, io, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
