@@ -129,7 +129,11 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
   T p_prev = (inside && jb > 0) ? p_[(size_t)(jb - 1) * plane + col] : (T)0;
   const T ihx = (T)g.ihx, ihy = (T)g.ihy, ihz = (T)g.ihz;
   const T ihx2 = ihx * ihx, ihy2 = ihy * ihy, ihz2 = ihz * ihz;
-  const T h = (T)0.5;
+  // Every advective flux is a product of two two-point averages,
+  // (a + b)/2 * (c + d)/2: the exact factor 1/4 is carried by the inverse
+  // spacings it is multiplied with (q* = ih* / 4), which leaves each term's
+  // rounding unchanged.
+  const T qx = ihx * (T)0.25, qy = ihy * (T)0.25, qz = ihz * (T)0.25;
   const bool n_prev = zet != (T)0;  // N^{n-2} unused (and maybe unset) at stage 1
   int pb = 0;                       // P ring slot of plane j (0 or PL)
   for (int j = jb; j < je; ++j) {
@@ -164,14 +168,14 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
         const T uup = Up[0], udn = Um[0];
         const T uu = hi ? (IO ? 2 * ug - u0 : -u0) : uup, ud = lo ? -u0 : udn;
         const T lap = (ue - 2 * u0 + uw) * ihx2 + (un - 2 * u0 + us) * ihz2 + (uu - 2 * u0 + ud) * ihy2;
-        const T uc = h * (u0 + ue), ucm = h * (uw + u0);
-        const T txx = (uc * uc - ucm * ucm) * ihx;
-        // y-flux at the faces j (zero at the wall j = 0) and j+1 (zero at j+1 = ny)
-        const T fy0 = lo ? (T)0 : (h * (Vc[-1] + v0)) * (h * (udn + u0));
-        const T fy1 = hi ? (IO ? (h * (vgw + vgo)) * ug : (T)0) : (h * (Vp[-1] + Vp[0])) * (h * (u0 + uup));
-        const T fz0 = (h * (Wc[-1] + w0)) * (h * (us + u0));
-        const T fz1 = (h * (Wc[HX - 1] + Wc[HX])) * (h * (u0 + un));
-        const T N = txx + (fy1 - fy0) * ihy + (fz1 - fz0) * ihz;
+        const T uc = u0 + ue, ucm = uw + u0;  // twice the averages
+        const T txx = (uc * uc - ucm * ucm) * qx;
+        // y-flux at the faces j (zero at the wall j = 0) and j+1 (zero at j+1 = ny), times 4
+        const T fy0 = lo ? (T)0 : (Vc[-1] + v0) * (udn + u0);
+        const T fy1 = hi ? (IO ? (vgw + vgo) * (ug + ug) : (T)0) : (Vp[-1] + Vp[0]) * (u0 + uup);
+        const T fz0 = (Wc[-1] + w0) * (us + u0);
+        const T fz1 = (Wc[HX - 1] + Wc[HX]) * (u0 + un);
+        const T N = txx + (fy1 - fy0) * qy + (fz1 - fz0) * qz;
         const T G = (p0 - Pc[-1]) * ihx;
         const T np = n_prev ? Nu[idx] : (T)0;
         du[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
@@ -183,13 +187,13 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
         const T wup = Wp[0], wdn = Wm[0];
         const T wu = hi ? (IO ? 2 * wg - w0 : -w0) : wup, wd = lo ? -w0 : wdn;
         const T lap = (we - 2 * w0 + ww) * ihx2 + (wn - 2 * w0 + ws) * ihz2 + (wu - 2 * w0 + wd) * ihy2;
-        const T wc = h * (w0 + wn), wcm = h * (ws + w0);
-        const T tzz = (wc * wc - wcm * wcm) * ihz;
-        const T fx0 = (h * (Uc[-HX] + u0)) * (h * (ww + w0));
-        const T fx1 = (h * (Uc[1 - HX] + Uc[1])) * (h * (w0 + we));
-        const T fy0 = lo ? (T)0 : (h * (Vc[-HX] + v0)) * (h * (wdn + w0));
-        const T fy1 = hi ? (IO ? (h * (vgs + vgo)) * wg : (T)0) : (h * (Vp[-HX] + Vp[0])) * (h * (w0 + wup));
-        const T N = tzz + (fx1 - fx0) * ihx + (fy1 - fy0) * ihy;
+        const T wc = w0 + wn, wcm = ws + w0;
+        const T tzz = (wc * wc - wcm * wcm) * qz;
+        const T fx0 = (Uc[-HX] + u0) * (ww + w0);
+        const T fx1 = (Uc[1 - HX] + Uc[1]) * (w0 + we);
+        const T fy0 = lo ? (T)0 : (Vc[-HX] + v0) * (wdn + w0);
+        const T fy1 = hi ? (IO ? (vgs + vgo) * (wg + wg) : (T)0) : (Vp[-HX] + Vp[0]) * (w0 + wup);
+        const T N = tzz + (fx1 - fx0) * qx + (fy1 - fy0) * qy;
         const T G = (p0 - Pc[-HX]) * ihz;
         const T np = n_prev ? Nw[idx] : (T)0;
         dw[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
@@ -203,13 +207,13 @@ k_explicit(Geo g, const T *__restrict__ u_, const T *__restrict__ v_, const T *_
         const T ve = Vc[1], vw = Vc[-1], vn = Vc[HX], vs = Vc[-HX];
         const T vu = hi ? (IO ? vgo : (T)0) : Vp[0], vd = j - 1 <= 0 ? (IO ? v_lo : (T)0) : Vm[0];
         const T lap = (ve - 2 * v0 + vw) * ihx2 + (vn - 2 * v0 + vs) * ihz2 + (vu - 2 * v0 + vd) * ihy2;
-        const T vc = h * (v0 + vu), vcm = h * (vd + v0);
-        const T tyy = (vc * vc - vcm * vcm) * ihy;
-        const T fx0 = (h * (Um[0] + u0)) * (h * (vw + v0));
-        const T fx1 = (h * (Um[1] + Uc[1])) * (h * (v0 + ve));
-        const T fz0 = (h * (Wm[0] + w0)) * (h * (vs + v0));
-        const T fz1 = (h * (Wm[HX] + Wc[HX])) * (h * (v0 + vn));
-        const T N = tyy + (fx1 - fx0) * ihx + (fz1 - fz0) * ihz;
+        const T vc = v0 + vu, vcm = vd + v0;
+        const T tyy = (vc * vc - vcm * vcm) * qy;
+        const T fx0 = (Um[0] + u0) * (vw + v0);
+        const T fx1 = (Um[1] + Uc[1]) * (v0 + ve);
+        const T fz0 = (Wm[0] + w0) * (vs + v0);
+        const T fz1 = (Wm[HX] + Wc[HX]) * (v0 + vn);
+        const T N = tyy + (fx1 - fx0) * qx + (fz1 - fz0) * qz;
         const T G = (p0 - p_prev) * ihy;
         const T np = n_prev ? Nv[idx] : (T)0;
         dv[idx] = dt * (c_visc * lap - c_pres * G - gam * N - zet * np);
