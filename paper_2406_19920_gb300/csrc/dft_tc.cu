@@ -287,7 +287,7 @@ k_dft_fwd(DftShape d, int ny, Ptr3<const float *> in_, Ptr3<float2 *> S_, const 
     __syncthreads();
     if (!consts) {
       ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_c, 0, err, kWaitNs));
-      consts = true;
+      consts = ok;  // a copy that did not land is waited for again in the epilogue
       if (!ok) break;
     }
     // stage 1: D1[(g,k)][(c,m)] = sum_i X[(g,k)][i] Fx[(c,m)][i]
@@ -416,7 +416,7 @@ k_dft_inv(DftShape d, int ny, Ptr3<float2 *> S_, Ptr3<float *> out_, Ptr3<const 
       __syncthreads();
       if (!consts) {
         ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_c, 0, err, kWaitNs));
-        consts = true;
+        consts = ok;
         if (!ok) break;
       }
       if (tid == 0) {
