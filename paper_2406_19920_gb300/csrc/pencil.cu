@@ -597,12 +597,10 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
     __syncthreads();  // the staging buffer is free: start the next tile's copies
     if (t + G < tiles)
       seg_issue<T, S>(seg_tile<T, S>(pp, S_, lamx, lamz, t + G, nblk, seg, lane, Lh), tl, tm, seg, plane);
-    const bool full = len == S;
     const T wconst = a * rcp<T>(a + ep);
     cplx<T> y;
     T prod, qlast;
     if (cw) seg_forward<T, S, true, true>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
-    else if (full) seg_forward<T, S, true, false>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
     else seg_forward<T, S, false, false>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
     cf[(0 * L + seg) * 32 + lane] = y.x;
     cf[(1 * L + seg) * 32 + lane] = y.y;
@@ -636,7 +634,6 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
     }
     cplx<T> x;
     if (cw) x = seg_middle<T, S, true, true>(v, len, wconst, wc, c);
-    else if (full) x = seg_middle<T, S, true, false>(v, len, wconst, wc, c);
     else x = seg_middle<T, S, false, false>(v, len, wconst, wc, c);
     cb[(0 * L + seg) * 32 + lane] = x.x;
     cb[(1 * L + seg) * 32 + lane] = x.y;
@@ -648,7 +645,6 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
       c.y = fma(pw, c.y, cb[(1 * L + s2) * 32 + lane]);
     }
     if (cw) seg_store<T, S, true, true>(v, len, wconst, wc, c, cur.live, cur.col, cur.step);
-    else if (full) seg_store<T, S, true, false>(v, len, wconst, wc, c, cur.live, cur.col, cur.step);
     else seg_store<T, S, false, false>(v, len, wconst, wc, c, cur.live, cur.col, cur.step);
     if (seg == 0 && cur.live) {
       cur.c0[(long)m * plane] = xm;
