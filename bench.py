@@ -625,6 +625,28 @@ def solve_twice(n, plane_mode=None):
     ibm.ibm_plan_destroy(plan)
 
 
+def spread_twice(n, mode):
+    """Profiling aid: two spreads of an n-marker Fibonacci sphere (radius
+    0.25) on the 128^3 workload grid, FP32, in spreading mode `mode`
+    (atomic, direct or gather)."""
+    import torch
+    import paper_2406_19920_gb300 as ibm
+    from paper_2406_19920_gb300 import synth
+    g = workload_grid()
+    X, dV = synth.fibonacci_sphere(n, 0.25, (math.pi, 1.0, math.pi), g[3])
+    F = synth.marker_forces(n, workload=3)
+    plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
+    ibm.ibm_plan_set_spread(plan, {"atomic": ibm.IBM_SPREAD_ATOMIC, "direct": ibm.IBM_SPREAD_ATOMIC_DIRECT,
+                                   "gather": ibm.IBM_SPREAD_GATHER}[mode])
+    Xd, Fd, dVd = (torch.from_numpy(np.ascontiguousarray(a)).to("cuda", torch.float32) for a in (X, F, dV))
+    f = [torch.zeros((NY, NZ, NX), dtype=torch.float32, device="cuda") for _ in range(3)]
+    for _ in range(2):
+        ibm.ibm_spread(plan, n, Xd, Fd, dVd, *f)
+    torch.cuda.synchronize()
+    ibm.ibm_plan_check(plan)
+    ibm.ibm_plan_destroy(plan)
+
+
 def _batch_ms(ibm, torch, dims, hs, rhs, phi, reps=5):
     """Creates (and tunes) a batch, runs the four right-hand-side sets once,
     then times `reps` rounds of them; returns (batch, ms per round, create s)."""
@@ -956,6 +978,10 @@ def main():
     ap.add_argument("--solve", type=int, metavar="N",
                     help="profiling aid: two refined FP32 Poisson solves on an N^3 grid (the first one warms up), "
                          "then exit; `ncu -s <launches of one solve>` captures the second")
+    ap.add_argument("--spread", type=int, metavar="N",
+                    help="profiling aid: two spreads of an N-marker sphere on the 128^3 grid, then exit")
+    ap.add_argument("--spread-mode", default="atomic", choices=["atomic", "direct", "gather"],
+                    help="with --spread: the spreading mode")
     ap.add_argument("--plane-mode", type=int, default=None, metavar="M",
                     help="with --solve: force plane mode M of the transforms (0 split, 1 one CTA per plane, "
                          "2/4/8 cluster, -1 tensor-core DFT products)")
@@ -965,6 +991,9 @@ def main():
         return
     if args.solve:
         solve_twice(args.solve, args.plane_mode)
+        return
+    if args.spread:
+        spread_twice(args.spread, args.spread_mode)
         return
     if args.warmup < 3:
         args.warmup = 3
