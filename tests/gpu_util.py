@@ -5,8 +5,8 @@ import math
 import numpy as np
 
 # Relative L2 tolerances against the FP64 oracle.
-#   FP64 path: direct method, round-off only (spec target 1e-12).
-#   FP32 path after refinement: 1e-6 (spec target); FP32 storage of the
+#   FP64 path: direct method, round-off only (accuracy target 1e-12).
+#   FP32 path after refinement: 1e-6 (accuracy target); FP32 storage of the
 #   result alone contributes ~6e-8.
 TOL_FP64 = 1e-12
 TOL_FP32 = 1e-6

@@ -29,7 +29,7 @@ def lib():
     return ctypes.CDLL(path)
 
 
-def test_header_declares_the_survey_entry_points():
+def test_header_declares_the_boundary_entry_points():
     names = declared_functions()
     for required in ("ibm_plan_create", "ibm_plan_destroy", "ibm_poisson_solve", "ibm_helmholtz_solve",
                      "ibm_interp", "ibm_spread", "ibm_substep", "ibm_submit", "ibm_poll", "ibm_last_error",
