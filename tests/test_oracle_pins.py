@@ -634,3 +634,27 @@ def test_inout_stage_projects_onto_the_through_flow():
     d = O.divergence(new["u"], new["v"], new["w"], g, 0.5, vo)
     assert np.max(np.abs(d)) <= 1e-10 * np.max(np.abs(new["v"])) / g[4]
     assert np.all(new["v"][0] == 0.5)
+
+
+def test_outflow_update_closed_forms():
+    """The outlet's first-order upwind step (Sec. 3's advective condition):
+    with C = 0 the planes stay (up to the mass shift, here zero); with a
+    Courant number of one over the distance to the last interior value
+    (step C = hy/2 for u and w at the wall, step C = hy for v's face) the
+    outlet takes exactly that value; the v shift restores mean = v_in."""
+    g = _grid(8, 6, 4, Lx=1.0, Ly=1.2, Lz=0.8)
+    nx, ny, nz, hx, hy, hz = g
+    r = np.random.default_rng(11)
+    u, v, w = (r.standard_normal((ny, nz, nx)) for _ in range(3))
+    vo0 = r.standard_normal((nz, nx))
+    vo0 += 0.3 - vo0.mean()
+    io = dict(v_in=0.3, c_out=0.0, u_out=r.standard_normal((nz, nx)), v_out=vo0, w_out=r.standard_normal((nz, nx)))
+    uo, vo, wo = O.outflow_update(io, u, v, w, g, 0.01)
+    assert np.array_equal(uo, io["u_out"]) and np.array_equal(wo, io["w_out"])
+    assert np.max(np.abs(vo - io["v_out"])) <= 1e-15
+    io1 = dict(io, c_out=1.0)
+    uo, _, wo = O.outflow_update(io1, u, v, w, g, 0.5 * hy)
+    assert np.max(np.abs(uo - u[-1])) <= 1e-15 and np.max(np.abs(wo - w[-1])) <= 1e-15
+    _, vo, _ = O.outflow_update(io1, u, v, w, g, hy)
+    assert np.max(np.abs(vo - (v[-1] + (0.3 - v[-1].mean())))) <= 1e-14
+    assert abs(vo.mean() - 0.3) <= 1e-15
