@@ -658,3 +658,26 @@ def test_outflow_update_closed_forms():
     _, vo, _ = O.outflow_update(io1, u, v, w, g, hy)
     assert np.max(np.abs(vo - (v[-1] + (0.3 - v[-1].mean())))) <= 1e-14
     assert abs(vo.mean() - 0.3) <= 1e-15
+
+
+def test_advection_with_wall_data_telescopes_to_the_wall_fluxes():
+    """Conservative form: the x and z fluxes telescope over the periodic
+    axes, the y fluxes to the two walls.  With inflow v_lo (u = w = 0 on
+    that wall) and outlet values (u_hi, v_hi, w_hi), the grid sum of each
+    component equals its net wall flux over hy: u and w carry
+    avg(v_hi) * g through the outlet and nothing through the inflow wall; v
+    carries (v on the cell centre)^2 from the first to the last cell row."""
+    g = _grid(12, 10, 8, Lx=1.1, Ly=1.4, Lz=0.9)
+    nx, ny, nz, hx, hy, hz = g
+    r = np.random.default_rng(21)
+    u, v, w = (r.standard_normal((ny, nz, nx)) for _ in range(3))
+    v_lo = 0.4
+    u_hi, v_hi, w_hi = (r.standard_normal((nz, nx)) for _ in range(3))
+    Nu, Nv, Nw = O.advection(u, v, w, g, (v_lo, u_hi, v_hi, w_hi))
+    vx = 0.5 * (v_hi + np.roll(v_hi, 1, 1))   # outlet v at the u points (x-faces)
+    vz = 0.5 * (v_hi + np.roll(v_hi, 1, 0))   # ... at the w points (z-faces)
+    assert abs(Nu.sum() - (vx * u_hi).sum() / hy) <= 1e-11 * np.abs(Nu).sum()
+    assert abs(Nw.sum() - (vz * w_hi).sum() / hy) <= 1e-11 * np.abs(Nw).sum()
+    vc_top = 0.5 * (v[ny - 1] + v_hi)
+    vc_bot = 0.5 * (v_lo + v[1])
+    assert abs(Nv.sum() - ((vc_top ** 2).sum() - (vc_bot ** 2).sum()) / hy) <= 1e-11 * np.abs(Nv).sum()
