@@ -63,14 +63,23 @@ static void stage_copy(void *dst, const void *src, size_t bytes) {
   }
   const size_t part = (bytes / nt + 63) / 64 * 64;
   std::vector<std::thread> th;
+  size_t done_from = bytes;  // parts from here on are copied by this thread (a helper could not start)
   for (int t = 1; t < nt; ++t) {
     const size_t off = part * t;
     if (off >= bytes) break;
-    th.emplace_back([=] {
-      std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off, std::min(part, bytes - off));
-    });
+    try {
+      th.emplace_back([=] {
+        std::memcpy(static_cast<char *>(dst) + off, static_cast<const char *>(src) + off,
+                    std::min(part, bytes - off));
+      });
+    } catch (...) {
+      done_from = off;
+      break;
+    }
   }
   std::memcpy(dst, src, std::min(part, bytes));
+  if (done_from < bytes)
+    std::memcpy(static_cast<char *>(dst) + done_from, static_cast<const char *>(src) + done_from, bytes - done_from);
   for (auto &x : th) x.join();
 }
 
