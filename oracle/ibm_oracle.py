@@ -22,7 +22,18 @@ Grid and layout (shared convention with the library, restated here):
     ((i+1/2)hx, (j+1/2)hy, k hz), v on y-faces ((i+1/2)hx, j hy, (k+1/2)hz);
     v plane j is face j; plane 0 is the bottom wall and the top wall face
     j = ny is not stored -- both wall faces carry v = 0 and the stored plane
-    0 is ignored on input and written as 0 on output.
+    0 is ignored on input and written as 0 on output (no-slip walls; the
+    inflow-outflow stage of rk_stage carries v_in and the outlet plane
+    there instead).
+
+Pins (tests/test_oracle_pins.py) tie every function to results fixed by the
+mathematics: closed forms, dense brute-force solves, invariants and special
+cases.  The RK stage (rk_stage) is pinned by the following, and "parity
+unpinned" beyond them, because the paper prints no stage values:
+  * a closed-form viscous mode carried through a full stage;
+  * the scheme's stability polynomial;
+  * projection to round-off;
+  * the inflow-outflow reductions.
 
 Boundary kinds of a field along y ("field_bc"):
   NEUMANN         cell-centred, ghost x_{-1} = x_0 (Appendix B, Neumann rows
