@@ -28,12 +28,21 @@ Grid and layout (shared convention with the library, restated here):
 
 Pins (tests/test_oracle_pins.py) tie every function to results fixed by the
 mathematics: closed forms, dense brute-force solves, invariants and special
-cases.  The RK stage (rk_stage) is pinned by the following, and "parity
-unpinned" beyond them, because the paper prints no stage values:
-  * a closed-form viscous mode carried through a full stage;
-  * the scheme's stability polynomial;
-  * projection to round-off;
+cases.  The paper prints no stage values, so the RK stage (rk_stage) is
+pinned term by term, each by a case in which that term alone has a
+closed-form effect on the stage's output:
+  * a viscous eigenmode carried through a full stage (the alpha / beta
+    split of Eq. 2a and 2e);
+  * the history term -zeta N_prev on a divergence-free Helmholtz eigenmode;
+  * the advection term -gamma N(u), by superposition against the history
+    term (out(u) + out(-u) isolates it);
+  * -(alpha+beta) G p with the projection and the pressure update of Eq.
+    2g-2h, which cancel exactly for a y-only pressure mode;
+  * the scheme's stability polynomial, projection to round-off, the
+    Lagrangian force at the stage start time;
   * the inflow-outflow reductions.
+marker_motion is pinned by the heave's values at quarter periods, its
+period and its velocity as the derivative of its position.
 
 Boundary kinds of a field along y ("field_bc"):
   NEUMANN         cell-centred, ghost x_{-1} = x_0 (Appendix B, Neumann rows

@@ -491,6 +491,159 @@ def test_rk_stage_projection_and_forcing_invariants():
     assert np.allclose(info["F"], (np.array([0.1, 0, 0])[None, :] - info["Ue"]) / 1e-3)
 
 
+def _no_markers():
+    return dict(X0=np.zeros((0, 3)), dV=np.zeros(0), kind=O.MOTION_STATIC, params=())
+
+
+@pytest.mark.parametrize("stage", [2, 3])
+@pytest.mark.parametrize("comp", [0, 2])
+def test_rk_stage_history_term_closed_form(stage, comp):
+    """The -zeta N^{n-2} term of Eq. 2a on its own.  With u = v = w = p = 0
+    and N_prev a single mode that is an eigenfunction of its component's
+    Helmholtz operator and carries no divergence (the u component varies in
+    y and z only, the w component in y and x only), Eq. 2a gives
+    u^e = -zeta dt N_prev, Eq. 2e divides by 1 + beta nu dt lam, the
+    divergence and hence phi vanish, so u^n = -zeta dt N_prev / (1 + beta nu
+    dt lam) and p^n = 0.  A wrong sign or factor on zeta, or the history
+    term landing on another component, fails this."""
+    g = _grid(16, 12, 8, Lx=1.7, Ly=1.1, Lz=0.9)
+    nx, ny, nz, hx, hy, hz = g
+    m, q = 3, 2
+    j = np.arange(ny)
+    ymode = np.sin(math.pi * m * (j + 0.5) / ny)
+    if comp == 0:   # u on x-faces: vary along z (k hz + hz/2 is a shift; the cos mode stays an eigenvector)
+        f = ymode[:, None, None] * np.cos(2 * math.pi * q * np.arange(nz) / nz)[None, :, None] * np.ones((1, 1, nx))
+        lam = O.modified_wavenumber_sq(math.pi * m / ny, hy) + O.modified_wavenumber_sq(2 * math.pi * q / nz, hz)
+    else:           # w on z-faces: vary along x
+        f = ymode[:, None, None] * np.ones((1, nz, 1)) * np.cos(2 * math.pi * q * np.arange(nx) / nx)[None, None, :]
+        lam = O.modified_wavenumber_sq(math.pi * m / ny, hy) + O.modified_wavenumber_sq(2 * math.pi * q / nx, hx)
+    z = np.zeros_like(f)
+    Np = [z, z, z]
+    Np[comp] = f
+    dt, nu, stage_i = 3e-3, 0.2, stage - 1
+    st = dict(u=z.copy(), v=z.copy(), w=z.copy(), p=z.copy(), N_prev=tuple(Np), t=0.0)
+    new, info = O.rk_stage(st, _no_markers(), stage, dt, nu, g)
+    zeta, beta = O.RK_ZETA[stage_i], O.RK_BETA[stage_i]
+    want = -zeta * dt * f / (1.0 + beta * nu * dt * lam)
+    names = ("u", "v", "w")
+    assert O.rel_l2(new[names[comp]], want) < 1e-13
+    for c in range(3):
+        if c != comp:
+            assert np.abs(new[names[c]]).max() < 1e-14
+    assert np.abs(new["p"]).max() < 1e-12 * np.abs(want).max()
+    assert np.abs(info["phi"]).max() < 1e-12 * np.abs(want).max()
+    for c in range(3):                      # N(0) = 0 is the next stage's history
+        assert np.abs(new["N_prev"][c]).max() == 0.0
+
+
+@pytest.mark.parametrize("stage", [1, 2, 3])
+def test_rk_stage_pressure_gradient_projection_and_update_cancel(stage):
+    """The -(alpha+beta) G p term of Eq. 2a, the projection (Eq. 2g) and the
+    pressure update (Eq. 2h) together.  u = v = w = 0 and p a y-only
+    Neumann mode cos(pi m (j+1/2)/ny): u^e = -(a+b) dt G p is a single
+    face-Dirichlet mode of v (the discrete gradient of the cosine is the
+    sine on faces), Eq. 2e divides it by 1 + c lam (c = beta dt nu), its
+    divergence over (a+b) dt is lam p / (1 + c lam), so Eq. 2f gives
+    phi = -p / (1 + c lam).  The projection then returns u^n = 0 exactly and
+    Eq. 2h p^n = p + phi - c L phi = 0.  A wrong coefficient on G p, a sign
+    slip in the projection, or a wrong sign or factor in the pressure update
+    leaves a non-zero u^n or p^n."""
+    g = _grid(8, 16, 6, Lx=1.0, Ly=1.3, Lz=0.8)
+    nx, ny, nz, hx, hy, hz = g
+    m = 2
+    p = np.cos(math.pi * m * (np.arange(ny) + 0.5) / ny)[:, None, None] * np.ones((1, nz, nx))
+    lam = O.modified_wavenumber_sq(math.pi * m / ny, hy)
+    dt, nu = 2e-3, 0.7
+    z = np.zeros_like(p)
+    st = dict(u=z.copy(), v=z.copy(), w=z.copy(), p=p, N_prev=(z, z, z), t=0.0)
+    new, info = O.rk_stage(st, _no_markers(), stage, dt, nu, g)
+    cH = O.RK_BETA[stage - 1] * dt * nu
+    assert O.rel_l2(info["phi"], -p / (1.0 + cH * lam)) < 1e-12
+    # v* carries the whole pressure-gradient step before the projection
+    ab = O.RK_ALPHA[stage - 1] + O.RK_BETA[stage - 1]
+    gv = np.zeros_like(p)
+    gv[1:] = (p[1:] - p[:-1]) / hy
+    assert O.rel_l2(info["ustar"][1], -ab * dt * gv / (1.0 + cH * lam)) < 1e-12
+    vmax = ab * dt * np.abs(gv).max()
+    for name in ("u", "v", "w"):
+        assert np.abs(new[name]).max() < 1e-12 * vmax
+    assert np.abs(new["p"]).max() < 1e-12
+
+
+@pytest.mark.parametrize("stage", [2, 3])
+def test_rk_stage_advection_term_by_superposition(stage):
+    """The -gamma N(u) term of Eq. 2a, pinned against the history term.
+
+    With p = 0 and no markers every output of the stage is an affine map of
+    the explicit estimate u^e, and u^e = lin(u) - dt (gamma N(u) + zeta
+    N_prev) with lin linear in u and N quadratic.  Hence
+      out(u) + out(-u) = 2 S(-gamma dt N(u))            (the linear parts cancel)
+      out(u; N_prev = N(u)) - out(u; 0) = S(-zeta dt N(u)),
+    S the linear solve-and-project map, so the second difference equals
+    zeta / gamma times half the first.  The history term is pinned on its
+    own above, so this fixes gamma's sign and size, and that the advection
+    enters every component."""
+    g = _grid(16, 12, 8, Lx=1.0, Ly=1.5, Lz=0.8)
+    u, v, w = synth.div_free_velocity(g, workload=5, kmax=4)
+    z = np.zeros_like(u)
+    dt, nu = 4e-3, 0.05
+    names = ("u", "v", "w", "p")
+
+    def run(sign, Np):
+        st = dict(u=sign * u, v=sign * v, w=sign * w, p=z.copy(), N_prev=Np, t=0.0)
+        return O.rk_stage(st, _no_markers(), stage, dt, nu, g)[0]
+
+    N = O.advection(u, v, w, g)
+    plus, minus, hist = run(1.0, (z, z, z)), run(-1.0, (z, z, z)), run(1.0, N)
+    ratio = O.RK_ZETA[stage - 1] / O.RK_GAMMA[stage - 1]
+    for name in names:
+        sym = 0.5 * (plus[name] + minus[name])          # S(-gamma dt N(u))
+        assert np.abs(sym).max() > 1e-6                 # the advection term is present
+        d = hist[name] - plus[name]                     # S(-zeta dt N(u))
+        assert np.abs(d - ratio * sym).max() <= 1e-10 * np.abs(sym).max(), name
+
+
+def test_heave_motion_closed_form_values():
+    """HEAVE (L2): at t = 0, T/4, T/2, 3T/4 the plate sits at y0, y0 + A, y0,
+    y0 - A with vertical velocity 2 pi A / T, 0, -2 pi A / T, 0; x and z
+    never move; the motion has period T; U^d is the time derivative of X
+    (central difference)."""
+    X0 = np.array([[0.3, 1.1, 2.0], [1.0, 0.9, 0.1]])
+    A, T = 0.5, 1.7
+    w = 2 * math.pi * A / T
+    for t, dy, vy in ((0.0, 0.0, w), (T / 4, A, 0.0), (T / 2, 0.0, -w), (3 * T / 4, -A, 0.0)):
+        X, Ud = O.marker_motion(X0, t, O.MOTION_HEAVE, (A, T))
+        assert np.allclose(X[:, 1] - X0[:, 1], dy, atol=1e-14)
+        assert np.allclose(Ud[:, 1], vy, atol=1e-14)
+        assert np.array_equal(X[:, [0, 2]], X0[:, [0, 2]])
+        assert np.array_equal(Ud[:, [0, 2]], np.zeros((2, 2)))
+    for t in (0.137, 0.9, 2.3):
+        X, Ud = O.marker_motion(X0, t, O.MOTION_HEAVE, (A, T))
+        Xp = O.marker_motion(X0, t + T, O.MOTION_HEAVE, (A, T))[0]
+        assert np.allclose(X, Xp, atol=1e-13)
+        e = 1e-5
+        d = (O.marker_motion(X0, t + e, O.MOTION_HEAVE, (A, T))[0]
+             - O.marker_motion(X0, t - e, O.MOTION_HEAVE, (A, T))[0]) / (2 * e)
+        assert np.allclose(d, Ud, atol=1e-8)
+
+
+def test_rk_stage_forces_markers_at_the_stage_start_time():
+    """With every field zero the interpolated velocity is zero, so Eq. 2c
+    gives F = U^d / dt with U^d the heave velocity at the stage's start
+    time t (not t + dt or the end of the stage)."""
+    g = _grid(16, 16, 16)
+    X0, dV = synth.fibonacci_sphere(50, 0.25, (math.pi, 1.0, math.pi), g[3])
+    z = np.zeros((16, 16, 16))
+    A, T, t0, dt = 0.1, 0.8, 0.13, 1e-3
+    st = dict(u=z.copy(), v=z.copy(), w=z.copy(), p=z.copy(), N_prev=(z, z, z), t=t0)
+    mk = dict(X0=X0, dV=dV, kind=O.MOTION_HEAVE, params=(A, T))
+    new, info = O.rk_stage(st, mk, 1, dt, 1e-2, g)
+    vy = 2 * math.pi * A / T * math.cos(2 * math.pi * t0 / T)
+    assert np.allclose(info["F"][:, 1], vy / dt, rtol=1e-13)
+    assert np.abs(info["F"][:, [0, 2]]).max() == 0.0
+    assert abs(new["t"] - (t0 + (O.RK_ALPHA[0] + O.RK_BETA[0]) * dt)) < 1e-16
+
+
 # ---------------------------------------------------------------------------
 # Inhomogeneous wall data (Appendix B: boundary values on the first and last
 # pencil rows' right-hand sides)
