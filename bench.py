@@ -1,21 +1,27 @@
-"""Benchmark: one RK stage (ibm_substep) of the immersed-boundary solver.
+"""Benchmark: the FP32-refined Poisson solve at 256^3 (the metric's headline).
 
-A step is one pass of the whole hot path over one state: E1 explicit terms,
-L2 marker motion, L1 interpolation / force / spreading, three Helmholtz
-solves, divergence, the refined Poisson solve and the projection with the
-pressure update.  Workload: 128^3 grid on [0,2pi) x [0,2] x [0,2pi]
-(periodic x, z; walls in y), FP32 fields with one refinement step, a
-20,000-marker Fibonacci sphere (radius 0.25, centre (pi, 1, pi)) translating
-at 0.1 in x, a seeded discretely divergence-free velocity with energy
-spectrum ~ k^-5/3 (k <= 16).  Four independent states rotate across steps
-(4 x 56 MB > 129 MB L2) so every step reads its fields from HBM.
+A step is one call of ibm_poisson_solve on a 256^3 grid of the domain
+[0,2pi) x [0,2] x [0,2pi] (periodic x, z; homogeneous Neumann walls in y):
+forward x/z transforms, the y tridiagonal solves with the FP64 zero mode,
+inverse transforms, one float-float residual and the correction solve, and
+the FP64 mean removal.  The right-hand side is seeded zero-mean N(0,1) noise
+low-pass filtered to |k| <= 32.  Four right-hand sides and four solutions
+rotate across steps (512 MB > 129 MB L2), so every step reads from HBM.
 
-Output: one JSON line (rank 0).  `value` is grid points advanced per second
-(all ranks) over the untraced timed region, `e2e` the same through host
-buffers, `roofline` the dominant kernel's achieved HBM bandwidth from CUDA
-events around each of its launches in an identical second pass of the same
-steps, `cpu_baseline` the FP64 CPU oracle on a bounded sample.
-`--impl reference` times that oracle alone.
+Output: one JSON line (rank 0).  `value` is grid points solved per second
+(all ranks) over the untraced timed region (`solves_per_s` beside it),
+`e2e` the same through ibm_poisson_solve with host buffers (upload of the
+right-hand side and download of the solution inside the timed region),
+`roofline` the dominant kernel kind's achieved HBM bandwidth from CUDA
+events around each of its launches in an identical second pass,
+`roofline_solve` the whole solve against its method bytes, `oracle_error`
+the result's relative L2 and max-abs error against the FP64 oracle, and
+`cpu_baseline` the oracle's 256^3 solve on the host cores (one thread and
+all cores, best of 3).  Extra keys: the FP32 solve without refinement and
+the FP64 solve at 256^3, the triply periodic branch, one RK stage at 128^3
+(with its oracle error), the heaving-plate stage at 384x256x256 (with its
+oracle error), spreading, batched, tensor-core DFT and serving samples.
+`--impl reference` times the oracle's solve alone, on the same config.
 """
 
 from __future__ import annotations
@@ -38,6 +44,18 @@ sys.path.insert(0, ROOT)
 
 METRIC = ("Poisson solves/s and grid-pts/s at 1 GB300 (% HBM roofline); FP32-refined vs FP64 at 1e-6; "
           "p50/p99")
+# the headline workload: one refined FP32 Poisson solve at 256^3
+HEAD_N = 256
+HEAD_REFINE = 1
+HEAD_BUFS = 4
+HEAD_KMAX = 32.0
+WORKLOAD = "ibm_poisson_solve 256^3 FP32 + 1 float-float refinement step"
+CONFIG = {"workload": WORKLOAD, "grid": [HEAD_N, HEAD_N, HEAD_N], "domain": "[0,2pi)x[0,2]x[0,2pi]",
+          "bc": "periodic x, z; homogeneous Neumann walls in y",
+          "rhs": "seeded zero-mean N(0,1) noise low-pass filtered to |k| <= 32",
+          "precision": "FP32 fields, FP64 zero mode, nullspace and norms, 1 float-float refinement step",
+          "l2": "4 rotating right-hand sides and solutions (512 MB) > 129 MB L2"}
+# the RK-stage extra: 128^3, 20k-marker translating sphere
 NX = NY = NZ = 128
 N_MARKERS = 20000
 DT, NU = 1e-3, 1e-2
@@ -53,7 +71,19 @@ KERNEL_KIND = (("k_plane_fwd", "forward"), ("k_rows_fwd", "forward"), ("k_cplane
                ("k_pencil", "pencil"), ("k_residual", "residual"), ("k_explicit", "explicit"),
                ("k_divergence", "divergence"), ("k_project", "project"), ("k_interp", "interp"),
                ("k_spread", "spread"), ("k_motion", "motion"))
-WORKLOAD = "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere"
+STAGE_WORKLOAD = "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere"
+
+
+def head_grid():
+    from paper_2406_19920_gb300 import synth
+    return synth.grid(HEAD_N, HEAD_N, HEAD_N)
+
+
+def head_rhs():
+    """The headline right-hand side, FP32 (both arms and the oracle check
+    use these same FP32 values)."""
+    from paper_2406_19920_gb300 import synth
+    return synth.rhs_lowpass_noise(HEAD_N, HEAD_N, HEAD_N, kmax=HEAD_KMAX, workload=1).astype(np.float32)
 
 
 def workload_grid():
@@ -62,7 +92,7 @@ def workload_grid():
 
 
 def make_inputs(g):
-    """Seeded host inputs (FP64) shared by the GPU arm and the CPU baseline."""
+    """Seeded host inputs (FP64) of the 128^3 RK-stage extra."""
     from paper_2406_19920_gb300 import synth
     u, v, w = synth.div_free_velocity(g, workload=1, kmax=16.0)
     X0, dV = synth.fibonacci_sphere(N_MARKERS, 0.25, (math.pi, 1.0, math.pi), g[3])
@@ -167,8 +197,26 @@ def ncu_traffic(kind, workload):
     return e.get("dram_bytes_per_step")
 
 
+def solve_kind_bytes(n, esz=4, refine=HEAD_REFINE):
+    """Compulsory HBM bytes per Poisson solve on an n^3 grid, per kernel kind.
+
+    pts = n^3 real points; spec = n n (n/2+1) complex entries; a solve with
+    `refine` refinement steps transforms 1 + refine right-hand sides.
+    forward: read field + write spectrum per transform; pencil: read + write
+    spectrum; inverse: read spectrum + write field, plus the read of the
+    field the correction is added to; residual: read b and x, write r.  The
+    spectrum round trip between split x and z passes is not counted (it is
+    not compulsory: a plane kernel avoids it)."""
+    pts = n ** 3
+    spec = n * n * (n // 2 + 1)
+    cs = 2 * esz
+    sets = 1 + refine
+    return {"forward": sets * (pts * esz + spec * cs), "pencil": sets * 2 * spec * cs,
+            "inverse": sets * (spec * cs + pts * esz) + refine * pts * esz, "residual": refine * 3 * pts * esz}
+
+
 def algorithmic_bytes(kind, esz=4):
-    """Compulsory HBM bytes per step (one RK stage) of each kernel kind.
+    """Compulsory HBM bytes per step of the 128^3 RK-stage extra, per kernel kind.
 
     pts = nx ny nz real points; spec = ny nz (nx/2+1) complex entries.  A
     stage transforms five fields each way: the three Helmholtz increments
@@ -279,6 +327,11 @@ def job_throughput(units_per_rank, world_size, ms):
     return units_per_rank * world_size / (ms * 1e-3)
 
 
+def _clock_ok(clk):
+    return not any(r in clk.get("reasons", []) for r in ("hw_slowdown", "hw_thermal_slowdown",
+                                                         "sw_thermal_slowdown"))
+
+
 def run_gpu(args):
     import torch
     import paper_2406_19920_gb300 as ibm
@@ -289,41 +342,27 @@ def run_gpu(args):
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
-    g = workload_grid()
-    (u, v, w), X0, dV = make_inputs(g)
+    n = HEAD_N
+    g = head_grid()
+    b32 = head_rhs()
     f32 = torch.float32
-    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", f32)
-    plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
-    # N_STATES independent states; each step advances the next one
-    states, keep = [], []
-    for s in range(N_STATES):
-        fields = [dev(u), dev(v), dev(w), torch.zeros((NY, NZ, NX), dtype=f32, device="cuda")]
-        Ns = [torch.zeros((NY, NZ, NX), dtype=f32, device="cuda") for _ in range(3)]
-        st = ibm.ibm_state(*[t.data_ptr() for t in fields + Ns], 0.0)
-        states.append(st)
-        keep.append((fields, Ns))
-    X0d, dVd = dev(X0), dev(dV)
-    X = torch.empty((N_MARKERS, 3), dtype=f32, device="cuda")
-    Ud = torch.empty_like(X)
-    F = torch.empty_like(X)
-    params = (ctypes.c_double * 4)(0.1, 0.0, 0.0, 0.0)
-    mk = ibm.ibm_markers(N_MARKERS, X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
-                         ibm.IBM_MOTION_TRANSLATE, params)
+    plan = ibm.ibm_plan_create(n, n, n, g[3:], ibm.IBM_FP32_REFINED, HEAD_REFINE)
+    rhs = [torch.from_numpy(b32).to("cuda") for _ in range(HEAD_BUFS)]
+    phi = [torch.empty_like(r) for r in rhs]
     stream = torch.cuda.current_stream()
 
     def step(i):
-        st = states[i % N_STATES]
-        ibm.ibm_substep(plan, st, (i // N_STATES) % 3 + 1, DT, NU, mk, stream=stream)
-
-    for i in range(args.warmup):
-        step(i)
-    torch.cuda.synchronize()
-    info = ibm.ibm_substep(plan, states[0], 1, DT, NU, mk, info=True)
+        ibm.ibm_poisson_solve(plan, rhs[i % HEAD_BUFS], phi[i % HEAD_BUFS], stream=stream)
 
     def barrier():
         if dist:
             dist.barrier()
         torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    ibm.ibm_plan_check(plan)
 
     if args.quick:
         barrier()
@@ -338,11 +377,11 @@ def run_gpu(args):
         ms = e0.elapsed_time(e1)
         if rank == 0:
             print(json.dumps({"quick": True, "ms_per_step": ms / args.steps,
-                              "value": NX * NY * NZ * args.steps * ws / (ms * 1e-3)}), flush=True)
+                              "value": n ** 3 * args.steps * ws / (ms * 1e-3)}), flush=True)
         ibm.ibm_plan_destroy(plan)
         return
 
-    # ---- timed region: K steps, no tracing; clocks sampled throughout ----
+    # ---- timed region: K solves, no tracing; clocks sampled throughout ----
     ev = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps + 1)]
     with ClockSampler(local) as clk:
         time.sleep(0.3)  # let the sampler start before the timed region
@@ -356,10 +395,11 @@ def run_gpu(args):
         t_host1 = time.time()
     step_ms = [ev[i].elapsed_time(ev[i + 1]) for i in range(args.steps)]
     total_ms = job_ms(ev[0].elapsed_time(ev[-1]), dist, "cuda")
-    pts = NX * NY * NZ
+    pts = n ** 3
     value = job_throughput(pts * args.steps, ws, total_ms)
+    ms_step = total_ms / args.steps
 
-    # ---- identical pass with CUDA events around every kernel (roofline) ----
+    # ---- identical pass with CUDA events around every kernel kind (roofline) ----
     ibm.ibm_plan_profile(plan, True)
     ibm.ibm_plan_profile_read(plan)
     barrier()
@@ -372,19 +412,35 @@ def run_gpu(args):
     traced_ms = e0.elapsed_time(e1)
     prof = ibm.ibm_plan_profile_read(plan)
     ibm.ibm_plan_profile(plan, False)
+    info = ibm.ibm_poisson_solve(plan, rhs[0], phi[0], info=True)
+    ibm.ibm_plan_check(plan)
+
+    # ---- accuracy of the timed result against the FP64 oracle ----
+    got = phi[0].double().cpu().numpy()
+    oracle_error = None
+    if rank == 0 and not args.no_oracle:
+        from oracle import ibm_oracle as O
+        t0 = time.perf_counter()
+        ref, _ = O.poisson_solve(b32.astype(np.float64), g)
+        d = got - ref
+        oracle_error = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref)),
+                        "rel_max_abs": float(np.abs(d).max() / np.abs(ref).max()),
+                        "target": 1e-6, "oracle_s": time.perf_counter() - t0,
+                        "what": "FP32-refined GPU solution against the FP64 oracle's solution of the same FP32 "
+                                "right-hand side (dense eigen-bases, mean-zero nullspace)"}
+        del ref, d
 
     # ---- end to end: host buffers, copies inside the timed region ----
-    # Every step uploads its inputs (7 fields) from pinned host memory and
-    # reads its 4 result fields back.  Two device state sets alternate: step
-    # i's upload runs on an upload stream while step i-1 computes, and its
-    # download on a download stream while step i+1 computes (the plan's
-    # stages stay in order on the compute stream).
-    host_in = [torch.from_numpy(np.ascontiguousarray(a)).to(f32).pin_memory()
-               for a in (u, v, w, np.zeros_like(u), np.zeros_like(u), np.zeros_like(u), np.zeros_like(u))]
-    host_out = [torch.empty((NY, NZ, NX), dtype=f32).pin_memory() for _ in range(4)]
-    h2d = sum(t.numel() * t.element_size() for t in host_in)
-    d2h = sum(t.numel() * t.element_size() for t in host_out)
-    e2e_steps = max(3, min(args.steps, 20))
+    # Every step uploads its right-hand side from pinned host memory, solves
+    # through ibm_poisson_solve and reads the solution back.  Two device
+    # buffer sets alternate: step i's upload runs on an upload stream while
+    # step i-1 solves, its download on a download stream while step i+1
+    # solves (the solves stay in order on the compute stream).
+    host_in = torch.from_numpy(b32).pin_memory()
+    host_out = [torch.empty((n, n, n), dtype=f32).pin_memory() for _ in range(2)]
+    h2d = host_in.numel() * host_in.element_size()
+    d2h = host_out[0].numel() * host_out[0].element_size()
+    e2e_steps = max(3, min(args.steps, 40))
     s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
     ev_up = [torch.cuda.Event() for _ in range(2)]
     ev_done = [torch.cuda.Event() for _ in range(2)]
@@ -394,115 +450,206 @@ def run_gpu(args):
     s_up.wait_stream(stream)
     s_down.wait_stream(stream)
     for i in range(e2e_steps):
-        b = i % 2
-        fields_b, Ns_b = keep[b]
+        bi = i % 2
         with torch.cuda.stream(s_up):
             if i >= 2:
-                s_up.wait_event(ev_down[b])  # buffer b's previous results are out
-            for dsrc, hsrc in zip(fields_b + Ns_b, host_in):
-                dsrc.copy_(hsrc, non_blocking=True)
-            ev_up[b].record(s_up)
-        stream.wait_event(ev_up[b])
-        states[b].t = 0.0
-        ibm.ibm_substep(plan, states[b], 1, DT, NU, mk, stream=stream)
-        ev_done[b].record(stream)
+                s_up.wait_event(ev_down[bi])  # buffer bi's previous solution is out
+            rhs[bi].copy_(host_in, non_blocking=True)
+            ev_up[bi].record(s_up)
+        stream.wait_event(ev_up[bi])
+        ibm.ibm_poisson_solve(plan, rhs[bi], phi[bi], stream=stream)
+        ev_done[bi].record(stream)
         with torch.cuda.stream(s_down):
-            s_down.wait_event(ev_done[b])
-            for hdst, dsrc in zip(host_out, fields_b):
-                hdst.copy_(dsrc, non_blocking=True)
-            ev_down[b].record(s_down)
+            s_down.wait_event(ev_done[bi])
+            host_out[bi].copy_(phi[bi], non_blocking=True)
+            ev_down[bi].record(s_down)
     stream.wait_stream(s_up)
     stream.wait_stream(s_down)
     e1.record()
     barrier()
-    e2e_ms = e0.elapsed_time(e1)
-    e2e_value = pts * e2e_steps * ws / (e2e_ms * 1e-3)
+    e2e_ms = job_ms(e0.elapsed_time(e1), dist, "cuda")
+    e2e_value = job_throughput(pts * e2e_steps, ws, e2e_ms)
+    e2e_same = bool(np.array_equal(host_out[(e2e_steps - 1) % 2].numpy(), got.astype(np.float32)))
+    ibm.ibm_plan_destroy(plan)
+    del rhs, phi, host_in, host_out
+    torch.cuda.empty_cache()
 
-    # ---- standalone Poisson: FP32-refined vs FP64 at 128^3, and 256^3 ----
-    solves = poisson_compare(ibm, torch, NX, (("fp32_refined", ibm.IBM_FP32_REFINED, 1), ("fp64", ibm.IBM_FP64, 0)))
-    solves_256 = None
-    if not args.no_extras:
-        solves_256 = poisson_compare(ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0),
-                                                       ("fp32_refined", ibm.IBM_FP32_REFINED, 1),
-                                                       ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20)
-        # triply periodic branch (y-FFT pencil step instead of the Thomas sweep)
-        solves_256["triply_periodic"] = poisson_compare(
-            ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0), ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
-            bc=ibm.IBM_BC_TRIPLY_PERIODIC)
-
-    # ---- spreading: atomic L1 kernel vs deterministic Eulerian gather ----
-    spreading = spread_compare(ibm, torch) if not args.no_extras else None
-
-    # ---- batched (64 instances, one graph launch) and served workloads ----
-    batched = batched_compare(ibm, torch) if not args.no_extras else None
-    dft = dft_compare(ibm, torch) if not args.no_extras else None
-    serving = serve_sample(ibm) if not args.no_extras else None
-    plate = large_plate(ibm, torch) if not args.no_extras else None
-    plate_inflow = large_plate(ibm, torch, v_in=1.0) if not args.no_extras else None
-
-    # ---- roofline of the dominant kernel kind (all its launches of a step) ----
-    dom = max(prof, key=lambda k: prof[k][0])
-    dom_ms, dom_launches = prof[dom]
-    avg_ms = dom_ms / max(dom_launches, 1)
+    # ---- roofline: the dominant kernel kind, and the whole solve ----
+    kb = solve_kind_bytes(n)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_ms, dom_launches = kinds[dom]
     dom_step_ms = dom_ms / args.steps
-    alg = algorithmic_bytes(dom)
     peak, peak_src = measured_peak()
+    alg = kb[dom]
     achieved = alg / (dom_step_ms * 1e-3) / 1e9
-    workload_name = WORKLOAD
-    traffic = ncu_traffic(dom, workload_name)
-    launches = sum(c for _, c in prof.values())
-
+    traffic = ncu_traffic(dom, WORKLOAD)
+    launches = sum(c for _, c in kinds.values())
+    mb = method_bytes(n, 4, HEAD_REFINE)
     clocks = clk.summary()
+    cfg = dict(CONFIG, parallelism="replicas" if ws > 1 else "1 GPU")
     out = {
         "metric": METRIC,
         "value": value,
         "unit": "grid-pts/s",
+        "solves_per_s": value / pts,
         "n_gpus": ws,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": total_ms / args.steps,
+        "ms_per_step": ms_step,
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "f32",
         "data": "synthetic",
-        "config": {"workload": workload_name, "grid": [NX, NY, NZ], "domain": "[0,2pi)x[0,2]x[0,2pi]",
-                   "markers": N_MARKERS, "precision": "FP32 fields, FP64 zero mode, 1 float-float refinement",
-                   "l2": "4 rotating states (224 MB) > 129 MB L2", "parallelism": "replicas" if ws > 1 else "1 GPU"},
+        "config": cfg,
         "e2e": {"value": e2e_value, "unit": "grid-pts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                "steps": e2e_steps,
-                "overlap": "two device state sets: step i's upload and download overlap the neighbouring "
-                           "steps' compute (separate upload, compute and download streams)"},
+                "steps": e2e_steps, "solves_per_s": e2e_value / pts, "result_matches_device_run": e2e_same,
+                "overlap": "two device buffer sets: step i's upload and download overlap the neighbouring "
+                           "steps' solves (separate upload, compute and download streams)"},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
-                     "per": "step (all launches of the kind in one RK stage)",
+                     "per": "step (all launches of the kind in one refined solve)",
                      "algorithmic_bytes": alg, "ms_per_step": dom_step_ms,
-                     "launches_per_step": dom_launches / args.steps, "avg_launch_ms": avg_ms},
-        "kernels_ms_per_step": {k: prof[k][0] / args.steps for k in prof},
-        "launches_per_step": {k: prof[k][1] / args.steps for k in prof},
+                     "launches_per_step": dom_launches / args.steps, "avg_launch_ms": dom_ms / dom_launches},
+        "roofline_solve": {"bound": "hbm", "method_bytes": mb, "achieved": mb / (ms_step * 1e-3) / 1e9,
+                           "peak": peak, "unit": "GB/s", "frac": mb / (ms_step * 1e-3) / 1e9 / peak,
+                           "peak_source": peak_src, "target_frac": 0.6,
+                           "method": "forward, pencil and inverse passes each read and write the field once "
+                                     "(24 B/pt FP32) per transform set; the refinement step adds the residual "
+                                     "pass (12 B/pt), a second set and the read of the corrected field (4 B/pt)"},
+        "oracle_error": oracle_error,
+        "info": {k: info[k] for k in ("rel_residual", "removed_mean", "refine_iters")},
+        "phase_ms_per_solve": {k: v for k, v in info["phase_ms"].items() if v > 0},
+        "kernels_ms_per_step": {k: kinds[k][0] / args.steps for k in kinds},
+        "launches_per_step": {k: kinds[k][1] / args.steps for k in kinds},
         "p50_ms": float(np.percentile(step_ms, 50)),
         "p99_ms": float(np.percentile(step_ms, 99)),
         "value_traced": pts * args.steps * ws / (traced_ms * 1e-3),
-        "poisson": solves,
-        "poisson_256": solves_256,
-        "spreading": spreading,
-        "batched": batched,
-        "dft_tensor_core": dft,
-        "serving": serving,
-        "large_plate": plate,
-        "large_plate_inflow": plate_inflow,
-        "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")},
         "clocks": clocks,
         "timed_region_s": t_host1 - t_host0,
     }
+
+    # ---- extras (outside the timed region) ----
+    if not args.no_extras:
+        out["poisson_256"] = poisson_compare(ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0),
+                                                               ("fp32_refined", ibm.IBM_FP32_REFINED, 1),
+                                                               ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
+                                             oracle=rank == 0 and not args.no_oracle)
+        # triply periodic branch (y-FFT pencil step instead of the Thomas sweep)
+        out["poisson_256"]["triply_periodic"] = poisson_compare(
+            ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0), ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
+            bc=ibm.IBM_BC_TRIPLY_PERIODIC)
+        out["poisson_128"] = poisson_compare(ibm, torch, NX, (("fp32_refined", ibm.IBM_FP32_REFINED, 1),
+                                                              ("fp64", ibm.IBM_FP64, 0)))
+        out["stage_128"] = stage_128(ibm, torch, args, oracle=rank == 0 and not args.no_oracle)
+        out["spreading"] = spread_compare(ibm, torch)
+        out["batched"] = batched_compare(ibm, torch)
+        out["dft_tensor_core"] = dft_compare(ibm, torch)
+        out["serving"] = serve_sample(ibm)
+        out["large_plate"] = large_plate(ibm, torch, oracle=rank == 0 and not args.no_oracle)
+        out["large_plate_inflow"] = large_plate(ibm, torch, v_in=1.0)
     if rank == 0 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(args)
-    ibm.ibm_plan_destroy(plan)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def stage_128(ibm, torch, args, oracle=True):
+    """One RK stage (ibm_substep, every row of the path) at 128^3 with FP32
+    fields and one refinement step, a 20,000-marker Fibonacci sphere (radius
+    0.25, centre (pi, 1, pi)) translating at 0.1 in x, from a seeded
+    discretely divergence-free velocity with energy ~ k^-5/3 (k <= 16).
+    Four independent states rotate (4 x 56 MB > 129 MB L2).  Reports grid
+    points per second, the dominant kernel kind's HBM roofline from an
+    event-traced pass, and the stage's per-field error against the oracle's
+    rk_stage from the same FP32 inputs."""
+    g = workload_grid()
+    (u, v, w), X0, dV = make_inputs(g)
+    f32 = torch.float32
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", f32)
+    plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
+    states, keep = [], []
+    for s in range(N_STATES):
+        fields = [dev(u), dev(v), dev(w), torch.zeros((NY, NZ, NX), dtype=f32, device="cuda")]
+        Ns = [torch.zeros((NY, NZ, NX), dtype=f32, device="cuda") for _ in range(3)]
+        states.append(ibm.ibm_state(*[t.data_ptr() for t in fields + Ns], 0.0))
+        keep.append((fields, Ns))
+    X0d, dVd = dev(X0), dev(dV)
+    X = torch.empty((N_MARKERS, 3), dtype=f32, device="cuda")
+    Ud, F = torch.empty_like(X), torch.empty_like(X)
+    params = (ctypes.c_double * 4)(0.1, 0.0, 0.0, 0.0)
+    mk = ibm.ibm_markers(N_MARKERS, X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
+                         ibm.IBM_MOTION_TRANSLATE, params)
+    stream = torch.cuda.current_stream()
+    steps = 200
+
+    def step(i):
+        ibm.ibm_substep(plan, states[i % N_STATES], (i // N_STATES) % 3 + 1, DT, NU, mk, stream=stream)
+
+    # the oracle comparison: stage 1 of state 1 from the initial fields (run first)
+    err = None
+    if oracle:
+        from oracle import ibm_oracle as O
+        ibm.ibm_substep(plan, states[1], 1, DT, NU, mk, stream=stream)
+        torch.cuda.synchronize()
+        fields, Ns = keep[1]
+        got = {k: t.double().cpu().numpy() for k, t in zip("uvwp", fields)}
+        got["F"] = F.double().cpu().numpy()
+        c32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+        z = np.zeros_like(u)
+        st = dict(u=c32(u), v=c32(v), w=c32(w), p=z.copy(), N_prev=(z, z, z), t=0.0)
+        mko = dict(X0=c32(X0), dV=c32(dV), kind=O.MOTION_TRANSLATE, params=(0.1, 0.0, 0.0))
+        t0 = time.perf_counter()
+        ref, rinfo = O.rk_stage(st, mko, 1, DT, NU, g)
+        ref["F"] = rinfo["F"]
+        err = {"oracle_s": time.perf_counter() - t0}
+        for k in ("u", "v", "w", "p", "F"):
+            d = got[k] - ref[k]
+            err[k] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref[k])),
+                      "rel_max_abs": float(np.abs(d).max() / np.abs(ref[k]).max())}
+        # back to the initial state for the timed steps
+        for t, a in zip(fields, (u, v, w, z)):
+            t.copy_(dev(a))
+        for t in Ns:
+            t.zero_()
+        states[1].t = 0.0
+    for i in range(5):
+        step(i)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for i in range(steps):
+        step(5 + i)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / steps
+    ibm.ibm_plan_profile(plan, True)
+    ibm.ibm_plan_profile_read(plan)
+    for i in range(steps):
+        step(5 + steps + i)
+    prof = ibm.ibm_plan_profile_read(plan)
+    ibm.ibm_plan_profile(plan, False)
+    info = ibm.ibm_substep(plan, states[0], 1, DT, NU, mk, info=True)
+    ibm.ibm_plan_destroy(plan)
+    kinds = {k: v for k, v in prof.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    dom_step_ms = kinds[dom][0] / steps
+    peak, peak_src = measured_peak()
+    alg = algorithmic_bytes(dom)
+    achieved = alg / (dom_step_ms * 1e-3) / 1e9
+    return {"workload": STAGE_WORKLOAD, "ms_per_stage": ms, "grid_pts_per_s": NX * NY * NZ / (ms * 1e-3),
+            "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_source": peak_src, "algorithmic_bytes": alg,
+                         "ms_per_step": dom_step_ms, "traffic": ncu_traffic(dom, STAGE_WORKLOAD)},
+            "kernels_ms_per_stage": {k: kinds[k][0] / steps for k in kinds},
+            "launches_per_stage": {k: kinds[k][1] / steps for k in kinds},
+            "phase_ms_one_stage": {k: v for k, v in info["phase_ms"].items() if v > 0},
+            "oracle_error": err, "tolerance_per_field": 3e-6,
+            "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")}}
 
 
 def method_bytes(n, precision_bytes, refine):
@@ -517,14 +664,16 @@ def method_bytes(n, precision_bytes, refine):
     return solve + refine * (3 * pts * s + solve + pts * s)
 
 
-def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None):
+def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None, oracle=False):
     """Standalone Poisson solves on an n^3 grid ([0,2pi)x[0,2]x[0,2pi],
     low-passed noise right-hand side): solves/s, p50/p99 latency, and the
     achieved fraction of the measured HBM bandwidth for the solve's method
-    bytes; relative L2 of each FP32 result against the FP64 GPU result."""
+    bytes; relative L2 of each FP32 result against the FP64 GPU result and,
+    with `oracle`, every result's relative L2 and max-abs error against the
+    FP64 oracle (the FP32 right-hand side's values on both sides)."""
     from paper_2406_19920_gb300 import synth
     g = synth.grid(n, n, n)
-    b = synth.rhs_lowpass_noise(n, n, n, kmax=min(32.0, n / 4), workload=1)
+    b = synth.rhs_lowpass_noise(n, n, n, kmax=min(32.0, n / 4), workload=1).astype(np.float32).astype(np.float64)
     res = {}
     outs = {}
     for name, prec, ref in variants:
@@ -556,6 +705,13 @@ def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None):
         if name != "fp64" and "fp64" in outs:
             d = outs[name] - outs["fp64"]
             res[name]["rel_l2_vs_fp64"] = float(np.linalg.norm(d) / np.linalg.norm(outs["fp64"]))
+    if oracle:
+        from oracle import ibm_oracle as O
+        ref, _ = O.poisson_solve(b, g)
+        for name in outs:
+            d = outs[name] - ref
+            res[name]["oracle_rel_l2"] = float(np.linalg.norm(d) / np.linalg.norm(ref))
+            res[name]["oracle_rel_max_abs"] = float(np.abs(d).max() / np.abs(ref).max())
     if "fp32_refined" in res and "fp64" in res:
         res["speedup_fp32_refined_over_fp64"] = res["fp32_refined"]["solves_per_s"] / res["fp64"]["solves_per_s"]
     return res
@@ -762,7 +918,7 @@ def dft_compare(ibm, torch, sizes=(32, 48, 64), reps=50):
     return out
 
 
-def large_plate(ibm, torch, stages=48, v_in=None):
+def large_plate(ibm, torch, stages=48, v_in=None, oracle=False):
     """Bio-inspired external-flow workload: 384x256x256 on a uniform h = 2 pi/384
     grid (periodic x, z; walls in y), FP32 + 1 refinement, a flat plate of
     100,000 markers (250 x 400 lattice, chord 1, span 2) heaving with amplitude
@@ -800,6 +956,28 @@ def large_plate(ibm, torch, stages=48, v_in=None):
     Ud, F = torch.empty_like(X), torch.empty_like(X)
     mk = ibm.ibm_markers(X0.shape[0], X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
                          ibm.IBM_MOTION_HEAVE, (ctypes.c_double * 4)(0.5, 1.0, 0.0, 0.0))
+    err = None
+    if oracle:
+        # one stage from the initial fields on both sides, field by field
+        from oracle import ibm_oracle as O
+        st.t = 0.0
+        substep(1)
+        torch.cuda.synchronize()
+        got = {k: t.double().cpu().numpy() for k, t in zip("uvwp", fields)}
+        got["F"] = F.double().cpu().numpy()
+        c32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+        z = np.zeros((ny, nz, nx))
+        ost = dict(u=c32(u), v=c32(v), w=c32(w), p=z.copy(), N_prev=(z, z, z), t=0.0)
+        mko = dict(X0=c32(X0), dV=c32(dV), kind=O.MOTION_HEAVE, params=(0.5, 1.0))
+        t0 = time.perf_counter()
+        ref, rinfo = O.rk_stage(ost, mko, 1, DT, NU, g)
+        ref["F"] = rinfo["F"]
+        err = {"oracle_s": time.perf_counter() - t0, "stage": 1}
+        for k in ("u", "v", "w", "p", "F"):
+            d = got[k] - ref[k]
+            err[k] = {"rel_l2": float(np.linalg.norm(d) / np.linalg.norm(ref[k])),
+                      "rel_max_abs": float(np.abs(d).max() / np.abs(ref[k]).max())}
+        del ref, rinfo, got
     substep(1)
     torch.cuda.synchronize()
     ibm.ibm_plan_profile(plan, True)
@@ -824,7 +1002,8 @@ def large_plate(ibm, torch, stages=48, v_in=None):
             "grid_pts_per_s": nx * ny * nz / (ms * 1e-3),
             "kernel_ms_per_stage": {k: v[0] / stages for k, v in prof.items()},
             "div_max_after_projection": info["div_max"], "div_max_before": info["div_before"],
-            "poisson_rel_residual_refined": pinfo["rel_residual"], "sim_time": st.t}
+            "phase_ms_one_stage": {k: v for k, v in info["phase_ms"].items() if v > 0},
+            "poisson_rel_residual_refined": pinfo["rel_residual"], "sim_time": st.t, "oracle_error": err}
 
 
 def serve_sample(ibm, duration_s=2.0, rate=2000.0):
@@ -914,49 +1093,84 @@ def serve_sample(ibm, duration_s=2.0, rate=2000.0):
 # CPU oracle arm
 # ---------------------------------------------------------------------------
 
-def oracle_stage_rate(n_stages):
-    """Time the FP64 oracle's RK stage on the benchmark workload."""
+def oracle_solve_times(rhs_path, reps):
+    """Wall times of `reps` oracle 256^3 Poisson solves of the right-hand
+    side stored at rhs_path (this process's BLAS threads)."""
     from oracle import ibm_oracle as O
-    g = workload_grid()
-    (u, v, w), X0, dV = make_inputs(g)
-    z = np.zeros_like(u)
-    st = dict(u=u, v=v, w=w, p=z.copy(), N_prev=(z, z, z), t=0.0)
-    mk = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=(0.1, 0.0, 0.0))
-    t0 = time.perf_counter()
-    for i in range(n_stages):
-        st, _ = O.rk_stage(st, mk, i % 3 + 1, DT, NU, g)
-    el = time.perf_counter() - t0
-    return NX * NY * NZ * n_stages / el, el
+    g = head_grid()
+    b = np.load(rhs_path).astype(np.float64)
+    times = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        O.poisson_solve(b, g)
+        times.append(time.perf_counter() - t0)
+    return times
+
+
+def _oracle_child(rhs_path, reps, threads=None):
+    """oracle_solve_times in a fresh child process, with `threads` BLAS /
+    OpenMP threads (None: the library default, every host core)."""
+    env = dict(os.environ)
+    if threads is not None:
+        for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+            env[k] = str(threads)
+    p = subprocess.run([sys.executable, os.path.abspath(__file__), "--oracle-time", rhs_path, "--reps", str(reps)],
+                       env=env, capture_output=True, text=True, timeout=1800)
+    if p.returncode != 0:
+        raise RuntimeError("oracle child failed: " + p.stderr[-2000:])
+    return json.loads([ln for ln in p.stdout.splitlines() if ln.startswith("{")][-1])["times_s"]
+
+
+def _head_rhs_file():
+    import tempfile
+    fd, path = tempfile.mkstemp(suffix=".npy", prefix="ibm_rhs_")
+    os.close(fd)
+    np.save(path, head_rhs())
+    return path
 
 
 def cpu_baseline(args):
-    n = 3
-    rate, el = oracle_stage_rate(n)
-    return {"value": rate, "unit": "grid-pts/s", "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d consecutive RK stages of the same 128^3 workload (FP64 numpy, dense eigen-bases, "
-                      "BLAS threads = all host cores), %.1f s" % (n, el)}
+    """The oracle's solve of the headline workload on the host cores: one
+    BLAS thread and all cores, best of 3 each, in child processes."""
+    path = _head_rhs_file()
+    try:
+        one = _oracle_child(path, 3, threads=1)
+        allc = _oracle_child(path, 3)
+    finally:
+        os.unlink(path)
+    pts = HEAD_N ** 3
+    cores = os.cpu_count()
+    return {"value": pts / min(allc), "unit": "grid-pts/s", "cores": cores, "kind": "oracle",
+            "solves_per_s": 1.0 / min(allc),
+            "single_thread": {"value": pts / min(one), "threads": 1, "best_s": min(one), "times_s": one},
+            "all_cores": {"value": pts / min(allc), "threads": cores, "best_s": min(allc), "times_s": allc},
+            "sample": "the FP64 oracle's 256^3 Poisson solve (numpy, dense eigen-bases, no FFT or Thomas) of "
+                      "the headline right-hand side, best of 3, in child processes with 1 BLAS thread and with "
+                      "the default BLAS threads (all %d host cores); %.1f s of CPU work" % (cores, sum(one) + sum(allc))}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle's solve of the headline workload,
+    as it stands, on the host cores.  One step is one 256^3 solve."""
     ws, rank, local = dist_env()
     if rank != 0:
         return
-    for _ in range(args.warmup):
-        oracle_stage_rate(1)
-    t0 = time.perf_counter()
-    stage_s = []
-    for _ in range(args.steps):
-        r, el = oracle_stage_rate(1)
-        stage_s.append(el)
-    total = time.perf_counter() - t0
-    value = NX * NY * NZ * args.steps / sum(stage_s)
-    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid-pts/s", "n_gpus": ws,
-           "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(stage_s) / args.steps,
-           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere", "grid": [NX, NY, NZ],
-                      "markers": N_MARKERS},
+    path = _head_rhs_file()
+    try:
+        times = _oracle_child(path, args.warmup + args.steps)
+    finally:
+        os.unlink(path)
+    solve_s = times[args.warmup:]
+    pts = HEAD_N ** 3
+    value = pts * args.steps / sum(solve_s)
+    cfg = dict(CONFIG, parallelism="replicas" if ws > 1 else "1 GPU")
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "grid-pts/s",
+           "solves_per_s": value / pts, "n_gpus": ws, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * sum(solve_s) / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "config": cfg,
            "cpu_baseline": {"value": value, "unit": "grid-pts/s", "cores": os.cpu_count(), "kind": "oracle",
-                            "sample": "one FP64 oracle RK stage of the workload per step, %.1f s total" % total},
+                            "sample": "one FP64 oracle 256^3 Poisson solve per step (numpy, dense eigen-bases, "
+                                      "default BLAS threads on all host cores), %.1f s timed" % sum(solve_s)},
            "e2e": {"value": value, "unit": "grid-pts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out), flush=True)
 
@@ -968,7 +1182,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-extras", action="store_true", help="skip the batched and serving samples")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="the headline solve only (no 128^3 stage, plate, batched, serving or other samples)")
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error checks")
+    ap.add_argument("--oracle-time", metavar="NPY", help=argparse.SUPPRESS)
+    ap.add_argument("--reps", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--quick", action="store_true",
                     help="warm-up and timed steps only (no tracing pass, e2e, Poisson comparison or CPU baseline); "
                          "the timed steps are the profiler region, for ncu launch lists")
@@ -986,6 +1204,9 @@ def main():
                     help="with --solve: force plane mode M of the transforms (0 split, 1 one CTA per plane, "
                          "2/4/8 cluster, -1 tensor-core DFT products)")
     args = ap.parse_args()
+    if args.oracle_time:
+        print(json.dumps({"times_s": oracle_solve_times(args.oracle_time, args.reps)}), flush=True)
+        return
     if args.ncu_summary:
         ncu_summary(args.ncu_summary, args.steps)
         return

@@ -29,9 +29,15 @@
  *     is the bottom wall and the top wall face j = ny is not stored.  Both
  *     wall faces carry v = 0: plane 0 is ignored on input and written as 0.
  * Markers: positions X and velocities/forces are arrays [n][3] (x, y, z),
- *   volumes dV are [n], all in device memory, plan precision.  Markers must
- *   stay in 1.5 hy (3-point kernel) / 2 hy (4-point kernel) of the walls'
- *   interior; support points beyond the stored planes are dropped.
+ *   volumes dV are [n], all in device memory, plan precision.  The wall
+ *   rule: the support of delta_h (Eq. 2b, 2d) reaches 1.5 hy (3-point
+ *   kernel) / 2 hy (4-point kernel) from a marker along y, and a marker
+ *   closer than that to a wall (Y < 1.5 hy or Y > Ly - 1.5 hy; 2 hy for the
+ *   4-point kernel; NaN too) would need values beyond the wall.  Marker
+ *   positions live on the device, so the kernels apply the rule: such a
+ *   marker is neither interpolated (its U and F are written as 0) nor
+ *   spread, and the plan's error word counts it.  ibm_plan_check, and the
+ *   next call with a non-NULL info, then return IBM_ERR_ARG with the count.
  * Alignment: field pointers must be 16-byte aligned (they are moved with
  *   bulk asynchronous copies); marker arrays need their element alignment.
  * Ownership: all field and marker pointers belong to the caller; the plan
@@ -97,6 +103,22 @@ enum { IBM_DELTA_ROMA3 = 0, IBM_DELTA_PESKIN4 = 1 };
 /* Prescribed marker motion (L2, Sec. 2.3.2). */
 enum { IBM_MOTION_STATIC = 0, IBM_MOTION_TRANSLATE = 1, IBM_MOTION_HEAVE = 2 };
 
+enum {
+  IBM_K_FORWARD = 0,   /* x/z forward transform of a right-hand side      */
+  IBM_K_PENCIL = 1,    /* tridiagonal solves along y                      */
+  IBM_K_INVERSE = 2,   /* z/x inverse transform                           */
+  IBM_K_RESIDUAL = 3,  /* refinement residual                             */
+  IBM_K_EXPLICIT = 4,  /* E1 explicit terms                               */
+  IBM_K_MOTION = 5,    /* L2 marker motion (fused into IBM_K_INTERP: no   */
+                       /* launches of its own)                            */
+  IBM_K_INTERP = 6,    /* L2 motion + L1 interpolation + force            */
+  IBM_K_SPREAD = 7,    /* L1 spreading                                    */
+  IBM_K_DIVERGENCE = 8,/* E2 divergence                                   */
+  IBM_K_PROJECT = 9,   /* E3 projection + pressure update                 */
+  IBM_K_OUTFLOW = 10,  /* outlet update + mass balance (inflow-outflow)   */
+  IBM_K_COUNT = 11
+};
+
 typedef struct {
   double rel_residual;  /* ||b - A x||_2 / ||b||_2 of the returned x (FP64 sums)  */
   double removed_mean;  /* Poisson: mean(b) removed to make b compatible          */
@@ -105,6 +127,9 @@ typedef struct {
   double t_ms;          /* device time of the call (events), when info is given   */
   int refine_iters;     /* refinement steps applied                              */
   int reserved;
+  double phase_ms[IBM_K_COUNT]; /* device time of each kernel kind (IBM_K_*) in   */
+                        /* the call, from events around its launches (the      */
+                        /* per-task split the paper reports in Sec. 4)          */
 } ibm_info;
 
 /* ---------------------------------------------------------------------------
@@ -151,19 +176,28 @@ int ibm_plan_set_spread(ibm_plan plan, int mode);
 /* Bytes of device memory the plan holds. */
 size_t ibm_plan_workspace_bytes(ibm_plan plan);
 
-/* Synchronise the device and report whether any kernel of this plan gave up
- * one of its bounded waits (IBM_ERR_TIMEOUT; the word is then cleared). */
+/* Synchronise the device and report the plan's device error word, then
+ * clear it: IBM_ERR_TIMEOUT when a kernel gave up one of its bounded waits,
+ * IBM_ERR_ARG when markers were rejected by the wall rule (the message gives
+ * their count, summed over the calls since the last check), IBM_OK
+ * otherwise.  Calls with a non-NULL info perform the same check. */
 int ibm_plan_check(ibm_plan plan);
 
-/* Diagnostic of the bounded waits (no fault is involved): launches one CTA
- * that allocates tensor memory, waits on an mbarrier that nothing completes,
- * gives up after limit_ms milliseconds (0 < limit_ms <= 5000), records the
- * timeout in the plan's error word, frees the tensor memory and returns.
+/* Diagnostic of the bounded waits (no fault is involved).  Every wait of the
+ * library's kernels on an mbarrier (bulk copies, tensor-core commits) gives
+ * up after a fixed wall time (100 ms), records IBM_ERR_TIMEOUT in the plan's
+ * error word, waits once more (bounded) for work in flight and returns.
+ * This launches one CTA that takes that way out on purpose, after limit_ms
+ * milliseconds (0 < limit_ms <= 5000), on one of two paths:
+ *   IBM_SELFTEST_TENSOR_MEMORY  holds tensor memory and waits on an mbarrier
+ *                               that nothing completes, then frees the memory;
+ *   IBM_SELFTEST_BULK_COPY      issues one in-bounds 16-byte bulk copy whose
+ *                               barrier expects twice its bytes, so the wait
+ *                               cannot complete, then waits once more.
  * The next ibm_plan_check (after the stream has drained) returns
- * IBM_ERR_TIMEOUT; the plan and the context stay usable.  This is the path
- * every kernel that waits on bulk copies or tensor-core work takes when a
- * wait runs out. */
-int ibm_selftest_timeout(ibm_plan plan, double limit_ms, void *stream);
+ * IBM_ERR_TIMEOUT; the plan and the context stay usable. */
+enum { IBM_SELFTEST_TENSOR_MEMORY = 0, IBM_SELFTEST_BULK_COPY = 1 };
+int ibm_selftest_timeout(ibm_plan plan, int path, double limit_ms, void *stream);
 
 /* Per-kernel timing (tracing).  While enabled, every kernel the plan
  * launches is bracketed by a pair of CUDA events on its stream; the pairs
@@ -172,21 +206,7 @@ int ibm_selftest_timeout(ibm_plan plan, double limit_ms, void *stream);
  * of the first max_kinds kinds to ms[] / launches[] (either may be NULL),
  * clears the record and returns IBM_K_COUNT.  The paper reports per-task
  * time shares (Sec. 4); this gives the same breakdown per kernel. */
-enum {
-  IBM_K_FORWARD = 0,   /* x/z forward transform of a right-hand side      */
-  IBM_K_PENCIL = 1,    /* tridiagonal solves along y                      */
-  IBM_K_INVERSE = 2,   /* z/x inverse transform                           */
-  IBM_K_RESIDUAL = 3,  /* refinement residual                             */
-  IBM_K_EXPLICIT = 4,  /* E1 explicit terms                               */
-  IBM_K_MOTION = 5,    /* L2 marker motion (fused into IBM_K_INTERP: no   */
-                       /* launches of its own)                            */
-  IBM_K_INTERP = 6,    /* L2 motion + L1 interpolation + force            */
-  IBM_K_SPREAD = 7,    /* L1 spreading                                    */
-  IBM_K_DIVERGENCE = 8,/* E2 divergence                                   */
-  IBM_K_PROJECT = 9,   /* E3 projection + pressure update                 */
-  IBM_K_OUTFLOW = 10,  /* outlet update + mass balance (inflow-outflow)   */
-  IBM_K_COUNT = 11
-};
+
 int ibm_plan_profile(ibm_plan plan, int enable);
 int ibm_plan_profile_read(ibm_plan plan, int max_kinds, double *ms, int *launches);
 
@@ -204,19 +224,25 @@ int ibm_poisson_solve(ibm_plan plan, const void *rhs, void *phi, void *stream,
 /* Poisson solve for callers that cannot allocate device memory.  The paper
  * has no counterpart: it exists for hosts that own the GPU's memory budget
  * (memory pools, frameworks that hand out only their own buffers) or must
- * not call cudaMalloc mid-run.  Same FP32 method and result as
+ * not call cudaMalloc mid-run.  Same FP32 method, kernels and result as
  * ibm_poisson_solve on an IBM_FP32_REFINED plan with refine_iters steps, but
  * no plan: the workspace lives in one static 24 MiB device array that the
  * library holds on every GPU that loads it until the process exits, enough
  * for a 128^3 grid with one refinement step.  Larger grids return
- * IBM_ERR_ARG with the bytes needed.  rhs and phi are distinct float fields
- * [ny][nz][nx] in device memory (16-byte aligned).  The first call on a
- * device looks up the array's device address; make that first call before
+ * IBM_ERR_ARG with the bytes needed, before any CUDA call.  rhs and phi are
+ * distinct float fields [ny][nz][nx] in device memory (16-byte aligned).
+ * status (optional, host memory) receives the solve's device error word
+ * through a copy queued on `stream` after the solve: 0 when every bounded
+ * wait of the solve completed, non-zero (bit 0: a wait gave up) when phi is
+ * not valid.  Read it once the stream has reached the end of the call; with
+ * pinned memory the copy is asynchronous, with pageable memory the call
+ * returns only after the solve has finished.  The first call on a device
+ * looks up the array's device address; make that first call before
  * capturing a stream into a CUDA graph.  All calls share the array and it
  * keeps the last call's contents: calls that overlap on the GPU race, so
  * serialise them (one stream, one host thread at a time). */
 int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[3], int refine_iters,
-                              const float *rhs, float *phi, void *stream);
+                              const float *rhs, float *phi, int *status, void *stream);
 
 /* Helmholtz solve, Eq. 2e (S1.1 + S1.2): (I - c L_h) u = rhs, c > 0, with the
  * wall rows selected by field_bc (Appendix B; IBM_FIELD_PERIODIC, and only

@@ -520,13 +520,34 @@ def _stencil(X, grid, comp, kernel):
     return JY, KZ, IX, wgt, valid
 
 
+def clear_of_walls(X, grid, kernel=ROMA3):
+    """The wall rule for markers: True where the support of delta_h along y,
+    |y - Y| < (S/2) hy (S = 3 for ROMA3, 4 for PESKIN4), stays between the
+    walls, i.e. (S/2) hy <= Y <= Ly - (S/2) hy.  Such a marker's stencil
+    touches stored unknowns only (v's wall face gets zero weight).  The
+    paper states no rule for markers nearer a wall; a closer marker would
+    need values beyond the wall, and it is treated as invalid input."""
+    nx, ny, nz, hx, hy, hz = grid
+    r = 1.5 if kernel == ROMA3 else 2.0
+    s = np.asarray(X, dtype=np.float64).reshape(-1, 3)[:, 1] / hy
+    return (s >= r) & (s <= ny - r)
+
+
+def _require_clear(X, grid, kernel):
+    ok = clear_of_walls(X, grid, kernel)
+    if not np.all(ok):
+        raise ValueError("%d marker(s) within the delta kernel's support of a wall" % int((~ok).sum()))
+
+
 def interp(X, u, v, w, grid, kernel=ROMA3):
     """U(X_eta) = sum_xi u(x_xi) delta_h(x_xi - X_eta) h^3  (Eq. 2b).
 
     delta_h is the tensor product of phi((x - X)/h) / h per axis, so the h^3
     cancels and U is a weighted sum with weights phi phi phi.
-    Returns U of shape (N, 3).
+    Returns U of shape (N, 3).  Markers must be clear of the walls
+    (clear_of_walls); otherwise ValueError.
     """
+    _require_clear(X, grid, kernel)
     out = np.zeros((len(X), 3))
     for comp, f in enumerate((u, v, w)):
         JY, KZ, IX, wgt, valid = _stencil(X, grid, comp, kernel)
@@ -539,9 +560,11 @@ def spread(X, F, dV, grid, kernel=ROMA3):
     """f(x_xi) = sum_eta F(X_eta) delta_h(x_xi - X_eta) dV_eta  (Eq. 2d).
 
     delta_h = phi phi phi / (hx hy hz).  Accumulation runs in marker order in
-    FP64 (deterministic).  Returns (fu, fv, fw).
+    FP64 (deterministic).  Returns (fu, fv, fw).  Markers must be clear of
+    the walls (clear_of_walls); otherwise ValueError.
     """
     nx, ny, nz, hx, hy, hz = grid
+    _require_clear(X, grid, kernel)
     X = np.asarray(X, dtype=np.float64)
     F = np.asarray(F, dtype=np.float64)
     dV = np.asarray(dV, dtype=np.float64)

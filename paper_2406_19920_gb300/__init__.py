@@ -24,6 +24,7 @@ IBM_FIELD_CELL_NEUMANN, IBM_FIELD_CELL_DIRICHLET, IBM_FIELD_FACE_DIRICHLET, IBM_
 IBM_DELTA_ROMA3, IBM_DELTA_PESKIN4 = 0, 1
 IBM_SPREAD_ATOMIC, IBM_SPREAD_GATHER, IBM_SPREAD_ATOMIC_DIRECT = 0, 1, 2
 IBM_MOTION_STATIC, IBM_MOTION_TRANSLATE, IBM_MOTION_HEAVE = 0, 1, 2
+IBM_SELFTEST_TENSOR_MEMORY, IBM_SELFTEST_BULK_COPY = 0, 1
 IBM_REQ_POISSON, IBM_REQ_HELMHOLTZ, IBM_REQ_SUBSTEP = 0, 1, 2
 
 
@@ -33,13 +34,19 @@ class IbmError(RuntimeError):
         self.code = code
 
 
+IBM_K_COUNT = 11
+
+
 class ibm_info(ctypes.Structure):
     _fields_ = [("rel_residual", ctypes.c_double), ("removed_mean", ctypes.c_double),
                 ("div_max", ctypes.c_double), ("div_before", ctypes.c_double),
-                ("t_ms", ctypes.c_double), ("refine_iters", ctypes.c_int), ("reserved", ctypes.c_int)]
+                ("t_ms", ctypes.c_double), ("refine_iters", ctypes.c_int), ("reserved", ctypes.c_int),
+                ("phase_ms", ctypes.c_double * IBM_K_COUNT)]
 
     def as_dict(self):
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f not in ("reserved", "phase_ms")}
+        d["phase_ms"] = {k: self.phase_ms[i] for i, k in enumerate(KERNEL_KINDS)}
+        return d
 
 
 class ibm_state(ctypes.Structure):
@@ -83,14 +90,14 @@ _SIG = {
     "ibm_plan_set_spread": (_I, [_P, _I]),
     "ibm_plan_workspace_bytes": (ctypes.c_size_t, [_P]),
     "ibm_plan_check": (_I, [_P]),
-    "ibm_selftest_timeout": (_I, [_P, _D, _P]),
+    "ibm_selftest_timeout": (_I, [_P, _I, _D, _P]),
     "ibm_plan_profile": (_I, [_P, _I]),
     "ibm_plan_profile_read": (_I, [_P, _I, ctypes.POINTER(_D), ctypes.POINTER(_I)]),
     "ibm_poisson_solve": (_I, [_P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_helmholtz_solve": (_I, [_P, _D, _I, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_poisson_solve_bc": (_I, [_P, _P, _P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
     "ibm_helmholtz_solve_bc": (_I, [_P, _D, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ibm_info)]),
-    "ibm_poisson_solve_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_D), _I, _P, _P, _P]),
+    "ibm_poisson_solve_noalloc": (_I, [_I, _I, _I, ctypes.POINTER(_D), _I, _P, _P, ctypes.POINTER(_I), _P]),
     "ibm_interp": (_I, [_P, _I, _P, _P, _P, _P, _P, _P]),
     "ibm_spread": (_I, [_P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "ibm_substep": (_I, [_P, ctypes.POINTER(ibm_state), _I, _D, _D, ctypes.POINTER(ibm_markers), _P,
@@ -214,11 +221,14 @@ def ibm_poisson_solve(plan, rhs, phi, stream=None, info=False):
     return inf.as_dict() if inf is not None else None
 
 
-def ibm_poisson_solve_noalloc(nx, ny, nz, h, refine_iters, rhs, phi, stream=None):
+def ibm_poisson_solve_noalloc(nx, ny, nz, h, refine_iters, rhs, phi, stream=None, status=None):
     """FP32 Poisson solve whose workspace is the library's static device
-    scratch (no device allocation; see include/ibm.h)."""
+    scratch (no device allocation; see include/ibm.h).  status: None, or a
+    ctypes.c_int that receives the solve's device error word (valid once
+    the stream has finished the call)."""
     hh = (_D * 3)(*[float(x) for x in h])
     return _check(lib().ibm_poisson_solve_noalloc(nx, ny, nz, hh, refine_iters, _ptr(rhs), _ptr(phi),
+                                                  ctypes.byref(status) if status is not None else None,
                                                   _stream(stream)))
 
 
@@ -272,8 +282,11 @@ def ibm_substep_inout(plan, state, inout, rk_stage, dt, nu, markers, stream=None
     return inf.as_dict() if inf is not None else None
 
 
-def ibm_selftest_timeout(plan, limit_ms, stream=None):
-    return _check(lib().ibm_selftest_timeout(plan, float(limit_ms), _stream(stream)))
+def ibm_selftest_timeout(plan, limit_ms, stream=None, path=None):
+    """Runs one bounded wait that cannot complete (path: IBM_SELFTEST_TENSOR_MEMORY,
+    the default, or IBM_SELFTEST_BULK_COPY); see include/ibm.h."""
+    path = IBM_SELFTEST_TENSOR_MEMORY if path is None else path
+    return _check(lib().ibm_selftest_timeout(plan, int(path), float(limit_ms), _stream(stream)))
 
 
 def ibm_batch_create(dims, hs, precision=IBM_FP32_REFINED, refine_iters=1):

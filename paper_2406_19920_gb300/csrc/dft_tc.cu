@@ -58,7 +58,6 @@ constexpr uint32_t kLboTab = 128;  // constant operands: dense
 constexpr uint32_t kHdr = 128;     // barriers and the tensor-memory address
 constexpr int kXLoads = 8;         // float4 loads of an x-row tile per thread (<= 128 rows x 16 / 256)
 constexpr int kSLoads = 17;        // float2 loads of a spectrum group per thread (<= 128 x 33 / 256)
-constexpr uint64_t kWaitNs = 1000000000ull;  // a wait on copies or MMAs gives up after 1 s
 // Main accumulators (fewer when tensor memory is short).  Measured on GB300,
 // relative L2 error of an unrefined FP32 Poisson solve on 64 x 24 x 64 with
 // 1 / 2 / 3 main accumulators: 3.2e-6 / 1.4e-6 / 1.1e-6 (the FFT plane
@@ -219,8 +218,8 @@ __device__ __forceinline__ void dft_epilogue(DftHdr *hdr, uint32_t tmem, uint32_
                                              uint32_t ph) {
   if (!ok) {
     if (threadIdx.x == 0) {
-      if (!consts) mbar_wait_ns(&hdr->bar_c, 0, nullptr, kWaitNs);
-      mbar_wait_ns(&hdr->bar_m, ph, nullptr, kWaitNs);
+      if (!consts) mbar_wait(&hdr->bar_c, 0, nullptr);
+      mbar_wait(&hdr->bar_m, ph, nullptr);
     }
   }
   tc_fence_before();
@@ -286,7 +285,7 @@ k_dft_fwd(DftShape d, int ny, Ptr3<const float *> in_, Ptr3<float2 *> S_, const 
     fence_proxy_async();
     __syncthreads();
     if (!consts) {
-      ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_c, 0, err, kWaitNs));
+      ok = __syncthreads_and(mbar_wait(&hdr->bar_c, 0, err));
       consts = ok;  // a copy that did not land is waited for again in the epilogue
       if (!ok) break;
     }
@@ -296,7 +295,7 @@ k_dft_fwd(DftShape d, int ny, Ptr3<const float *> in_, Ptr3<float2 *> S_, const 
       mma3(tmem, (uint32_t)d.wf, d.ns, sAh, sAl, kLboPad, sbo_x, sFh, sFl, kLboTab, sbo_f, nx / 8, 0, id1);
       tc_commit(&hdr->bar_m);
     }
-    ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_m, ph, err, kWaitNs));
+    ok = __syncthreads_and(mbar_wait(&hdr->bar_m, ph, err));
     if (!ok) break;
     ph ^= 1u;
     tc_fence_after();
@@ -326,7 +325,7 @@ k_dft_fwd(DftShape d, int ny, Ptr3<const float *> in_, Ptr3<float2 *> S_, const 
              c * (nz / 8), id2);
         tc_commit(&hdr->bar_m);
       }
-      ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_m, ph, err, kWaitNs));
+      ok = __syncthreads_and(mbar_wait(&hdr->bar_m, ph, err));
       if (ok) ph ^= 1u;
     }
     if (!ok) break;
@@ -415,7 +414,7 @@ k_dft_inv(DftShape d, int ny, Ptr3<float2 *> S_, Ptr3<float *> out_, Ptr3<const 
       tc_fence_before();
       __syncthreads();
       if (!consts) {
-        ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_c, 0, err, kWaitNs));
+        ok = __syncthreads_and(mbar_wait(&hdr->bar_c, 0, err));
         consts = ok;
         if (!ok) break;
       }
@@ -426,7 +425,7 @@ k_dft_inv(DftShape d, int ny, Ptr3<float2 *> S_, Ptr3<float *> out_, Ptr3<const 
              c * (nz / 8), id1);
         tc_commit(&hdr->bar_m);
       }
-      ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_m, ph, err, kWaitNs));
+      ok = __syncthreads_and(mbar_wait(&hdr->bar_m, ph, err));
       if (ok) ph ^= 1u;
     }
     if (!ok) break;
@@ -463,7 +462,7 @@ k_dft_inv(DftShape d, int ny, Ptr3<float2 *> S_, Ptr3<float *> out_, Ptr3<const 
       mma3(tmem, (uint32_t)d.wi, d.ns, sAh, sAl, kLboPad, sbo_y, sFh, sFl, kLboTab, sbo_f, d.Kf / 8, 0, id2);
       tc_commit(&hdr->bar_m);
     }
-    ok = __syncthreads_and(mbar_wait_ns(&hdr->bar_m, ph, err, kWaitNs));
+    ok = __syncthreads_and(mbar_wait(&hdr->bar_m, ph, err));
     if (!ok) break;
     ph ^= 1u;
     tc_fence_after();

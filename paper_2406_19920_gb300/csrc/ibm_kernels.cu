@@ -6,8 +6,14 @@
 // three-point kernel of Roma, Peskin & Berger (1999), PESKIN4 the four-point
 // kernel of Peskin (2002).  Each velocity component lives on its own
 // staggered sub-grid (origin in grid units: u (0,1/2,1/2), v (1/2,0,1/2),
-// w (1/2,1/2,0)); x and z wrap periodically; along y only stored unknowns
-// are touched (v's wall face 0 and points beyond the walls are dropped).
+// w (1/2,1/2,0)); x and z wrap periodically.  Along y the support of an
+// S-point kernel reaches S/2 cells from the marker; a marker closer than
+// that to a wall (Y < (S/2) hy or Y > Ly - (S/2) hy) would need values
+// beyond the wall and is rejected: it is neither interpolated (its U and F
+// are 0) nor spread, and the plan's error word records it (kErrWall and a
+// count), which ibm_plan_check reports as IBM_ERR_ARG.  Every support point
+// of an accepted marker is a stored unknown (v's wall face 0 included:
+// accepted markers give it zero weight).
 //
 // One thread per (marker, component).  The stencil origin and offset are
 // computed in FP64 on the FP64 path and in float-float on the FP32 path, so
@@ -19,6 +25,7 @@
 #include <cmath>
 
 #include "plan.h"
+#include "tma.cuh"
 
 namespace ibm {
 
@@ -27,7 +34,26 @@ struct IbmGrid {
   double inv_h[3];
   float ih_hi[3], ih_lo[3];  // 1/h as float-float for the FP32 path
   double vol_inv;            // 1 / (hx hy hz)
+  int *err;                  // the plan's error word (flags, rejected-marker count)
 };
+
+// The wall rule: Y at least S/2 cells from both walls.  FP64: plain
+// doubles.  FP32: Y / hy as a float-float (the error-free product used for
+// the stencil origin), so the decision does not see the rounding of Y / hy.
+template <int S> __device__ __forceinline__ bool clear_of_walls(const IbmGrid &g, double Y) {
+  const double s = Y * g.inv_h[1], r = 0.5 * S;
+  return s >= r && s <= (double)g.ny - r;
+}
+template <int S> __device__ __forceinline__ bool clear_of_walls(const IbmGrid &g, float Y) {
+  const ff p = two_prod(Y, g.ih_hi[1]);
+  const float lo = fmaf(Y, g.ih_lo[1], p.lo);
+  const float r = 0.5f * S;
+  return (p.hi - r) + lo >= 0.f && (((float)g.ny - r) - p.hi) - lo >= 0.f;
+}
+__device__ __forceinline__ void report_wall(const IbmGrid &g) {
+  atomicOr(g.err, kErrWall);
+  atomicAdd(g.err + 1, 1);
+}
 
 // L2 for the rigid motions (Sec. 2.3.2 moves the markers before L1): every
 // marker is displaced by the same d(t) with velocity v(t), both evaluated on
@@ -130,6 +156,12 @@ k_interp(IbmGrid g, int n, const T *X, const T *__restrict__ u, const T *__restr
   }
   const int ml = threadIdx.x - c;  // this marker's first thread in the CTA
   const T mx = X0 ? xs[ml] : X[3 * m], my = X0 ? xs[ml + 1] : X[3 * m + 1], mz = X0 ? xs[ml + 2] : X[3 * m + 2];
+  if (!clear_of_walls<S>(g, my)) {  // the wall rule: no interpolation, no force
+    if (c == 0) report_wall(g);
+    if (U) U[t] = (T)0;
+    if (F) F[t] = (T)0;
+    return;
+  }
   int bx, by, bz;
   T fx, fy, fz;
   stencil_origin<T, S>(g, c, mx, my, mz, bx, by, bz, fx, fy, fz);
@@ -176,6 +208,10 @@ k_spread(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F, con
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= 3 * n) return;
   const int m = t / 3, c = t - 3 * m;
+  if (!clear_of_walls<S>(g, X[3 * m + 1])) {  // the wall rule: not spread
+    if (c == 0) report_wall(g);
+    return;
+  }
   int bx, by, bz;
   T fx, fy, fz;
   stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], bx, by, bz, fx, fy, fz);
@@ -234,8 +270,12 @@ k_spread_box(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F,
   __shared__ int red[6][8];
   pdl_wait();
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  const bool valid = t < 3 * n;
-  const int m = valid ? t / 3 : 0, c = valid ? t - 3 * m : 0;
+  const int m = t < 3 * n ? t / 3 : 0, c = t < 3 * n ? t - 3 * m : 0;
+  bool valid = t < 3 * n;
+  if (valid && !clear_of_walls<S>(g, X[3 * m + 1])) {  // the wall rule: not spread
+    if (c == 0) report_wall(g);
+    valid = false;
+  }
   int bx = 0, by = 0, bz = 0;
   T fx = 0, fy = 0, fz = 0, amp = 0;
   if (valid) {
@@ -253,6 +293,7 @@ k_spread_box(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F,
   }
   __syncthreads();
   int lo[3], dim[3];
+  bool any = false;
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     int mn = INT_MAX, mxn = INT_MAX;
@@ -260,9 +301,11 @@ k_spread_box(IbmGrid g, int n, const T *__restrict__ X, const T *__restrict__ F,
       mn = min(mn, red[q][w]);
       mxn = min(mxn, red[q + 3][w]);
     }
-    lo[q] = mn;
-    dim[q] = -mxn - mn + S;  // (max - min) + S points along this axis
+    any = mn != INT_MAX;  // the same for every axis and every thread
+    lo[q] = any ? mn : 0;
+    dim[q] = any ? -mxn - mn + S : 0;  // (max - min) + S points along this axis
   }
+  if (!any) return;  // every entry of the CTA was rejected by the wall rule
   const long vol = (long)dim[0] * dim[1] * dim[2];
   const bool use_box = vol > 0 && 3 * vol * (long)sizeof(T) <= kSpreadBoxBytes && dim[0] <= g.nx && dim[2] <= g.nz;
   T wx[S], wz[S];
@@ -410,6 +453,10 @@ k_gather_prep(IbmGrid g, BrickGeom bg, int n, const T *__restrict__ X, const T *
   StencilRec<T> r;
   stencil_origin<T, S>(g, c, X[3 * m], X[3 * m + 1], X[3 * m + 2], r.bx, r.by, r.bz, r.fx, r.fy, r.fz);
   r.amp = scale * F[t] * dV[m] * (T)g.vol_inv;
+  if (!clear_of_walls<S>(g, X[3 * m + 1])) {  // the wall rule: a record that adds nothing
+    if (c == 0) report_wall(g);
+    r.amp = (T)0;
+  }
   const int bx_raw = r.bx, bz_raw = r.bz;
   r.bx = wrap(r.bx, g.nx);  // records keep the periodic origins wrapped
   r.bz = wrap(r.bz, g.nz);
@@ -611,6 +658,7 @@ static IbmGrid ibm_grid(const ibm_plan_s *p) {
     g.ih_lo[d] = (float)(g.inv_h[d] - (double)g.ih_hi[d]);
   }
   g.vol_inv = 1.0 / (p->h[0] * p->h[1] * p->h[2]);
+  g.err = p->derr;
   return g;
 }
 

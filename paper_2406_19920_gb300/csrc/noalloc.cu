@@ -74,7 +74,7 @@ static size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 using namespace ibm;
 
 extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[3], int refine_iters,
-                                         const float *rhs, float *phi, void *stream) {
+                                         const float *rhs, float *phi, int *status, void *stream) {
   if (!h || !rhs || !phi) return set_error(IBM_ERR_ARG, "ibm_poisson_solve_noalloc: NULL argument");
   if (!transform_size_supported(nx) || !transform_size_supported(nz))
     return set_error(IBM_ERR_ARG, "ibm_poisson_solve_noalloc: nx=%d nz=%d must be 2^a 3^b (b<=1) in [8,512]",
@@ -111,9 +111,17 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[
   int rc = noalloc_scratch(&base);
   if (rc) return rc;
 
-  // a plan descriptor on the host stack pointing into the scratch; no device allocation
-  ibm_plan_s p;
+  // a plan descriptor on the host stack pointing into the scratch; no device
+  // allocation.  Value-initialised: every member plan_solve reaches that is
+  // not set below (the periodic-branch tables, the three-field spectra, the
+  // tensor-core DFT tables) is null, and the kernels are the ones
+  // ibm_plan_create picks for this shape (same boundary kind, plane mode and
+  // pencil mode).
+  ibm_plan_s p{};
   p.nx = nx; p.ny = ny; p.nz = nz; p.P = P;
+  p.bc = IBM_BC_PXZ_WALL_Y;
+  p.use_plane = default_plane_mode<float>(nx, ny, nz);
+  p.use_plane_fields = 0;
   p.h[0] = h[0]; p.h[1] = h[1]; p.h[2] = h[2];
   p.precision = IBM_FP32_REFINED;
   p.refine = refine_iters;
@@ -146,5 +154,12 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[
                                                      (float *)p.lamz, h[0], h[2], p.derr);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_error(e, "ibm_poisson_solve_noalloc: table kernel");
-  return plan_solve(&p, 0, 0.0, 0, rhs, phi, nullptr, st, nullptr);
+  rc = plan_solve(&p, 0, 0.0, 0, rhs, phi, nullptr, st, nullptr);
+  if (rc) return rc;
+  // the solve's error word (0: every bounded wait completed) to the caller
+  if (status) {
+    e = cudaMemcpyAsync(status, p.derr, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e != cudaSuccess) return cuda_error(e, "ibm_poisson_solve_noalloc: status copy");
+  }
+  return IBM_OK;
 }

@@ -312,7 +312,10 @@ k_pencil(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict__ l
   __syncwarp();
   for (int j = lane; j < n; j += 32)
     bulk_g2s(tile + (size_t)j * TP, src + (long)j * plane, (uint32_t)(sizeof(cplx<T>) * np), bar);
-  if (!__all_sync(0xffffffffu, mbar_wait(bar, 0, pp.err))) return;
+  if (!__all_sync(0xffffffffu, mbar_wait(bar, 0, pp.err))) {
+    mbar_wait(bar, 0, nullptr);  // copies still in flight must land before the CTA's memory is reused
+    return;
+  }
   const int bottom = lane & 1, pl = lane >> 1;
   const int p = p0 + pl;
   // the (0,0) pencil is singular (g = 0): its sweep is skipped here and its
@@ -795,7 +798,10 @@ k_pencil_ss(cplx<T> *__restrict__ S, const T *__restrict__ lamx, const T *__rest
   if (warp == 0)
     for (int j = lane; j < ny; j += 32)
       bulk_g2s(tile + (size_t)j * TP, S + (size_t)j * plane + p0, (uint32_t)(sizeof(cplx<T>) * np), bar);
-  if (!__syncthreads_and(mbar_wait(bar, 0, pp.err))) return;
+  if (!__syncthreads_and(mbar_wait(bar, 0, pp.err))) {
+    mbar_wait(bar, 0, nullptr);  // copies still in flight must land before the CTA's memory is reused
+    return;
+  }
 
 
   const int c = SPLIT ? (lane >> 1) : lane;

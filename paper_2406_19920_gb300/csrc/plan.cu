@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "plan.h"
+#include "tma.cuh"
 
 namespace ibm {
 
@@ -117,6 +118,38 @@ ProfScope::~ProfScope() {
   }
   cudaEventRecord(b, st);
   p->prof.push_back({kind, launches, a, b});
+}
+
+void InfoTrace::read(double *phase_ms) {
+  for (int k = 0; k < IBM_K_COUNT; ++k) phase_ms[k] = 0.0;
+  for (size_t i = mark; i < p->prof.size(); ++i) {
+    const auto &r = p->prof[i];
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess && r.kind >= 0 && r.kind < IBM_K_COUNT)
+      phase_ms[r.kind] += t;
+  }
+  if (!was_on) {  // the caller is not tracing: the call's records go back to the pool
+    for (size_t i = mark; i < p->prof.size(); ++i) {
+      p->evpool.push_back(p->prof[i].a);
+      p->evpool.push_back(p->prof[i].b);
+    }
+    p->prof.resize(mark);
+  }
+}
+
+int plan_status(ibm_plan_s *p, cudaStream_t st) {
+  int w[2] = {0, 0};
+  IBM_CUDA_TRY(cudaMemcpyAsync(w, p->derr, 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  IBM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!w[0]) return IBM_OK;
+  IBM_CUDA_TRY(cudaMemsetAsync(p->derr, 0, 2 * sizeof(int), st));
+  if (w[0] & (kErrTimeout | kErrAlign))
+    return set_error(IBM_ERR_TIMEOUT, "a kernel of this plan gave up a bounded wait (error word %d)%s", w[0],
+                     (w[0] & kErrWall) ? "; markers were also rejected by the wall rule" : "");
+  return set_error(IBM_ERR_ARG,
+                   "%d marker(s) closer to a wall than the delta kernel's half-width (1.5 hy, 2 hy for the "
+                   "4-point kernel) were rejected: neither interpolated nor spread",
+                   w[1]);
 }
 
 static void plan_free(ibm_plan_s *p) {
@@ -233,6 +266,7 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
     IBM_CUDA_TRY(cudaMemcpyAsync(p->bsave, in, p->npts * sizeof(T), cudaMemcpyDeviceToDevice, st));
     b = static_cast<const T *>(p->bsave);
   }
+  InfoTrace trace(p, info != nullptr);
   if (info) {
     IBM_CUDA_TRY(cudaMemsetAsync(p->dsc, 0, 8 * sizeof(double), st));
     IBM_CUDA_TRY(cudaEventRecord(p->ev0, st));
@@ -261,9 +295,8 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
     const double *h = p->hsc;
     const double rr = std::max(0.0, h[4] - h[6] * h[6] / N);
     const double bb = h[5];
-    int derr = 0;
-    IBM_CUDA_TRY(cudaMemcpy(&derr, p->derr, sizeof(int), cudaMemcpyDeviceToHost));
-    if (derr) return set_error(IBM_ERR_TIMEOUT, "a kernel gave up a bounded wait (error word %d)", derr);
+    trace.read(info->phase_ms);
+    if ((rc = plan_status(p, st))) return rc;
     info->rel_residual = bb > 0 ? std::sqrt(rr / bb) : std::sqrt(rr);
     info->removed_mean = kind == 0 ? h[0] : 0.0;
     info->div_max = 0.0;
@@ -526,13 +559,7 @@ size_t ibm_plan_workspace_bytes(ibm_plan plan) { return plan ? plan->bytes : 0; 
 int ibm_plan_check(ibm_plan plan) {
   if (!plan) return set_error(IBM_ERR_ARG, "ibm_plan_check: NULL plan");
   IBM_CUDA_TRY(cudaDeviceSynchronize());
-  int derr = 0;
-  IBM_CUDA_TRY(cudaMemcpy(&derr, plan->derr, sizeof(int), cudaMemcpyDeviceToHost));
-  if (derr) {
-    IBM_CUDA_TRY(cudaMemset(plan->derr, 0, sizeof(int)));
-    return set_error(IBM_ERR_TIMEOUT, "a kernel of this plan gave up a bounded wait (error word %d)", derr);
-  }
-  return IBM_OK;
+  return plan_status(plan, 0);
 }
 
 int ibm_plan_profile(ibm_plan plan, int enable) {

@@ -80,6 +80,29 @@ struct ProfScope {
 }  // namespace ibm
 
 namespace ibm {
+// Per-kind device times of one call for ibm_info::phase_ms: turns tracing on
+// for the call (if it was off) and, at read(), sums the call's own event
+// pairs by kind and drops them again, leaving any trace the caller is
+// collecting with ibm_plan_profile untouched.
+// Inactive (no info requested) it changes nothing.
+struct InfoTrace {
+  ibm_plan_s *p;
+  size_t mark;
+  int was_on;
+  bool active;
+  InfoTrace(ibm_plan_s *plan, bool on) : p(plan), mark(plan->prof.size()), was_on(plan->prof_on), active(on) {
+    if (active) p->prof_on = 1;
+  }
+  void read(double *phase_ms);  // after the stream has drained
+  ~InfoTrace() {
+    if (active) p->prof_on = was_on;
+  }
+};
+// The plan's device error word, read through stream st (after the work it
+// reports on, which st must follow) and cleared: IBM_ERR_TIMEOUT when a
+// bounded wait gave up, IBM_ERR_ARG when markers were rejected by the wall
+// rule (with their count), else IBM_OK.  Synchronises st.
+int plan_status(ibm_plan_s *p, cudaStream_t st);
 inline bool aligned_to(const void *p, size_t a) { return ((uintptr_t)p % a) == 0; }
 TransformGeom geom_of(const ibm_plan_s *p);
 // Solve A x = b with the plan's direct method (+ refinement for FP32).

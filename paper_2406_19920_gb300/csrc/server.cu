@@ -383,6 +383,9 @@ static void slot_worker(ibm_server_s *s, int k) {
     int rc = launch(s, q, sl);
     cudaError_t e = cudaStreamSynchronize(sl.st);
     if (rc == IBM_OK && e != cudaSuccess) rc = cuda_error(e, "server request");
+    // a bounded wait that gave up, or markers rejected by the wall rule,
+    // fail this request (the resident plan's word is cleared for the next)
+    if (rc == IBM_OK) rc = plan_status(q->res->plan, sl.st);
     if (rc == IBM_OK) {
       stage_copy(q->r.out, sl.pinned, q->out_bytes);
       cudaEventElapsedTime(&q->device_ms, sl.e0, sl.e1);

@@ -528,6 +528,7 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, const ibm_inout *io, int stage
   T *du = (T *)p->sub[0], *dv = (T *)p->sub[1], *dw = (T *)p->sub[2], *phi = (T *)p->sub[3];
   T *rhs = (T *)p->bsave;
   const Launch3 L3 = stencil_launch(p->nx, p->ny, p->nz);
+  InfoTrace trace(p, info != nullptr);
   if (info) {
     IBM_CUDA_TRY(cudaMemsetAsync(p->dsc + 8, 0, 2 * sizeof(double), st));
     IBM_CUDA_TRY(cudaEventRecord(p->ev0, st));
@@ -608,6 +609,8 @@ static int substep_t(ibm_plan_s *p, ibm_state *s, const ibm_inout *io, int stage
     IBM_CUDA_TRY(cudaStreamSynchronize(st));
     float ms = 0.f;
     IBM_CUDA_TRY(cudaEventElapsedTime(&ms, p->ev0, p->ev1));
+    trace.read(info->phase_ms);
+    if ((rc = plan_status(p, st))) return rc;
     info->rel_residual = -1.0;
     info->removed_mean = p->hsc[0];
     info->div_max = p->hsc[8];

@@ -3,9 +3,11 @@
 // bounded waits.
 //
 // A copy must start and end on 16-byte boundaries (both addresses and the
-// size).  Every wait spins at most kSpinLimit times; on expiry the kernel
-// ORs kErrTimeout into the error word it was given (the plan's device error
-// word, read back by the host) and the caller returns early instead of
+// size).  Every wait is bounded by wall time (the %globaltimer nanosecond
+// clock, kWaitLimitNs unless the caller gives another limit); on expiry the
+// kernel ORs kErrTimeout into the error word it was given (the plan's
+// device error word, read back by the host), waits once more (bounded) for
+// the copies it may still have in flight, and returns early instead of
 // hanging.
 #pragma once
 
@@ -15,9 +17,15 @@
 namespace ibm {
 
 // Error-word bit flags OR-ed by kernels that give up.
+// Word 0 of a plan's error word holds the flags, word 1 the number of
+// markers rejected by the wall rule (kErrWall) since the last check.
 constexpr int kErrTimeout = 1;
 constexpr int kErrAlign = 2;
-constexpr long kSpinLimit = 1L << 24;
+constexpr int kErrWall = 4;
+// Every bounded wait of the library (bulk copies, tensor-core commits) gives
+// up after this long.  A copy or an MMA batch completes in microseconds; the
+// limit only has to exceed what a loaded GPU can take to schedule them.
+constexpr unsigned long long kWaitLimitNs = 100ull * 1000ull * 1000ull;  // 100 ms
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -49,24 +57,19 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
   return ok != 0;
 }
 
-// Wait for phase `parity` of the barrier; false (and the error word set) if
-// the bounded spin runs out.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err) {
-  for (long it = 0; it < kSpinLimit; ++it)
-    if (mbar_try_wait(bar, parity)) return true;
-  if (err) atomicOr(err, kErrTimeout);
-  return false;
-}
-
-// As mbar_wait, bounded by wall time (the %globaltimer nanosecond clock)
-// instead of a poll count: for waits on tensor-core work, whose polls may
-// each suspend the thread for a hardware-chosen time.
 __device__ __forceinline__ uint64_t global_ns() {
   uint64_t t;
   asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
   return t;
 }
-__device__ __forceinline__ bool mbar_wait_ns(uint64_t *bar, uint32_t parity, int *err, uint64_t limit_ns) {
+
+// Wait for phase `parity` of the barrier; false (and the error word set) if
+// it has not completed after limit_ns nanoseconds of wall time.  Bounded by
+// time, not by a poll count: a try_wait may suspend the thread for a
+// hardware-chosen interval, so a poll count bounds nothing.
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *err,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
   const uint64_t t0 = global_ns();
   while (!mbar_try_wait(bar, parity))
     if (global_ns() - t0 > limit_ns) {

@@ -1,4 +1,10 @@
-"""Helpers shared by the GPU tests (device transfer, tolerances)."""
+"""Helpers shared by the GPU tests (device transfer, tolerances, errors).
+
+Every parity gate compares a GPU result x with the oracle's ref through
+rel_err: the larger of the relative L2 error ||x - ref||_2 / ||ref||_2 and
+the relative max-abs error ||x - ref||_inf / ||ref||_inf, so that an error
+confined to a few points (one wall row of one plane) is not diluted by the
+square root of the number of points.  Assertion messages print both."""
 
 import math
 
@@ -35,3 +41,27 @@ def rel_l2(x, ref):
     x = np.asarray(x, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     return float(np.linalg.norm((x - ref).ravel()) / max(np.linalg.norm(ref.ravel()), 1e-300))
+
+
+def rel_inf(x, ref):
+    x = np.asarray(x, dtype=np.float64)
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.abs(x - ref).max(initial=0.0) / max(np.abs(ref).max(initial=0.0), 1e-300))
+
+
+class RelErr(float):
+    """max(relative L2, relative max-abs) error, printing both."""
+
+    def __new__(cls, l2, inf):
+        e = super().__new__(cls, max(l2, inf))
+        e.l2, e.inf = l2, inf
+        return e
+
+    def __repr__(self):
+        return "(l2 %.3g, max %.3g)" % (self.l2, self.inf)
+
+    __str__ = __repr__
+
+
+def rel_err(x, ref):
+    return RelErr(rel_l2(x, ref), rel_inf(x, ref))

@@ -52,3 +52,27 @@ def test_version_and_error_strings_without_gpu(lib):
     assert lib.ibm_plan_create(30, 32, 32, 1, h, 1, 1, ctypes.byref(out)) == -1
     assert b"nx=30" in lib.ibm_last_error()
     assert lib.ibm_plan_create(32, 32, 32, 7, h, 1, 1, ctypes.byref(out)) == -6
+
+
+def test_noalloc_argument_checks_without_gpu(lib):
+    """ibm_poisson_solve_noalloc validates its arguments, and rejects a grid
+    larger than its static scratch with the bytes it would need, before any
+    CUDA call; the optional status pointer does not take part in them."""
+    lib.ibm_last_error.restype = ctypes.c_char_p
+    f = lib.ibm_poisson_solve_noalloc
+    f.restype = ctypes.c_int
+    f.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.c_int,
+                  ctypes.c_void_p, ctypes.c_void_p, ctypes.POINTER(ctypes.c_int), ctypes.c_void_p]
+    h = (ctypes.c_double * 3)(0.1, 0.1, 0.1)
+    a, b = 4096, 8192        # aligned stand-ins: never dereferenced, every call fails first
+    status = ctypes.c_int(7)
+    assert f(256, 256, 256, h, 1, a, b, ctypes.byref(status), None) == -1
+    assert b"scratch" in lib.ibm_last_error()
+    assert f(32, 32, 32, h, 1, a, a, ctypes.byref(status), None) == -1       # rhs == phi
+    assert b"distinct" in lib.ibm_last_error()
+    assert f(32, 32, 32, h, 1, a + 4, b, None, None) == -1                    # misaligned rhs
+    assert b"aligned" in lib.ibm_last_error()
+    assert f(30, 32, 32, h, 1, a, b, None, None) == -1
+    assert f(32, 32, 32, h, 5, a, b, None, None) == -1
+    assert f(32, 32, 32, None, 1, a, b, None, None) == -1
+    assert status.value == 7  # untouched by calls that fail validation

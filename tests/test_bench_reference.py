@@ -29,4 +29,8 @@ def test_reference_arm_json_line():
     e2e = d["e2e"]
     assert e2e["value"] == d["value"] and e2e["unit"] == d["unit"]
     assert e2e["h2d_bytes_per_step"] == 0 and e2e["d2h_bytes_per_step"] == 0
-    assert "workload" in d["config"]
+    # the same config dict as the GPU arm prints (same workload, same keys)
+    sys.path.insert(0, ROOT)
+    import bench
+    assert d["config"] == dict(bench.CONFIG, parallelism="1 GPU")
+    assert d["solves_per_s"] * 256 ** 3 == __import__("pytest").approx(d["value"])

@@ -12,7 +12,7 @@ import pytest
 from oracle import ibm_oracle as O
 from paper_2406_19920_gb300 import synth
 import paper_2406_19920_gb300 as ibm
-from tests.gpu_util import TOL_FP32, TOL_FP64, dev, grid, host, rel_l2
+from tests.gpu_util import TOL_FP32, TOL_FP64, dev, grid, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -44,7 +44,7 @@ def test_batch_matches_oracle_and_replays(prec):
             ibm.ibm_batch_poisson(batch, rhs, phi)
             torch.cuda.synchronize()
             for i in range(len(DIMS)):
-                err = rel_l2(host(phi[i]), ref[i])
+                err = rel_err(host(phi[i]), ref[i])
                 assert err <= tol, (i, DIMS[i], err)
             # refill the in-place instance for the replay
             rhs[3].copy_(dev(O.laplacian(ref[3], grids[3], O.NEUMANN), dt))

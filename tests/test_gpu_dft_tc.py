@@ -19,7 +19,7 @@ import pytest
 from oracle import ibm_oracle as O
 from paper_2406_19920_gb300 import synth
 import paper_2406_19920_gb300 as ibm
-from tests.gpu_util import TOL_FP32, dev, grid, host, rel_l2
+from tests.gpu_util import TOL_FP32, dev, grid, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -61,7 +61,7 @@ def test_dft_mode_solves_match_oracle(shape):
         for mode in (DFT, 0):
             plan = _plan(nx, ny, nz, g, refine, mode)
             try:
-                errs[(refine, mode)] = rel_l2(_poisson(plan, b32), ref)
+                errs[(refine, mode)] = rel_err(_poisson(plan, b32), ref)
                 if refine == 1 and mode == DFT:
                     for kind in (ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_CELL_DIRICHLET,
                                  ibm.IBM_FIELD_FACE_DIRICHLET):
@@ -73,7 +73,7 @@ def test_dft_mode_solves_match_oracle(shape):
                         got = host(u)
                         if kind == ibm.IBM_FIELD_FACE_DIRICHLET:
                             got, href = got[1:], href[1:]
-                        assert rel_l2(got, href) <= TOL_FP32, (kind, rel_l2(got, href))
+                        assert rel_err(got, href) <= TOL_FP32, (kind, rel_err(got, href))
                 ibm.ibm_plan_check(plan)
             finally:
                 ibm.ibm_plan_destroy(plan)
@@ -106,13 +106,13 @@ def test_dft_mode_triply_periodic(shape):
     ref, _ = O.poisson_solve(b32, g, ybc=O.PERIODIC)
     plan = _plan(nx, ny, nz, g, 1, DFT, bc=ibm.IBM_BC_TRIPLY_PERIODIC)
     try:
-        assert rel_l2(_poisson(plan, b32), ref) <= TOL_FP32
+        assert rel_err(_poisson(plan, b32), ref) <= TOL_FP32
         href = O.helmholtz_solve(b32, g, 0.02, O.PERIODIC)
         rhs = dev(b32, torch.float32)
         u = torch.empty_like(rhs)
         ibm.ibm_helmholtz_solve(plan, 0.02, ibm.IBM_FIELD_PERIODIC, rhs, u)
         torch.cuda.synchronize()
-        assert rel_l2(host(u), href) <= TOL_FP32
+        assert rel_err(host(u), href) <= TOL_FP32
     finally:
         ibm.ibm_plan_destroy(plan)
 
@@ -128,7 +128,7 @@ def test_dft_mode_in_place_and_repeated():
         x = dev(b32, torch.float32)
         ibm.ibm_poisson_solve(plan, x, x)
         torch.cuda.synchronize()
-        assert rel_l2(host(x), ref) <= TOL_FP32
+        assert rel_err(host(x), ref) <= TOL_FP32
         rhs = dev(b32, torch.float32)
         outs = []
         for _ in range(10):
@@ -141,19 +141,24 @@ def test_dft_mode_in_place_and_repeated():
         ibm.ibm_plan_destroy(plan)
 
 
-def test_bounded_wait_runs_out_and_plan_stays_usable():
-    """A wait on an mbarrier that nothing completes (the bounded-wait path of
-    the tensor-core and bulk-copy kernels) gives up after its limit,
-    reports IBM_ERR_TIMEOUT through the plan's error word and frees its
-    tensor memory; the same plan then solves (in the tensor-core DFT mode)
-    to the oracle."""
+@pytest.mark.parametrize("path", ["tensor_memory", "bulk_copy"])
+def test_bounded_wait_runs_out_and_plan_stays_usable(path):
+    """A wait that cannot complete gives up after its limit, reports
+    IBM_ERR_TIMEOUT through the plan's error word and leaves the context
+    usable: the same plan then solves (in the tensor-core DFT mode) to the
+    oracle.  Two paths: a wait on an mbarrier that nothing completes while
+    the CTA holds tensor memory (the tensor-core kernels' wait, which frees
+    the memory before returning), and a wait on a real in-bounds bulk copy
+    whose barrier expects twice its bytes (the tile kernels' wait, which
+    waits once more for copies in flight before returning; two limits)."""
     import time
+    code = {"tensor_memory": ibm.IBM_SELFTEST_TENSOR_MEMORY, "bulk_copy": ibm.IBM_SELFTEST_BULK_COPY}[path]
     nx, ny, nz = 32, 16, 32
     g = grid(nx, ny, nz)
     plan = _plan(nx, ny, nz, g, 1, DFT)
     try:
         t0 = time.perf_counter()
-        ibm.ibm_selftest_timeout(plan, 50.0)
+        ibm.ibm_selftest_timeout(plan, 50.0, path=code)
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         assert 0.04 <= dt < 5.0, dt
@@ -163,10 +168,13 @@ def test_bounded_wait_runs_out_and_plan_stays_usable():
         ibm.ibm_plan_check(plan)  # the word was cleared
         b32 = (synth.white_noise(nx, ny, nz, workload=94, stream=0) + 0.2).astype(np.float32).astype(np.float64)
         ref, _ = O.poisson_solve(b32, g)
-        assert rel_l2(_poisson(plan, b32), ref) <= TOL_FP32
+        assert rel_err(_poisson(plan, b32), ref) <= TOL_FP32
         ibm.ibm_plan_check(plan)
         with pytest.raises(ibm.IbmError) as e:
-            ibm.ibm_selftest_timeout(plan, 0.0)
+            ibm.ibm_selftest_timeout(plan, 0.0, path=code)
+        assert e.value.code == ibm.IBM_ERR_ARG
+        with pytest.raises(ibm.IbmError) as e:
+            ibm.ibm_selftest_timeout(plan, 10.0, path=7)
         assert e.value.code == ibm.IBM_ERR_ARG
     finally:
         ibm.ibm_plan_destroy(plan)

@@ -24,7 +24,7 @@ import pytest
 from oracle import ibm_oracle as O
 from paper_2406_19920_gb300 import synth
 import paper_2406_19920_gb300 as ibm
-from tests.gpu_util import TOL_FP32, TOL_FP64, dev, host, rel_l2
+from tests.gpu_util import TOL_FP32, TOL_FP64, dev, host, rel_err
 from tests.test_gpu_substep import TOL_STAGE_FP32, _run_gpu
 
 pytestmark = pytest.mark.gpu
@@ -50,9 +50,9 @@ def _f32(a):
 
 
 def _stage_errors(got, ref, rinfo):
-    errs = {k: rel_l2(got[k], ref[k]) for k in ("u", "v", "w", "p")}
-    errs.update({"N%d" % c: rel_l2(got["N"][c], ref["N_prev"][c]) for c in range(3)})
-    errs["F"] = rel_l2(got["F"], rinfo["F"])
+    errs = {k: rel_err(got[k], ref[k]) for k in ("u", "v", "w", "p")}
+    errs.update({"N%d" % c: rel_err(got["N"][c], ref["N_prev"][c]) for c in range(3)})
+    errs["F"] = rel_err(got["F"], rinfo["F"])
     return errs
 
 
@@ -87,7 +87,7 @@ def test_poisson_256_full_size():
             phi = torch.empty_like(rhs)
             ibm.ibm_poisson_solve(plan, rhs, phi)
             torch.cuda.synchronize()
-            err = rel_l2(host(phi), ref)
+            err = rel_err(host(phi), ref)
             assert err <= tol, (prec, err)
             ibm.ibm_plan_check(plan)
         finally:

@@ -19,7 +19,7 @@ import pytest
 from oracle import ibm_oracle as O
 from paper_2406_19920_gb300 import synth
 import paper_2406_19920_gb300 as ibm
-from tests.gpu_util import TOL_FP32, TOL_FP64, grid, rel_l2
+from tests.gpu_util import TOL_FP32, TOL_FP64, grid, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -102,12 +102,12 @@ def test_results_alone_equal_results_in_the_mix():
         alone, res1 = _serve([q], n_streams=1)
         assert res1[0][0] == ibm.IBM_OK
         tol = TOL_FP64 if q["prec"] == ibm.IBM_FP64 else TOL_FP32
-        assert rel_l2(mixed[i], alone[0]) <= tol, (i, q["kind"], rel_l2(mixed[i], alone[0]))
+        assert rel_err(mixed[i], alone[0]) <= tol, (i, q["kind"], rel_err(mixed[i], alone[0]))
         if q["kind"] == ibm.IBM_REQ_POISSON:
             g = grid(*q["shape"])
             data = q["data"].astype(np.float32).astype(np.float64) if q["prec"] else q["data"]
             ref, _ = O.poisson_solve(data, g)
-            assert rel_l2(mixed[i], ref) <= tol
+            assert rel_err(mixed[i], ref) <= tol
 
 
 def test_substep_through_server_matches_oracle():
@@ -127,7 +127,7 @@ def test_substep_through_server_matches_oracle():
     mk = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=(0.1, 0.0, 0.0))
     ref, _ = O.rk_stage(st, mk, 1, 1e-3, 1e-2, g)
     for c, k in enumerate(("u", "v", "w", "p")):
-        assert rel_l2(outs[0][c], ref[k]) <= 1e-11
+        assert rel_err(outs[0][c], ref[k]) <= 1e-11
 
 
 def test_cancel_budget_and_fault_hook():

@@ -16,7 +16,7 @@ import pytest
 from oracle import ibm_oracle as O
 from paper_2406_19920_gb300 import synth
 import paper_2406_19920_gb300 as ibm
-from tests.gpu_util import TOL_FP32, TOL_FP64, dev, grid, host, rel_l2
+from tests.gpu_util import TOL_FP32, TOL_FP64, dev, grid, host, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -50,7 +50,7 @@ def test_poisson_fp64_matches_oracle(shape):
         rhs = dev(b, torch.float64)
         phi = torch.empty_like(rhs)
         info = ibm.ibm_poisson_solve(plan, rhs, phi, info=True)
-        assert rel_l2(host(phi), ref) <= TOL_FP64
+        assert rel_err(host(phi), ref) <= TOL_FP64
         assert abs(info["removed_mean"] - mean_b) <= 1e-12 * max(1.0, abs(mean_b))
         assert info["rel_residual"] < 1e-12
     finally:
@@ -69,7 +69,7 @@ def test_poisson_fp32_refined_matches_oracle(shape, refine):
         rhs = dev(b32, torch.float32)
         phi = torch.empty_like(rhs)
         info = ibm.ibm_poisson_solve(plan, rhs, phi, info=True)
-        assert rel_l2(host(phi), ref) <= TOL_FP32
+        assert rel_err(host(phi), ref) <= TOL_FP32
         assert info["refine_iters"] == refine
     finally:
         ibm.ibm_plan_destroy(plan)
@@ -88,7 +88,7 @@ def test_poisson_workload0_eigen_rhs_both_precisions():
             phi = torch.empty_like(rhs)
             ibm.ibm_poisson_solve(plan, rhs, phi)
             torch.cuda.synchronize()
-            assert rel_l2(host(phi), ref) <= tol
+            assert rel_err(host(phi), ref) <= tol
         finally:
             ibm.ibm_plan_destroy(plan)
 
@@ -102,7 +102,7 @@ def test_poisson_in_place_and_128_lowpass():
     try:
         x = dev(b, torch.float32)
         info = ibm.ibm_poisson_solve(plan, x, x, info=True)
-        err = rel_l2(host(x), ref)
+        err = rel_err(host(x), ref)
         assert err <= TOL_FP32, (err, info)
     finally:
         ibm.ibm_plan_destroy(plan)
@@ -126,7 +126,7 @@ def test_helmholtz_matches_oracle(shape, bc, c):
             ibm.ibm_helmholtz_solve(plan, c, bc, rhs, u)
             torch.cuda.synchronize()
             got = host(u)
-            assert rel_l2(got, ref) <= tol, (prec, rel_l2(got, ref))
+            assert rel_err(got, ref) <= tol, (prec, rel_err(got, ref))
             if bc == ibm.IBM_FIELD_FACE_DIRICHLET:
                 assert np.all(got[0] == 0.0)
         finally:
@@ -175,12 +175,12 @@ def test_every_plane_mode_matches_oracle(shape):
                 phi = torch.empty_like(rhs)
                 ibm.ibm_poisson_solve(plan, rhs, phi)
                 torch.cuda.synchronize()
-                assert rel_l2(host(phi), ref) <= tol, (mode, prec, rel_l2(host(phi), ref))
+                assert rel_err(host(phi), ref) <= tol, (mode, prec, rel_err(host(phi), ref))
                 if prec == ibm.IBM_FP32_REFINED:
                     u = torch.empty_like(rhs)
                     ibm.ibm_helmholtz_solve(plan, 0.01, ibm.IBM_FIELD_CELL_DIRICHLET, rhs, u)
                     torch.cuda.synchronize()
-                    assert rel_l2(host(u), href) <= tol, (mode, rel_l2(host(u), href))
+                    assert rel_err(host(u), href) <= tol, (mode, rel_err(host(u), href))
                 ibm.ibm_plan_check(plan)
             finally:
                 ibm.ibm_plan_destroy(plan)
@@ -214,13 +214,13 @@ def test_every_pencil_kernel_matches_oracle(shape):
                 phi = torch.empty_like(rhs)
                 ibm.ibm_poisson_solve(plan, rhs, phi)
                 torch.cuda.synchronize()
-                assert rel_l2(host(phi), ref) <= tol, (mode, prec, rel_l2(host(phi), ref))
+                assert rel_err(host(phi), ref) <= tol, (mode, prec, rel_err(host(phi), ref))
                 if prec == ibm.IBM_FP32_REFINED:
                     for bc, href in helm.items():
                         u = torch.empty_like(rhs)
                         ibm.ibm_helmholtz_solve(plan, 0.02, bc, rhs, u)
                         torch.cuda.synchronize()
-                        assert rel_l2(host(u), href) <= tol, (mode, bc, rel_l2(host(u), href))
+                        assert rel_err(host(u), href) <= tol, (mode, bc, rel_err(host(u), href))
                 ibm.ibm_plan_check(plan)
             finally:
                 ibm.ibm_plan_destroy(plan)
@@ -247,7 +247,7 @@ def test_segmented_sweep_unrefined_fp32_accuracy(shape):
             phi = torch.empty_like(rhs)
             ibm.ibm_poisson_solve(plan, rhs, phi)
             torch.cuda.synchronize()
-            errs[mode] = rel_l2(host(phi), ref)
+            errs[mode] = rel_err(host(phi), ref)
         finally:
             ibm.ibm_plan_destroy(plan)
     assert errs[4] <= 1e-5, errs
@@ -276,7 +276,7 @@ def test_fp32_fields_must_be_16_byte_aligned():
         phi = out[4:4 + n].view(ny, nz, nx)
         ibm.ibm_poisson_solve(plan, rhs, phi)
         torch.cuda.synchronize()
-        assert rel_l2(host(phi), ref) <= TOL_FP32
+        assert rel_err(host(phi), ref) <= TOL_FP32
     finally:
         ibm.ibm_plan_destroy(plan)
 
@@ -302,23 +302,23 @@ def test_solves_with_wall_data_match_oracle(prec, shape):
         phi = torch.empty_like(rhs)
         info = ibm.ibm_poisson_solve_bc(plan, rhs, phi, glo, ghi, info=True)
         ref, removed = O.poisson_solve(b, g, q_lo=lo, q_hi=hi)
-        assert rel_l2(host(phi), ref) <= tol
+        assert rel_err(host(phi), ref) <= tol
         assert abs(info["removed_mean"] - removed) <= 1e-5 * max(1.0, abs(removed))
         for bc in (ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_CELL_DIRICHLET, ibm.IBM_FIELD_FACE_DIRICHLET):
             u = torch.empty_like(rhs)
             ibm.ibm_helmholtz_solve_bc(plan, 0.02, bc, rhs, u, glo, ghi)
             torch.cuda.synchronize()
             href = O.helmholtz_solve(b, g, 0.02, bc, lo, hi)
-            assert rel_l2(host(u), href) <= tol, bc
+            assert rel_err(host(u), href) <= tol, bc
             # one wall only
             ibm.ibm_helmholtz_solve_bc(plan, 0.02, bc, rhs, u, None, ghi)
             torch.cuda.synchronize()
-            assert rel_l2(host(u), O.helmholtz_solve(b, g, 0.02, bc, None, hi)) <= tol, bc
+            assert rel_err(host(u), O.helmholtz_solve(b, g, 0.02, bc, None, hi)) <= tol, bc
         assert torch.equal(rhs, keep)
         # in place
         ibm.ibm_helmholtz_solve_bc(plan, 0.02, ibm.IBM_FIELD_CELL_DIRICHLET, rhs, rhs, glo, ghi)
         torch.cuda.synchronize()
-        assert rel_l2(host(rhs), O.helmholtz_solve(b, g, 0.02, ibm.IBM_FIELD_CELL_DIRICHLET, lo, hi)) <= tol
+        assert rel_err(host(rhs), O.helmholtz_solve(b, g, 0.02, ibm.IBM_FIELD_CELL_DIRICHLET, lo, hi)) <= tol
         ibm.ibm_plan_check(plan)
     finally:
         ibm.ibm_plan_destroy(plan)

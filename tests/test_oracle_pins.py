@@ -416,6 +416,38 @@ def test_spread_conserves_force_and_moment_and_is_adjoint(kernel):
     assert abs(lhs - rhs) < 1e-12 * abs(lhs) + 1e-12
 
 
+@pytest.mark.parametrize("kernel", [O.ROMA3, O.PESKIN4])
+def test_wall_rule_is_the_support_of_the_delta_kernel(kernel):
+    """The markers clear_of_walls accepts are exactly those whose stencil,
+    enumerated point by point with the delta kernel's own weights, puts
+    non-zero weight only on stored unknowns of every component (cell rows
+    0..ny-1, v faces 1..ny-1): the one-dimensional support of phi has
+    half-width 1.5 (ROMA3) or 2 (PESKIN4) cells, and v's wall face sits on
+    the wall.  Brute force over Y sweeping both wall regions."""
+    g = _grid(8, 12, 8, Ly=1.2)
+    nx, ny, nz, hx, hy, hz = g
+    S = 3 if kernel == O.ROMA3 else 4
+    Y = np.concatenate([np.linspace(0.0, 3.0 * hy, 601), np.linspace(g[4] * ny - 3.0 * hy, g[4] * ny, 601)])
+    Y = Y[np.abs(Y / hy - round(S / 2)) > 1e-9]          # off the exact boundary
+    Y = Y[np.abs((ny * hy - Y) / hy - round(S / 2)) > 1e-9]
+    X = np.column_stack([np.full_like(Y, 0.37), Y, np.full_like(Y, 1.1)])
+    ok = O.clear_of_walls(X, g, kernel)
+    s = np.arange(-S, S + 1)
+    for i, y in enumerate(Y):
+        needs_outside = False
+        for lo, origin in ((0, 0.5), (0, 0.5), (1, 0.0)):  # u, w (cell rows), v (faces)
+            j = np.floor(y / hy - origin) + s            # candidate rows around the marker
+            wgt = O.delta_1d(y / hy - origin - j, kernel)
+            hit = j[wgt > 0]
+            needs_outside |= bool(np.any((hit < lo) | (hit > ny - 1)))
+        assert ok[i] == (not needs_outside), (y / hy, ok[i])
+    assert ok.any() and (~ok).any()
+    with pytest.raises(ValueError):
+        O.interp(X, *np.zeros((3, ny, nz, nx)), g, kernel)
+    with pytest.raises(ValueError):
+        O.spread(X, np.ones_like(X), np.ones(len(X)), g, kernel)
+
+
 def test_interp_spread_periodic_wrap():
     """A marker at x = 0 sees the same neighbourhood as one at x = Lx."""
     g = _grid(16, 16, 16)
