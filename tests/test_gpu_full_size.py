@@ -25,7 +25,7 @@ from oracle import ibm_oracle as O
 from paper_2406_19920_gb300 import synth
 import paper_2406_19920_gb300 as ibm
 from tests.gpu_util import TOL_FP32, TOL_FP64, dev, host, rel_err
-from tests.test_gpu_substep import TOL_STAGE_FP32, _run_gpu
+from tests.test_gpu_substep import TOL_STAGE_FP32, TOL_STAGE_FP32_N, _run_gpu, stage_ok
 
 pytestmark = pytest.mark.gpu
 
@@ -70,7 +70,8 @@ def test_stage_128_full_size():
     got = _run_gpu(g, fields, Np, X0, dV, 1, DT, NU, ibm.IBM_MOTION_TRANSLATE, (0.1, 0.0, 0.0),
                    ibm.IBM_FP32_REFINED, torch.float32, 0.0)
     errs = _stage_errors(got, ref, rinfo)
-    assert max(errs.values()) <= TOL_STAGE_FP32, errs
+    assert stage_ok(errs, TOL_STAGE_FP32, TOL_STAGE_FP32_N), errs
+    print("stage errors", errs)
     assert got["info"]["div_max"] <= 1e-5 * max(1.0, got["info"]["div_before"]), got["info"]
 
 
@@ -117,4 +118,5 @@ def test_plate_stage_full_size():
     mk = dict(X0=X0, dV=dV, kind=O.MOTION_HEAVE, params=(0.5, 1.0))
     ref, rinfo = O.rk_stage(st, mk, 1, DT, NU, g)
     errs = _stage_errors(got, ref, rinfo)
-    assert max(errs.values()) <= TOL_STAGE_FP32, errs
+    assert stage_ok(errs, TOL_STAGE_FP32, TOL_STAGE_FP32_N), errs
+    print("stage errors", errs)

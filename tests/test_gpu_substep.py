@@ -30,6 +30,18 @@ torch = pytest.importorskip("torch")
 
 TOL_STAGE_FP64 = 1e-11
 TOL_STAGE_FP32 = 3e-6
+# The stored advection term N = div(u u) in FP32: each flux is a product of
+# two-point averages rounded to FP32 (relative error a few eps32 of |u|^2)
+# and N is a difference of fluxes over h, of size |u|^2 k; its relative
+# error is therefore ~ eps32 / (k h) per point (about 1e-6 for the k <= 16
+# content of the 384-cell grids), and the max over 25M points runs several
+# times higher (measured: 2.1e-6 L2, 6.3e-6 max at 384x256x256).
+TOL_STAGE_FP32_N = 1e-5
+
+
+def stage_ok(errs, tol, tol_n):
+    """Every field within tol, the stored advection terms (N0..N2) within tol_n."""
+    return all(v <= (tol_n if k.startswith("N") else tol) for k, v in errs.items())
 
 
 def _setup(nx, ny, nz, nmk, npdt, wl):
@@ -127,7 +139,8 @@ def test_inout_substep_matches_oracle(shape, stage, prec):
     errs.update({"N%d" % c: rel_err(got["N"][c], ref["N_prev"][c]) for c in range(3)})
     errs.update({k: rel_err(got[k], ref["inout"][k]) for k in ("u_out", "v_out", "w_out")})
     errs["F"] = rel_err(got["F"], rinfo["F"])
-    assert max(errs.values()) <= tol, errs
+    assert stage_ok(errs, tol, tol if prec == ibm.IBM_FP64 else TOL_STAGE_FP32_N), errs
+    print("stage errors", errs)
     assert np.all(got["v"][0] == npdt(io["v_in"]))
     # outflow = inflow to rounding of the stored outlet plane
     assert abs(got["v_out"].mean() - io["v_in"]) <= (1e-14 if prec == ibm.IBM_FP64 else 1e-6)
@@ -159,7 +172,8 @@ def test_inout_full_rk_step_matches_oracle(prec):
     tol = 3 * (TOL_STAGE_FP64 if prec == ibm.IBM_FP64 else TOL_STAGE_FP32)
     errs = {k: rel_err(got[k], st[k]) for k in ("u", "v", "w", "p")}
     errs.update({k: rel_err(got[k], ref_io[k]) for k in ("u_out", "v_out", "w_out")})
-    assert max(errs.values()) <= tol, errs
+    assert stage_ok(errs, tol, tol if prec == ibm.IBM_FP64 else TOL_STAGE_FP32_N), errs
+    print("stage errors", errs)
     assert abs(got["t"] - dt) < 1e-15
 
 
@@ -205,7 +219,8 @@ def test_substep_matches_oracle(shape, stage, prec):
     errs = {k: rel_err(got[k], ref[k]) for k in ("u", "v", "w", "p")}
     errs.update({"N%d" % c: rel_err(got["N"][c], ref["N_prev"][c]) for c in range(3)})
     errs["F"] = rel_err(got["F"], rinfo["F"])
-    assert max(errs.values()) <= tol, errs
+    assert stage_ok(errs, tol, tol if prec == ibm.IBM_FP64 else TOL_STAGE_FP32_N), errs
+    print("stage errors", errs)
     a, b = O.RK_ALPHA[stage - 1], O.RK_BETA[stage - 1]
     assert abs(got["t"] - (a + b) * dt) < 1e-15
     assert np.all(got["v"][0] == 0.0)
@@ -242,7 +257,7 @@ def test_three_field_helmholtz_every_kernel(prec):
             del os.environ["IBM_PLANE_MODE_FIELDS"]
             del os.environ["IBM_PENCIL_MODE"]
         errs = {k: rel_err(got[k], ref[k]) for k in ("u", "v", "w", "p")}
-        assert max(errs.values()) <= tol, (plane_mode, pencil_mode, errs)
+        assert stage_ok(errs, tol, tol if prec == ibm.IBM_FP64 else TOL_STAGE_FP32_N), (plane_mode, pencil_mode, errs)
         assert np.all(got["v"][0] == 0.0)
 
 
@@ -282,6 +297,7 @@ def test_substep_with_gather_spreading(prec):
     runs = [_run_gpu(g, [u, v, w, p], Np, X0, dV, 2, dt, nu, ibm.IBM_MOTION_TRANSLATE, params, prec, dt_t, 0.0,
                      spread=ibm.IBM_SPREAD_GATHER) for _ in range(2)]
     errs = {k: rel_err(runs[0][k], ref[k]) for k in ("u", "v", "w", "p")}
-    assert max(errs.values()) <= tol, errs
+    assert stage_ok(errs, tol, tol if prec == ibm.IBM_FP64 else TOL_STAGE_FP32_N), errs
+    print("stage errors", errs)
     for k in ("u", "v", "w", "p"):
         assert np.array_equal(runs[0][k], runs[1][k]), k
