@@ -203,6 +203,17 @@ template <typename T>
 cudaError_t launch_ypencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const cplx<T> *twy, const T *lamx,
                            const T *lamz, const T *lamy, double *mean_out, cudaStream_t st);
 
+// The fused FP32 solve (slab.cu) for wall-bounded grids with ny and nz in
+// {64, 128, 256}: phase 0 the x rows forward into the kx-major spectrum
+// S[kx][y][z], phase 1 the slab kernel (z transforms and the y sweep of one
+// kx slab per cluster, the FP64 zero mode included), phase 2 the x rows
+// inverse (out = addend + scale x).  Single fields with unknowns on every
+// row (j0 = 0) only.
+bool slab_supported(int nx, int ny, int nz);
+cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, float2 *S, float *out,
+                              const float *addend, const float2 *twx, const float2 *twz, const float *lamx,
+                              const float *lamz, double *mean_out, float scale, cudaStream_t st, int phase);
+
 // Residual r = b - (sigma x + tau L x) with float-float arithmetic for FP32.
 struct StencilCoef {
   double cx, cy, cz;  // 1/h^2 per axis

@@ -121,6 +121,7 @@ extern "C" int ibm_poisson_solve_noalloc(int nx, int ny, int nz, const double h[
   p.nx = nx; p.ny = ny; p.nz = nz; p.P = P;
   p.bc = IBM_BC_PXZ_WALL_Y;
   p.use_plane = default_plane_mode<float>(nx, ny, nz);
+  p.use_slab = default_use_slab(IBM_FP32_REFINED, IBM_BC_PXZ_WALL_Y, nx, ny, nz) ? 1 : 0;
   p.use_plane_fields = 0;
   p.h[0] = h[0]; p.h[1] = h[1]; p.h[2] = h[2];
   p.precision = IBM_FP32_REFINED;

@@ -179,9 +179,33 @@ static int dalloc(ibm_plan_s *p, void **ptr, size_t bytes) {
 // ---------------------------------------------------------------------------
 // solve
 // ---------------------------------------------------------------------------
+bool default_use_slab(int precision, int bc, int nx, int ny, int nz) {
+  const bool off = getenv("IBM_SLAB") && atoi(getenv("IBM_SLAB")) == 0;  // read per plan (A/B timing, tests)
+  return !off && precision == IBM_FP32_REFINED && bc == IBM_BC_PXZ_WALL_Y && slab_supported(nx, ny, nz);
+}
+
+// The fused slab path: three passes, each reading and writing the field once.
+static int solve_once_slab(ibm_plan_s *p, const PencilParams &pp, const float *in, float *out, const float *addend,
+                           double *mean_out, cudaStream_t st) {
+  float2 *S = static_cast<float2 *>(p->S);
+  const float2 *twx = static_cast<const float2 *>(p->twx), *twz = static_cast<const float2 *>(p->twz);
+  const float *lamx = static_cast<const float *>(p->lamx), *lamz = static_cast<const float *>(p->lamz);
+  const float scale = (float)(1.0 / ((double)p->nx * p->nz));
+  static const int kinds[3] = {IBM_K_FORWARD, IBM_K_PENCIL, IBM_K_INVERSE};
+  for (int phase = 0; phase < 3; ++phase) {
+    ProfScope ps(p, kinds[phase], st);
+    IBM_CUDA_TRY(launch_slab_solve(pp, p->nx, in, S, out, addend, twx, twz, lamx, lamz, mean_out, scale, st, phase));
+  }
+  return IBM_OK;
+}
+
 template <typename T>
 static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out, const T *addend,
                       double *mean_out, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (p->use_slab && pp.j0 == 0 && pp.nb == 1 && !pp.periodic)
+      return solve_once_slab(p, pp, in, out, addend, mean_out, st);
+  }
   TransformGeom gf = geom_of(p), gi = geom_of(p);
   if (pp.zero_mode) {
     gf.zrhs = p->zbuf;                               // plane sums of b (FP64)
@@ -462,6 +486,7 @@ int ibm_plan_create(int nx, int ny, int nz, int bc, const double h[3], int preci
   // DFT products) and fails the plan when the shape has no such mode (A/B
   // timing and tests)
   p->use_plane = precision == IBM_FP64 ? default_plane_mode<double>(nx, ny, nz) : default_plane_mode<float>(nx, ny, nz);
+  p->use_slab = default_use_slab(precision, bc, nx, ny, nz) ? 1 : 0;
   // three-field solves: split passes (their small CTAs share the SMs
   // between fields); IBM_PLANE_MODE_FIELDS=m forces another mode
   p->use_plane_fields = 0;

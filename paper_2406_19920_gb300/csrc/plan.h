@@ -36,6 +36,7 @@ struct ibm_plan_s {
   int use_plane = 1; // plane mode: 0 split x / z passes; 1 one CTA per plane; C >= 2 a cluster of C CTAs per plane;
                      // -1 (kPlaneDft) tensor-core DFT products (FP32, short planes)
   int use_plane_fields = 0; // plane mode of three-field solves
+  int use_slab = 0;  // FP32 single-field solves through the fused slab path (slab.cu)
   size_t esz;        // element size: 4 or 8
   size_t npts;       // nx * ny * nz
   size_t nspec;      // ny * nz * P complex entries
@@ -116,6 +117,11 @@ int plan_solve(ibm_plan_s *p, int kind, double c, int field_bc, const void *in, 
 // addend).  Allocates the extra spectra on first use.
 int plan_solve_fields(ibm_plan_s *p, double c, int nb, const int *field_bc, const void *const *in, void *const *out,
                       const void *const *addend, cudaStream_t st);
+
+// Whether a plan of this kind takes the fused slab path for its single-field
+// solves by default (FP32, wall branch, supported shape; IBM_SLAB=0 turns it
+// off).
+bool default_use_slab(int precision, int bc, int nx, int ny, int nz);
 
 // Autotuner result for one shape (batch.cu).
 struct TuneChoice {

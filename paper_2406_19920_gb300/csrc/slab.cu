@@ -1,0 +1,478 @@
+// slab.cu -- the fused direct solve for FP32 wall-bounded grids whose
+// (y, z) slabs fit a thread-block cluster (Sec. 2.3.3, S1.1 + S1.2 / S2.1 +
+// S2.2, the same method as the split passes in three global passes):
+//
+//   1. x rows forward (k_rows_fwd_t): every real row pair -> half spectra,
+//      written kx-major, S[kx][y][z], so that one kx slab [y][z] is
+//      contiguous;
+//   2. slab (k_slab): a cluster of C CTAs per kx, CTA r holding the 32 rows
+//      y in [32 r, 32 r + 32) of the slab in shared memory (one bulk copy
+//      each half): the forward z transform of every row, the tridiagonal
+//      solve along y of every kz pencil as the segmented two-ended sweep of
+//      k_pencil_seg with one 32-row segment per CTA (the per-segment
+//      carries cross the cluster through distributed shared memory), the
+//      FP64 zero mode in the kx = 0 cluster, the inverse z transform, and
+//      one bulk copy back;
+//   3. x rows inverse (k_rows_inv_t): half spectra -> real rows, scaled by
+//      1 / (nx nz), plus the optional addend.
+//
+// Each pass reads and writes the field once: 24 B per point in FP32, the
+// method's compulsory traffic, against 40 B for the split passes (whose z
+// passes read and write the spectrum twice more).  The z transforms and the
+// sweep run on data already in shared memory.
+#include <cooperative_groups.h>
+
+#include <algorithm>
+#include <mutex>
+
+#include "fft2.cuh"
+#include "internal.h"
+#include "seg.cuh"
+#include "tma.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace ibm {
+
+// ---------------------------------------------------------------------------
+// x rows with the kx-major spectrum.  Element (kx, row) of the spectrum is at
+// S[kx * rows + row] with row = y nz + z (rows = ny nz).  A CTA takes RP
+// consecutive row pairs (2p, 2p + 1: the same y, consecutive z).
+//   forward: step 1 with lanes along n1 (the row's consecutive x), the
+//            exchange [n1][k2][p] (pitch QF, odd), step 3 with lanes along p
+//            so that each kx writes 2 RP consecutive complex values;
+//   inverse: step 1 with lanes along p (each kx read as 2 RP consecutive
+//            values), the exchange [p][n1][k2] (pitch QI, odd), step 3 with
+//            lanes along k2 (consecutive x of one row).
+// ---------------------------------------------------------------------------
+constexpr int kRowT = 256;
+
+template <int N> struct RowT {
+  static constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
+  static constexpr int RP = kRowT / N1 > 1 ? kRowT / N1 : 1;  // row pairs per CTA
+  static constexpr int QF = N2 * RP + 1;
+  static constexpr int QI = N1 * N2 + 1;
+  static constexpr size_t smem_f = sizeof(float2) * ((size_t)N + (size_t)N1 * QF);
+  static constexpr size_t smem_i = sizeof(float2) * ((size_t)N + (size_t)RP * QI);
+};
+
+template <int N>
+__global__ void __launch_bounds__(kRowT)
+k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 *__restrict__ tw, int npairs,
+             int rows, float in_scale) {
+  using Cfg = RowT<N>;
+  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
+  float2 *X = tw2 + N;  // [N1][k2][p]
+  load_step_twiddles<float, N>(tw2, tw);
+  pdl_wait();  // the input field is the predecessor's output
+  const int pair0 = blockIdx.x * RP;
+  const int np = min(RP, npairs - pair0);
+  __syncthreads();
+  for (int job = threadIdx.x; job < np * N1; job += kRowT) {
+    const int p = job / N1, n1 = job - p * N1;
+    const float *a = in + (size_t)(pair0 + p) * 2 * N;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[N + n1 + N1 * n2] * in_scale);
+    reg_dft<false, N2>(v);
+    float2 *x = X + n1 * QF + p;
+    x[0] = v[0];
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) x[k2 * RP] = cmul(v[k2], tw2[k2 * N1 + n1]);
+  }
+  __syncthreads();
+  // step 3: the columns q and N2 - q give Z_k and Z_{N-k} together; the half
+  // spectra of the pair's rows are A_k = (Z_k + conj Z_{N-k}) / 2 and
+  // B_k = -i (Z_k - conj Z_{N-k}) / 2 for k <= N/2
+  for (int job = threadIdx.x; job < np * J3; job += kRowT) {
+    const int q = job / np, p = job - q * np;
+    float2 *dA = S + 2 * (size_t)(pair0 + p);
+    auto put = [&](int k, float2 zk, float2 zn) {
+      float2 *d = dA + (size_t)k * rows;
+      d[0] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+      d[1] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+    };
+    float2 u[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[n1 * QF + q * RP + p];
+    reg_dft<false, N1>(u);
+    if (q == 0) {
+#pragma unroll
+      for (int k1 = 0; k1 <= N1 / 2; ++k1) put(N2 * k1, u[k1], u[(N1 - k1) % N1]);
+    } else if (q == N2 / 2) {
+#pragma unroll
+      for (int k1 = 0; k1 < N1 / 2; ++k1) put(q + N2 * k1, u[k1], u[N1 - 1 - k1]);
+    } else {
+      float2 w[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) w[n1] = X[n1 * QF + (N2 - q) * RP + p];
+      reg_dft<false, N1>(w);
+#pragma unroll
+      for (int k1 = 0; k1 < N1 / 2; ++k1) {
+        put(q + N2 * k1, u[k1], w[N1 - 1 - k1]);
+        put(N2 - q + N2 * k1, w[k1], u[N1 - 1 - k1]);
+      }
+    }
+  }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRowT)
+k_rows_inv_t(const float2 *__restrict__ S, float *out, const float *add, const float2 *__restrict__ tw, int npairs,
+             int rows, float scale) {
+  using Cfg = RowT<N>;
+  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QI = Cfg::QI;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
+  float2 *X = tw2 + N;  // [p][n1][k2]
+  load_step_twiddles<float, N>(tw2, tw);
+  pdl_wait();  // the spectrum is the predecessor's output
+  const int pair0 = blockIdx.x * RP;
+  const int np = min(RP, npairs - pair0);
+  __syncthreads();
+  // step 1: Z_n = A_n + i B_n (imaginary parts of bins 0 and N/2 dropped) and
+  // its Hermitian extension for n > N/2
+  for (int job = threadIdx.x; job < np * N1; job += kRowT) {
+    const int n1 = job / np, p = job - n1 * np;
+    const float2 *sA = S + 2 * (size_t)(pair0 + p);
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) {
+      const int n = n1 + N1 * n2;
+      if (n <= N / 2) {
+        const float2 *s = sA + (size_t)n * rows;
+        float2 a = s[0], b = s[1];
+        if (n == 0 || n == N / 2) { a.y = 0.f; b.y = 0.f; }
+        v[n2] = make_float2(a.x - b.y, a.y + b.x);
+      } else {
+        const float2 *s = sA + (size_t)(N - n) * rows;
+        const float2 a = s[0], b = s[1];
+        v[n2] = make_float2(a.x + b.y, b.x - a.y);
+      }
+    }
+    reg_dft<true, N2>(v);
+    float2 *x = X + p * QI + n1 * N2;
+    x[0] = v[0];
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmulc(v[k2], tw2[k2 * N1 + n1]);
+  }
+  __syncthreads();
+  for (int job = threadIdx.x; job < np * N2; job += kRowT) {
+    const int p = job / N2, k2 = job - p * N2;
+    const size_t r = 2 * (size_t)(pair0 + p);
+    float *da = out + r * N, *db = da + N;
+    const float *aa = add ? add + r * N : nullptr;
+    float a0[N1], a1[N1];
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {  // the addend's loads go out first
+      a0[k1] = aa ? aa[k2 + N2 * k1] : 0.f;
+      a1[k1] = aa ? aa[N + k2 + N2 * k1] : 0.f;
+    }
+    float2 u[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[p * QI + n1 * N2 + k2];
+    reg_dft<true, N1>(u);
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) {
+      da[k2 + N2 * k1] = fmaf(u[k1].x, scale, a0[k1]);
+      db[k2 + N2 * k1] = fmaf(u[k1].y, scale, a1[k1]);
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// The slab kernel.  Rows y of the slab are the unknowns of every kz pencil
+// (n = ny rows, j0 = 0: Poisson and the cell-centred Helmholtz kinds).  The
+// two-ended sweep splits them as k_pencil_seg does: rows 0 .. m-1 top-down,
+// rows n-1 .. m+1 bottom-up, meeting at m = n/2, in 32-row segments.  CTA r
+// < C/2 owns top segment r (rows 32 r ..), CTA r >= C/2 bottom segment
+// C/2 + (C - 1 - r) (its rows counted from the top wall); CTA C/2 also holds
+// the meeting row m as its local row 0 (its segment has 31 rows).
+// ---------------------------------------------------------------------------
+template <int NZ, int C> struct SlabCfg {
+  static constexpr int R = 32;        // rows per CTA (one sweep segment)
+  static constexpr int NY = R * C;
+  static constexpr int THREADS = NZ;  // one thread per kz pencil
+  static constexpr int N1 = TwoStep<NZ>::N1, N2 = TwoStep<NZ>::N2;
+  static constexpr int W = THREADS / N1;  // rows per z-transform round
+  static constexpr int PN = W * N2 + 1;   // exchange pitch per n1 (odd)
+  static constexpr size_t al(size_t b) { return (b + 127) & ~(size_t)127; }
+  static constexpr size_t o_slab = 0;
+  static constexpr size_t o_x = o_slab + al((size_t)R * NZ * 8);
+  static constexpr size_t xbytes = (size_t)N1 * PN * 8 > (size_t)R * NZ * 4 ? (size_t)N1 * PN * 8 : (size_t)R * NZ * 4;
+  static constexpr size_t o_tw = o_x + al(xbytes);
+  static constexpr size_t o_cf = o_tw + al((size_t)NZ * 8);
+  static constexpr size_t o_cb = o_cf + al((size_t)4 * NZ * 4);
+  static constexpr size_t o_zm = o_cb + al((size_t)2 * NZ * 4);
+  static constexpr size_t o_bar = o_zm + al((size_t)3 * NY * 8);
+  static constexpr size_t bytes = o_bar + 128;
+  static_assert(W * N1 == THREADS, "one row per N1 threads in step 1");
+  static_assert((R / 2) % W == 0, "each half of the rows is whole transform rounds");
+};
+
+__device__ __forceinline__ void cluster_arrive() { asm volatile("barrier.cluster.arrive.release.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_wait() { asm volatile("barrier.cluster.wait.acquire.aligned;" ::: "memory"); }
+__device__ __forceinline__ void cluster_sync_all() {
+  cluster_arrive();
+  cluster_wait();
+}
+
+// W rows of `rows` (row pitch NZ) transformed along z in place: step 1 with
+// thread (c, n1) (W N1 = blockDim threads), the exchange [n1][c][k2] (pitch
+// PN per n1), step 3 with job (c, k2) (W N2 jobs).
+template <int NZ, int W, bool INV>
+__device__ __forceinline__ void zfft_rows(float2 *rows, float2 *X, const float2 *tw2) {
+  constexpr int N1 = TwoStep<NZ>::N1, N2 = TwoStep<NZ>::N2, PN = W * N2 + 1;
+  {
+    const int c = threadIdx.x / N1, n1 = threadIdx.x - c * N1;
+    const float2 *row = rows + c * NZ;
+    float2 v[N2];
+#pragma unroll
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = row[n1 + N1 * n2];
+    reg_dft<INV, N2>(v);
+    float2 *x = X + n1 * PN + c * N2;
+    x[0] = v[0];
+#pragma unroll
+    for (int k2 = 1; k2 < N2; ++k2) {
+      const float2 t = tw2[k2 * N1 + n1];
+      x[k2] = INV ? cmulc(v[k2], t) : cmul(v[k2], t);
+    }
+  }
+  __syncthreads();
+  for (int job = threadIdx.x; job < W * N2; job += blockDim.x) {
+    const int c = job / N2, k2 = job - c * N2;
+    float2 u[N1];
+#pragma unroll
+    for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[n1 * PN + c * N2 + k2];
+    reg_dft<INV, N1>(u);
+    float2 *row = rows + c * NZ;
+#pragma unroll
+    for (int k1 = 0; k1 < N1; ++k1) row[k2 + N2 * k1] = u[k1];
+  }
+  __syncthreads();
+}
+
+template <int NZ, int C>
+__global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NZ, (NZ >= 256 ? 2 : 3))
+k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx, const float *__restrict__ lamz,
+       PencilParams pp, double *mean_out) {
+  using Cfg = SlabCfg<NZ, C>;
+  constexpr int R = Cfg::R, NY = Cfg::NY, W = Cfg::W, Lh = C / 2;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int rank = (int)cluster.block_rank();
+  const int kx = blockIdx.x / C;
+  const int tid = threadIdx.x;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float2 *slab = reinterpret_cast<float2 *>(smem + Cfg::o_slab);  // [R][NZ]
+  float2 *X = reinterpret_cast<float2 *>(smem + Cfg::o_x);        // z-transform exchange
+  float *ws = reinterpret_cast<float *>(smem + Cfg::o_x);         // [R][NZ] w of every row (after the transforms)
+  float2 *tw2 = reinterpret_cast<float2 *>(smem + Cfg::o_tw);
+  float *cf = reinterpret_cast<float *>(smem + Cfg::o_cf);  // [4][NZ] yhat_end.x, .y, prod w, q of the last row
+  float *cb = reinterpret_cast<float *>(smem + Cfg::o_cb);  // [2][NZ] xhat at the segment's first row
+  double *zr = reinterpret_cast<double *>(smem + Cfg::o_zm);  // zero mode (CTA 0 of the kx = 0 cluster): rhs,
+  double *zw = zr + NY;                                       // scratch,
+  double *zo = zw + NY;                                       // solution
+  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Cfg::o_bar);
+
+  // plan constants before the grid-dependency wait
+  load_step_twiddles<float, NZ>(tw2, twz);
+  const int kz = tid;
+  const float a = (float)pp.a;
+  const float g = (float)pp.g_add + (float)pp.g_mul * (lamx[kx] + lamz[kz]);
+  if (tid == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_wait();  // the spectrum is the predecessor's output
+  float2 *gslab = S + (size_t)kx * NY * NZ + (size_t)rank * R * NZ;
+  constexpr uint32_t kHalf = (uint32_t)(R / 2) * NZ * 8;
+  if (tid == 0) {
+    mbar_arrive_expect_tx(&bar[0], kHalf);
+    bulk_g2s(slab, gslab, kHalf, &bar[0]);
+    mbar_arrive_expect_tx(&bar[1], kHalf);
+    bulk_g2s(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1]);
+  }
+  // forward z transforms.  A wait that gives up leaves ok false: the CTA
+  // still reaches every cluster barrier (its peers wait there) and stores
+  // nothing.
+  bool ok = true;
+#pragma unroll 1
+  for (int r0 = 0; r0 < R; r0 += W) {
+    if (r0 == 0 || r0 == R / 2) ok = __syncthreads_and(mbar_wait(&bar[r0 == 0 ? 0 : 1], 0, pp.err) && ok);
+    zfft_rows<NZ, W, false>(slab + r0 * NZ, X, tw2);
+  }
+
+  // the zero mode's right-hand side (kx = 0): Re of bin kz = 0 of every row,
+  // the plane sums, gathered in CTA 0
+  const bool zm = pp.zero_mode && kx == 0;
+  if (zm && tid < R) cluster.map_shared_rank(zr, 0)[rank * R + tid] = (double)slab[tid * NZ].x;
+
+  // forward elimination of my segment
+  const bool top = rank < Lh;
+  const int seg = top ? rank : Lh + (C - 1 - rank);
+  const int k0 = top ? rank * R : NY - (rank + 1) * R;  // distance of my first row from its wall
+  const int len = rank == Lh ? R - 1 : R;
+  const int lr0 = top ? 0 : R - 1, lstep = top ? 1 : -1;  // local row of sweep row u: lr0 + lstep u
+  const bool live = !(zm && kz == 0);
+  const float e0 = g + a * (float)(top ? pp.beta_s : pp.beta_e);
+  const float sgn = pp.neg_rhs ? -1.f : 1.f;
+  float ep, D, z;
+  const bool cw = __all_sync(0xffffffffu, seg_pivots<float>(a, g, e0, k0, ep, D, z)) && len == R;
+  float2 v[R];
+#pragma unroll
+  for (int u = 0; u < R; ++u) v[u] = u < len ? slab[(lr0 + lstep * u) * NZ + kz] : make_float2(0.f, 0.f);
+  float *wc = ws + kz;  // w of sweep row u at wc[NZ u]
+  float2 y;
+  float prod, qlast;
+  if (cw) seg_forward<float, R, true, true, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
+  else seg_forward<float, R, false, false, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
+  cf[0 * NZ + kz] = y.x;
+  cf[1 * NZ + kz] = y.y;
+  cf[2 * NZ + kz] = prod;
+  cf[3 * NZ + kz] = qlast;
+  cluster_sync_all();  // #1: every segment's carries, row m and the zero mode's rhs are visible
+
+  // carry into my segment and the last y of both halves
+  auto rank_of = [](int s2) { return s2 < Lh ? s2 : C - 1 - (s2 - Lh); };
+  float2 c = make_float2(0.f, 0.f), yT = c, yB = c;
+#pragma unroll
+  for (int s2 = 0; s2 < C; ++s2) {
+    const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
+    if (s2 == seg) c = s2 < Lh ? yT : yB;
+    const float pw = pcf[2 * NZ + kz], ax = pcf[kz], ay = pcf[NZ + kz];
+    if (s2 < Lh) {
+      yT.x = fmaf(pw, yT.x, ax);
+      yT.y = fmaf(pw, yT.y, ay);
+    } else {
+      yB.x = fmaf(pw, yB.x, ax);
+      yB.y = fmaf(pw, yB.y, ay);
+    }
+  }
+  // meeting row: (g + a q^T + a q^B) x_m = sgn f_m + a (y^T_{m-1} + y^B_{m+1})
+  const float qT = cluster.map_shared_rank(cf, Lh - 1)[3 * NZ + kz];
+  const float qB = cluster.map_shared_rank(cf, Lh)[3 * NZ + kz];
+  const float2 fm = cluster.map_shared_rank(slab, Lh)[kz];
+  float2 xm;
+  {
+    const float rm = rcp<float>(g + a * qT + a * qB);
+    xm.x = (sgn * fm.x + a * (yT.x + yB.x)) * rm;
+    xm.y = (sgn * fm.y + a * (yT.y + yB.y)) * rm;
+  }
+  const float wconst = a * rcp<float>(a + ep);
+  float2 x;
+  if (cw) x = seg_middle<float, R, true, true, NZ>(v, len, wconst, wc, c);
+  else x = seg_middle<float, R, false, false, NZ>(v, len, wconst, wc, c);
+  cb[kz] = x.x;
+  cb[NZ + kz] = x.y;
+  // the FP64 zero mode: removed mean, pin, nullspace (one warp of CTA 0)
+  if (zm && rank == 0 && tid < 32) zero_mode_fp64(zr, zo, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);
+  cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
+
+  // x after my last row (towards the meeting row), then my rows stored
+  c = xm;
+#pragma unroll
+  for (int s2 = C - 1; s2 >= 0; --s2) {
+    if (s2 <= seg || s2 >= (top ? Lh : C)) continue;
+    const int rk = rank_of(s2);
+    const float pw = cluster.map_shared_rank(cf, rk)[2 * NZ + kz];
+    const float *pcb = cluster.map_shared_rank(cb, rk);
+    c.x = fmaf(pw, c.x, pcb[kz]);
+    c.y = fmaf(pw, c.y, pcb[NZ + kz]);
+  }
+  float2 *col = slab + lr0 * NZ + kz;
+  if (cw) seg_store<float, R, true, true, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
+  else seg_store<float, R, false, false, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
+  if (rank == Lh && live) slab[kz] = xm;
+  if (zm && tid < R) slab[tid * NZ] = make_float2((float)cluster.map_shared_rank(zo, 0)[rank * R + tid], 0.f);
+  cluster_arrive();  // #3 (arrival): this CTA reads no peer memory any more
+  __syncthreads();
+
+  // inverse z transforms and the store
+#pragma unroll 1
+  for (int r0 = 0; r0 < R; r0 += W) zfft_rows<NZ, W, true>(slab + r0 * NZ, X, tw2);
+  fence_proxy_async();
+  __syncthreads();
+  if (tid == 0) {
+    if (ok) {
+      bulk_s2g(gslab, slab, (uint32_t)R * NZ * 8);
+      bulk_commit();
+      bulk_wait_read();
+    } else {  // copies that may still be in flight land before the memory is released
+      mbar_wait(&bar[0], 0, nullptr);
+      mbar_wait(&bar[1], 0, nullptr);
+    }
+  }
+  cluster_wait();  // #3: the peers have finished reading this CTA's memory
+}
+
+// ---------------------------------------------------------------------------
+// dispatch
+// ---------------------------------------------------------------------------
+#define IBM_SLAB_ROWS_N(X) X(8) X(12) X(16) X(24) X(32) X(48) X(64) X(96) X(128) X(192) X(256) X(384) X(512)
+
+bool slab_supported(int nx, int ny, int nz) {
+  (void)nx;
+  return (nz == 64 || nz == 128 || nz == 256) && (ny == 64 || ny == 128 || ny == 256);
+}
+
+template <int NZ, int C>
+static cudaError_t launch_slab_kernel(const PencilParams &pp, float2 *S, const float2 *twz, const float *lamx,
+                                      const float *lamz, double *mean_out, cudaStream_t st) {
+  using Cfg = SlabCfg<NZ, C>;
+  {
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+      err = cudaFuncSetAttribute(k_slab<NZ, C>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)Cfg::bytes);
+    });
+    if (err != cudaSuccess) return err;
+  }
+  IBM_KTRY(launch_pdl(k_slab<NZ, C>, dim3(pp.P * C), dim3(Cfg::THREADS), Cfg::bytes, st, S, twz, lamx, lamz, pp,
+                      mean_out));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, float2 *S, float *out,
+                              const float *addend, const float2 *twx, const float2 *twz, const float *lamx,
+                              const float *lamz, double *mean_out, float scale, cudaStream_t st, int phase) {
+  const int ny = pp.ny, nz = pp.nz;
+  const int npairs = ny * nz / 2, rows = ny * nz;
+  if (phase == 0) {
+    bool done = false;
+#define X(N)                                                                                               \
+  if (nx == N) {                                                                                           \
+    IBM_KTRY(ensure_max_smem<k_rows_fwd_t<N>>());                                                          \
+    IBM_KTRY(launch_pdl(k_rows_fwd_t<N>, dim3(ceil_div(npairs, RowT<N>::RP)), dim3(kRowT), RowT<N>::smem_f, \
+                        st, in, S, twx, npairs, rows, 1.0f));                                               \
+    done = true;                                                                                           \
+  }
+    IBM_SLAB_ROWS_N(X)
+#undef X
+    return done ? cudaGetLastError() : cudaErrorInvalidValue;
+  }
+  if (phase == 1) {
+    const int C = ny / 32;
+#define S_(NZ_, C_) \
+  if (nz == NZ_ && C == C_) return launch_slab_kernel<NZ_, C_>(pp, S, twz, lamx, lamz, mean_out, st);
+    S_(64, 2) S_(64, 4) S_(64, 8) S_(128, 2) S_(128, 4) S_(128, 8) S_(256, 2) S_(256, 4) S_(256, 8)
+#undef S_
+    return cudaErrorInvalidValue;
+  }
+  bool done = false;
+#define X(N)                                                                                               \
+  if (nx == N) {                                                                                           \
+    IBM_KTRY(ensure_max_smem<k_rows_inv_t<N>>());                                                          \
+    IBM_KTRY(launch_pdl(k_rows_inv_t<N>, dim3(ceil_div(npairs, RowT<N>::RP)), dim3(kRowT), RowT<N>::smem_i, \
+                        st, S, out, addend, twx, npairs, rows, scale));                                     \
+    done = true;                                                                                           \
+  }
+  IBM_SLAB_ROWS_N(X)
+#undef X
+  return done ? cudaGetLastError() : cudaErrorInvalidValue;
+}
+
+}  // namespace ibm
