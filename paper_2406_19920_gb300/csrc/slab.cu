@@ -306,10 +306,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     zfft_rows<NZ, W, false>(slab + r0 * NZ, X, tw2);
   }
 
-  // the zero mode's right-hand side (kx = 0): Re of bin kz = 0 of every row,
-  // the plane sums, gathered in CTA 0
   const bool zm = pp.zero_mode && kx == 0;
-  if (zm && tid < R) cluster.map_shared_rank(zr, 0)[rank * R + tid] = (double)slab[tid * NZ].x;
 
   // forward elimination of my segment
   const bool top = rank < Lh;
@@ -334,7 +331,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   cf[1 * NZ + kz] = y.y;
   cf[2 * NZ + kz] = prod;
   cf[3 * NZ + kz] = qlast;
-  cluster_sync_all();  // #1: every segment's carries, row m and the zero mode's rhs are visible
+  cluster_sync_all();  // #1: every CTA has started; every segment's carries and row m are visible
 
   // carry into my segment and the last y of both halves
   auto rank_of = [](int s2) { return s2 < Lh ? s2 : C - 1 - (s2 - Lh); };
@@ -368,8 +365,15 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   else x = seg_middle<float, R, false, false, NZ>(v, len, wconst, wc, c);
   cb[kz] = x.x;
   cb[NZ + kz] = x.y;
-  // the FP64 zero mode: removed mean, pin, nullspace (one warp of CTA 0)
-  if (zm && rank == 0 && tid < 32) zero_mode_fp64(zr, zo, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);
+  // the FP64 zero mode (one warp of CTA 0 of the kx = 0 cluster): its
+  // right-hand side is Re of bin kz = 0 of every row (the plane sums), read
+  // from the peers' slabs, which the forward sweep left untouched; then the
+  // removed mean, the pin and the nullspace
+  if (zm && rank == 0 && tid < 32) {
+    for (int j = tid; j < NY; j += 32) zr[j] = (double)cluster.map_shared_rank(slab, j / R)[(j % R) * NZ].x;
+    __syncwarp();
+    zero_mode_fp64(zr, zo, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);
+  }
   cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
 
   // x after my last row (towards the meeting row), then my rows stored
