@@ -207,7 +207,8 @@ cudaError_t launch_ypencil(const PencilParams &pp, Ptr3<cplx<T> *> S3, const cpl
 // {64, 128, 256}: phase 0 the x rows forward into the kx-major spectrum
 // S[kx][y][z], phase 1 the slab kernel (z transforms and the y sweep of one
 // kx slab per cluster, the FP64 zero mode included), phase 2 the x rows
-// inverse (out = addend + scale x).  Single fields with unknowns on every
+// inverse (out = scale x, or out += scale x when addend == out; any other
+// addend is cudaErrorInvalidValue).  Single fields with unknowns on every
 // row (j0 = 0) only.
 bool slab_supported(int nx, int ny, int nz);
 cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, float2 *S, float *out,

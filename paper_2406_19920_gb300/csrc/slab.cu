@@ -37,42 +37,70 @@ namespace ibm {
 // ---------------------------------------------------------------------------
 // x rows with the kx-major spectrum.  Element (kx, row) of the spectrum is at
 // S[kx * rows + row] with row = y nz + z (rows = ny nz).  A CTA takes RP
-// consecutive row pairs (2p, 2p + 1: the same y, consecutive z).
-//   forward: step 1 with lanes along n1 (the row's consecutive x), the
-//            exchange [n1][k2][p] (pitch QF, odd), step 3 with lanes along p
-//            so that each kx writes 2 RP consecutive complex values;
-//   inverse: step 1 with lanes along p (each kx read as 2 RP consecutive
-//            values), the exchange [p][n1][k2] (pitch QI, odd), step 3 with
-//            lanes along k2 (consecutive x of one row).
+// consecutive row pairs (2p, 2p + 1: the same y, consecutive z), i.e. one
+// contiguous block of real rows and, for every kx, one contiguous run of
+// 2 RP spectrum values.  Both move by bulk copies through a staging area in
+// shared memory (padded so that the transform steps read and write it
+// without bank conflicts):
+//   forward: the row pairs in (pitch 2N + 16 floats), step 1 with lanes
+//            along n1, the exchange [n1][k2][p] (pitch QF, odd), step 3 with
+//            lanes along p writing (A_k, B_k) pairs to the staging [kx][2 RP],
+//            one bulk store per kx;
+//   inverse: one bulk load per kx into the staging [kx][2 RP], step 1 with
+//            lanes along p, the exchange [p][n1][k2] (pitch QI, odd), step 3
+//            with lanes along k2 writing the rows (pitch N + 16) to the
+//            staging, one bulk store per row, or a bulk add (FP32 reduction at
+//            the destination) when the result is added to the output in place.
 // ---------------------------------------------------------------------------
 constexpr int kRowT = 256;
 
 template <int N> struct RowT {
-  static constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
+  static constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2, P = N / 2 + 1;
   static constexpr int RP = kRowT / N1 > 1 ? kRowT / N1 : 1;  // row pairs per CTA
   static constexpr int QF = N2 * RP + 1;
   static constexpr int QI = N1 * N2 + 1;
-  static constexpr size_t smem_f = sizeof(float2) * ((size_t)N + (size_t)N1 * QF);
-  static constexpr size_t smem_i = sizeof(float2) * ((size_t)N + (size_t)RP * QI);
+  static constexpr int PIN = 2 * N + 16;  // floats per staged row pair (forward input)
+  static constexpr int POUT = N + 16;     // floats per staged row (inverse output)
+  static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
+  static constexpr size_t stage_f = mx((size_t)RP * PIN * 4, (size_t)P * 2 * RP * 8);
+  static constexpr size_t stage_i = mx((size_t)P * 2 * RP * 8, (size_t)2 * RP * POUT * 4);
+  static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8 + stage_f + 16;
+  static constexpr size_t smem_i = (size_t)N * 8 + (size_t)RP * QI * 8 + stage_i + 16;
 };
 
 template <int N>
 __global__ void __launch_bounds__(kRowT)
 k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 *__restrict__ tw, int npairs,
-             int rows, float in_scale) {
+             int rows, float in_scale, int *err) {
   using Cfg = RowT<N>;
-  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1;
+  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1, P = Cfg::P,
+                PIN = Cfg::PIN;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *X = tw2 + N;  // [N1][k2][p]
+  float2 *X = tw2 + N;                                          // [N1][k2][p]
+  float *stin = reinterpret_cast<float *>(X + N1 * QF);         // [RP][PIN] row pairs in
+  float4 *stout = reinterpret_cast<float4 *>(stin);             // [P][RP] (A, B) out (after step 1)
+  uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(stin) + Cfg::stage_f);
   load_step_twiddles<float, N>(tw2, tw);
-  pdl_wait();  // the input field is the predecessor's output
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
   const int pair0 = blockIdx.x * RP;
   const int np = min(RP, npairs - pair0);
   __syncthreads();
+  pdl_wait();  // the input field is the predecessor's output
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)np * 2 * N * 4);
+  __syncthreads();
+  if (threadIdx.x < np)
+    bulk_g2s(stin + threadIdx.x * PIN, in + (size_t)(pair0 + threadIdx.x) * 2 * N, 2 * N * 4, bar);
+  if (!__syncthreads_and(mbar_wait(bar, 0, err))) {
+    mbar_wait(bar, 0, nullptr);  // copies still in flight land before the CTA's memory is reused
+    return;
+  }
   for (int job = threadIdx.x; job < np * N1; job += kRowT) {
     const int p = job / N1, n1 = job - p * N1;
-    const float *a = in + (size_t)(pair0 + p) * 2 * N;
+    const float *a = stin + p * PIN;
     float2 v[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[N + n1 + N1 * n2] * in_scale);
@@ -88,11 +116,9 @@ k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 
   // B_k = -i (Z_k - conj Z_{N-k}) / 2 for k <= N/2
   for (int job = threadIdx.x; job < np * J3; job += kRowT) {
     const int q = job / np, p = job - q * np;
-    float2 *dA = S + 2 * (size_t)(pair0 + p);
     auto put = [&](int k, float2 zk, float2 zn) {
-      float2 *d = dA + (size_t)k * rows;
-      d[0] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
-      d[1] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
+      stout[k * RP + p] = make_float4(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y), 0.5f * (zk.y + zn.y),
+                                      -0.5f * (zk.x - zn.x));
     };
     float2 u[N1];
 #pragma unroll
@@ -116,40 +142,63 @@ k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 
       }
     }
   }
+  fence_proxy_async();
+  __syncthreads();
+  bool issued = false;
+  for (int k = threadIdx.x; k < P; k += kRowT) {
+    bulk_s2g(S + (size_t)k * rows + 2 * (size_t)pair0, stout + k * RP, (uint32_t)np * 16);
+    issued = true;
+  }
+  if (issued) {
+    bulk_commit();
+    bulk_wait_read();
+  }
 }
 
 template <int N>
 __global__ void __launch_bounds__(kRowT)
-k_rows_inv_t(const float2 *__restrict__ S, float *out, const float *add, const float2 *__restrict__ tw, int npairs,
-             int rows, float scale) {
+k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *__restrict__ tw, int npairs, int rows,
+             float scale, int *err) {
   using Cfg = RowT<N>;
-  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QI = Cfg::QI;
+  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QI = Cfg::QI, P = Cfg::P, POUT = Cfg::POUT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *X = tw2 + N;  // [p][n1][k2]
+  float2 *X = tw2 + N;                                         // [p][n1][k2]
+  float4 *stin = reinterpret_cast<float4 *>(X + RP * QI);      // [P][RP] (A, B) in
+  float *stout = reinterpret_cast<float *>(stin);              // [2 RP][POUT] rows out (after step 1)
+  uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(stin) + Cfg::stage_i);
   load_step_twiddles<float, N>(tw2, tw);
-  pdl_wait();  // the spectrum is the predecessor's output
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
   const int pair0 = blockIdx.x * RP;
   const int np = min(RP, npairs - pair0);
   __syncthreads();
+  pdl_wait();  // the spectrum is the predecessor's output
+  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)P * np * 16);
+  __syncthreads();
+  for (int k = threadIdx.x; k < P; k += kRowT)
+    bulk_g2s(stin + k * RP, S + (size_t)k * rows + 2 * (size_t)pair0, (uint32_t)np * 16, bar);
+  if (!__syncthreads_and(mbar_wait(bar, 0, err))) {
+    mbar_wait(bar, 0, nullptr);  // copies still in flight land before the CTA's memory is reused
+    return;
+  }
   // step 1: Z_n = A_n + i B_n (imaginary parts of bins 0 and N/2 dropped) and
   // its Hermitian extension for n > N/2
   for (int job = threadIdx.x; job < np * N1; job += kRowT) {
     const int n1 = job / np, p = job - n1 * np;
-    const float2 *sA = S + 2 * (size_t)(pair0 + p);
     float2 v[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) {
       const int n = n1 + N1 * n2;
       if (n <= N / 2) {
-        const float2 *s = sA + (size_t)n * rows;
-        float2 a = s[0], b = s[1];
-        if (n == 0 || n == N / 2) { a.y = 0.f; b.y = 0.f; }
-        v[n2] = make_float2(a.x - b.y, a.y + b.x);
+        float4 ab = stin[n * RP + p];
+        if (n == 0 || n == N / 2) { ab.y = 0.f; ab.w = 0.f; }
+        v[n2] = make_float2(ab.x - ab.w, ab.y + ab.z);
       } else {
-        const float2 *s = sA + (size_t)(N - n) * rows;
-        const float2 a = s[0], b = s[1];
-        v[n2] = make_float2(a.x + b.y, b.x - a.y);
+        const float4 ab = stin[(N - n) * RP + p];
+        v[n2] = make_float2(ab.x + ab.w, ab.z - ab.y);
       }
     }
     reg_dft<true, N2>(v);
@@ -161,24 +210,26 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, const float *add, const f
   __syncthreads();
   for (int job = threadIdx.x; job < np * N2; job += kRowT) {
     const int p = job / N2, k2 = job - p * N2;
-    const size_t r = 2 * (size_t)(pair0 + p);
-    float *da = out + r * N, *db = da + N;
-    const float *aa = add ? add + r * N : nullptr;
-    float a0[N1], a1[N1];
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {  // the addend's loads go out first
-      a0[k1] = aa ? aa[k2 + N2 * k1] : 0.f;
-      a1[k1] = aa ? aa[N + k2 + N2 * k1] : 0.f;
-    }
     float2 u[N1];
 #pragma unroll
     for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[p * QI + n1 * N2 + k2];
     reg_dft<true, N1>(u);
+    float *da = stout + (2 * p) * POUT, *db = da + POUT;
 #pragma unroll
     for (int k1 = 0; k1 < N1; ++k1) {
-      da[k2 + N2 * k1] = fmaf(u[k1].x, scale, a0[k1]);
-      db[k2 + N2 * k1] = fmaf(u[k1].y, scale, a1[k1]);
+      da[k2 + N2 * k1] = u[k1].x * scale;
+      db[k2 + N2 * k1] = u[k1].y * scale;
     }
+  }
+  fence_proxy_async();
+  __syncthreads();
+  if (threadIdx.x < 2 * np) {
+    const int r = threadIdx.x;
+    float *dst = out + (2 * (size_t)pair0 + r) * N;
+    if (add) bulk_s2g_add_f32(dst, stout + r * POUT, (uint32_t)N * 4);
+    else bulk_s2g(dst, stout + r * POUT, (uint32_t)N * 4);
+    bulk_commit();
+    bulk_wait_read();
   }
 }
 
@@ -204,8 +255,8 @@ template <int NZ, int C> struct SlabCfg {
   static constexpr size_t xbytes = (size_t)N1 * PN * 8 > (size_t)R * NZ * 4 ? (size_t)N1 * PN * 8 : (size_t)R * NZ * 4;
   static constexpr size_t o_tw = o_x + al(xbytes);
   static constexpr size_t o_cf = o_tw + al((size_t)NZ * 8);
-  static constexpr size_t o_cb = o_cf + al((size_t)4 * NZ * 4);
-  static constexpr size_t o_zm = o_cb + al((size_t)2 * NZ * 4);
+  static constexpr size_t o_cb = o_cf + al((size_t)2 * 4 * NZ * 4);  // two parities of [4][NZ]
+  static constexpr size_t o_zm = o_cb + al((size_t)2 * 2 * NZ * 4);  // two parities of [2][NZ]
   static constexpr size_t o_bar = o_zm + al((size_t)3 * NY * 8);
   static constexpr size_t bytes = o_bar + 128;
   static_assert(W * N1 == THREADS, "one row per N1 threads in step 1");
@@ -254,6 +305,14 @@ __device__ __forceinline__ void zfft_rows(float2 *rows, float2 *X, const float2 
   __syncthreads();
 }
 
+// Persistent: cluster q of the grid's Q clusters takes the slabs kx = q,
+// q + Q, ...  Between slabs a CTA waits until the bulk store of the previous
+// slab has read its shared memory, then loads the next one; the two CTAs an
+// SM holds belong to different clusters and drift out of phase, so one
+// computes while the other moves data.  The per-segment carries (cf, cb) are
+// kept in two parities: a peer can still read slab i's carries while this
+// CTA writes slab i + 1's (it cannot be two slabs behind: every slab has two
+// cluster barriers).
 template <int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NZ, (NZ >= 256 ? 2 : 3))
 k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx, const float *__restrict__ lamz,
@@ -262,15 +321,15 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   constexpr int R = Cfg::R, NY = Cfg::NY, W = Cfg::W, Lh = C / 2;
   cg::cluster_group cluster = cg::this_cluster();
   const int rank = (int)cluster.block_rank();
-  const int kx = blockIdx.x / C;
+  const int q = blockIdx.x / C, Q = gridDim.x / C;
   const int tid = threadIdx.x;
   extern __shared__ __align__(128) unsigned char smem[];
   float2 *slab = reinterpret_cast<float2 *>(smem + Cfg::o_slab);  // [R][NZ]
   float2 *X = reinterpret_cast<float2 *>(smem + Cfg::o_x);        // z-transform exchange
   float *ws = reinterpret_cast<float *>(smem + Cfg::o_x);         // [R][NZ] w of every row (after the transforms)
   float2 *tw2 = reinterpret_cast<float2 *>(smem + Cfg::o_tw);
-  float *cf = reinterpret_cast<float *>(smem + Cfg::o_cf);  // [4][NZ] yhat_end.x, .y, prod w, q of the last row
-  float *cb = reinterpret_cast<float *>(smem + Cfg::o_cb);  // [2][NZ] xhat at the segment's first row
+  float *cf2 = reinterpret_cast<float *>(smem + Cfg::o_cf);  // [2][4][NZ] yhat_end.x, .y, prod w, q of the last row
+  float *cb2 = reinterpret_cast<float *>(smem + Cfg::o_cb);  // [2][2][NZ] xhat at the segment's first row
   double *zr = reinterpret_cast<double *>(smem + Cfg::o_zm);  // zero mode (CTA 0 of the kx = 0 cluster): rhs,
   double *zw = zr + NY;                                       // scratch,
   double *zo = zw + NY;                                       // solution
@@ -280,7 +339,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   load_step_twiddles<float, NZ>(tw2, twz);
   const int kz = tid;
   const float a = (float)pp.a;
-  const float g = (float)pp.g_add + (float)pp.g_mul * (lamx[kx] + lamz[kz]);
+  const float lz = lamz[kz];
   if (tid == 0) {
     mbar_init(&bar[0], 1);
     mbar_init(&bar[1], 1);
@@ -288,129 +347,151 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   }
   __syncthreads();
   pdl_wait();  // the spectrum is the predecessor's output
-  float2 *gslab = S + (size_t)kx * NY * NZ + (size_t)rank * R * NZ;
-  constexpr uint32_t kHalf = (uint32_t)(R / 2) * NZ * 8;
-  if (tid == 0) {
-    mbar_arrive_expect_tx(&bar[0], kHalf);
-    bulk_g2s(slab, gslab, kHalf, &bar[0]);
-    mbar_arrive_expect_tx(&bar[1], kHalf);
-    bulk_g2s(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1]);
-  }
-  // forward z transforms.  A wait that gives up leaves ok false: the CTA
-  // still reaches every cluster barrier (its peers wait there) and stores
-  // nothing.
-  bool ok = true;
-#pragma unroll 1
-  for (int r0 = 0; r0 < R; r0 += W) {
-    if (r0 == 0 || r0 == R / 2) ok = __syncthreads_and(mbar_wait(&bar[r0 == 0 ? 0 : 1], 0, pp.err) && ok);
-    zfft_rows<NZ, W, false>(slab + r0 * NZ, X, tw2);
-  }
 
-  const bool zm = pp.zero_mode && kx == 0;
-
-  // forward elimination of my segment
+  // segment geometry (the same for every slab)
   const bool top = rank < Lh;
   const int seg = top ? rank : Lh + (C - 1 - rank);
   const int k0 = top ? rank * R : NY - (rank + 1) * R;  // distance of my first row from its wall
   const int len = rank == Lh ? R - 1 : R;
   const int lr0 = top ? 0 : R - 1, lstep = top ? 1 : -1;  // local row of sweep row u: lr0 + lstep u
-  const bool live = !(zm && kz == 0);
-  const float e0 = g + a * (float)(top ? pp.beta_s : pp.beta_e);
   const float sgn = pp.neg_rhs ? -1.f : 1.f;
-  float ep, D, z;
-  const bool cw = __all_sync(0xffffffffu, seg_pivots<float>(a, g, e0, k0, ep, D, z)) && len == R;
-  float2 v[R];
-#pragma unroll
-  for (int u = 0; u < R; ++u) v[u] = u < len ? slab[(lr0 + lstep * u) * NZ + kz] : make_float2(0.f, 0.f);
-  float *wc = ws + kz;  // w of sweep row u at wc[NZ u]
-  float2 y;
-  float prod, qlast;
-  if (cw) seg_forward<float, R, true, true, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
-  else seg_forward<float, R, false, false, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
-  cf[0 * NZ + kz] = y.x;
-  cf[1 * NZ + kz] = y.y;
-  cf[2 * NZ + kz] = prod;
-  cf[3 * NZ + kz] = qlast;
-  cluster_sync_all();  // #1: every CTA has started; every segment's carries and row m are visible
-
-  // carry into my segment and the last y of both halves
   auto rank_of = [](int s2) { return s2 < Lh ? s2 : C - 1 - (s2 - Lh); };
-  float2 c = make_float2(0.f, 0.f), yT = c, yB = c;
-#pragma unroll
-  for (int s2 = 0; s2 < C; ++s2) {
-    const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
-    if (s2 == seg) c = s2 < Lh ? yT : yB;
-    const float pw = pcf[2 * NZ + kz], ax = pcf[kz], ay = pcf[NZ + kz];
-    if (s2 < Lh) {
-      yT.x = fmaf(pw, yT.x, ax);
-      yT.y = fmaf(pw, yT.y, ay);
-    } else {
-      yB.x = fmaf(pw, yB.x, ax);
-      yB.y = fmaf(pw, yB.y, ay);
+  constexpr uint32_t kHalf = (uint32_t)(R / 2) * NZ * 8;
+
+  // A wait that gives up leaves ok false: the CTA still reaches every
+  // cluster barrier of every slab (its peers wait there), issues no further
+  // copies and stores nothing.  fail_par remembers the phase of the slab
+  // whose copies may still be in flight (fail_bar >= 0: there was one).
+  bool ok = true;
+  int fail_bar = -1;
+  uint32_t fail_par = 0;
+  for (int it = 0;; ++it) {
+    const int kx = q + it * Q;
+    if (kx >= pp.P) break;  // the same for the whole cluster
+    const uint32_t par = (uint32_t)(it & 1);
+    float *cf = cf2 + par * 4 * NZ;
+    float *cb = cb2 + par * 2 * NZ;
+    float2 *gslab = S + (size_t)kx * NY * NZ + (size_t)rank * R * NZ;
+    if (tid == 0 && ok) {
+      bulk_wait_read();  // the previous slab's store has read the buffer
+      mbar_arrive_expect_tx(&bar[0], kHalf);
+      bulk_g2s(slab, gslab, kHalf, &bar[0]);
+      mbar_arrive_expect_tx(&bar[1], kHalf);
+      bulk_g2s(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1]);
     }
-  }
-  // meeting row: (g + a q^T + a q^B) x_m = sgn f_m + a (y^T_{m-1} + y^B_{m+1})
-  const float qT = cluster.map_shared_rank(cf, Lh - 1)[3 * NZ + kz];
-  const float qB = cluster.map_shared_rank(cf, Lh)[3 * NZ + kz];
-  const float2 fm = cluster.map_shared_rank(slab, Lh)[kz];
-  float2 xm;
-  {
-    const float rm = rcp<float>(g + a * qT + a * qB);
-    xm.x = (sgn * fm.x + a * (yT.x + yB.x)) * rm;
-    xm.y = (sgn * fm.y + a * (yT.y + yB.y)) * rm;
-  }
-  const float wconst = a * rcp<float>(a + ep);
-  float2 x;
-  if (cw) x = seg_middle<float, R, true, true, NZ>(v, len, wconst, wc, c);
-  else x = seg_middle<float, R, false, false, NZ>(v, len, wconst, wc, c);
-  cb[kz] = x.x;
-  cb[NZ + kz] = x.y;
-  // the FP64 zero mode (one warp of CTA 0 of the kx = 0 cluster): its
-  // right-hand side is Re of bin kz = 0 of every row (the plane sums), read
-  // from the peers' slabs, which the forward sweep left untouched; then the
-  // removed mean, the pin and the nullspace
-  if (zm && rank == 0 && tid < 32) {
-    for (int j = tid; j < NY; j += 32) zr[j] = (double)cluster.map_shared_rank(slab, j / R)[(j % R) * NZ].x;
-    __syncwarp();
-    zero_mode_fp64(zr, zo, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);
-  }
-  cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
-
-  // x after my last row (towards the meeting row), then my rows stored
-  c = xm;
-#pragma unroll
-  for (int s2 = C - 1; s2 >= 0; --s2) {
-    if (s2 <= seg || s2 >= (top ? Lh : C)) continue;
-    const int rk = rank_of(s2);
-    const float pw = cluster.map_shared_rank(cf, rk)[2 * NZ + kz];
-    const float *pcb = cluster.map_shared_rank(cb, rk);
-    c.x = fmaf(pw, c.x, pcb[kz]);
-    c.y = fmaf(pw, c.y, pcb[NZ + kz]);
-  }
-  float2 *col = slab + lr0 * NZ + kz;
-  if (cw) seg_store<float, R, true, true, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
-  else seg_store<float, R, false, false, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
-  if (rank == Lh && live) slab[kz] = xm;
-  if (zm && tid < R) slab[tid * NZ] = make_float2((float)cluster.map_shared_rank(zo, 0)[rank * R + tid], 0.f);
-  cluster_arrive();  // #3 (arrival): this CTA reads no peer memory any more
-  __syncthreads();
-
-  // inverse z transforms and the store
+    const float g = (float)pp.g_add + (float)pp.g_mul * (lamx[kx] + lz);
+    // forward z transforms
 #pragma unroll 1
-  for (int r0 = 0; r0 < R; r0 += W) zfft_rows<NZ, W, true>(slab + r0 * NZ, X, tw2);
-  fence_proxy_async();
-  __syncthreads();
-  if (tid == 0) {
-    if (ok) {
+    for (int r0 = 0; r0 < R; r0 += W) {
+      if (r0 == 0 || r0 == R / 2) {
+        const int b = r0 == 0 ? 0 : 1;
+        const bool got = ok ? __syncthreads_and(mbar_wait(&bar[b], par, pp.err)) : false;
+        if (ok && !got) { fail_bar = b; fail_par = par; }
+        ok = ok && got;
+      }
+      zfft_rows<NZ, W, false>(slab + r0 * NZ, X, tw2);
+    }
+    const bool zm = pp.zero_mode && kx == 0;
+
+    // forward elimination of my segment
+    const bool live = !(zm && kz == 0);
+    const float e0 = g + a * (float)(top ? pp.beta_s : pp.beta_e);
+    float ep, D, z;
+    const bool cw = __all_sync(0xffffffffu, seg_pivots<float>(a, g, e0, k0, ep, D, z)) && len == R;
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) v[u] = u < len ? slab[(lr0 + lstep * u) * NZ + kz] : make_float2(0.f, 0.f);
+    float *wc = ws + kz;  // w of sweep row u at wc[NZ u]
+    float2 y;
+    float prod, qlast;
+    if (cw) seg_forward<float, R, true, true, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
+    else seg_forward<float, R, false, false, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
+    cf[0 * NZ + kz] = y.x;
+    cf[1 * NZ + kz] = y.y;
+    cf[2 * NZ + kz] = prod;
+    cf[3 * NZ + kz] = qlast;
+    cluster_sync_all();  // #1: every CTA has started; every segment's carries and row m are visible
+
+    // carry into my segment and the last y of both halves
+    float2 c = make_float2(0.f, 0.f), yT = c, yB = c;
+#pragma unroll
+    for (int s2 = 0; s2 < C; ++s2) {
+      const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
+      if (s2 == seg) c = s2 < Lh ? yT : yB;
+      const float pw = pcf[2 * NZ + kz], ax = pcf[kz], ay = pcf[NZ + kz];
+      if (s2 < Lh) {
+        yT.x = fmaf(pw, yT.x, ax);
+        yT.y = fmaf(pw, yT.y, ay);
+      } else {
+        yB.x = fmaf(pw, yB.x, ax);
+        yB.y = fmaf(pw, yB.y, ay);
+      }
+    }
+    // meeting row: (g + a q^T + a q^B) x_m = sgn f_m + a (y^T_{m-1} + y^B_{m+1})
+    const float qT = cluster.map_shared_rank(cf, Lh - 1)[3 * NZ + kz];
+    const float qB = cluster.map_shared_rank(cf, Lh)[3 * NZ + kz];
+    const float2 fm = cluster.map_shared_rank(slab, Lh)[kz];
+    float2 xm;
+    {
+      const float rm = rcp<float>(g + a * qT + a * qB);
+      xm.x = (sgn * fm.x + a * (yT.x + yB.x)) * rm;
+      xm.y = (sgn * fm.y + a * (yT.y + yB.y)) * rm;
+    }
+    const float wconst = a * rcp<float>(a + ep);
+    float2 x;
+    if (cw) x = seg_middle<float, R, true, true, NZ>(v, len, wconst, wc, c);
+    else x = seg_middle<float, R, false, false, NZ>(v, len, wconst, wc, c);
+    cb[kz] = x.x;
+    cb[NZ + kz] = x.y;
+    // the FP64 zero mode (one warp of CTA 0 of the kx = 0 cluster): its
+    // right-hand side is Re of bin kz = 0 of every row (the plane sums), read
+    // from the peers' slabs, which the forward sweep left untouched; then the
+    // removed mean, the pin and the nullspace
+    if (zm && rank == 0 && tid < 32) {
+      for (int j = tid; j < NY; j += 32) zr[j] = (double)cluster.map_shared_rank(slab, j / R)[(j % R) * NZ].x;
+      __syncwarp();
+      zero_mode_fp64(zr, zo, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);
+    }
+    cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
+
+    // x after my last row (towards the meeting row), then my rows stored
+    c = xm;
+#pragma unroll
+    for (int s2 = C - 1; s2 >= 0; --s2) {
+      if (s2 <= seg || s2 >= (top ? Lh : C)) continue;
+      const int rk = rank_of(s2);
+      const float pw = cluster.map_shared_rank(cf, rk)[2 * NZ + kz];
+      const float *pcb = cluster.map_shared_rank(cb, rk);
+      c.x = fmaf(pw, c.x, pcb[kz]);
+      c.y = fmaf(pw, c.y, pcb[NZ + kz]);
+    }
+    float2 *col = slab + lr0 * NZ + kz;
+    if (cw) seg_store<float, R, true, true, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
+    else seg_store<float, R, false, false, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
+    if (rank == Lh && live) slab[kz] = xm;
+    if (zm && tid < R) slab[tid * NZ] = make_float2((float)cluster.map_shared_rank(zo, 0)[rank * R + tid], 0.f);
+    __syncthreads();
+
+    // inverse z transforms and the store (completed before the buffer is reloaded)
+#pragma unroll 1
+    for (int r0 = 0; r0 < R; r0 += W) zfft_rows<NZ, W, true>(slab + r0 * NZ, X, tw2);
+    fence_proxy_async();
+    __syncthreads();
+    if (tid == 0 && ok) {
       bulk_s2g(gslab, slab, (uint32_t)R * NZ * 8);
       bulk_commit();
-      bulk_wait_read();
-    } else {  // copies that may still be in flight land before the memory is released
-      mbar_wait(&bar[0], 0, nullptr);
-      mbar_wait(&bar[1], 0, nullptr);
     }
   }
-  cluster_wait();  // #3: the peers have finished reading this CTA's memory
+  if (tid == 0) {
+    if (ok) {
+      bulk_wait_all();  // the last slab's store is complete
+    } else if (fail_bar >= 0) {  // both halves of the failed slab's copies may still be in flight
+      mbar_wait(&bar[0], fail_par, nullptr);
+      mbar_wait(&bar[1], fail_par, nullptr);
+    }
+  }
+  __syncthreads();
+  cluster_sync_all();  // the peers have finished reading this CTA's memory
 }
 
 // ---------------------------------------------------------------------------
@@ -435,7 +516,21 @@ static cudaError_t launch_slab_kernel(const PencilParams &pp, float2 *S, const f
     });
     if (err != cudaSuccess) return err;
   }
-  IBM_KTRY(launch_pdl(k_slab<NZ, C>, dim3(pp.P * C), dim3(Cfg::THREADS), Cfg::bytes, st, S, twz, lamx, lamz, pp,
+  // as many clusters as can be resident at once (every one loops over its
+  // share of the P slabs), and never more clusters than slabs
+  static std::once_flag once_q;
+  static int resident = 0;
+  std::call_once(once_q, [] {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(C * 1024);
+    cfg.blockDim = dim3(Cfg::THREADS);
+    cfg.dynamicSmemBytes = Cfg::bytes;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, k_slab<NZ, C>, &cfg) == cudaSuccess) resident = n;
+    cudaGetLastError();
+  });
+  const int Q = resident > 0 ? std::min(resident, pp.P) : pp.P;
+  IBM_KTRY(launch_pdl(k_slab<NZ, C>, dim3(Q * C), dim3(Cfg::THREADS), Cfg::bytes, st, S, twz, lamx, lamz, pp,
                       mean_out));
   return cudaGetLastError();
 }
@@ -451,7 +546,7 @@ cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, f
   if (nx == N) {                                                                                           \
     IBM_KTRY(ensure_max_smem<k_rows_fwd_t<N>>());                                                          \
     IBM_KTRY(launch_pdl(k_rows_fwd_t<N>, dim3(ceil_div(npairs, RowT<N>::RP)), dim3(kRowT), RowT<N>::smem_f, \
-                        st, in, S, twx, npairs, rows, 1.0f));                                               \
+                        st, in, S, twx, npairs, rows, 1.0f, pp.err));                                       \
     done = true;                                                                                           \
   }
     IBM_SLAB_ROWS_N(X)
@@ -466,12 +561,13 @@ cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, f
 #undef S_
     return cudaErrorInvalidValue;
   }
+  if (addend && addend != out) return cudaErrorInvalidValue;  // the inverse adds in place only
   bool done = false;
 #define X(N)                                                                                               \
   if (nx == N) {                                                                                           \
     IBM_KTRY(ensure_max_smem<k_rows_inv_t<N>>());                                                          \
     IBM_KTRY(launch_pdl(k_rows_inv_t<N>, dim3(ceil_div(npairs, RowT<N>::RP)), dim3(kRowT), RowT<N>::smem_i, \
-                        st, S, out, addend, twx, npairs, rows, scale));                                     \
+                        st, S, out, addend != nullptr, twx, npairs, rows, scale, pp.err));                  \
     done = true;                                                                                           \
   }
   IBM_SLAB_ROWS_N(X)

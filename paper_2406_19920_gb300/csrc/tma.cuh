@@ -94,6 +94,13 @@ __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t by
                "r"(bytes)
                : "memory");
 }
+// shared -> global with FP32 addition at the destination (bulk group):
+// dst[i] += src[i] for bytes / 4 floats.
+__device__ __forceinline__ void bulk_s2g_add_f32(float *dst, const float *src, uint32_t bytes) {
+  asm volatile("cp.reduce.async.bulk.global.shared::cta.bulk_group.add.f32 [%0], [%1], %2;" ::"l"(dst),
+               "r"(smem_u32(src)), "r"(bytes)
+               : "memory");
+}
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 // Wait until every committed bulk store has finished reading shared memory.
 __device__ __forceinline__ void bulk_wait_read() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
