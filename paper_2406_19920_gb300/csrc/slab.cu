@@ -255,9 +255,9 @@ template <int NZ, int C> struct SlabCfg {
   static constexpr size_t xbytes = (size_t)N1 * PN * 8 > (size_t)R * NZ * 4 ? (size_t)N1 * PN * 8 : (size_t)R * NZ * 4;
   static constexpr size_t o_tw = o_x + al(xbytes);
   static constexpr size_t o_cf = o_tw + al((size_t)NZ * 8);
-  static constexpr size_t o_cb = o_cf + al((size_t)2 * 4 * NZ * 4);  // two parities of [4][NZ]
-  static constexpr size_t o_zm = o_cb + al((size_t)2 * 2 * NZ * 4);  // two parities of [2][NZ]
-  static constexpr size_t o_bar = o_zm + al((size_t)3 * NY * 8);
+  static constexpr size_t o_cb = o_cf + al((size_t)4 * NZ * 4);
+  static constexpr size_t o_zm = o_cb + al((size_t)3 * NZ * 4);
+  static constexpr size_t o_bar = o_zm + al((size_t)2 * NY * 8);
   static constexpr size_t bytes = o_bar + 128;
   static_assert(W * N1 == THREADS, "one row per N1 threads in step 1");
   static_assert((R / 2) % W == 0, "each half of the rows is whole transform rounds");
@@ -309,10 +309,12 @@ __device__ __forceinline__ void zfft_rows(float2 *rows, float2 *X, const float2 
 // q + Q, ...  Between slabs a CTA waits until the bulk store of the previous
 // slab has read its shared memory, then loads the next one; the two CTAs an
 // SM holds belong to different clusters and drift out of phase, so one
-// computes while the other moves data.  The per-segment carries (cf, cb) are
-// kept in two parities: a peer can still read slab i's carries while this
-// CTA writes slab i + 1's (it cannot be two slabs behind: every slab has two
-// cluster barriers).
+// computes while the other moves data.  Every peer reads this CTA's forward
+// carries (cf), its meeting row and its zero-mode rows only between the
+// slab's two cluster barriers, and its back-substitution carries (cb, with
+// the segment's product of w) only between the second barrier and the next
+// slab's first, before which this CTA rewrites neither: one copy of each
+// suffices.
 template <int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NZ, (NZ >= 256 ? 2 : 3))
 k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx, const float *__restrict__ lamz,
@@ -328,11 +330,10 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   float2 *X = reinterpret_cast<float2 *>(smem + Cfg::o_x);        // z-transform exchange
   float *ws = reinterpret_cast<float *>(smem + Cfg::o_x);         // [R][NZ] w of every row (after the transforms)
   float2 *tw2 = reinterpret_cast<float2 *>(smem + Cfg::o_tw);
-  float *cf2 = reinterpret_cast<float *>(smem + Cfg::o_cf);  // [2][4][NZ] yhat_end.x, .y, prod w, q of the last row
-  float *cb2 = reinterpret_cast<float *>(smem + Cfg::o_cb);  // [2][2][NZ] xhat at the segment's first row
-  double *zr = reinterpret_cast<double *>(smem + Cfg::o_zm);  // zero mode (CTA 0 of the kx = 0 cluster): rhs,
-  double *zw = zr + NY;                                       // scratch,
-  double *zo = zw + NY;                                       // solution
+  float *cf = reinterpret_cast<float *>(smem + Cfg::o_cf);  // [4][NZ] yhat_end.x, .y, prod w, q of the last row
+  float *cb = reinterpret_cast<float *>(smem + Cfg::o_cb);  // [3][NZ] xhat at the segment's first row, prod w
+  double *zr = reinterpret_cast<double *>(smem + Cfg::o_zm);  // zero mode (CTA 0 of the kx = 0 cluster): rhs and
+  double *zw = zr + NY;                                       // then solution; scratch
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Cfg::o_bar);
 
   // plan constants before the grid-dependency wait
@@ -369,8 +370,6 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     const int kx = q + it * Q;
     if (kx >= pp.P) break;  // the same for the whole cluster
     const uint32_t par = (uint32_t)(it & 1);
-    float *cf = cf2 + par * 4 * NZ;
-    float *cb = cb2 + par * 2 * NZ;
     float2 *gslab = S + (size_t)kx * NY * NZ + (size_t)rank * R * NZ;
     if (tid == 0 && ok) {
       bulk_wait_read();  // the previous slab's store has read the buffer
@@ -443,6 +442,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     else x = seg_middle<float, R, false, false, NZ>(v, len, wconst, wc, c);
     cb[kz] = x.x;
     cb[NZ + kz] = x.y;
+    cb[2 * NZ + kz] = prod;
     // the FP64 zero mode (one warp of CTA 0 of the kx = 0 cluster): its
     // right-hand side is Re of bin kz = 0 of every row (the plane sums), read
     // from the peers' slabs, which the forward sweep left untouched; then the
@@ -450,7 +450,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     if (zm && rank == 0 && tid < 32) {
       for (int j = tid; j < NY; j += 32) zr[j] = (double)cluster.map_shared_rank(slab, j / R)[(j % R) * NZ].x;
       __syncwarp();
-      zero_mode_fp64(zr, zo, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);
+      zero_mode_fp64(zr, zr, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);  // solution over the rhs
     }
     cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
 
@@ -459,9 +459,8 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
 #pragma unroll
     for (int s2 = C - 1; s2 >= 0; --s2) {
       if (s2 <= seg || s2 >= (top ? Lh : C)) continue;
-      const int rk = rank_of(s2);
-      const float pw = cluster.map_shared_rank(cf, rk)[2 * NZ + kz];
-      const float *pcb = cluster.map_shared_rank(cb, rk);
+      const float *pcb = cluster.map_shared_rank(cb, rank_of(s2));
+      const float pw = pcb[2 * NZ + kz];
       c.x = fmaf(pw, c.x, pcb[kz]);
       c.y = fmaf(pw, c.y, pcb[NZ + kz]);
     }
@@ -469,7 +468,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     if (cw) seg_store<float, R, true, true, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
     else seg_store<float, R, false, false, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
     if (rank == Lh && live) slab[kz] = xm;
-    if (zm && tid < R) slab[tid * NZ] = make_float2((float)cluster.map_shared_rank(zo, 0)[rank * R + tid], 0.f);
+    if (zm && tid < R) slab[tid * NZ] = make_float2((float)cluster.map_shared_rank(zr, 0)[rank * R + tid], 0.f);
     __syncthreads();
 
     // inverse z transforms and the store (completed before the buffer is reloaded)
