@@ -533,8 +533,13 @@ def run_gpu(args):
 
     # ---- extras (outside the timed region) ----
     if not args.no_extras:
+        # the split x / z passes (IBM_SLAB=0) beside the fused slab path, same solves
         out["poisson_256"] = poisson_compare(ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0),
                                                                ("fp32_refined", ibm.IBM_FP32_REFINED, 1),
+                                                               ("fp32_split", ibm.IBM_FP32_REFINED, 0,
+                                                                {"IBM_SLAB": "0"}),
+                                                               ("fp32_refined_split", ibm.IBM_FP32_REFINED, 1,
+                                                                {"IBM_SLAB": "0"}),
                                                                ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
                                              oracle=rank == 0 and not args.no_oracle)
         # triply periodic branch (y-FFT pencil step instead of the Thomas sweep)
@@ -542,6 +547,8 @@ def run_gpu(args):
             ibm, torch, 256, (("fp32", ibm.IBM_FP32_REFINED, 0), ("fp64", ibm.IBM_FP64, 0)), nb=4, K=20,
             bc=ibm.IBM_BC_TRIPLY_PERIODIC)
         out["poisson_128"] = poisson_compare(ibm, torch, NX, (("fp32_refined", ibm.IBM_FP32_REFINED, 1),
+                                                              ("fp32_refined_split", ibm.IBM_FP32_REFINED, 1,
+                                                               {"IBM_SLAB": "0"}),
                                                               ("fp64", ibm.IBM_FP64, 0)))
         out["stage_128"] = stage_128(ibm, torch, args, oracle=rank == 0 and not args.no_oracle)
         out["spreading"] = spread_compare(ibm, torch)
@@ -676,9 +683,20 @@ def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None, oracle=False)
     b = synth.rhs_lowpass_noise(n, n, n, kmax=min(32.0, n / 4), workload=1).astype(np.float32).astype(np.float64)
     res = {}
     outs = {}
-    for name, prec, ref in variants:
+    for variant in variants:
+        name, prec, ref = variant[:3]
+        env = variant[3] if len(variant) > 3 else {}
         dt = torch.float32 if prec == ibm.IBM_FP32_REFINED else torch.float64
-        plan = ibm.ibm_plan_create(n, n, n, g[3:], prec, ref, bc=bc if bc is not None else ibm.IBM_BC_PXZ_WALL_Y)
+        old = {k: os.environ.get(k) for k in env}
+        os.environ.update(env)
+        try:
+            plan = ibm.ibm_plan_create(n, n, n, g[3:], prec, ref, bc=bc if bc is not None else ibm.IBM_BC_PXZ_WALL_Y)
+        finally:
+            for k, v in old.items():
+                if v is None:
+                    os.environ.pop(k, None)
+                else:
+                    os.environ[k] = v
         rhs = [torch.from_numpy(b).to("cuda", dt) for _ in range(nb)]  # nb rhs + nb solutions > L2
         phi = [torch.empty_like(r) for r in rhs]
         for i in range(3):

@@ -39,18 +39,19 @@ namespace ibm {
 // S[kx * rows + row] with row = y nz + z (rows = ny nz).  A CTA takes RP
 // consecutive row pairs (2p, 2p + 1: the same y, consecutive z), i.e. one
 // contiguous block of real rows and, for every kx, one contiguous run of
-// 2 RP spectrum values.  Both move by bulk copies through a staging area in
-// shared memory (padded so that the transform steps read and write it
-// without bank conflicts):
-//   forward: the row pairs in (pitch 2N + 16 floats), step 1 with lanes
-//            along n1, the exchange [n1][k2][p] (pitch QF, odd), step 3 with
-//            lanes along p writing (A_k, B_k) pairs to the staging [kx][2 RP],
-//            one bulk store per kx;
-//   inverse: one bulk load per kx into the staging [kx][2 RP], step 1 with
-//            lanes along p, the exchange [p][n1][k2] (pitch QI, odd), step 3
-//            with lanes along k2 writing the rows (pitch N + 16) to the
-//            staging, one bulk store per row, or a bulk add (FP32 reduction at
-//            the destination) when the result is added to the output in place.
+// 2 RP spectrum values.
+//   forward: step 1 with lanes along n1 (the row's consecutive x, read
+//            straight from global memory), the exchange [n1][k2][p] (pitch
+//            QF, odd), step 3 with lanes along p so that each kx is written
+//            as 2 RP consecutive values (A_k, B_k of the pair);
+//   inverse: one bulk load per kx into a staging area [kx][2 RP] in shared
+//            memory, step 1 with lanes along p, the exchange [p][n1][k2]
+//            (pitch QI, odd), step 3 with lanes along k2 writing the rows
+//            (pitch N + 16 floats: no bank conflicts) to the staging, one bulk
+//            store per row, or a bulk add (FP32 reduction at the destination)
+//            when the result is added to the output in place.  Read straight
+//            from global memory, the 2 RP-value runs of all kx of a CTA came
+//            in 20 % slower.
 // ---------------------------------------------------------------------------
 constexpr int kRowT = 256;
 
@@ -59,12 +60,10 @@ template <int N> struct RowT {
   static constexpr int RP = kRowT / N1 > 1 ? kRowT / N1 : 1;  // row pairs per CTA
   static constexpr int QF = N2 * RP + 1;
   static constexpr int QI = N1 * N2 + 1;
-  static constexpr int PIN = 2 * N + 16;  // floats per staged row pair (forward input)
   static constexpr int POUT = N + 16;     // floats per staged row (inverse output)
   static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
-  static constexpr size_t stage_f = mx((size_t)RP * PIN * 4, (size_t)P * 2 * RP * 8);
   static constexpr size_t stage_i = mx((size_t)P * 2 * RP * 8, (size_t)2 * RP * POUT * 4);
-  static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8 + stage_f + 16;
+  static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8;
   static constexpr size_t smem_i = (size_t)N * 8 + (size_t)RP * QI * 8 + stage_i + 16;
 };
 
@@ -73,34 +72,19 @@ __global__ void __launch_bounds__(kRowT)
 k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 *__restrict__ tw, int npairs,
              int rows, float in_scale, int *err) {
   using Cfg = RowT<N>;
-  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1, P = Cfg::P,
-                PIN = Cfg::PIN;
+  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1;
+  (void)err;  // no waits: every access is a plain coalesced load or store
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *X = tw2 + N;                                          // [N1][k2][p]
-  float *stin = reinterpret_cast<float *>(X + N1 * QF);         // [RP][PIN] row pairs in
-  float4 *stout = reinterpret_cast<float4 *>(stin);             // [P][RP] (A, B) out (after step 1)
-  uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(stin) + Cfg::stage_f);
+  float2 *X = tw2 + N;  // [N1][k2][p]
   load_step_twiddles<float, N>(tw2, tw);
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
+  pdl_wait();  // the input field is the predecessor's output
   const int pair0 = blockIdx.x * RP;
   const int np = min(RP, npairs - pair0);
   __syncthreads();
-  pdl_wait();  // the input field is the predecessor's output
-  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)np * 2 * N * 4);
-  __syncthreads();
-  if (threadIdx.x < np)
-    bulk_g2s(stin + threadIdx.x * PIN, in + (size_t)(pair0 + threadIdx.x) * 2 * N, 2 * N * 4, bar);
-  if (!__syncthreads_and(mbar_wait(bar, 0, err))) {
-    mbar_wait(bar, 0, nullptr);  // copies still in flight land before the CTA's memory is reused
-    return;
-  }
   for (int job = threadIdx.x; job < np * N1; job += kRowT) {
     const int p = job / N1, n1 = job - p * N1;
-    const float *a = stin + p * PIN;
+    const float *a = in + (size_t)(pair0 + p) * 2 * N;
     float2 v[N2];
 #pragma unroll
     for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[N + n1 + N1 * n2] * in_scale);
@@ -116,9 +100,11 @@ k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 
   // B_k = -i (Z_k - conj Z_{N-k}) / 2 for k <= N/2
   for (int job = threadIdx.x; job < np * J3; job += kRowT) {
     const int q = job / np, p = job - q * np;
+    float2 *dA = S + 2 * (size_t)(pair0 + p);
     auto put = [&](int k, float2 zk, float2 zn) {
-      stout[k * RP + p] = make_float4(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y), 0.5f * (zk.y + zn.y),
-                                      -0.5f * (zk.x - zn.x));
+      float2 *d = dA + (size_t)k * rows;
+      d[0] = make_float2(0.5f * (zk.x + zn.x), 0.5f * (zk.y - zn.y));
+      d[1] = make_float2(0.5f * (zk.y + zn.y), -0.5f * (zk.x - zn.x));
     };
     float2 u[N1];
 #pragma unroll
@@ -141,17 +127,6 @@ k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 
         put(N2 - q + N2 * k1, w[k1], u[N1 - 1 - k1]);
       }
     }
-  }
-  fence_proxy_async();
-  __syncthreads();
-  bool issued = false;
-  for (int k = threadIdx.x; k < P; k += kRowT) {
-    bulk_s2g(S + (size_t)k * rows + 2 * (size_t)pair0, stout + k * RP, (uint32_t)np * 16);
-    issued = true;
-  }
-  if (issued) {
-    bulk_commit();
-    bulk_wait_read();
   }
 }
 
