@@ -554,7 +554,7 @@ def run_gpu(args):
         out["spreading"] = spread_compare(ibm, torch)
         out["batched"] = batched_compare(ibm, torch)
         out["dft_tensor_core"] = dft_compare(ibm, torch)
-        out["serving"] = serve_sample(ibm)
+        out["serving"] = serve_sample(ibm, torch, duration_s=args.serve_seconds, oracle=rank == 0 and not args.no_oracle)
         out["large_plate"] = large_plate(ibm, torch, oracle=rank == 0 and not args.no_oracle)
         out["large_plate_inflow"] = large_plate(ibm, torch, v_in=1.0)
     if rank == 0 and not args.no_cpu_baseline:
@@ -1024,86 +1024,215 @@ def large_plate(ibm, torch, stages=48, v_in=None, oracle=False):
             "poisson_rel_residual_refined": pinfo["rel_residual"], "sim_time": st.t, "oracle_error": err}
 
 
-def serve_sample(ibm, duration_s=2.0, rate=2000.0):
-    """Open-loop Poisson arrivals at `rate` req/s for `duration_s` into one
-    server per precision.  Kinds: 60 % Poisson, 25 % Helmholtz, 15 % RK stage;
-    grids log-uniform in points between 32^3 and 128^3, snapped to supported
-    shapes with nx >= ny = nz; markers log-uniform in [1k, 20k].  The same
-    arrival trace runs twice on one server: cold (every plan and staging
-    buffer made on first use) and warm (plans and buffers resident)."""
-    from paper_2406_19920_gb300 import synth
-    rng = np.random.default_rng(4004)
-    sizes = [16, 24, 32, 48, 64, 96, 128]
-    shapes = sorted({(nx, ny, ny) for nx in sizes for ny in sizes if nx >= ny and 32 ** 3 <= nx * ny * ny <= 128 ** 3})
+SERVE_SIZES = (32, 48, 64, 96, 128, 192, 256, 384)
+SERVE_MARKERS = (1000, 2000, 5000, 10000, 20000, 50000, 100000)
+
+
+def serve_trace(seed, duration_s, rate):
+    """The request trace of the serving workload: Poisson arrivals at `rate`
+    per second for `duration_s`; kinds 60 % Poisson, 25 % Helmholtz, 15 % RK
+    stage; grid points log-uniform between 32^3 and 384 x 256 x 256, snapped
+    to the nearest supported shape (nx >= ny = nz, lengths 2^a 3^b); marker
+    counts log-uniform in [1k, 100k], snapped to a precomputed sphere size.
+    Returns [(arrival offset s, kind, shape, markers)]."""
+    rng = np.random.default_rng(seed)
+    lo, hi = 32 ** 3, 384 * 256 * 256
+    shapes = sorted({(nx, ny, ny) for nx in SERVE_SIZES for ny in SERVE_SIZES if nx >= ny and lo <= nx * ny * ny <= hi})
     logs = np.log([a * b * c for a, b, c in shapes])
+    mlog = np.log(SERVE_MARKERS)
+    n = int(rng.poisson(rate * duration_s))
+    t = np.cumsum(rng.exponential(1.0 / rate, n))
+    kinds = rng.choice([0, 1, 2], n, p=[0.6, 0.25, 0.15])
+    pts = np.exp(rng.uniform(np.log(lo), np.log(hi), n))
+    mk = np.exp(rng.uniform(np.log(1000), np.log(100000), n))
+    out = []
+    for k in range(n):
+        sh = shapes[int(np.argmin(np.abs(logs - np.log(pts[k]))))]
+        m = SERVE_MARKERS[int(np.argmin(np.abs(mlog - np.log(mk[k]))))] if kinds[k] == 2 else 0
+        out.append((float(t[k]), int(kinds[k]), sh, m))
+    return out
 
-    def draw_shape():
-        t = rng.uniform(np.log(32 ** 3), np.log(128 ** 3))
-        return shapes[int(np.argmin(np.abs(logs - t)))]
 
-    n_req = int(rate * duration_s)
-    gaps = rng.exponential(1.0 / rate, n_req)
-    kinds = rng.choice([0, 1, 2], n_req, p=[0.6, 0.25, 0.15])
-    plan = [(k, draw_shape(), int(np.exp(rng.uniform(np.log(1000), np.log(20000))))) for k in kinds]
-    inputs = {}
-    for k, sh, m in plan:
-        key = (k, sh)
-        if key not in inputs:
+class ServeInputs:
+    """Device-resident inputs of the serving workload in one precision: per
+    (kind, shape) one input and a ring of outputs (requests of one shape
+    cycle through the ring), and Fibonacci spheres of every marker count
+    (radius 0.25, centre (pi, 1, pi))."""
+
+    RING = 4
+
+    @staticmethod
+    def host_data(keys):
+        """Seeded host inputs (FP64) per (kind, shape) and the spheres."""
+        from paper_2406_19920_gb300 import synth
+        data = {}
+        for kind, sh in sorted(keys):
             nx, ny, nz = sh
             g = synth.grid(nx, ny, nz)
-            if k == 2:
+            if kind == 2:
                 u, v, w = synth.div_free_velocity(g, workload=4, kmax=4)
-                data = np.ascontiguousarray(np.stack([u, v, w, np.zeros_like(u)]))
+                x = np.stack([u, v, w, np.zeros_like(u)])
             else:
-                data = synth.white_noise(nx, ny, nz, workload=4, stream=len(inputs))
-            inputs[key] = (g, data, np.zeros_like(data))
-    X0, dV = synth.fibonacci_sphere(20000, 0.25, (math.pi, 1.0, math.pi), 2 * math.pi / 32)
-    X0, dV = np.ascontiguousarray(X0), np.ascontiguousarray(dV)
-    out = {}
-    for name, prec in (("fp32_refined", ibm.IBM_FP32_REFINED), ("fp64", ibm.IBM_FP64)):
-        srv = ibm.ibm_server_create(64 << 30, 8, 1 << 16)
-        reqs = []
-        for k, sh, m in plan:
-            g, data, dst = inputs[(k, sh)]
-            r = ibm.ibm_request()
-            r.kind, (r.nx, r.ny, r.nz) = k, sh
-            r.h = (ctypes.c_double * 3)(*g[3:])
-            r.precision, r.refine_iters = prec, 1
-            r.c, r.field_bc = 0.5 * DT * NU, ibm.IBM_FIELD_CELL_DIRICHLET
-            r.in_, r.out = data.ctypes.data, dst.ctypes.data
-            r.n_markers = m if k == 2 else 0
-            r.X0, r.dV = X0.ctypes.data, dV.ctypes.data
-            r.motion, r.params = ibm.IBM_MOTION_TRANSLATE, (ctypes.c_double * 4)(0.1, 0, 0, 0)
-            r.dt, r.nu, r.rk_stage = DT, NU, 1
-            reqs.append(r)
-        passes = {}
-        for phase in ("cold", "warm"):
-            tickets = []
-            t0 = time.perf_counter()
-            t_next = t0
-            for r, gap in zip(reqs, gaps):
-                t_next += gap
-                while time.perf_counter() < t_next:
-                    pass
-                tickets.append(ibm.ibm_submit(srv, r))
-            lat, dev_ms, ok = [], [], 0
-            for t in tickets:
-                if t is None:
-                    continue
-                rc, res = ibm.ibm_wait(srv, t, 300.0)
-                if rc == ibm.IBM_OK:
-                    ok += 1
-                    lat.append(res.total_ms)
-                    dev_ms.append(res.device_ms)
-            wall = time.perf_counter() - t0
-            passes[phase] = {"requests": n_req, "completed": ok, "throughput_req_per_s": ok / wall,
-                             "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
-                             "device_ms_mean": float(np.mean(dev_ms))}
-        ibm.ibm_server_destroy(srv)
-        out[name] = dict(passes["warm"], cold=passes["cold"])
-    out["workload"] = ("Poisson arrivals %.0f req/s for %.1f s; 60/25/15 %% Poisson/Helmholtz/RK stage; grids "
-                       "log-uniform 32^3..128^3; 8 streams; top-level figures: the warm pass (the same trace "
-                       "again on the same server), 'cold': the first pass" % (rate, duration_s))
+                x = synth.white_noise(nx, ny, nz, workload=4, stream=kind)
+            data[(kind, sh)] = (g, np.ascontiguousarray(x))
+        spheres = {m: synth.fibonacci_sphere(m, 0.25, (math.pi, 1.0, math.pi), 2 * math.pi / 32)
+                   for m in SERVE_MARKERS}
+        return data, spheres
+
+    def __init__(self, ibm, torch, prec, host):
+        self.ibm, self.torch, self.prec = ibm, torch, prec
+        self.dt = torch.float32 if prec == ibm.IBM_FP32_REFINED else torch.float64
+        self.fields, self.next = {}, {}
+        data, spheres = host
+        for key, (g, x) in data.items():
+            din = torch.from_numpy(x).to("cuda", self.dt)
+            self.fields[key] = (g, din, [torch.empty_like(din) for _ in range(self.RING)])
+            self.next[key] = 0
+        self.spheres = {m: (torch.from_numpy(np.ascontiguousarray(X0)).to("cuda", self.dt),
+                            torch.from_numpy(np.ascontiguousarray(dV)).to("cuda", self.dt))
+                        for m, (X0, dV) in spheres.items()}
+
+    def request(self, kind, sh, m, out=None):
+        ibm = self.ibm
+        g, din, ring = self.fields[(kind, sh)]
+        if out is None:
+            out = ring[self.next[(kind, sh)] % self.RING]
+            self.next[(kind, sh)] += 1
+        r = ibm.ibm_request()
+        r.kind, (r.nx, r.ny, r.nz) = kind, sh
+        r.h = (ctypes.c_double * 3)(*g[3:])
+        r.precision, r.refine_iters = self.prec, 1
+        r.c, r.field_bc = 0.5 * DT * NU, ibm.IBM_FIELD_CELL_DIRICHLET
+        r.in_, r.out, r.data = din.data_ptr(), out.data_ptr(), ibm.IBM_DATA_DEVICE
+        r.n_markers = m
+        if m:
+            X0, dV = self.spheres[m]
+            r.X0, r.dV = X0.data_ptr(), dV.data_ptr()
+        r.motion, r.params = ibm.IBM_MOTION_TRANSLATE, (ctypes.c_double * 4)(0.1, 0, 0, 0)
+        r.dt, r.nu, r.rk_stage = DT, NU, 1
+        return r
+
+
+def serve_run(ibm, srv, inputs, trace, checks=()):
+    """Submits `trace` open loop (busy-waiting for each arrival time) and
+    waits for every request; `checks` = [(index, out tensor)] gives some
+    requests private outputs.  Returns latency and throughput figures."""
+    chk = dict(checks)
+    reqs = [inputs.request(k, sh, m, chk.get(i)) for i, (_, k, sh, m) in enumerate(trace)]
+    tickets = []
+    t0 = time.perf_counter()
+    for (t_arr, _, _, _), r in zip(trace, reqs):
+        while time.perf_counter() - t0 < t_arr:
+            pass
+        tickets.append(ibm.ibm_submit(srv, r))
+    submit_s = time.perf_counter() - t0
+    lat, dev_ms, ok, failed = [], [], 0, 0
+    for t in tickets:
+        if t is None:
+            failed += 1
+            continue
+        rc, res = ibm.ibm_wait(srv, t, 600.0)
+        if rc == ibm.IBM_OK:
+            ok += 1
+            lat.append(res.total_ms)
+            dev_ms.append(res.device_ms)
+        else:
+            failed += 1
+    wall = time.perf_counter() - t0
+    return {"requests": len(trace), "completed": ok, "failed_or_rejected": failed, "offered_req_per_s":
+            len(trace) / max(trace[-1][0], 1e-9) if trace else 0.0, "throughput_req_per_s": ok / wall,
+            "wall_s": wall, "submit_s": submit_s,
+            "p50_ms": float(np.percentile(lat, 50)) if lat else None,
+            "p99_ms": float(np.percentile(lat, 99)) if lat else None,
+            "device_ms_mean": float(np.mean(dev_ms)) if dev_ms else None}
+
+
+def serve_oracle_checks(ibm, torch, inputs, outs):
+    """Relative L2 and max-abs errors of sampled results against the FP64
+    oracle (the request's own input values in the plan precision)."""
+    from oracle import ibm_oracle as O
+    res = []
+    for (kind, sh, m), out in outs:
+        g, din, _ = inputs.fields[(kind, sh)]
+        x = din.double().cpu().numpy()
+        if kind == 0:
+            ref, _ = O.poisson_solve(x, g)
+            refs = [ref]
+            got = [out.double().cpu().numpy()]
+        elif kind == 1:
+            refs = [O.helmholtz_solve(x, g, 0.5 * DT * NU, O.CELL_DIRICHLET)]
+            got = [out.double().cpu().numpy()]
+        else:
+            X0, dV = (a.double().cpu().numpy() for a in inputs.spheres[m])
+            z = np.zeros_like(x[0])
+            st = dict(u=x[0], v=x[1], w=x[2], p=x[3], N_prev=(z, z, z), t=0.0)
+            mko = dict(X0=X0, dV=dV, kind=O.MOTION_TRANSLATE, params=(0.1, 0.0, 0.0))
+            ref, _ = O.rk_stage(st, mko, 1, DT, NU, g)
+            refs = [ref[k] for k in ("u", "v", "w", "p")]
+            o = out.double().cpu().numpy()
+            got = [o[c] for c in range(4)]
+        l2 = max(float(np.linalg.norm(a - b) / np.linalg.norm(b)) for a, b in zip(got, refs))
+        mx = max(float(np.abs(a - b).max() / np.abs(b).max()) for a, b in zip(got, refs))
+        res.append({"kind": ("poisson", "helmholtz", "rk_stage")[kind], "grid": list(sh), "markers": m,
+                    "rel_l2": l2, "rel_max_abs": mx})
+    return res
+
+
+def serve_sample(ibm, torch, duration_s=60.0, duration_fp64_s=10.0, rate=2000.0, oracle=True):
+    """The serving workload: Poisson arrivals at 2000 req/s; 60 % Poisson,
+    25 % Helmholtz, 15 % RK stage; grids log-uniform in points from 32^3 to
+    384 x 256 x 256; spheres of 1k-100k markers; requests carry device data
+    in the plan precision (IBM_DATA_DEVICE) into one server per precision (8
+    streams, resident plans).  Every (kind, shape) of the trace is served
+    once first (plans and slot buffers made); then the timed trace runs,
+    `duration_s` for FP32 with one refinement step and `duration_fp64_s`
+    for plain FP64 (whose capacity is below the offered rate), followed by
+    4-second runs at rising rates: the sustainable rate is the highest one
+    whose requests all complete at >= 95 % of the offered rate with p99 <=
+    20 ms.  A sample of results (one of each kind, the largest grid among
+    them) is checked against the FP64 oracle."""
+    trace = serve_trace(4004, duration_s, rate)
+    keys = {(k, sh) for _, k, sh, _ in trace}
+    samples = [(0, (384, 256, 256), 0), (1, (128, 64, 64), 0), (2, (64, 32, 32), 1000), (0, (48, 48, 48), 0)]
+    keys |= {(k, sh) for k, sh, _ in samples}
+    out = {"workload": "Poisson arrivals %.0f req/s; 60/25/15 %% Poisson/Helmholtz/RK stage; grids log-uniform in "
+                       "points 32^3 .. 384x256x256 (%d shapes); markers 1k..100k; device data in the plan precision; "
+                       "8 streams; %.0f s FP32-refined, %.0f s FP64" % (rate, len({sh for _, sh in keys}), duration_s,
+                                                                     duration_fp64_s)}
+    host = ServeInputs.host_data(keys)
+    for name, prec, dur, rates in (("fp32_refined", ibm.IBM_FP32_REFINED, duration_s, (4000.0, 8000.0, 16000.0)),
+                                   ("fp64", ibm.IBM_FP64, duration_fp64_s, (250.0, 500.0, 1000.0))):
+        inputs = ServeInputs(ibm, torch, prec, host)
+        srv = ibm.ibm_server_create(96 << 30, 8, 1 << 18)
+        try:
+            warm = [(0.0, k, sh, (1000 if k == 2 else 0)) for k, sh in sorted(keys)]
+            serve_run(ibm, srv, inputs, warm)
+            tr = [x for x in trace if x[0] < dur]
+            priv = {}
+            for j, (k, sh, m) in enumerate(samples):  # private outputs for the checked requests
+                idx = (j + 1) * len(tr) // (len(samples) + 1)
+                tr[idx] = (tr[idx][0], k, sh, m)
+                priv[idx] = ((k, sh, m), torch.empty_like(inputs.fields[(k, sh)][1]))
+            row = serve_run(ibm, srv, inputs, tr, [(i, o) for i, (_, o) in priv.items()])
+            if oracle:
+                row["oracle_check"] = serve_oracle_checks(ibm, torch, inputs, list(priv.values()))
+            sweep, sustainable = [], None
+            for lam in (rate,) + rates:
+                tr2 = [x for x in serve_trace(5000 + int(lam), 4.0, lam) if (x[1], x[2]) in inputs.fields]
+                rr = serve_run(ibm, srv, inputs, tr2)
+                good = rr["failed_or_rejected"] == 0 and rr["throughput_req_per_s"] >= 0.95 * rr["offered_req_per_s"] \
+                    and rr["p99_ms"] is not None and rr["p99_ms"] <= 20.0
+                sweep.append({"rate": lam, "throughput_req_per_s": rr["throughput_req_per_s"], "p50_ms": rr["p50_ms"],
+                              "p99_ms": rr["p99_ms"], "sustained": good})
+                if good:
+                    sustainable = lam
+            row["rate_sweep_4s"] = sweep
+            row["sustainable_req_per_s"] = sustainable
+            out[name] = row
+        finally:
+            ibm.ibm_server_destroy(srv)
+            del inputs
+            torch.cuda.empty_cache()
     return out
 
 
@@ -1203,6 +1332,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true",
                     help="the headline solve only (no 128^3 stage, plate, batched, serving or other samples)")
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle error checks")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="duration of the FP32-refined serving trace (the workload's 60 s by default)")
     ap.add_argument("--oracle-time", metavar="NPY", help=argparse.SUPPRESS)
     ap.add_argument("--reps", type=int, default=3, help=argparse.SUPPRESS)
     ap.add_argument("--quick", action="store_true",

@@ -365,6 +365,15 @@ int ibm_batch_poisson(ibm_batch batch, const void *const *rhs, void *const *phi,
 
 enum { IBM_REQ_POISSON = 0, IBM_REQ_HELMHOLTZ = 1, IBM_REQ_SUBSTEP = 2 };
 
+/* Where a request's data live (ibm_request.data). */
+enum {
+  IBM_DATA_HOST_FP64 = 0, /* host FP64 arrays: staged through pinned memory and
+                             converted to the plan precision on the device    */
+  IBM_DATA_DEVICE = 1     /* device arrays in the plan precision (float for
+                             IBM_FP32_REFINED, double for IBM_FP64), 16-byte
+                             aligned: no staging, no conversion                */
+};
+
 typedef struct {
   int kind;              /* IBM_REQ_*                                         */
   int nx, ny, nz;
@@ -373,17 +382,18 @@ typedef struct {
   int refine_iters;
   double c;              /* Helmholtz coefficient                             */
   int field_bc;          /* Helmholtz wall rows                               */
-  const double *in;      /* HOST FP64 input: rhs [ny][nz][nx] (Poisson,
-                            Helmholtz) or u,v,w,p packed [4][ny][nz][nx]
-                            (substep)                                        */
-  double *out;           /* HOST FP64 output, same shape as `in`              */
+  const void *in;        /* input: rhs [ny][nz][nx] (Poisson, Helmholtz) or
+                            u,v,w,p packed [4][ny][nz][nx] (substep); host
+                            FP64 or device, by `data`                         */
+  void *out;             /* output, same shape as `in` (distinct from it)      */
   int n_markers;         /* substep: markers                                  */
-  const double *X0;      /* substep: HOST [n][3]                              */
-  const double *dV;      /* substep: HOST [n]                                 */
+  const void *X0;        /* substep: [n][3], host FP64 or device, by `data`   */
+  const void *dV;        /* substep: [n], likewise                            */
   int motion;
   double params[4];
   double dt, nu;         /* substep                                           */
   int rk_stage;          /* substep                                           */
+  int data;              /* IBM_DATA_*                                        */
 } ibm_request;
 
 typedef struct {
@@ -402,8 +412,11 @@ typedef struct {
 int ibm_server_create(size_t hbm_budget_bytes, int n_streams, int max_queue,
                       ibm_server *out);
 int ibm_server_destroy(ibm_server server);
-/* Non-blocking: copies the request descriptor (not the data; `in` and `out`
- * must stay valid until completion) and returns a ticket. */
+/* Non-blocking: copies the request descriptor (not the data; `in`, `out`
+ * and the marker arrays must stay valid and, for IBM_DATA_DEVICE, unchanged
+ * until completion) and returns a ticket.  A substep request's `out` receives
+ * the stage's u, v, w, p; with IBM_DATA_DEVICE the stage runs on `out`
+ * itself after a device copy of `in`. */
 int ibm_submit(ibm_server server, const ibm_request *req, uint64_t *ticket);
 /* Non-blocking: IBM_PENDING while running; IBM_OK (result filled, `out`
  * written) once done; an error code for a failed request.  A finished

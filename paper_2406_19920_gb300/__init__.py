@@ -26,6 +26,7 @@ IBM_SPREAD_ATOMIC, IBM_SPREAD_GATHER, IBM_SPREAD_ATOMIC_DIRECT = 0, 1, 2
 IBM_MOTION_STATIC, IBM_MOTION_TRANSLATE, IBM_MOTION_HEAVE = 0, 1, 2
 IBM_SELFTEST_TENSOR_MEMORY, IBM_SELFTEST_BULK_COPY = 0, 1
 IBM_REQ_POISSON, IBM_REQ_HELMHOLTZ, IBM_REQ_SUBSTEP = 0, 1, 2
+IBM_DATA_HOST_FP64, IBM_DATA_DEVICE = 0, 1
 
 
 class IbmError(RuntimeError):
@@ -72,7 +73,8 @@ class ibm_request(ctypes.Structure):
                 ("in_", ctypes.c_void_p), ("out", ctypes.c_void_p),
                 ("n_markers", ctypes.c_int), ("X0", ctypes.c_void_p), ("dV", ctypes.c_void_p),
                 ("motion", ctypes.c_int), ("params", ctypes.c_double * 4),
-                ("dt", ctypes.c_double), ("nu", ctypes.c_double), ("rk_stage", ctypes.c_int)]
+                ("dt", ctypes.c_double), ("nu", ctypes.c_double), ("rk_stage", ctypes.c_int),
+                ("data", ctypes.c_int)]
 
 
 class ibm_result(ctypes.Structure):

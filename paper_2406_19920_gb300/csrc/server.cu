@@ -1,7 +1,9 @@
 // server.cu -- continuous-batching request server (ibm_server_*).
 //
 // Requests (Poisson, Helmholtz or one RK stage) arrive with FP64 host
-// buffers.  A scheduler thread
+// buffers (IBM_DATA_HOST_FP64) or with device buffers in the plan precision
+// (IBM_DATA_DEVICE, solved in place of the caller's output with no staging).
+// A scheduler thread
 //   * admits queued requests in arrival order whenever a stream slot is free
 //     and the request's device memory fits the HBM budget: resident plans are
 //     reused per (shape, precision, refinement); idle ones are evicted least
@@ -157,9 +159,15 @@ static size_t esz_of(const ibm_request &r) { return r.precision == IBM_FP64 ? 8 
 static int nfields_of(const ibm_request &r) { return r.kind == IBM_REQ_SUBSTEP ? 4 : 1; }
 
 // Device bytes a request needs besides its plan: FP64 staging of the
-// largest buffer, plan-precision fields and markers.
+// largest buffer, plan-precision fields and markers (device data: the stage's
+// advection fields and marker outputs only).
 static size_t io_bytes(const ibm_request &r) {
   const size_t n = npts_of(r), e = esz_of(r);
+  if (r.data == IBM_DATA_DEVICE) {
+    if (r.kind != IBM_REQ_SUBSTEP) return 4096;
+    const size_t m = (size_t)std::max(0, r.n_markers);
+    return 3 * n * e + m * e * 9 + 3 * 4096;
+  }
   if (r.kind == IBM_REQ_SUBSTEP) {
     const size_t m = (size_t)std::max(0, r.n_markers);
     return 4 * n * 8 + 7 * n * e + m * (3 * 8 + 8) + m * e * (3 + 1 + 3 + 3 + 3) + 4096;
@@ -204,6 +212,54 @@ template <typename T> static cudaError_t convert_out(const T *src, double *dst, 
   return cudaGetLastError();
 }
 
+// Device data (IBM_DATA_DEVICE): the solve reads the caller's `in` and
+// writes its `out`; a stage copies `in` to `out` and advances it in place,
+// with the advection fields and marker outputs in the slot's buffer.
+static int launch_device(Req *q, Slot &sl) {
+  const ibm_request &r = q->r;
+  const size_t n = npts_of(r), e = esz_of(r);
+  const size_t nm = (size_t)std::max(0, r.n_markers);
+  cudaStream_t st = sl.st;
+  ibm_plan_s *p = q->res->plan;
+  q->out_bytes = 0;
+  IBM_CUDA_TRY(cudaEventRecord(sl.e0, st));
+  int rc = IBM_OK;
+  if (r.kind == IBM_REQ_POISSON || r.kind == IBM_REQ_HELMHOLTZ) {
+    rc = r.kind == IBM_REQ_POISSON ? plan_solve(p, 0, 0.0, 0, r.in, r.out, nullptr, st, nullptr)
+                                   : plan_solve(p, 1, r.c, r.field_bc, r.in, r.out, nullptr, st, nullptr);
+    if (rc) return rc;
+  } else {
+    unsigned char *dp = static_cast<unsigned char *>(sl.dev);
+    auto take = [&](size_t bytes) {
+      unsigned char *x = dp;
+      dp += (bytes + 255) / 256 * 256;
+      return (void *)x;
+    };
+    IBM_CUDA_TRY(cudaMemcpyAsync(r.out, r.in, 4 * n * e, cudaMemcpyDeviceToDevice, st));
+    void *N[3];
+    for (int c = 0; c < 3; ++c) {
+      N[c] = take(n * e);
+      IBM_CUDA_TRY(cudaMemsetAsync(N[c], 0, n * e, st));
+    }
+    void *X = take(nm * 3 * e), *Ud = take(nm * 3 * e), *F = take(nm * 3 * e);
+    unsigned char *f = static_cast<unsigned char *>(r.out);
+    ibm_state stt{f, f + n * e, f + 2 * n * e, f + 3 * n * e, N[0], N[1], N[2], 0.0};
+    ibm_markers mk{};
+    mk.n = (int)nm;
+    mk.X0 = r.X0;
+    mk.dV = r.dV;
+    mk.X = X;
+    mk.Ud = Ud;
+    mk.F = F;
+    mk.motion = r.motion;
+    for (int k = 0; k < 4; ++k) mk.params[k] = r.params[k];
+    rc = ibm_substep(p, &stt, r.rk_stage, r.dt, r.nu, nm ? &mk : nullptr, st, nullptr);
+    if (rc) return rc;
+  }
+  IBM_CUDA_TRY(cudaEventRecord(sl.e1, st));
+  return IBM_OK;
+}
+
 // Stages and launches the device work of an admitted request on its slot
 // (worker thread, server lock not held); returns an IBM_* code.
 static int launch(ibm_server_s *s, Req *q, Slot &sl) {
@@ -211,6 +267,24 @@ static int launch(ibm_server_s *s, Req *q, Slot &sl) {
   const size_t n = npts_of(r), e = esz_of(r);
   const int nf = nfields_of(r);
   const size_t nm = (size_t)std::max(0, r.n_markers);
+  if (r.data == IBM_DATA_DEVICE) {
+    q->dbytes = io_bytes(r);
+    if (sl.dev_bytes < q->dbytes) {
+      // admission already reserved the growth in s->used
+      if (sl.dev) cudaFree(sl.dev);
+      sl.dev = nullptr;
+      cudaError_t e2 = cudaMalloc(&sl.dev, q->dbytes);
+      if (e2 != cudaSuccess) {
+        std::lock_guard<std::mutex> lock(s->mu);
+        s->used -= q->dbytes;
+        sl.dev_bytes = 0;
+        return cuda_error(e2, "server slot buffer");
+      }
+      sl.dev_bytes = q->dbytes;
+    }
+    q->dmem = sl.dev;
+    return launch_device(q, sl);
+  }
   const size_t in_host = nf * n * 8 + (r.kind == IBM_REQ_SUBSTEP ? nm * 4 * 8 : 0);
   // pinned staging for the slot
   if (sl.pinned_bytes < in_host) {
@@ -387,7 +461,7 @@ static void slot_worker(ibm_server_s *s, int k) {
     // fail this request (the resident plan's word is cleared for the next)
     if (rc == IBM_OK) rc = plan_status(q->res->plan, sl.st);
     if (rc == IBM_OK) {
-      stage_copy(q->r.out, sl.pinned, q->out_bytes);
+      if (q->r.data == IBM_DATA_HOST_FP64) stage_copy(q->r.out, sl.pinned, q->out_bytes);
       cudaEventElapsedTime(&q->device_ms, sl.e0, sl.e1);
     }
     lock.lock();
@@ -423,6 +497,13 @@ static int validate_request(const ibm_request *r) {
     return set_error(IBM_ERR_ARG, "ibm_submit: precision");
   if (r->refine_iters < 0 || r->refine_iters > 4) return set_error(IBM_ERR_ARG, "ibm_submit: refine_iters");
   if (!r->in || !r->out) return set_error(IBM_ERR_ARG, "ibm_submit: NULL in/out");
+  if (r->data != IBM_DATA_HOST_FP64 && r->data != IBM_DATA_DEVICE)
+    return set_error(IBM_ERR_ARG, "ibm_submit: data %d", r->data);
+  if (r->data == IBM_DATA_DEVICE) {
+    if (r->in == r->out) return set_error(IBM_ERR_ARG, "ibm_submit: device in and out must be distinct");
+    if (!aligned_to(r->in, 16) || !aligned_to(r->out, 16))
+      return set_error(IBM_ERR_ARG, "ibm_submit: device fields must be 16-byte aligned");
+  }
   if (r->kind == IBM_REQ_HELMHOLTZ && (!(r->c > 0) || r->field_bc < 0 || r->field_bc > 2))
     return set_error(IBM_ERR_ARG, "ibm_submit: Helmholtz c / field_bc");
   if (r->kind == IBM_REQ_SUBSTEP) {

@@ -171,3 +171,89 @@ def test_cancel_budget_and_fault_hook():
         assert codes == [ibm.IBM_OK, ibm.IBM_ERR_OOM, ibm.IBM_OK]
     finally:
         ibm.ibm_server_destroy(srv)
+
+
+def test_device_data_requests_equal_host_fp64_requests():
+    """IBM_DATA_DEVICE: requests whose fields and markers are device arrays in
+    the plan precision (no host staging, no FP64 conversion) give the results
+    of the same requests served from FP64 host buffers, in a concurrent mix,
+    and Poisson results match the oracle.  A stage's input stays untouched
+    (it runs on a copy in the output)."""
+    reqs = _mix()
+    host_out, res = _serve(reqs, n_streams=4)
+    assert all(rc == ibm.IBM_OK for rc, _ in res)
+    srv = ibm.ibm_server_create(8 << 30, 6, 1024)
+    keep, tickets, outs = [], [], []
+    try:
+        for q in reqs:
+            dt = torch.float64 if q["prec"] == ibm.IBM_FP64 else torch.float32
+            din = torch.from_numpy(q["data"]).to("cuda", dt)
+            dout = torch.zeros_like(din)
+            kw = {k: v for k, v in q.items() if k not in ("kind", "shape", "prec", "data")}
+            dm = {}
+            if "X0" in kw:
+                dm = dict(X0=torch.from_numpy(kw.pop("X0")).to("cuda", dt), dV=torch.from_numpy(kw.pop("dV")).to("cuda", dt))
+            r = _request(q["kind"], q["shape"], q["prec"], q["data"], q["data"], **kw)
+            r.in_, r.out, r.data = din.data_ptr(), dout.data_ptr(), ibm.IBM_DATA_DEVICE
+            if dm:
+                r.X0, r.dV = dm["X0"].data_ptr(), dm["dV"].data_ptr()
+            keep.append((r, din, dout, dm))
+            t = ibm.ibm_submit(srv, r)
+            assert t is not None
+            tickets.append(t)
+        for t in tickets:
+            rc, res1 = ibm.ibm_wait(srv, t, 120.0)
+            assert rc == ibm.IBM_OK and res1.device_ms > 0.0
+        for (r, din, dout, dm), q, ho in zip(keep, reqs, host_out):
+            tol = TOL_FP64 if q["prec"] == ibm.IBM_FP64 else TOL_FP32
+            got = dout.double().cpu().numpy()
+            assert rel_err(got, ho) <= tol, (q["kind"], rel_err(got, ho))
+            assert np.array_equal(din.double().cpu().numpy(),
+                                  q["data"].astype(np.float32 if q["prec"] else np.float64).astype(np.float64))
+            if q["kind"] == ibm.IBM_REQ_POISSON:
+                data = q["data"].astype(np.float32).astype(np.float64) if q["prec"] else q["data"]
+                ref, _ = O.poisson_solve(data, grid(*q["shape"]))
+                assert rel_err(got, ref) <= tol
+    finally:
+        ibm.ibm_server_destroy(srv)
+    # rejected before admission: aliasing and misaligned device fields, an unknown data kind
+    srv = ibm.ibm_server_create(1 << 30, 1, 4)
+    try:
+        x = torch.zeros(4096, device="cuda")
+        r = _request(ibm.IBM_REQ_POISSON, (16, 16, 16), ibm.IBM_FP32_REFINED, np.zeros(1), np.zeros(1))
+        r.data, r.in_, r.out = ibm.IBM_DATA_DEVICE, x.data_ptr(), x.data_ptr()
+        with pytest.raises(ibm.IbmError):
+            ibm.ibm_submit(srv, r)
+        r.out = x.data_ptr() + 4
+        with pytest.raises(ibm.IbmError):
+            ibm.ibm_submit(srv, r)
+        r.out, r.data = x.data_ptr() + 8192, 5
+        with pytest.raises(ibm.IbmError):
+            ibm.ibm_submit(srv, r)
+    finally:
+        ibm.ibm_server_destroy(srv)
+
+
+def test_request_with_a_marker_past_the_wall_rule_fails():
+    """A stage request whose sphere reaches within the delta support of a wall
+    fails with IBM_ERR_ARG (the wall rule), and the server's next request of
+    the same shape (the same resident plan) succeeds."""
+    shape = (32, 32, 32)
+    g = grid(*shape)
+    u, v, w = synth.div_free_velocity(g, workload=71, kmax=4)
+    data = np.ascontiguousarray(np.stack([u, v, w, np.zeros_like(u)]))
+    X0, dV = synth.fibonacci_sphere(200, 0.25, (math.pi, 0.2, math.pi), g[3])  # reaches y = -0.05
+    ok0, okdV = synth.fibonacci_sphere(200, 0.25, (math.pi, 1.0, math.pi), g[3])
+    srv = ibm.ibm_server_create(2 << 30, 1, 16)
+    try:
+        outs = [np.zeros_like(data) for _ in range(2)]
+        bad = _request(ibm.IBM_REQ_SUBSTEP, shape, ibm.IBM_FP32_REFINED, data, outs[0], n_markers=200,
+                       X0=np.ascontiguousarray(X0), dV=np.ascontiguousarray(dV), motion=ibm.IBM_MOTION_STATIC)
+        good = _request(ibm.IBM_REQ_SUBSTEP, shape, ibm.IBM_FP32_REFINED, data, outs[1], n_markers=200,
+                        X0=np.ascontiguousarray(ok0), dV=np.ascontiguousarray(okdV), motion=ibm.IBM_MOTION_STATIC)
+        t1 = ibm.ibm_submit(srv, bad)
+        assert ibm.ibm_wait(srv, t1, 60.0)[0] == ibm.IBM_ERR_ARG
+        t2 = ibm.ibm_submit(srv, good)
+        assert ibm.ibm_wait(srv, t2, 60.0)[0] == ibm.IBM_OK
+    finally:
+        ibm.ibm_server_destroy(srv)
