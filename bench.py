@@ -879,13 +879,101 @@ def batched_compare(ibm, torch):
               for a, c in zip(phi[0], p64))
     for pl in plans:
         ibm.ibm_plan_destroy(pl)
+    stage = batched_stage(ibm, torch, b, dims, hs)
     ibm.ibm_batch_destroy(b)
-    return {"instances": 64, "rhs_per_instance": 4, "grid_pts_per_set": pts // 4,
+    return {"instances": 64, "rhs_per_instance": 4, "grid_pts_per_set": pts // 4, "rk_stage_with_markers": stage,
             "fp32_refined_batched": {"solves_per_s": 256e3 / ms, "grid_pts_per_s": pts / (ms * 1e-3),
                                      "ms_per_256_solves": ms},
             "fp32_refined_batched_fft_only": {"solves_per_s": 256e3 / ms_fft, "ms_per_256_solves": ms_fft},
             "fp64_sequential": {"solves_per_s": 64e3 / ms64, "grid_pts_per_s": (pts / 4) / (ms64 * 1e-3)},
             "speedup": (256e3 / ms) / (64e3 / ms64), "max_rel_l2_vs_fp64": err, "create_and_tune_s": create_s}
+
+
+def batched_stage(ibm, torch, b, dims, hs, reps=6):
+    """The batched workload's instances with their marker spheres: each of the
+    64 instances gets a still Fibonacci sphere of radius 0.25 with a marker
+    count drawn uniformly from [500, 8000] and one RK stage (ibm_substep:
+    explicit terms, interpolation, force and spreading on its sphere, three
+    Helmholtz and one refined Poisson solve, projection) -- all 64 stages as
+    one graph launch (ibm_batch_substep, replayed) against the same stages
+    run one instance after another (FP32 + refinement, and plain FP64).
+    Reports stages/s, grid points/s and the first instance's stage against
+    the FP64 oracle."""
+    from paper_2406_19920_gb300 import synth
+    rng = np.random.default_rng(3006)
+    counts = [int(c) for c in rng.integers(500, 8001, len(dims))]
+    pts = sum(d[0] * d[1] * d[2] for d in dims)
+    out = {"markers_per_instance": [min(counts), max(counts)], "markers_total": sum(counts)}
+    keep = []
+
+    def make(prec, i, d, m):
+        g = synth.grid(*d)
+        dt = torch.float32 if prec == ibm.IBM_FP32_REFINED else torch.float64
+        u, v, w = synth.div_free_velocity(g, workload=90 + i % 8, kmax=min(d) / 4)
+        X0, dV = synth.fibonacci_sphere(m, 0.25, (math.pi, 1.0, math.pi), g[3])
+        f = [torch.from_numpy(a).to("cuda", dt) for a in (u, v, w, np.zeros_like(u))]
+        f += [torch.zeros(u.shape, dtype=dt, device="cuda") for _ in range(3)]
+        Xd, dVd = (torch.from_numpy(np.ascontiguousarray(a)).to("cuda", dt) for a in (X0, dV))
+        X, Ud, F = (torch.empty((m, 3), dtype=dt, device="cuda") for _ in range(3))
+        keep.append((f, Xd, dVd, X, Ud, F))
+        st = ibm.ibm_state(*[t.data_ptr() for t in f], 0.0)
+        mk = ibm.ibm_markers(m, Xd.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
+                             ibm.IBM_MOTION_STATIC, (ctypes.c_double * 4)(0, 0, 0, 0))
+        return st, mk, (u, v, w, X0, dV, g)
+
+    inst = [make(ibm.IBM_FP32_REFINED, i, d, m) for i, (d, m) in enumerate(zip(dims, counts))]
+    states, mks = [x[0] for x in inst], [x[1] for x in inst]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ibm.ibm_batch_substep(b, states, mks, 1, DT, NU)  # capture
+    ibm.ibm_batch_substep(b, states, mks, 1, DT, NU)  # replay
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(reps):
+        ibm.ibm_batch_substep(b, states, mks, 1, DT, NU)
+    e1.record()
+    torch.cuda.synchronize()
+    ms_batch = e0.elapsed_time(e1) / reps
+    out["fp32_refined_batched"] = {"ms_per_64_stages": ms_batch, "stages_per_s": 64e3 / ms_batch,
+                                   "grid_pts_per_s": pts / (ms_batch * 1e-3)}
+    for name, prec in (("fp32_refined_sequential", ibm.IBM_FP32_REFINED), ("fp64_sequential", ibm.IBM_FP64)):
+        plans = [ibm.ibm_plan_create(*d, h, prec, 1 if prec == ibm.IBM_FP32_REFINED else 0) for d, h in zip(dims, hs)]
+        seq = inst if prec == ibm.IBM_FP32_REFINED else [make(prec, i, d, m) for i, (d, m) in
+                                                         enumerate(zip(dims, counts))]
+        for pl, x in zip(plans, seq):
+            ibm.ibm_substep(pl, x[0], 1, DT, NU, x[1])
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(2):
+            for pl, x in zip(plans, seq):
+                ibm.ibm_substep(pl, x[0], 1, DT, NU, x[1])
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / 2
+        out[name] = {"ms_per_64_stages": ms, "stages_per_s": 64e3 / ms, "grid_pts_per_s": pts / (ms * 1e-3)}
+        for pl in plans:
+            ibm.ibm_plan_destroy(pl)
+    out["speedup_batched_fp32_over_sequential_fp64"] = out["fp64_sequential"]["ms_per_64_stages"] / ms_batch
+    # the first instance, one fresh batched stage, against the oracle
+    from oracle import ibm_oracle as O
+    solo = ibm.ibm_batch_create([dims[0]], [hs[0]], ibm.IBM_FP32_REFINED, 1)
+    try:
+        st, mk, (u, v, w, X0, dV, g) = make(ibm.IBM_FP32_REFINED, 0, dims[0], counts[0])
+        ibm.ibm_batch_substep(solo, [st], [mk], 1, DT, NU)
+        torch.cuda.synchronize()
+        f = keep[-1][0]
+        c32 = lambda a: np.asarray(a, dtype=np.float32).astype(np.float64)
+        z = np.zeros_like(u)
+        ref, _ = O.rk_stage(dict(u=c32(u), v=c32(v), w=c32(w), p=z.copy(), N_prev=(z, z, z), t=0.0),
+                            dict(X0=c32(X0), dV=c32(dV), kind=O.MOTION_STATIC, params=()), 1, DT, NU, g)
+        out["oracle_error_instance0"] = {
+            k: {"rel_l2": float(np.linalg.norm(f[c].double().cpu().numpy() - ref[k]) / np.linalg.norm(ref[k])),
+                "rel_max_abs": float(np.abs(f[c].double().cpu().numpy() - ref[k]).max() / np.abs(ref[k]).max())}
+            for c, k in enumerate("uvwp")}
+        out["oracle_grid"] = list(dims[0])
+    finally:
+        ibm.ibm_batch_destroy(solo)
+    del keep
+    return out
 
 
 def dft_compare(ibm, torch, sizes=(32, 48, 64), reps=50):

@@ -358,6 +358,18 @@ int ibm_batch_destroy(ibm_batch batch);
  * pointer set and replayed as a single graph launch on `stream`. */
 int ibm_batch_poisson(ibm_batch batch, const void *const *rhs, void *const *phi,
                       void *stream);
+/* One RK stage (as ibm_substep, Eq. 2a-2h with the immersed boundary of
+ * Sec. 2.3.2) of every instance: states[i] is instance i's state and
+ * markers[i] its marker set (n = 0, or markers == NULL, for none).  The
+ * instances' stages run as concurrent branches of one CUDA graph launch on
+ * `stream`.  When no instance's markers move (IBM_MOTION_STATIC) the graph
+ * is kept per set of pointers, stage, dt and nu and replayed by later calls;
+ * moving markers (whose positions are evaluated at the stage start time on
+ * the host) are captured anew on every call.  The first call of a plan
+ * allocates its stage buffers.  Every state's t is advanced as by
+ * ibm_substep.  Errors as ibm_substep, per instance. */
+int ibm_batch_substep(ibm_batch batch, ibm_state *states, ibm_markers *markers, int rk_stage,
+                      double dt, double nu, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Serving: continuous batching of solve requests with HBM-based admission

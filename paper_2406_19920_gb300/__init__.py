@@ -109,6 +109,7 @@ _SIG = {
     "ibm_batch_create": (_I, [_I, ctypes.POINTER(_I), ctypes.POINTER(_D), _I, _I, ctypes.POINTER(_P)]),
     "ibm_batch_destroy": (_I, [_P]),
     "ibm_batch_poisson": (_I, [_P, ctypes.POINTER(_P), ctypes.POINTER(_P), _P]),
+    "ibm_batch_substep": (_I, [_P, ctypes.POINTER(ibm_state), ctypes.POINTER(ibm_markers), _I, _D, _D, _P]),
     "ibm_server_create": (_I, [ctypes.c_size_t, _I, _I, ctypes.POINTER(_P)]),
     "ibm_server_destroy": (_I, [_P]),
     "ibm_submit": (_I, [_P, ctypes.POINTER(ibm_request), ctypes.POINTER(ctypes.c_uint64)]),
@@ -309,6 +310,17 @@ def ibm_batch_poisson(batch, rhs_list, phi_list, stream=None):
     r = (_P * n)(*[_ptr(t) for t in rhs_list])
     p = (_P * n)(*[_ptr(t) for t in phi_list])
     return _check(lib().ibm_batch_poisson(batch, r, p, _stream(stream)))
+
+
+def ibm_batch_substep(batch, states, markers, rk_stage, dt, nu, stream=None):
+    """One RK stage of every instance (states: list of ibm_state, markers:
+    list of ibm_markers or None); the states' t are advanced in place."""
+    n = len(states)
+    S = (ibm_state * n)(*states)
+    M = (ibm_markers * n)(*markers) if markers is not None else None
+    _check(lib().ibm_batch_substep(batch, S, M, int(rk_stage), float(dt), float(nu), _stream(stream)))
+    for i, st in enumerate(states):
+        st.t = S[i].t
 
 
 def ibm_server_create(hbm_budget_bytes, n_streams=4, max_queue=4096):

@@ -181,11 +181,13 @@ struct ibm_batch_s {
     cudaGraphExec_t exec;
   };
   std::vector<Graph> graphs;  // most recently used last
+  std::vector<Graph> stage_graphs;  // RK-stage graphs (instances with still markers), most recently used last
 };
 
 static void batch_free(ibm_batch_s *b) {
   if (!b) return;
   for (auto &g : b->graphs) cudaGraphExecDestroy(g.exec);
+  for (auto &g : b->stage_graphs) cudaGraphExecDestroy(g.exec);
   for (auto *p : b->plans)
     if (p) ibm_plan_destroy(p);
   for (int k = 0; k < ibm_batch_s::kMaxBranches; ++k) {
@@ -211,6 +213,37 @@ static int capture_batch(ibm_batch_s *b, int K, const void *const *rhs, void *co
   for (size_t n = 0; n < b->order.size() && rc == IBM_OK; ++n) {
     const int i = b->order[n];
     rc = plan_solve(b->plans[i], 0, 0.0, 0, rhs[i], phi[i], nullptr, b->side[n % K], nullptr);
+  }
+  for (int k = 0; k < K && rc == IBM_OK; ++k) {
+    e = cudaEventRecord(b->ev_join[k], b->side[k]);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(st, b->ev_join[k], 0);
+    if (e != cudaSuccess) rc = cuda_error(e, "batch join");
+  }
+  e = cudaStreamEndCapture(st, &graph);
+  if (rc) {
+    if (graph) cudaGraphDestroy(graph);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_error(e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(out, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_error(e, "cudaGraphInstantiate");
+  return IBM_OK;
+}
+
+// Captures one RK stage of every instance as one graph with K branches.
+static int capture_stage(ibm_batch_s *b, int K, ibm_state *states, ibm_markers *markers, int rk_stage, double dt,
+                         double nu, cudaStream_t st, cudaGraphExec_t *out) {
+  cudaGraph_t graph = nullptr;
+  IBM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  int rc = IBM_OK;
+  cudaError_t e = cudaEventRecord(b->ev_fork, st);
+  for (int k = 0; k < K && e == cudaSuccess; ++k) e = cudaStreamWaitEvent(b->side[k], b->ev_fork, 0);
+  if (e != cudaSuccess) rc = cuda_error(e, "batch fork");
+  for (size_t n = 0; n < b->order.size() && rc == IBM_OK; ++n) {
+    const int i = b->order[n];
+    ibm_markers *mk = markers && markers[i].n > 0 ? &markers[i] : nullptr;
+    rc = substep_checked(b->plans[i], &states[i], rk_stage, dt, nu, mk, b->side[n % K]);
   }
   for (int k = 0; k < K && rc == IBM_OK; ++k) {
     e = cudaEventRecord(b->ev_join[k], b->side[k]);
@@ -394,6 +427,81 @@ int ibm_batch_poisson(ibm_batch b, const void *const *rhs, void *const *phi, voi
   IBM_CUDA_TRY(cudaEventRecord(b->ev_out, st));
   IBM_CUDA_TRY(cudaStreamWaitEvent(user, b->ev_out, 0));
   return IBM_OK;
+}
+
+int ibm_batch_substep(ibm_batch b, ibm_state *states, ibm_markers *markers, int rk_stage, double dt, double nu,
+                      void *stream) {
+  if (!b || !states) return set_error(IBM_ERR_ARG, "ibm_batch_substep: NULL argument");
+  if (rk_stage < 1 || rk_stage > 3) return set_error(IBM_ERR_ARG, "ibm_batch_substep: rk_stage %d", rk_stage);
+  if (!(dt > 0) || !(nu > 0)) return set_error(IBM_ERR_ARG, "ibm_batch_substep: dt and nu must be > 0");
+  // every buffer a stage uses exists before any capture; the graph can be
+  // replayed only when no instance's markers move (their positions are
+  // evaluated on the host at capture)
+  bool still = true;
+  std::vector<uintptr_t> key;
+  key.reserve(12 * (size_t)b->count + 3);
+  key.push_back((uintptr_t)rk_stage);
+  uint64_t bits[2];
+  std::memcpy(&bits[0], &dt, 8);
+  std::memcpy(&bits[1], &nu, 8);
+  key.push_back((uintptr_t)bits[0]);
+  key.push_back((uintptr_t)bits[1]);
+  for (int i = 0; i < b->count; ++i) {
+    const ibm_markers *mk = markers ? &markers[i] : nullptr;
+    const int nmk = mk ? mk->n : 0;
+    if (nmk < 0) return set_error(IBM_ERR_ARG, "ibm_batch_substep: instance %d: negative marker count", i);
+    if (nmk > 0 && mk->motion != IBM_MOTION_STATIC) still = false;
+    int rc = prepare_substep(b->plans[i], nmk);
+    if (rc) return rc;
+    const ibm_state &s = states[i];
+    for (const void *f : {s.u, s.v, s.w, s.p, s.Nu, s.Nv, s.Nw}) key.push_back((uintptr_t)f);
+    key.push_back((uintptr_t)nmk);
+    if (nmk > 0)
+      for (const void *f : {mk->X0, mk->dV, (const void *)mk->X, (const void *)mk->Ud, (const void *)mk->F})
+        key.push_back((uintptr_t)f);
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  cudaStream_t st = b->cap;
+  IBM_CUDA_TRY(cudaEventRecord(b->ev_in, user));
+  IBM_CUDA_TRY(cudaStreamWaitEvent(st, b->ev_in, 0));
+  auto launch = [&](cudaGraphExec_t ex) -> int {
+    IBM_CUDA_TRY(cudaGraphLaunch(ex, st));
+    IBM_CUDA_TRY(cudaEventRecord(b->ev_out, st));
+    IBM_CUDA_TRY(cudaStreamWaitEvent(user, b->ev_out, 0));
+    return IBM_OK;
+  };
+  if (still) {
+    for (size_t g = 0; g < b->stage_graphs.size(); ++g) {
+      if (b->stage_graphs[g].key == key) {
+        auto hit = b->stage_graphs[g];
+        b->stage_graphs.erase(b->stage_graphs.begin() + g);
+        b->stage_graphs.push_back(hit);
+        for (int i = 0; i < b->count; ++i)  // what the captured stage did on the host
+          states[i].t += stage_time_advance(rk_stage, dt);
+        return launch(hit.exec);
+      }
+    }
+  }
+  // the stage advances every instance's state: no tuning runs on the caller's
+  // data; the fork width is the Poisson batch's, else min(8, count)
+  const int K = b->branches > 0 ? b->branches : std::min(8, b->count);
+  cudaGraphExec_t exec = nullptr;
+  {
+    int rc = capture_stage(b, K, states, markers, rk_stage, dt, nu, st, &exec);
+    if (rc) return rc;
+  }
+  int rc = launch(exec);
+  if (!still) {
+    IBM_CUDA_TRY(cudaStreamSynchronize(st));
+    cudaGraphExecDestroy(exec);
+    return rc;
+  }
+  if (b->stage_graphs.size() >= 6) {
+    cudaGraphExecDestroy(b->stage_graphs.front().exec);
+    b->stage_graphs.erase(b->stage_graphs.begin());
+  }
+  b->stage_graphs.push_back({key, exec});
+  return rc;
 }
 
 }  // extern "C"

@@ -123,6 +123,15 @@ int plan_solve_fields(ibm_plan_s *p, double c, int nb, const int *field_bc, cons
 // off).
 bool default_use_slab(int precision, int bc, int nx, int ny, int nz);
 
+// One validated RK stage without info (substep.cu), and the allocation of
+// every buffer a stage with nmk markers uses, so that a stage can be captured
+// into a CUDA graph (no allocation during capture).
+int substep_checked(ibm_plan_s *p, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
+                    cudaStream_t stream);
+int prepare_substep(ibm_plan_s *p, int nmk);
+// (alpha_n + beta_n) dt: how far stage n advances the state time.
+double stage_time_advance(int rk_stage, double dt);
+
 // Autotuner result for one shape (batch.cu).
 struct TuneChoice {
   int pencil_mode, use_plane;

@@ -661,6 +661,28 @@ static int substep_entry(ibm_plan plan, ibm_state *st, const ibm_inout *io, int 
   return substep_t<float>(plan, st, io, rk_stage, dt, nu, mk, (cudaStream_t)stream, info);
 }
 
+namespace ibm {
+double stage_time_advance(int rk_stage, double dt) { return (kAlpha[rk_stage - 1] + kBeta[rk_stage - 1]) * dt; }
+
+int substep_checked(ibm_plan_s *p, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
+                    cudaStream_t stream) {
+  return substep_entry(p, st, nullptr, rk_stage, dt, nu, mk, stream, nullptr);
+}
+
+int prepare_substep(ibm_plan_s *p, int nmk) {
+  int rc = ensure_substep_buffers(p, nmk);
+  if (rc) return rc;
+  for (int b = 0; b < 2; ++b) {  // the spectra of the stage's three-field Helmholtz launches
+    if (!p->Sx[b]) {
+      cudaError_t e = cudaMalloc(&p->Sx[b], p->nspec * 2 * p->esz);
+      if (e != cudaSuccess) { p->Sx[b] = nullptr; return cuda_error(e, "field spectrum"); }
+      p->bytes += p->nspec * 2 * p->esz;
+    }
+  }
+  return IBM_OK;
+}
+}  // namespace ibm
+
 extern "C" int ibm_substep(ibm_plan plan, ibm_state *st, int rk_stage, double dt, double nu, ibm_markers *mk,
                            void *stream, ibm_info *info) {
   return substep_entry(plan, st, nullptr, rk_stage, dt, nu, mk, stream, info);
