@@ -91,7 +91,11 @@ def test_batched_stage_with_markers_equals_instances_alone(prec):
     counts = [500, 1200, 2000, 800, 600, 1500]
     grids = [grid(*d) for d in dims]
     batch = ibm.ibm_batch_create(dims, [g[3:] for g in grids], prec, 1)
-    tol = TOL_FP32 if prec == ibm.IBM_FP32_REFINED else 1e-11
+    # the batch's plans take the kernels its tuner picked, the lone plans the
+    # default ones, so FP32 fields differ by rounding that accumulates over
+    # the stages: the FP32 stage tolerance (the pressure, defined up to a
+    # constant and concentrated at the sphere, carries most of it)
+    tol = 3e-6 if prec == ibm.IBM_FP32_REFINED else 1e-11
     try:
         inst = [_stage_instance(d, i, prec, m) for i, (d, m) in enumerate(zip(dims, counts))]
         alone = [_stage_instance(d, i, prec, m) for i, (d, m) in enumerate(zip(dims, counts))]
