@@ -60,15 +60,20 @@ NX = NY = NZ = 128
 N_MARKERS = 20000
 DT, NU = 1e-3, 1e-2
 N_STATES = 4
-KERNEL_SOURCES = {"forward": ("transforms.cu", "axis.cu", "fft2.cuh"),
-                  "inverse": ("transforms.cu", "axis.cu", "fft2.cuh"), "pencil": ("pencil.cu",),
-                  "residual": ("stencil.cu",), "explicit": ("substep.cu",), "divergence": ("substep.cu",),
-                  "project": ("substep.cu",), "interp": ("ibm_kernels.cu",), "spread": ("ibm_kernels.cu",),
-                  "motion": ("ibm_kernels.cu",)}
+# sources of each kernel kind per workload (a DRAM-traffic figure taken by ncu
+# is reported only while these are unchanged)
+KERNEL_SOURCES = {
+    "headline": {"forward": ("slab.cu", "fft2.cuh"), "pencil": ("slab.cu", "seg.cuh", "fft2.cuh"),
+                 "inverse": ("slab.cu", "fft2.cuh"), "residual": ("stencil.cu",)},
+    "stage": {"forward": ("transforms.cu", "axis.cu", "fft2.cuh"),
+              "inverse": ("transforms.cu", "axis.cu", "fft2.cuh"), "pencil": ("pencil.cu", "seg.cuh"),
+              "residual": ("stencil.cu",), "explicit": ("substep.cu",), "divergence": ("substep.cu",),
+              "project": ("substep.cu",), "interp": ("ibm_kernels.cu",), "spread": ("ibm_kernels.cu",),
+              "motion": ("ibm_kernels.cu",)}}
 # kernel-name prefix -> kind (the names ncu prints)
 KERNEL_KIND = (("k_plane_fwd", "forward"), ("k_rows_fwd", "forward"), ("k_cplane_fwd", "forward"),
                ("k_plane_inv", "inverse"), ("k_rows_inv", "inverse"), ("k_cplane_inv", "inverse"),
-               ("k_pencil", "pencil"), ("k_residual", "residual"), ("k_explicit", "explicit"),
+               ("k_pencil", "pencil"), ("k_slab", "pencil"), ("k_residual", "residual"), ("k_explicit", "explicit"),
                ("k_divergence", "divergence"), ("k_project", "project"), ("k_interp", "interp"),
                ("k_spread", "spread"), ("k_motion", "motion"))
 STAGE_WORKLOAD = "ibm_substep 128^3 FP32+1 refinement, 20k-marker sphere"
@@ -174,27 +179,63 @@ def measured_peak():
         return 6800.0, "of fallback"
 
 
-def source_digest(kind):
+def source_digest(kind, which="headline"):
     h = hashlib.sha256()
-    for name in KERNEL_SOURCES[kind]:
+    for name in KERNEL_SOURCES[which][kind]:
         with open(os.path.join(ROOT, "paper_2406_19920_gb300", "csrc", name), "rb") as f:
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def ncu_traffic(kind, workload):
-    """DRAM bytes per step of a kernel kind from the committed ncu summary,
-    if its sources are unchanged since the capture; else None."""
+def ncu_traffic(kind, which="headline"):
+    """DRAM bytes per step of a kernel kind (its launches in one step) from
+    the committed single-kernel ncu captures, if the kind's sources are
+    unchanged since the capture; else None."""
     p = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
         with open(p) as f:
             d = json.load(f)
     except (OSError, ValueError):
         return None
-    e = d.get(kind)
-    if not e or e.get("workload") != workload or e.get("source_sha256_16") != source_digest(kind):
+    e = d.get(which, {}).get(kind)
+    if not e or e.get("source_sha256_16") != source_digest(kind, which):
         return None
     return e.get("dram_bytes_per_step")
+
+
+def ncu_counters(csv_path, which, launches_per_step):
+    """Records, from a raw-page CSV of a single-kernel ncu capture
+    (`ncu -i rep --page raw --csv`), the captured kernel's DRAM bytes per
+    launch times its launches per step in profiles/dram_traffic.json under
+    `which` ("headline" or "stage") and the kernel's kind."""
+    import csv
+    rows = list(csv.reader(open(csv_path)))
+    hdr, units, data = rows[0], rows[1], rows[2:]
+    idx = {h: k for k, h in enumerate(hdr)}
+    scale = {"byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}
+    per = {}
+    for d in data:
+        kind = kernel_kind(d[idx["Kernel Name"]])
+        b = sum(float(d[idx[m]].replace(",", "")) * scale.get(units[idx[m]], 1.0)
+                for m in ("dram__bytes_read.sum", "dram__bytes_write.sum"))
+        per.setdefault(kind, []).append(b)
+    p = os.path.join(ROOT, "profiles", "dram_traffic.json")
+    try:
+        with open(p) as f:
+            out = json.load(f)
+    except (OSError, ValueError):
+        out = {}
+    for kind, vals in per.items():
+        out.setdefault(which, {})[kind] = {
+            "dram_bytes_per_launch": sum(vals) / len(vals), "launches_per_step": launches_per_step,
+            "dram_bytes_per_step": sum(vals) / len(vals) * launches_per_step,
+            "source_sha256_16": source_digest(kind, which),
+            "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum of a single-kernel capture (-k, -c <= 3) of "
+                    "`bench.py --solve 256`, averaged over the captured launches; the replay flushes caches before a "
+                    "launch, not after, so writes still in L2 at the kernel's end are not counted"}
+        print(kind, out[which][kind]["dram_bytes_per_launch"])
+    with open(p, "w") as f:
+        json.dump(out, f, indent=1, sort_keys=True)
 
 
 def solve_kind_bytes(n, esz=4, refine=HEAD_REFINE):
@@ -259,51 +300,31 @@ def kernel_kind(name):
 
 
 def ncu_summary(csv_path, steps):
-    """Per-kind launches, device time and DRAM bytes per step from an ncu
-    --csv launch list of `bench.py --quick` (profiler region = the timed
-    steps); writes profiles/dram_traffic.json and prints a markdown table."""
+    """Per-kernel launches, device time per step and share from an ncu --csv
+    launch list (gpu__time_duration.sum) of `bench.py --quick --steps K`
+    (profiler region = the timed steps); prints a markdown table."""
     import csv
-    rows = []
     with open(csv_path) as f:
         lines = [ln for ln in f if ln.startswith('"')]
-    for r in csv.DictReader(lines):
-        rows.append(r)
     agg = {}
-    for r in rows:
+    for r in csv.DictReader(lines):
+        if r["Metric Name"] != "gpu__time_duration.sum":
+            continue
         kind = kernel_kind(r["Kernel Name"])
         if kind is None:
             continue
         short = r["Kernel Name"].replace("void ", "", 1).replace("ibm::", "").split("(")[0]
-        a = agg.setdefault((kind, short), {"ids": set(), "ns": 0.0, "rd": 0.0, "wr": 0.0})
+        a = agg.setdefault((kind, short), {"ids": set(), "ns": 0.0})
         a["ids"].add(r["ID"])
         val = float(r["Metric Value"].replace(",", ""))
-        unit = r["Metric Unit"]
-        scale = {"ns": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6, "nsecond": 1.0,
-                 "byte": 1.0, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1e3, "MB": 1e6, "GB": 1e9}.get(unit, 1.0)
-        if r["Metric Name"] == "gpu__time_duration.sum":
-            a["ns"] += val * scale
-        elif r["Metric Name"] == "dram__bytes_read.sum":
-            a["rd"] += val * scale
-        elif r["Metric Name"] == "dram__bytes_write.sum":
-            a["wr"] += val * scale
+        a["ns"] += val * {"ns": 1.0, "nsecond": 1.0, "us": 1e3, "usecond": 1e3, "ms": 1e6, "msecond": 1e6}.get(
+            r["Metric Unit"], 1.0)
     total_ns = sum(a["ns"] for a in agg.values())
-    print("| kernel | kind | launches/step | us/step | share | DRAM MB/step (read+write) |")
-    print("|---|---|---|---|---|---|")
-    kinds = {}
+    print("| kernel | kind | launches/step | us/step | share |")
+    print("|---|---|---|---|---|")
     for (kind, name), a in sorted(agg.items(), key=lambda kv: -kv[1]["ns"]):
-        print("| %s | %s | %.1f | %.2f | %.1f%% | %.2f |" % (name, kind, len(a["ids"]) / steps, a["ns"] / 1e3 / steps,
-                                                         100 * a["ns"] / total_ns, (a["rd"] + a["wr"]) / 1e6 / steps))
-        k = kinds.setdefault(kind, {"ns": 0.0, "bytes": 0.0})
-        k["ns"] += a["ns"]
-        k["bytes"] += a["rd"] + a["wr"]
-    out = {kind: {"workload": WORKLOAD, "dram_bytes_per_step": v["bytes"] / steps,
-                  "device_us_per_step": v["ns"] / 1e3 / steps, "share": v["ns"] / total_ns,
-                  "source_sha256_16": source_digest(kind),
-                  "note": "ncu dram__bytes_read.sum + dram__bytes_write.sum summed over the kind's launches of "
-                          "one step, each launch replayed with caches flushed"}
-           for kind, v in kinds.items()}
-    with open(os.path.join(ROOT, "profiles", "dram_traffic.json"), "w") as f:
-        json.dump(out, f, indent=1, sort_keys=True)
+        print("| %s | %s | %.1f | %.2f | %.1f%% |" % (name, kind, len(a["ids"]) / steps, a["ns"] / 1e3 / steps,
+                                                      100 * a["ns"] / total_ns))
 
 
 # ---------------------------------------------------------------------------
@@ -483,7 +504,7 @@ def run_gpu(args):
     peak, peak_src = measured_peak()
     alg = kb[dom]
     achieved = alg / (dom_step_ms * 1e-3) / 1e9
-    traffic = ncu_traffic(dom, WORKLOAD)
+    traffic = ncu_traffic(dom, "headline")
     launches = sum(c for _, c in kinds.values())
     mb = method_bytes(n, 4, HEAD_REFINE)
     clocks = clk.summary()
@@ -563,6 +584,41 @@ def run_gpu(args):
         print(json.dumps(out), flush=True)
     if dist:
         dist.destroy_process_group()
+
+
+def quick_stage(args):
+    """Profiling aid: `args.warmup` then `args.steps` RK stages of the 128^3
+    workload (20k-marker sphere, four rotating states), the timed stages
+    inside cudaProfilerStart/Stop (`ncu --profile-from-start off`)."""
+    import torch
+    import paper_2406_19920_gb300 as ibm
+    g = workload_grid()
+    (u, v, w), X0, dV = make_inputs(g)
+    f32 = torch.float32
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to("cuda", f32)
+    plan = ibm.ibm_plan_create(NX, NY, NZ, g[3:], ibm.IBM_FP32_REFINED, 1)
+    states, keep = [], []
+    for _ in range(N_STATES):
+        f = [dev(u), dev(v), dev(w)] + [torch.zeros((NY, NZ, NX), dtype=f32, device="cuda") for _ in range(4)]
+        states.append(ibm.ibm_state(*[t.data_ptr() for t in f], 0.0))
+        keep.append(f)
+    X0d, dVd = dev(X0), dev(dV)
+    X = torch.empty((N_MARKERS, 3), dtype=f32, device="cuda")
+    Ud, F = torch.empty_like(X), torch.empty_like(X)
+    mk = ibm.ibm_markers(N_MARKERS, X0d.data_ptr(), dVd.data_ptr(), X.data_ptr(), Ud.data_ptr(), F.data_ptr(),
+                         ibm.IBM_MOTION_TRANSLATE, (ctypes.c_double * 4)(0.1, 0.0, 0.0, 0.0))
+    for i in range(args.warmup):
+        ibm.ibm_substep(plan, states[i % N_STATES], (i // N_STATES) % 3 + 1, DT, NU, mk)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStart()
+    for i in range(args.steps):
+        j = args.warmup + i
+        ibm.ibm_substep(plan, states[j % N_STATES], (j // N_STATES) % 3 + 1, DT, NU, mk)
+    torch.cuda.synchronize()
+    torch.cuda.cudart().cudaProfilerStop()
+    ibm.ibm_plan_check(plan)
+    ibm.ibm_plan_destroy(plan)
+    print(json.dumps({"quick_stage": True, "steps": args.steps}))
 
 
 def stage_128(ibm, torch, args, oracle=True):
@@ -651,7 +707,7 @@ def stage_128(ibm, torch, args, oracle=True):
     return {"workload": STAGE_WORKLOAD, "ms_per_stage": ms, "grid_pts_per_s": NX * NY * NZ / (ms * 1e-3),
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "peak_source": peak_src, "algorithmic_bytes": alg,
-                         "ms_per_step": dom_step_ms, "traffic": ncu_traffic(dom, STAGE_WORKLOAD)},
+                         "ms_per_step": dom_step_ms, "traffic": ncu_traffic(dom, "stage")},
             "kernels_ms_per_stage": {k: kinds[k][0] / steps for k in kinds},
             "launches_per_stage": {k: kinds[k][1] / steps for k in kinds},
             "phase_ms_one_stage": {k: v for k, v in info["phase_ms"].items() if v > 0},
@@ -1424,12 +1480,19 @@ def main():
                     help="duration of the FP32-refined serving trace (the workload's 60 s by default)")
     ap.add_argument("--oracle-time", metavar="NPY", help=argparse.SUPPRESS)
     ap.add_argument("--reps", type=int, default=3, help=argparse.SUPPRESS)
+    ap.add_argument("--quick-stage", action="store_true",
+                    help="profiling aid: --warmup then --steps RK stages of the 128^3 workload, the timed stages the "
+                         "profiler region")
     ap.add_argument("--quick", action="store_true",
                     help="warm-up and timed steps only (no tracing pass, e2e, Poisson comparison or CPU baseline); "
                          "the timed steps are the profiler region, for ncu launch lists")
     ap.add_argument("--ncu-summary", metavar="CSV",
-                    help="summarise an ncu --csv launch list of `--quick --steps K` (pass the same --steps): "
-                         "writes profiles/dram_traffic.json, prints a markdown table")
+                    help="summarise an ncu --csv launch list (gpu__time_duration.sum) of `--quick --steps K` (pass "
+                         "the same --steps): prints a markdown table")
+    ap.add_argument("--ncu-counters", metavar="CSV",
+                    help="record the DRAM bytes of a single-kernel ncu capture (raw-page CSV) of `--solve 256` in "
+                         "profiles/dram_traffic.json (with --launches-per-step)")
+    ap.add_argument("--launches-per-step", type=int, default=2, help=argparse.SUPPRESS)
     ap.add_argument("--solve", type=int, metavar="N",
                     help="profiling aid: two refined FP32 Poisson solves on an N^3 grid (the first one warms up), "
                          "then exit; `ncu -s <launches of one solve>` captures the second")
@@ -1447,8 +1510,14 @@ def main():
     if args.ncu_summary:
         ncu_summary(args.ncu_summary, args.steps)
         return
+    if args.ncu_counters:
+        ncu_counters(args.ncu_counters, "headline", args.launches_per_step)
+        return
     if args.solve:
         solve_twice(args.solve, args.plane_mode)
+        return
+    if args.quick_stage:
+        quick_stage(args)
         return
     if args.spread:
         spread_twice(args.spread, args.spread_mode)
