@@ -40,7 +40,8 @@ __device__ __forceinline__ double warp_excl_scan(double v, int lane) {
 // CTA of the pencil grid) concurrently with the other pencils.  Input
 // f_j = Re S[j][0][0] (zrhs, written by the forward transform); output
 // zsol[j] (read by the inverse transform).  zs is shared scratch of ny doubles.
-// zsol may alias zrhs (zrhs is read only before zsol is written).
+// zrhs, zsol and zs may be one array: each lane reads and writes only its
+// own rows, zrhs before zs and zs before zsol.
 __device__ __forceinline__ void zero_mode_fp64(const double *zrhs, double *zsol, double *zs, int ny,
                                double inv_ny, double hy2, double inv_nxnz, double *mean_out) {
   const int lane = threadIdx.x & 31;

@@ -231,8 +231,9 @@ template <int NZ, int C> struct SlabCfg {
   static constexpr size_t o_tw = o_x + al(xbytes);
   static constexpr size_t o_cf = o_tw + al((size_t)NZ * 8);
   static constexpr size_t o_cb = o_cf + al((size_t)4 * NZ * 4);
-  static constexpr size_t o_zm = o_cb + al((size_t)3 * NZ * 4);
-  static constexpr size_t o_bar = o_zm + al((size_t)2 * NY * 8);
+  static constexpr size_t o_xm = o_cb + al((size_t)3 * NZ * 4);
+  static constexpr size_t o_zm = o_xm + al((size_t)NZ * 8);
+  static constexpr size_t o_bar = o_zm + al((size_t)NY * 8);
   static constexpr size_t bytes = o_bar + 128;
   static_assert(W * N1 == THREADS, "one row per N1 threads in step 1");
   static_assert((R / 2) % W == 0, "each half of the rows is whole transform rounds");
@@ -281,15 +282,17 @@ __device__ __forceinline__ void zfft_rows(float2 *rows, float2 *X, const float2 
 }
 
 // Persistent: cluster q of the grid's Q clusters takes the slabs kx = q,
-// q + Q, ...  Between slabs a CTA waits until the bulk store of the previous
-// slab has read its shared memory, then loads the next one; the two CTAs an
-// SM holds belong to different clusters and drift out of phase, so one
-// computes while the other moves data.  Every peer reads this CTA's forward
-// carries (cf), its meeting row and its zero-mode rows only between the
-// slab's two cluster barriers, and its back-substitution carries (cb, with
-// the segment's product of w) only between the second barrier and the next
-// slab's first, before which this CTA rewrites neither: one copy of each
-// suffices.
+// q + Q, ...; while it works on one slab the next one is prefetched into L2.
+// Between slabs a CTA waits until the bulk store of the previous slab has
+// read its shared memory, then loads the next one.  Every peer reads this
+// CTA's forward carries (cf) and its zero-mode rows only between the slab's
+// two cluster barriers, and its back-substitution carries (cb, with the
+// segment's product of w) and the meeting row's solution (xmb, CTA C/2)
+// only between the second barrier and the next slab's first, before which
+// this CTA rewrites neither: one copy of each suffices.  The carries cross
+// the cluster as few times as the sweep needs: each CTA reads those of the
+// segments before its own in its half, and only CTA C/2 reads both halves'
+// (for the meeting row).
 template <int NZ, int C>
 __global__ void __cluster_dims__(C, 1, 1) __launch_bounds__(NZ, (NZ >= 256 ? 2 : 3))
 k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx, const float *__restrict__ lamz,
@@ -307,8 +310,9 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
   float2 *tw2 = reinterpret_cast<float2 *>(smem + Cfg::o_tw);
   float *cf = reinterpret_cast<float *>(smem + Cfg::o_cf);  // [4][NZ] yhat_end.x, .y, prod w, q of the last row
   float *cb = reinterpret_cast<float *>(smem + Cfg::o_cb);  // [3][NZ] xhat at the segment's first row, prod w
-  double *zr = reinterpret_cast<double *>(smem + Cfg::o_zm);  // zero mode (CTA 0 of the kx = 0 cluster): rhs and
-  double *zw = zr + NY;                                       // then solution; scratch
+  double *zr = reinterpret_cast<double *>(smem + Cfg::o_zm);  // zero mode (CTA 0 of the kx = 0 cluster): rhs,
+                                                              // scratch, then solution
+  float2 *xmb = reinterpret_cast<float2 *>(smem + Cfg::o_xm);  // [NZ] meeting row solution (CTA C/2)
   uint64_t *bar = reinterpret_cast<uint64_t *>(smem + Cfg::o_bar);
 
   // plan constants before the grid-dependency wait
@@ -352,6 +356,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
       bulk_g2s(slab, gslab, kHalf, &bar[0]);
       mbar_arrive_expect_tx(&bar[1], kHalf);
       bulk_g2s(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1]);
+      if (kx + Q < pp.P) bulk_prefetch_l2(gslab + (size_t)Q * NY * NZ, 2 * kHalf);  // the next slab, into L2
     }
     const float g = (float)pp.g_add + (float)pp.g_mul * (lamx[kx] + lz);
     // forward z transforms
@@ -386,30 +391,36 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     cf[3 * NZ + kz] = qlast;
     cluster_sync_all();  // #1: every CTA has started; every segment's carries and row m are visible
 
-    // carry into my segment and the last y of both halves
-    float2 c = make_float2(0.f, 0.f), yT = c, yB = c;
+    // the carry into my segment: the segments before it in its half of the sweep
+    float2 c = make_float2(0.f, 0.f);
 #pragma unroll
     for (int s2 = 0; s2 < C; ++s2) {
+      if (s2 >= seg || s2 < (top ? 0 : Lh)) continue;
       const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
-      if (s2 == seg) c = s2 < Lh ? yT : yB;
-      const float pw = pcf[2 * NZ + kz], ax = pcf[kz], ay = pcf[NZ + kz];
-      if (s2 < Lh) {
-        yT.x = fmaf(pw, yT.x, ax);
-        yT.y = fmaf(pw, yT.y, ay);
-      } else {
-        yB.x = fmaf(pw, yB.x, ax);
-        yB.y = fmaf(pw, yB.y, ay);
-      }
+      const float pw = pcf[2 * NZ + kz];
+      c.x = fmaf(pw, c.x, pcf[kz]);
+      c.y = fmaf(pw, c.y, pcf[NZ + kz]);
     }
-    // meeting row: (g + a q^T + a q^B) x_m = sgn f_m + a (y^T_{m-1} + y^B_{m+1})
-    const float qT = cluster.map_shared_rank(cf, Lh - 1)[3 * NZ + kz];
-    const float qB = cluster.map_shared_rank(cf, Lh)[3 * NZ + kz];
-    const float2 fm = cluster.map_shared_rank(slab, Lh)[kz];
-    float2 xm;
-    {
-      const float rm = rcp<float>(g + a * qT + a * qB);
+    // the meeting row, solved by CTA C/2 (its sweep ends next to it, and it
+    // holds the row) and read by the others after the second barrier:
+    // (g + a q^T + a q^B) x_m = sgn f_m + a (y^T_{m-1} + y^B_{m+1})
+    float2 xm = make_float2(0.f, 0.f);
+    if (rank == Lh) {
+      float2 yT = make_float2(0.f, 0.f);
+#pragma unroll
+      for (int s2 = 0; s2 < Lh; ++s2) {
+        const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
+        const float pw = pcf[2 * NZ + kz];
+        yT.x = fmaf(pw, yT.x, pcf[kz]);
+        yT.y = fmaf(pw, yT.y, pcf[NZ + kz]);
+      }
+      const float qT = cluster.map_shared_rank(cf, Lh - 1)[3 * NZ + kz];
+      const float2 yB = make_float2(fmaf(prod, c.x, y.x), fmaf(prod, c.y, y.y));
+      const float2 fm = slab[kz];
+      const float rm = rcp<float>(g + a * qT + a * qlast);
       xm.x = (sgn * fm.x + a * (yT.x + yB.x)) * rm;
       xm.y = (sgn * fm.y + a * (yT.y + yB.y)) * rm;
+      xmb[kz] = xm;
     }
     const float wconst = a * rcp<float>(a + ep);
     float2 x;
@@ -425,12 +436,12 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     if (zm && rank == 0 && tid < 32) {
       for (int j = tid; j < NY; j += 32) zr[j] = (double)cluster.map_shared_rank(slab, j / R)[(j % R) * NZ].x;
       __syncwarp();
-      zero_mode_fp64(zr, zr, zw, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);  // solution over the rhs
+      zero_mode_fp64(zr, zr, zr, NY, pp.inv_ny, pp.hy2, pp.inv_nxnz, mean_out);  // solution over the rhs
     }
     cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
 
     // x after my last row (towards the meeting row), then my rows stored
-    c = xm;
+    c = rank == Lh ? xm : cluster.map_shared_rank(xmb, Lh)[kz];
 #pragma unroll
     for (int s2 = C - 1; s2 >= 0; --s2) {
       if (s2 <= seg || s2 >= (top ? Lh : C)) continue;
