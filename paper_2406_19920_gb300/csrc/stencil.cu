@@ -4,10 +4,10 @@
 // Sec. 2.1 with periodic x, z and the ghost rule of the field's wall kind
 // along y (Appendix B; periodic for the triply periodic branch).  Poisson:
 // sigma = 0, tau = 1; Helmholtz (I - c L):
-// sigma = 1, tau = -c.  In FP32 the stencil is evaluated in float-float
-// arithmetic (exact second differences of the stored FP32 values, 1/h^2 and
-// tau carried as hi + lo pairs) and rounded once to FP32; a plain FP32
-// stencil would limit iterative refinement to ~eps32 * cond.  Optionally the
+// sigma = 1, tau = -c.  In FP32 the second differences of the stored values
+// are taken exactly (hi + lo) and the other terms, all O(|b|), are summed in
+// FP32 (residual_point below): a plain FP32 stencil would lose the residual
+// in the cancelling second differences.  Optionally the
 // FP64 sums of r^2, b^2, r and b are accumulated for the relative residual.
 // An optional device scalar is subtracted from b first (the Poisson
 // right-hand side's removed mean), so the residual is that of the compatible
@@ -63,24 +63,18 @@ __device__ __forceinline__ void block_accumulate(double r2, double b2, double r1
   }
 }
 
-// FP32 residual.  The exact value
+// FP32 residual.  The value
 //   r = (b - m) - sigma x0 + sum_a K_a D_a,   K_a = -tau c_a,
-// D_a = x(+1) + x(-1) - 2 x0 the second difference along axis a, is
-// evaluated as if in twice the working precision and rounded once:
-//   * D_a exactly as hi + lo (two error-free sums of FP32 values);
-//   * K_a D_a as an error-free product of the high parts plus the cross
-//     terms in FMAs (K_a is the FP64 coefficient split into hi + lo);
-//   * all high parts summed by a chain of error-free sums, all low parts and
-//     sum errors added in FP32 (cascaded summation, Ogita, Rump & Oishi
-//     2005), the two totals added last.
-__device__ __forceinline__ void sum_into(float &S, float &E, float h) {
-  const ff t = two_sum(S, h);
-  S = t.hi;
-  E += t.lo;
-}
-
-// One point: returns r and sets bt to the compatible right-hand side b - m
-// (for the norms).  SIGMA: the Helmholtz sigma x0 term.
+// D_a = x(+1) + x(-1) - 2 x0 the second difference along axis a.  The
+// second differences are where a plain FP32 stencil loses the residual:
+// the stored values are O(|x|) and cancel to O(h^2 |x''|).  They are taken
+// exactly, as hi + lo (two error-free sums of FP32 values).  Every other
+// term is O(|b|) and is summed in FP32 (K_a as its FP64 value split into
+// hi + lo, the small products first): a few FP32 roundings of |b|, against
+// a residual of an FP32 solution that is 1e-5 .. 1e-3 of |b| (its rounding
+// errors are grid-scale, which L_h amplifies by ~1/h^2), so the correction
+// is accurate to better than 1 % and the refined solution reaches the FP32
+// rounding of its storage.
 template <bool SIGMA>
 __device__ __forceinline__ float residual_point(const ResidualArgs &A, float bv, float2 m, float x0, float xe, float xw,
                                                 float xn, float xs, float xu, float xd, float &bt) {
@@ -92,20 +86,15 @@ __device__ __forceinline__ float residual_point(const ResidualArgs &A, float bv,
   const float Dzh = t.hi, Dzl = t.lo + s.lo;
   s = two_sum(xu, xd); t = two_sum(s.hi, x2);
   const float Dyh = t.hi, Dyl = t.lo + s.lo;
-  // (b - m) - sigma x0 + sum_a K_a D_a, cascaded
-  const ff bm = two_sum(bv, -m.x);
-  float S = bm.hi, E = bm.lo - m.y;
-  bt = bm.hi + E;
-  if (SIGMA) sum_into(S, E, -A.sigma * x0);
-  ff p = two_prod(A.kx.hi, Dxh);
-  sum_into(S, E, p.hi);
-  E += fmaf(A.kx.hi, Dxl, fmaf(A.kx.lo, Dxh, p.lo));
-  p = two_prod(A.kz.hi, Dzh);
-  sum_into(S, E, p.hi);
-  E += fmaf(A.kz.hi, Dzl, fmaf(A.kz.lo, Dzh, p.lo));
-  p = two_prod(A.ky.hi, Dyh);
-  sum_into(S, E, p.hi);
-  E += fmaf(A.ky.hi, Dyl, fmaf(A.ky.lo, Dyh, p.lo));
+  const float bm = (bv - m.x) - m.y;
+  bt = bm;
+  float E = fmaf(A.kx.hi, Dxl, A.kx.lo * Dxh);
+  E = fmaf(A.kz.hi, Dzl, fmaf(A.kz.lo, Dzh, E));
+  E = fmaf(A.ky.hi, Dyl, fmaf(A.ky.lo, Dyh, E));
+  float S = SIGMA ? fmaf(-A.sigma, x0, bm) : bm;
+  S = fmaf(A.kx.hi, Dxh, S);
+  S = fmaf(A.kz.hi, Dzh, S);
+  S = fmaf(A.ky.hi, Dyh, S);
   return S + E;
 }
 
