@@ -238,22 +238,38 @@ def ncu_counters(csv_path, which, launches_per_step):
         json.dump(out, f, indent=1, sort_keys=True)
 
 
-def solve_kind_bytes(n, esz=4, refine=HEAD_REFINE):
+def solve_kind_bytes(n, esz=4, refine=HEAD_REFINE, fused=True):
     """Compulsory HBM bytes per Poisson solve on an n^3 grid, per kernel kind.
 
     pts = n^3 real points; spec = n n (n/2+1) complex entries; a solve with
     `refine` refinement steps transforms 1 + refine right-hand sides.
     forward: read field + write spectrum per transform; pencil: read + write
     spectrum; inverse: read spectrum + write field, plus the read of the
-    field the correction is added to; residual: read b and x, write r.  The
-    spectrum round trip between split x and z passes is not counted (it is
-    not compulsory: a plane kernel avoids it)."""
+    field the correction is added to; residual: read b and x, write r, or,
+    `fused` (the slab path), read b and x and write the correction's
+    spectrum (its forward x rows run in the same pass).  The spectrum round
+    trip between split x and z passes is not counted (it is not compulsory:
+    a plane kernel avoids it)."""
     pts = n ** 3
     spec = n * n * (n // 2 + 1)
     cs = 2 * esz
     sets = 1 + refine
-    return {"forward": sets * (pts * esz + spec * cs), "pencil": sets * 2 * spec * cs,
-            "inverse": sets * (spec * cs + pts * esz) + refine * pts * esz, "residual": refine * 3 * pts * esz}
+    fwd_sets = 1 if fused else sets
+    res = refine * (2 * pts * esz + spec * cs) if fused else refine * 3 * pts * esz
+    return {"forward": fwd_sets * (pts * esz + spec * cs), "pencil": sets * 2 * spec * cs,
+            "inverse": sets * (spec * cs + pts * esz) + refine * pts * esz, "residual": res}
+
+
+def slab_path(n, precision_fp32, bc=None, env=None):
+    """Whether an n^3 plan takes the fused slab path (the library's default:
+    FP32 wall-bounded 256 x 256 (y, z) slabs; IBM_SLAB forces it on or off)."""
+    flag = (env or {}).get("IBM_SLAB", os.environ.get("IBM_SLAB"))
+    walls = bc is None or bc == 1  # IBM_BC_PXZ_WALL_Y
+    if not precision_fp32 or not walls or n not in (64, 128, 256):
+        return False
+    if flag is not None:
+        return flag == "1"
+    return n == 256
 
 
 def algorithmic_bytes(kind, esz=4):
@@ -496,7 +512,8 @@ def run_gpu(args):
     torch.cuda.empty_cache()
 
     # ---- roofline: the dominant kernel kind, and the whole solve ----
-    kb = solve_kind_bytes(n)
+    fused = slab_path(n, True)
+    kb = solve_kind_bytes(n, fused=fused)
     kinds = {k: v for k, v in prof.items() if v[1] > 0}
     dom = max(kinds, key=lambda k: kinds[k][0])
     dom_ms, dom_launches = kinds[dom]
@@ -506,7 +523,7 @@ def run_gpu(args):
     achieved = alg / (dom_step_ms * 1e-3) / 1e9
     traffic = ncu_traffic(dom, "headline")
     launches = sum(c for _, c in kinds.values())
-    mb = method_bytes(n, 4, HEAD_REFINE)
+    mb = method_bytes(n, 4, HEAD_REFINE, fused)
     clocks = clk.summary()
     cfg = dict(CONFIG, parallelism="replicas" if ws > 1 else "1 GPU")
     out = {
@@ -538,8 +555,12 @@ def run_gpu(args):
                            "peak": peak, "unit": "GB/s", "frac": mb / (ms_step * 1e-3) / 1e9 / peak,
                            "peak_source": peak_src, "target_frac": 0.6,
                            "method": "forward, pencil and inverse passes each read and write the field once "
-                                     "(24 B/pt FP32) per transform set; the refinement step adds the residual "
-                                     "pass (12 B/pt), a second set and the read of the corrected field (4 B/pt)"},
+                                     "(24 B/pt FP32) per transform set; the refinement step adds "
+                                     + ("the residual fused with the correction's forward x rows (reads b and x, "
+                                        "writes the spectrum: 12 B/pt), its pencil and inverse passes and the read "
+                                        "of the corrected field (4 B/pt)" if fused else
+                                        "the residual pass (12 B/pt), a second set and the read of the corrected "
+                                        "field (4 B/pt)")},
         "oracle_error": oracle_error,
         "info": {k: info[k] for k in ("rel_residual", "removed_mean", "refine_iters")},
         "phase_ms_per_solve": {k: v for k, v in info["phase_ms"].items() if v > 0},
@@ -715,15 +736,19 @@ def stage_128(ibm, torch, args, oracle=True):
             "stage_info": {k: info[k] for k in ("div_max", "div_before", "removed_mean")}}
 
 
-def method_bytes(n, precision_bytes, refine):
+def method_bytes(n, precision_bytes, refine, fused=False):
     """Compulsory HBM bytes of one Poisson solve on an n^3 grid: forward
     (read field, write spectrum), pencil (read + write spectrum), inverse
     (read spectrum, write field); a refinement step adds the residual (read
-    b and x, write r), a second solve and the read of the updated field."""
+    b and x, write r), a second solve and the read of the updated field.
+    `fused` (the slab path): the residual and the correction's forward x
+    rows are one pass (read b and x, write the spectrum)."""
     pts = n ** 3
     spec = n * n * (n // 2 + 1)
     s = precision_bytes
     solve = pts * s + 2 * spec * s + 2 * 2 * spec * s + 2 * spec * s + pts * s
+    if fused:
+        return solve + refine * (2 * pts * s + 2 * spec * s + 2 * 2 * spec * s + 2 * spec * s + 2 * pts * s)
     return solve + refine * (3 * pts * s + solve + pts * s)
 
 
@@ -767,7 +792,8 @@ def poisson_compare(ibm, torch, n, variants, nb=16, K=40, bc=None, oracle=False)
         lat = [evs[i].elapsed_time(evs[i + 1]) for i in range(K)]
         ms = evs[0].elapsed_time(evs[-1]) / K
         outs[name] = phi[0].double().cpu().numpy()
-        mb = method_bytes(n, 4 if dt == torch.float32 else 8, ref if dt == torch.float32 else 0)
+        fused = dt == torch.float32 and ref > 0 and slab_path(n, True, bc, env)
+        mb = method_bytes(n, 4 if dt == torch.float32 else 8, ref if dt == torch.float32 else 0, fused)
         res[name] = {"solves_per_s": 1e3 / ms, "grid_pts_per_s": n ** 3 * 1e3 / ms, "ms": ms,
                      "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
                      "method_bytes": mb,

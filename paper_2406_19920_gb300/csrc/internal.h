@@ -224,6 +224,14 @@ struct StencilCoef {
 template <typename T>
 cudaError_t launch_residual(int nx, int ny, int nz, const StencilCoef &c, const T *b, const T *x, T *r,
                             const double *boff, double *norms, cudaStream_t st);
+// The slab path's refinement pass (slab.cu): the FP32 residual r = b - A x
+// of the coefficients c (wall kinds IBM_FIELD_CELL_NEUMANN and
+// IBM_FIELD_CELL_DIRICHLET) and its forward x rows into the kx-major spectrum
+// S, as launch_residual followed by launch_slab_solve phase 0 but without
+// storing r.  boff / norms as for launch_residual.
+cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, int nz, const float *b, const float *x,
+                                         float2 *S, const float2 *twx, const double *boff, double *norms,
+                                         cudaStream_t st);
 // dst plane jlo += clo g_lo, plane jhi += chi g_hi ([nz][nx] planes; NULL skips a side).
 template <typename T>
 cudaError_t launch_wall_rhs(int nx, int nz, T *dst, int jlo, int jhi, const T *glo, const T *ghi, double clo,

@@ -191,25 +191,29 @@ bool default_use_slab(int precision, int bc, int nx, int ny, int nz) {
 
 // The fused slab path: three passes, each reading and writing the field once.
 static int solve_once_slab(ibm_plan_s *p, const PencilParams &pp, const float *in, float *out, const float *addend,
-                           double *mean_out, cudaStream_t st) {
+                           double *mean_out, cudaStream_t st, int first_phase = 0) {
   float2 *S = static_cast<float2 *>(p->S);
   const float2 *twx = static_cast<const float2 *>(p->twx), *twz = static_cast<const float2 *>(p->twz);
   const float *lamx = static_cast<const float *>(p->lamx), *lamz = static_cast<const float *>(p->lamz);
   const float scale = (float)(1.0 / ((double)p->nx * p->nz));
   static const int kinds[3] = {IBM_K_FORWARD, IBM_K_PENCIL, IBM_K_INVERSE};
-  for (int phase = 0; phase < 3; ++phase) {
+  for (int phase = first_phase; phase < 3; ++phase) {
     ProfScope ps(p, kinds[phase], st);
     IBM_CUDA_TRY(launch_slab_solve(pp, p->nx, in, S, out, addend, twx, twz, lamx, lamz, mean_out, scale, st, phase));
   }
   return IBM_OK;
 }
 
+// FP32 single-field solves of the plan's slab kinds take the slab path.
+static bool slab_applies(const ibm_plan_s *p, const PencilParams &pp) {
+  return p->use_slab && pp.j0 == 0 && pp.nb == 1 && !pp.periodic;
+}
+
 template <typename T>
 static int solve_once(ibm_plan_s *p, const PencilParams &pp, const T *in, T *out, const T *addend,
                       double *mean_out, cudaStream_t st) {
   if constexpr (sizeof(T) == 4) {
-    if (p->use_slab && pp.j0 == 0 && pp.nb == 1 && !pp.periodic)
-      return solve_once_slab(p, pp, in, out, addend, mean_out, st);
+    if (slab_applies(p, pp)) return solve_once_slab(p, pp, in, out, addend, mean_out, st);
   }
   TransformGeom gf = geom_of(p), gi = geom_of(p);
   if (pp.zero_mode) {
@@ -304,6 +308,19 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
   if (rc) return rc;
   T *r = static_cast<T *>(p->work);
   for (int it = 0; it < iters; ++it) {
+    if constexpr (sizeof(T) == 4) {
+      if (slab_applies(p, pp)) {  // the residual goes straight into the correction's x rows
+        {
+          ProfScope ps(p, IBM_K_RESIDUAL, st);
+          IBM_CUDA_TRY(launch_slab_residual_forward(sc, p->nx, p->ny, p->nz, b, out, static_cast<float2 *>(p->S),
+                                                    static_cast<const float2 *>(p->twx),
+                                                    kind == 0 ? p->dsc : nullptr, nullptr, st));
+        }
+        rc = solve_once_slab(p, pp, nullptr, out, out, nullptr, st, 1);
+        if (rc) return rc;
+        continue;
+      }
+    }
     {
       ProfScope ps(p, IBM_K_RESIDUAL, st);
       IBM_CUDA_TRY(launch_residual<T>(p->nx, p->ny, p->nz, sc, b, out, r, kind == 0 ? p->dsc : nullptr, nullptr,

@@ -28,6 +28,7 @@
 #include "fft2.cuh"
 #include "internal.h"
 #include "seg.cuh"
+#include "stencil.cuh"
 #include "tma.cuh"
 
 namespace cg = cooperative_groups;
@@ -64,30 +65,24 @@ template <int N> struct RowT {
   static constexpr size_t mx(size_t a, size_t b) { return a > b ? a : b; }
   static constexpr size_t stage_i = mx((size_t)P * 2 * RP * 8, (size_t)2 * RP * POUT * 4);
   static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8;
+  static constexpr size_t smem_r = smem_f + (size_t)2 * RP * (N + 8) * 4;  // + the residual tile
   static constexpr size_t smem_i = (size_t)N * 8 + (size_t)RP * QI * 8 + stage_i + 16;
 };
 
+// Steps 1 - 3 of the forward x rows of the CTA's np row pairs: real rows
+// 2 p and 2 p + 1 at src + 2 p pitch and src + (2 p + 1) pitch (global
+// memory or a shared tile), spectra to S from pair pair0 on.
 template <int N>
-__global__ void __launch_bounds__(kRowT)
-k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 *__restrict__ tw, int npairs,
-             int rows, float in_scale, int *err) {
+__device__ __forceinline__ void rows_fwd_steps(const float *src, int pitch, float in_scale, float2 *__restrict__ S,
+                                               int pair0, int np, int rows, const float2 *tw2, float2 *X) {
   using Cfg = RowT<N>;
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1;
-  (void)err;  // no waits: every access is a plain coalesced load or store
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *X = tw2 + N;  // [N1][k2][p]
-  load_step_twiddles<float, N>(tw2, tw);
-  pdl_wait();  // the input field is the predecessor's output
-  const int pair0 = blockIdx.x * RP;
-  const int np = min(RP, npairs - pair0);
-  __syncthreads();
   for (int job = threadIdx.x; job < np * N1; job += kRowT) {
     const int p = job / N1, n1 = job - p * N1;
-    const float *a = in + (size_t)(pair0 + p) * 2 * N;
+    const float *a = src + (size_t)(2 * p) * pitch;
     float2 v[N2];
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[N + n1 + N1 * n2] * in_scale);
+    for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[pitch + n1 + N1 * n2] * in_scale);
     reg_dft<false, N2>(v);
     float2 *x = X + n1 * QF + p;
     x[0] = v[0];
@@ -128,6 +123,60 @@ k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 
       }
     }
   }
+}
+
+template <int N>
+__global__ void __launch_bounds__(kRowT)
+k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 *__restrict__ tw, int npairs,
+             int rows, float in_scale, int *err) {
+  using Cfg = RowT<N>;
+  (void)err;  // no waits: every access is a plain coalesced load or store
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
+  float2 *X = tw2 + N;  // [N1][k2][p]
+  load_step_twiddles<float, N>(tw2, tw);
+  pdl_wait();  // the input field is the predecessor's output
+  const int pair0 = blockIdx.x * Cfg::RP;
+  const int np = min(Cfg::RP, npairs - pair0);
+  __syncthreads();
+  rows_fwd_steps<N>(in + (size_t)pair0 * 2 * N, N, in_scale, S, pair0, np, rows, tw2, X);
+}
+
+// The refinement's correction right-hand side and its forward x rows in one
+// pass: the residual r = b - A x (residual4, the slab path's wall kinds) of
+// the CTA's 2 RP rows into a shared tile (pitch N + 8 floats: the two rows a
+// warp reads in step 1 fall on different banks), then the forward x rows of
+// the tile.  r itself never reaches global memory.  norms: the FP64 sums of
+// the residual pass, when wanted.
+template <int N, int BC, bool SIGMA>
+__global__ void __launch_bounds__(kRowT)
+k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float2 *__restrict__ S,
+                 const float2 *__restrict__ tw, int npairs, int rows, double *norms) {
+  using Cfg = RowT<N>;
+  constexpr int TP = N + 8, Q4 = N / 4;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
+  float2 *X = tw2 + N;                                            // [N1][k2][p]
+  float *tile = reinterpret_cast<float *>(X + Cfg::N1 * Cfg::QF);  // [2 RP][TP]
+  load_step_twiddles<float, N>(tw2, tw);
+  pdl_wait();  // x is the predecessor's output
+  const int pair0 = blockIdx.x * Cfg::RP;
+  const int np = min(Cfg::RP, npairs - pair0);
+  const int row0 = 2 * pair0;
+  float2 m = make_float2(0.f, 0.f);
+  if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
+  double r2 = 0.0, b2 = 0.0, r1 = 0.0, b1 = 0.0;
+  for (int job = threadIdx.x; job < 2 * np * Q4; job += kRowT) {
+    const int rr = job / Q4, i0 = 4 * (job - rr * Q4);
+    const int row = row0 + rr, j = row / A.nz, k = row - j * A.nz;
+    float4 bt;
+    const float4 res = residual4<BC, SIGMA>(A, b, x, j, k, i0, m, bt);
+    if (norms) residual4_norms(res, bt, r2, b2, r1, b1);
+    *reinterpret_cast<float4 *>(tile + rr * TP + i0) = res;
+  }
+  if (norms) block_accumulate(r2, b2, r1, b1, norms);
+  __syncthreads();
+  rows_fwd_steps<N>(tile, TP, 1.0f, S, pair0, np, rows, tw2, X);
 }
 
 template <int N>
@@ -518,6 +567,43 @@ static cudaError_t launch_slab_kernel(const PencilParams &pp, float2 *S, const f
   IBM_KTRY(launch_pdl(k_slab<NZ, C>, dim3(Q * C), dim3(Cfg::THREADS), Cfg::bytes, st, S, twz, lamx, lamz, pp,
                       mean_out));
   return cudaGetLastError();
+}
+
+template <int N, int B, bool SG>
+static cudaError_t launch_rows_fwd_res(const ResidualArgs &A, const float *b, const float *x, float2 *S,
+                                       const float2 *twx, int npairs, int rows, double *norms, cudaStream_t st) {
+  constexpr auto kern = k_rows_fwd_res_t<N, B, SG>;
+  {  // its own size: the kernel also has static shared memory (the norm sums)
+    static std::once_flag once;
+    static cudaError_t err = cudaSuccess;
+    std::call_once(once, [] {
+      err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RowT<N>::smem_r);
+    });
+    IBM_KTRY(err);
+  }
+  IBM_KTRY(launch_pdl(kern, dim3(ceil_div(npairs, RowT<N>::RP)), dim3(kRowT), RowT<N>::smem_r, st, A, b, x, S, twx,
+                      npairs, rows, norms));
+  return cudaGetLastError();
+}
+
+cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, int nz, const float *b, const float *x,
+                                         float2 *S, const float2 *twx, const double *boff, double *norms,
+                                         cudaStream_t st) {
+  if (nx % 4 != 0 || ((uintptr_t)b | (uintptr_t)x) & 15u) return cudaErrorInvalidValue;
+  if (c.bc != BC_NEUMANN && c.bc != BC_CELL_DIRICHLET) return cudaErrorInvalidValue;  // the slab path's kinds
+  const ResidualArgs A = make_args(nx, ny, nz, c, boff);
+  const bool sg = c.sigma != 0.0, neu = c.bc == BC_NEUMANN;
+  const int npairs = ny * nz / 2, rows = ny * nz;
+#define X(N)                                                                                                    \
+  if (nx == N) {                                                                                                \
+    if (neu) return sg ? launch_rows_fwd_res<N, BC_NEUMANN, true>(A, b, x, S, twx, npairs, rows, norms, st)      \
+                       : launch_rows_fwd_res<N, BC_NEUMANN, false>(A, b, x, S, twx, npairs, rows, norms, st);    \
+    return sg ? launch_rows_fwd_res<N, BC_CELL_DIRICHLET, true>(A, b, x, S, twx, npairs, rows, norms, st)        \
+              : launch_rows_fwd_res<N, BC_CELL_DIRICHLET, false>(A, b, x, S, twx, npairs, rows, norms, st);      \
+  }
+  IBM_SLAB_ROWS_N(X)
+#undef X
+  return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, float2 *S, float *out,
