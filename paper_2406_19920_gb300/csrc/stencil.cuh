@@ -56,36 +56,35 @@ __device__ __forceinline__ void block_accumulate(double r2, double b2, double r1
 
 // FP32 residual.  The value
 //   r = (b - m) - sigma x0 + sum_a K_a D_a,   K_a = -tau c_a,
-// D_a = x(+1) + x(-1) - 2 x0 the second difference along axis a.  The
-// second differences are where a plain FP32 stencil loses the residual:
-// the stored values are O(|x|) and cancel to O(h^2 |x''|).  They are taken
-// exactly, as hi + lo (two error-free sums of FP32 values).  Every other
-// term is O(|b|) and is summed in FP32 (K_a as its FP64 value split into
-// hi + lo, the small products first): a few FP32 roundings of |b|, against
-// a residual of an FP32 solution that is 1e-5 .. 1e-3 of |b| (its rounding
-// errors are grid-scale, which L_h amplifies by ~1/h^2), so the correction
-// is accurate to better than 1 % and the refined solution reaches the FP32
-// rounding of its storage.
+// D_a = (x(+1) - x0) + (x(-1) - x0) the second difference along axis a.
+// The second differences are where a plain FP32 stencil loses the residual:
+// summed as x(+1) + x(-1) - 2 x0, O(|x|) values cancel to O(h^2 |x''|).  As
+// differences from the centre value they are exact wherever the neighbours
+// lie within a factor 2 of it (Sterbenz), i.e. everywhere a field is smooth
+// on the grid scale, and only their sum is rounded, relative to D itself;
+// where a field is rough, or crosses zero, the differences' rounding is
+// O(eps |b|) and O(eps |x'| / h) respectively.  Every other term is O(|b|)
+// and is summed in FP32 (K_a as its FP64 value split into hi + lo, the small
+// products first): a few FP32 roundings of |b|, against a residual of an
+// FP32 solution that is 1e-5 .. 1e-3 of |b| (its rounding errors are
+// grid-scale, which L_h amplifies by ~1/h^2).  The correction is accurate to
+// about 1 % and the refined solution reaches the FP32 rounding of its
+// storage.
 template <bool SIGMA>
 __device__ __forceinline__ float residual_point(const ResidualArgs &A, float bv, float2 m, float x0, float xe, float xw,
                                                 float xn, float xs, float xu, float xd, float &bt) {
-  const float x2 = -2.0f * x0;
-  // exact second differences D = hi + lo
-  ff s = two_sum(xe, xw), t = two_sum(s.hi, x2);
-  const float Dxh = t.hi, Dxl = t.lo + s.lo;
-  s = two_sum(xn, xs); t = two_sum(s.hi, x2);
-  const float Dzh = t.hi, Dzl = t.lo + s.lo;
-  s = two_sum(xu, xd); t = two_sum(s.hi, x2);
-  const float Dyh = t.hi, Dyl = t.lo + s.lo;
+  const float Dx = (xe - x0) + (xw - x0);
+  const float Dz = (xn - x0) + (xs - x0);
+  const float Dy = (xu - x0) + (xd - x0);
   const float bm = (bv - m.x) - m.y;
   bt = bm;
-  float E = fmaf(A.kx.hi, Dxl, A.kx.lo * Dxh);
-  E = fmaf(A.kz.hi, Dzl, fmaf(A.kz.lo, Dzh, E));
-  E = fmaf(A.ky.hi, Dyl, fmaf(A.ky.lo, Dyh, E));
+  float E = A.kx.lo * Dx;
+  E = fmaf(A.kz.lo, Dz, E);
+  E = fmaf(A.ky.lo, Dy, E);
   float S = SIGMA ? fmaf(-A.sigma, x0, bm) : bm;
-  S = fmaf(A.kx.hi, Dxh, S);
-  S = fmaf(A.kz.hi, Dzh, S);
-  S = fmaf(A.ky.hi, Dyh, S);
+  S = fmaf(A.kx.hi, Dx, S);
+  S = fmaf(A.kz.hi, Dz, S);
+  S = fmaf(A.ky.hi, Dy, S);
   return S + E;
 }
 
