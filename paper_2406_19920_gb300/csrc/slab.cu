@@ -66,7 +66,7 @@ template <int N> struct RowT {
   static constexpr size_t stage_i = mx((size_t)P * 2 * RP * 8, (size_t)2 * RP * POUT * 4);
   static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8;
   static constexpr size_t smem_r = smem_f + (size_t)2 * RP * (N + 8) * 4;  // + the residual tile
-  static constexpr size_t smem_i = (size_t)N * 8 + (size_t)RP * QI * 8 + stage_i + 16;
+  static constexpr size_t smem_i = (size_t)N * 8 + (size_t)RP * QI * 8 + 2 * stage_i + 16;  // two stages
 };
 
 // Steps 1 - 3 of the forward x rows of the CTA's np row pairs: real rows
@@ -187,74 +187,109 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QI = Cfg::QI, P = Cfg::P, POUT = Cfg::POUT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *X = tw2 + N;                                         // [p][n1][k2]
-  float4 *stin = reinterpret_cast<float4 *>(X + RP * QI);      // [P][RP] (A, B) in
-  float *stout = reinterpret_cast<float *>(stin);              // [2 RP][POUT] rows out (after step 1)
-  uint64_t *bar = reinterpret_cast<uint64_t *>(reinterpret_cast<unsigned char *>(stin) + Cfg::stage_i);
+  float2 *X = tw2 + N;                                                      // [p][n1][k2]
+  unsigned char *stage0 = reinterpret_cast<unsigned char *>(X + RP * QI);  // two stages of stage_i bytes
+  uint64_t *bar = reinterpret_cast<uint64_t *>(stage0 + 2 * Cfg::stage_i);
   load_step_twiddles<float, N>(tw2, tw);
   if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
     fence_mbar_init();
   }
-  const int pair0 = blockIdx.x * RP;
-  const int np = min(RP, npairs - pair0);
+  const int nblk = (npairs + RP - 1) / RP;
   __syncthreads();
   pdl_wait();  // the spectrum is the predecessor's output
-  if (threadIdx.x == 0) mbar_arrive_expect_tx(bar, (uint32_t)P * np * 16);
-  __syncthreads();
-  for (int k = threadIdx.x; k < P; k += kRowT)
-    bulk_g2s(stin + k * RP, S + (size_t)k * rows + 2 * (size_t)pair0, (uint32_t)np * 16, bar);
-  if (!__syncthreads_and(mbar_wait(bar, 0, err))) {
-    mbar_wait(bar, 0, nullptr);  // copies still in flight land before the CTA's memory is reused
-    return;
+  // The P runs of block blk into stage st, completion on bar[st] (thread 0
+  // arms the barrier; a barrier orders that before the copies).
+  auto arm = [&](int blk, int st) {
+    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar[st], (uint32_t)P * min(RP, npairs - blk * RP) * 16);
+  };
+  auto issue = [&](int blk, int st) {
+    float4 *stin = reinterpret_cast<float4 *>(stage0 + st * Cfg::stage_i);
+    const int pair0 = blk * RP;
+    const uint32_t nb = (uint32_t)min(RP, npairs - pair0) * 16;
+    for (int k = threadIdx.x; k < P; k += kRowT) bulk_g2s(stin + k * RP, S + (size_t)k * rows + 2 * (size_t)pair0, nb,
+                                                          &bar[st]);
+  };
+  int blk = blockIdx.x;
+  if (blk < nblk) {
+    arm(blk, 0);
+    __syncthreads();
+    issue(blk, 0);
   }
-  // step 1: Z_n = A_n + i B_n (imaginary parts of bins 0 and N/2 dropped) and
-  // its Hermitian extension for n > N/2
-  for (int job = threadIdx.x; job < np * N1; job += kRowT) {
-    const int n1 = job / np, p = job - n1 * np;
-    float2 v[N2];
+  bool loaded_next = false;  // the other stage has copies issued (and not yet waited for)
+  for (int i = 0; blk < nblk; ++i, blk += gridDim.x) {
+    const int st = i & 1;
+    const int nxt = blk + gridDim.x;
+    // the next block's runs into the other stage, once the stores of the
+    // block before this one (the other stage's output rows) have read it
+    loaded_next = false;
+    if (nxt < nblk) {
+      if (threadIdx.x < 2 * RP) bulk_wait_read();
+      arm(nxt, st ^ 1);
+      __syncthreads();
+      issue(nxt, st ^ 1);
+      loaded_next = true;
+    }
+    if (!__syncthreads_and(mbar_wait(&bar[st], (uint32_t)((i >> 1) & 1), err))) {
+      // copies still in flight land before the CTA's memory is reused
+      mbar_wait(&bar[st], (uint32_t)((i >> 1) & 1), nullptr);
+      if (loaded_next) mbar_wait(&bar[st ^ 1], (uint32_t)(((i + 1) >> 1) & 1), nullptr);
+      loaded_next = false;
+      break;
+    }
+    const float4 *stin = reinterpret_cast<const float4 *>(stage0 + st * Cfg::stage_i);  // [P][RP] (A, B) in
+    float *stout = reinterpret_cast<float *>(stage0 + st * Cfg::stage_i);               // [2 RP][POUT] rows out
+    const int pair0 = blk * RP;
+    const int np = min(RP, npairs - pair0);
+    // step 1: Z_n = A_n + i B_n (imaginary parts of bins 0 and N/2 dropped)
+    // and its Hermitian extension for n > N/2
+    for (int job = threadIdx.x; job < np * N1; job += kRowT) {
+      const int n1 = job / np, p = job - n1 * np;
+      float2 v[N2];
 #pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) {
-      const int n = n1 + N1 * n2;
-      if (n <= N / 2) {
-        float4 ab = stin[n * RP + p];
-        if (n == 0 || n == N / 2) { ab.y = 0.f; ab.w = 0.f; }
-        v[n2] = make_float2(ab.x - ab.w, ab.y + ab.z);
-      } else {
-        const float4 ab = stin[(N - n) * RP + p];
-        v[n2] = make_float2(ab.x + ab.w, ab.z - ab.y);
+      for (int n2 = 0; n2 < N2; ++n2) {
+        const int n = n1 + N1 * n2;
+        if (n <= N / 2) {
+          float4 ab = stin[n * RP + p];
+          if (n == 0 || n == N / 2) { ab.y = 0.f; ab.w = 0.f; }
+          v[n2] = make_float2(ab.x - ab.w, ab.y + ab.z);
+        } else {
+          const float4 ab = stin[(N - n) * RP + p];
+          v[n2] = make_float2(ab.x + ab.w, ab.z - ab.y);
+        }
+      }
+      reg_dft<true, N2>(v);
+      float2 *x = X + p * QI + n1 * N2;
+      x[0] = v[0];
+#pragma unroll
+      for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmulc(v[k2], tw2[k2 * N1 + n1]);
+    }
+    __syncthreads();
+    for (int job = threadIdx.x; job < np * N2; job += kRowT) {
+      const int p = job / N2, k2 = job - p * N2;
+      float2 u[N1];
+#pragma unroll
+      for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[p * QI + n1 * N2 + k2];
+      reg_dft<true, N1>(u);
+      float *da = stout + (2 * p) * POUT, *db = da + POUT;
+#pragma unroll
+      for (int k1 = 0; k1 < N1; ++k1) {
+        da[k2 + N2 * k1] = u[k1].x * scale;
+        db[k2 + N2 * k1] = u[k1].y * scale;
       }
     }
-    reg_dft<true, N2>(v);
-    float2 *x = X + p * QI + n1 * N2;
-    x[0] = v[0];
-#pragma unroll
-    for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmulc(v[k2], tw2[k2 * N1 + n1]);
-  }
-  __syncthreads();
-  for (int job = threadIdx.x; job < np * N2; job += kRowT) {
-    const int p = job / N2, k2 = job - p * N2;
-    float2 u[N1];
-#pragma unroll
-    for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[p * QI + n1 * N2 + k2];
-    reg_dft<true, N1>(u);
-    float *da = stout + (2 * p) * POUT, *db = da + POUT;
-#pragma unroll
-    for (int k1 = 0; k1 < N1; ++k1) {
-      da[k2 + N2 * k1] = u[k1].x * scale;
-      db[k2 + N2 * k1] = u[k1].y * scale;
+    fence_proxy_async();
+    __syncthreads();  // (also: every thread is done with X before the next block's step 1)
+    if (threadIdx.x < 2 * np) {
+      const int r = threadIdx.x;
+      float *dst = out + (2 * (size_t)pair0 + r) * N;
+      if (add) bulk_s2g_add_f32(dst, stout + r * POUT, (uint32_t)N * 4);
+      else bulk_s2g(dst, stout + r * POUT, (uint32_t)N * 4);
+      bulk_commit();
     }
   }
-  fence_proxy_async();
-  __syncthreads();
-  if (threadIdx.x < 2 * np) {
-    const int r = threadIdx.x;
-    float *dst = out + (2 * (size_t)pair0 + r) * N;
-    if (add) bulk_s2g_add_f32(dst, stout + r * POUT, (uint32_t)N * 4);
-    else bulk_s2g(dst, stout + r * POUT, (uint32_t)N * 4);
-    bulk_commit();
-    bulk_wait_read();
-  }
+  if (threadIdx.x < 2 * RP) bulk_wait_all();  // this thread's stores are complete
 }
 
 // ---------------------------------------------------------------------------
@@ -569,6 +604,23 @@ static cudaError_t launch_slab_kernel(const PencilParams &pp, float2 *S, const f
   return cudaGetLastError();
 }
 
+// CTAs of kernel K resident at once on the device (the grid of the
+// persistent x-rows kernels).  Set the kernel's shared-memory attribute
+// first.
+template <auto K> static int resident_ctas(size_t smem, int threads) {
+  static std::once_flag once;
+  static int n = 0;
+  std::call_once(once, [&] {
+    int per = 0, dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, K, threads, smem) == cudaSuccess)
+      n = per * sms;
+    cudaGetLastError();
+  });
+  return n;
+}
+
 template <int N, int B, bool SG>
 static cudaError_t launch_rows_fwd_res(const ResidualArgs &A, const float *b, const float *x, float2 *S,
                                        const float2 *twx, int npairs, int rows, double *norms, cudaStream_t st) {
@@ -637,7 +689,9 @@ cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, f
 #define X(N)                                                                                               \
   if (nx == N) {                                                                                           \
     IBM_KTRY(ensure_max_smem<k_rows_inv_t<N>>());                                                          \
-    IBM_KTRY(launch_pdl(k_rows_inv_t<N>, dim3(ceil_div(npairs, RowT<N>::RP)), dim3(kRowT), RowT<N>::smem_i, \
+    const int nblk = ceil_div(npairs, RowT<N>::RP);                                                        \
+    const int res = resident_ctas<k_rows_inv_t<N>>(RowT<N>::smem_i, kRowT);                                 \
+    IBM_KTRY(launch_pdl(k_rows_inv_t<N>, dim3(res > 0 ? std::min(nblk, res) : nblk), dim3(kRowT), RowT<N>::smem_i, \
                         st, S, out, addend != nullptr, twx, npairs, rows, scale, pp.err));                  \
     done = true;                                                                                           \
   }
