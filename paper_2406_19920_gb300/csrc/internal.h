@@ -229,6 +229,7 @@ cudaError_t launch_residual(int nx, int ny, int nz, const StencilCoef &c, const 
 // IBM_FIELD_CELL_DIRICHLET) and its forward x rows into the kx-major spectrum
 // S, as launch_residual followed by launch_slab_solve phase 0 but without
 // storing r.  boff / norms as for launch_residual.
+bool slab_residual_fused(int nx, int nz);  // the pass exists for this x length (every CTA's rows in one y plane)
 cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, int nz, const float *b, const float *x,
                                          float2 *S, const float2 *twx, const double *boff, double *norms,
                                          cudaStream_t st);

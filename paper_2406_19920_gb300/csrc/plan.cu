@@ -309,7 +309,7 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
   T *r = static_cast<T *>(p->work);
   for (int it = 0; it < iters; ++it) {
     if constexpr (sizeof(T) == 4) {
-      if (slab_applies(p, pp)) {  // the residual goes straight into the correction's x rows
+      if (slab_applies(p, pp) && slab_residual_fused(p->nx, p->nz)) {  // r straight into the correction's x rows
         {
           ProfScope ps(p, IBM_K_RESIDUAL, st);
           IBM_CUDA_TRY(launch_slab_residual_forward(sc, p->nx, p->ny, p->nz, b, out, static_cast<float2 *>(p->S),

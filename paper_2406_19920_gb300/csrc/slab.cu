@@ -162,15 +162,18 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
   pdl_wait();  // x is the predecessor's output
   const int pair0 = blockIdx.x * Cfg::RP;
   const int np = min(Cfg::RP, npairs - pair0);
-  const int row0 = 2 * pair0;
+  // the CTA's rows lie in one y plane (2 RP divides nz on the slab path)
+  const int row0 = 2 * pair0, j = row0 / A.nz, k0 = row0 - j * A.nz;
+  const size_t pl = (size_t)A.nx * A.nz;
+  const float *xc = x + (size_t)row0 * N, *bc = b + (size_t)row0 * N;
+  const float *xlo = j > 0 ? xc - pl : nullptr, *xhi = j + 1 < A.ny ? xc + pl : nullptr;
   float2 m = make_float2(0.f, 0.f);
   if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
   double r2 = 0.0, b2 = 0.0, r1 = 0.0, b1 = 0.0;
   for (int job = threadIdx.x; job < 2 * np * Q4; job += kRowT) {
     const int rr = job / Q4, i0 = 4 * (job - rr * Q4);
-    const int row = row0 + rr, j = row / A.nz, k = row - j * A.nz;
     float4 bt;
-    const float4 res = residual4<BC, SIGMA>(A, b, x, j, k, i0, m, bt);
+    const float4 res = residual4_rows<BC, SIGMA>(A, bc, xc, xlo, xhi, rr * N + i0, i0, k0 + rr, m, bt);
     if (norms) residual4_norms(res, bt, r2, b2, r1, b1);
     *reinterpret_cast<float4 *>(tile + rr * TP + i0) = res;
   }
@@ -621,6 +624,15 @@ template <auto K> static int resident_ctas(size_t smem, int threads) {
   return n;
 }
 
+bool slab_residual_fused(int nx, int nz) {
+  int rows = 0;  // rows a CTA of the x-rows passes takes
+#define X(N) \
+  if (nx == N) rows = 2 * RowT<N>::RP;
+  IBM_SLAB_ROWS_N(X)
+#undef X
+  return rows > 0 && nx % 4 == 0 && nz % rows == 0;
+}
+
 template <int N, int B, bool SG>
 static cudaError_t launch_rows_fwd_res(const ResidualArgs &A, const float *b, const float *x, float2 *S,
                                        const float2 *twx, int npairs, int rows, double *norms, cudaStream_t st) {
@@ -643,6 +655,7 @@ cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, i
                                          cudaStream_t st) {
   if (nx % 4 != 0 || ((uintptr_t)b | (uintptr_t)x) & 15u) return cudaErrorInvalidValue;
   if (c.bc != BC_NEUMANN && c.bc != BC_CELL_DIRICHLET) return cudaErrorInvalidValue;  // the slab path's kinds
+  if (!slab_residual_fused(nx, nz)) return cudaErrorInvalidValue;
   const ResidualArgs A = make_args(nx, ny, nz, c, boff);
   const bool sg = c.sigma != 0.0, neu = c.bc == BC_NEUMANN;
   const int npairs = ny * nz / 2, rows = ny * nz;

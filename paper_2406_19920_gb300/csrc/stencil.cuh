@@ -144,6 +144,39 @@ __device__ __forceinline__ float4 residual4(const ResidualArgs &A, const float *
   return res;
 }
 
+// The same four points for a block of consecutive rows of one y plane
+// (the wall kinds Neumann and cell Dirichlet only), with the addressing
+// reduced to 32-bit offsets from the block's first row: xc, bc point at x, b
+// there, xlo / xhi at x one plane below / above (NULL at a wall: the ghost
+// value), off = (row - first row) nx + i0, k the row's z index.
+template <int BC, bool SIGMA>
+__device__ __forceinline__ float4 residual4_rows(const ResidualArgs &A, const float *__restrict__ bc,
+                                                 const float *__restrict__ xc, const float *__restrict__ xlo,
+                                                 const float *__restrict__ xhi, int off, int i0, int k, float2 m,
+                                                 float4 &bt) {
+  static_assert(BC == BC_NEUMANN || BC == BC_CELL_DIRICHLET, "wall kinds with ghost values");
+  const int nx = A.nx;
+  const float4 x0 = *reinterpret_cast<const float4 *>(xc + off);
+  const float xW = xc[off + (i0 == 0 ? nx - 1 : -1)];
+  const float xE = xc[off + (i0 + 4 == nx ? 4 - nx : 4)];
+  const int dn = k + 1 == A.nz ? -(A.nz - 1) * nx : nx;
+  const int ds = k == 0 ? (A.nz - 1) * nx : -nx;
+  const float4 xn = *reinterpret_cast<const float4 *>(xc + off + dn);
+  const float4 xs = *reinterpret_cast<const float4 *>(xc + off + ds);
+  const float gs = BC == BC_NEUMANN ? 1.0f : -1.0f;
+  const float4 xd = xlo ? *reinterpret_cast<const float4 *>(xlo + off)
+                        : make_float4(gs * x0.x, gs * x0.y, gs * x0.z, gs * x0.w);
+  const float4 xu = xhi ? *reinterpret_cast<const float4 *>(xhi + off)
+                        : make_float4(gs * x0.x, gs * x0.y, gs * x0.z, gs * x0.w);
+  const float4 bv = *reinterpret_cast<const float4 *>(bc + off);
+  float4 res;
+  res.x = residual_point<SIGMA>(A, bv.x, m, x0.x, x0.y, xW, xn.x, xs.x, xu.x, xd.x, bt.x);
+  res.y = residual_point<SIGMA>(A, bv.y, m, x0.y, x0.z, x0.x, xn.y, xs.y, xu.y, xd.y, bt.y);
+  res.z = residual_point<SIGMA>(A, bv.z, m, x0.z, x0.w, x0.y, xn.z, xs.z, xu.z, xd.z, bt.z);
+  res.w = residual_point<SIGMA>(A, bv.w, m, x0.w, xE, x0.z, xn.w, xs.w, xu.w, xd.w, bt.w);
+  return res;
+}
+
 // The four points' shares of the norm sums (r^2, b^2, r, b).
 __device__ __forceinline__ void residual4_norms(float4 res, float4 bt, double &r2, double &b2, double &r1,
                                                 double &b1) {
