@@ -64,14 +64,14 @@ N_STATES = 4
 # is reported only while these are unchanged)
 KERNEL_SOURCES = {
     "headline": {"forward": ("slab.cu", "fft2.cuh"), "pencil": ("slab.cu", "seg.cuh", "fft2.cuh"),
-                 "inverse": ("slab.cu", "fft2.cuh"), "residual": ("stencil.cu",)},
+                 "inverse": ("slab.cu", "fft2.cuh"), "residual": ("slab.cu", "stencil.cuh", "fft2.cuh")},
     "stage": {"forward": ("transforms.cu", "axis.cu", "fft2.cuh"),
               "inverse": ("transforms.cu", "axis.cu", "fft2.cuh"), "pencil": ("pencil.cu", "seg.cuh"),
               "residual": ("stencil.cu",), "explicit": ("substep.cu",), "divergence": ("substep.cu",),
               "project": ("substep.cu",), "interp": ("ibm_kernels.cu",), "spread": ("ibm_kernels.cu",),
               "motion": ("ibm_kernels.cu",)}}
 # kernel-name prefix -> kind (the names ncu prints)
-KERNEL_KIND = (("k_plane_fwd", "forward"), ("k_rows_fwd", "forward"), ("k_cplane_fwd", "forward"),
+KERNEL_KIND = (("k_plane_fwd", "forward"), ("k_rows_fwd_res", "residual"), ("k_rows_fwd", "forward"), ("k_cplane_fwd", "forward"),
                ("k_plane_inv", "inverse"), ("k_rows_inv", "inverse"), ("k_cplane_inv", "inverse"),
                ("k_pencil", "pencil"), ("k_slab", "pencil"), ("k_residual", "residual"), ("k_explicit", "explicit"),
                ("k_divergence", "divergence"), ("k_project", "project"), ("k_interp", "interp"),
