@@ -469,27 +469,31 @@ def run_gpu(args):
 
     # ---- end to end: host buffers, copies inside the timed region ----
     # Every step uploads its right-hand side from pinned host memory, solves
-    # through ibm_poisson_solve and reads the solution back.  Two device
-    # buffer sets alternate: step i's upload runs on an upload stream while
-    # step i-1 solves, its download on a download stream while step i+1
-    # solves (the solves stay in order on the compute stream).
+    # through ibm_poisson_solve and reads the solution back.  NB device
+    # buffer sets rotate: step i's upload runs on an upload stream while
+    # earlier steps solve, its download on a download stream while later
+    # steps solve (the solves stay in order on the compute stream).  With two
+    # sets the period is (upload + solve + download) / 2, as step i's upload
+    # waits for step i-2's download; with NB >= 3 it is bounded by the slower
+    # copy direction alone.
+    NB = len(rhs)
     host_in = torch.from_numpy(b32).pin_memory()
-    host_out = [torch.empty((n, n, n), dtype=f32).pin_memory() for _ in range(2)]
+    host_out = [torch.empty((n, n, n), dtype=f32).pin_memory() for _ in range(NB)]
     h2d = host_in.numel() * host_in.element_size()
     d2h = host_out[0].numel() * host_out[0].element_size()
     e2e_steps = max(3, min(args.steps, 40))
     s_up, s_down = torch.cuda.Stream(), torch.cuda.Stream()
-    ev_up = [torch.cuda.Event() for _ in range(2)]
-    ev_done = [torch.cuda.Event() for _ in range(2)]
-    ev_down = [torch.cuda.Event() for _ in range(2)]
+    ev_up = [torch.cuda.Event() for _ in range(NB)]
+    ev_done = [torch.cuda.Event() for _ in range(NB)]
+    ev_down = [torch.cuda.Event() for _ in range(NB)]
     barrier()
     e0.record()
     s_up.wait_stream(stream)
     s_down.wait_stream(stream)
     for i in range(e2e_steps):
-        bi = i % 2
+        bi = i % NB
         with torch.cuda.stream(s_up):
-            if i >= 2:
+            if i >= NB:
                 s_up.wait_event(ev_down[bi])  # buffer bi's previous solution is out
             rhs[bi].copy_(host_in, non_blocking=True)
             ev_up[bi].record(s_up)
@@ -506,7 +510,7 @@ def run_gpu(args):
     barrier()
     e2e_ms = job_ms(e0.elapsed_time(e1), dist, "cuda")
     e2e_value = job_throughput(pts * e2e_steps, ws, e2e_ms)
-    e2e_same = bool(np.array_equal(host_out[(e2e_steps - 1) % 2].numpy(), got.astype(np.float32)))
+    e2e_same = bool(np.array_equal(host_out[(e2e_steps - 1) % NB].numpy(), got.astype(np.float32)))
     ibm.ibm_plan_destroy(plan)
     del rhs, phi, host_in, host_out
     torch.cuda.empty_cache()
@@ -543,8 +547,8 @@ def run_gpu(args):
         "config": cfg,
         "e2e": {"value": e2e_value, "unit": "grid-pts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                 "steps": e2e_steps, "solves_per_s": e2e_value / pts, "result_matches_device_run": e2e_same,
-                "overlap": "two device buffer sets: step i's upload and download overlap the neighbouring "
-                           "steps' solves (separate upload, compute and download streams)"},
+                "overlap": "%d device buffer sets: step i's upload and download overlap other steps' solves "
+                           "and each other (separate upload, compute and download streams)" % NB},
         "gpu_launches": launches,
         "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak, "peak_source": peak_src, "traffic": traffic,
