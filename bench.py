@@ -3,8 +3,8 @@
 A step is one call of ibm_poisson_solve on a 256^3 grid of the domain
 [0,2pi) x [0,2] x [0,2pi] (periodic x, z; homogeneous Neumann walls in y):
 forward x/z transforms, the y tridiagonal solves with the FP64 zero mode,
-inverse transforms, one float-float residual and the correction solve, and
-the FP64 mean removal.  The right-hand side is seeded zero-mean N(0,1) noise
+inverse transforms, one FP32 residual (computed inside the correction's
+forward x-rows pass) and the correction solve, and the FP64 mean removal.  The right-hand side is seeded zero-mean N(0,1) noise
 low-pass filtered to |k| <= 32.  Four right-hand sides and four solutions
 rotate across steps (512 MB > 129 MB L2), so every step reads from HBM.
 
