@@ -21,8 +21,10 @@
 // passes read and write the spectrum twice more).  The z transforms and the
 // sweep run on data already in shared memory.
 #include <cooperative_groups.h>
+#include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstring>
 #include <mutex>
 
 #include "fft2.cuh"
@@ -66,7 +68,10 @@ template <int N> struct RowT {
   static constexpr size_t stage_i = mx((size_t)P * 2 * RP * 8, (size_t)2 * RP * POUT * 4);
   static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8;
   static constexpr size_t smem_r = smem_f + (size_t)2 * RP * (N + 8) * 4;  // + the residual tile
-  static constexpr size_t smem_i = (size_t)N * 8 + (size_t)RP * QI * 8 + 2 * stage_i + 16;  // two stages
+  static constexpr size_t a128(size_t b) { return (b + 127) & ~(size_t)127; }
+  static constexpr size_t o_stage = a128((size_t)N * 8 + (size_t)RP * QI * 8);  // 128-byte aligned tensor-load targets
+  static constexpr size_t stage_a = a128(stage_i);
+  static constexpr size_t smem_i = o_stage + 2 * stage_a + 16;  // two stages
 };
 
 // Steps 1 - 3 of the forward x rows of the CTA's np row pairs: real rows
@@ -185,14 +190,14 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
 template <int N>
 __global__ void __launch_bounds__(kRowT)
 k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *__restrict__ tw, int npairs, int rows,
-             float scale, int *err) {
+             float scale, const __grid_constant__ CUtensorMap tmap, bool use_tmap, int *err) {
   using Cfg = RowT<N>;
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QI = Cfg::QI, P = Cfg::P, POUT = Cfg::POUT;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
   float2 *X = tw2 + N;                                                      // [p][n1][k2]
-  unsigned char *stage0 = reinterpret_cast<unsigned char *>(X + RP * QI);  // two stages of stage_i bytes
-  uint64_t *bar = reinterpret_cast<uint64_t *>(stage0 + 2 * Cfg::stage_i);
+  unsigned char *stage0 = smem_raw + Cfg::o_stage;  // two stages of stage_a bytes
+  uint64_t *bar = reinterpret_cast<uint64_t *>(stage0 + 2 * Cfg::stage_a);
   load_step_twiddles<float, N>(tw2, tw);
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -203,13 +208,20 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
   __syncthreads();
   pdl_wait();  // the spectrum is the predecessor's output
   // The P runs of block blk into stage st, completion on bar[st] (thread 0
-  // arms the barrier; a barrier orders that before the copies).
+  // arms the barrier; a barrier orders that before the copies): one tensor
+  // load of the [P][2 RP] box of the spectrum (whole box, the rows past a
+  // partial last block read as zero), or one bulk copy per run.
   auto arm = [&](int blk, int st) {
-    if (threadIdx.x == 0) mbar_arrive_expect_tx(&bar[st], (uint32_t)P * min(RP, npairs - blk * RP) * 16);
+    if (threadIdx.x == 0)
+      mbar_arrive_expect_tx(&bar[st], (uint32_t)P * (use_tmap ? RP : min(RP, npairs - blk * RP)) * 16);
   };
   auto issue = [&](int blk, int st) {
-    float4 *stin = reinterpret_cast<float4 *>(stage0 + st * Cfg::stage_i);
+    float4 *stin = reinterpret_cast<float4 *>(stage0 + st * Cfg::stage_a);
     const int pair0 = blk * RP;
+    if (use_tmap) {
+      if (threadIdx.x == 0) tensor_g2s_2d(stin, &tmap, 4 * pair0, 0, &bar[st]);
+      return;
+    }
     const uint32_t nb = (uint32_t)min(RP, npairs - pair0) * 16;
     for (int k = threadIdx.x; k < P; k += kRowT) bulk_g2s(stin + k * RP, S + (size_t)k * rows + 2 * (size_t)pair0, nb,
                                                           &bar[st]);
@@ -241,8 +253,8 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
       loaded_next = false;
       break;
     }
-    const float4 *stin = reinterpret_cast<const float4 *>(stage0 + st * Cfg::stage_i);  // [P][RP] (A, B) in
-    float *stout = reinterpret_cast<float *>(stage0 + st * Cfg::stage_i);               // [2 RP][POUT] rows out
+    const float4 *stin = reinterpret_cast<const float4 *>(stage0 + st * Cfg::stage_a);  // [P][RP] (A, B) in
+    float *stout = reinterpret_cast<float *>(stage0 + st * Cfg::stage_a);               // [2 RP][POUT] rows out
     const int pair0 = blk * RP;
     const int np = min(RP, npairs - pair0);
     // step 1: Z_n = A_n + i B_n (imaginary parts of bins 0 and N/2 dropped)
@@ -633,6 +645,32 @@ bool slab_residual_fused(int nx, int nz) {
   return rows > 0 && nx % 4 == 0 && nz % rows == 0;
 }
 
+// The inverse x rows' view of the kx-major spectrum for tensor loads: S as a
+// [P][rows] array of complex values (2 floats), box [P][2 RP complex].
+// false where the box does not fit the tensor unit's limits (P > 256) or
+// the driver has no encoder: the kernel then issues one bulk copy per run.
+static bool spectrum_tmap(CUtensorMap *tm, const float2 *S, int P, int rows, int rp) {
+  static std::once_flag once;
+  static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
+  std::call_once(once, [] {
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    cudaGetLastError();
+  });
+  std::memset(tm, 0, sizeof *tm);
+  if (!encode || P > 256 || 4 * rp > 256) return false;
+  const cuuint64_t dims[2] = {(cuuint64_t)rows * 2, (cuuint64_t)P};
+  const cuuint64_t strides[1] = {(cuuint64_t)rows * 8};  // bytes between kx rows
+  const cuuint32_t box[2] = {(cuuint32_t)(4 * rp), (cuuint32_t)P};
+  const cuuint32_t estr[2] = {1, 1};
+  return encode(tm, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float2 *>(S), dims, strides, box, estr,
+                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 template <int N, int B, bool SG>
 static cudaError_t launch_rows_fwd_res(const ResidualArgs &A, const float *b, const float *x, float2 *S,
                                        const float2 *twx, int npairs, int rows, double *norms, cudaStream_t st) {
@@ -704,8 +742,10 @@ cudaError_t launch_slab_solve(const PencilParams &pp, int nx, const float *in, f
     IBM_KTRY(ensure_max_smem<k_rows_inv_t<N>>());                                                          \
     const int nblk = ceil_div(npairs, RowT<N>::RP);                                                        \
     const int res = resident_ctas<k_rows_inv_t<N>>(RowT<N>::smem_i, kRowT);                                 \
+    CUtensorMap tm;                                                                                        \
+    const bool use_tm = spectrum_tmap(&tm, S, RowT<N>::P, rows, RowT<N>::RP);                               \
     IBM_KTRY(launch_pdl(k_rows_inv_t<N>, dim3(res > 0 ? std::min(nblk, res) : nblk), dim3(kRowT), RowT<N>::smem_i, \
-                        st, S, out, addend != nullptr, twx, npairs, rows, scale, pp.err));                  \
+                        st, S, out, addend != nullptr, twx, npairs, rows, scale, tm, use_tm, pp.err));      \
     done = true;                                                                                           \
   }
   IBM_SLAB_ROWS_N(X)

@@ -94,6 +94,18 @@ __device__ __forceinline__ void bulk_prefetch_l2(const void *src, uint32_t bytes
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
+// 2-D tiled tensor load: the box of the tensor map `tmap` (a kernel
+// parameter) at element coordinates (x, y) into shared memory, completion
+// counted on `bar` (x * element size % 16 == 0; out-of-range elements read
+// as zero and count toward the transaction bytes).
+__device__ __forceinline__ void tensor_g2s_2d(void *dst, const void *tmap, int x, int y, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_u32(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+
 // shared -> global (bulk group); call fence_proxy_async() + barrier before.
 __device__ __forceinline__ void bulk_s2g(void *dst, const void *src, uint32_t bytes) {
   asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(dst), "r"(smem_u32(src)),
