@@ -172,6 +172,11 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
   const size_t pl = (size_t)A.nx * A.nz;
   const float *xc = x + (size_t)row0 * N, *bc = b + (size_t)row0 * N;
   const float *xlo = j > 0 ? xc - pl : nullptr, *xhi = j + 1 < A.ny ? xc + pl : nullptr;
+  {  // the block's rows of b and x and x's neighbouring planes, into L2 while the first loads go out
+    const uint32_t nb = (uint32_t)(2 * np) * N * 4;
+    const float *pf = threadIdx.x == 0 ? bc : threadIdx.x == 1 ? xc : threadIdx.x == 2 ? xlo : xhi;
+    if (threadIdx.x < 4 && pf) bulk_prefetch_l2(pf, nb);
+  }
   float2 m = make_float2(0.f, 0.f);
   if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
   double r2 = 0.0, b2 = 0.0, r1 = 0.0, b1 = 0.0;
