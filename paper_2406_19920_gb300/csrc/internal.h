@@ -228,10 +228,11 @@ cudaError_t launch_residual(int nx, int ny, int nz, const StencilCoef &c, const 
 // of the coefficients c (wall kinds IBM_FIELD_CELL_NEUMANN and
 // IBM_FIELD_CELL_DIRICHLET) and its forward x rows into the kx-major spectrum
 // S, as launch_residual followed by launch_slab_solve phase 0 but without
-// storing r.  boff / norms as for launch_residual.
+// storing r.  boff / norms as for launch_residual; err: the plan's device
+// error word (bounded waits of the streaming form, 256-point x rows).
 bool slab_residual_fused(int nx, int nz);  // the pass exists for this x length (every CTA's rows in one y plane)
 cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, int nz, const float *b, const float *x,
-                                         float2 *S, const float2 *twx, const double *boff, double *norms,
+                                         float2 *S, const float2 *twx, const double *boff, double *norms, int *err,
                                          cudaStream_t st);
 // dst plane jlo += clo g_lo, plane jhi += chi g_hi ([nz][nx] planes; NULL skips a side).
 template <typename T>

@@ -314,7 +314,7 @@ static int plan_solve_t(ibm_plan_s *p, int kind, double c, int field_bc, const T
           ProfScope ps(p, IBM_K_RESIDUAL, st);
           IBM_CUDA_TRY(launch_slab_residual_forward(sc, p->nx, p->ny, p->nz, b, out, static_cast<float2 *>(p->S),
                                                     static_cast<const float2 *>(p->twx),
-                                                    kind == 0 ? p->dsc : nullptr, nullptr, st));
+                                                    kind == 0 ? p->dsc : nullptr, nullptr, p->derr, st));
         }
         rc = solve_once_slab(p, pp, nullptr, out, out, nullptr, st, 1);
         if (rc) return rc;

@@ -24,6 +24,7 @@
 #include <cudaTypedefs.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cstring>
 #include <mutex>
 
@@ -74,31 +75,41 @@ template <int N> struct RowT {
   static constexpr size_t smem_i = o_stage + 2 * stage_a + 16;  // two stages
 };
 
-// Steps 1 - 3 of the forward x rows of the CTA's np row pairs: real rows
-// 2 p and 2 p + 1 at src + 2 p pitch and src + (2 p + 1) pitch (global
-// memory or a shared tile), spectra to S from pair pair0 on.
+// Steps of the forward x rows of np row pairs: real rows 2 p and 2 p + 1 at
+// src + 2 p pitch and src + (2 p + 1) pitch (global memory or a shared
+// tile), spectra to S from pair pair0 on.
+//   step 1, job (p, n1): the length-N2 DFT of the pair's entries n1 + N1 n2
+//           (loaded and transformed in registers, then stored into the
+//           exchange X [n1][k2][p] with the step-2 twiddles);
+//   step 3, job (q, p): the columns q and N2 - q give Z_k and Z_{N-k}
+//           together; the half spectra of the pair's rows are
+//           A_k = (Z_k + conj Z_{N-k}) / 2 and B_k = -i (Z_k - conj Z_{N-k}) / 2
+//           for k <= N/2, written as the 2 np consecutive values of each kx.
 template <int N>
-__device__ __forceinline__ void rows_fwd_steps(const float *src, int pitch, float in_scale, float2 *__restrict__ S,
-                                               int pair0, int np, int rows, const float2 *tw2, float2 *X) {
+__device__ __forceinline__ void rows_fwd_load1(const float *src, int pitch, float in_scale, int p, int n1,
+                                               float2 (&v)[TwoStep<N>::N2]) {
+  constexpr int N1 = TwoStep<N>::N1, N2 = TwoStep<N>::N2;
+  const float *a = src + (size_t)(2 * p) * pitch;
+#pragma unroll
+  for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[pitch + n1 + N1 * n2] * in_scale);
+  reg_dft<false, N2>(v);
+}
+template <int N>
+__device__ __forceinline__ void rows_fwd_store1(float2 *X, int p, int n1, const float2 (&v)[TwoStep<N>::N2],
+                                                const float2 *tw2) {
+  using Cfg = RowT<N>;
+  constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF;
+  float2 *x = X + n1 * QF + p;
+  x[0] = v[0];
+#pragma unroll
+  for (int k2 = 1; k2 < N2; ++k2) x[k2 * RP] = cmul(v[k2], tw2[k2 * N1 + n1]);
+}
+template <int N>
+__device__ __forceinline__ void rows_fwd_step3(const float2 *X, float2 *__restrict__ S, int pair0, int np, int rows,
+                                               int tid, int nthr) {
   using Cfg = RowT<N>;
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QF = Cfg::QF, J3 = N2 / 2 + 1;
-  for (int job = threadIdx.x; job < np * N1; job += kRowT) {
-    const int p = job / N1, n1 = job - p * N1;
-    const float *a = src + (size_t)(2 * p) * pitch;
-    float2 v[N2];
-#pragma unroll
-    for (int n2 = 0; n2 < N2; ++n2) v[n2] = make_float2(a[n1 + N1 * n2] * in_scale, a[pitch + n1 + N1 * n2] * in_scale);
-    reg_dft<false, N2>(v);
-    float2 *x = X + n1 * QF + p;
-    x[0] = v[0];
-#pragma unroll
-    for (int k2 = 1; k2 < N2; ++k2) x[k2 * RP] = cmul(v[k2], tw2[k2 * N1 + n1]);
-  }
-  __syncthreads();
-  // step 3: the columns q and N2 - q give Z_k and Z_{N-k} together; the half
-  // spectra of the pair's rows are A_k = (Z_k + conj Z_{N-k}) / 2 and
-  // B_k = -i (Z_k - conj Z_{N-k}) / 2 for k <= N/2
-  for (int job = threadIdx.x; job < np * J3; job += kRowT) {
+  for (int job = tid; job < np * J3; job += nthr) {
     const int q = job / np, p = job - q * np;
     float2 *dA = S + 2 * (size_t)(pair0 + p);
     auto put = [&](int k, float2 zk, float2 zn) {
@@ -128,6 +139,21 @@ __device__ __forceinline__ void rows_fwd_steps(const float *src, int pitch, floa
       }
     }
   }
+}
+
+// Steps 1 - 3 by the whole CTA (kRowT threads).
+template <int N>
+__device__ __forceinline__ void rows_fwd_steps(const float *src, int pitch, float in_scale, float2 *__restrict__ S,
+                                               int pair0, int np, int rows, const float2 *tw2, float2 *X) {
+  constexpr int N1 = RowT<N>::N1, N2 = RowT<N>::N2;
+  for (int job = threadIdx.x; job < np * N1; job += kRowT) {
+    const int p = job / N1, n1 = job - p * N1;
+    float2 v[N2];
+    rows_fwd_load1<N>(src, pitch, in_scale, p, n1, v);
+    rows_fwd_store1<N>(X, p, n1, v, tw2);
+  }
+  __syncthreads();
+  rows_fwd_step3<N>(X, S, pair0, np, rows, threadIdx.x, kRowT);
 }
 
 template <int N>
@@ -190,6 +216,179 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
   if (norms) block_accumulate(r2, b2, r1, b1, norms);
   __syncthreads();
   rows_fwd_steps<N>(tile, TP, 1.0f, S, pair0, np, rows, tw2, X);
+}
+
+// ---------------------------------------------------------------------------
+// Streaming form of the refinement's first pass for 256-point x rows (the
+// same r = b - A x and forward x rows as k_rows_fwd_res_t).
+//
+// A CTA takes one block of ZB = 32 consecutive z rows (z0 .. z0 + 31) and
+// walks up a range of y planes ya .. yb - 1.  The x rows it needs (planes
+// y - 1, y, y + 1, each with the two z neighbours z0 - 1 and z0 + 32,
+// periodic in z) arrive by bulk copies in a ring of four plane slots, two
+// planes ahead of their first use: every x value is read from memory once
+// per CTA (plus one plane at each end of its range) instead of three times
+// (once per plane that uses it), and no thread waits on a global load of x.
+// Two warp groups work on consecutive planes:
+//   residual group (threads 256 .. 511): r of plane y into tile buffer
+//     y & 1, x from the ring, b from global memory (prefetched into L2 one
+//     plane ahead); its first thread issues the ring's copies, each as soon
+//     as the group is done with the plane the slot held;
+//   transform group (threads 0 .. 255): the forward x rows of the buffer of
+//     the plane before (step 1 reads the tile into registers, after which
+//     the buffer serves as the exchange area of steps 2 and 3).
+// A buffer is handed over through mbarriers (full: 256 residual arrivals,
+// free: 256 transform arrivals).  Every wait is bounded; a group that gives
+// up leaves its loop as a whole (the AND of its threads' results), the
+// other group's waits then give up too, and the copies in flight are waited
+// for before the CTA exits.
+// ---------------------------------------------------------------------------
+struct StreamCfg {
+  static constexpr int N = 256, ZB = 32, SR = ZB + 2;  // x rows, rows per block, rows per ring slot
+  static constexpr int TP = N + 8;                     // tile pitch (floats)
+  static constexpr int GT = 256;                       // threads per warp group
+  static constexpr size_t slot_bytes = (size_t)SR * N * 4;
+  static constexpr size_t buf_bytes = (size_t)ZB * TP * 4;
+  static constexpr size_t o_ring = 0;
+  static constexpr size_t o_buf = o_ring + 4 * slot_bytes;
+  static constexpr size_t o_tw = o_buf + 2 * buf_bytes;
+  static constexpr size_t o_bar = o_tw + (size_t)N * 8;
+  static constexpr size_t bytes = o_bar + 128;
+  static_assert(buf_bytes >= (size_t)RowT<N>::N1 * RowT<N>::QF * 8, "the exchange area fits a tile buffer");
+  static_assert(2 * RowT<N>::RP == ZB && RowT<N>::RP * RowT<N>::N1 == GT, "one step-1 job per transform thread");
+};
+
+template <int BC, bool SIGMA>
+__global__ void __launch_bounds__(2 * StreamCfg::GT, 1)
+k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__restrict__ x, float2 *__restrict__ S,
+                 const float2 *__restrict__ tw, int rows, int kper, int *err) {
+  using Cfg = StreamCfg;
+  constexpr int N = Cfg::N, ZB = Cfg::ZB, SR = Cfg::SR, TP = Cfg::TP, GT = Cfg::GT;
+  constexpr int N1 = RowT<N>::N1, N2 = RowT<N>::N2, RP = RowT<N>::RP;
+  extern __shared__ __align__(128) unsigned char smem[];
+  float *ring = reinterpret_cast<float *>(smem + Cfg::o_ring);
+  unsigned char *bufs = smem + Cfg::o_buf;
+  float2 *tw2 = reinterpret_cast<float2 *>(smem + Cfg::o_tw);
+  uint64_t *xbar = reinterpret_cast<uint64_t *>(smem + Cfg::o_bar);  // [4] ring slots
+  uint64_t *full = xbar + 4, *freeb = xbar + 6;                       // [2] each, per tile buffer
+  const int nz = A.nz, ny = A.ny;
+  const int zb = blockIdx.x / kper, part = blockIdx.x - zb * kper;
+  const int z0 = zb * ZB;
+  const int ya = (int)((long)ny * part / kper), yb = (int)((long)ny * (part + 1) / kper);
+  const int nsteps = yb - ya, nv = nsteps + 2;  // virtual planes v = 0 .. nv - 1 are planes ya - 1 + v
+  const size_t pl = (size_t)N * nz;             // floats per y plane
+  load_step_twiddles<float, N>(tw2, tw);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 4; ++i) mbar_init(&xbar[i], 1);
+    for (int i = 0; i < 2; ++i) {
+      mbar_init(&full[i], GT);
+      mbar_init(&freeb[i], GT);
+    }
+    fence_mbar_init();
+  }
+  __syncthreads();
+  pdl_wait();  // x is the predecessor's output
+  const int t = threadIdx.x & (GT - 1);
+
+  if (threadIdx.x >= GT) {  // ---- residual group ----
+    // virtual plane v into slot v & 3, or a plain arrival where there is no
+    // such plane (the wall side), so that every slot's phases stay in step
+    auto issue = [&](int v) {
+      const int pp = ya - 1 + v;
+      uint64_t *bar = &xbar[v & 3];
+      if (pp < 0 || pp >= ny) {
+        mbar_arrive(bar);
+        return;
+      }
+      float *dst = ring + (size_t)(v & 3) * SR * N;
+      const float *src = x + (size_t)pp * pl;
+      mbar_arrive_expect_tx(bar, (uint32_t)Cfg::slot_bytes);
+      bulk_g2s(dst + N, src + (size_t)z0 * N, (uint32_t)ZB * N * 4, bar);
+      bulk_g2s(dst, src + (size_t)((z0 + nz - 1) % nz) * N, N * 4, bar);
+      bulk_g2s(dst + (size_t)(ZB + 1) * N, src + (size_t)((z0 + ZB) % nz) * N, N * 4, bar);
+    };
+    int issued = 0;  // (thread t == 0)
+    if (t == 0) {
+      for (; issued < 4 && issued < nv; ++issued) issue(issued);
+      if (nsteps > 0) bulk_prefetch_l2(b + ((size_t)ya * nz + z0) * N, (uint32_t)ZB * N * 4);
+    }
+    float2 m = make_float2(0.f, 0.f);
+    if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
+    const float gs = BC == BC_NEUMANN ? 1.0f : -1.0f;
+    const int lane = t & 31, c = t & 63, i0 = 4 * c, r0 = 8 * (t >> 6);  // float4 column, first of 8 rows
+    int waited = 0;  // virtual planes seen complete
+    for (int s = 0; s < nsteps; ++s) {
+      const int y = ya + s, bi = s & 1;
+      bool got = true;
+      while (got && waited <= s + 2) {
+        if (mbar_wait(&xbar[waited & 3], (uint32_t)((waited >> 2) & 1), err)) ++waited;
+        else got = false;
+      }
+      if (got && s >= 2) got = mbar_wait(&freeb[bi], (uint32_t)(((s - 2) >> 1) & 1), err);
+      if (!named_bar_and(1, GT, got)) break;
+      if (t == 0 && s + 1 < nsteps) bulk_prefetch_l2(b + ((size_t)(y + 1) * nz + z0) * N, (uint32_t)ZB * N * 4);
+      const float *sy = ring + (size_t)((s + 1) & 3) * SR * N;  // plane y
+      const float *slo = ring + (size_t)(s & 3) * SR * N;       // plane y - 1
+      const float *shi = ring + (size_t)((s + 2) & 3) * SR * N; // plane y + 1
+      const bool lo = y > 0, hi = y + 1 < ny;
+      float *tile = reinterpret_cast<float *>(bufs + bi * Cfg::buf_bytes);
+      const float *brow = b + ((size_t)y * nz + z0 + r0) * N + i0;
+      float4 bv[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) bv[u] = *reinterpret_cast<const float4 *>(brow + (size_t)u * N);
+      // rows r0 - 1, r0 of the block are slot rows r0, r0 + 1
+      float4 xs = *reinterpret_cast<const float4 *>(sy + r0 * N + i0);
+      float4 x0 = *reinterpret_cast<const float4 *>(sy + (r0 + 1) * N + i0);
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int r = r0 + u;  // block row (z0 + r), slot row r + 1
+        const float4 xn = *reinterpret_cast<const float4 *>(sy + (r + 2) * N + i0);
+        const float4 g4 = make_float4(gs * x0.x, gs * x0.y, gs * x0.z, gs * x0.w);
+        const float4 xd = lo ? *reinterpret_cast<const float4 *>(slo + (r + 1) * N + i0) : g4;
+        const float4 xu = hi ? *reinterpret_cast<const float4 *>(shi + (r + 1) * N + i0) : g4;
+        // x neighbours of the quadruple: the adjacent lanes' values, the
+        // warp's end lanes from the ring (periodic x)
+        float xW = __shfl_up_sync(0xffffffffu, x0.w, 1);
+        float xE = __shfl_down_sync(0xffffffffu, x0.x, 1);
+        if (lane == 0) xW = sy[(r + 1) * N + ((i0 + N - 1) & (N - 1))];
+        if (lane == 31) xE = sy[(r + 1) * N + ((i0 + 4) & (N - 1))];
+        float4 res, bt;
+        res.x = residual_point<SIGMA>(A, bv[u].x, m, x0.x, x0.y, xW, xn.x, xs.x, xu.x, xd.x, bt.x);
+        res.y = residual_point<SIGMA>(A, bv[u].y, m, x0.y, x0.z, x0.x, xn.y, xs.y, xu.y, xd.y, bt.y);
+        res.z = residual_point<SIGMA>(A, bv[u].z, m, x0.z, x0.w, x0.y, xn.z, xs.z, xu.z, xd.z, bt.z);
+        res.w = residual_point<SIGMA>(A, bv[u].w, m, x0.w, xE, x0.z, xn.w, xs.w, xu.w, xd.w, bt.w);
+        *reinterpret_cast<float4 *>(tile + r * TP + i0) = res;
+        xs = x0;
+        x0 = xn;
+      }
+      mbar_arrive(&full[bi]);
+      named_bar_sync(1, GT);  // the group is done with plane y - 1: its slot takes virtual plane s + 4
+      if (t == 0 && s + 4 < nv) issue(issued++);
+    }
+    if (t == 0) {  // the copies still in flight (a wait gave up) land before the CTA exits
+      for (int j = 0; j < 4; ++j) {
+        int v = issued - 1;
+        while (v >= 0 && (v & 3) != j) --v;
+        if (v >= waited) mbar_wait(&xbar[j], (uint32_t)((v >> 2) & 1), nullptr);
+      }
+    }
+  } else {  // ---- transform group ----
+    const int p = t / N1, n1 = t - p * N1;  // step-1 job
+    for (int s = 0; s < nsteps; ++s) {
+      const int y = ya + s, bi = s & 1;
+      const bool got = mbar_wait(&full[bi], (uint32_t)((s >> 1) & 1), err);
+      if (!named_bar_and(2, GT, got)) break;
+      float *tile = reinterpret_cast<float *>(bufs + bi * Cfg::buf_bytes);
+      float2 *X = reinterpret_cast<float2 *>(tile);
+      float2 v[N2];
+      rows_fwd_load1<N>(tile, TP, 1.0f, p, n1, v);
+      named_bar_sync(2, GT);  // every thread holds its tile values: the buffer becomes the exchange area
+      rows_fwd_store1<N>(X, p, n1, v, tw2);
+      named_bar_sync(2, GT);
+      rows_fwd_step3<N>(X, S, (y * nz + z0) / 2, RP, rows, t, GT);
+      mbar_arrive(&freeb[bi]);
+    }
+  }
 }
 
 template <int N>
@@ -693,8 +892,39 @@ static cudaError_t launch_rows_fwd_res(const ResidualArgs &A, const float *b, co
   return cudaGetLastError();
 }
 
+template <int B, bool SG>
+static cudaError_t launch_rows_fwd_res_stream(const ResidualArgs &A, const float *b, const float *x, float2 *S,
+                                              const float2 *twx, int rows, int *err, cudaStream_t st) {
+  constexpr auto kern = k_rows_fwd_res_s<B, SG>;
+  static std::once_flag once;
+  static cudaError_t e = cudaSuccess;
+  static int sms = 0;
+  std::call_once(once, [] {
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)StreamCfg::bytes);
+    int dev = 0;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  });
+  IBM_KTRY(e);
+  // one CTA per SM: every block of 32 z rows gets the same number of CTAs,
+  // each a contiguous range of at least 4 y planes
+  const int nzb = A.nz / StreamCfg::ZB;
+  const int kper = std::max(1, std::min(sms / nzb, A.ny / 4));
+  IBM_KTRY(launch_pdl(kern, dim3(nzb * kper), dim3(2 * StreamCfg::GT), StreamCfg::bytes, st, A, b, x, S, twx, rows,
+                      kper, err));
+  return cudaGetLastError();
+}
+
+// Whether the streaming form of the refinement's first pass takes the
+// shape: 256-point x rows, z in blocks of 32 (IBM_RES_STREAM=0 keeps the
+// block form everywhere).
+static bool stream_residual_applies(int nx, int ny, int nz) {
+  const char *e = getenv("IBM_RES_STREAM");
+  return !(e && atoi(e) == 0) && nx == 256 && nz % 32 == 0 && ny >= 1;
+}
+
 cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, int nz, const float *b, const float *x,
-                                         float2 *S, const float2 *twx, const double *boff, double *norms,
+                                         float2 *S, const float2 *twx, const double *boff, double *norms, int *err,
                                          cudaStream_t st) {
   if (nx % 4 != 0 || ((uintptr_t)b | (uintptr_t)x) & 15u) return cudaErrorInvalidValue;
   if (c.bc != BC_NEUMANN && c.bc != BC_CELL_DIRICHLET) return cudaErrorInvalidValue;  // the slab path's kinds
@@ -702,6 +932,12 @@ cudaError_t launch_slab_residual_forward(const StencilCoef &c, int nx, int ny, i
   const ResidualArgs A = make_args(nx, ny, nz, c, boff);
   const bool sg = c.sigma != 0.0, neu = c.bc == BC_NEUMANN;
   const int npairs = ny * nz / 2, rows = ny * nz;
+  if (!norms && stream_residual_applies(nx, ny, nz)) {
+    if (neu) return sg ? launch_rows_fwd_res_stream<BC_NEUMANN, true>(A, b, x, S, twx, rows, err, st)
+                       : launch_rows_fwd_res_stream<BC_NEUMANN, false>(A, b, x, S, twx, rows, err, st);
+    return sg ? launch_rows_fwd_res_stream<BC_CELL_DIRICHLET, true>(A, b, x, S, twx, rows, err, st)
+              : launch_rows_fwd_res_stream<BC_CELL_DIRICHLET, false>(A, b, x, S, twx, rows, err, st);
+  }
 #define X(N)                                                                                                    \
   if (nx == N) {                                                                                                \
     if (neu) return sg ? launch_rows_fwd_res<N, BC_NEUMANN, true>(A, b, x, S, twx, npairs, rows, norms, st)      \
