@@ -310,12 +310,22 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
     int issued = 0;  // (thread t == 0)
     if (t == 0) {
       for (; issued < 4 && issued < nv; ++issued) issue(issued);
-      if (nsteps > 0) bulk_prefetch_l2(b + ((size_t)ya * nz + z0) * N, (uint32_t)ZB * N * 4);
+      for (int s = 0; s < 2 && s < nsteps; ++s)
+        bulk_prefetch_l2(b + ((size_t)(ya + s) * nz + z0) * N, (uint32_t)ZB * N * 4);
     }
     float2 m = make_float2(0.f, 0.f);
     if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
     const float gs = BC == BC_NEUMANN ? 1.0f : -1.0f;
     const int lane = t & 31, c = t & 63, i0 = 4 * c, r0 = 8 * (t >> 6);  // float4 column, first of 8 rows
+    // b of the thread's 8 quadruples, loaded one plane ahead (at the end of
+    // the step before, so that the loads are in flight across the waits)
+    float4 bv[8];
+    auto load_b = [&](int y) {
+      const float *brow = b + ((size_t)y * nz + z0 + r0) * N + i0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u) bv[u] = *reinterpret_cast<const float4 *>(brow + (size_t)u * N);
+    };
+    if (nsteps > 0) load_b(ya);
     int waited = 0;  // virtual planes seen complete
     for (int s = 0; s < nsteps; ++s) {
       const int y = ya + s, bi = s & 1;
@@ -326,16 +336,12 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
       }
       if (got && s >= 2) got = mbar_wait(&freeb[bi], (uint32_t)(((s - 2) >> 1) & 1), err);
       if (!named_bar_and(1, GT, got)) break;
-      if (t == 0 && s + 1 < nsteps) bulk_prefetch_l2(b + ((size_t)(y + 1) * nz + z0) * N, (uint32_t)ZB * N * 4);
+      if (t == 0 && s + 2 < nsteps) bulk_prefetch_l2(b + ((size_t)(y + 2) * nz + z0) * N, (uint32_t)ZB * N * 4);
       const float *sy = ring + (size_t)((s + 1) & 3) * SR * N;  // plane y
       const float *slo = ring + (size_t)(s & 3) * SR * N;       // plane y - 1
       const float *shi = ring + (size_t)((s + 2) & 3) * SR * N; // plane y + 1
       const bool lo = y > 0, hi = y + 1 < ny;
       float *tile = reinterpret_cast<float *>(bufs + bi * Cfg::buf_bytes);
-      const float *brow = b + ((size_t)y * nz + z0 + r0) * N + i0;
-      float4 bv[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) bv[u] = *reinterpret_cast<const float4 *>(brow + (size_t)u * N);
       // rows r0 - 1, r0 of the block are slot rows r0, r0 + 1
       float4 xs = *reinterpret_cast<const float4 *>(sy + r0 * N + i0);
       float4 x0 = *reinterpret_cast<const float4 *>(sy + (r0 + 1) * N + i0);
@@ -352,15 +358,19 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
         float xE = __shfl_down_sync(0xffffffffu, x0.x, 1);
         if (lane == 0) xW = sy[(r + 1) * N + ((i0 + N - 1) & (N - 1))];
         if (lane == 31) xE = sy[(r + 1) * N + ((i0 + 4) & (N - 1))];
-        float4 res, bt;
-        res.x = residual_point<SIGMA>(A, bv[u].x, m, x0.x, x0.y, xW, xn.x, xs.x, xu.x, xd.x, bt.x);
-        res.y = residual_point<SIGMA>(A, bv[u].y, m, x0.y, x0.z, x0.x, xn.y, xs.y, xu.y, xd.y, bt.y);
-        res.z = residual_point<SIGMA>(A, bv[u].z, m, x0.z, x0.w, x0.y, xn.z, xs.z, xu.z, xd.z, bt.z);
-        res.w = residual_point<SIGMA>(A, bv[u].w, m, x0.w, xE, x0.z, xn.w, xs.w, xu.w, xd.w, bt.w);
-        *reinterpret_cast<float4 *>(tile + r * TP + i0) = res;
+        const float2 lo2 = residual_pair<SIGMA>(
+            A, make_float2(bv[u].x, bv[u].y), m, make_float2(x0.x, x0.y), make_float2(x0.y, x0.z),
+            make_float2(xW, x0.x), make_float2(xn.x, xn.y), make_float2(xs.x, xs.y), make_float2(xu.x, xu.y),
+            make_float2(xd.x, xd.y));
+        const float2 hi2 = residual_pair<SIGMA>(
+            A, make_float2(bv[u].z, bv[u].w), m, make_float2(x0.z, x0.w), make_float2(x0.w, xE),
+            make_float2(x0.y, x0.z), make_float2(xn.z, xn.w), make_float2(xs.z, xs.w), make_float2(xu.z, xu.w),
+            make_float2(xd.z, xd.w));
+        *reinterpret_cast<float4 *>(tile + r * TP + i0) = make_float4(lo2.x, lo2.y, hi2.x, hi2.y);
         xs = x0;
         x0 = xn;
       }
+      if (s + 1 < nsteps) load_b(y + 1);
       mbar_arrive(&full[bi]);
       named_bar_sync(1, GT);  // the group is done with plane y - 1: its slot takes virtual plane s + 4
       if (t == 0 && s + 4 < nv) issue(issued++);

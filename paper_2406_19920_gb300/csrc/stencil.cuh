@@ -88,6 +88,28 @@ __device__ __forceinline__ float residual_point(const ResidualArgs &A, float bv,
   return S + E;
 }
 
+// residual_point at two points at once with paired FP32 instructions
+// (FADD2 / FMUL2 / FFMA2 on sm_100 and later): the same operations in the
+// same order, each rounded once per lane, so the values equal
+// residual_point's; a - b is fma(b, -1, a).
+template <bool SIGMA>
+__device__ __forceinline__ float2 residual_pair(const ResidualArgs &A, float2 bv, float2 m, float2 x0, float2 xe,
+                                                float2 xw, float2 xn, float2 xs, float2 xu, float2 xd) {
+  const float2 m1 = make_float2(-1.f, -1.f);
+  const float2 Dx = __fadd2_rn(__ffma2_rn(x0, m1, xe), __ffma2_rn(x0, m1, xw));
+  const float2 Dz = __fadd2_rn(__ffma2_rn(x0, m1, xn), __ffma2_rn(x0, m1, xs));
+  const float2 Dy = __fadd2_rn(__ffma2_rn(x0, m1, xu), __ffma2_rn(x0, m1, xd));
+  const float2 bm = __ffma2_rn(make_float2(m.y, m.y), m1, __ffma2_rn(make_float2(m.x, m.x), m1, bv));
+  float2 E = __fmul2_rn(make_float2(A.kx.lo, A.kx.lo), Dx);
+  E = __ffma2_rn(make_float2(A.kz.lo, A.kz.lo), Dz, E);
+  E = __ffma2_rn(make_float2(A.ky.lo, A.ky.lo), Dy, E);
+  float2 S = SIGMA ? __ffma2_rn(make_float2(-A.sigma, -A.sigma), x0, bm) : bm;
+  S = __ffma2_rn(make_float2(A.kx.hi, A.kx.hi), Dx, S);
+  S = __ffma2_rn(make_float2(A.kz.hi, A.kz.hi), Dz, S);
+  S = __ffma2_rn(make_float2(A.ky.hi, A.ky.hi), Dy, S);
+  return __fadd2_rn(S, E);
+}
+
 inline ResidualArgs make_args(int nx, int ny, int nz, const StencilCoef &c, const double *boff) {
   ResidualArgs A;
   A.boff = boff;
