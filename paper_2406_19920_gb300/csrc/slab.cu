@@ -704,15 +704,28 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     cf[3 * NZ + kz] = qlast;
     cluster_sync_all();  // #1: every CTA has started; every segment's carries and row m are visible
 
-    // the carry into my segment: the segments before it in its half of the sweep
+    // the carry into my segment: the segments before it in its half of the
+    // sweep (at most Lh - 1 of them).  Every peer load is issued before the
+    // first is used (the segments that are not needed read this CTA's own
+    // copy and are left out of the fold), so the reads cost one round trip.
     float2 c = make_float2(0.f, 0.f);
+    {
+      constexpr int NPR = Lh > 1 ? Lh - 1 : 1;
+      float pw[NPR], px[NPR], py[NPR];
 #pragma unroll
-    for (int s2 = 0; s2 < C; ++s2) {
-      if (s2 >= seg || s2 < (top ? 0 : Lh)) continue;
-      const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
-      const float pw = pcf[2 * NZ + kz];
-      c.x = fmaf(pw, c.x, pcf[kz]);
-      c.y = fmaf(pw, c.y, pcf[NZ + kz]);
+      for (int j = 0; j < Lh - 1; ++j) {
+        const int s2 = (top ? 0 : Lh) + j;
+        const float *pcf = cluster.map_shared_rank(cf, s2 < seg ? rank_of(s2) : rank);
+        pw[j] = pcf[2 * NZ + kz];
+        px[j] = pcf[kz];
+        py[j] = pcf[NZ + kz];
+      }
+#pragma unroll
+      for (int j = 0; j < Lh - 1; ++j) {
+        const bool in = (top ? 0 : Lh) + j < seg;
+        c.x = in ? fmaf(pw[j], c.x, px[j]) : c.x;
+        c.y = in ? fmaf(pw[j], c.y, py[j]) : c.y;
+      }
     }
     // the meeting row, solved by CTA C/2 (its sweep ends next to it, and it
     // holds the row) and read by the others after the second barrier:
@@ -720,14 +733,20 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     float2 xm = make_float2(0.f, 0.f);
     if (rank == Lh) {
       float2 yT = make_float2(0.f, 0.f);
+      float pw[Lh], px[Lh], py[Lh];
 #pragma unroll
       for (int s2 = 0; s2 < Lh; ++s2) {
         const float *pcf = cluster.map_shared_rank(cf, rank_of(s2));
-        const float pw = pcf[2 * NZ + kz];
-        yT.x = fmaf(pw, yT.x, pcf[kz]);
-        yT.y = fmaf(pw, yT.y, pcf[NZ + kz]);
+        pw[s2] = pcf[2 * NZ + kz];
+        px[s2] = pcf[kz];
+        py[s2] = pcf[NZ + kz];
       }
       const float qT = cluster.map_shared_rank(cf, Lh - 1)[3 * NZ + kz];
+#pragma unroll
+      for (int s2 = 0; s2 < Lh; ++s2) {
+        yT.x = fmaf(pw[s2], yT.x, px[s2]);
+        yT.y = fmaf(pw[s2], yT.y, py[s2]);
+      }
       const float2 yB = make_float2(fmaf(prod, c.x, y.x), fmaf(prod, c.y, y.y));
       const float2 fm = slab[kz];
       const float rm = rcp<float>(g + a * qT + a * qlast);
@@ -753,15 +772,29 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     }
     cluster_sync_all();  // #2: every segment's xhat and the zero mode's solution are visible
 
-    // x after my last row (towards the meeting row), then my rows stored
-    c = rank == Lh ? xm : cluster.map_shared_rank(xmb, Lh)[kz];
+    // x after my last row (towards the meeting row): the meeting row folded
+    // back through the segments between it and mine (at most Lh - 1; every
+    // peer load issued before the first is used), then my rows stored
+    {
+      const float2 xmr = rank == Lh ? xm : cluster.map_shared_rank(xmb, Lh)[kz];
+      const int send = top ? Lh : C;  // segments seg + 1 .. send - 1 lie between
+      constexpr int NPR = Lh > 1 ? Lh - 1 : 1;
+      float pw[NPR], px[NPR], py[NPR];
 #pragma unroll
-    for (int s2 = C - 1; s2 >= 0; --s2) {
-      if (s2 <= seg || s2 >= (top ? Lh : C)) continue;
-      const float *pcb = cluster.map_shared_rank(cb, rank_of(s2));
-      const float pw = pcb[2 * NZ + kz];
-      c.x = fmaf(pw, c.x, pcb[kz]);
-      c.y = fmaf(pw, c.y, pcb[NZ + kz]);
+      for (int j = 0; j < Lh - 1; ++j) {
+        const int s2 = send - 1 - j;
+        const float *pcb = cluster.map_shared_rank(cb, s2 > seg ? rank_of(s2) : rank);
+        pw[j] = pcb[2 * NZ + kz];
+        px[j] = pcb[kz];
+        py[j] = pcb[NZ + kz];
+      }
+      c = xmr;
+#pragma unroll
+      for (int j = 0; j < Lh - 1; ++j) {
+        const bool in = send - 1 - j > seg;
+        c.x = in ? fmaf(pw[j], c.x, px[j]) : c.x;
+        c.y = in ? fmaf(pw[j], c.y, py[j]) : c.y;
+      }
     }
     float2 *col = slab + lr0 * NZ + kz;
     if (cw) seg_store<float, R, true, true, NZ>(v, len, wconst, wc, c, live, col, (long)lstep * NZ);
