@@ -663,10 +663,16 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     if (kx >= pp.P) break;  // the same for the whole cluster
     const uint32_t par = (uint32_t)(it & 1);
     float2 *gslab = S + (size_t)kx * NY * NZ + (size_t)rank * R * NZ;
+    // The halves of the CTA's rows are stored and reloaded one at a time:
+    // the first half's copy for this slab went out during the previous
+    // slab's inverse transforms (once that half's store had read it); the
+    // second goes out here, once the previous slab's second half is read.
     if (tid == 0 && ok) {
-      bulk_wait_read();  // the previous slab's store has read the buffer
-      mbar_arrive_expect_tx(&bar[0], kHalf);
-      bulk_g2s(slab, gslab, kHalf, &bar[0]);
+      if (it == 0) {
+        mbar_arrive_expect_tx(&bar[0], kHalf);
+        bulk_g2s(slab, gslab, kHalf, &bar[0]);
+      }
+      bulk_wait_read();
       mbar_arrive_expect_tx(&bar[1], kHalf);
       bulk_g2s(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1]);
       if (kx + Q < pp.P) bulk_prefetch_l2(gslab + (size_t)Q * NY * NZ, 2 * kHalf);  // the next slab, into L2
@@ -803,14 +809,26 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     if (zm && tid < R) slab[tid * NZ] = make_float2((float)cluster.map_shared_rank(zr, 0)[rank * R + tid], 0.f);
     __syncthreads();
 
-    // inverse z transforms and the store (completed before the buffer is reloaded)
+    // inverse z transforms; each half stored as soon as it is done, and the
+    // next slab's first half copied in once its store has read the buffer
+    // (under the second half's transforms)
 #pragma unroll 1
-    for (int r0 = 0; r0 < R; r0 += W) zfft_rows<NZ, W, true>(slab + r0 * NZ, X, tw2);
-    fence_proxy_async();
-    __syncthreads();
-    if (tid == 0 && ok) {
-      bulk_s2g(gslab, slab, (uint32_t)R * NZ * 8);
-      bulk_commit();
+    for (int r0 = 0; r0 < R; r0 += W) {
+      zfft_rows<NZ, W, true>(slab + r0 * NZ, X, tw2);
+      if (r0 + W == R / 2 || r0 + W == R) {
+        const int h = r0 + W == R ? 1 : 0;
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0 && ok) {
+          bulk_s2g(gslab + h * (R / 2) * NZ, slab + h * (R / 2) * NZ, kHalf);
+          bulk_commit();
+          if (h == 0 && kx + Q < pp.P) {
+            bulk_wait_read();
+            mbar_arrive_expect_tx(&bar[0], kHalf);
+            bulk_g2s(slab, gslab + (size_t)Q * NY * NZ, kHalf, &bar[0]);
+          }
+        }
+      }
     }
   }
   if (tid == 0) {
