@@ -70,9 +70,16 @@ template <int N> struct RowT {
   static constexpr size_t smem_f = (size_t)N * 8 + (size_t)N1 * QF * 8;
   static constexpr size_t smem_r = smem_f + (size_t)2 * RP * (N + 8) * 4;  // + the residual tile
   static constexpr size_t a128(size_t b) { return (b + 127) & ~(size_t)127; }
-  static constexpr size_t o_stage = a128((size_t)N * 8 + (size_t)RP * QI * 8);  // 128-byte aligned tensor-load targets
+  // inverse: where each thread has one job in both steps (N1 = N2), the
+  // exchange area lies in the block's own stage (the spectrum is read into
+  // registers before it is written, and it is read before the output rows
+  // are), which lets three CTAs share an SM instead of two
+  static constexpr bool XSTAGE = N1 == N2;
+  static constexpr size_t o_stage = a128((size_t)N * 8 + (XSTAGE ? 0 : (size_t)RP * QI * 8));  // 128-byte aligned tensor-load targets
   static constexpr size_t stage_a = a128(stage_i);
   static constexpr size_t smem_i = o_stage + 2 * stage_a + 16;  // two stages
+  static_assert(!XSTAGE || (size_t)RP * QI * 8 <= stage_a, "the exchange area fits a stage");
+  static_assert(!XSTAGE || RP * N1 == kRowT, "one job per thread in both steps");
 };
 
 // Steps of the forward x rows of np row pairs: real rows 2 p and 2 p + 1 at
@@ -409,7 +416,7 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
   constexpr int N1 = Cfg::N1, N2 = Cfg::N2, RP = Cfg::RP, QI = Cfg::QI, P = Cfg::P, POUT = Cfg::POUT;
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *X = tw2 + N;                                                      // [p][n1][k2]
+  float2 *Xsep = tw2 + N;                            // [p][n1][k2] (unless it lies in the stage)
   unsigned char *stage0 = smem_raw + Cfg::o_stage;  // two stages of stage_a bytes
   uint64_t *bar = reinterpret_cast<uint64_t *>(stage0 + 2 * Cfg::stage_a);
   load_step_twiddles<float, N>(tw2, tw);
@@ -469,13 +476,12 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
     }
     const float4 *stin = reinterpret_cast<const float4 *>(stage0 + st * Cfg::stage_a);  // [P][RP] (A, B) in
     float *stout = reinterpret_cast<float *>(stage0 + st * Cfg::stage_a);               // [2 RP][POUT] rows out
+    float2 *X = Cfg::XSTAGE ? reinterpret_cast<float2 *>(stage0 + st * Cfg::stage_a) : Xsep;
     const int pair0 = blk * RP;
     const int np = min(RP, npairs - pair0);
     // step 1: Z_n = A_n + i B_n (imaginary parts of bins 0 and N/2 dropped)
     // and its Hermitian extension for n > N/2
-    for (int job = threadIdx.x; job < np * N1; job += kRowT) {
-      const int n1 = job / np, p = job - n1 * np;
-      float2 v[N2];
+    auto step1_load = [&](int n1, int p, float2 (&v)[N2]) {
 #pragma unroll
       for (int n2 = 0; n2 < N2; ++n2) {
         const int n = n1 + N1 * n2;
@@ -489,23 +495,56 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
         }
       }
       reg_dft<true, N2>(v);
+    };
+    auto step1_store = [&](int n1, int p, const float2 (&v)[N2]) {
       float2 *x = X + p * QI + n1 * N2;
       x[0] = v[0];
 #pragma unroll
       for (int k2 = 1; k2 < N2; ++k2) x[k2] = cmulc(v[k2], tw2[k2 * N1 + n1]);
-    }
-    __syncthreads();
-    for (int job = threadIdx.x; job < np * N2; job += kRowT) {
-      const int p = job / N2, k2 = job - p * N2;
-      float2 u[N1];
-#pragma unroll
-      for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[p * QI + n1 * N2 + k2];
-      reg_dft<true, N1>(u);
+    };
+    auto step3_store = [&](int p, int k2, const float2 (&u)[N1]) {
       float *da = stout + (2 * p) * POUT, *db = da + POUT;
 #pragma unroll
       for (int k1 = 0; k1 < N1; ++k1) {
         da[k2 + N2 * k1] = u[k1].x * scale;
         db[k2 + N2 * k1] = u[k1].y * scale;
+      }
+    };
+    if constexpr (Cfg::XSTAGE) {
+      // one job per thread: every read of an area ends (barrier) before it
+      // is overwritten: spectrum -> registers -> exchange -> registers -> rows
+      const int job = threadIdx.x;
+      const bool a1 = job < np * N1, a3 = job < np * N2;
+      const int n1 = job / np, p1 = job - n1 * np;
+      const int p3 = job / N2, k2 = job - p3 * N2;
+      float2 v[N2];
+      if (a1) step1_load(n1, p1, v);
+      __syncthreads();
+      if (a1) step1_store(n1, p1, v);
+      __syncthreads();
+      float2 u[N1];
+      if (a3) {
+#pragma unroll
+        for (int q = 0; q < N1; ++q) u[q] = X[p3 * QI + q * N2 + k2];
+        reg_dft<true, N1>(u);
+      }
+      __syncthreads();
+      if (a3) step3_store(p3, k2, u);
+    } else {
+      for (int job = threadIdx.x; job < np * N1; job += kRowT) {
+        const int n1 = job / np, p = job - n1 * np;
+        float2 v[N2];
+        step1_load(n1, p, v);
+        step1_store(n1, p, v);
+      }
+      __syncthreads();
+      for (int job = threadIdx.x; job < np * N2; job += kRowT) {
+        const int p = job / N2, k2 = job - p * N2;
+        float2 u[N1];
+#pragma unroll
+        for (int n1 = 0; n1 < N1; ++n1) u[n1] = X[p * QI + n1 * N2 + k2];
+        reg_dft<true, N1>(u);
+        step3_store(p, k2, u);
       }
     }
     fence_proxy_async();
