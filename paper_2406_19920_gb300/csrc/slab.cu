@@ -238,9 +238,10 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
 // (once per plane that uses it), and no thread waits on a global load of x.
 // Two warp groups work on consecutive planes:
 //   residual group (threads 256 .. 511): r of plane y into tile buffer
-//     y & 1, x from the ring, b from global memory (prefetched into L2 one
-//     plane ahead); its first thread issues the ring's copies, each as soon
-//     as the group is done with the plane the slot held;
+//     y & 1, x from the ring, b from global memory (into registers one plane
+//     ahead, into L2 two planes ahead); its first thread issues the ring's
+//     copies, each as soon as the group is done with the plane the slot
+//     held;
 //   transform group (threads 0 .. 255): the forward x rows of the buffer of
 //     the plane before (step 1 reads the tile into registers, after which
 //     the buffer serves as the exchange area of steps 2 and 3).
