@@ -153,6 +153,50 @@ __device__ __forceinline__ void seg_forward(cplx<T> (&v)[S], int len, int k0, T 
   }
 }
 
+// seg_forward for a segment whose pivots have not converged, with the pivot
+// recurrence in projective form.  The excess e_k = a N_k / D_k obeys the
+// linear recurrence (N, D) -> s ((1 + g/a) N + (g/a) D, N + D) (the Moebius
+// map e -> g + a e / (a + e) written on homogeneous coordinates), and then
+// p_k = a (N_k + D_k) / D_k, w_k = a / p_k = D_k / (N_k + D_k),
+// q_k = e_k / p_k = N_k / (N_k + D_k).  Every coefficient is non-negative, so
+// nothing cancels; s = 1 / (2 + g/a) bounds the dominant eigenvalue of the
+// map by 1 (and from below by 1/2), so 32 rows neither overflow nor
+// underflow.  The recurrence is two FMAs deep per row and the reciprocal
+// is off the chain (the reciprocal recurrence has one per row on it).
+// FP32 only.
+template <int S, bool FULL, int WST = 32>
+__device__ __forceinline__ void seg_forward_lin(cplx<float> (&v)[S], int len, int k0, float a, float g, float e0,
+                                                float sgn, float ep, float D, float z, float *wc, cplx<float> &y,
+                                                float &prod, float &qlast) {
+  y = mk<float>(0, 0);
+  prod = 1.f;
+  qlast = 0.f;
+  const float ia = rcp<float>(a), gh = g * ia;
+  const float sc = rcp<float>(2.f + gh);
+  const float c11 = sc * (1.f + gh), c12 = sc * gh;
+  const float e = k0 == 0 ? e0 : fmaf(D * z, rcp<float>(1.f - z), ep);
+  float Nn = e * ia, Dd = 1.f;
+  const float rs = sgn * ia;
+#pragma unroll
+  for (int u = 0; u < S; ++u) {
+    const float t = Nn + Dd;
+    const float it = rcp<float>(t);
+    const float w = Dd * it;
+    const bool in = FULL || u < len;
+    const float wu = in ? w : 1.f;
+    const float ru = in ? rs * w : 0.f;
+    wc[WST * u] = wu;
+    y.x = fmaf(wu, y.x, ru * v[u].x);
+    y.y = fmaf(wu, y.y, ru * v[u].y);
+    v[u] = y;
+    prod *= wu;
+    if (FULL ? u == S - 1 : u == len - 1) qlast = Nn * it;
+    const float nN = fmaf(c11, Nn, c12 * Dd);
+    Dd = sc * t;
+    Nn = nN;
+  }
+}
+
 // Carry c (y before the segment) folded in, then the local back substitution
 // from a zero carry; returns xhat at the segment's first row.
 template <typename T, int S, bool FULL, bool CW, int WST = 32>

@@ -743,7 +743,7 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     float2 y;
     float prod, qlast;
     if (cw) seg_forward<float, R, true, true, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
-    else seg_forward<float, R, false, false, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
+    else seg_forward_lin<R, false, NZ>(v, len, k0, a, g, e0, sgn, ep, D, z, wc, y, prod, qlast);
     cf[0 * NZ + kz] = y.x;
     cf[1 * NZ + kz] = y.y;
     cf[2 * NZ + kz] = prod;
