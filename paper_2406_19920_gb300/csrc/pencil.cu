@@ -437,6 +437,8 @@ k_pencil_seg(Ptr3<cplx<T> *> S_, const T *__restrict__ lamx, const T *__restrict
     cplx<T> y;
     T prod, qlast;
     if (cw) seg_forward<T, S, true, true>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
+    else if constexpr (sizeof(T) == 4)  // FP32: the projective pivot recurrence (reciprocal off the chain)
+      seg_forward_lin<S, false>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
     else seg_forward<T, S, false, false>(v, len, k0, a, g, ti.e0, sgn, ep, D, z, wc, y, prod, qlast);
     cf[(0 * L + seg) * 32 + lane] = y.x;
     cf[(1 * L + seg) * 32 + lane] = y.y;
