@@ -12,9 +12,12 @@
 //      k_pencil_seg with one 32-row segment per CTA (the per-segment
 //      carries cross the cluster through distributed shared memory), the
 //      FP64 zero mode in the kx = 0 cluster, the inverse z transform, and
-//      one bulk copy back;
+//      one bulk copy back per half;
 //   3. x rows inverse (k_rows_inv_t): half spectra -> real rows, scaled by
 //      1 / (nx nz), plus the optional addend.
+// A refinement step adds the residual r = b - A x computed inside the
+// correction's forward x rows (k_rows_fwd_res_s for 256-point rows,
+// k_rows_fwd_res_t otherwise), then passes 2 and 3 again.
 //
 // Each pass reads and writes the field once: 24 B per point in FP32, the
 // method's compulsory traffic, against 40 B for the split passes (whose z
