@@ -34,6 +34,8 @@ SLAB_SHAPES = [
     (12, 128, 256),
     (96, 256, 128),   # 8-CTA clusters
     (24, 256, 64),
+    (16, 256, 256),   # 8-CTA clusters, 256-point z rows (the 256^3 configuration's slabs)
+    (48, 256, 256),
 ]
 
 
@@ -97,7 +99,7 @@ def test_slab_and_split_paths_agree_in_place(shape):
     assert rel_err(outs[0], outs[1]) <= TOL_FP32
 
 
-@pytest.mark.parametrize("shape", [(48, 64, 64), (12, 128, 256), (96, 256, 128)])
+@pytest.mark.parametrize("shape", [(48, 64, 64), (12, 128, 256), (96, 256, 128), (16, 256, 256)])
 @pytest.mark.parametrize("bc", [ibm.IBM_FIELD_CELL_NEUMANN, ibm.IBM_FIELD_CELL_DIRICHLET,
                                 ibm.IBM_FIELD_FACE_DIRICHLET])
 @pytest.mark.parametrize("c", [5e-6, 0.05])
