@@ -328,8 +328,9 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
     if (A.boff) m = *reinterpret_cast<const float2 *>(A.boff + 1);
     const float gs = BC == BC_NEUMANN ? 1.0f : -1.0f;
     const int lane = t & 31, c = t & 63, i0 = 4 * c, r0 = 8 * (t >> 6);  // float4 column, first of 8 rows
-    // b of the thread's 8 quadruples, loaded one plane ahead (at the end of
-    // the step before, so that the loads are in flight across the waits)
+    // b of the thread's 8 quadruples, loaded one plane ahead: each as soon as
+    // the row before has used its register, so that a load has a whole step
+    // to arrive
     float4 bv[8];
     auto load_b = [&](int y) {
       const float *brow = b + ((size_t)y * nz + z0 + r0) * N + i0;
@@ -353,6 +354,8 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
       const float *shi = ring + (size_t)((s + 2) & 3) * SR * N; // plane y + 1
       const bool lo = y > 0, hi = y + 1 < ny;
       float *tile = reinterpret_cast<float *>(bufs + bi * Cfg::buf_bytes);
+      const bool bnext = s + 1 < nsteps;
+      const float *bn = b + ((size_t)(y + 1) * nz + z0 + r0) * N + i0;  // b of plane y + 1
       // rows r0 - 1, r0 of the block are slot rows r0, r0 + 1
       float4 xs = *reinterpret_cast<const float4 *>(sy + r0 * N + i0);
       float4 x0 = *reinterpret_cast<const float4 *>(sy + (r0 + 1) * N + i0);
@@ -378,10 +381,10 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
             make_float2(x0.y, x0.z), make_float2(xn.z, xn.w), make_float2(xs.z, xs.w), make_float2(xu.z, xu.w),
             make_float2(xd.z, xd.w));
         *reinterpret_cast<float4 *>(tile + r * TP + i0) = make_float4(lo2.x, lo2.y, hi2.x, hi2.y);
+        if (bnext) bv[u] = *reinterpret_cast<const float4 *>(bn + (size_t)u * N);
         xs = x0;
         x0 = xn;
       }
-      if (s + 1 < nsteps) load_b(y + 1);
       mbar_arrive(&full[bi]);
       named_bar_sync(1, GT);  // the group is done with plane y - 1: its slot takes virtual plane s + 4
       if (t == 0 && s + 4 < nv) issue(issued++);
