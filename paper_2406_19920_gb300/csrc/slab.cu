@@ -249,10 +249,13 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
 //     the plane before (step 1 reads the tile into registers, after which
 //     the buffer serves as the exchange area of steps 2 and 3).
 // A buffer is handed over through mbarriers (full: 256 residual arrivals,
-// free: 256 transform arrivals).  Every wait is bounded; a group that gives
-// up leaves its loop as a whole (the AND of its threads' results), the
-// other group's waits then give up too, and the copies in flight are waited
-// for before the CTA exits.
+// free: 256 transform arrivals), and so is a ring slot (sfree: 256 residual
+// arrivals once the plane is read for the last time; the first residual
+// thread waits for them before it reuses the slot), so that no residual warp
+// waits for the others at a barrier.  Every wait is bounded; a residual warp
+// that gives up leaves its loop as a whole, the transform group as a whole
+// (the AND of its threads' results), the other waits then give up too, and
+// the copies in flight are waited for before the CTA exits.
 // ---------------------------------------------------------------------------
 struct StreamCfg {
   static constexpr int N = 256, ZB = 32, SR = ZB + 2;  // x rows, rows per block, rows per ring slot
@@ -282,6 +285,7 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
   float2 *tw2 = reinterpret_cast<float2 *>(smem + Cfg::o_tw);
   uint64_t *xbar = reinterpret_cast<uint64_t *>(smem + Cfg::o_bar);  // [4] ring slots
   uint64_t *full = xbar + 4, *freeb = xbar + 6;                       // [2] each, per tile buffer
+  uint64_t *sfree = xbar + 8;                                         // [4] ring slots read for the last time
   const int nz = A.nz, ny = A.ny;
   const int zb = blockIdx.x / kper, part = blockIdx.x - zb * kper;
   const int z0 = zb * ZB;
@@ -295,6 +299,7 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
       mbar_init(&full[i], GT);
       mbar_init(&freeb[i], GT);
     }
+    for (int i = 0; i < 4; ++i) mbar_init(&sfree[i], GT);
     fence_mbar_init();
   }
   __syncthreads();
@@ -347,7 +352,7 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
         else got = false;
       }
       if (got && s >= 2) got = mbar_wait(&freeb[bi], (uint32_t)(((s - 2) >> 1) & 1), err);
-      if (!named_bar_and(1, GT, got)) break;
+      if (!__all_sync(0xffffffffu, got)) break;  // warp by warp (the shuffles below want whole warps)
       if (t == 0 && s + 2 < nsteps) bulk_prefetch_l2(b + ((size_t)(y + 2) * nz + z0) * N, (uint32_t)ZB * N * 4);
       const float *sy = ring + (size_t)((s + 1) & 3) * SR * N;  // plane y
       const float *slo = ring + (size_t)(s & 3) * SR * N;       // plane y - 1
@@ -386,8 +391,13 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
         x0 = xn;
       }
       mbar_arrive(&full[bi]);
-      named_bar_sync(1, GT);  // the group is done with plane y - 1: its slot takes virtual plane s + 4
-      if (t == 0 && s + 4 < nv) issue(issued++);
+      mbar_arrive(&sfree[s & 3]);  // done with plane y - 1
+      bool ok = true;
+      if (t == 0 && s + 4 < nv) {  // once the whole group is, its slot takes virtual plane s + 4
+        ok = mbar_wait(&sfree[s & 3], (uint32_t)((s >> 2) & 1), err);
+        if (ok) issue(issued++);
+      }
+      if (!__all_sync(0xffffffffu, ok)) break;
     }
     if (t == 0) {  // the copies still in flight (a wait gave up) land before the CTA exits
       for (int j = 0; j < 4; ++j) {
