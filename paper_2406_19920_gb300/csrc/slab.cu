@@ -319,9 +319,10 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
       float *dst = ring + (size_t)(v & 3) * SR * N;
       const float *src = x + (size_t)pp * pl;
       mbar_arrive_expect_tx(bar, (uint32_t)Cfg::slot_bytes);
-      bulk_g2s(dst + N, src + (size_t)z0 * N, (uint32_t)ZB * N * 4, bar);
-      bulk_g2s(dst, src + (size_t)((z0 + nz - 1) % nz) * N, N * 4, bar);
-      bulk_g2s(dst + (size_t)(ZB + 1) * N, src + (size_t)((z0 + ZB) % nz) * N, N * 4, bar);
+      const uint64_t pol = l2_evict_first();  // x is read for the last time
+      bulk_g2s_hint(dst + N, src + (size_t)z0 * N, (uint32_t)ZB * N * 4, bar, pol);
+      bulk_g2s_hint(dst, src + (size_t)((z0 + nz - 1) % nz) * N, N * 4, bar, pol);
+      bulk_g2s_hint(dst + (size_t)(ZB + 1) * N, src + (size_t)((z0 + ZB) % nz) * N, N * 4, bar, pol);
     };
     int issued = 0;  // (thread t == 0)
     if (t == 0) {
@@ -457,12 +458,13 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
     float4 *stin = reinterpret_cast<float4 *>(stage0 + st * Cfg::stage_a);
     const int pair0 = blk * RP;
     if (use_tmap) {
-      if (threadIdx.x == 0) tensor_g2s_2d(stin, &tmap, 4 * pair0, 0, &bar[st]);
+      if (threadIdx.x == 0) tensor_g2s_2d_hint(stin, &tmap, 4 * pair0, 0, &bar[st], l2_evict_first());
       return;
     }
     const uint32_t nb = (uint32_t)min(RP, npairs - pair0) * 16;
-    for (int k = threadIdx.x; k < P; k += kRowT) bulk_g2s(stin + k * RP, S + (size_t)k * rows + 2 * (size_t)pair0, nb,
-                                                          &bar[st]);
+    const uint64_t pol = l2_evict_first();  // the spectrum is read for the last time
+    for (int k = threadIdx.x; k < P; k += kRowT)
+      bulk_g2s_hint(stin + k * RP, S + (size_t)k * rows + 2 * (size_t)pair0, nb, &bar[st], pol);
   };
   int blk = blockIdx.x;
   if (blk < nblk) {
@@ -570,7 +572,7 @@ k_rows_inv_t(const float2 *__restrict__ S, float *out, bool add, const float2 *_
       const int r = threadIdx.x;
       float *dst = out + (2 * (size_t)pair0 + r) * N;
       if (add) bulk_s2g_add_f32(dst, stout + r * POUT, (uint32_t)N * 4);
-      else bulk_s2g(dst, stout + r * POUT, (uint32_t)N * 4);
+      else bulk_s2g_hint(dst, stout + r * POUT, (uint32_t)N * 4, l2_evict_last());  // (the residual pass reads it)
       bulk_commit();
     }
   }
@@ -726,11 +728,11 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
     if (tid == 0 && ok) {
       if (it == 0) {
         mbar_arrive_expect_tx(&bar[0], kHalf);
-        bulk_g2s(slab, gslab, kHalf, &bar[0]);
+        bulk_g2s_hint(slab, gslab, kHalf, &bar[0], l2_evict_first());
       }
       bulk_wait_read();
       mbar_arrive_expect_tx(&bar[1], kHalf);
-      bulk_g2s(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1]);
+      bulk_g2s_hint(slab + (R / 2) * NZ, gslab + (R / 2) * NZ, kHalf, &bar[1], l2_evict_first());
       if (kx + Q < pp.P) bulk_prefetch_l2(gslab + (size_t)Q * NY * NZ, 2 * kHalf);  // the next slab, into L2
     }
     const float g = (float)pp.g_add + (float)pp.g_mul * (lamx[kx] + lz);
@@ -876,12 +878,12 @@ k_slab(float2 *S, const float2 *__restrict__ twz, const float *__restrict__ lamx
         fence_proxy_async();
         __syncthreads();
         if (tid == 0 && ok) {
-          bulk_s2g(gslab + h * (R / 2) * NZ, slab + h * (R / 2) * NZ, kHalf);
+          bulk_s2g_hint(gslab + h * (R / 2) * NZ, slab + h * (R / 2) * NZ, kHalf, l2_evict_last());  // (the inverse x rows read it)
           bulk_commit();
           if (h == 0 && kx + Q < pp.P) {
             bulk_wait_read();
             mbar_arrive_expect_tx(&bar[0], kHalf);
-            bulk_g2s(slab, gslab + (size_t)Q * NY * NZ, kHalf, &bar[0]);
+            bulk_g2s_hint(slab, gslab + (size_t)Q * NY * NZ, kHalf, &bar[0], l2_evict_first());
           }
         }
       }
