@@ -319,7 +319,7 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
       float *dst = ring + (size_t)(v & 3) * SR * N;
       const float *src = x + (size_t)pp * pl;
       mbar_arrive_expect_tx(bar, (uint32_t)Cfg::slot_bytes);
-      const uint64_t pol = l2_evict_first();  // x is read for the last time
+      const uint64_t pol = l2_evict_last();  // (the correction is added to x after the next pass)
       bulk_g2s_hint(dst + N, src + (size_t)z0 * N, (uint32_t)ZB * N * 4, bar, pol);
       bulk_g2s_hint(dst, src + (size_t)((z0 + nz - 1) % nz) * N, N * 4, bar, pol);
       bulk_g2s_hint(dst + (size_t)(ZB + 1) * N, src + (size_t)((z0 + ZB) % nz) * N, N * 4, bar, pol);
@@ -338,10 +338,11 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
     // the row before has used its register, so that a load has a whole step
     // to arrive
     float4 bv[8];
+    const uint64_t bpol = l2_evict_first();  // b is read for the last time
     auto load_b = [&](int y) {
       const float *brow = b + ((size_t)y * nz + z0 + r0) * N + i0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) bv[u] = *reinterpret_cast<const float4 *>(brow + (size_t)u * N);
+      for (int u = 0; u < 8; ++u) bv[u] = ld_hint(brow + (size_t)u * N, bpol);
     };
     if (nsteps > 0) load_b(ya);
     int waited = 0;  // virtual planes seen complete
@@ -387,7 +388,7 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
             make_float2(x0.y, x0.z), make_float2(xn.z, xn.w), make_float2(xs.z, xs.w), make_float2(xu.z, xu.w),
             make_float2(xd.z, xd.w));
         *reinterpret_cast<float4 *>(tile + r * TP + i0) = make_float4(lo2.x, lo2.y, hi2.x, hi2.y);
-        if (bnext) bv[u] = *reinterpret_cast<const float4 *>(bn + (size_t)u * N);
+        if (bnext) bv[u] = ld_hint(bn + (size_t)u * N, bpol);
         xs = x0;
         x0 = xn;
       }
