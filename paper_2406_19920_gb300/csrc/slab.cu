@@ -338,11 +338,10 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
     // the row before has used its register, so that a load has a whole step
     // to arrive
     float4 bv[8];
-    const uint64_t bpol = l2_evict_first();  // b is read for the last time
     auto load_b = [&](int y) {
       const float *brow = b + ((size_t)y * nz + z0 + r0) * N + i0;
 #pragma unroll
-      for (int u = 0; u < 8; ++u) bv[u] = ld_hint(brow + (size_t)u * N, bpol);
+      for (int u = 0; u < 8; ++u) bv[u] = *reinterpret_cast<const float4 *>(brow + (size_t)u * N);
     };
     if (nsteps > 0) load_b(ya);
     int waited = 0;  // virtual planes seen complete
@@ -388,7 +387,7 @@ k_rows_fwd_res_s(ResidualArgs A, const float *__restrict__ b, const float *__res
             make_float2(x0.y, x0.z), make_float2(xn.z, xn.w), make_float2(xs.z, xs.w), make_float2(xu.z, xu.w),
             make_float2(xd.z, xd.w));
         *reinterpret_cast<float4 *>(tile + r * TP + i0) = make_float4(lo2.x, lo2.y, hi2.x, hi2.y);
-        if (bnext) bv[u] = ld_hint(bn + (size_t)u * N, bpol);
+        if (bnext) bv[u] = *reinterpret_cast<const float4 *>(bn + (size_t)u * N);
         xs = x0;
         x0 = xn;
       }

@@ -126,14 +126,6 @@ __device__ __forceinline__ uint64_t l2_evict_first() {
   asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
   return p;
 }
-// a 16-byte global load with an L2 eviction priority
-__device__ __forceinline__ float4 ld_hint(const float *src, uint64_t pol) {
-  float4 v;
-  asm("ld.global.L2::cache_hint.v4.f32 {%0, %1, %2, %3}, [%4], %5;"
-               : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-               : "l"(src), "l"(pol));
-  return v;
-}
 // bulk_g2s with an L2 eviction priority
 __device__ __forceinline__ void bulk_g2s_hint(void *dst, const void *src, uint32_t bytes, uint64_t *bar,
                                               uint64_t pol) {
