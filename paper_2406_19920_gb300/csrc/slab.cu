@@ -971,7 +971,8 @@ bool slab_residual_fused(int nx, int nz) {
 // The inverse x rows' view of the kx-major spectrum for tensor loads: S as a
 // [P][rows] array of complex values (2 floats), box [P][2 RP complex].
 // false where the box does not fit the tensor unit's limits (P > 256) or
-// the driver has no encoder: the kernel then issues one bulk copy per run.
+// the CUDA driver has no tensor-map encoder: the kernel then issues one bulk
+// copy per run.
 static bool spectrum_tmap(CUtensorMap *tm, const float2 *S, int P, int rows, int rp) {
   static std::once_flag once;
   static PFN_cuTensorMapEncodeTiled_v12000 encode = nullptr;
