@@ -241,10 +241,12 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
 // (once per plane that uses it), and no thread waits on a global load of x.
 // Two warp groups work on consecutive planes:
 //   residual group (threads 256 .. 511): r of plane y into tile buffer
-//     y & 1, x from the ring, b from global memory (into registers one plane
-//     ahead, into L2 two planes ahead); its first thread issues the ring's
+//     y & 1, x from the ring, b from global memory (each quadruple of the
+//     next plane into its register once the row before has used it, the
+//     block into L2 two planes ahead); its first thread issues the ring's
 //     copies, each as soon as the group is done with the plane the slot
-//     held;
+//     held (x stays in L2 at evict-last priority: the correction is added
+//     to it after the next pass);
 //   transform group (threads 0 .. 255): the forward x rows of the buffer of
 //     the plane before (step 1 reads the tile into registers, after which
 //     the buffer serves as the exchange area of steps 2 and 3).
