@@ -172,7 +172,7 @@ k_rows_fwd_t(const float *__restrict__ in, float2 *__restrict__ S, const float2 
              int rows, float in_scale, int *err) {
   using Cfg = RowT<N>;
   (void)err;  // no waits: every access is a plain coalesced load or store
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
   float2 *X = tw2 + N;  // [N1][k2][p]
   load_step_twiddles<float, N>(tw2, tw);
@@ -195,7 +195,7 @@ k_rows_fwd_res_t(ResidualArgs A, const float *__restrict__ b, const float *__res
                  const float2 *__restrict__ tw, int npairs, int rows, double *norms) {
   using Cfg = RowT<N>;
   constexpr int TP = N + 8, Q4 = N / 4;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *tw2 = reinterpret_cast<float2 *>(smem_raw);
   float2 *X = tw2 + N;                                            // [N1][k2][p]
   float *tile = reinterpret_cast<float *>(X + Cfg::N1 * Cfg::QF);  // [2 RP][TP]
