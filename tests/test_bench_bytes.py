@@ -65,3 +65,14 @@ def test_unrefined_solve_bytes():
     k = bench.solve_kind_bytes(n, esz=4, refine=0)
     F, S = _field(n), _spec(n)
     assert k == {"forward": F + S, "pencil": 2 * S, "inverse": S + F, "residual": 0}
+
+
+@pytest.mark.parametrize("refine,fused", [(0, True), (1, True), (1, False), (2, False)])
+def test_method_bytes_agrees_with_the_per_kind_count(refine, fused):
+    """The whole-solve count (the Poisson comparison's denominator) equals
+    the per-kind sum (the headline's), and FP64 moves twice the bytes."""
+    import bench
+    n = 256
+    total = sum(bench.solve_kind_bytes(n, esz=4, refine=refine, fused=fused).values())
+    assert bench.method_bytes(n, 4, refine, fused=fused) == total
+    assert bench.method_bytes(n, 8, refine, fused=fused) == 2 * total
