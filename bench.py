@@ -364,9 +364,21 @@ def job_throughput(units_per_rank, world_size, ms):
     return units_per_rank * world_size / (ms * 1e-3)
 
 
-def _clock_ok(clk):
-    return not any(r in clk.get("reasons", []) for r in ("hw_slowdown", "hw_thermal_slowdown",
-                                                         "sw_thermal_slowdown"))
+def clock_verdict(clk, low=0.9):
+    """Whether a timed region's clock record passes the timing rules: no
+    hardware or thermal slowdown active, and the median SM clock under load
+    not stuck well below the maximum with no reason given (a clock lock left
+    by another user); a power cap is kept and noted."""
+    reasons = clk.get("reasons") or []
+    bad = [r for r in ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown") if r in reasons]
+    if bad:
+        return {"accepted": False, "why": ",".join(bad)}
+    sm, mx = clk.get("sm_mhz"), clk.get("sm_max_mhz")
+    if sm is None or not mx:
+        return {"accepted": None, "why": "no clock samples"}
+    if sm < low * mx and "sw_power_cap" not in reasons:
+        return {"accepted": False, "why": "pinned_low"}
+    return {"accepted": True, "why": "sw_power_cap" if "sw_power_cap" in reasons else ""}
 
 
 def run_gpu(args):
@@ -529,6 +541,7 @@ def run_gpu(args):
     launches = sum(c for _, c in kinds.values())
     mb = method_bytes(n, 4, HEAD_REFINE, fused)
     clocks = clk.summary()
+    clocks.update(clock_verdict(clocks))
     cfg = dict(CONFIG, parallelism="replicas" if ws > 1 else "1 GPU")
     out = {
         "metric": METRIC,

@@ -63,3 +63,24 @@ def test_counters_record(tmp_path, monkeypatch):
     assert bench.ncu_traffic("inverse") == e["dram_bytes_per_step"]
     monkeypatch.setattr(bench, "source_digest", lambda kind, which="headline": "changed")
     assert bench.ncu_traffic("inverse") is None
+
+
+def test_clock_record_and_verdict():
+    import bench
+    s = bench.ClockSampler(0)
+    # index, sm, max sm, power, active, hw_slowdown, hw_thermal, sw_thermal, sw_power_cap
+    s.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 2040, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 950.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    c = s.summary()
+    assert c["sm_mhz"] == 2070.0 and c["sm_max_mhz"] == 2070.0 and c["samples"] == 3
+    assert c["reasons"] == ["sw_power_cap"]
+    assert bench.clock_verdict(c) == {"accepted": True, "why": "sw_power_cap"}
+    assert bench.clock_verdict({"sm_mhz": 2070.0, "sm_max_mhz": 2070.0, "reasons": []})["accepted"] is True
+    v = bench.clock_verdict({"sm_mhz": 2000.0, "sm_max_mhz": 2070.0, "reasons": ["hw_thermal_slowdown"]})
+    assert v == {"accepted": False, "why": "hw_thermal_slowdown"}
+    # stuck well below the maximum with no reason: a leftover clock lock
+    assert bench.clock_verdict({"sm_mhz": 1400.0, "sm_max_mhz": 2070.0, "reasons": []}) == \
+        {"accepted": False, "why": "pinned_low"}
+    assert bench.clock_verdict({"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]})["accepted"] is None
